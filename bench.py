@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: ABFT Cholesky on one B300 (per rank), one JSON line on stdout.
+
+A step is one FP64 ABFT-protected blocked Cholesky factorization
+(full checksums, faults injected at 1 per 10 steps) of the n = 16384,
+block 256 matrix A = M M^T / n + I (M iid N(0, 1), seeded), resident in HBM:
+the working copy is reset from a pristine copy and factored; the report
+(events, counters) is read back.  The matrix (2.1 GB) is larger than L2, so
+no separate L2 flush is needed between steps.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded
+sample of the same workload instead (rank 0 only).
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+WORKLOAD = "FP64 ABFT Cholesky (full checksums, faults 1 per 10 steps), n=16384, block 256"
+METRIC = "ABFT Cholesky TFLOP/s & % peak at n=16384: FP64 vs BF16+IR at 1e-12 residual"
+CPU_SAMPLE_N = 4096   # oracle sample: one full ABFT Cholesky at this order, block 256 (~13 s)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--nb", type=int, default=256)
+    p.add_argument("--no-overhead", action="store_true", help="skip the NONE-mode overhead run")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def chol_flops(n):
+    return n ** 3 / 3.0
+
+
+def tmu_flops(n, nb):
+    """Algorithmic flops of the symmetric trailing updates of one factorization:
+    step k updates the lower triangle of an m_k x m_k block with a rank-kb
+    product, m_k (m_k + 1) kb flops (border and diagonal-block extras excluded)."""
+    tot = 0.0
+    for K0 in range(0, n, nb):
+        kb = min(nb, n - K0)
+        m = n - K0 - kb
+        tot += m * (m + 1) * kb
+    return tot
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- helpers
+def dgemm_peak(dev):
+    """Measured FP64 peak: cuBLAS DGEMM (torch.matmul float64, 4096^3), best of 3."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    best = 1e30
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2301_03166_b300", "csrc", "k_gemm_f64.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+# ncu-measured DRAM traffic of the FP64 TMU kernel (per step, summed over the
+# step's launches), valid only for the kernel source it was measured on.
+TMU_TRAFFIC = {}   # {source_hash: bytes_per_factorization}
+
+
+def cpu_baseline(steps=1, warm=0):
+    """The oracle as it stands (plain C, single thread) on one bounded sample:
+    a full FP64 ABFT Cholesky at n = CPU_SAMPLE_N, block 256."""
+    import oracle
+    from paper_2301_03166_b300 import workloads as W
+    n = CPU_SAMPLE_N
+    A = W.spd_mmt(n, seed=1000 + n)
+    faults = W.fault_schedule(n, 256, "cholesky", seed=2000 + n)
+    times = []
+    for i in range(warm + steps):
+        t0 = time.perf_counter()
+        oracle.potrf(A, 256, oracle.FULL, faults)
+        t = time.perf_counter() - t0
+        if i >= warm:
+            times.append(t)
+    return times, n
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, dev):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- arms
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    times, n = cpu_baseline(steps=args.steps, warm=args.warmup)
+    t = sum(times) / len(times)
+    v = chol_flops(n) / t / 1e12
+    sample = (f"one full FP64 ABFT Cholesky (full checksums, faults 1 per 10 steps) at n={n}, "
+              f"block 256, per step; TFLOP/s counted as n^3/3")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "nb": args.nb, "mode": "full",
+                   "cpu_sample_n": n},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    from paper_2301_03166_b300 import abft
+    from paper_2301_03166_b300 import workloads as W
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, nb = args.n, args.nb
+    peak = dgemm_peak(dev)
+    A0 = W.spd_mmt_torch(n, seed=1000 + n, device=dev)
+    A = torch.empty_like(A0)
+    faults = W.fault_schedule(n, nb, "cholesky", seed=2000 + n)
+    wsp = abft.Workspace()
+    expected = sorted((f[0], 0, f[2], f[3]) for f in faults)
+
+    def step(mode=abft.FULL, fl=faults):
+        A.copy_(A0)
+        rc, rep = abft.potrf(A, nb, mode, faults=fl, workspace=wsp)
+        return rc, rep
+
+    for _ in range(args.warmup):
+        rc, rep = step()
+    assert rc == 0, f"potrf returned {rc}"
+    events_ok = [(e[0], e[1], e[2], e[3]) for e in rep["loc"]] == expected
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    abft.timing_enable(True)
+    launches0 = abft.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rc, rep = step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    launches = abft.launch_count() - launches0
+    phases = abft.timing_read()
+    abft.timing_enable(False)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, ws, dev)
+    ms_step = ms / args.steps
+    value = ws * chol_flops(n) / (ms_step * 1e-3) / 1e12
+
+    # roofline of the dominant kernel (the FP64 trailing update)
+    tmu_ms, tmu_launches = phases["tmu"]
+    tmu_achieved = tmu_flops(n, nb) * args.steps / (tmu_ms * 1e-3) / 1e12 if tmu_ms > 0 else None
+    traffic = TMU_TRAFFIC.get(kernel_source_hash())
+    roofline = {"bound": "alu", "kernel": "k_gemm_f64 (FP64 DFMA trailing update)",
+                "achieved": tmu_achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (tmu_achieved / peak) if tmu_achieved else None,
+                "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (B300 has no FP64 tensor path; "
+                               "DFMA microbenchmark 1.13 TFLOP/s)",
+                "traffic": (traffic / tmu_launches * args.steps) if traffic else None,
+                "tmu_share_of_step": tmu_ms / ms if ms > 0 else None,
+                "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
+
+    overhead = None
+    if not args.no_overhead:
+        step(abft.NONE, ())
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(args.steps):
+            step(abft.NONE, ())
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_none = e0.elapsed_time(e1) / args.steps
+        overhead = {"ms_full": ms_step, "ms_none": ms_none,
+                    "abft_overhead_pct": 100.0 * (ms_step / ms_none - 1.0)}
+
+    e2e = None
+    if not args.no_e2e:
+        A0h = A0.cpu().pin_memory()
+        Lh = torch.empty_like(A0h).pin_memory()
+        def e2e_step():
+            A.copy_(A0h, non_blocking=True)
+            rc, rep = abft.potrf(A, nb, abft.FULL, faults=faults, workspace=wsp)
+            Lh.copy_(A, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            return rc
+        e2e_step()
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        t = (time.perf_counter() - t0) / args.steps
+        t = max_over_ranks(t, ws, dev)
+        e2e = {"value": ws * chol_flops(n) / t / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8 + ctypes.sizeof(abft.Report),
+               "ms_per_step": t * 1e3}
+        del A0h, Lh
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        times, ns = cpu_baseline()
+        cpu = {"value": chol_flops(ns) / times[0] / 1e12, "unit": "TFLOP/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"one full FP64 ABFT Cholesky (full checksums, faults 1 per 10 steps) "
+                         f"at n={ns}, block 256, {times[0]:.1f} s; TFLOP/s counted as n^3/3"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nb": nb, "mode": "full",
+                       "faults_per_step": len(faults), "l2": "inputs larger than L2 (2.1 GB matrix)",
+                       "parallelism": f"replicas x{ws}"},
+            "pct_of_fp64_peak": 100.0 * value / ws / peak,
+            "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
+                     "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
+                     "max_ratio": rep["max_ratio"], **(overhead or {})},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+        }), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * abft.h -- C ABI of the B300 ABFT one-sided decomposition library (libabft.so).
+ *
+ * The library factors dense matrices resident in GPU memory with blocked
+ * right-looking algorithms (Sec. 2.1 of "Improving Energy Saving of One-sided
+ * Matrix Decompositions on CPU-GPU Heterogeneous Systems", PPoPP'23: each
+ * iteration runs the panel decomposition PD, the panel update PU and the
+ * trailing-matrix update TMU) and protects every iteration with ABFT
+ * checksums (Sec. 3.1.2: checksums encoded per matrix block before the
+ * operation, carried through it, verified after each iteration; errors are
+ * located and corrected; single-side checksums tolerate 0D errors, full
+ * checksums 0D and 1D errors; error classes 0D / 1D / 2D).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are dense, ROW-MAJOR, FP64, with leading dimension ld >= max(1, n).
+ *  - All matrix, vector and workspace pointers are DEVICE pointers owned by the
+ *    caller; the library never allocates device memory.  `faults` and `rep`
+ *    are HOST pointers.  `stream` is a cudaStream_t (NULL = legacy stream).
+ *  - Workspace protocol: call with ws == NULL to receive the required size in
+ *    *ws_bytes (nothing is launched); then call again with ws pointing to at
+ *    least that many bytes (256-byte aligned) and *ws_bytes set to its size.
+ *  - Work is enqueued on `stream` asynchronously.  If rep != NULL the call
+ *    synchronizes the stream at the end and fills *rep; with rep == NULL the
+ *    call only enqueues work (no host synchronization).
+ *  - Return value: 0 on success; > 0 is the LAPACK-style info (1-based index
+ *    of the first non-positive pivot of potrf, or of the first exactly-zero
+ *    pivot of getrf; known only when rep != NULL); -i when argument i
+ *    (1-based) is invalid; ABFT_ERR_* below for the remaining failures.
+ *  - Checksum block size g equals the block size nb (one checksum tile per
+ *    matrix block, Sec. 3.1.2).  nb must be a positive multiple of 32 and at
+ *    most 512.
+ */
+#ifndef ABFT_H
+#define ABFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic of the trailing update (the PD, verify and correction always run in FP64). */
+typedef enum {
+    ABFT_F64 = 0,        /* FP64 everywhere */
+    ABFT_F32 = 1,        /* reserved */
+    ABFT_MIXED_BF16 = 2, /* TMU inputs BF16 with per-tile power-of-two scales, FP32 accumulate */
+    ABFT_MIXED_F16 = 3   /* TMU inputs FP16 with per-tile power-of-two scales, FP32 accumulate */
+} abft_dtype;
+
+/* Checksum strength (Sec. 3.1.2: single-side vs full checksum ABFT). */
+typedef enum {
+    ABFT_MODE_NONE = 0,   /* no checksums: the plain blocked factorization   */
+    ABFT_MODE_SINGLE = 1, /* column checksums + weighted column checksums    */
+    ABFT_MODE_FULL = 2    /* column and row checksums                        */
+} abft_mode;
+
+/* Kinds of injected fault (host-listed, numeric; Sec. 3.1.2 error classes). */
+typedef enum {
+    ABFT_FAULT_MEMORY = 0,  /* +delta at (row, col) after the TMU has stored its result   */
+    ABFT_FAULT_COMPUTE = 1, /* +delta added to (row, col) inside the TMU epilogue          */
+    ABFT_FAULT_ROW1D = 2,   /* +delta along row `row`, from col to the end of col's block  */
+    ABFT_FAULT_COL1D = 3,   /* +delta down column `col`, from row to the end of row's block */
+    ABFT_FAULT_PANEL = 4    /* +delta at (row, col) of the panel-update output, before its verify */
+} abft_fault_kind;
+
+/* Kinds of reported event. */
+typedef enum {
+    ABFT_EV_0D = 0,            /* single element located and corrected                    */
+    ABFT_EV_ROW = 1,           /* element of a 1D row error corrected                     */
+    ABFT_EV_COL = 2,           /* element of a 1D column error corrected                  */
+    ABFT_EV_UNCORRECTABLE = 3, /* block with a 2D (or unlocatable) error; row/col = origin */
+    ABFT_EV_CHECKSUM = 4,      /* checksum itself wrong, re-encoded; row/col = block origin */
+    ABFT_EV_PD = 5             /* panel-decomposition check failed (detect only)          */
+} abft_event_kind;
+
+/* A fault to inject (input) or an event that was handled (output).
+ * step: 0-based iteration; row, col: 0-based global indices; delta: the
+ * injected value, or for events the error size the checksums estimated. */
+typedef struct {
+    int32_t step;
+    int32_t kind;
+    int64_t row;
+    int64_t col;
+    double delta;
+} abft_fault;
+
+#define ABFT_MAX_LOC 64
+
+/* Result of one call (host memory, filled when rep != NULL). */
+typedef struct {
+    int64_t detected;          /* blocks (or PD checks) that raised a flag            */
+    int64_t corrected;         /* elements corrected                                  */
+    int64_t uncorrectable;     /* blocks or PD checks that could not be corrected     */
+    int64_t checksum_repaired; /* blocks whose checksums were re-encoded              */
+    int32_t nloc;              /* number of entries in loc (<= ABFT_MAX_LOC)          */
+    int32_t info;              /* as the return value's info                          */
+    abft_fault loc[ABFT_MAX_LOC]; /* events sorted by (step, row, col, kind); if more
+                                     than ABFT_MAX_LOC occurred, which ones are kept
+                                     is unspecified (the counters stay exact)         */
+    double max_ratio;          /* max |d| / tau over verified blocks without a flag   */
+    double tau;                /* detection threshold of the last verified step       */
+    int32_t ir_iters;          /* iterative refinement iterations (posv_ir)           */
+    int32_t reserved;
+    double backward_err;       /* final normwise backward error (posv_ir)             */
+} abft_report;
+
+#define ABFT_OK 0
+#define ABFT_ERR_UNCORRECTABLE (-1000) /* rep != NULL and an uncorrectable error was reported */
+#define ABFT_ERR_TIMEOUT (-1001)       /* a bounded device wait gave up                    */
+#define ABFT_ERR_CUDA (-1002)          /* a CUDA launch or runtime call failed             */
+#define ABFT_ERR_UNSUPPORTED (-1003)   /* valid but unsupported combination (e.g. dtype)   */
+
+/*
+ * abft_potrf -- ABFT-protected blocked Cholesky A = L L^T (lower).
+ * Sec. 2.1 (PD = Cholesky of the diagonal block, PU = triangular solve of the
+ * panel, TMU = symmetric rank-nb update); Sec. 3.1.2 (checksums).
+ *   n, nb      order and block size (nb multiple of 32, <= 512)
+ *   dtype      abft_dtype of the TMU
+ *   mode       abft_mode
+ *   A, lda     n x n row-major; only the lower triangle is read; on return it
+ *              holds L; the strict upper triangle is left as it was
+ *   faults     host array of nfaults faults to inject (NULL if nfaults == 0);
+ *              each must lie in the region its step updates: TMU kinds need
+ *              row, col >= (step+1) nb with col/nb <= row/nb; PANEL needs
+ *              row >= (step+1) nb and step nb <= col < (step+1) nb; step < N-1
+ *   tau_scale  multiplies the detection threshold tau = 8 u n nb max_i a_ii
+ *   rep        host report or NULL (see conventions)
+ *   ws, ws_bytes  workspace protocol (see conventions)
+ * Errors: -1 n < 0; -2 nb invalid; -3 dtype; -4 mode; -5 A NULL with n > 0;
+ * -6 lda < max(1,n); -7 faults invalid (or more than 4 COMPUTE faults in one
+ * step); -8 nfaults < 0; -9 tau_scale <= 0;
+ * -12 workspace too small.
+ */
+int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               const abft_fault* faults, int32_t nfaults, double tau_scale,
+               abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Diagnostics (no counterpart in the paper; the paper profiles per-operation
+ * times only to predict slack, Sec. 3.2.1).
+ * abft_timing_enable(on): when on != 0, every entry point records CUDA events
+ *   around its phases on its stream (0 PD + PD check, 1 PU + panel verify,
+ *   2 TMU, 3 fault injection + trailing verify, 4 encode / set-up), then
+ *   synchronizes its stream before returning; resets the accumulators.
+ * abft_timing_read(ms, count, nphase): accumulated milliseconds (and number of
+ *   timed intervals) per phase since the last enable.
+ * abft_launch_count(): number of kernels this library has launched so far.
+ */
+int abft_timing_enable(int32_t on);
+int abft_timing_read(double* ms, int64_t* count, int32_t nphase);
+int64_t abft_launch_count(void);
+
+/* Library version string. */
+const char* abft_version(void);
+
+/* Text for a return code. */
+const char* abft_strerror(int32_t code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABFT_H */

@@ -1,0 +1,181 @@
+"""Thin Python binding of libabft.so (ctypes): argument marshalling only.
+
+Every step of every factorization runs in the library's CUDA kernels; torch
+supplies device memory (matrices and workspace) and the current stream.
+There is no CPU fallback: if the compiled library is missing, or a tensor is
+not on a CUDA device, the call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+F64, F32, MIXED_BF16, MIXED_F16 = 0, 1, 2, 3
+NONE, SINGLE, FULL = 0, 1, 2
+F_MEMORY, F_COMPUTE, F_ROW1D, F_COL1D, F_PANEL = 0, 1, 2, 3, 4
+E_0D, E_ROW, E_COL, E_UNCORR, E_CKSUM, E_PD = 0, 1, 2, 3, 4, 5
+ERR_UNCORRECTABLE, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = -1000, -1001, -1002, -1003
+MAX_LOC = 64
+
+
+class Fault(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("row", ctypes.c_int64), ("col", ctypes.c_int64),
+                ("delta", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("detected", ctypes.c_int64), ("corrected", ctypes.c_int64),
+                ("uncorrectable", ctypes.c_int64), ("checksum_repaired", ctypes.c_int64),
+                ("nloc", ctypes.c_int32), ("info", ctypes.c_int32),
+                ("loc", Fault * MAX_LOC), ("max_ratio", ctypes.c_double),
+                ("tau", ctypes.c_double), ("ir_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double)]
+
+
+class AbftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+_i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+_sz = ctypes.POINTER(ctypes.c_size_t)
+
+_SIGNATURES = {
+    "abft_potrf": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
+                   ctypes.POINTER(Report), _vp, _sz, _vp],
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libabft.so (building it in-tree first when nvcc is available and
+    the sources are newer).  Raises if the library cannot be loaded."""
+    global _lib
+    if _lib is None:
+        if _build.stale():
+            try:
+                _build.build()
+            except Exception as e:  # no compiler here: use what is on disk, or fail
+                if not os.path.exists(_build.LIB):
+                    raise RuntimeError(f"libabft.so is missing and could not be built: {e}")
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libabft.so is missing; run paper_2301_03166_b300/build.py")
+        L = ctypes.CDLL(_build.LIB)
+        for name, argt in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = ctypes.c_int
+        L.abft_timing_enable.argtypes = [_i32]
+        L.abft_timing_enable.restype = ctypes.c_int
+        L.abft_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
+        L.abft_timing_read.restype = ctypes.c_int
+        L.abft_launch_count.restype = _i64
+        L.abft_version.restype = ctypes.c_char_p
+        L.abft_strerror.restype = ctypes.c_char_p
+        L.abft_strerror.argtypes = [_i32]
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().abft_strerror(int(code)).decode()
+
+
+def _faults(faults):
+    faults = list(faults or [])
+    arr = (Fault * max(1, len(faults)))()
+    for i, f in enumerate(faults):
+        arr[i].step, arr[i].kind = int(f[0]), int(f[1])
+        arr[i].row, arr[i].col, arr[i].delta = int(f[2]), int(f[3]), float(f[4])
+    return arr, len(faults)
+
+
+def report_dict(r):
+    return {
+        "detected": r.detected, "corrected": r.corrected,
+        "uncorrectable": r.uncorrectable, "checksum_repaired": r.checksum_repaired,
+        "info": r.info, "max_ratio": r.max_ratio, "tau": r.tau,
+        "ir_iters": r.ir_iters, "backward_err": r.backward_err,
+        "loc": [(r.loc[i].step, r.loc[i].kind, r.loc[i].row, r.loc[i].col, r.loc[i].delta)
+                for i in range(r.nloc)],
+    }
+
+
+def _check_matrix(A, name="A"):
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (no CPU fallback)")
+    if A.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError(f"{name} must be a row-major 2-D tensor (stride(1) == 1)")
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Workspace:
+    """Caller-owned device workspace reused across calls (grown on demand)."""
+
+    def __init__(self, device=None):
+        self.buf = None
+        self.device = device
+
+    def get(self, nbytes, device):
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+        return self.buf
+
+
+def potrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
+          workspace=None, stream=None, check=True):
+    """ABFT Cholesky in place: the lower triangle of A becomes L.
+    Returns (info_or_code, report dict or None)."""
+    _check_matrix(A)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    L = lib()
+    fa, nf = _faults(faults)
+    need = ctypes.c_size_t(0)
+    rc = L.abft_potrf(n, nb, dtype, mode, None, max(1, A.stride(0)), fa, nf, tau_scale,
+                      None, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    rep = Report() if report else None
+    size = ctypes.c_size_t(ws.numel())
+    rc = L.abft_potrf(n, nb, dtype, mode, ctypes.c_void_p(A.data_ptr()), max(1, A.stride(0)),
+                      fa, nf, tau_scale, ctypes.byref(rep) if rep is not None else None,
+                      ctypes.c_void_p(ws.data_ptr()), ctypes.byref(size), _stream(stream))
+    if check and rc < 0 and rc != ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    return rc, (report_dict(rep) if rep is not None else None)
+
+
+PHASES = ("pd", "pu", "tmu", "verify", "other")
+
+
+def timing_enable(on=True):
+    """Per-phase CUDA-event timing inside the library (resets the totals)."""
+    lib().abft_timing_enable(1 if on else 0)
+
+
+def timing_read():
+    ms = (ctypes.c_double * len(PHASES))()
+    cnt = (ctypes.c_int64 * len(PHASES))()
+    lib().abft_timing_read(ms, cnt, len(PHASES))
+    return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def launch_count():
+    return int(lib().abft_launch_count())

@@ -1,0 +1,357 @@
+// abft_api.cu -- host side of the C ABI: argument checks, workspace layout
+// and the per-iteration launch sequence of the blocked ABFT factorizations
+// (Sec. 2.1 PD / PU / TMU per iteration; Sec. 3.1.2 encode, carry, verify,
+// locate, correct).  No host synchronization happens inside the step loop;
+// the only device-to-host copy is the final status when a report is wanted.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace abft {
+
+// ------------------------------------------------ launch and time accounting
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<cudaEvent_t> g_pool;      // reusable events
+size_t g_pool_used = 0;
+std::vector<Mark> g_marks;            // marks of the current call
+double g_ms[PH_COUNT] = {0, 0, 0, 0, 0};
+long long g_calls[PH_COUNT] = {0, 0, 0, 0, 0};
+cudaEvent_t next_event() {
+    if (g_pool_used == g_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g_pool.push_back(e);
+    }
+    return g_pool[g_pool_used++];
+}
+}  // namespace
+
+bool timing_on() { return g_timing; }
+
+void timing_mark(int phase, int begin, cudaStream_t s) {
+    if (!g_timing) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    cudaEvent_t e = next_event();
+    if (!e) return;
+    cudaEventRecord(e, s);
+    if (begin) {
+        g_marks.push_back({phase, e, nullptr});
+    } else {
+        for (auto it = g_marks.rbegin(); it != g_marks.rend(); ++it)
+            if (it->phase == phase && it->b == nullptr) { it->b = e; break; }
+    }
+}
+
+cudaError_t timing_collect(cudaStream_t s) {
+    if (!g_timing) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (const Mark& m : g_marks) {
+        if (!m.b) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            g_ms[m.phase] += ms;
+            g_calls[m.phase] += 1;
+        }
+    }
+    g_marks.clear();
+    g_pool_used = 0;
+    return cudaSuccess;
+}
+
+}  // namespace abft
+
+using namespace abft;
+
+namespace {
+
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Byte offsets of the pieces of a Cholesky workspace.
+struct CholWs {
+    size_t st, cs, cr, xr, v, save, total;
+    int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
+    int64_t nt;
+};
+
+CholWs chol_ws(int64_t n, int64_t nb, int mode) {
+    CholWs w{};
+    w.nt = (n + nb - 1) / nb;
+    w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
+    size_t off = 0;
+    w.st = off; off = align_up(off + sizeof(DevStatus));
+    w.cs = off; off = align_up(off + sizeof(double) * (size_t)(w.nc * w.nt) * (size_t)n);
+    w.cr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n * (size_t)w.nt : 0));
+    w.xr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n : 0));
+    w.v = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)nb : 0));
+    w.save = off; off = align_up(off + sizeof(double) * (size_t)n * (size_t)nb);
+    w.total = off;
+    return w;
+}
+
+bool chol_fault_ok(const abft_fault& f, int64_t n, int64_t nb, int64_t N) {
+    if (f.step < 0 || f.step >= N - 1) return false;
+    int64_t K0 = (int64_t)f.step * nb, T0 = std::min(K0 + nb, n);
+    if (f.row < 0 || f.row >= n || f.col < 0 || f.col >= n) return false;
+    if (f.kind == ABFT_FAULT_PANEL) return f.row >= T0 && f.col >= K0 && f.col < T0;
+    if (f.kind < ABFT_FAULT_MEMORY || f.kind > ABFT_FAULT_PANEL) return false;
+    return f.row >= T0 && f.col >= T0 && f.col / nb <= f.row / nb;
+}
+
+bool event_less(const abft_fault& a, const abft_fault& b) {
+    if (a.step != b.step) return a.step < b.step;
+    if (a.row != b.row) return a.row < b.row;
+    if (a.col != b.col) return a.col < b.col;
+    return a.kind < b.kind;
+}
+
+// Copy the device status into *rep (synchronizes the stream).
+int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s) {
+    DevStatus h;
+    ABFT_CUDA_TRY(cudaMemcpyAsync(&h, dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    ABFT_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memset(rep, 0, sizeof(*rep));
+    rep->detected = (int64_t)h.detected;
+    rep->corrected = (int64_t)h.corrected;
+    rep->uncorrectable = (int64_t)h.uncorrectable;
+    rep->checksum_repaired = (int64_t)h.repaired;
+    rep->nloc = std::min(h.nloc, (int)ABFT_MAX_LOC);
+    rep->info = h.info;
+    for (int i = 0; i < rep->nloc; ++i) rep->loc[i] = h.loc[i];
+    std::sort(rep->loc, rep->loc + rep->nloc, event_less);
+    double r;
+    std::memcpy(&r, &h.max_ratio_bits, sizeof(r));
+    rep->max_ratio = r;
+    rep->tau = h.tau;
+    if (h.error) return ABFT_ERR_TIMEOUT;
+    if (h.info) return h.info;
+    if (h.uncorrectable) return ABFT_ERR_UNCORRECTABLE;
+    return ABFT_OK;
+}
+
+// Factor the kb x kb diagonal block at A (lower) in 64-column chunks.
+cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* st, cudaStream_t s) {
+    for (int64_t c = 0; c < kb; c += 64) {
+        int64_t w = std::min<int64_t>(64, kb - c);
+        double* Lc = A + c * lda + c;
+        cudaError_t e = launch_potf2_small(Lc, lda, w, K0 + c, st, s);
+        if (e != cudaSuccess) return e;
+        int64_t r = kb - c - w;
+        if (r <= 0) continue;
+        TrsmSeg seg{Lc + w * lda, lda, r};
+        e = launch_trsm_rlt(Lc, lda, w, &seg, 1, nullptr, nullptr, st, s);
+        if (e != cudaSuccess) return e;
+        GemmSeg g{};
+        g.A = Lc + w * lda; g.lda = lda;
+        g.B = Lc + w * lda; g.ldb = lda;
+        g.C = Lc + w * lda + w; g.ldc = lda;
+        g.M = r; g.N = r; g.K = w;
+        g.g = 64; g.row0 = 0; g.col0 = 0;
+        e = launch_gemm_f64(&g, 1, 0, nullptr, 0, st, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Blocked ABFT Cholesky step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
+int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
+               const abft_fault* faults, int32_t nfaults, double tau_scale, const CholWs& w,
+               char* base, cudaStream_t s) {
+    DevStatus* st = (DevStatus*)(base + w.st);
+    double* CS = (double*)(base + w.cs);
+    double* Cr = (double*)(base + w.cr);
+    double* xr = (double*)(base + w.xr);
+    double* v = (double*)(base + w.v);
+    double* save = (double*)(base + w.save);
+    const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt;
+    const bool full = mode == ABFT_MODE_FULL, check = mode != ABFT_MODE_NONE;
+
+    timing_mark(PH_OTHER, 1, s);
+    ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 0, s));
+    ABFT_CUDA_TRY(launch_tau_chol(A, lda, n, g, tau_scale, st, s));
+    // checksum tile sets (Sec. 3.1.2: per matrix block)
+    TileSet base_ts{};
+    base_ts.A = A; base_ts.lda = lda;
+    base_ts.cc = CS; base_ts.cw = CS + n; base_ts.ccI = nc * n;
+    base_ts.cr = Cr; base_ts.crs = nt; base_ts.crJ = 1;
+    base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
+    if (check) {
+        TileSet ts = base_ts;
+        ts.I0 = 0; ts.I1 = nt; ts.J0 = 0; ts.J1 = nt; ts.lower = 1;
+        ABFT_CUDA_TRY(launch_encode(ts, mode, s));
+    }
+    timing_mark(PH_OTHER, 0, s);
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
+        double* Akk = A + K0 * lda + K0;
+        // PD and its checksum check
+        timing_mark(PH_PD, 1, s);
+        ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, st, s));
+        if (check)
+            ABFT_CUDA_TRY(launch_chol_pd_check(Akk, lda, kb, CS + (k * nc) * n + K0, K0, (int)k,
+                                               full ? v : nullptr, mode, st, s));
+        timing_mark(PH_PD, 0, s);
+        if (m <= 0) break;
+        // PU: panel rows and the carried checksum rows through X L_kk^T = B
+        timing_mark(PH_PU, 1, s);
+        TrsmSeg segs[2] = {{A + T0 * lda + K0, lda, m},
+                           {CS + ((k + 1) * nc) * n + K0, n, (nt - k - 1) * nc}};
+        ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, full ? v : nullptr,
+                                      full ? xr + T0 : nullptr, st, s));
+        for (int f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)
+                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
+        if (check) {
+            TileSet ts = base_ts;
+            ts.cr = xr; ts.crs = 1; ts.crJ = 0;
+            ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k; ts.J1 = k + 1; ts.lower = 0;
+            ts.ncol_end = T0;
+            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+        }
+        timing_mark(PH_PU, 0, s);
+        // TMU with the checksum borders folded into the same launch
+        GemmSeg gs[3] = {};
+        gs[0].A = A + T0 * lda + K0; gs[0].lda = lda;
+        gs[0].B = A + T0 * lda + K0; gs[0].ldb = lda;
+        gs[0].C = A + T0 * lda + T0; gs[0].ldc = lda;
+        gs[0].M = m; gs[0].N = m; gs[0].K = kb;
+        gs[0].g = g; gs[0].row0 = T0; gs[0].col0 = T0;
+        int nseg = 1;
+        if (check) {  // border rows: c_I -= s_I L_J^T (and the weighted rows)
+            GemmSeg& b = gs[nseg++];
+            b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
+            b.B = A + T0 * lda + K0; b.ldb = lda;
+            b.C = CS + ((k + 1) * nc) * n + T0; b.ldc = n;
+            b.M = (nt - k - 1) * nc; b.N = m; b.K = kb;
+        }
+        if (full) {   // border columns: r_I -= L_I s_J^T
+            GemmSeg& b = gs[nseg++];
+            b.A = A + T0 * lda + K0; b.lda = lda;
+            b.B = CS + (k + 1) * n + K0; b.ldb = n;
+            b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
+            b.M = m; b.N = nt - k - 1; b.K = kb;
+        }
+        ComputeFault cf[MAX_CF];
+        int ncf = 0;
+        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                cf[ncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
+        timing_mark(PH_TMU, 1, s);
+        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, cf, ncf, st, s));
+        timing_mark(PH_TMU, 0, s);
+        timing_mark(PH_VERIFY, 1, s);
+        for (int f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
+                                        faults[f].kind == ABFT_FAULT_ROW1D ||
+                                        faults[f].kind == ABFT_FAULT_COL1D))
+                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
+        if (check) {
+            TileSet ts = base_ts;
+            ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 1;
+            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+        }
+        timing_mark(PH_VERIFY, 0, s);
+    }
+    timing_mark(PH_OTHER, 1, s);
+    ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 1, s));
+    timing_mark(PH_OTHER, 0, s);
+    return ABFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* abft_version(void) { return "abft-b300 0.1 (sm_103a)"; }
+
+int64_t abft_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int abft_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing = on != 0;
+    for (int i = 0; i < PH_COUNT; ++i) { g_ms[i] = 0.0; g_calls[i] = 0; }
+    g_marks.clear();
+    g_pool_used = 0;
+    return ABFT_OK;
+}
+
+int abft_timing_read(double* ms, int64_t* count, int32_t nphase) {
+    if (ms == nullptr || nphase < 0) return -1;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (int i = 0; i < nphase && i < PH_COUNT; ++i) {
+        ms[i] = g_ms[i];
+        if (count) count[i] = g_calls[i];
+    }
+    return ABFT_OK;
+}
+
+const char* abft_strerror(int32_t code) {
+    if (code == ABFT_OK) return "ok";
+    if (code > 0) return "non-positive or zero pivot (info)";
+    switch (code) {
+        case ABFT_ERR_UNCORRECTABLE: return "uncorrectable error reported by the checksums";
+        case ABFT_ERR_TIMEOUT: return "bounded device wait gave up";
+        case ABFT_ERR_CUDA: return "CUDA launch or runtime error";
+        case ABFT_ERR_UNSUPPORTED: return "unsupported combination of arguments";
+        default: return "invalid argument";
+    }
+}
+
+int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               const abft_fault* faults, int32_t nfaults, double tau_scale, abft_report* rep,
+               void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
+    if (dtype != ABFT_F64) return dtype < 0 || dtype > 3 ? -3 : ABFT_ERR_UNSUPPORTED;
+    if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -4;
+    if (n > 0 && A == nullptr && ws != nullptr) return -5;
+    if (lda < std::max<int64_t>(1, n)) return -6;
+    if (nfaults < 0) return -8;
+    if (nfaults > 0 && faults == nullptr) return -7;
+    if (!(tau_scale > 0.0)) return -9;
+    if (ws_bytes == nullptr) return -12;
+    const int64_t N = (n + nb - 1) / nb;
+    for (int f = 0; f < nfaults; ++f) {
+        if (!chol_fault_ok(faults[f], n, nb, N)) return -7;
+        int same = 0;  // compute faults are carried as TMU launch arguments
+        for (int h = 0; h < nfaults; ++h)
+            same += faults[h].kind == ABFT_FAULT_COMPUTE && faults[h].step == faults[f].step;
+        if (same > MAX_CF) return -7;
+    }
+    const CholWs w = chol_ws(n, nb, mode);
+    if (ws == nullptr) {
+        *ws_bytes = w.total;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < w.total) return -12;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    DevStatus* st = (DevStatus*)(base + w.st);
+    ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    if (n > 0) {
+        int rc = chol_steps(n, nb, mode, A, lda, faults, nfaults, tau_scale, w, base, s);
+        if (rc != ABFT_OK) return rc;
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    if (rep) return finish_report(st, rep, s);
+    return ABFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// common.cuh -- internal declarations shared by the CUDA translation units of
+// libabft.so (device status block, tile sets, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "abft.h"
+
+namespace abft {
+
+// Device-resident status of one factorization call.  Lives at the start of
+// the caller's workspace; zeroed at the start of every call.
+struct DevStatus {
+    int info;                          // 1-based first bad pivot (0 = none)
+    int nloc;                          // events appended (may exceed ABFT_MAX_LOC)
+    unsigned long long detected;
+    unsigned long long corrected;
+    unsigned long long uncorrectable;
+    unsigned long long repaired;
+    unsigned long long max_ratio_bits; // bit pattern of a non-negative double
+    double tau;                        // current detection threshold
+    double amax;                       // max |a_ij| of the input (LU) / max column norm (QR)
+    double umax;                       // running max |u_ij| (LU)
+    int error;                         // internal error code (timeouts)
+    int pad;
+    abft_fault loc[ABFT_MAX_LOC];
+};
+
+enum { MODE_NONE = 0, MODE_SINGLE = 1, MODE_FULL = 2 };
+enum { EV_0D = 0, EV_ROW = 1, EV_COL = 2, EV_UNCORR = 3, EV_CKSUM = 4, EV_PD = 5 };
+
+__device__ __forceinline__ void record_event(DevStatus* st, int step, int kind, int64_t row,
+                                             int64_t col, double d) {
+    int idx = atomicAdd(&st->nloc, 1);
+    if (idx < ABFT_MAX_LOC) {
+        abft_fault& e = st->loc[idx];
+        e.step = step;
+        e.kind = kind;
+        e.row = row;
+        e.col = col;
+        e.delta = d;
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+    if (!(v >= 0.0)) return;
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// A set of g x g checksum tiles (I, J), I in [I0, I1), J in [J0, J1),
+// optionally restricted to J <= I (lower block triangle).  Element pointers:
+//   T(I,J)  = A  + (I g) lda + (J g)
+//   cc(I,J) = cc + I ccI + J g           (column sums, a row vector)
+//   cw(I,J) = cw + I ccI + J g           (weighted column sums)
+//   cr(I,J) = cr + (I g) crs + J crJ     (row sums, stride crs)
+// Rows end at nrow_end, columns at ncol_end (global indices).
+struct TileSet {
+    double* A;
+    int64_t lda;
+    double* cc;
+    double* cw;
+    int64_t ccI;
+    double* cr;
+    int64_t crs, crJ;
+    int64_t g;
+    int64_t I0, I1, J0, J1;
+    int lower;
+    int64_t nrow_end, ncol_end;
+};
+
+cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s);
+cudaError_t launch_verify(const TileSet& ts, int mode, int step, DevStatus* st, cudaStream_t s);
+cudaError_t launch_inject(double* A, int64_t lda, int64_t n, int64_t g, const abft_fault& f,
+                          cudaStream_t s);
+cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, double* save,
+                               int restore, cudaStream_t s);
+cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
+                            DevStatus* st, cudaStream_t s);
+
+// FP64 update C -= A_op * B_op^T (NT) or A_op * B_op (NN), over up to three
+// segments (the main tiles and the checksum border rows / columns).
+struct GemmSeg {
+    const double* A;   // A[i*lda + p]
+    int64_t lda;
+    const double* B;   // NT: B[j*ldb + p];  NN: B[p*ldb + j]
+    int64_t ldb;
+    double* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    // lower-block mask: element (i, j) is updated only when
+    // (i + row0) / g >= (j + col0) / g  (g == 0: no mask)
+    int64_t g, row0, col0;
+};
+struct ComputeFault {
+    int64_t row, col;  // indices local to segment 0, -1 = none
+    double delta;
+};
+enum { MAX_CF = 4 };
+cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int b_kmajor, const ComputeFault* cf,
+                            int ncf, const DevStatus* st, cudaStream_t s);
+
+cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_base,
+                               DevStatus* st, cudaStream_t s);
+// X L^T = B for the rows of up to two row segments (in place); L lower nb x nb.
+// If v != NULL, x[i] = B_i . v is stored for the rows of segment 0 before the solve.
+struct TrsmSeg {
+    double* B;
+    int64_t ldb;
+    int64_t rows;
+};
+cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
+                            int nseg, const double* v, double* x, const DevStatus* st,
+                            cudaStream_t s);
+cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
+                                 int64_t K0, int step, double* v, int mode, DevStatus* st,
+                                 cudaStream_t s);
+
+// Kernel launch accounting (every launcher calls note_launch once per kernel).
+void note_launch();
+
+// Per-phase GPU time accounting with CUDA events on the launch stream.
+enum { PH_PD = 0, PH_PU = 1, PH_TMU = 2, PH_VERIFY = 3, PH_OTHER = 4, PH_COUNT = 5 };
+bool timing_on();
+void timing_mark(int phase, int begin, cudaStream_t s);
+cudaError_t timing_collect(cudaStream_t s);
+
+}  // namespace abft
+
+#define ABFT_CUDA_TRY(expr)                                  \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return ABFT_ERR_CUDA;         \
+    } while (0)

@@ -1,0 +1,364 @@
+// k_checksum.cu -- checksum encode, verify / locate / correct, fault injection,
+// diagonal-block mirroring and the detection threshold (Sec. 3.1.2 ABFT:
+// encode per matrix block before the operation, verify the checksum relation
+// after it, locate and correct; 0D / 1D / 2D error classes).
+//
+// One CTA handles one g x g checksum tile (g <= 512).  Warp w sums rows
+// w, w+8, ...; lane l holds the running column sums of columns l + 32 t, so
+// every global load is a coalesced 256-byte row segment and the tile is read
+// from HBM exactly once.  Row sums use warp shuffles.  All reductions run in a
+// fixed order, so repeated runs give identical sums.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxG = 512;
+constexpr int kMaxT = kMaxG / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void tile_coords(const TileSet& ts, int64_t idx, int64_t& I, int64_t& J) {
+    if (ts.lower) {
+        // (a, b), a >= b, in row-major order of the lower triangle
+        int64_t a = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+        while (a * (a + 1) / 2 > idx) --a;
+        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+        I = ts.I0 + a;
+        J = ts.J0 + (idx - a * (a + 1) / 2);
+    } else {
+        int64_t nJ = ts.J1 - ts.J0;
+        I = ts.I0 + idx / nJ;
+        J = ts.J0 + idx % nJ;
+    }
+}
+
+// Sums of one tile into shared memory: colsum[j], wsum[j] (weights 1..nr,
+// single mode), rowsum[i] (full mode).
+template <int MODE>
+__device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* colsum,
+                          double* wsum, double* rowsum, double (*part)[kMaxG]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = (nc + 31) >> 5;
+    double acc[kMaxT], wacc[kMaxT];
+#pragma unroll
+    for (int t = 0; t < kMaxT; ++t) { acc[t] = 0.0; wacc[t] = 0.0; }
+    for (int i = warp; i < nr; i += kWarps) {
+        const double* row = T + (int64_t)i * ldt;
+        double rs = 0.0;
+        const double wi = (double)(i + 1);
+#pragma unroll
+        for (int t = 0; t < kMaxT; ++t) {
+            if (t < nt) {
+                int j = lane + 32 * t;
+                double v = (j < nc) ? row[j] : 0.0;
+                acc[t] += v;
+                if (MODE == MODE_SINGLE) wacc[t] = fma(wi, v, wacc[t]);
+                rs += v;
+            }
+        }
+        if (MODE == MODE_FULL) {
+            rs = warp_sum(rs);
+            if (lane == 0) rowsum[i] = rs;
+        }
+    }
+    // combine the per-warp column partial sums in warp order
+#pragma unroll
+    for (int t = 0; t < kMaxT; ++t)
+        if (t < nt) part[warp][lane + 32 * t] = acc[t];
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += part[w][j];
+        colsum[j] = s;
+    }
+    __syncthreads();
+    if (MODE == MODE_SINGLE) {
+#pragma unroll
+        for (int t = 0; t < kMaxT; ++t)
+            if (t < nt) part[warp][lane + 32 * t] = wacc[t];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += part[w][j];
+            wsum[j] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void tile_extent(const TileSet& ts, int64_t I, int64_t J, int& nr,
+                                            int& nc) {
+    int64_t r0 = I * ts.g, c0 = J * ts.g;
+    int64_t a = ts.nrow_end - r0, b = ts.ncol_end - c0;
+    nr = (int)(a < ts.g ? a : ts.g);
+    nc = (int)(b < ts.g ? b : ts.g);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
+    __shared__ double part[kWarps][kMaxG];
+    __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
+    int64_t I, J;
+    tile_coords(ts, blockIdx.x, I, J);
+    int nr, nc;
+    tile_extent(ts, I, J, nr, nc);
+    if (nr <= 0 || nc <= 0) return;
+    const double* T = ts.A + I * ts.g * ts.lda + J * ts.g;
+    tile_sums<MODE>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    double* cc = ts.cc + I * ts.ccI + J * ts.g;
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        cc[j] = colsum[j];
+        if (MODE == MODE_SINGLE) ts.cw[I * ts.ccI + J * ts.g + j] = wsum[j];
+    }
+    if (MODE == MODE_FULL) {
+        double* cr = ts.cr + I * ts.g * ts.crs + J * ts.crJ;
+        for (int i = threadIdx.x; i < nr; i += kThreads) cr[(int64_t)i * ts.crs] = rowsum[i];
+    }
+}
+
+// Verify, classify and correct one tile.  Flags: |d| > tau (NaN flags).
+// Full mode: 1 row + 1 col -> 0D (T[i][j] -= d^c_j when |d^c_j - d^r_i| <= tau,
+// else uncorrectable); 1 row + >=2 cols -> 1D row (T[i][j] -= d^c_j);
+// >=2 rows + 1 col -> 1D column (T[i][j] -= d^r_i); one side only -> the
+// checksum is wrong, re-encode it; >=2 rows and >=2 cols -> 2D, uncorrectable.
+// Single mode: each flagged column is located at i = rint(d^w_j / d^c_j) - 1
+// (accepted within 0.05 of an integer and inside the tile) and corrected by d^c_j.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevStatus* st) {
+    __shared__ double part[kWarps][kMaxG];
+    __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
+    __shared__ int s_nfc, s_nfr, s_fc, s_fr;
+    __shared__ double s_dmax[kWarps];
+    if (st->info != 0) return;
+    int64_t I, J;
+    tile_coords(ts, blockIdx.x, I, J);
+    int nr, nc;
+    tile_extent(ts, I, J, nr, nc);
+    if (nr <= 0 || nc <= 0) return;
+    const int64_t r0 = I * ts.g, c0 = J * ts.g;
+    double* T = ts.A + r0 * ts.lda + c0;
+    double* cc = ts.cc + I * ts.ccI + J * ts.g;
+    double* cw = (MODE == MODE_SINGLE) ? ts.cw + I * ts.ccI + J * ts.g : nullptr;
+    double* cr = (MODE == MODE_FULL) ? ts.cr + r0 * ts.crs + J * ts.crJ : nullptr;
+    if (threadIdx.x == 0) { s_nfc = 0; s_nfr = 0; s_fc = 1 << 30; s_fr = 1 << 30; }
+    tile_sums<MODE>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    const double tau = st->tau;
+    double dmax = 0.0;
+    // d = recomputed - carried, kept in place of the sums
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        double d = colsum[j] - cc[j];
+        colsum[j] = d;
+        if (MODE == MODE_SINGLE) wsum[j] = wsum[j] - cw[j];
+        double a = fabs(d);
+        if (!(a <= tau)) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
+        if (a > dmax) dmax = a;
+    }
+    if (MODE == MODE_FULL)
+        for (int i = threadIdx.x; i < nr; i += kThreads) {
+            double d = rowsum[i] - cr[(int64_t)i * ts.crs];
+            rowsum[i] = d;
+            double a = fabs(d);
+            if (!(a <= tau)) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
+            if (a > dmax) dmax = a;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0) s_dmax[threadIdx.x >> 5] = dmax;
+    __syncthreads();
+    const int nfc = s_nfc, nfr = s_nfr, fc = s_fc, fr = s_fr;
+    if (nfc == 0 && nfr == 0) {
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kWarps; ++w) m = fmax(m, s_dmax[w]);
+            if (tau > 0.0) atomic_max_nonneg(&st->max_ratio_bits, m / tau);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) atomicAdd(&st->detected, 1ull);
+    if (MODE == MODE_SINGLE) {
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            double dc = colsum[j];
+            if (fabs(dc) <= tau) continue;
+            double rho = wsum[j] / dc;
+            double ri = rint(rho);
+            int64_t i = (int64_t)ri - 1;
+            if (fabs(rho - ri) <= 0.05 && i >= 0 && i < nr) {
+                T[i * ts.lda + j] -= dc;
+                atomicAdd(&st->corrected, 1ull);
+                record_event(st, step, EV_0D, r0 + i, c0 + j, dc);
+            } else {
+                atomicAdd(&st->uncorrectable, 1ull);
+                record_event(st, step, EV_UNCORR, r0, c0 + j, dc);
+            }
+        }
+        return;
+    }
+    if (nfr == 1 && nfc == 1) {
+        if (threadIdx.x == 0) {
+            double dc = colsum[fc], dr = rowsum[fr];
+            if (fabs(dc - dr) <= tau) {
+                T[(int64_t)fr * ts.lda + fc] -= dc;
+                atomicAdd(&st->corrected, 1ull);
+                record_event(st, step, EV_0D, r0 + fr, c0 + fc, dc);
+            } else {
+                atomicAdd(&st->uncorrectable, 1ull);
+                record_event(st, step, EV_UNCORR, r0, c0, dc);
+            }
+        }
+    } else if (nfr == 1 && nfc >= 2) {
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            double dc = colsum[j];
+            if (fabs(dc) <= tau) continue;
+            T[(int64_t)fr * ts.lda + j] -= dc;
+            atomicAdd(&st->corrected, 1ull);
+            record_event(st, step, EV_ROW, r0 + fr, c0 + j, dc);
+        }
+    } else if (nfr >= 2 && nfc == 1) {
+        for (int i = threadIdx.x; i < nr; i += kThreads) {
+            double dr = rowsum[i];
+            if (fabs(dr) <= tau) continue;
+            T[(int64_t)i * ts.lda + fc] -= dr;
+            atomicAdd(&st->corrected, 1ull);
+            record_event(st, step, EV_COL, r0 + i, c0 + fc, dr);
+        }
+    } else if (nfr == 0 || nfc == 0) {
+        // the checksum itself is wrong: re-encode it from the data
+        for (int j = threadIdx.x; j < nc; j += kThreads) cc[j] += colsum[j];
+        for (int i = threadIdx.x; i < nr; i += kThreads) cr[(int64_t)i * ts.crs] += rowsum[i];
+        if (threadIdx.x == 0) {
+            atomicAdd(&st->repaired, 1ull);
+            record_event(st, step, EV_CKSUM, r0, c0, 0.0);
+        }
+    } else if (threadIdx.x == 0) {
+        atomicAdd(&st->uncorrectable, 1ull);
+        record_event(st, step, EV_UNCORR, r0, c0, 0.0);
+    }
+}
+
+__global__ void k_inject(double* A, int64_t lda, int64_t row, int64_t col, int64_t len, int along_row,
+                         double delta) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    if (along_row) A[row * lda + col + t] += delta;
+    else A[(row + t) * lda + col] += delta;
+}
+
+// Save the strict upper triangle of every nb x nb diagonal block and mirror the
+// lower triangle into it (restore = 1 puts the saved values back).
+__global__ void k_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, double* save,
+                              int restore) {
+    int64_t K0 = blockIdx.x * nb;
+    int64_t kb = n - K0 < nb ? n - K0 : nb;
+    for (int64_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+        int64_t i = e / kb, j = e % kb;
+        if (j <= i) continue;
+        double* up = A + (K0 + i) * lda + K0 + j;
+        double* sv = save + (K0 + i) * nb + j;
+        if (restore) {
+            *up = *sv;
+        } else {
+            *sv = *up;
+            *up = A[(K0 + j) * lda + K0 + i];
+        }
+    }
+}
+
+// tau = tau_scale * 8 * u * n * g * max_i a_ii (left to right).
+__global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
+                           DevStatus* st) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double d = A[i * lda + i];
+        if (d > m) m = d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        double t = tau_scale * 8.0;
+        t *= 0x1p-53;
+        t *= (double)n;
+        t *= (double)g;
+        t *= m;
+        st->tau = t;
+    }
+}
+
+int64_t tile_count(const TileSet& ts) {
+    if (ts.lower) {
+        int64_t a = ts.I1 - ts.I0;
+        return a * (a + 1) / 2;
+    }
+    return (ts.I1 - ts.I0) * (ts.J1 - ts.J0);
+}
+
+}  // namespace
+
+cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s) {
+    int64_t nt = tile_count(ts);
+    if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
+    if (mode == MODE_FULL) k_encode<MODE_FULL><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    else k_encode<MODE_SINGLE><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_verify(const TileSet& ts, int mode, int step, DevStatus* st, cudaStream_t s) {
+    int64_t nt = tile_count(ts);
+    if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
+    if (mode == MODE_FULL) k_verify<MODE_FULL><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
+    else k_verify<MODE_SINGLE><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(double* A, int64_t lda, int64_t n, int64_t g, const abft_fault& f,
+                          cudaStream_t s) {
+    int64_t len = 1;
+    int along_row = 1;
+    if (f.kind == ABFT_FAULT_ROW1D) {
+        int64_t end = (f.col / g + 1) * g;
+        if (end > n) end = n;
+        len = end - f.col;
+    } else if (f.kind == ABFT_FAULT_COL1D) {
+        int64_t end = (f.row / g + 1) * g;
+        if (end > n) end = n;
+        len = end - f.row;
+        along_row = 0;
+    }
+    k_inject<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(A, lda, f.row, f.col, len, along_row,
+                                                          f.delta);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, double* save,
+                               int restore, cudaStream_t s) {
+    int64_t nblk = (n + nb - 1) / nb;
+    if (nblk <= 0) return cudaSuccess;
+    k_mirror_diag<<<(unsigned)nblk, 256, 0, s>>>(A, lda, n, nb, save, restore);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
+                            DevStatus* st, cudaStream_t s) {
+    k_tau_chol<<<1, 1024, 0, s>>>(A, lda, n, g, tau_scale, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft

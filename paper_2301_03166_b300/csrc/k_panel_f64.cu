@@ -1,0 +1,266 @@
+// k_panel_f64.cu -- FP64 panel kernels of the blocked Cholesky (Sec. 2.1:
+// PD = factorization of the diagonal block, PU = triangular solve of the
+// panel below it) and the PD checksum check (Sec. 3.1.2).
+//
+// The diagonal block is factored by the host in 64-column chunks: a one-CTA
+// Cholesky of the 64 x 64 leaf in shared memory, a solve of the rows below
+// it, and a rank-64 update (the DFMA tile kernel).  Solves use true division
+// by the diagonal, never a reciprocal, so integer inputs stay exact.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int LEAF = 64;
+
+// Unblocked right-looking Cholesky of an nb x nb (nb <= 64) lower block in
+// shared memory.  On a non-positive or NaN pivot at column j the first such
+// index info_base + j + 1 is recorded and the block is left as it is.
+__global__ void __launch_bounds__(256) k_potf2_small(double* A, int64_t lda, int nb,
+                                                     int64_t info_base, DevStatus* st) {
+    __shared__ double a[LEAF][LEAF + 1];
+    __shared__ int fail;
+    if (st->info != 0) return;
+    const int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        int i = e / nb, j = e % nb;
+        if (j <= i) a[i][j] = A[(int64_t)i * lda + j];
+    }
+    if (t == 0) fail = -1;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (t == 0) {
+            double d = a[j][j];
+            if (!(d > 0.0)) fail = j;
+            else a[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail >= 0) break;
+        const double djj = a[j][j];
+        for (int i = j + 1 + t; i < nb; i += blockDim.x) a[i][j] = a[i][j] / djj;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = t; e < m * m; e += blockDim.x) {
+            int i = j + 1 + e / m, l = j + 1 + e % m;
+            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        }
+        __syncthreads();
+    }
+    if (fail >= 0) {
+        if (t == 0) atomicCAS(&st->info, 0, (int)(info_base + fail + 1));
+        return;
+    }
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        int i = e / nb, j = e % nb;
+        if (j <= i) A[(int64_t)i * lda + j] = a[i][j];
+    }
+}
+
+constexpr int RB = 32;     // rows per CTA
+constexpr int CW = 32;     // column chunk
+constexpr int TT = 256;
+
+struct TrsmArgs {
+    const double* L;
+    int64_t ldl;
+    int nb;
+    TrsmSeg seg[2];
+    int64_t start[3];
+    int nseg;
+    const double* v;
+    double* x;
+    const DevStatus* st;
+};
+
+// Solve X L^T = B for RB rows at a time (in place), L lower nb x nb.
+// Columns are processed in chunks of 32: X[:, c] -= X[:, :c] L[c, :c]^T
+// (all threads), then a per-row forward substitution inside the chunk.
+__global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
+    extern __shared__ double smem[];
+    const int ldx = a.nb + 1;
+    double* X = smem;                       // RB x (nb + 1)
+    double* Ls = smem + RB * ldx;           // CW x (CW + 1)
+    if (a.st && a.st->info != 0) return;
+    const int64_t bid = blockIdx.x;
+    const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    const TrsmSeg& g = a.seg[s];
+    const int64_t r0 = (bid - a.start[s]) * RB;
+    const int nr = (int)((g.rows - r0) < RB ? (g.rows - r0) : RB);
+    const int nb = a.nb, t = threadIdx.x;
+    for (int e = t; e < RB * nb; e += TT) {
+        int r = e / nb, p = e % nb;
+        X[r * ldx + p] = (r < nr) ? g.B[(r0 + r) * g.ldb + p] : 0.0;
+    }
+    __syncthreads();
+    if (a.v != nullptr && s == 0) {  // carried row sums x = B v, before the solve
+        const int warp = t >> 5, lane = t & 31;
+        for (int r = warp; r < nr; r += TT / 32) {
+            double acc = 0.0;
+            for (int p = lane; p < nb; p += 32) acc = fma(X[r * ldx + p], a.v[p], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) a.x[r0 + r] = acc;
+        }
+        __syncthreads();
+    }
+    const int gr = t >> 3, gq = (t & 7) * 4;  // GEMM part: row gr, cols gq..gq+3
+    for (int c0 = 0; c0 < nb; c0 += CW) {
+        const int w = (nb - c0) < CW ? (nb - c0) : CW;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int p0 = 0; p0 < c0; p0 += CW) {
+            __syncthreads();
+            for (int e = t; e < CW * CW; e += TT) {
+                int q = e / CW, pp = e % CW;
+                Ls[q * (CW + 1) + pp] = (q < w) ? a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int pp = 0; pp < CW; ++pp) {
+                double xv = X[gr * ldx + p0 + pp];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(xv, Ls[(gq + u) * (CW + 1) + pp], acc[u]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (gq + u < w) X[gr * ldx + c0 + gq + u] -= acc[u];
+        for (int e = t; e < CW * CW; e += TT) {
+            int q = e / CW, pp = e % CW;
+            Ls[q * (CW + 1) + pp] = (q < w && pp <= q) ? a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp] : 0.0;
+        }
+        __syncthreads();
+        if (t < RB) {
+            double* xr = X + t * ldx + c0;
+            for (int jj = 0; jj < w; ++jj) {
+                double v = xr[jj];
+                for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
+                xr[jj] = v / Ls[jj * (CW + 1) + jj];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < nr * nb; e += TT) {
+        int r = e / nb, p = e % nb;
+        g.B[(r0 + r) * g.ldb + p] = X[r * ldx + p];
+    }
+}
+
+// PD check on column sums: 1^T A_kk (carried, cc) vs (1^T L) L^T, and, when
+// v != NULL, v = L^{-T} 1 (blocked back substitution, chunks of 32).
+__global__ void __launch_bounds__(512) k_chol_pd_check(const double* L, int64_t ldl, int nb,
+                                                       const double* cc, int64_t K0, int step,
+                                                       double* v, int check, DevStatus* st) {
+    __shared__ double cs[512];
+    __shared__ double tv[512];
+    if (st->info != 0) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    if (check) {
+        for (int p = t; p < nb; p += blockDim.x) {
+            double s = 0.0;
+            for (int q = p; q < nb; ++q) s += L[(int64_t)q * ldl + p];
+            cs[p] = s;
+        }
+        __syncthreads();
+        const double tau = st->tau;
+        for (int j = warp; j < nb; j += nw) {
+            double y = 0.0;
+            for (int p = lane; p <= j; p += 32) y = fma(cs[p], L[(int64_t)j * ldl + p], y);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane == 0) {
+                double d = y - cc[j];
+                if (!(fabs(d) <= tau)) {
+                    atomicAdd(&st->detected, 1ull);
+                    atomicAdd(&st->uncorrectable, 1ull);
+                    record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+                }
+            }
+        }
+    }
+    if (v == nullptr) return;
+    for (int p = t; p < nb; p += blockDim.x) tv[p] = 1.0;
+    __syncthreads();
+    for (int c1 = nb; c1 > 0; c1 -= 32) {
+        const int c0 = c1 - 32 > 0 ? c1 - 32 : 0;
+        if (warp == 0) {
+            const int p = c0 + lane;
+            double tp = (p < c1) ? tv[p] : 0.0;
+            for (int j = c1 - 1; j >= c0; --j) {
+                double tj = __shfl_sync(0xffffffffu, tp, j - c0);
+                double vj = tj / L[(int64_t)j * ldl + j];
+                if (p == j) tp = vj;
+                if (p < j) tp -= L[(int64_t)j * ldl + p] * vj;
+            }
+            if (p < c1) tv[p] = tp;
+        }
+        __syncthreads();
+        for (int p = t; p < c0; p += blockDim.x) {
+            double s = tv[p];
+            for (int j = c0; j < c1; ++j) s -= L[(int64_t)j * ldl + p] * tv[j];
+            tv[p] = s;
+        }
+        __syncthreads();
+    }
+    for (int p = t; p < nb; p += blockDim.x) v[p] = tv[p];
+}
+
+}  // namespace
+
+cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_base,
+                               DevStatus* st, cudaStream_t s) {
+    k_potf2_small<<<1, 256, 0, s>>>(A, lda, (int)nb, info_base, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
+                            int nseg, const double* v, double* x, const DevStatus* st,
+                            cudaStream_t s) {
+    TrsmArgs a{};
+    a.L = L;
+    a.ldl = ldl;
+    a.nb = (int)nb;
+    a.nseg = 0;
+    int64_t total = 0;
+    for (int i = 0; i < nseg; ++i) {
+        if (segs[i].rows <= 0) {
+            if (i == 0) v = nullptr;  // x belongs to segment 0
+            continue;
+        }
+        a.seg[a.nseg] = segs[i];
+        a.start[a.nseg] = total;
+        total += (segs[i].rows + RB - 1) / RB;
+        a.nseg++;
+    }
+    if (total == 0) return cudaSuccess;
+    a.start[a.nseg] = total;
+    a.v = v;
+    a.x = x;
+    a.st = st;
+    size_t smem = (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((RB * 513 + CW * (CW + 1)) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_trsm_rlt<<<(unsigned)total, TT, smem, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
+                                 int64_t K0, int step, double* v, int mode, DevStatus* st,
+                                 cudaStream_t s) {
+    k_chol_pd_check<<<1, 512, 0, s>>>(L, ldl, (int)nb, cc, K0, step, v, mode != MODE_NONE ? 1 : 0,
+                                      st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft
