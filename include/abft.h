@@ -110,6 +110,7 @@ typedef struct {
 #define ABFT_ERR_TIMEOUT (-1001)       /* a bounded device wait gave up                    */
 #define ABFT_ERR_CUDA (-1002)          /* a CUDA launch or runtime call failed             */
 #define ABFT_ERR_UNSUPPORTED (-1003)   /* valid but unsupported combination (e.g. dtype)   */
+#define ABFT_ERR_TOO_LARGE (-1004)     /* the problem needs more than the built-in scratch */
 
 /*
  * abft_potrf -- ABFT-protected blocked Cholesky A = L L^T (lower).
@@ -135,6 +136,28 @@ typedef struct {
 int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                const abft_fault* faults, int32_t nfaults, double tau_scale,
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it exists for host programs whose
+ * own allocator or arena owns the whole GPU (or that may not grow the
+ * process's device footprint) and therefore can neither call cudaMalloc nor
+ * pass a workspace.  Arguments and results are those of abft_potrf without
+ * ws / ws_bytes; A is still the caller's.  The workspace is a built-in device
+ * array of abft_noalloc_capacity() bytes (16 MiB), present on every GPU where
+ * the library's device code is loaded and kept there until the process
+ * exits; a problem whose abft_potrf workspace would exceed it is rejected with
+ * ABFT_ERR_TOO_LARGE (for example, FULL mode fits n = 4096 with nb <= 256).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array, so calls whose GPU work overlaps (on different
+ * streams, or from different threads) race; serialize them.  The function
+ * itself performs no device allocation.
+ */
+int abft_potrf_noalloc(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+                       const abft_fault* faults, int32_t nfaults, double tau_scale,
+                       abft_report* rep, void* stream);
+size_t abft_noalloc_capacity(void);
 
 /*
  * Diagnostics (no counterpart in the paper; the paper profiles per-operation

@@ -16,7 +16,7 @@ F64, F32, MIXED_BF16, MIXED_F16 = 0, 1, 2, 3
 NONE, SINGLE, FULL = 0, 1, 2
 F_MEMORY, F_COMPUTE, F_ROW1D, F_COL1D, F_PANEL = 0, 1, 2, 3, 4
 E_0D, E_ROW, E_COL, E_UNCORR, E_CKSUM, E_PD = 0, 1, 2, 3, 4, 5
-ERR_UNCORRECTABLE, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = -1000, -1001, -1002, -1003
+ERR_UNCORRECTABLE, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_TOO_LARGE = -1000, -1001, -1002, -1003, -1004
 MAX_LOC = 64
 
 
@@ -46,6 +46,8 @@ _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
+    "abft_potrf_noalloc": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
+                           ctypes.POINTER(Report), _vp],
     "abft_potrf": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
 }
@@ -78,6 +80,7 @@ def lib():
         L.abft_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         L.abft_timing_read.restype = ctypes.c_int
         L.abft_launch_count.restype = _i64
+        L.abft_noalloc_capacity.restype = ctypes.c_size_t
         L.abft_version.restype = ctypes.c_char_p
         L.abft_strerror.restype = ctypes.c_char_p
         L.abft_strerror.argtypes = [_i32]

@@ -310,6 +310,7 @@ const char* abft_strerror(int32_t code) {
         case ABFT_ERR_TIMEOUT: return "bounded device wait gave up";
         case ABFT_ERR_CUDA: return "CUDA launch or runtime error";
         case ABFT_ERR_UNSUPPORTED: return "unsupported combination of arguments";
+        case ABFT_ERR_TOO_LARGE: return "problem needs more workspace than the built-in scratch array";
         default: return "invalid argument";
     }
 }
