@@ -138,6 +138,28 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_getrf -- ABFT-protected blocked LU with partial pivoting, P A = L U.
+ * Sec. 2.1 (PD = pivoted factorization of the n-K0 x nb panel, PU = unit
+ * lower triangular solve of the block row, TMU = rank-nb GEMM update);
+ * Sec. 3.1.2 (checksums; row interchanges move the row checksums and add the
+ * row difference to the column checksums of the two block rows).
+ *   A, lda     n x n row-major; on return L (unit, strictly below the
+ *              diagonal) and U (on and above), LAPACK getrf layout
+ *   ipiv       device int64[n]: 0-based row interchanged with row i at step i
+ *              (first index of the largest |a|, as LAPACK)
+ *   faults     TMU kinds need row, col >= (step+1) nb; PANEL faults hit the
+ *              block row of U: step nb <= row < (step+1) nb, col >= (step+1) nb
+ *   tau_scale  tau_k = tau_scale * 8 u n nb max(max|a_ij|, max|u_ij| so far)
+ * Returns as abft_potrf; info > 0 is the first exactly-zero pivot (the
+ * factorization is completed, as LAPACK).  Errors: -1 n; -2 nb; -3 dtype;
+ * -4 mode; -5 A; -6 lda; -7 ipiv NULL; -8 faults; -9 nfaults; -10 tau_scale;
+ * -13 workspace.
+ */
+int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               int64_t* ipiv, const abft_fault* faults, int32_t nfaults, double tau_scale,
+               abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
  * own allocator or arena owns the whole GPU (or that may not grow the

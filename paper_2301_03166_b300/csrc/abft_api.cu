@@ -123,7 +123,7 @@ bool event_less(const abft_fault& a, const abft_fault& b) {
 }
 
 // Copy the device status into *rep (synchronizes the stream).
-int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s) {
+int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s, bool lu = false) {
     DevStatus h;
     ABFT_CUDA_TRY(cudaMemcpyAsync(&h, dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     ABFT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -133,7 +133,7 @@ int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s) {
     rep->uncorrectable = (int64_t)h.uncorrectable;
     rep->checksum_repaired = (int64_t)h.repaired;
     rep->nloc = std::min(h.nloc, (int)ABFT_MAX_LOC);
-    rep->info = h.info;
+    rep->info = lu ? h.lu_info : h.info;
     for (int i = 0; i < rep->nloc; ++i) rep->loc[i] = h.loc[i];
     std::sort(rep->loc, rep->loc + rep->nloc, event_less);
     double r;
@@ -141,7 +141,7 @@ int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s) {
     rep->max_ratio = r;
     rep->tau = h.tau;
     if (h.error) return ABFT_ERR_TIMEOUT;
-    if (h.info) return h.info;
+    if (rep->info) return rep->info;
     if (h.uncorrectable) return ABFT_ERR_UNCORRECTABLE;
     return ABFT_OK;
 }
@@ -164,7 +164,7 @@ cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* s
         g.C = Lc + w * lda + w; g.ldc = lda;
         g.M = r; g.N = r; g.K = w;
         g.g = 64; g.row0 = 0; g.col0 = 0;
-        e = launch_gemm_f64(&g, 1, 0, nullptr, 0, st, s);
+        e = launch_gemm_f64(&g, 1, 0, 0, nullptr, 0, st, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -254,7 +254,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
                 cf[ncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
         timing_mark(PH_TMU, 1, s);
-        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, cf, ncf, st, s));
+        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 0, cf, ncf, st, s));
         timing_mark(PH_TMU, 0, s);
         timing_mark(PH_VERIFY, 1, s);
         for (int f = 0; f < nfaults; ++f)
@@ -274,6 +274,209 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
     timing_mark(PH_OTHER, 0, s);
     return ABFT_OK;
 }
+
+// ------------------------------------------------------------------ LU
+struct LuWs {
+    size_t st, cs, cr, colchk, colchkw, ptot, part, z, zw, pv, pi, total;
+    int64_t nc, nt;
+};
+
+LuWs lu_ws(int64_t n, int64_t nb, int mode) {
+    LuWs w{};
+    w.nt = (n + nb - 1) / nb;
+    w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
+    const size_t d = sizeof(double);
+    size_t off = 0;
+    w.st = off; off = align_up(off + sizeof(DevStatus));
+    w.cs = off; off = align_up(off + d * (size_t)(w.nc * w.nt) * (size_t)n);
+    w.cr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? d * (size_t)n * (size_t)w.nt : 0));
+    w.colchk = off; off = align_up(off + d * (size_t)n);
+    w.colchkw = off; off = align_up(off + d * (size_t)n);
+    w.ptot = off; off = align_up(off + d * (size_t)nb);
+    w.part = off; off = align_up(off + d * (size_t)w.nt * (size_t)nb);
+    w.z = off; off = align_up(off + d * (size_t)nb);
+    w.zw = off; off = align_up(off + d * (size_t)nb);
+    w.pv = off; off = align_up(off + d * 1024);
+    w.pi = off; off = align_up(off + sizeof(int64_t) * 1024);
+    w.total = off;
+    return w;
+}
+
+bool lu_fault_ok(const abft_fault& f, int64_t n, int64_t nb, int64_t N) {
+    if (f.step < 0 || f.step >= N - 1) return false;
+    int64_t K0 = (int64_t)f.step * nb, T0 = std::min(K0 + nb, n);
+    if (f.row < 0 || f.row >= n || f.col < 0 || f.col >= n) return false;
+    if (f.kind == ABFT_FAULT_PANEL) return f.row >= K0 && f.row < T0 && f.col >= T0;
+    if (f.kind < ABFT_FAULT_MEMORY || f.kind > ABFT_FAULT_PANEL) return false;
+    return f.row >= T0 && f.col >= T0;
+}
+
+// Blocked ABFT LU step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
+int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_t* ipiv,
+             const abft_fault* faults, int32_t nfaults, double tau_scale, const LuWs& w,
+             char* base, cudaStream_t s) {
+    DevStatus* st = (DevStatus*)(base + w.st);
+    double* CS = (double*)(base + w.cs);
+    double* Cr = (double*)(base + w.cr);
+    double* colchk = (double*)(base + w.colchk);
+    double* colchkw = (double*)(base + w.colchkw);
+    double* ptot = (double*)(base + w.ptot);
+    double* part = (double*)(base + w.part);
+    double* z = (double*)(base + w.z);
+    double* zw = (double*)(base + w.zw);
+    double* pv = (double*)(base + w.pv);
+    int64_t* pi = (int64_t*)(base + w.pi);
+    const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt;
+    const bool full = mode == ABFT_MODE_FULL, check = mode != ABFT_MODE_NONE;
+
+    TileSet base_ts{};
+    base_ts.A = A; base_ts.lda = lda;
+    base_ts.cc = CS; base_ts.cw = CS + n; base_ts.ccI = nc * n;
+    base_ts.cr = Cr; base_ts.crs = nt; base_ts.crJ = 1;
+    base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
+    timing_mark(PH_OTHER, 1, s);
+    if (check) {
+        ABFT_CUDA_TRY(launch_absmax(A, lda, n, n, &st->amax, s));
+        TileSet ts = base_ts;
+        ts.I0 = 0; ts.I1 = nt; ts.J0 = 0; ts.J1 = nt; ts.lower = 0;
+        ABFT_CUDA_TRY(launch_encode(ts, mode, s));
+    }
+    timing_mark(PH_OTHER, 0, s);
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
+        double* P = A + K0 * lda + K0;
+        timing_mark(PH_PD, 1, s);
+        if (check) ABFT_CUDA_TRY(launch_coltot(CS, n, nc, k, nt, K0, kb, ptot, s));
+        ABFT_CUDA_TRY(launch_getf2_coop(P, lda, n - K0, kb, K0, ipiv, st, pv, pi, s));
+        ABFT_CUDA_TRY(launch_laswp(A, lda, n, K0, kb, ipiv, CS, n, nc, g, Cr, nt, mode, s));
+        if (check) {
+            ABFT_CUDA_TRY(launch_lu_colsums(P, lda, n - K0, kb, g, k, nt, K0, CS, n, nc, mode,
+                                            part, nb, s));
+            ABFT_CUDA_TRY(launch_lu_pd_check(P, lda, kb, ptot, part, nb, (int)(nt - k), (int)k,
+                                             K0, n, g, tau_scale, z, zw, mode, st, s));
+        }
+        timing_mark(PH_PD, 0, s);
+        if (m <= 0) break;
+        // PU: U = L_kk^{-1} A_kJ with the row-checksum columns t_J = L_kk^{-1} r_kJ folded in
+        timing_mark(PH_PU, 1, s);
+        ABFT_CUDA_TRY(launch_trsm_llu(P, lda, kb, A + K0 * lda + T0, lda, m,
+                                      full ? Cr + K0 * nt + (k + 1) : nullptr, nt, nt - k - 1,
+                                      check ? z : nullptr, zw, colchk + T0,
+                                      mode == ABFT_MODE_SINGLE ? colchkw + T0 : nullptr, s));
+        for (int f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)
+                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
+        if (check) {
+            TileSet ts = base_ts;
+            ts.cc = colchk; ts.cw = colchkw; ts.ccI = 0;
+            ts.I0 = k; ts.I1 = k + 1; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 0;
+            ts.nrow_end = T0;
+            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+            ABFT_CUDA_TRY(launch_absmax(A + K0 * lda + T0, lda, kb, m, &st->umax, s));
+        }
+        timing_mark(PH_PU, 0, s);
+        // TMU: A22 -= L21 U12 with the checksum borders
+        GemmSeg gs[3] = {};
+        gs[0].A = A + T0 * lda + K0; gs[0].lda = lda;
+        gs[0].B = A + K0 * lda + T0; gs[0].ldb = lda;
+        gs[0].C = A + T0 * lda + T0; gs[0].ldc = lda;
+        gs[0].M = m; gs[0].N = m; gs[0].K = kb;
+        int nseg = 1;
+        if (check) {   // c_I -= (1^T L_Ik) U_kJ (and weighted)
+            GemmSeg& b = gs[nseg++];
+            b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
+            b.B = A + K0 * lda + T0; b.ldb = lda;
+            b.C = CS + ((k + 1) * nc) * n + T0; b.ldc = n;
+            b.M = (nt - k - 1) * nc; b.N = m; b.K = kb;
+        }
+        if (full) {    // r_I -= L_Ik t_J
+            GemmSeg& b = gs[nseg++];
+            b.A = A + T0 * lda + K0; b.lda = lda;
+            b.B = Cr + K0 * nt + (k + 1); b.ldb = nt;
+            b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
+            b.M = m; b.N = nt - k - 1; b.K = kb;
+        }
+        ComputeFault cf[MAX_CF];
+        int ncf = 0;
+        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                cf[ncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
+        timing_mark(PH_TMU, 1, s);
+        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 1, cf, ncf, st, s));
+        timing_mark(PH_TMU, 0, s);
+        timing_mark(PH_VERIFY, 1, s);
+        for (int f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
+                                        faults[f].kind == ABFT_FAULT_ROW1D ||
+                                        faults[f].kind == ABFT_FAULT_COL1D))
+                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
+        if (check) {
+            TileSet ts = base_ts;
+            ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 0;
+            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+        }
+        timing_mark(PH_VERIFY, 0, s);
+    }
+    return ABFT_OK;
+}
+
+int check_common(int64_t n, int64_t nb, int32_t dtype, int32_t mode, const void* A, int64_t lda,
+                 const abft_fault* faults, int32_t nfaults, double tau_scale, const void* ws,
+                 size_t* ws_bytes) {
+    if (n < 0) return -1;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
+    if (dtype != ABFT_F64) return dtype < 0 || dtype > 3 ? -3 : ABFT_ERR_UNSUPPORTED;
+    if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -4;
+    if (n > 0 && A == nullptr && ws != nullptr) return -5;
+    if (lda < std::max<int64_t>(1, n)) return -6;
+    if (nfaults < 0) return -9;
+    if (nfaults > 0 && faults == nullptr) return -8;
+    if (!(tau_scale > 0.0)) return -10;
+    if (ws_bytes == nullptr) return -13;
+    for (int f = 0; f < nfaults; ++f) {
+        int same = 0;
+        for (int h = 0; h < nfaults; ++h)
+            same += faults[h].kind == ABFT_FAULT_COMPUTE && faults[h].step == faults[f].step;
+        if (same > MAX_CF) return -8;
+    }
+    return ABFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               int64_t* ipiv, const abft_fault* faults, int32_t nfaults, double tau_scale,
+               abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes);
+    if (rc != ABFT_OK) return rc;
+    if (n > 0 && ipiv == nullptr && ws != nullptr) return -7;
+    const int64_t N = (n + nb - 1) / nb;
+    for (int f = 0; f < nfaults; ++f)
+        if (!lu_fault_ok(faults[f], n, nb, N)) return -8;
+    const LuWs w = lu_ws(n, nb, mode);
+    if (ws == nullptr) {
+        *ws_bytes = w.total;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < w.total) return -13;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    DevStatus* st = (DevStatus*)(base + w.st);
+    ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    if (n > 0) {
+        rc = lu_steps(n, nb, mode, A, lda, ipiv, faults, nfaults, tau_scale, w, base, s);
+        if (rc != ABFT_OK) return rc;
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    if (rep) return finish_report(st, rep, s, true);
+    return ABFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
 
 }  // namespace
 

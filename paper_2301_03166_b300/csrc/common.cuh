@@ -23,9 +23,51 @@ struct DevStatus {
     double amax;                       // max |a_ij| of the input (LU) / max column norm (QR)
     double umax;                       // running max |u_ij| (LU)
     int error;                         // internal error code (timeouts)
-    int pad;
+    int lu_info;                       // LU: 1-based first exactly-zero pivot (factorization continues)
+    unsigned int bar_arrive;           // grid barrier of the cooperative panel kernels
+    unsigned int bar_gen;
     abft_fault loc[ABFT_MAX_LOC];
 };
+
+// Grid-wide barrier for cooperative launches (all CTAs co-resident).  The
+// wait is bounded: after kBarrierNs of spinning the CTA records a timeout in
+// st->error and the barrier returns false, so no CTA can wait forever.
+constexpr unsigned long long kBarrierNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &st->bar_gen;
+        unsigned int gen = *vgen;
+        __threadfence();
+        unsigned int ticket = atomicAdd(&st->bar_arrive, 1u);
+        if (ticket == nblocks - 1) {
+            atomicExch(&st->bar_arrive, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (global_ns() - t0 > kBarrierNs) {
+                    atomicExch(&st->error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int*)&st->error == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 enum { MODE_NONE = 0, MODE_SINGLE = 1, MODE_FULL = 2 };
 enum { EV_0D = 0, EV_ROW = 1, EV_COL = 2, EV_UNCORR = 3, EV_CKSUM = 4, EV_PD = 5 };
@@ -81,7 +123,7 @@ cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, 
 // FP64 update C -= A_op * B_op^T (NT) or A_op * B_op (NN), over up to three
 // segments (the main tiles and the checksum border rows / columns).
 struct GemmSeg {
-    const double* A;   // A[i*lda + p]
+    const double* A;   // A[i*lda + p] (K-major: A[p*lda + i])
     int64_t lda;
     const double* B;   // NT: B[j*ldb + p];  NN: B[p*ldb + j]
     int64_t ldb;
@@ -97,8 +139,8 @@ struct ComputeFault {
     double delta;
 };
 enum { MAX_CF = 4 };
-cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int b_kmajor, const ComputeFault* cf,
-                            int ncf, const DevStatus* st, cudaStream_t s);
+cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int a_kmajor, int b_kmajor,
+                            const ComputeFault* cf, int ncf, const DevStatus* st, cudaStream_t s);
 
 cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_base,
                                DevStatus* st, cudaStream_t s);
@@ -115,6 +157,30 @@ cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const Trsm
 cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
                                  int64_t K0, int step, double* v, int mode, DevStatus* st,
                                  cudaStream_t s);
+
+// LU kernels (k_lu.cu).
+int num_sms();
+cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int64_t K0,
+                              int64_t* ipiv, DevStatus* st, double* part_v, int64_t* part_i,
+                              cudaStream_t s);
+cudaError_t launch_laswp(double* A, int64_t lda, int64_t n, int64_t K0, int64_t kb,
+                         const int64_t* ipiv, double* CS, int64_t ldcs, int64_t nc, int64_t g,
+                         double* Cr, int64_t nt, int mode, cudaStream_t s);
+cudaError_t launch_coltot(const double* CS, int64_t ldcs, int64_t nc, int64_t k, int64_t nt,
+                          int64_t K0, int64_t kb, double* ptot, cudaStream_t s);
+cudaError_t launch_lu_colsums(const double* P, int64_t lda, int64_t m, int64_t kb, int64_t g,
+                              int64_t k, int64_t nt, int64_t K0, double* CS, int64_t ldcs,
+                              int64_t nc, int mode, double* part, int64_t ldpart, cudaStream_t s);
+cudaError_t launch_lu_pd_check(const double* P, int64_t lda, int64_t kb, const double* ptot,
+                               const double* part, int64_t ldpart, int nparts, int step,
+                               int64_t K0, int64_t n, int64_t g, double tau_scale, double* z,
+                               double* zw, int mode, DevStatus* st, cudaStream_t s);
+cudaError_t launch_trsm_llu(const double* L, int64_t ldl, int64_t kb, double* B0, int64_t ldb0,
+                            int64_t ncols0, double* B1, int64_t ldb1, int64_t ncols1,
+                            const double* z, const double* zw, double* colchk, double* colchkw,
+                            cudaStream_t s);
+cudaError_t launch_absmax(const double* A, int64_t lda, int64_t rows, int64_t cols, double* out,
+                          cudaStream_t s);
 
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();

@@ -9,6 +9,7 @@
 // 8 flop/B against HBM -- two orders of magnitude above the FP64 balance
 // point -- so the only goal is to keep the DFMA pipe issuing every cycle.
 //
+// Operands may be row-major over K or K-major (A^T or B^T layouts).
 // A launch carries up to three segments; CTAs are numbered over the 64x64
 // tiles of segment 0, then 1, then 2.  Segment 0 is the main trailing block
 // (with a lower-block mask for the symmetric update: diagonal blocks are
@@ -31,7 +32,7 @@ struct GemmArgs {
     const DevStatus* st;
 };
 
-template <int KMAJOR_B>
+template <int KMAJOR_A, int KMAJOR_B>
 __global__ void __launch_bounds__(NTH) k_gemm_f64(GemmArgs args) {
     __shared__ double As[2][BK][BM + 1];
     __shared__ double Bs[2][BK][BN + 1];
@@ -60,11 +61,20 @@ __global__ void __launch_bounds__(NTH) k_gemm_f64(GemmArgs args) {
         for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
     auto load = [&](int64_t k0) {
-        const int64_t ia = i0 + la_r;
+        if (KMAJOR_A) {  // A[p*lda + i]
+            const int64_t k = k0 + lb_k;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int64_t k = k0 + la_k + u;
-            ra[u] = (ia < g.M && k < g.K) ? g.A[ia * g.lda + k] : 0.0;
+            for (int u = 0; u < 4; ++u) {
+                int64_t i = i0 + lb_c + u;
+                ra[u] = (k < g.K && i < g.M) ? g.A[k * g.lda + i] : 0.0;
+            }
+        } else {
+            const int64_t ia = i0 + la_r;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t k = k0 + la_k + u;
+                ra[u] = (ia < g.M && k < g.K) ? g.A[ia * g.lda + k] : 0.0;
+            }
         }
         if (KMAJOR_B) {
             const int64_t k = k0 + lb_k;
@@ -83,8 +93,13 @@ __global__ void __launch_bounds__(NTH) k_gemm_f64(GemmArgs args) {
         }
     };
     auto store = [&](int buf) {
+        if (KMAJOR_A) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) As[buf][la_k + u][la_r] = ra[u];
+            for (int u = 0; u < 4; ++u) As[buf][lb_k][lb_c + u] = ra[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) As[buf][la_k + u][la_r] = ra[u];
+        }
         if (KMAJOR_B) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) Bs[buf][lb_k][lb_c + u] = rb[u];
@@ -137,8 +152,8 @@ __global__ void __launch_bounds__(NTH) k_gemm_f64(GemmArgs args) {
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int b_kmajor, const ComputeFault* cf,
-                            int ncf, const DevStatus* st, cudaStream_t s) {
+cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int a_kmajor, int b_kmajor,
+                            const ComputeFault* cf, int ncf, const DevStatus* st, cudaStream_t s) {
     GemmArgs a{};
     a.nseg = 0;
     int64_t total = 0;
@@ -159,8 +174,10 @@ cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int b_kmajor, const C
     if (nseg > 0 && segs[0].M > 0 && segs[0].N > 0 && segs[0].K > 0)
         for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
     a.st = st;
-    if (b_kmajor) k_gemm_f64<1><<<(unsigned)total, NTH, 0, s>>>(a);
-    else k_gemm_f64<0><<<(unsigned)total, NTH, 0, s>>>(a);
+    if (a_kmajor && b_kmajor) k_gemm_f64<1, 1><<<(unsigned)total, NTH, 0, s>>>(a);
+    else if (a_kmajor) k_gemm_f64<1, 0><<<(unsigned)total, NTH, 0, s>>>(a);
+    else if (b_kmajor) k_gemm_f64<0, 1><<<(unsigned)total, NTH, 0, s>>>(a);
+    else k_gemm_f64<0, 0><<<(unsigned)total, NTH, 0, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }

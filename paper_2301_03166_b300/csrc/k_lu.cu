@@ -1,0 +1,513 @@
+// k_lu.cu -- kernels of the blocked ABFT LU with partial pivoting
+// (Sec. 2.1: PD  L.1 x U11 <- A.1,  PU  U12 <- L11^{-1} A12,  TMU  A22 <- A22 - L21 U12;
+// Sec. 3.1.2: checksums carried through each operation).
+//
+// The panel factorization (getf2 on the (n - K0) x kb panel) is one
+// cooperative launch: each CTA owns a contiguous block of panel rows; per
+// column the CTAs publish their local (max |a|, first index), meet at a
+// bounded grid barrier, CTA 0 picks the pivot and swaps the two panel rows,
+// they meet again, and every CTA scales and updates its own rows.  The panel
+// (<= 32 MB at n = 16384) stays in L2 across the column loop.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int PT = 256;          // threads of the panel kernels
+constexpr int MAXR = 1024;       // max rows per CTA in the cooperative panel
+
+__device__ __forceinline__ void better(double& bv, int64_t& bi, double v, int64_t i) {
+    // larger |a| wins; equal values keep the smaller index (first max)
+    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+
+__device__ void block_argmax(double& v, int64_t& idx) {
+    __shared__ double sv[PT / 32];
+    __shared__ int64_t si[PT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int64_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        better(v, idx, ov, oi);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sv[w] = v; si[w] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) better(v, idx, sv[k], si[k]);
+        sv[0] = v; si[0] = idx;
+    }
+    __syncthreads();
+    v = sv[0]; idx = si[0];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64_t m, int kb,
+                                                   int64_t K0, int64_t* ipiv, DevStatus* st,
+                                                   double* part_v, int64_t* part_i) {
+    __shared__ double urow[512];
+    __shared__ double lcol[MAXR];
+    const unsigned G = gridDim.x;
+    const int64_t R = (m + G - 1) / G;
+    const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
+    for (int j = 0; j < kb; ++j) {
+        // A: local first-max of |P[i][j]| over my rows i >= j
+        double bv = -1.0;
+        int64_t bi = INT64_MAX;
+        for (int64_t i = (r0 > j ? r0 : j) + threadIdx.x; i < r1; i += PT)
+            better(bv, bi, fabs(P[i * lda + j]), i);
+        block_argmax(bv, bi);
+        if (threadIdx.x == 0) { part_v[blockIdx.x] = bv; part_i[blockIdx.x] = bi; }
+        if (!grid_barrier(st, G)) return;
+        // B: CTA 0 picks the pivot and swaps the two panel rows
+        if (blockIdx.x == 0) {
+            double v = -1.0;
+            int64_t idx = INT64_MAX;
+            for (unsigned b = threadIdx.x; b < G; b += PT) better(v, idx, part_v[b], part_i[b]);
+            block_argmax(v, idx);
+            int64_t p = (idx == INT64_MAX) ? j : idx;
+            if (threadIdx.x == 0) ipiv[K0 + j] = K0 + p;
+            double piv = P[p * lda + j];
+            if (piv == 0.0) {
+                if (threadIdx.x == 0) atomicCAS(&st->lu_info, 0, (int)(K0 + j + 1));
+            } else if (p != j) {
+                for (int c = threadIdx.x; c < kb; c += PT) {
+                    double a = P[(int64_t)j * lda + c];
+                    P[(int64_t)j * lda + c] = P[p * lda + c];
+                    P[p * lda + c] = a;
+                }
+            }
+        }
+        if (!grid_barrier(st, G)) return;
+        // C: scale and rank-1 update of my rows below the pivot
+        const double piv = P[(int64_t)j * lda + j];
+        if (piv == 0.0) continue;
+        for (int c = j + 1 + threadIdx.x; c < kb; c += PT) urow[c] = P[(int64_t)j * lda + c];
+        const int64_t ibeg = (r0 > j + 1 ? r0 : j + 1);
+        for (int64_t i = ibeg + threadIdx.x; i < r1; i += PT) {
+            double l = P[i * lda + j] / piv;
+            P[i * lda + j] = l;
+            lcol[i - r0] = l;
+        }
+        __syncthreads();
+        const int w = kb - j - 1;
+        if (w > 0 && ibeg < r1) {
+            const int64_t nrow = r1 - ibeg;
+            for (int64_t e = threadIdx.x; e < nrow * w; e += PT) {
+                int64_t i = ibeg + e / w;
+                int c = j + 1 + (int)(e % w);
+                double* a = P + i * lda + c;
+                *a = __dsub_rn(*a, __dmul_rn(lcol[i - r0], urow[c]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Row interchanges of the panel applied to every column outside the panel
+// (one thread per column, interchanges in order), and to the row-checksum
+// columns.  For trailing columns the two tile-rows' column (and weighted)
+// sums receive the row difference at the time of each interchange.
+__global__ void k_laswp(double* A, int64_t lda, int64_t n, int64_t K0, int kb,
+                        const int64_t* ipiv, double* CS, int64_t ldcs, int64_t nc, int64_t g,
+                        double* Cr, int64_t nt, int mode) {
+    const int64_t T0 = K0 + kb;
+    const int64_t ndata = n - kb;
+    const int64_t ncr = (mode == MODE_FULL) ? nt : 0;
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= ndata + ncr) return;
+    if (v < ndata) {
+        const int64_t c = v < K0 ? v : v + kb;
+        const bool trail = c >= T0 && mode != MODE_NONE;
+        for (int j = 0; j < kb; ++j) {
+            const int64_t i = K0 + j, p = ipiv[K0 + j];
+            if (p == i) continue;
+            double a = A[i * lda + c], b = A[p * lda + c];
+            A[i * lda + c] = b;
+            A[p * lda + c] = a;
+            if (trail) {
+                const int64_t Ii = i / g, Ip = p / g;
+                CS[(Ii * nc) * ldcs + c] += b - a;
+                CS[(Ip * nc) * ldcs + c] += a - b;
+                if (mode == MODE_SINGLE) {
+                    const double wi = (double)(i - Ii * g + 1), wp = (double)(p - Ip * g + 1);
+                    CS[(Ii * nc + 1) * ldcs + c] += wi * (b - a);
+                    CS[(Ip * nc + 1) * ldcs + c] += wp * (a - b);
+                }
+            }
+        }
+    } else {
+        const int64_t J = v - ndata;
+        for (int j = 0; j < kb; ++j) {
+            const int64_t i = K0 + j, p = ipiv[K0 + j];
+            if (p == i) continue;
+            double a = Cr[i * nt + J];
+            Cr[i * nt + J] = Cr[p * nt + J];
+            Cr[p * nt + J] = a;
+        }
+    }
+}
+
+// ptot[j] = sum over tile-rows I >= k of the carried column sums of panel column j.
+__global__ void k_coltot(const double* CS, int64_t ldcs, int64_t nc, int64_t k, int64_t nt,
+                         int64_t K0, int kb, double* ptot) {
+    for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t I = k; I < nt; ++I) s += CS[(I * nc) * ldcs + K0 + j];
+        ptot[j] = s;
+    }
+}
+
+// Column sums of L per tile-row of the panel (strictly below the unit
+// diagonal in tile-row k): the border rows 1^T L_Ik (and weighted) of the
+// TMU for I > k, and the per-tile parts of the PD check.
+__global__ void k_lu_colsums(const double* P, int64_t lda, int64_t m, int kb, int64_t g,
+                             int64_t k, int64_t K0, double* CS, int64_t ldcs, int64_t nc,
+                             int mode, double* part, int64_t ldpart) {
+    const int64_t I = k + blockIdx.x;
+    const int64_t gr0 = I * g, gr1 = (gr0 + g < K0 + m) ? gr0 + g : K0 + m;
+    for (int q = threadIdx.x; q < kb; q += blockDim.x) {
+        double s = 0.0, sw = 0.0;
+        for (int64_t gi = gr0; gi < gr1; ++gi) {
+            const int64_t i = gi - K0;
+            if (i <= q) continue;
+            double l = P[i * lda + q];
+            s += l;
+            sw += (double)(gi - gr0 + 1) * l;
+        }
+        part[blockIdx.x * ldpart + q] = s;
+        if (I > k && mode != MODE_NONE) {
+            CS[(I * nc) * ldcs + K0 + q] = s;
+            if (mode == MODE_SINGLE) CS[(I * nc + 1) * ldcs + K0 + q] = sw;
+        }
+    }
+}
+
+// Single CTA: running max |U| and the step's threshold, the PD check
+// (total panel column sums vs (1^T L) U_kk), and z = L_kk^{-T} 1,
+// zw = L_kk^{-T} (1..kb) for the column sums of U.
+__global__ void __launch_bounds__(512) k_lu_pd_check(const double* P, int64_t lda, int kb,
+                                                     const double* ptot, const double* part,
+                                                     int64_t ldpart, int nparts, int step,
+                                                     int64_t K0, int64_t n, int64_t g,
+                                                     double tau_scale, double* z, double* zw,
+                                                     int mode, DevStatus* st) {
+    __shared__ double lsum[512];
+    __shared__ double red[16];
+    __shared__ double tz[512], tw[512];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    double m = 0.0;
+    for (int e = t; e < kb * kb; e += blockDim.x) {
+        int i = e / kb, j = e % kb;
+        if (j >= i) m = fmax(m, fabs(P[(int64_t)i * lda + j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp] = m;
+    for (int q = t; q < kb; q += blockDim.x) {
+        double s = 1.0;
+        for (int b = 0; b < nparts; ++b) s += part[b * ldpart + q];
+        lsum[q] = s;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < nw; ++w) m = fmax(m, red[w]);
+        double um = fmax(st->umax, m);
+        st->umax = um;
+        double M = st->amax > um ? st->amax : um;
+        double tau = tau_scale * 8.0;
+        tau *= 0x1p-53;
+        tau *= (double)n;
+        tau *= (double)g;
+        tau *= M;
+        st->tau = tau;
+    }
+    __syncthreads();
+    if (mode == MODE_NONE) return;
+    const double tau = st->tau;
+    for (int j = warp; j < kb; j += nw) {
+        double y = 0.0;
+        for (int q = lane; q <= j; q += 32) y = fma(lsum[q], P[(int64_t)q * lda + j], y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        if (lane == 0) {
+            double d = y - ptot[j];
+            if (!(fabs(d) <= tau)) {
+                atomicAdd(&st->detected, 1ull);
+                atomicAdd(&st->uncorrectable, 1ull);
+                record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+            }
+        }
+    }
+    // z = L^{-T} 1, zw = L^{-T} w (unit upper L^T), chunks of 32 from the end
+    for (int p = t; p < kb; p += blockDim.x) { tz[p] = 1.0; tw[p] = (double)(p + 1); }
+    __syncthreads();
+    for (int c1 = kb; c1 > 0; c1 -= 32) {
+        const int c0 = c1 - 32 > 0 ? c1 - 32 : 0;
+        if (warp == 0) {
+            const int p = c0 + lane;
+            double a = (p < c1) ? tz[p] : 0.0, b = (p < c1) ? tw[p] : 0.0;
+            for (int j = c1 - 1; j >= c0; --j) {
+                double zj = __shfl_sync(0xffffffffu, a, j - c0);
+                double wj = __shfl_sync(0xffffffffu, b, j - c0);
+                if (p < j) {
+                    double l = P[(int64_t)j * lda + p];
+                    a -= l * zj;
+                    b -= l * wj;
+                }
+            }
+            if (p < c1) { tz[p] = a; tw[p] = b; }
+        }
+        __syncthreads();
+        for (int p = t; p < c0; p += blockDim.x) {
+            double a = tz[p], b = tw[p];
+            for (int j = c0; j < c1; ++j) {
+                double l = P[(int64_t)j * lda + p];
+                a -= l * tz[j];
+                b -= l * tw[j];
+            }
+            tz[p] = a; tw[p] = b;
+        }
+        __syncthreads();
+    }
+    for (int p = t; p < kb; p += blockDim.x) { z[p] = tz[p]; zw[p] = tw[p]; }
+}
+
+constexpr int CB = 32;    // columns per CTA of the U solve
+struct TrsmLSeg {
+    double* B;
+    int64_t ldb;
+    int64_t ncols;
+};
+struct TrsmLArgs {
+    const double* L;
+    int64_t ldl;
+    int kb;
+    TrsmLSeg seg[2];
+    int64_t start[3];
+    int nseg;
+    const double* z;
+    const double* zw;
+    double* colchk;
+    double* colchkw;
+};
+
+// U = L^{-1} B (L unit lower kb x kb) for CB columns per CTA, in place; the
+// row-checksum columns are a second segment of the same launch.  Before the
+// solve, segment 0 also produces the U column sums z^T B (and zw^T B).
+__global__ void __launch_bounds__(256) k_trsm_llu(TrsmLArgs a) {
+    extern __shared__ double smem[];
+    const int kb = a.kb;
+    double* X = smem;                    // kb x (CB + 1)
+    double* Ls = smem + kb * (CB + 1);   // 32 x 33
+    const int64_t bid = blockIdx.x;
+    const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    const TrsmLSeg& g = a.seg[s];
+    const int64_t c0 = (bid - a.start[s]) * CB;
+    const int nc = (int)((g.ncols - c0) < CB ? (g.ncols - c0) : CB);
+    const int t = threadIdx.x;
+    for (int e = t; e < kb * CB; e += 256) {
+        int r = e / CB, c = e % CB;
+        X[r * (CB + 1) + c] = (c < nc) ? g.B[(int64_t)r * g.ldb + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (s == 0 && a.z != nullptr) {
+        const int warp = t >> 5, lane = t & 31;
+        for (int c = warp; c < nc; c += 8) {
+            double u = 0.0, w = 0.0;
+            for (int r = lane; r < kb; r += 32) {
+                double x = X[r * (CB + 1) + c];
+                u = fma(a.z[r], x, u);
+                w = fma(a.zw[r], x, w);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                a.colchk[c0 + c] = u;
+                if (a.colchkw) a.colchkw[c0 + c] = w;
+            }
+        }
+        __syncthreads();
+    }
+    const int gr = t >> 3, gq = (t & 7) * 4;   // row gr of the chunk, columns gq..gq+3
+    for (int r0 = 0; r0 < kb; r0 += 32) {
+        const int w = (kb - r0) < 32 ? (kb - r0) : 32;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int p0 = 0; p0 < r0; p0 += 32) {
+            __syncthreads();
+            for (int e = t; e < 32 * 32; e += 256) {
+                int q = e / 32, pp = e % 32;
+                Ls[q * 33 + pp] = (q < w) ? a.L[(int64_t)(r0 + q) * a.ldl + p0 + pp] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int pp = 0; pp < 32; ++pp) {
+                double l = Ls[gr * 33 + pp];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(l, X[(p0 + pp) * (CB + 1) + gq + u], acc[u]);
+            }
+        }
+        __syncthreads();
+        if (gr < w)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) X[(r0 + gr) * (CB + 1) + gq + u] -= acc[u];
+        for (int e = t; e < 32 * 32; e += 256) {
+            int q = e / 32, pp = e % 32;
+            Ls[q * 33 + pp] = (q < w && pp < q) ? a.L[(int64_t)(r0 + q) * a.ldl + r0 + pp] : 0.0;
+        }
+        __syncthreads();
+        if (t < CB) {
+            for (int jj = 0; jj < w; ++jj) {
+                double v = X[(r0 + jj) * (CB + 1) + t];
+                for (int p = 0; p < jj; ++p) v -= Ls[jj * 33 + p] * X[(r0 + p) * (CB + 1) + t];
+                X[(r0 + jj) * (CB + 1) + t] = v;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < kb * CB; e += 256) {
+        int r = e / CB, c = e % CB;
+        if (c < nc) g.B[(int64_t)r * g.ldb + c0 + c] = X[r * (CB + 1) + c];
+    }
+}
+
+__global__ void k_absmax(const double* A, int64_t lda, int64_t rows, int64_t cols,
+                         double* out) {
+    __shared__ double red[32];
+    double m = 0.0;
+    const int64_t tot = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / cols, j = e % cols;
+        double v = fabs(A[i * lda + j]);
+        if (v > m) m = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        atomic_max_nonneg((unsigned long long*)out, m);
+    }
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int64_t K0,
+                              int64_t* ipiv, DevStatus* st, double* part_v, int64_t* part_i,
+                              cudaStream_t s) {
+    int64_t want = (m + 63) / 64;
+    int64_t G = want < num_sms() ? want : num_sms();
+    if (G < 1) G = 1;
+    while ((m + G - 1) / G > MAXR) ++G;   // rows per CTA must fit the shared buffer
+    if (G > num_sms()) return cudaErrorInvalidValue;
+    int kbi = (int)kb;
+    void* args[] = {&P, &lda, &m, &kbi, &K0, &ipiv, &st, &part_v, &part_i};
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_getf2_coop, dim3((unsigned)G), dim3(PT),
+                                                args, 0, s);
+    note_launch();
+    return e;
+}
+
+cudaError_t launch_laswp(double* A, int64_t lda, int64_t n, int64_t K0, int64_t kb,
+                         const int64_t* ipiv, double* CS, int64_t ldcs, int64_t nc, int64_t g,
+                         double* Cr, int64_t nt, int mode, cudaStream_t s) {
+    int64_t tot = (n - kb) + (mode == MODE_FULL ? nt : 0);
+    if (tot <= 0) return cudaSuccess;
+    k_laswp<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(A, lda, n, K0, (int)kb, ipiv, CS, ldcs,
+                                                          nc, g, Cr, nt, mode);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coltot(const double* CS, int64_t ldcs, int64_t nc, int64_t k, int64_t nt,
+                          int64_t K0, int64_t kb, double* ptot, cudaStream_t s) {
+    k_coltot<<<1, 512, 0, s>>>(CS, ldcs, nc, k, nt, K0, (int)kb, ptot);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_colsums(const double* P, int64_t lda, int64_t m, int64_t kb, int64_t g,
+                              int64_t k, int64_t nt, int64_t K0, double* CS, int64_t ldcs,
+                              int64_t nc, int mode, double* part, int64_t ldpart, cudaStream_t s) {
+    k_lu_colsums<<<(unsigned)(nt - k), 256, 0, s>>>(P, lda, m, (int)kb, g, k, K0, CS, ldcs, nc,
+                                                     mode, part, ldpart);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_pd_check(const double* P, int64_t lda, int64_t kb, const double* ptot,
+                               const double* part, int64_t ldpart, int nparts, int step,
+                               int64_t K0, int64_t n, int64_t g, double tau_scale, double* z,
+                               double* zw, int mode, DevStatus* st, cudaStream_t s) {
+    k_lu_pd_check<<<1, 512, 0, s>>>(P, lda, (int)kb, ptot, part, ldpart, nparts, step, K0, n, g,
+                                    tau_scale, z, zw, mode, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_llu(const double* L, int64_t ldl, int64_t kb, double* B0, int64_t ldb0,
+                            int64_t ncols0, double* B1, int64_t ldb1, int64_t ncols1,
+                            const double* z, const double* zw, double* colchk, double* colchkw,
+                            cudaStream_t s) {
+    TrsmLArgs a{};
+    a.L = L; a.ldl = ldl; a.kb = (int)kb;
+    a.nseg = 0;
+    int64_t total = 0;
+    TrsmLSeg segs[2] = {{B0, ldb0, ncols0}, {B1, ldb1, ncols1}};
+    for (int i = 0; i < 2; ++i) {
+        if (segs[i].ncols <= 0 || segs[i].B == nullptr) {
+            if (i == 0) z = nullptr;
+            continue;
+        }
+        a.seg[a.nseg] = segs[i];
+        a.start[a.nseg] = total;
+        total += (segs[i].ncols + CB - 1) / CB;
+        a.nseg++;
+    }
+    if (total == 0) return cudaSuccess;
+    a.start[a.nseg] = total;
+    a.z = z; a.zw = zw; a.colchk = colchk; a.colchkw = colchkw;
+    size_t smem = (size_t)(kb * (CB + 1) + 32 * 33) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_llu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((512 * (CB + 1) + 32 * 33) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_trsm_llu<<<(unsigned)total, 256, smem, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const double* A, int64_t lda, int64_t rows, int64_t cols, double* out,
+                          cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    int64_t blocks = (rows * cols + 255) / 256;
+    if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
+    k_absmax<<<(unsigned)blocks, 256, 0, s>>>(A, lda, rows, cols, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft
