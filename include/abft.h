@@ -160,6 +160,28 @@ int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_geqrf -- ABFT-protected blocked Householder QR, A = Q R.
+ * Sec. 2.1 (PD = Householder factorization of the n-K0 x nb panel and the
+ * triangular factor T of its block reflector I - V T V^T; TMU = block
+ * reflector applied to the trailing columns, C -= V T^T V^T C); Sec. 3.1.2
+ * (the row checksums ride through the update as extra columns, the column
+ * checksums of each block row are updated by (1^T V_I) T^T V^T C).
+ *   A, lda     n x n row-major; on return R on and above the diagonal and the
+ *              reflectors v (unit leading entry implicit) below, LAPACK
+ *              geqrf layout; reflectors follow LAPACK larfg:
+ *              beta = -sign(alpha) ||x||, sign(0) = +, tau = (beta - alpha)/beta
+ *   tau        device double[n], the reflector scalars
+ *   faults     TMU kinds (no PANEL kind): row >= step nb, col >= (step+1) nb
+ *   tau_scale  tau = tau_scale * 8 u n nb max_j ||a_j||_2
+ * Returns as abft_potrf (no info).  Errors: -1 n; -2 nb; -3 dtype; -4 mode;
+ * -5 A; -6 lda; -7 tau NULL; -8 faults; -9 nfaults; -10 tau_scale;
+ * -13 workspace.
+ */
+int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               double* tau, const abft_fault* faults, int32_t nfaults, double tau_scale,
+               abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
  * own allocator or arena owns the whole GPU (or that may not grow the

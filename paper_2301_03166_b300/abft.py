@@ -46,6 +46,8 @@ _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
+    "abft_geqrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
+                   ctypes.POINTER(Report), _vp, _sz, _vp],
     "abft_getrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
     "abft_potrf_noalloc": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
@@ -212,3 +214,31 @@ def getrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, ipiv[:n], (report_dict(rep) if rep is not None else None)
+
+
+def geqrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
+          workspace=None, stream=None, check=True):
+    """ABFT Householder QR in place (LAPACK geqrf layout).
+    Returns (code, tau float64 CUDA tensor, report dict or None)."""
+    _check_matrix(A)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    L = lib()
+    fa, nf = _faults(faults)
+    need = ctypes.c_size_t(0)
+    rc = L.abft_geqrf(n, nb, dtype, mode, None, max(1, A.stride(0)), None, fa, nf, tau_scale,
+                      None, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    tau = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
+    rep = Report() if report else None
+    size = ctypes.c_size_t(ws.numel())
+    rc = L.abft_geqrf(n, nb, dtype, mode, ctypes.c_void_p(A.data_ptr()), max(1, A.stride(0)),
+                      ctypes.c_void_p(tau.data_ptr()), fa, nf, tau_scale,
+                      ctypes.byref(rep) if rep is not None else None,
+                      ctypes.c_void_p(ws.data_ptr()), ctypes.byref(size), _stream(stream))
+    if check and rc < 0 and rc != ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    return rc, tau[:n], (report_dict(rep) if rep is not None else None)

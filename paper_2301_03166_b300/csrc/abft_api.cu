@@ -478,6 +478,179 @@ int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
 
 namespace {
 
+// ------------------------------------------------------------------ QR
+struct QrWs {
+    size_t st, cs, cr, nrm, part, wv, V, G, T, W, X, total;
+    int64_t nc, nt, ldw;
+};
+
+QrWs qr_ws(int64_t n, int64_t nb, int mode) {
+    QrWs w{};
+    w.nt = (n + nb - 1) / nb;
+    w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
+    w.ldw = n + w.nt;
+    const size_t d = sizeof(double);
+    size_t off = 0;
+    w.st = off; off = align_up(off + sizeof(DevStatus));
+    w.cs = off; off = align_up(off + d * (size_t)(w.nc * w.nt) * (size_t)n);
+    w.cr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? d * (size_t)n * (size_t)w.nt : 0));
+    w.nrm = off; off = align_up(off + d * (size_t)nb);
+    w.part = off; off = align_up(off + d * 1024 * (size_t)(nb + 1));
+    w.wv = off; off = align_up(off + d * (size_t)nb);
+    w.V = off; off = align_up(off + d * (size_t)n * (size_t)nb);
+    w.G = off; off = align_up(off + d * (size_t)nb * (size_t)nb);
+    w.T = off; off = align_up(off + d * (size_t)nb * (size_t)nb);
+    w.W = off; off = align_up(off + d * (size_t)nb * (size_t)w.ldw);
+    w.X = off; off = align_up(off + d * (size_t)nb * (size_t)w.ldw);
+    w.total = off;
+    return w;
+}
+
+bool qr_fault_ok(const abft_fault& f, int64_t n, int64_t nb, int64_t N) {
+    if (f.step < 0 || f.step >= N - 1) return false;
+    int64_t K0 = (int64_t)f.step * nb, T0 = std::min(K0 + nb, n);
+    if (f.row < 0 || f.row >= n || f.col < 0 || f.col >= n) return false;
+    if (f.kind < ABFT_FAULT_MEMORY || f.kind > ABFT_FAULT_COL1D) return false;
+    return f.row >= K0 && f.col >= T0;
+}
+
+// Blocked ABFT Householder QR step loop.
+int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double* tau,
+             const abft_fault* faults, int32_t nfaults, double tau_scale, const QrWs& w,
+             char* base, cudaStream_t s) {
+    DevStatus* st = (DevStatus*)(base + w.st);
+    double* CS = (double*)(base + w.cs);
+    double* Cr = (double*)(base + w.cr);
+    double* nrm = (double*)(base + w.nrm);
+    double* part = (double*)(base + w.part);
+    double* wv = (double*)(base + w.wv);
+    double* V = (double*)(base + w.V);
+    double* Gn = (double*)(base + w.G);
+    double* T = (double*)(base + w.T);
+    double* Wb = (double*)(base + w.W);
+    double* Xb = (double*)(base + w.X);
+    const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt, ldw = w.ldw;
+    const bool full = mode == ABFT_MODE_FULL, check = mode != ABFT_MODE_NONE;
+
+    TileSet base_ts{};
+    base_ts.A = A; base_ts.lda = lda;
+    base_ts.cc = CS; base_ts.cw = CS + n; base_ts.ccI = nc * n;
+    base_ts.cr = Cr; base_ts.crs = nt; base_ts.crJ = 1;
+    base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
+    timing_mark(PH_OTHER, 1, s);
+    ABFT_CUDA_TRY(launch_qr_tau(A, lda, n, g, tau_scale, st, s));
+    if (check) {
+        TileSet ts = base_ts;
+        ts.I0 = 0; ts.I1 = nt; ts.J0 = 0; ts.J1 = nt; ts.lower = 0;
+        ABFT_CUDA_TRY(launch_encode(ts, mode, s));
+    }
+    timing_mark(PH_OTHER, 0, s);
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - K0;
+        double* P = A + K0 * lda + K0;
+        timing_mark(PH_PD, 1, s);
+        ABFT_CUDA_TRY(launch_geqr2_coop(P, lda, m, kb, tau + K0, nrm, part, wv, st, s));
+        if (check) ABFT_CUDA_TRY(launch_qr_pd_check(P, lda, kb, nrm, (int)k, K0, st, s));
+        if (T0 >= n) { timing_mark(PH_PD, 0, s); break; }
+        ABFT_CUDA_TRY(launch_qr_prep_v(P, lda, m, kb, V, s));
+        if (check) ABFT_CUDA_TRY(launch_qr_vsums(V, m, kb, g, k, nt, K0, CS, n, nc, mode, s));
+        ABFT_CUDA_TRY(cudaMemsetAsync(Gn, 0, sizeof(double) * kb * kb, s));
+        {
+            GemmSeg gg{};   // Gn = -V^T V
+            gg.A = V; gg.lda = kb; gg.B = V; gg.ldb = kb; gg.C = Gn; gg.ldc = kb;
+            gg.M = kb; gg.N = kb; gg.K = m;
+            ABFT_CUDA_TRY(launch_gemm_f64(&gg, 1, 1, 1, nullptr, 0, st, s));
+        }
+        ABFT_CUDA_TRY(launch_larft(Gn, kb, tau + K0, T, s));
+        timing_mark(PH_PD, 0, s);
+        // TMU (larfb): W = -V^T [C, r]; X = -T^T W; [C, r] -= V X; c_I -= (1^T V_I) X
+        const int64_t ncs = full ? nt - k - 1 : 0, nd = n - T0, ncol = nd + ncs;
+        timing_mark(PH_TMU, 1, s);
+        ABFT_CUDA_TRY(cudaMemsetAsync(Wb, 0, sizeof(double) * kb * ldw, s));
+        ABFT_CUDA_TRY(cudaMemsetAsync(Xb, 0, sizeof(double) * kb * ldw, s));
+        GemmSeg g1[2] = {};
+        g1[0].A = V; g1[0].lda = kb; g1[0].B = A + K0 * lda + T0; g1[0].ldb = lda;
+        g1[0].C = Wb; g1[0].ldc = ldw; g1[0].M = kb; g1[0].N = nd; g1[0].K = m;
+        g1[1].A = V; g1[1].lda = kb; g1[1].B = Cr + K0 * nt + (k + 1); g1[1].ldb = nt;
+        g1[1].C = Wb + nd; g1[1].ldc = ldw; g1[1].M = kb; g1[1].N = ncs; g1[1].K = m;
+        ABFT_CUDA_TRY(launch_gemm_f64(g1, full ? 2 : 1, 1, 1, nullptr, 0, st, s));
+        GemmSeg g2{};
+        g2.A = T; g2.lda = kb; g2.B = Wb; g2.ldb = ldw; g2.C = Xb; g2.ldc = ldw;
+        g2.M = kb; g2.N = ncol; g2.K = kb;
+        ABFT_CUDA_TRY(launch_gemm_f64(&g2, 1, 1, 1, nullptr, 0, st, s));
+        GemmSeg g3[3] = {};
+        g3[0].A = V; g3[0].lda = kb; g3[0].B = Xb; g3[0].ldb = ldw;
+        g3[0].C = A + K0 * lda + T0; g3[0].ldc = lda; g3[0].M = m; g3[0].N = nd; g3[0].K = kb;
+        int nseg = 1;
+        if (check) {
+            GemmSeg& b = g3[nseg++];
+            b.A = CS + (k * nc) * n + K0; b.lda = n; b.B = Xb; b.ldb = ldw;
+            b.C = CS + (k * nc) * n + T0; b.ldc = n; b.M = (nt - k) * nc; b.N = nd; b.K = kb;
+        }
+        if (full) {
+            GemmSeg& b = g3[nseg++];
+            b.A = V; b.lda = kb; b.B = Xb + nd; b.ldb = ldw;
+            b.C = Cr + K0 * nt + (k + 1); b.ldc = nt; b.M = m; b.N = ncs; b.K = kb;
+        }
+        ComputeFault cf[MAX_CF];
+        int ncf = 0;
+        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                cf[ncf++] = {faults[f].row - K0, faults[f].col - T0, faults[f].delta};
+        ABFT_CUDA_TRY(launch_gemm_f64(g3, nseg, 0, 1, cf, ncf, st, s));
+        timing_mark(PH_TMU, 0, s);
+        timing_mark(PH_VERIFY, 1, s);
+        for (int f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
+                                        faults[f].kind == ABFT_FAULT_ROW1D ||
+                                        faults[f].kind == ABFT_FAULT_COL1D))
+                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
+        if (check) {
+            TileSet ts = base_ts;
+            ts.I0 = k; ts.I1 = nt; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 0;
+            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+        }
+        timing_mark(PH_VERIFY, 0, s);
+    }
+    return ABFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
+               double* tau, const abft_fault* faults, int32_t nfaults, double tau_scale,
+               abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes);
+    if (rc != ABFT_OK) return rc;
+    if (n > 0 && tau == nullptr && ws != nullptr) return -7;
+    const int64_t N = (n + nb - 1) / nb;
+    for (int f = 0; f < nfaults; ++f)
+        if (!qr_fault_ok(faults[f], n, nb, N)) return -8;
+    const QrWs w = qr_ws(n, nb, mode);
+    if (ws == nullptr) {
+        *ws_bytes = w.total;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < w.total) return -13;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    DevStatus* st = (DevStatus*)(base + w.st);
+    ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    if (n > 0) {
+        rc = qr_steps(n, nb, mode, A, lda, tau, faults, nfaults, tau_scale, w, base, s);
+        if (rc != ABFT_OK) return rc;
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    if (rep) return finish_report(st, rep, s);
+    return ABFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
 }  // namespace
 
 extern "C" {

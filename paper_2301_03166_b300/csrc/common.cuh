@@ -182,6 +182,22 @@ cudaError_t launch_trsm_llu(const double* L, int64_t ldl, int64_t kb, double* B0
 cudaError_t launch_absmax(const double* A, int64_t lda, int64_t rows, int64_t cols, double* out,
                           cudaStream_t s);
 
+// QR kernels (k_qr.cu).
+cudaError_t launch_geqr2_coop(double* P, int64_t lda, int64_t m, int64_t kb, double* tau,
+                              double* nrm, double* part, double* wv, DevStatus* st,
+                              cudaStream_t s);
+cudaError_t launch_qr_pd_check(const double* P, int64_t lda, int64_t kb, const double* nrm,
+                               int step, int64_t K0, DevStatus* st, cudaStream_t s);
+cudaError_t launch_qr_prep_v(const double* P, int64_t lda, int64_t m, int64_t kb, double* V,
+                             cudaStream_t s);
+cudaError_t launch_qr_vsums(const double* V, int64_t m, int64_t kb, int64_t g, int64_t k,
+                            int64_t nt, int64_t K0, double* CS, int64_t ldcs, int64_t nc, int mode,
+                            cudaStream_t s);
+cudaError_t launch_larft(const double* Gneg, int64_t kb, const double* tau, double* T,
+                         cudaStream_t s);
+cudaError_t launch_qr_tau(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
+                          DevStatus* st, cudaStream_t s);
+
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();
 

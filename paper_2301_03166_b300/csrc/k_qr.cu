@@ -1,0 +1,266 @@
+// k_qr.cu -- kernels of the blocked ABFT Householder QR (Sec. 2.1 PD / TMU;
+// Sec. 3.1.2 checksums).  PD = geqr2 on the (n - K0) x kb panel (LAPACK larfg
+// convention) as one cooperative launch, then the triangular factor T of the
+// block reflector I - V T V^T; the TMU is three FP64 GEMM launches of
+// k_gemm_f64 (W = V^T C, X = T^T W, C -= V X) issued by the host.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int QT = 256;
+constexpr int QMAXR = 1024;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    return s;
+}
+
+// Cooperative geqr2 on the panel P (m x kb, row-major, ld lda).  part is a
+// G x (kb + 1) scratch of per-CTA partial sums, wv a kb scratch for the
+// reflector's row vector w, nrm receives the column norms before the PD.
+__global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64_t m, int kb,
+                                                   double* tau, double* nrm, double* part,
+                                                   double* wv, DevStatus* st) {
+    __shared__ double red[QT / 32];
+    __shared__ double wl[512];
+    __shared__ double vloc[QMAXR];
+    const unsigned G = gridDim.x;
+    const int64_t R = (m + G - 1) / G;
+    const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
+    const int ld = kb + 1;
+    double* mypart = part + (int64_t)blockIdx.x * ld;
+    // column norms before the PD (for the norm-preservation check)
+    for (int c = threadIdx.x; c < kb; c += QT) {
+        double s = 0.0;
+        for (int64_t i = r0; i < r1; ++i) s += P[i * lda + c] * P[i * lda + c];
+        mypart[c] = s;
+    }
+    if (!grid_barrier(st, G)) return;
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < kb; c += QT) {
+            double s = 0.0;
+            for (unsigned b = 0; b < G; ++b) s += part[(int64_t)b * ld + c];
+            nrm[c] = sqrt(s);
+        }
+    if (!grid_barrier(st, G)) return;
+    for (int j = 0; j < kb; ++j) {
+        // A: partial |x(2:)|^2 and partial dots x(2:)^T P[:, c] over my rows i > j
+        const int64_t ibeg = r0 > j + 1 ? r0 : j + 1;
+        double ss = 0.0;
+        for (int64_t i = ibeg + threadIdx.x; i < r1; i += QT) {
+            double x = P[i * lda + j];
+            ss += x * x;
+        }
+        ss = block_sum(ss, red);
+        if (threadIdx.x == 0) mypart[0] = ss;
+        for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
+            double d = 0.0;
+            for (int64_t i = ibeg; i < r1; ++i) d += P[i * lda + j] * P[i * lda + c];
+            mypart[1 + c] = d;
+        }
+        if (!grid_barrier(st, G)) return;
+        // B: every CTA forms beta, tau; CTA b reduces the dots of columns c = j+1+b, +G, ...
+        double sst = 0.0;
+        for (unsigned b = 0; b < G; ++b) sst += part[(int64_t)b * ld];
+        const double alpha = P[(int64_t)j * lda + j];
+        double tj = 0.0, beta = alpha, scal = 1.0;
+        if (sst != 0.0) {
+            double nr = sqrt(alpha * alpha + sst);
+            beta = alpha >= 0.0 ? -nr : nr;
+            tj = (beta - alpha) / beta;
+            scal = alpha - beta;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) tau[j] = tj;
+        if (tj != 0.0)
+            for (int c = j + 1 + blockIdx.x * QT + threadIdx.x; c < kb; c += G * QT) {
+                double d = 0.0;
+                for (unsigned b = 0; b < G; ++b) d += part[(int64_t)b * ld + 1 + c];
+                wv[c] = P[(int64_t)j * lda + c] + d / scal;
+            }
+        if (!grid_barrier(st, G)) return;
+        // C: v_i = x_i / (alpha - beta); a -= tau v w on my rows
+        if (tj == 0.0) continue;
+        for (int c = j + 1 + threadIdx.x; c < kb; c += QT) wl[c] = wv[c];
+        for (int64_t i = ibeg + threadIdx.x; i < r1; i += QT) {
+            double v = P[i * lda + j] / scal;
+            P[i * lda + j] = v;
+            vloc[i - r0] = v;
+        }
+        __syncthreads();
+        const int w = kb - j - 1;
+        if (w > 0) {
+            if (ibeg < r1) {
+                const int64_t nrow = r1 - ibeg;
+                for (int64_t e = threadIdx.x; e < nrow * w; e += QT) {
+                    int64_t i = ibeg + e / w;
+                    int c = j + 1 + (int)(e % w);
+                    double* a = P + i * lda + c;
+                    *a = __dsub_rn(*a, __dmul_rn(__dmul_rn(tj, vloc[i - r0]), wl[c]));
+                }
+            }
+            if (j >= r0 && j < r1)
+                for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
+                    double* a = P + (int64_t)j * lda + c;
+                    *a = __dsub_rn(*a, __dmul_rn(tj, wl[c]));
+                }
+        }
+        if (threadIdx.x == 0 && j >= r0 && j < r1) P[(int64_t)j * lda + j] = beta;
+        __syncthreads();
+    }
+}
+
+// PD check: column norms preserved, ||R[0:j+1, j]|| vs the norm before the PD.
+__global__ void k_qr_pd_check(const double* P, int64_t lda, int kb, const double* nrm, int step,
+                              int64_t K0, DevStatus* st) {
+    const double tau = st->tau;
+    for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += P[(int64_t)i * lda + j] * P[(int64_t)i * lda + j];
+        double d = sqrt(s) - nrm[j];
+        if (!(fabs(d) <= tau)) {
+            atomicAdd(&st->detected, 1ull);
+            atomicAdd(&st->uncorrectable, 1ull);
+            record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+        }
+    }
+}
+
+// V (unit lower trapezoidal, explicit ones and zeros) from the panel, and the
+// border rows 1^T V_I (and weighted) per tile-row I >= k.
+__global__ void k_qr_prep_v(const double* P, int64_t lda, int64_t m, int kb, double* V) {
+    const int64_t tot = m * kb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / kb;
+        int q = (int)(e % kb);
+        V[e] = (i == q) ? 1.0 : (i < q ? 0.0 : P[i * lda + q]);
+    }
+}
+
+__global__ void k_qr_vsums(const double* V, int64_t m, int kb, int64_t g, int64_t k, int64_t K0,
+                           double* CS, int64_t ldcs, int64_t nc, int mode) {
+    const int64_t I = k + blockIdx.x;
+    const int64_t gr0 = I * g, gr1 = (gr0 + g < K0 + m) ? gr0 + g : K0 + m;
+    for (int q = threadIdx.x; q < kb; q += blockDim.x) {
+        double s = 0.0, sw = 0.0;
+        for (int64_t gi = gr0; gi < gr1; ++gi) {
+            double v = V[(gi - K0) * kb + q];
+            s += v;
+            sw += (double)(gi - gr0 + 1) * v;
+        }
+        CS[(I * nc) * ldcs + K0 + q] = s;
+        if (mode == MODE_SINGLE) CS[(I * nc + 1) * ldcs + K0 + q] = sw;
+    }
+}
+
+// larft (forward, columnwise) from Gneg = -V^T V: T[j][j] = tau_j,
+// T[0:j, j] = -tau_j T[0:j, 0:j] (V^T v_j)[0:j].  One CTA, columns in order.
+__global__ void __launch_bounds__(512) k_larft(const double* Gneg, int kb, const double* tau,
+                                               double* T) {
+    __shared__ double y[512];
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) T[e] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        const double tj = tau[j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = -Gneg[(int64_t)i * kb + j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            double s = 0.0;
+            for (int q = i; q < j; ++q) s += T[(int64_t)i * kb + q] * y[q];
+            T[(int64_t)i * kb + j] = -tj * s;
+        }
+        if (threadIdx.x == 0) T[(int64_t)j * kb + j] = tj;
+        __syncthreads();
+    }
+}
+
+__global__ void k_colnorm_max(const double* A, int64_t lda, int64_t n, DevStatus* st) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (c < n)
+        for (int64_t i = 0; i < n; ++i) s += A[i * lda + c] * A[i * lda + c];
+    double v = sqrt(s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg((unsigned long long*)&st->amax, v);
+}
+
+__global__ void k_set_tau(double tau_scale, int64_t n, int64_t g, DevStatus* st) {
+    double t = tau_scale * 8.0;
+    t *= 0x1p-53;
+    t *= (double)n;
+    t *= (double)g;
+    t *= st->amax;
+    st->tau = t;
+}
+
+}  // namespace
+
+cudaError_t launch_geqr2_coop(double* P, int64_t lda, int64_t m, int64_t kb, double* tau,
+                              double* nrm, double* part, double* wv, DevStatus* st,
+                              cudaStream_t s) {
+    int64_t want = (m + 63) / 64;
+    int64_t G = want < num_sms() ? want : num_sms();
+    if (G < 1) G = 1;
+    while ((m + G - 1) / G > QMAXR) ++G;
+    if (G > num_sms()) return cudaErrorInvalidValue;
+    int kbi = (int)kb;
+    void* args[] = {&P, &lda, &m, &kbi, &tau, &nrm, &part, &wv, &st};
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_geqr2_coop, dim3((unsigned)G), dim3(QT),
+                                                args, 0, s);
+    note_launch();
+    return e;
+}
+
+cudaError_t launch_qr_pd_check(const double* P, int64_t lda, int64_t kb, const double* nrm,
+                               int step, int64_t K0, DevStatus* st, cudaStream_t s) {
+    k_qr_pd_check<<<1, 512, 0, s>>>(P, lda, (int)kb, nrm, step, K0, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qr_prep_v(const double* P, int64_t lda, int64_t m, int64_t kb, double* V,
+                             cudaStream_t s) {
+    int64_t blocks = (m * kb + 255) / 256;
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    k_qr_prep_v<<<(unsigned)blocks, 256, 0, s>>>(P, lda, m, (int)kb, V);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qr_vsums(const double* V, int64_t m, int64_t kb, int64_t g, int64_t k,
+                            int64_t nt, int64_t K0, double* CS, int64_t ldcs, int64_t nc, int mode,
+                            cudaStream_t s) {
+    k_qr_vsums<<<(unsigned)(nt - k), 256, 0, s>>>(V, m, (int)kb, g, k, K0, CS, ldcs, nc, mode);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_larft(const double* Gneg, int64_t kb, const double* tau, double* T,
+                         cudaStream_t s) {
+    k_larft<<<1, 512, 0, s>>>(Gneg, (int)kb, tau, T);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qr_tau(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
+                          DevStatus* st, cudaStream_t s) {
+    k_colnorm_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, lda, n, st);
+    note_launch();
+    k_set_tau<<<1, 1, 0, s>>>(tau_scale, n, g, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft
