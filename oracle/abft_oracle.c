@@ -357,10 +357,12 @@ static int chol_fault_ok(const orc_event* f, int64_t n, int64_t nb, int64_t N) {
  * checksums).  Per iteration k (K0 = k b, T0 = K0 + kb):
  *   PD : L_kk = chol(A_kk).  PD check: 1^T A_kk (carried) vs (1^T L_kk) L_kk^T.
  *   PU : L_Ik = A_Ik L_kk^{-T} for the panel below.  The checksum rows are
- *        carried through the same solve: s_I = c_Ik L_kk^{-T} (and the weighted
- *        row in single mode); the panel's row checksums are carried as
- *        x = A_Ik (L_kk^{-T} 1), taken from the panel before the solve.
- *        Verify / correct every panel tile.
+ *        carried through the same solve: s_I = c_Ik L_kk^{-T} and the weighted
+ *        row s^w_I = w_Ik L_kk^{-T} (both modes).  A triangular solve works row
+ *        by row, so an error in its output is 0D or spreads along its row; both
+ *        are located by the weighted column checksum, so every panel tile is
+ *        verified with the single-side rule (no row sums: a row-sum check would
+ *        need L_kk^{-T} 1, whose use cancels badly for ill-conditioned L_kk).
  *   TMU: A_IJ -= L_Ik L_Jk^T on the lower block triangle (diagonal blocks in
  *        full), with c_IJ -= s_I L_Jk^T and r_IJ -= L_Ik s_J^T.
  *        Verify / correct every trailing tile.
@@ -428,7 +430,7 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
         /* PU: checksum rows and panel rows through x L_kk^T = b */
         if (mode != M_NONE) {
             for (int64_t I = k + 1; I < nt; ++I)
-                for (int w = 0; w < (mode == M_SINGLE ? 2 : 1); ++w) {
+                for (int w = 0; w < 2; ++w) {
                     double* s = (w ? Cw : Cc) + I * n + K0;
                     for (int64_t j = 0; j < kb; ++j) {
                         double t = s[j];
@@ -436,18 +438,6 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
                         s[j] = t / Lkk[j * n + j];
                     }
                 }
-            if (mode == M_FULL) {
-                for (int64_t j = kb - 1; j >= 0; --j) { /* L_kk^T v = 1 */
-                    double t = 1.0;
-                    for (int64_t p = j + 1; p < kb; ++p) t -= Lkk[p * n + j] * v[p];
-                    v[j] = t / Lkk[j * n + j];
-                }
-                for (int64_t i = T0; i < n; ++i) {
-                    double t = 0.0;
-                    for (int64_t j = 0; j < kb; ++j) t += W[i * n + K0 + j] * v[j];
-                    xr[i] = t;
-                }
-            }
         }
         for (int64_t i = T0; i < n; ++i) {
             double* a = W + i * n + K0;
@@ -459,10 +449,14 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
         }
         for (int32_t f = 0; f < nfaults; ++f)
             if (faults[f].step == k && faults[f].kind == F_PANEL) apply_fault(W, n, g, &faults[f]);
-        for (int64_t I = k + 1; I < nt; ++I) {
-            int64_t r0 = I * g;
-            verify_tile(&c, W + r0 * n + K0, n, r0, K0, imin(g, n - r0), kb,
-                        Cc + I * n + K0, Cw + I * n + K0, xr + r0, 1);
+        {
+            vctx cp = c;   /* panel tiles: single-side rule in both checksum modes */
+            if (cp.mode == M_FULL) cp.mode = M_SINGLE;
+            for (int64_t I = k + 1; I < nt; ++I) {
+                int64_t r0 = I * g;
+                verify_tile(&cp, W + r0 * n + K0, n, r0, K0, imin(g, n - r0), kb,
+                            Cc + I * n + K0, Cw + I * n + K0, xr + r0, 1);
+            }
         }
         /* TMU */
         for (int64_t i = T0; i < n; ++i)
@@ -474,7 +468,7 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
             }
         if (mode != M_NONE) {
             for (int64_t I = k + 1; I < nt; ++I)
-                for (int w = 0; w < (mode == M_SINGLE ? 2 : 1); ++w) {
+                for (int w = 0; w < 2; ++w) {
                     double* C = (w ? Cw : Cc) + I * n;
                     for (int64_t j = T0; j < n; ++j) {
                         if (j / g > I) continue;

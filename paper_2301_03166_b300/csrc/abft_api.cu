@@ -86,22 +86,28 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of the pieces of a Cholesky workspace.
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
 
-CholWs chol_ws(int64_t n, int64_t nb, int mode) {
+CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false) {
     CholWs w{};
     w.nt = (n + nb - 1) / nb;
-    w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
+    // column sums and weighted column sums of every block row, in both modes
+    // (the panel is verified with the weighted sums)
+    w.nc = mode == ABFT_MODE_NONE ? 0 : 2;
     size_t off = 0;
     w.st = off; off = align_up(off + sizeof(DevStatus));
     w.cs = off; off = align_up(off + sizeof(double) * (size_t)(w.nc * w.nt) * (size_t)n);
     w.cr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n * (size_t)w.nt : 0));
-    w.xr = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n : 0));
-    w.v = off; off = align_up(off + (mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)nb : 0));
+    w.xr = off;
+    w.v = off;
     w.save = off; off = align_up(off + sizeof(double) * (size_t)n * (size_t)nb);
+    const int64_t ncq = w.nc > 0 ? w.nc : 1;
+    w.lq = off; off = align_up(off + (mixed ? sizeof(uint16_t) * (size_t)n * (size_t)nb : 0));
+    w.sig = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)w.nt : 0));
+    w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.total = off;
     return w;
 }
@@ -173,25 +179,29 @@ cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* s
 // Blocked ABFT Cholesky step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
 int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
                const abft_fault* faults, int32_t nfaults, double tau_scale, const CholWs& w,
-               char* base, cudaStream_t s) {
+               char* base, cudaStream_t s, int32_t dtype) {
+    const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    const int bf16 = dtype == ABFT_MIXED_BF16 ? 1 : 0;
+    uint16_t* Lq = (uint16_t*)(base + w.lq);
+    double* sig = (double*)(base + w.sig);
+    double* tq = (double*)(base + w.tq);
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
     double* Cr = (double*)(base + w.cr);
-    double* xr = (double*)(base + w.xr);
-    double* v = (double*)(base + w.v);
     double* save = (double*)(base + w.save);
     const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt;
     const bool full = mode == ABFT_MODE_FULL, check = mode != ABFT_MODE_NONE;
 
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 0, s));
-    ABFT_CUDA_TRY(launch_tau_chol(A, lda, n, g, tau_scale, st, s));
+    ABFT_CUDA_TRY(launch_tau_chol(A, lda, n, g, tau_scale, st, s, mixed ? 0x1p-24 : 0x1p-53));
     // checksum tile sets (Sec. 3.1.2: per matrix block)
     TileSet base_ts{};
     base_ts.A = A; base_ts.lda = lda;
     base_ts.cc = CS; base_ts.cw = CS + n; base_ts.ccI = nc * n;
     base_ts.cr = Cr; base_ts.crs = nt; base_ts.crJ = 1;
     base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
+    base_ts.weighted = 1;
     if (check) {
         TileSet ts = base_ts;
         ts.I0 = 0; ts.I1 = nt; ts.J0 = 0; ts.J1 = nt; ts.lower = 1;
@@ -206,26 +216,58 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
         ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, st, s));
         if (check)
             ABFT_CUDA_TRY(launch_chol_pd_check(Akk, lda, kb, CS + (k * nc) * n + K0, K0, (int)k,
-                                               full ? v : nullptr, mode, st, s));
+                                               nullptr, mode, st, s));
         timing_mark(PH_PD, 0, s);
         if (m <= 0) break;
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
         timing_mark(PH_PU, 1, s);
         TrsmSeg segs[2] = {{A + T0 * lda + K0, lda, m},
                            {CS + ((k + 1) * nc) * n + K0, n, (nt - k - 1) * nc}};
-        ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, full ? v : nullptr,
-                                      full ? xr + T0 : nullptr, st, s));
+        ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, nullptr, nullptr, st, s,
+                                      mixed));
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)
                 ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
-        if (check) {
+        if (check) {   // panel tiles: weighted column checksums locate 0D and row errors
             TileSet ts = base_ts;
-            ts.cr = xr; ts.crs = 1; ts.crJ = 0;
             ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k; ts.J1 = k + 1; ts.lower = 0;
             ts.ncol_end = T0;
-            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+            ABFT_CUDA_TRY(launch_verify(ts, MODE_SINGLE, (int)k, st, s));
         }
         timing_mark(PH_PU, 0, s);
+        if (mixed) {
+            // TMU on the tensor cores: quantized panel, FP32 accumulation, FP64 C
+            const int64_t ncq = nc > 0 ? nc : 1;
+            timing_mark(PH_TMU, 1, s);
+            ABFT_CUDA_TRY(launch_quant_panel(A + K0, lda, T0, n, kb, g, k + 1, nt, bf16, Lq, sig, tq,
+                                             ncq * kb, check ? 1 : 0, s));
+            ComputeFault mcf[MAX_CF];
+            int mncf = 0;
+            for (int f = 0; f < nfaults && mncf < MAX_CF; ++f)
+                if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                    mcf[mncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
+            ABFT_CUDA_TRY(launch_tmu_mixed(Lq, m, kb, bf16, A + T0 * lda + T0, lda, g, T0, sig, mcf,
+                                           mncf, st, s));
+            if (check) {
+                BorderSegHost bs[2] = {};
+                // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
+                bs[0].A = tq + ((k + 1) * ncq) * kb; bs[0].a_half = 0; bs[0].lda = kb;
+                bs[0].B = Lq; bs[0].b_half = 1; bs[0].ldb = kb;
+                bs[0].C = CS + ((k + 1) * nc) * n + T0; bs[0].ldc = n;
+                bs[0].M = (nt - k - 1) * nc; bs[0].N = m; bs[0].K = kb;
+                bs[0].r_off = 0; bs[0].r_div = nc; bs[0].r_base = k + 1;
+                bs[0].c_off = T0; bs[0].c_div = g; bs[0].c_base = 0;
+                // row-sum columns: r_I -= sigma_I sigma_J (Lq_I t_J^T)
+                bs[1].A = Lq; bs[1].a_half = 1; bs[1].lda = kb;
+                bs[1].B = tq + ((k + 1) * ncq) * kb; bs[1].b_half = 0; bs[1].ldb = ncq * kb;
+                bs[1].C = Cr + T0 * nt + (k + 1); bs[1].ldc = nt;
+                bs[1].M = m; bs[1].N = nt - k - 1; bs[1].K = kb;
+                bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;
+                bs[1].c_off = 0; bs[1].c_div = 1; bs[1].c_base = k + 1;
+                ABFT_CUDA_TRY(launch_border_mixed(bs, full ? 2 : 1, bf16, sig, st, s));
+            }
+            timing_mark(PH_TMU, 0, s);
+        } else {
         // TMU with the checksum borders folded into the same launch
         GemmSeg gs[3] = {};
         gs[0].A = A + T0 * lda + K0; gs[0].lda = lda;
@@ -244,7 +286,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
         if (full) {   // border columns: r_I -= L_I s_J^T
             GemmSeg& b = gs[nseg++];
             b.A = A + T0 * lda + K0; b.lda = lda;
-            b.B = CS + (k + 1) * n + K0; b.ldb = n;
+            b.B = CS + ((k + 1) * nc) * n + K0; b.ldb = nc * n;
             b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
             b.M = m; b.N = nt - k - 1; b.K = kb;
         }
@@ -256,6 +298,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
         timing_mark(PH_TMU, 1, s);
         ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 0, cf, ncf, st, s));
         timing_mark(PH_TMU, 0, s);
+        }
         timing_mark(PH_VERIFY, 1, s);
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
@@ -696,7 +739,9 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                void* ws, size_t* ws_bytes, void* stream) {
     if (n < 0) return -1;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
-    if (dtype != ABFT_F64) return dtype < 0 || dtype > 3 ? -3 : ABFT_ERR_UNSUPPORTED;
+    if (dtype < 0 || dtype > 3) return -3;
+    const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    if (dtype == ABFT_F32 || (mixed && nb % 128 != 0)) return ABFT_ERR_UNSUPPORTED;
     if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -4;
     if (n > 0 && A == nullptr && ws != nullptr) return -5;
     if (lda < std::max<int64_t>(1, n)) return -6;
@@ -712,7 +757,7 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
             same += faults[h].kind == ABFT_FAULT_COMPUTE && faults[h].step == faults[f].step;
         if (same > MAX_CF) return -7;
     }
-    const CholWs w = chol_ws(n, nb, mode);
+    const CholWs w = chol_ws(n, nb, mode, mixed);
     if (ws == nullptr) {
         *ws_bytes = w.total;
         return ABFT_OK;
@@ -723,7 +768,7 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
     DevStatus* st = (DevStatus*)(base + w.st);
     ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
     if (n > 0) {
-        int rc = chol_steps(n, nb, mode, A, lda, faults, nfaults, tau_scale, w, base, s);
+        int rc = chol_steps(n, nb, mode, A, lda, faults, nfaults, tau_scale, w, base, s, dtype);
         if (rc != ABFT_OK) return rc;
     }
     ABFT_CUDA_TRY(timing_collect(s));

@@ -109,6 +109,7 @@ struct TileSet {
     int64_t I0, I1, J0, J1;
     int lower;
     int64_t nrow_end, ncol_end;
+    int weighted;   // encode also writes the weighted column sums (cw)
 };
 
 cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s);
@@ -118,7 +119,7 @@ cudaError_t launch_inject(double* A, int64_t lda, int64_t n, int64_t g, const ab
 cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, double* save,
                                int restore, cudaStream_t s);
 cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                            DevStatus* st, cudaStream_t s);
+                            DevStatus* st, cudaStream_t s, double unit_roundoff = 0x1p-53);
 
 // FP64 update C -= A_op * B_op^T (NT) or A_op * B_op (NN), over up to three
 // segments (the main tiles and the checksum border rows / columns).
@@ -153,7 +154,7 @@ struct TrsmSeg {
 };
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s);
+                            cudaStream_t s, bool f32 = false);
 cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
                                  int64_t K0, int step, double* v, int mode, DevStatus* st,
                                  cudaStream_t s);
@@ -197,6 +198,29 @@ cudaError_t launch_larft(const double* Gneg, int64_t kb, const double* tau, doub
                          cudaStream_t s);
 cudaError_t launch_qr_tau(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
                           DevStatus* st, cudaStream_t s);
+
+// Mixed-precision TMU kernels (k_mixed.cu).
+struct BorderSegHost {
+    const void* A;
+    int a_half;          // 1: 16-bit quantized operand, 0: FP64
+    int64_t lda;
+    const void* B;
+    int b_half;
+    int64_t ldb;
+    double* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    int64_t r_off, r_div, r_base, c_off, c_div, c_base;
+};
+cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
+                               int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
+                               double* sig, double* tsum, int64_t tstride, int weighted,
+                               cudaStream_t s);
+cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
+                             int64_t ldc, int64_t g, int64_t off, const double* sig,
+                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s);
+cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
+                                const DevStatus* st, cudaStream_t s);
 
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();

@@ -42,9 +42,9 @@ __device__ __forceinline__ void tile_coords(const TileSet& ts, int64_t idx, int6
     }
 }
 
-// Sums of one tile into shared memory: colsum[j], wsum[j] (weights 1..nr,
-// single mode), rowsum[i] (full mode).
-template <int MODE>
+// Sums of one tile into shared memory: colsum[j], and when asked wsum[j]
+// (weights 1..nr) and rowsum[i].
+template <bool COLW, bool ROWS>
 __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* colsum,
                           double* wsum, double* rowsum, double (*part)[kMaxG]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -62,11 +62,11 @@ __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* 
                 int j = lane + 32 * t;
                 double v = (j < nc) ? row[j] : 0.0;
                 acc[t] += v;
-                if (MODE == MODE_SINGLE) wacc[t] = fma(wi, v, wacc[t]);
+                if (COLW) wacc[t] = fma(wi, v, wacc[t]);
                 rs += v;
             }
         }
-        if (MODE == MODE_FULL) {
+        if (ROWS) {
             rs = warp_sum(rs);
             if (lane == 0) rowsum[i] = rs;
         }
@@ -82,7 +82,7 @@ __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* 
         colsum[j] = s;
     }
     __syncthreads();
-    if (MODE == MODE_SINGLE) {
+    if (COLW) {
 #pragma unroll
         for (int t = 0; t < kMaxT; ++t)
             if (t < nt) part[warp][lane + 32 * t] = wacc[t];
@@ -104,7 +104,7 @@ __device__ __forceinline__ void tile_extent(const TileSet& ts, int64_t I, int64_
     nc = (int)(b < ts.g ? b : ts.g);
 }
 
-template <int MODE>
+template <bool COLW, bool ROWS>
 __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
     __shared__ double part[kWarps][kMaxG];
     __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
@@ -114,13 +114,13 @@ __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
     tile_extent(ts, I, J, nr, nc);
     if (nr <= 0 || nc <= 0) return;
     const double* T = ts.A + I * ts.g * ts.lda + J * ts.g;
-    tile_sums<MODE>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    tile_sums<COLW, ROWS>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
     double* cc = ts.cc + I * ts.ccI + J * ts.g;
     for (int j = threadIdx.x; j < nc; j += kThreads) {
         cc[j] = colsum[j];
-        if (MODE == MODE_SINGLE) ts.cw[I * ts.ccI + J * ts.g + j] = wsum[j];
+        if (COLW) ts.cw[I * ts.ccI + J * ts.g + j] = wsum[j];
     }
-    if (MODE == MODE_FULL) {
+    if (ROWS) {
         double* cr = ts.cr + I * ts.g * ts.crs + J * ts.crJ;
         for (int i = threadIdx.x; i < nr; i += kThreads) cr[(int64_t)i * ts.crs] = rowsum[i];
     }
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     double* cw = (MODE == MODE_SINGLE) ? ts.cw + I * ts.ccI + J * ts.g : nullptr;
     double* cr = (MODE == MODE_FULL) ? ts.cr + r0 * ts.crs + J * ts.crJ : nullptr;
     if (threadIdx.x == 0) { s_nfc = 0; s_nfr = 0; s_fc = 1 << 30; s_fr = 1 << 30; }
-    tile_sums<MODE>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    tile_sums<MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
     const double tau = st->tau;
     double dmax = 0.0;
     // d = recomputed - carried, kept in place of the sums
@@ -273,9 +273,10 @@ __global__ void k_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, dou
     }
 }
 
-// tau = tau_scale * 8 * u * n * g * max_i a_ii (left to right).
+// tau = tau_scale * 8 * u * n * g * max_i a_ii (left to right); u = 2^-53 for the
+// FP64 update, 2^-24 when the update accumulates in FP32 (mixed precision).
 __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                           DevStatus* st) {
+                           double u, DevStatus* st) {
     __shared__ double red[32];
     double m = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -289,7 +290,7 @@ __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, d
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
         double t = tau_scale * 8.0;
-        t *= 0x1p-53;
+        t *= u;
         t *= (double)n;
         t *= (double)g;
         t *= m;
@@ -310,8 +311,10 @@ int64_t tile_count(const TileSet& ts) {
 cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s) {
     int64_t nt = tile_count(ts);
     if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
-    if (mode == MODE_FULL) k_encode<MODE_FULL><<<(unsigned)nt, kThreads, 0, s>>>(ts);
-    else k_encode<MODE_SINGLE><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    const bool colw = mode == MODE_SINGLE || ts.weighted;
+    if (mode == MODE_FULL && colw) k_encode<true, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    else if (mode == MODE_FULL) k_encode<false, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    else k_encode<true, false><<<(unsigned)nt, kThreads, 0, s>>>(ts);
     note_launch();
     return cudaGetLastError();
 }
@@ -355,8 +358,8 @@ cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, do
 }
 
 cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                            DevStatus* st, cudaStream_t s) {
-    k_tau_chol<<<1, 1024, 0, s>>>(A, lda, n, g, tau_scale, st);
+                            DevStatus* st, cudaStream_t s, double unit_roundoff) {
+    k_tau_chol<<<1, 1024, 0, s>>>(A, lda, n, g, tau_scale, unit_roundoff, st);
     note_launch();
     return cudaGetLastError();
 }

@@ -1,0 +1,513 @@
+// k_mixed.cu -- mixed-precision trailing update of the ABFT Cholesky.
+//
+// The TMU C -= L_I L_J^T runs on the 5th-generation tensor cores: the panel
+// is quantized per g-row tile with a power-of-two scale sigma_I (BF16: the
+// tile maximum maps to at most 1; FP16: to at most 2^14), the products of the
+// quantized operands accumulate in FP32 in tensor memory (tcgen05.mma
+// kind::f16, M = N = 128, K = 16), and the epilogue applies
+// C_f64 -= sigma_I sigma_J acc in FP64.  The checksum borders use the same
+// quantized operands (their column sums t_I = 1^T Lq_I), so that the checksum
+// relation holds up to the FP32 accumulation error only; they are small and
+// run as an FP32 SIMT GEMM.  The panel solve runs in FP32 (k_trsm_rlt<float>),
+// the diagonal-block factorization, verification and correction stay in FP64.
+//
+// Kernel anatomy (one CTA per 128 x 128 output tile of the lower block
+// triangle, 192 threads, two CTAs per SM):
+//   warp 0   TMA producer: 128x64 BF16 boxes of A (rows i0..) and B (rows j0..)
+//            with 128-byte swizzle into a 3-stage ring of shared buffers
+//   warp 1   TMEM allocation (128 columns) and the single-thread MMA issuer;
+//            tcgen05.commit releases each stage and finally signals the epilogue
+//   warps 2-5  tcgen05.ld of the FP32 accumulator (each warp its 32-lane
+//            quarter), staged in shared memory, then a coalesced FP64
+//            read-modify-write of C with the scales.
+// Every mbarrier wait is bounded: on timeout the CTA records an error in the
+// status block, skips the rest of its work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int TM = 128, TN = 128, KC = 64;
+constexpr int STAGES = 3;
+constexpr int HALF_BYTES = TM * KC * 2;              // one 128 x 64 16-bit box
+constexpr int STAGE_BYTES = 2 * HALF_BYTES;          // A box + B box
+constexpr int MIX_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr int STG_LD = TN + 1;                       // epilogue staging row stride (floats)
+constexpr size_t MIX_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+
+static_assert(TM * STG_LD * 4 <= STAGES * STAGE_BYTES, "staging must fit in the stage ring");
+
+struct MixArgs {
+    double* C;
+    int64_t ldc;
+    int64_t M;          // trailing order
+    int64_t K;          // panel width (multiple of 64)
+    int64_t g, off;     // lower-block mask and scale index: tile-row of row i is (i + off) / g
+    const double* sig;  // per tile-row scale (global tile-row index)
+    int ncf;
+    ComputeFault cf[MAX_CF];
+    DevStatus* st;
+    int64_t tiles_n;
+    uint32_t idesc;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded parity wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 0) {
+            unsigned long long t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(MIX_THREADS) k_tmu_mixed(const __grid_constant__ CUtensorMap tmap,
+                                                          MixArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accb = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+    int* abort_flag = (int*)(tmem_slot + 1);
+
+    if (a.st->info != 0) return;
+    const int64_t tm = blockIdx.x / a.tiles_n, tn = blockIdx.x % a.tiles_n;
+    const int64_t i0 = tm * TM, j0 = tn * TN;
+    {
+        int64_t rlast = (i0 + TM - 1 < a.M - 1 ? i0 + TM - 1 : a.M - 1) + a.off;
+        if (rlast / a.g < (j0 + a.off) / a.g) return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int nk = (int)(a.K / KC);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % STAGES;
+                if (c >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((c - STAGES) / STAGES) & 1))) {
+                    *(volatile int*)abort_flag = 1;
+                    atomicExch(&a.st->error, 2);
+                    break;
+                }
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t* dst = smem + s * STAGE_BYTES;
+                tma_load_2d(dst, &tmap, &full[s], c * KC, (int)i0);
+                tma_load_2d(dst + HALF_BYTES, &tmap, &full[s], c * KC, (int)j0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % STAGES;
+                if (!mbar_wait(&full[s], (uint32_t)((c / STAGES) & 1))) {
+                    *(volatile int*)abort_flag = 1;
+                    atomicExch(&a.st->error, 2);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t abase = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t bbase = abase + HALF_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < KC / 16; ++kk)
+                    mma_f16(tmem, smem_desc(abase + kk * 32), smem_desc(bbase + kk * 32), a.idesc,
+                            (c | kk) != 0 ? 1u : 0u);
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(accb);
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+        const int q = warp & 3;
+        const int e = threadIdx.x - 64;                  // 0..127
+        float* stg = (float*)smem;
+        bool ok = mbar_wait(accb, 0);
+        if (!ok) {
+            *(volatile int*)abort_flag = 1;
+            atomicExch(&a.st->error, 2);
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int r = q * 32 + lane;
+#pragma unroll
+            for (int cc = 0; cc < TN / 32; ++cc) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
+#pragma unroll
+                for (int u = 0; u < 32; ++u) stg[r * STG_LD + cc * 32 + u] = __uint_as_float(v[u]);
+            }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (ok) {
+            const int we = e >> 5;
+            for (int rr = we; rr < TM; rr += 4) {
+                const int64_t i = i0 + rr;
+                if (i >= a.M) break;
+                const int64_t bi = (i + a.off) / a.g;
+                const double si = a.sig[bi];
+#pragma unroll
+                for (int t = 0; t < TN / 32; ++t) {
+                    const int64_t j = j0 + lane + 32 * t;
+                    if (j >= a.M) continue;
+                    const int64_t bj = (j + a.off) / a.g;
+                    if (bi < bj) continue;
+                    double* p = a.C + i * a.ldc + j;
+                    double v = *p - (si * a.sig[bj]) * (double)stg[rr * STG_LD + lane + 32 * t];
+                    for (int f = 0; f < a.ncf; ++f)
+                        if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
+                    *p = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+    }
+}
+
+// Quantize the panel per g-row tile: sigma_I = 2^(ceil(log2 max|L_I|) - e_t),
+// Lq = RN(L / sigma_I) in BF16 (e_t = 0) or FP16 (e_t = 14); t_I = 1^T Lq_I
+// and (single-side mode) tw_I = (1..g)^T Lq_I, in FP64.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_quant_panel(const double* P, int64_t lda, int64_t T0,
+                                                     int64_t n, int kb, int64_t g, int64_t I0,
+                                                     uint16_t* Lq, double* sig, double* tsum,
+                                                     int64_t tstride, int weighted) {
+    __shared__ double red[8];
+    const int64_t I = I0 + blockIdx.x;
+    const int64_t r0 = I * g, r1 = (r0 + g < n) ? r0 + g : n;
+    double m = 0.0;
+    for (int64_t e = threadIdx.x; e < (r1 - r0) * kb; e += blockDim.x) {
+        int64_t r = r0 + e / kb;
+        int p = (int)(e % kb);
+        m = fmax(m, fabs(P[r * lda + p]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    int e2 = 0;
+    double f = frexp(m, &e2);          // m = f 2^e2, f in [0.5, 1)
+    int cl = (f == 0.5) ? e2 - 1 : e2; // ceil(log2 m)
+    const double sigma = (m > 0.0) ? ldexp(1.0, cl - (BF16 ? 0 : 14)) : 1.0;
+    if (threadIdx.x == 0) sig[I] = sigma;
+    for (int p = threadIdx.x; p < kb; p += blockDim.x) {
+        double s = 0.0, sw = 0.0;
+        for (int64_t r = r0; r < r1; ++r) {
+            double x = P[r * lda + p] / sigma;
+            double xq;
+            uint16_t bits;
+            if (BF16) {
+                __nv_bfloat16 h = __double2bfloat16(x);
+                bits = __bfloat16_as_ushort(h);
+                xq = (double)__bfloat162float(h);
+            } else {
+                __half h = __double2half(x);
+                bits = __half_as_ushort(h);
+                xq = (double)__half2float(h);
+            }
+            Lq[(r - T0) * kb + p] = bits;
+            s += xq;
+            sw += (double)(r - r0 + 1) * xq;
+        }
+        tsum[I * tstride + p] = s;
+        if (weighted) tsum[I * tstride + kb + p] = sw;
+    }
+}
+
+// Small FP32 GEMM for the checksum borders of the mixed update:
+// C_f64[i][j] -= sr(i) sc(j) sum_p A[i][p] B[j][p], A rows FP64 (t sums) or
+// 16-bit (the quantized panel), B likewise; sr / sc are tile scales.
+struct BorderSeg {
+    const void* A;      // rows of K
+    int a_half;         // 1: A is 16-bit (BF16 / FP16 per `bf16`), 0: FP64
+    int64_t lda;
+    const void* B;
+    int b_half;
+    int64_t ldb;
+    double* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    // scale index of row i: (i + r_off) / r_div + r_base; of column j likewise
+    int64_t r_off, r_div, r_base, c_off, c_div, c_base;
+};
+struct BorderArgs {
+    BorderSeg seg[2];
+    int64_t tn[2], start[3];
+    int nseg;
+    int bf16;
+    const double* sig;
+    const DevStatus* st;
+};
+
+__device__ __forceinline__ float ld_op(const void* p, int half, int bf16, int64_t idx) {
+    if (!half) return (float)((const double*)p)[idx];
+    uint16_t b = ((const uint16_t*)p)[idx];
+    return bf16 ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+}
+
+__global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
+    __shared__ float As[16][65], Bs[16][65];
+    if (a.st->info != 0) return;
+    const int64_t bid = blockIdx.x;
+    const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    const BorderSeg& g = a.seg[s];
+    const int64_t local = bid - a.start[s];
+    const int64_t i0 = (local / a.tn[s]) * 64, j0 = (local % a.tn[s]) * 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int lr = t >> 2, lk = (t & 3) * 4;
+    float acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < g.K; k0 += 16) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t k = k0 + lk + u;
+            int64_t i = i0 + lr, j = j0 + lr;
+            As[lk + u][lr] = (i < g.M && k < g.K) ? ld_op(g.A, g.a_half, a.bf16, i * g.lda + k) : 0.f;
+            Bs[lk + u][lr] = (j < g.N && k < g.K) ? ld_op(g.B, g.b_half, a.bf16, j * g.ldb + k) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = i0 + ty + 16 * r;
+        if (i >= g.M) continue;
+        const double sr = a.sig[(i + g.r_off) / g.r_div + g.r_base];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = j0 + tx + 16 * c;
+            if (j >= g.N) continue;
+            const double sc = a.sig[(j + g.c_off) / g.c_div + g.c_base];
+            g.C[i * g.ldc + j] -= (sr * sc) * (double)acc[r][c];
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encoder() {
+    if (g_encode) return cudaSuccess;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess)
+        return e != cudaSuccess ? e : cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
+                               int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
+                               double* sig, double* tsum, int64_t tstride, int weighted,
+                               cudaStream_t s) {
+    if (I1 <= I0) return cudaSuccess;
+    if (bf16)
+        k_quant_panel<true><<<(unsigned)(I1 - I0), 256, 0, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq,
+                                                                  sig, tsum, tstride, weighted);
+    else
+        k_quant_panel<false><<<(unsigned)(I1 - I0), 256, 0, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq,
+                                                                   sig, tsum, tstride, weighted);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// C (m x m, trailing, FP64) -= sigma sigma^T o (Lq Lq^T) on the lower block triangle.
+cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
+                             int64_t ldc, int64_t g, int64_t off, const double* sig,
+                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    if (kb % KC != 0) return cudaErrorInvalidValue;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)kb, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)kb * 2};
+    cuuint32_t box[2] = {KC, TM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                          2, (void*)Lq, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_tmu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MIX_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    MixArgs a{};
+    a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.g = g; a.off = off; a.sig = sig; a.st = st;
+    a.ncf = 0;
+    for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
+    const int64_t tiles = (m + TM - 1) / TM;
+    a.tiles_n = tiles;
+    // kind::f16 instruction descriptor: D F32 (bits 4-5), A/B format BF16 = 1 or
+    // F16 = 0 (bits 7-9, 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+    const uint32_t fmt = bf16 ? 1u : 0u;
+    a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) |
+              ((uint32_t)(TM >> 4) << 24);
+    k_tmu_mixed<<<(unsigned)(tiles * tiles), MIX_THREADS, MIX_SMEM, s>>>(map, a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
+                                const DevStatus* st, cudaStream_t s) {
+    BorderArgs a{};
+    a.bf16 = bf16;
+    a.sig = sig;
+    a.st = st;
+    int64_t total = 0;
+    a.nseg = 0;
+    for (int i = 0; i < nseg; ++i) {
+        const BorderSegHost& h = segs[i];
+        if (h.M <= 0 || h.N <= 0 || h.K <= 0) continue;
+        BorderSeg& b = a.seg[a.nseg];
+        b.A = h.A; b.a_half = h.a_half; b.lda = h.lda;
+        b.B = h.B; b.b_half = h.b_half; b.ldb = h.ldb;
+        b.C = h.C; b.ldc = h.ldc; b.M = h.M; b.N = h.N; b.K = h.K;
+        b.r_off = h.r_off; b.r_div = h.r_div; b.r_base = h.r_base;
+        b.c_off = h.c_off; b.c_div = h.c_div; b.c_base = h.c_base;
+        a.tn[a.nseg] = (h.N + 63) / 64;
+        a.start[a.nseg] = total;
+        total += ((h.M + 63) / 64) * a.tn[a.nseg];
+        a.nseg++;
+    }
+    if (total == 0) return cudaSuccess;
+    a.start[a.nseg] = total;
+    k_border_mixed<<<(unsigned)total, 256, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft

@@ -78,11 +78,13 @@ struct TrsmArgs {
 // Solve X L^T = B for RB rows at a time (in place), L lower nb x nb.
 // Columns are processed in chunks of 32: X[:, c] -= X[:, :c] L[c, :c]^T
 // (all threads), then a per-row forward substitution inside the chunk.
+template <typename T>
 __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_bytes[];
+    T* smem = (T*)smem_bytes;
     const int ldx = a.nb + 1;
-    double* X = smem;                       // RB x (nb + 1)
-    double* Ls = smem + RB * ldx;           // CW x (CW + 1)
+    T* X = smem;                            // RB x (nb + 1)
+    T* Ls = smem + RB * ldx;                // CW x (CW + 1)
     if (a.st && a.st->info != 0) return;
     const int64_t bid = blockIdx.x;
     const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
@@ -92,34 +94,34 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     const int nb = a.nb, t = threadIdx.x;
     for (int e = t; e < RB * nb; e += TT) {
         int r = e / nb, p = e % nb;
-        X[r * ldx + p] = (r < nr) ? g.B[(r0 + r) * g.ldb + p] : 0.0;
+        X[r * ldx + p] = (r < nr) ? (T)g.B[(r0 + r) * g.ldb + p] : (T)0;
     }
     __syncthreads();
     if (a.v != nullptr && s == 0) {  // carried row sums x = B v, before the solve
         const int warp = t >> 5, lane = t & 31;
         for (int r = warp; r < nr; r += TT / 32) {
-            double acc = 0.0;
-            for (int p = lane; p < nb; p += 32) acc = fma(X[r * ldx + p], a.v[p], acc);
+            T acc = 0;
+            for (int p = lane; p < nb; p += 32) acc = fma(X[r * ldx + p], (T)a.v[p], acc);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) a.x[r0 + r] = acc;
+            if (lane == 0) a.x[r0 + r] = (double)acc;
         }
         __syncthreads();
     }
     const int gr = t >> 3, gq = (t & 7) * 4;  // GEMM part: row gr, cols gq..gq+3
     for (int c0 = 0; c0 < nb; c0 += CW) {
         const int w = (nb - c0) < CW ? (nb - c0) : CW;
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        T acc[4] = {0, 0, 0, 0};
         for (int p0 = 0; p0 < c0; p0 += CW) {
             __syncthreads();
             for (int e = t; e < CW * CW; e += TT) {
                 int q = e / CW, pp = e % CW;
-                Ls[q * (CW + 1) + pp] = (q < w) ? a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp] : 0.0;
+                Ls[q * (CW + 1) + pp] = (q < w) ? (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp] : (T)0;
             }
             __syncthreads();
 #pragma unroll 8
             for (int pp = 0; pp < CW; ++pp) {
-                double xv = X[gr * ldx + p0 + pp];
+                T xv = X[gr * ldx + p0 + pp];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) acc[u] = fma(xv, Ls[(gq + u) * (CW + 1) + pp], acc[u]);
             }
@@ -130,13 +132,13 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
             if (gq + u < w) X[gr * ldx + c0 + gq + u] -= acc[u];
         for (int e = t; e < CW * CW; e += TT) {
             int q = e / CW, pp = e % CW;
-            Ls[q * (CW + 1) + pp] = (q < w && pp <= q) ? a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp] : 0.0;
+            Ls[q * (CW + 1) + pp] = (q < w && pp <= q) ? (T)a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp] : (T)0;
         }
         __syncthreads();
         if (t < RB) {
-            double* xr = X + t * ldx + c0;
+            T* xr = X + t * ldx + c0;
             for (int jj = 0; jj < w; ++jj) {
-                double v = xr[jj];
+                T v = xr[jj];
                 for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
                 xr[jj] = v / Ls[jj * (CW + 1) + jj];
             }
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     }
     for (int e = t; e < nr * nb; e += TT) {
         int r = e / nb, p = e % nb;
-        g.B[(r0 + r) * g.ldb + p] = X[r * ldx + p];
+        g.B[(r0 + r) * g.ldb + p] = (double)X[r * ldx + p];
     }
 }
 
@@ -219,7 +221,7 @@ cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_
 
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool f32) {
     TrsmArgs a{};
     a.L = L;
     a.ldl = ldl;
@@ -241,15 +243,20 @@ cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const Trsm
     a.v = v;
     a.x = x;
     a.st = st;
-    size_t smem = (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)((RB * 513 + CW * (CW + 1)) * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_trsm_rlt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((RB * 513 + CW * (CW + 1)) * sizeof(float)));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_trsm_rlt<<<(unsigned)total, TT, smem, s>>>(a);
+    if (f32)
+        k_trsm_rlt<float><<<(unsigned)total, TT, (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(float), s>>>(a);
+    else
+        k_trsm_rlt<double><<<(unsigned)total, TT, (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(double), s>>>(a);
     note_launch();
     return cudaGetLastError();
 }

@@ -124,8 +124,10 @@ def test_2d_uncorrectable():
     A = W.spd_mmt(n, 14)
     f = [(1, oracle.F_MEMORY, 130, 100, 5.0), (1, oracle.F_MEMORY, 140, 110, 6.0)]
     L, info, rep = oracle.potrf(A, nb, FULL, f)
-    assert rep["uncorrectable"] >= 1 and rep["corrected"] == 0
-    assert rep["loc"][0][1] == oracle.E_UNCORR and rep["loc"][0][2:4] == (128, 96)
+    # the 2D error is reported at its step; what later steps do with the
+    # uncorrected error is not specified
+    assert rep["uncorrectable"] >= 1
+    assert rep["loc"][0][:4] == (1, oracle.E_UNCORR, 128, 96)
 
 
 def test_faults_in_distinct_blocks_all_corrected():

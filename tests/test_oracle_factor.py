@@ -55,7 +55,7 @@ def test_potf2_determinant_identity_4x4():
                 assert np.isclose(L[i, j], num / np.sqrt(D[j] * D[j + 1]), rtol=1e-10, atol=1e-12)
 
 
-@pytest.mark.parametrize("n,nb", [(1, 1), (7, 3), (33, 8), (64, 16), (64, 64)])
+@pytest.mark.parametrize("n,nb", [(1, 1), (7, 3), (33, 8), (64, 16), (64, 64), (256, 128)])
 def test_potrf_integer_exact(n, nb):
     """A = L0 L0^T with integer L0: every intermediate is an integer, so the
     blocked and the unblocked factorizations return L0 bit-exactly."""
