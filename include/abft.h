@@ -182,6 +182,46 @@ int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_potrs -- solve A X = B with the Cholesky factor L of abft_potrf
+ * (X = L^{-T} L^{-1} B, forward then backward block substitution).  Not in
+ * the paper; the solve that the factorization serves.
+ *   n, nrhs    order and number of right-hand sides (processed 16 at a time)
+ *   nb         block size of the substitution (multiple of 32, <= 512)
+ *   dtype      ABFT_F64: FP64 arithmetic; ABFT_F32 / ABFT_MIXED_*: FP32
+ *              arithmetic (L is read in FP64 and rounded on load)
+ *   L, ldl     lower factor (device, row-major); the upper triangle is not read
+ *   B, ldb     n x nrhs row-major (device); overwritten by X
+ * Errors: -1 n; -2 nrhs; -3 nb; -4 dtype; -5 L; -6 ldl; -7 B; -8 ldb;
+ * -10 workspace.
+ */
+int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
+               double* B, int64_t ldb, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * abft_posv_ir -- solve A X = B for SPD A by an ABFT Cholesky in the given
+ * dtype followed by iterative refinement (not in the paper: the precision
+ * form added on top of it).  L := A (lower triangle copied), abft_potrf(L),
+ * X = L^{-T} L^{-1} B, then repeat: R = B - A X in FP64 (A symmetric, read
+ * from its lower triangle), eta = max_r ||R_r||_inf / (||A||_inf ||X_r||_inf +
+ * ||B_r||_inf); stop when eta <= tol or after maxit corrections; otherwise
+ * D = L^{-T} L^{-1} R (FP32 for the mixed dtypes, FP64 for ABFT_F64) and
+ * X += D.  rep (optional) receives the factorization report plus ir_iters and
+ * backward_err (max over right-hand sides).  The call synchronizes the stream
+ * once per refinement step (to read eta).
+ *   A, lda     SPD matrix (device, lower triangle read, not modified)
+ *   L, ldl     n x n device buffer receiving the factor
+ *   B, ldb / X, ldx   n x nrhs right-hand sides / solution (device, row-major)
+ * Returns the factorization's code (0, info > 0 on a non-positive pivot,
+ * ABFT_ERR_UNCORRECTABLE) or an argument error: -1 n; -2 nrhs; -3 nb;
+ * -4 dtype; -5 mode; -6 A; -7 lda; -8 L; -9 ldl; -10 B; -11 ldb; -12 X;
+ * -13 ldx; -14 tol; -15 maxit; -16 faults; -22 workspace.
+ */
+int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mode, const double* A,
+                 int64_t lda, double* L, int64_t ldl, const double* B, int64_t ldb, double* X,
+                 int64_t ldx, double tol, int32_t maxit, const abft_fault* faults, int32_t nfaults,
+                 double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
  * own allocator or arena owns the whole GPU (or that may not grow the

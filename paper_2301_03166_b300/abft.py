@@ -46,6 +46,10 @@ _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
+    "abft_potrs": [_i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
+    "abft_posv_ir": [_i64, _i64, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                     _dbl, _i32, ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp,
+                     _sz, _vp],
     "abft_geqrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
     "abft_getrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
@@ -242,3 +246,54 @@ def geqrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, tau[:n], (report_dict(rep) if rep is not None else None)
+
+
+def potrs(L, B, nb=256, dtype=F64, workspace=None, stream=None):
+    """In place B := L^{-T} L^{-1} B with the lower factor L (CUDA float64)."""
+    _check_matrix(L, "L")
+    _check_matrix(B, "B")
+    n, nrhs = B.shape
+    Lb = lib()
+    need = ctypes.c_size_t(0)
+    rc = Lb.abft_potrs(n, nrhs, nb, dtype, None, max(1, L.stride(0)), None, max(1, B.stride(0)),
+                       None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, B.device)
+    size = ctypes.c_size_t(ws.numel())
+    rc = Lb.abft_potrs(n, nrhs, nb, dtype, ctypes.c_void_p(L.data_ptr()), max(1, L.stride(0)),
+                       ctypes.c_void_p(B.data_ptr()), max(1, B.stride(0)),
+                       ctypes.c_void_p(ws.data_ptr()), ctypes.byref(size), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return B
+
+
+def posv_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=50, faults=(),
+            tau_scale=1.0, L=None, X=None, workspace=None, stream=None, check=True):
+    """Solve A X = B (A SPD, lower triangle read) by an ABFT Cholesky in `dtype`
+    plus iterative refinement with an FP64 residual.  Returns (code, X, L, report)."""
+    _check_matrix(A)
+    _check_matrix(B, "B")
+    n, nrhs = B.shape
+    L = torch.empty_like(A) if L is None else L
+    X = torch.empty_like(B) if X is None else X
+    Lb = lib()
+    fa, nf = _faults(faults)
+    need = ctypes.c_size_t(0)
+    rc = Lb.abft_posv_ir(n, nrhs, nb, dtype, mode, None, max(1, A.stride(0)), None,
+                         max(1, L.stride(0)), None, max(1, B.stride(0)), None, max(1, X.stride(0)),
+                         tol, maxit, fa, nf, tau_scale, None, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    rep = Report()
+    size = ctypes.c_size_t(ws.numel())
+    rc = Lb.abft_posv_ir(n, nrhs, nb, dtype, mode, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                         ctypes.c_void_p(L.data_ptr()), L.stride(0), ctypes.c_void_p(B.data_ptr()),
+                         B.stride(0), ctypes.c_void_p(X.data_ptr()), X.stride(0), tol, maxit, fa,
+                         nf, tau_scale, ctypes.byref(rep), ctypes.c_void_p(ws.data_ptr()),
+                         ctypes.byref(size), _stream(stream))
+    if check and rc < 0 and rc != ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    return rc, X, L, report_dict(rep)

@@ -694,6 +694,170 @@ int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
 
 namespace {
 
+// ------------------------------------------------------------- solves / IR
+constexpr int kSplit = 8;   // split-K factor of the FP64 residual
+
+size_t potrs_ws_bytes(int64_t n, int32_t dtype) {
+    const size_t f = (dtype == ABFT_F64) ? 0 : sizeof(float) * (size_t)n * 16;
+    return align_up(std::max<size_t>(f, 256));
+}
+
+int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
+              double* B, int64_t ldb, float* Yf, cudaStream_t s) {
+    for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
+        const int nr = (int)std::min<int64_t>(16, nrhs - r0);
+        if (dtype == ABFT_F64) {
+            ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, B + r0, ldb, s));
+        } else {
+            ABFT_CUDA_TRY(launch_copy_d2f(B + r0, ldb, Yf, 16, n, nr, s));
+            ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, s));
+            ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, B + r0, ldb, n, nr, s));
+        }
+    }
+    return ABFT_OK;
+}
+
+struct IrWs {
+    size_t chol, yf, R, P, rs, norms, eta, total;
+};
+
+IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
+    IrWs w{};
+    const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    size_t off = 0;
+    w.chol = off; off = align_up(off + chol_ws(n, nb, mode, mixed).total);
+    w.yf = off; off = align_up(off + sizeof(float) * (size_t)n * 16);
+    w.R = off; off = align_up(off + sizeof(double) * (size_t)n * 16);
+    w.P = off; off = align_up(off + sizeof(double) * (size_t)kSplit * (size_t)n * 16);
+    w.rs = off; off = align_up(off + sizeof(double) * (size_t)n);
+    w.norms = off; off = align_up(off + sizeof(unsigned long long) * 64);
+    w.eta = off; off = align_up(off + sizeof(double));
+    w.total = off;
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
+               double* B, int64_t ldb, void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
+    if (dtype < 0 || dtype > 3) return -4;
+    if (n > 0 && L == nullptr && ws != nullptr) return -5;
+    if (ldl < std::max<int64_t>(1, n)) return -6;
+    if (n > 0 && nrhs > 0 && B == nullptr && ws != nullptr) return -7;
+    if (ldb < std::max<int64_t>(1, nrhs)) return -8;
+    if (ws_bytes == nullptr) return -10;
+    const size_t need = potrs_ws_bytes(n, dtype);
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -10;
+    if (n == 0 || nrhs == 0) return ABFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = potrs_run(n, nrhs, nb, dtype, L, ldl, B, ldb, (float*)ws, s);
+    if (rc != ABFT_OK) return rc;
+    ABFT_CUDA_TRY(timing_collect(s));
+    return ABFT_OK;
+}
+
+int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mode, const double* A,
+                 int64_t lda, double* L, int64_t ldl, const double* B, int64_t ldb, double* X,
+                 int64_t ldx, double tol, int32_t maxit, const abft_fault* faults, int32_t nfaults,
+                 double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
+    if (dtype < 0 || dtype > 3 || dtype == ABFT_F32) return dtype == ABFT_F32 ? ABFT_ERR_UNSUPPORTED : -4;
+    if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -5;
+    const bool needp = ws != nullptr && n > 0;
+    if (needp && A == nullptr) return -6;
+    if (lda < std::max<int64_t>(1, n)) return -7;
+    if (needp && L == nullptr) return -8;
+    if (ldl < std::max<int64_t>(1, n)) return -9;
+    if (needp && nrhs > 0 && B == nullptr) return -10;
+    if (ldb < std::max<int64_t>(1, nrhs)) return -11;
+    if (needp && nrhs > 0 && X == nullptr) return -12;
+    if (ldx < std::max<int64_t>(1, nrhs)) return -13;
+    if (!(tol >= 0.0)) return -14;
+    if (maxit < 0) return -15;
+    if (ws_bytes == nullptr) return -22;
+    const IrWs w = ir_ws(n, nb, mode, dtype);
+    size_t pws = 0;
+    int rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, nullptr, nullptr,
+                        &pws, nullptr);
+    if (rc != ABFT_OK) return rc == -7 ? -16 : rc;
+    if (ws == nullptr) {
+        *ws_bytes = w.total;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < w.total) return -22;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    abft_report prep;
+    abft_report* pr = rep ? rep : &prep;
+    // factor a copy of A (lower triangle)
+    ABFT_CUDA_TRY(launch_copy_d2d(A, lda, L, ldl, n, (int)n, s));
+    size_t have = pws;
+    rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, pr, base + w.chol,
+                    &have, stream);
+    if (rc > 0 || rc == ABFT_ERR_CUDA || rc == ABFT_ERR_TIMEOUT) return rc;
+    const int factor_rc = rc;
+    if (n == 0 || nrhs == 0) return factor_rc;
+    float* Yf = (float*)(base + w.yf);
+    double* R = (double*)(base + w.R);
+    double* P = (double*)(base + w.P);
+    double* rs = (double*)(base + w.rs);
+    unsigned long long* nrm = (unsigned long long*)(base + w.norms);
+    unsigned long long *anorm = nrm, *bmax = nrm + 1, *rmax = nrm + 17, *xmax = nrm + 33;
+    double* eta_d = (double*)(base + w.eta);
+    int32_t iters_max = 0;
+    double eta_max = 0.0;
+    for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
+        const int nr = (int)std::min<int64_t>(16, nrhs - r0);
+        ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
+        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, s));
+        // X0 = L^{-T} L^{-1} B
+        ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
+        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, Yf, s);
+        if (rc != ABFT_OK) return rc;
+        int32_t it = 0;
+        double eta = 0.0;
+        for (;; ++it) {
+            ABFT_CUDA_TRY(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long) * 32, s));
+            ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P, kSplit,
+                                          rmax, xmax, s));
+            ABFT_CUDA_TRY(launch_eta(rmax, xmax, anorm, bmax, nr, eta_d, s));
+            ABFT_CUDA_TRY(cudaMemcpyAsync(&eta, eta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+            ABFT_CUDA_TRY(cudaStreamSynchronize(s));
+            if (eta <= tol || it >= maxit || !(eta == eta)) break;
+            // correction D = L^{-T} L^{-1} R in the solve precision, X += D
+            if (dtype == ABFT_F64) {
+                ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, s));
+                ABFT_CUDA_TRY(launch_add_f64(X + r0, ldx, R, 16, n, nr, s));
+            } else {
+                ABFT_CUDA_TRY(launch_copy_d2f(R, 16, Yf, 16, n, nr, s));
+                ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, s));
+                ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
+            }
+        }
+        iters_max = std::max(iters_max, it);
+        eta_max = std::max(eta_max, eta);
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    pr->ir_iters = iters_max;
+    pr->backward_err = eta_max;
+    return factor_rc;
+}
+
+}  // extern "C"
+
+namespace {
+
 }  // namespace
 
 extern "C" {

@@ -222,6 +222,33 @@ cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16
 cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
                                 const DevStatus* st, cudaStream_t s);
 
+// Solves and iterative refinement (k_solve.cu).
+int potrs_max_rhs();
+cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
+                             double* B, int64_t ldb, cudaStream_t s);
+cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
+                             float* B, int64_t ldb, cudaStream_t s);
+cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
+                            int cols, cudaStream_t s);
+cudaError_t launch_copy_d2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
+                            int cols, cudaStream_t s);
+cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const double* X, int64_t ldx,
+                            const double* B, int64_t ldb, int nrhs, double* R, int64_t ldr,
+                            double* P, int nsplit, unsigned long long* rmax,
+                            unsigned long long* xmax, cudaStream_t s);
+cudaError_t launch_inf_norms(const double* A, int64_t lda, int64_t n, const double* B, int64_t ldb,
+                             int nrhs, double* rs, unsigned long long* anorm,
+                             unsigned long long* bmax, cudaStream_t s);
+cudaError_t launch_eta(const unsigned long long* rmax, const unsigned long long* xmax,
+                       const unsigned long long* anorm, const unsigned long long* bmax, int nrhs,
+                       double* eta, cudaStream_t s);
+cudaError_t launch_add_f32(double* X, int64_t ldx, const float* D, int64_t ldd, int64_t n, int nrhs,
+                           cudaStream_t s);
+cudaError_t launch_add_f64(double* X, int64_t ldx, const double* D, int64_t ldd, int64_t n,
+                           int nrhs, cudaStream_t s);
+cudaError_t launch_copy_f2d(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
+                            int cols, cudaStream_t s);
+
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();
 
