@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-overhead", action="store_true", help="skip the NONE-mode overhead run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
+    p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
     return p.parse_args()
 
 
@@ -287,6 +289,70 @@ def run_ours(args, ws, rank, local):
         overhead = {"ms_full": ms_step, "ms_none": ms_none,
                     "abft_overhead_pct": 100.0 * (ms_step / ms_none - 1.0)}
 
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        out = None
+        for _ in range(steps):
+            out = fn()
+        t1.record()
+        torch.cuda.synchronize(dev)
+        return t0.elapsed_time(t1) / steps, out
+
+    mixed = None
+    if not args.no_mixed:
+        # time to solution of A X = B (16 right-hand sides) at a 1e-12 backward
+        # error: FP64 form = FP64 ABFT potrf + FP64 potrs; mixed = BF16 / FP16
+        # ABFT potrf + iterative refinement (posv_ir), same matrix and faults.
+        B = torch.from_numpy(W.rhs(n, 16, seed=1003)).to(dev)
+        Xb = torch.empty_like(B)
+        Lbuf = torch.empty_like(A0)
+        def fp64_solve():
+            A.copy_(A0)
+            abft.potrf(A, nb, abft.FULL, faults=faults, workspace=wsp)
+            Xb.copy_(B)
+            abft.potrs(A, Xb, nb, abft.F64)
+            return None
+        ms_fp64, _ = timed(fp64_solve, 1, 1)
+        mixed = {"fp64_ms_to_solution": ms_fp64}
+        for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
+            def mixed_solve():
+                return abft.posv_ir(A0, B, nb, dt, abft.FULL, tol=1e-12, maxit=100, faults=faults,
+                                    L=Lbuf, X=Xb, workspace=wsp)
+            ms_mix, res = timed(mixed_solve, max(1, args.steps), 1)
+            rc_m, _, _, rep_m = res
+            mixed[name] = {"ms_to_solution": ms_mix, "speedup_vs_fp64": ms_fp64 / ms_mix,
+                           "tflops_equiv": chol_flops(n) / (ms_mix * 1e-3) / 1e12,
+                           "ir_iters": rep_m["ir_iters"], "backward_err": rep_m["backward_err"],
+                           "rc": rc_m, "faults_corrected": rep_m["corrected"]}
+        del Lbuf, Xb, B
+
+    lu_qr = None
+    if not args.no_lu_qr:
+        lu_qr = {}
+        U0 = W.uniform_torch(n, seed=1001 + n, device=dev)
+        lu_f = W.fault_schedule(n, nb, "lu", seed=3000 + n)
+        qr_f = W.fault_schedule(n, nb, "qr", seed=4000 + n)
+        def lu_step():
+            A.copy_(U0)
+            return abft.getrf(A, nb, abft.FULL, faults=lu_f, workspace=wsp)
+        def qr_step():
+            A.copy_(U0)
+            return abft.geqrf(A, nb, abft.FULL, faults=qr_f, workspace=wsp)
+        for name, fn, fl, flops in (("lu", lu_step, lu_f, 2 * n ** 3 / 3),
+                                    ("qr", qr_step, qr_f, 4 * n ** 3 / 3)):
+            ms_x, res = timed(fn, 1, 1)
+            rep_x = res[-1]
+            lu_qr[name] = {"ms": ms_x, "tflops": flops / (ms_x * 1e-3) / 1e12,
+                           "pct_of_fp64_peak": 100 * flops / (ms_x * 1e-3) / 1e12 / peak,
+                           "faults_located": [(e[0], e[2], e[3]) for e in rep_x["loc"]]
+                           == sorted((f[0], f[2], f[3]) for f in fl)}
+        del U0
+
     e2e = None
     if not args.no_e2e:
         A0h = A0.cpu().pin_memory()
@@ -331,6 +397,7 @@ def run_ours(args, ws, rank, local):
             "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
+            "mixed_precision_ir": mixed, "lu_qr": lu_qr,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
