@@ -248,7 +248,8 @@ size_t abft_noalloc_capacity(void);
  * times only to predict slack, Sec. 3.2.1).
  * abft_timing_enable(on): when on != 0, every entry point records CUDA events
  *   around its phases on its stream (0 PD + PD check, 1 PU + panel verify,
- *   2 TMU, 3 fault injection + trailing verify, 4 encode / set-up), then
+ *   2 TMU, 3 fault injection + trailing verify, 4 encode / set-up, 5 solves
+ *   and refinement), then
  *   synchronizes its stream before returning; resets the accumulators.
  * abft_timing_read(ms, count, nphase): accumulated milliseconds (and number of
  *   timed intervals) per phase since the last enable.

@@ -173,7 +173,7 @@ def potrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
     return rc, (report_dict(rep) if rep is not None else None)
 
 
-PHASES = ("pd", "pu", "tmu", "verify", "other")
+PHASES = ("pd", "pu", "tmu", "verify", "other", "solve")
 
 
 def timing_enable(on=True):

@@ -27,8 +27,8 @@ bool g_timing = false;
 std::vector<cudaEvent_t> g_pool;      // reusable events
 size_t g_pool_used = 0;
 std::vector<Mark> g_marks;            // marks of the current call
-double g_ms[PH_COUNT] = {0, 0, 0, 0, 0};
-long long g_calls[PH_COUNT] = {0, 0, 0, 0, 0};
+double g_ms[PH_COUNT] = {};
+long long g_calls[PH_COUNT] = {};
 cudaEvent_t next_event() {
     if (g_pool_used == g_pool.size()) {
         cudaEvent_t e;
@@ -759,7 +759,9 @@ int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double*
     if (*ws_bytes < need) return -10;
     if (n == 0 || nrhs == 0) return ABFT_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    timing_mark(PH_SOLVE, 1, s);
     int rc = potrs_run(n, nrhs, nb, dtype, L, ldl, B, ldb, (float*)ws, s);
+    timing_mark(PH_SOLVE, 0, s);
     if (rc != ABFT_OK) return rc;
     ABFT_CUDA_TRY(timing_collect(s));
     return ABFT_OK;
@@ -822,6 +824,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
         ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, s));
         // X0 = L^{-T} L^{-1} B
+        timing_mark(PH_SOLVE, 1, s);
         ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
         rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, Yf, s);
         if (rc != ABFT_OK) return rc;
@@ -845,6 +848,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
                 ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
             }
         }
+        timing_mark(PH_SOLVE, 0, s);
         iters_max = std::max(iters_max, it);
         eta_max = std::max(eta_max, eta);
     }

@@ -253,7 +253,7 @@ cudaError_t launch_copy_f2d(const float* src, int64_t lds, double* dst, int64_t 
 void note_launch();
 
 // Per-phase GPU time accounting with CUDA events on the launch stream.
-enum { PH_PD = 0, PH_PU = 1, PH_TMU = 2, PH_VERIFY = 3, PH_OTHER = 4, PH_COUNT = 5 };
+enum { PH_PD = 0, PH_PU = 1, PH_TMU = 2, PH_VERIFY = 3, PH_OTHER = 4, PH_SOLVE = 5, PH_COUNT = 6 };
 bool timing_on();
 void timing_mark(int phase, int begin, cudaStream_t s);
 cudaError_t timing_collect(cudaStream_t s);

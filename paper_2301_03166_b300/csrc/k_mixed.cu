@@ -18,8 +18,9 @@
 //   warp 1   TMEM allocation (128 columns) and the single-thread MMA issuer;
 //            tcgen05.commit releases each stage and finally signals the epilogue
 //   warps 2-5  tcgen05.ld of the FP32 accumulator (each warp its 32-lane
-//            quarter), staged in shared memory, then a coalesced FP64
-//            read-modify-write of C with the scales.
+//            quarter), staged in shared memory; then all six warps do a
+//            coalesced FP64 read-modify-write of C with the scales, 16 loads
+//            in flight per thread.
 // Every mbarrier wait is bounded: on timeout the CTA records an error in the
 // status block, skips the rest of its work, frees its TMEM and returns.
 #include <cuda.h>
@@ -225,47 +226,67 @@ __global__ void __launch_bounds__(MIX_THREADS) k_tmu_mixed(const __grid_constant
             }
             if (ok) mma_commit(accb);
         }
-    } else {
-        // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+    }
+    __syncwarp();
+    // all warps: wait for the accumulator (bounded)
+    const bool acc_ok = mbar_wait(accb, 0);
+    if (!acc_ok && threadIdx.x == 0) {
+        *(volatile int*)abort_flag = 1;
+        atomicExch(&a.st->error, 2);
+    }
+    float* stg = (float*)smem;   // the stage ring is free once the accumulator is complete
+    if (acc_ok && warp >= 2) {
+        // TMEM -> shared staging: warp w reads its lane quarter q = w % 4
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int q = warp & 3;
-        const int e = threadIdx.x - 64;                  // 0..127
-        float* stg = (float*)smem;
-        bool ok = mbar_wait(accb, 0);
-        if (!ok) {
-            *(volatile int*)abort_flag = 1;
-            atomicExch(&a.st->error, 2);
-        } else {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int r = q * 32 + lane;
+        const int r = q * 32 + lane;
 #pragma unroll
-            for (int cc = 0; cc < TN / 32; ++cc) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
+        for (int cc = 0; cc < TN / 32; ++cc) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
 #pragma unroll
-                for (int u = 0; u < 32; ++u) stg[r * STG_LD + cc * 32 + u] = __uint_as_float(v[u]);
-            }
+            for (int u = 0; u < 32; ++u) stg[r * STG_LD + cc * 32 + u] = __uint_as_float(v[u]);
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (ok) {
-            const int we = e >> 5;
-            for (int rr = we; rr < TM; rr += 4) {
+    }
+    __syncthreads();
+    if (acc_ok && *(volatile int*)abort_flag == 0) {
+        // FP64 read-modify-write of C by all 6 warps, 4 rows x 4 column chunks
+        // (16 independent loads) in flight per thread
+        constexpr int NW = MIX_THREADS / 32;
+        for (int rb = warp; rb < TM; rb += NW * 4) {
+            double cv[4][4];
+            double* ptr[4][4];
+            double sc[4][4];
+            int rrv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rr = rb + u * NW;
+                rrv[u] = rr;
                 const int64_t i = i0 + rr;
-                if (i >= a.M) break;
-                const int64_t bi = (i + a.off) / a.g;
-                const double si = a.sig[bi];
+                const bool rowok = rr < TM && i < a.M;
+                const int64_t bi = rowok ? (i + a.off) / a.g : 0;
+                const double si = rowok ? a.sig[bi] : 0.0;
 #pragma unroll
                 for (int t = 0; t < TN / 32; ++t) {
                     const int64_t j = j0 + lane + 32 * t;
-                    if (j >= a.M) continue;
                     const int64_t bj = (j + a.off) / a.g;
-                    if (bi < bj) continue;
-                    double* p = a.C + i * a.ldc + j;
-                    double v = *p - (si * a.sig[bj]) * (double)stg[rr * STG_LD + lane + 32 * t];
-                    for (int f = 0; f < a.ncf; ++f)
-                        if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
-                    *p = v;
+                    const bool ok = rowok && j < a.M && bi >= bj;
+                    ptr[u][t] = ok ? a.C + i * a.ldc + j : nullptr;
+                    sc[u][t] = ok ? si * a.sig[bj] : 0.0;
+                    cv[u][t] = ok ? *ptr[u][t] : 0.0;
                 }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int t = 0; t < TN / 32; ++t) {
+                    if (ptr[u][t] == nullptr) continue;
+                    double v = cv[u][t] - sc[u][t] * (double)stg[rrv[u] * STG_LD + lane + 32 * t];
+                    const int64_t i = i0 + rrv[u], j = j0 + lane + 32 * t;
+                    for (int f = 0; f < a.ncf; ++f)
+                        if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
+                    *ptr[u][t] = v;
+                }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -20,24 +20,30 @@ constexpr int MAXRHS = 16;
 
 // Solve the kb x kb diagonal block in place: L Y = Y (TRANS = 0) or
 // L^T X = X (TRANS = 1) for nrhs <= 16 right-hand sides (Y row-major, ld ldy).
+// 32-row chunks: the chunk is first updated from the already solved rows (all
+// threads), then solved by substitution with its 32 x 32 block of L in shared
+// memory, one row per step, every (row, rhs) pair on its own thread.
 template <typename T, int TRANS>
-__global__ void __launch_bounds__(256) k_trsv_diag(const double* L, int64_t ldl, int kb, T* Y,
+__global__ void __launch_bounds__(512) k_trsv_diag(const double* L, int64_t ldl, int kb, T* Y,
                                                    int64_t ldy, int nrhs) {
     extern __shared__ __align__(16) unsigned char sb[];
     T* y = (T*)sb;                        // kb x MAXRHS
+    __shared__ T Lc[32][33];
+    __shared__ T xs[32][MAXRHS];
     const int t = threadIdx.x;
-    for (int e = t; e < kb * nrhs; e += 256) {
+    for (int e = t; e < kb * nrhs; e += blockDim.x) {
         int i = e / nrhs, r = e % nrhs;
         y[i * MAXRHS + r] = Y[(int64_t)i * ldy + r];
     }
     __syncthreads();
     const int nch = (kb + 31) / 32;
+    const int q = t >> 4, r = t & 15;     // this thread's (row in chunk, rhs)
     for (int ci = 0; ci < nch; ++ci) {
         const int c = TRANS ? nch - 1 - ci : ci;
         const int c0 = c * 32, c1 = (c0 + 32 < kb) ? c0 + 32 : kb, w = c1 - c0;
         // update the chunk from the solved rows
-        for (int e = t; e < w * nrhs; e += 256) {
-            const int q = e / nrhs, r = e % nrhs, i = c0 + q;
+        if (q < w && r < nrhs) {
+            const int i = c0 + q;
             T acc = 0;
             if (!TRANS) {
                 for (int p = 0; p < c0; ++p) acc += (T)L[(int64_t)i * ldl + p] * y[p * MAXRHS + r];
@@ -46,28 +52,31 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* L, int64_t ldl,
             }
             y[i * MAXRHS + r] -= acc;
         }
-        __syncthreads();
-        // substitution inside the chunk, one thread per right-hand side
-        if (t < nrhs) {
-            if (!TRANS) {
-                for (int j = c0; j < c1; ++j) {
-                    T v = y[j * MAXRHS + t];
-                    for (int p = c0; p < j; ++p) v -= (T)L[(int64_t)j * ldl + p] * y[p * MAXRHS + t];
-                    y[j * MAXRHS + t] = v / (T)L[(int64_t)j * ldl + j];
-                }
-            } else {
-                for (int j = c1 - 1; j >= c0; --j) {
-                    T v = y[j * MAXRHS + t];
-                    for (int p = j + 1; p < c1; ++p) v -= (T)L[(int64_t)p * ldl + j] * y[p * MAXRHS + t];
-                    y[j * MAXRHS + t] = v / (T)L[(int64_t)j * ldl + j];
-                }
-            }
+        // the chunk's block of L (transposed for the backward solve)
+        for (int e = t; e < 32 * 32; e += blockDim.x) {
+            int a = e >> 5, b = e & 31;
+            T v = 0;
+            if (a < w && b < w) v = TRANS ? (T)L[(int64_t)(c0 + b) * ldl + c0 + a]
+                                          : (T)L[(int64_t)(c0 + a) * ldl + c0 + b];
+            Lc[a][b] = v;     // row a of the (possibly transposed) chunk
         }
         __syncthreads();
+        // substitution: step s fixes row j (ascending, or descending for L^T)
+        for (int st = 0; st < w; ++st) {
+            const int jj = TRANS ? w - 1 - st : st;
+            if (r < nrhs && q < w) {
+                const T xj = y[(c0 + jj) * MAXRHS + r] / Lc[jj][jj];
+                if (q == jj) xs[q][r] = xj;
+                else if (TRANS ? q < jj : q > jj) y[(c0 + q) * MAXRHS + r] -= Lc[q][jj] * xj;
+            }
+            __syncthreads();
+        }
+        if (q < w && r < nrhs) y[(c0 + q) * MAXRHS + r] = xs[q][r];
+        __syncthreads();
     }
-    for (int e = t; e < kb * nrhs; e += 256) {
-        int i = e / nrhs, r = e % nrhs;
-        Y[(int64_t)i * ldy + r] = y[i * MAXRHS + r];
+    for (int e = t; e < kb * nrhs; e += blockDim.x) {
+        int i = e / nrhs, rr = e % nrhs;
+        Y[(int64_t)i * ldy + rr] = y[i * MAXRHS + rr];
     }
 }
 
@@ -269,7 +278,7 @@ cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ld
     const size_t smem = (size_t)nb * MAXRHS * sizeof(T);
     for (int64_t k = 0; k < N; ++k) {   // L Y = B
         const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0, T0 = K0 + kb;
-        k_trsv_diag<T, 0><<<1, 256, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
+        k_trsv_diag<T, 0><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
         note_launch();
         if (T0 < n) {
             k_trsv_update<T, 0><<<(unsigned)((n - T0 + 63) / 64), 256, 0, s>>>(
@@ -279,7 +288,7 @@ cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ld
     }
     for (int64_t k = N - 1; k >= 0; --k) {   // L^T X = Y
         const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0;
-        k_trsv_diag<T, 1><<<1, 256, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
+        k_trsv_diag<T, 1><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
         note_launch();
         if (K0 > 0) {
             k_trsv_update<T, 1><<<(unsigned)((K0 + 63) / 64), 256, 0, s>>>(
