@@ -222,6 +222,48 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
                  double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * Reverse mode (adjoints) of potrf, potrs and logdet -- not in the paper: the
+ * differentiation form added on top of it.  Convention: a function of a
+ * symmetric A that reads only its lower triangle has the lower-triangular
+ * adjoint Abar (df = sum_{i >= j} Abar[i][j] dA[i][j]); the symmetric gradient
+ * is (Abar + Abar^T) / 2.  All matrices are device, row-major FP64.
+ *
+ * abft_potrf_backward: given the factor L (lower triangle read) and the
+ * adjoint Lbar of L (lower triangle read), writes Abar: with sym == 0 the
+ * lower-triangle adjoint (strict upper triangle set to zero), with sym != 0
+ * the symmetric gradient (Abar + Abar^T) / 2 in both triangles.  Blocked reverse sweep of the
+ * right-looking algorithm (Murray, "Differentiation of the Cholesky
+ * decomposition", 2016), block size nb, from the last block to the first:
+ * Lbar21 -= (Abar22 + Abar22^T) L21; Abar21 = Lbar21 L11^{-1};
+ * Lbar11 -= tril(Abar21^T L21); Abar11 = Phi(S + S^T) with
+ * S = L11^{-T} Phi(L11^T Lbar11) L11^{-1}, Phi = lower triangle with halved
+ * diagonal.  Only L and Lbar are read: no forward intermediates are stored.
+ * Errors: -1 n; -2 nb; -3 L; -4 ldl; -5 Lbar; -6 ldlb; -7 Abar; -8 ldab; -11 ws.
+ *
+ * abft_potrs_backward: for X = A^{-1} B computed with the factor L and the
+ * adjoint Xbar of X (n x nrhs, nrhs <= 16): Bbar = A^{-1} Xbar, and
+ * Lbar -= tril((Bbar X^T + X Bbar^T) L) (accumulated into Lbar's lower
+ * triangle).  Errors: -1 n; -2 nrhs; -3 nb; -4..-13 pointers and leading
+ * dimensions in argument order; -15 ws.
+ *
+ * abft_logdet: *out (device double) = log det A = 2 sum_i log L[i][i].
+ * abft_logdet_backward: Lbar[i][i] += 2 gbar / L[i][i] for the adjoint gbar
+ * of log det A.
+ * abft_tril: zero the strict upper triangle of A (n x n).
+ */
+int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, const double* Lbar,
+                        int64_t ldlb, double* Abar, int64_t ldab, int32_t sym, void* ws,
+                        size_t* ws_bytes, void* stream);
+int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, int64_t ldl,
+                        const double* X, int64_t ldx, const double* Xbar, int64_t ldxb,
+                        double* Bbar, int64_t ldbb, double* Lbar, int64_t ldlb, void* ws,
+                        size_t* ws_bytes, void* stream);
+int abft_logdet(int64_t n, const double* L, int64_t ldl, double* out, void* stream);
+int abft_logdet_backward(int64_t n, const double* L, int64_t ldl, double gbar, double* Lbar,
+                         int64_t ldlb, void* stream);
+int abft_tril(int64_t n, double* A, int64_t lda, void* stream);
+
+/*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
  * own allocator or arena owns the whole GPU (or that may not grow the

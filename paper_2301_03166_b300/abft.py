@@ -46,6 +46,12 @@ _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
+    "abft_potrf_backward": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz, _vp],
+    "abft_potrs_backward": [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                            _i64, _vp, _sz, _vp],
+    "abft_logdet": [_i64, _vp, _i64, _vp, _vp],
+    "abft_logdet_backward": [_i64, _vp, _i64, _dbl, _vp, _i64, _vp],
+    "abft_tril": [_i64, _vp, _i64, _vp],
     "abft_potrs": [_i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
     "abft_posv_ir": [_i64, _i64, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                      _dbl, _i32, ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp,
@@ -297,3 +303,85 @@ def posv_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=50, faul
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, X, L, report_dict(rep)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ws_call(fn, query_args, run_args, device, workspace):
+    need = ctypes.c_size_t(0)
+    rc = fn(*query_args, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, device)
+    size = ctypes.c_size_t(ws.numel())
+    return run_args, ws, size
+
+
+def potrf_backward(L, Lbar, nb=256, sym=True, Abar=None, workspace=None, stream=None):
+    """Adjoint of the Cholesky factorization: Abar from L and Lbar (lower
+    triangles read).  sym=True returns the symmetric gradient."""
+    _check_matrix(L, "L")
+    _check_matrix(Lbar, "Lbar")
+    n = L.shape[0]
+    Abar = torch.empty_like(L) if Abar is None else Abar
+    Lb = lib()
+    need = ctypes.c_size_t(0)
+    rc = Lb.abft_potrf_backward(n, nb, None, max(1, L.stride(0)), None, max(1, Lbar.stride(0)), None,
+                                max(1, Abar.stride(0)), 1 if sym else 0, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, L.device)
+    size = ctypes.c_size_t(ws.numel())
+    rc = Lb.abft_potrf_backward(n, nb, _ptr(L), L.stride(0), _ptr(Lbar), Lbar.stride(0), _ptr(Abar),
+                                Abar.stride(0), 1 if sym else 0, _ptr(ws), ctypes.byref(size),
+                                _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return Abar
+
+
+def potrs_backward(L, X, Xbar, Lbar, nb=256, workspace=None, stream=None):
+    """For X = A^{-1} B: returns Bbar = A^{-1} Xbar and accumulates
+    Lbar -= tril((Bbar X^T + X Bbar^T) L)."""
+    n, nrhs = X.shape
+    Bbar = torch.empty_like(X)
+    Lb = lib()
+    need = ctypes.c_size_t(0)
+    rc = Lb.abft_potrs_backward(n, nrhs, nb, None, max(1, L.stride(0)), None, max(1, X.stride(0)),
+                                None, max(1, Xbar.stride(0)), None, max(1, Bbar.stride(0)), None,
+                                max(1, Lbar.stride(0)), None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, L.device)
+    size = ctypes.c_size_t(ws.numel())
+    rc = Lb.abft_potrs_backward(n, nrhs, nb, _ptr(L), L.stride(0), _ptr(X), X.stride(0), _ptr(Xbar),
+                                Xbar.stride(0), _ptr(Bbar), Bbar.stride(0), _ptr(Lbar),
+                                Lbar.stride(0), _ptr(ws), ctypes.byref(size), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return Bbar
+
+
+def logdet(L, out=None, stream=None):
+    out = torch.empty((), dtype=torch.float64, device=L.device) if out is None else out
+    rc = lib().abft_logdet(L.shape[0], _ptr(L), max(1, L.stride(0)), _ptr(out), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return out
+
+
+def logdet_backward(L, gbar, Lbar, stream=None):
+    rc = lib().abft_logdet_backward(L.shape[0], _ptr(L), max(1, L.stride(0)), float(gbar),
+                                    _ptr(Lbar), max(1, Lbar.stride(0)), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return Lbar
+
+
+def tril_(A, stream=None):
+    rc = lib().abft_tril(A.shape[0], _ptr(A), max(1, A.stride(0)), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return A

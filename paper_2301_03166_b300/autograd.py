@@ -1,0 +1,86 @@
+"""torch.autograd Functions over the library's Cholesky, solve and logdet.
+
+Forward and backward both run in libabft kernels (potrf / potrs / logdet and
+their adjoints); torch only allocates the tensors.  The Cholesky adjoint is
+the blocked reverse sweep, which needs L alone (no stored intermediates), so
+memory stays at the size of the factor for any n.
+"""
+import torch
+
+from . import abft
+
+
+class Cholesky(torch.autograd.Function):
+    """L = chol(A) (lower, zero above the diagonal) with ABFT checksums."""
+
+    @staticmethod
+    def forward(ctx, A, nb=256, mode=abft.FULL):
+        L = A.detach().contiguous().clone()
+        rc, rep = abft.potrf(L, nb, mode)
+        if rc != 0:
+            raise abft.AbftError(rc, abft.strerror(rc))
+        abft.tril_(L)
+        ctx.save_for_backward(L)
+        ctx.nb = nb
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        (L,) = ctx.saved_tensors
+        G = abft.potrf_backward(L, Lbar.contiguous(), ctx.nb, sym=True)
+        return G, None, None
+
+
+class CholeskySolve(torch.autograd.Function):
+    """X = A^{-1} B from the factor L of A."""
+
+    @staticmethod
+    def forward(ctx, L, B, nb=256):
+        X = B.detach().contiguous().clone()
+        abft.potrs(L.detach(), X, nb, abft.F64)
+        ctx.save_for_backward(L, X)
+        ctx.nb = nb
+        return X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        L, X = ctx.saved_tensors
+        Lbar = torch.zeros_like(L)
+        Bbar = abft.potrs_backward(L, X, Xbar.contiguous(), Lbar, ctx.nb)
+        return Lbar, Bbar, None
+
+
+class LogdetFromCholesky(torch.autograd.Function):
+    """log det A = 2 sum log L_ii from the factor L of A."""
+
+    @staticmethod
+    def forward(ctx, L):
+        out = abft.logdet(L.detach())
+        ctx.save_for_backward(L)
+        return out
+
+    @staticmethod
+    def backward(ctx, gbar):
+        (L,) = ctx.saved_tensors
+        Lbar = torch.zeros_like(L)
+        abft.logdet_backward(L, float(gbar), Lbar)
+        return Lbar
+
+
+def cholesky(A, nb=256, mode=abft.FULL):
+    return Cholesky.apply(A, nb, mode)
+
+
+def cholesky_solve(L, B, nb=256):
+    return CholeskySolve.apply(L, B, nb)
+
+
+def logdet_from_cholesky(L):
+    return LogdetFromCholesky.apply(L)
+
+
+def gp_negative_log_likelihood_terms(K, y, nb=256):
+    """loss = y^T K^{-1} y / 2 + logdet(K) / 2 through the ABFT Cholesky."""
+    L = cholesky(K, nb)
+    alpha = cholesky_solve(L, y.reshape(-1, 1), nb)
+    return 0.5 * (y.reshape(-1, 1) * alpha).sum() + 0.5 * logdet_from_cholesky(L)

@@ -862,6 +862,187 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
 
 namespace {
 
+// -------------------------------------------------------------- adjoint
+constexpr int kAdjSplit = 16;
+
+size_t adj_ws_bytes(int64_t nb) {
+    const size_t d = sizeof(double);
+    return align_up(d * nb * nb) * 3 + align_up(d * (size_t)kAdjSplit * nb * nb);
+}
+
+// Blocked reverse sweep of the right-looking Cholesky (lower convention).
+int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, double* Ab,
+                       int64_t ldab, char* ws, cudaStream_t s) {
+    double* P = (double*)ws;
+    double* Y = (double*)(ws + align_up(sizeof(double) * nb * nb));
+    double* Lc = (double*)(ws + 2 * align_up(sizeof(double) * nb * nb));
+    double* part = (double*)(ws + 3 * align_up(sizeof(double) * nb * nb));
+    const int64_t N = (n + nb - 1) / nb;
+    for (int64_t k = N - 1; k >= 0; --k) {
+        const int64_t K0 = k * nb, kb = std::min(nb, n - K0), T0 = K0 + kb, m = n - T0;
+        const double* L11 = L + K0 * ldl + K0;
+        double* A11 = Ab + K0 * ldab + K0;
+        if (m > 0) {
+            // trailing update A22' = A22 - L21 L21^T  =>  Lbar21 -= (Abar22 + Abar22^T) L21
+            timing_mark(PH_TMU, 1, s);
+            GemmSeg g1{};
+            g1.A = Ab + T0 * ldab + T0; g1.lda = ldab;
+            g1.B = L + T0 * ldl + K0; g1.ldb = ldl;
+            g1.C = Ab + T0 * ldab + K0; g1.ldc = ldab;
+            g1.M = m; g1.N = kb; g1.K = m;
+            ABFT_CUDA_TRY(launch_gemm_f64(&g1, 1, 2, 1, nullptr, 0, nullptr, s));
+            timing_mark(PH_TMU, 0, s);
+            // L21 = A21 L11^{-T}  =>  Abar21 = Lbar21 L11^{-1}, Lbar11 -= tril(Abar21^T L21)
+            timing_mark(PH_PU, 1, s);
+            TrsmSeg seg{Ab + T0 * ldab + K0, ldab, m};
+            ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &seg, 1, nullptr, nullptr, nullptr, s,
+                                          false, true));
+            GemmSeg g3{};
+            g3.A = Ab + T0 * ldab + K0; g3.lda = ldab;
+            g3.B = L + T0 * ldl + K0; g3.ldb = ldl;
+            g3.C = A11; g3.ldc = ldab;
+            g3.M = kb; g3.N = kb; g3.K = m;
+            g3.g = 1; g3.row0 = 0; g3.col0 = 0;
+            ABFT_CUDA_TRY(launch_gemm_f64_splitk(g3, 1, 1, kAdjSplit, part, nullptr, s));
+            timing_mark(PH_PU, 0, s);
+        }
+        // L11 = chol(A11)  =>  Abar11 = Phi(S + S^T), S = L11^{-T} Phi(L11^T Lbar11) L11^{-1}
+        timing_mark(PH_PD, 1, s);
+        ABFT_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * kb * kb, s));
+        ABFT_CUDA_TRY(launch_copy_lower(L11, ldl, Lc, kb, kb, s));   // L11 with zeros above
+        GemmSeg g4{};
+        g4.A = Lc; g4.lda = kb;
+        g4.B = A11; g4.ldb = ldab;
+        g4.C = P; g4.ldc = kb;
+        g4.M = kb; g4.N = kb; g4.K = kb;
+        ABFT_CUDA_TRY(launch_gemm_f64(&g4, 1, 1, 1, nullptr, 0, nullptr, s));
+        ABFT_CUDA_TRY(launch_phi_neg(P, kb, kb, s));
+        TrsmSeg sp{P, kb, kb};
+        ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &sp, 1, nullptr, nullptr, nullptr, s, false, true));
+        ABFT_CUDA_TRY(launch_transpose(P, kb, Y, kb, kb, s));
+        TrsmSeg sy{Y, kb, kb};
+        ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &sy, 1, nullptr, nullptr, nullptr, s, false, true));
+        ABFT_CUDA_TRY(launch_assemble_diag(Y, kb, A11, ldab, kb, s));
+        timing_mark(PH_PD, 0, s);
+    }
+    return ABFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, const double* Lbar,
+                        int64_t ldlb, double* Abar, int64_t ldab, int32_t sym, void* ws,
+                        size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
+    const bool run = ws != nullptr && n > 0;
+    if (run && L == nullptr) return -3;
+    if (ldl < std::max<int64_t>(1, n)) return -4;
+    if (run && Lbar == nullptr) return -5;
+    if (ldlb < std::max<int64_t>(1, n)) return -6;
+    if (run && Abar == nullptr) return -7;
+    if (ldab < std::max<int64_t>(1, n)) return -8;
+    if (ws_bytes == nullptr) return -11;
+    const size_t need = adj_ws_bytes(nb);
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -11;
+    if (n == 0) return ABFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    timing_mark(PH_OTHER, 1, s);
+    ABFT_CUDA_TRY(launch_copy_lower(Lbar, ldlb, Abar, ldab, n, s));
+    timing_mark(PH_OTHER, 0, s);
+    int rc = potrf_backward_run(n, nb, L, ldl, Abar, ldab, (char*)ws, s);
+    if (rc != ABFT_OK) return rc;
+    if (sym) ABFT_CUDA_TRY(launch_symmetrize_half(Abar, ldab, n, s));
+    ABFT_CUDA_TRY(timing_collect(s));
+    return ABFT_OK;
+}
+
+int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, int64_t ldl,
+                        const double* X, int64_t ldx, const double* Xbar, int64_t ldxb,
+                        double* Bbar, int64_t ldbb, double* Lbar, int64_t ldlb, void* ws,
+                        size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0 || nrhs > 16) return -2;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
+    const bool run = ws != nullptr && n > 0 && nrhs > 0;
+    if (run && L == nullptr) return -4;
+    if (ldl < std::max<int64_t>(1, n)) return -5;
+    if (run && X == nullptr) return -6;
+    if (ldx < std::max<int64_t>(1, nrhs)) return -7;
+    if (run && Xbar == nullptr) return -8;
+    if (ldxb < std::max<int64_t>(1, nrhs)) return -9;
+    if (run && Bbar == nullptr) return -10;
+    if (ldbb < std::max<int64_t>(1, nrhs)) return -11;
+    if (run && Lbar == nullptr) return -12;
+    if (ldlb < std::max<int64_t>(1, n)) return -13;
+    if (ws_bytes == nullptr) return -15;
+    const size_t need = align_up(sizeof(double) * (size_t)n * 16) * 4;
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -15;
+    if (!run) return ABFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t blk = align_up(sizeof(double) * (size_t)n * 16);
+    double* Xc = (double*)ws;
+    double* Bc = (double*)((char*)ws + blk);
+    double* U = (double*)((char*)ws + 2 * blk);
+    double* V = (double*)((char*)ws + 3 * blk);
+    timing_mark(PH_SOLVE, 1, s);
+    // Bbar = A^{-1} Xbar
+    ABFT_CUDA_TRY(launch_copy_d2d(Xbar, ldxb, Bbar, ldbb, n, (int)nrhs, s));
+    ABFT_CUDA_TRY(launch_potrs_f64(n, (int)nrhs, nb, L, ldl, Bbar, ldbb, s));
+    // Lbar -= tril((Bbar X^T + X Bbar^T) L) = tril(Bbar (L^T X)^T + X (L^T Bbar)^T)
+    ABFT_CUDA_TRY(launch_copy_d2d(X, ldx, Xc, 16, n, (int)nrhs, s));
+    ABFT_CUDA_TRY(launch_copy_d2d(Bbar, ldbb, Bc, 16, n, (int)nrhs, s));
+    ABFT_CUDA_TRY(launch_ltx(L, ldl, n, Xc, 16, (int)nrhs, U, 16, s));
+    ABFT_CUDA_TRY(launch_ltx(L, ldl, n, Bc, 16, (int)nrhs, V, 16, s));
+    ABFT_CUDA_TRY(launch_syr2k_lower(Bc, Xc, U, V, 16, n, (int)nrhs, Lbar, ldlb, s));
+    timing_mark(PH_SOLVE, 0, s);
+    ABFT_CUDA_TRY(timing_collect(s));
+    return ABFT_OK;
+}
+
+int abft_logdet(int64_t n, const double* L, int64_t ldl, double* out, void* stream) {
+    if (n < 0) return -1;
+    if (n > 0 && L == nullptr) return -2;
+    if (ldl < std::max<int64_t>(1, n)) return -3;
+    if (out == nullptr) return -4;
+    cudaStream_t s = (cudaStream_t)stream;
+    ABFT_CUDA_TRY(launch_logdet(L, ldl, n, out, s));
+    return ABFT_OK;
+}
+
+int abft_logdet_backward(int64_t n, const double* L, int64_t ldl, double gbar, double* Lbar,
+                         int64_t ldlb, void* stream) {
+    if (n < 0) return -1;
+    if (n > 0 && L == nullptr) return -2;
+    if (ldl < std::max<int64_t>(1, n)) return -3;
+    if (n > 0 && Lbar == nullptr) return -5;
+    if (ldlb < std::max<int64_t>(1, n)) return -6;
+    ABFT_CUDA_TRY(launch_logdet_backward(L, ldl, n, gbar, Lbar, ldlb, (cudaStream_t)stream));
+    return ABFT_OK;
+}
+
+int abft_tril(int64_t n, double* A, int64_t lda, void* stream) {
+    if (n < 0) return -1;
+    if (n > 0 && A == nullptr) return -2;
+    if (lda < std::max<int64_t>(1, n)) return -3;
+    ABFT_CUDA_TRY(launch_tril_zero(A, lda, n, (cudaStream_t)stream));
+    return ABFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
 }  // namespace
 
 extern "C" {

@@ -140,12 +140,18 @@ struct ComputeFault {
     double delta;
 };
 enum { MAX_CF = 4 };
+// a_kmajor: 0 row-major A, 1 K-major A, 2 symmetric A + A^T read from its lower triangle.
 cudaError_t launch_gemm_f64(const GemmSeg* segs, int nseg, int a_kmajor, int b_kmajor,
                             const ComputeFault* cf, int ncf, const DevStatus* st, cudaStream_t s);
+// One segment, K split over kparts CTAs (partials in `part`, kparts x M x N), then reduced
+// in a fixed order into C (with the lower-block mask).
+cudaError_t launch_gemm_f64_splitk(const GemmSeg& seg, int a_kmajor, int b_kmajor, int kparts,
+                                   double* part, const DevStatus* st, cudaStream_t s);
 
 cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_base,
                                DevStatus* st, cudaStream_t s);
-// X L^T = B for the rows of up to two row segments (in place); L lower nb x nb.
+// X L^T = B (nt = false) or X L = B (nt = true, FP64 only) for the rows of up
+// to two row segments (in place); L lower nb x nb.
 // If v != NULL, x[i] = B_i . v is stored for the rows of segment 0 before the solve.
 struct TrsmSeg {
     double* B;
@@ -154,7 +160,7 @@ struct TrsmSeg {
 };
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s, bool f32 = false);
+                            cudaStream_t s, bool f32 = false, bool nt = false);
 cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
                                  int64_t K0, int step, double* v, int mode, DevStatus* st,
                                  cudaStream_t s);
@@ -248,6 +254,25 @@ cudaError_t launch_add_f64(double* X, int64_t ldx, const double* D, int64_t ldd,
                            int nrhs, cudaStream_t s);
 cudaError_t launch_copy_f2d(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
                             int cols, cudaStream_t s);
+
+// Adjoint kernels (k_adjoint.cu).
+cudaError_t launch_copy_lower(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n,
+                              cudaStream_t s);
+cudaError_t launch_phi_neg(double* P, int64_t ld, int64_t kb, cudaStream_t s);
+cudaError_t launch_transpose(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t kb,
+                             cudaStream_t s);
+cudaError_t launch_assemble_diag(const double* St, int64_t lds, double* A, int64_t lda, int64_t kb,
+                                 cudaStream_t s);
+cudaError_t launch_ltx(const double* L, int64_t ldl, int64_t n, const double* X, int64_t ldx,
+                       int nrhs, double* U, int64_t ldu, cudaStream_t s);
+cudaError_t launch_syr2k_lower(const double* Bb, const double* X, const double* U, const double* V,
+                               int64_t ld16, int64_t n, int nrhs, double* Lbar, int64_t ldlb,
+                               cudaStream_t s);
+cudaError_t launch_logdet(const double* L, int64_t ldl, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_logdet_backward(const double* L, int64_t ldl, int64_t n, double gbar,
+                                   double* Lbar, int64_t ldlb, cudaStream_t s);
+cudaError_t launch_tril_zero(double* A, int64_t lda, int64_t n, cudaStream_t s);
+cudaError_t launch_symmetrize_half(double* A, int64_t lda, int64_t n, cudaStream_t s);
 
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();

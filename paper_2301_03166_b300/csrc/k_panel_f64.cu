@@ -75,10 +75,12 @@ struct TrsmArgs {
     const DevStatus* st;
 };
 
-// Solve X L^T = B for RB rows at a time (in place), L lower nb x nb.
-// Columns are processed in chunks of 32: X[:, c] -= X[:, :c] L[c, :c]^T
-// (all threads), then a per-row forward substitution inside the chunk.
-template <typename T>
+// Solve X L^T = B (NT = false) or X L = B (NT = true) for RB rows at a time
+// (in place), L lower nb x nb.  Columns are processed in chunks of 32, left to
+// right for L^T (X[:, c] -= X[:, :c] L[c, :c]^T) and right to left for L
+// (X[:, c] -= X[:, c1:] L[c1:, c]), the update by all threads, then a per-row
+// substitution inside the chunk.
+template <typename T, bool NT>
 __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     extern __shared__ __align__(16) unsigned char smem_bytes[];
     T* smem = (T*)smem_bytes;
@@ -109,19 +111,27 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
         __syncthreads();
     }
     const int gr = t >> 3, gq = (t & 7) * 4;  // GEMM part: row gr, cols gq..gq+3
-    for (int c0 = 0; c0 < nb; c0 += CW) {
+    const int nch = (nb + CW - 1) / CW;
+    for (int ci = 0; ci < nch; ++ci) {
+        const int c0 = (NT ? nch - 1 - ci : ci) * CW;
         const int w = (nb - c0) < CW ? (nb - c0) : CW;
+        const int c1 = c0 + w;
         T acc[4] = {0, 0, 0, 0};
-        for (int p0 = 0; p0 < c0; p0 += CW) {
+        const int pbeg = NT ? c1 : 0, pend = NT ? nb : c0;
+        for (int p0 = pbeg; p0 < pend; p0 += CW) {
             __syncthreads();
             for (int e = t; e < CW * CW; e += TT) {
                 int q = e / CW, pp = e % CW;
-                Ls[q * (CW + 1) + pp] = (q < w) ? (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp] : (T)0;
+                T v = 0;
+                if (q < w && p0 + pp < pend)
+                    v = NT ? (T)a.L[(int64_t)(p0 + pp) * a.ldl + c0 + q]
+                           : (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp];
+                Ls[q * (CW + 1) + pp] = v;
             }
             __syncthreads();
 #pragma unroll 8
             for (int pp = 0; pp < CW; ++pp) {
-                T xv = X[gr * ldx + p0 + pp];
+                T xv = (p0 + pp < pend) ? X[gr * ldx + p0 + pp] : (T)0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) acc[u] = fma(xv, Ls[(gq + u) * (CW + 1) + pp], acc[u]);
             }
@@ -130,17 +140,32 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (gq + u < w) X[gr * ldx + c0 + gq + u] -= acc[u];
+        // the chunk's diagonal block: Ls[q][p] = L[c0+q][c0+p] (p <= q) for L^T,
+        // L[c0+p][c0+q] (p >= q) for L
         for (int e = t; e < CW * CW; e += TT) {
             int q = e / CW, pp = e % CW;
-            Ls[q * (CW + 1) + pp] = (q < w && pp <= q) ? (T)a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp] : (T)0;
+            T v = 0;
+            if (q < w && pp < w) {
+                if (!NT && pp <= q) v = (T)a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp];
+                if (NT && pp >= q) v = (T)a.L[(int64_t)(c0 + pp) * a.ldl + c0 + q];
+            }
+            Ls[q * (CW + 1) + pp] = v;
         }
         __syncthreads();
         if (t < RB) {
             T* xr = X + t * ldx + c0;
-            for (int jj = 0; jj < w; ++jj) {
-                T v = xr[jj];
-                for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
-                xr[jj] = v / Ls[jj * (CW + 1) + jj];
+            if (!NT) {
+                for (int jj = 0; jj < w; ++jj) {
+                    T v = xr[jj];
+                    for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
+                    xr[jj] = v / Ls[jj * (CW + 1) + jj];
+                }
+            } else {
+                for (int jj = w - 1; jj >= 0; --jj) {
+                    T v = xr[jj];
+                    for (int p = jj + 1; p < w; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
+                    xr[jj] = v / Ls[jj * (CW + 1) + jj];
+                }
             }
         }
         __syncthreads();
@@ -221,7 +246,7 @@ cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_
 
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s, bool f32) {
+                            cudaStream_t s, bool f32, bool nt) {
     TrsmArgs a{};
     a.L = L;
     a.ldl = ldl;
@@ -245,18 +270,22 @@ cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const Trsm
     a.st = st;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((RB * 513 + CW * (CW + 1)) * sizeof(double)));
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_trsm_rlt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((RB * 513 + CW * (CW + 1)) * sizeof(float)));
+        const int bd = (int)((RB * 513 + CW * (CW + 1)) * sizeof(double));
+        const int bf = (int)((RB * 513 + CW * (CW + 1)) * sizeof(float));
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt<double, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bd);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm_rlt<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm_rlt<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (f32)
-        k_trsm_rlt<float><<<(unsigned)total, TT, (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(float), s>>>(a);
-    else
-        k_trsm_rlt<double><<<(unsigned)total, TT, (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(double), s>>>(a);
+    const size_t sd = (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(double);
+    const size_t sf = (size_t)(RB * (nb + 1) + CW * (CW + 1)) * sizeof(float);
+    if (nt) k_trsm_rlt<double, true><<<(unsigned)total, TT, sd, s>>>(a);
+    else if (f32) k_trsm_rlt<float, false><<<(unsigned)total, TT, sf, s>>>(a);
+    else k_trsm_rlt<double, false><<<(unsigned)total, TT, sd, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }
