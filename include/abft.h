@@ -264,6 +264,61 @@ int abft_logdet_backward(int64_t n, const double* L, int64_t ldl, double gbar, d
 int abft_tril(int64_t n, double* A, int64_t lda, void* stream);
 
 /*
+ * Batched ABFT Cholesky -- many independent small SPD matrices in one
+ * persistent launch (not in the paper: the batching form added on top of it).
+ * Each matrix is factored by one CTA with the same blocked algorithm and full
+ * (or no) checksums as abft_potrf, block size nb = 32 or 64 per matrix.
+ * Descriptors and statuses live in DEVICE memory; a CTA takes the next
+ * descriptor from an atomic queue, so order the descriptors by decreasing n
+ * (longest first).  At most one fault per matrix (kinds MEMORY, COMPUTE,
+ * PANEL; fstep = -1 for none) with the same placement rules as abft_potrf.
+ */
+typedef struct {
+    void* A;          /* device, row-major, FP64 (dtype ABFT_F64) or FP32 (ABFT_F32) */
+    int64_t lda;
+    int32_t n;        /* 1 .. 512 */
+    int32_t id;       /* index of this matrix's status entry */
+    int32_t nb;       /* 32 or 64 */
+    int32_t fstep;    /* injected fault: step (-1 = none), kind, row, col, delta */
+    int32_t fkind;
+    int32_t frow;
+    int32_t fcol;
+    int32_t pad;
+    double fdelta;
+} abft_batch_item;
+
+typedef struct {
+    int32_t info;          /* 1-based first non-positive pivot, 0 = factored */
+    int32_t detected;
+    int32_t corrected;
+    int32_t uncorrectable;
+    int32_t ev_step;       /* first event of this matrix (-1 = none) */
+    int32_t ev_kind;
+    int32_t ev_row;
+    int32_t ev_col;
+} abft_batch_status;
+
+/*
+ * abft_potrf_batched: factor `count` matrices described by the device array
+ * `items`; per-matrix results go to the device array `status` (indexed by
+ * item.id).  dtype: ABFT_F64 or ABFT_F32 (arithmetic and storage); mode:
+ * ABFT_MODE_NONE or ABFT_MODE_FULL; tau = tau_scale * 8 u n nb max_i a_ii
+ * with u the unit roundoff of dtype.  use_graph != 0: the launch sequence
+ * (queue reset + persistent kernel) is captured once into a CUDA graph per
+ * (items, count, dtype, mode, status, workspace, stream) and replayed.
+ * Workspace protocol as abft_potrf.  The arguments of the descriptors are
+ * not validated on the host (they are device memory); invalid n is skipped.
+ * Errors: -1 count; -2 items; -3 dtype; -4 mode; -6 status; -9 ws.
+ */
+int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtype, int32_t mode,
+                       double tau_scale, abft_batch_status* status, int32_t use_graph, void* ws,
+                       size_t* ws_bytes, void* stream);
+
+/* Destroy the CUDA graphs cached by abft_potrf_batched (call before freeing
+ * the memory their keys refer to, if the same addresses may be reused). */
+int abft_batched_graph_reset(void);
+
+/*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
  * own allocator or arena owns the whole GPU (or that may not grow the

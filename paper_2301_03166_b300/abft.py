@@ -46,6 +46,7 @@ _i64, _i32, _dbl, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.
 _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
+    "abft_potrf_batched": [_i32, _vp, _i32, _i32, _dbl, _vp, _i32, _vp, _sz, _vp],
     "abft_potrf_backward": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz, _vp],
     "abft_potrs_backward": [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
                             _i64, _vp, _sz, _vp],
@@ -385,3 +386,67 @@ def tril_(A, stream=None):
     if rc < 0:
         raise AbftError(rc, strerror(rc))
     return A
+
+
+# ------------------------------------------------------------------ batched
+import numpy as _np
+
+_ITEM = _np.dtype([("A", "<u8"), ("lda", "<i8"), ("n", "<i4"), ("id", "<i4"), ("nb", "<i4"),
+                   ("fstep", "<i4"), ("fkind", "<i4"), ("frow", "<i4"), ("fcol", "<i4"),
+                   ("pad", "<i4"), ("fdelta", "<f8")])
+_STATUS_FIELDS = ("info", "detected", "corrected", "uncorrectable", "ev_step", "ev_kind",
+                  "ev_row", "ev_col")
+
+
+class Batch:
+    """Device-resident descriptors of a batch of square matrices stored back
+    to back in one CUDA buffer; descriptors are ordered by decreasing n."""
+
+    def __init__(self, buf, sizes, offsets, nb, faults=None):
+        self.buf, self.sizes, self.offsets = buf, list(sizes), list(offsets)
+        esz = buf.element_size()
+        order = sorted(range(len(sizes)), key=lambda i: -sizes[i])
+        items = _np.zeros(len(sizes), dtype=_ITEM)
+        faults = faults or {}
+        for slot, i in enumerate(order):
+            n = int(sizes[i])
+            it = items[slot]
+            it["A"] = buf.data_ptr() + int(offsets[i]) * esz
+            it["lda"], it["n"], it["id"] = n, n, i
+            it["nb"] = nb(n) if callable(nb) else int(nb)
+            f = faults.get(i)
+            if f is None:
+                it["fstep"] = -1
+            else:
+                it["fstep"], it["fkind"], it["frow"], it["fcol"], it["fdelta"] = f
+        self.items = torch.from_numpy(items.view(_np.uint8)).to(buf.device)
+        self.status = torch.zeros((len(sizes), len(_STATUS_FIELDS)), dtype=torch.int32,
+                                  device=buf.device)
+
+    def matrix(self, i):
+        n, o = self.sizes[i], self.offsets[i]
+        return self.buf[o:o + n * n].view(n, n)
+
+    def statuses(self):
+        st = self.status.cpu().numpy()
+        return [dict(zip(_STATUS_FIELDS, map(int, row))) for row in st]
+
+
+def potrf_batched(batch, mode=FULL, tau_scale=1.0, use_graph=False, workspace=None, stream=None):
+    """Factor every matrix of `batch` in one persistent launch (FP64 or FP32
+    according to the buffer dtype)."""
+    dtype = F64 if batch.buf.dtype == torch.float64 else F32
+    L = lib()
+    need = ctypes.c_size_t(0)
+    count = len(batch.sizes)
+    rc = L.abft_potrf_batched(count, None, dtype, mode, tau_scale, None, 0, None,
+                              ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, batch.buf.device)
+    size = ctypes.c_size_t(ws.numel())
+    rc = L.abft_potrf_batched(count, _ptr(batch.items), dtype, mode, tau_scale, _ptr(batch.status),
+                              1 if use_graph else 0, _ptr(ws), ctypes.byref(size), _stream(stream))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return batch

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -1036,6 +1038,90 @@ int abft_tril(int64_t n, double* A, int64_t lda, void* stream) {
     if (n > 0 && A == nullptr) return -2;
     if (lda < std::max<int64_t>(1, n)) return -3;
     ABFT_CUDA_TRY(launch_tril_zero(A, lda, n, (cudaStream_t)stream));
+    return ABFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// -------------------------------------------------------------- batched
+struct GraphKey {
+    const void* items;
+    int count, dtype, mode;
+    const void* status;
+    const void* ws;
+    void* stream;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(items, count, dtype, mode, status, ws, stream) <
+               std::tie(o.items, o.count, o.dtype, o.mode, o.status, o.ws, o.stream);
+    }
+};
+std::mutex g_graph_mu;
+std::map<GraphKey, cudaGraphExec_t> g_graphs;
+
+}  // namespace
+
+extern "C" {
+
+int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtype, int32_t mode,
+                       double tau_scale, abft_batch_status* status, int32_t use_graph, void* ws,
+                       size_t* ws_bytes, void* stream) {
+    if (count < 0) return -1;
+    if (count > 0 && items == nullptr && ws != nullptr) return -2;
+    if (dtype != ABFT_F64 && dtype != ABFT_F32) return dtype < 0 || dtype > 3 ? -3 : ABFT_ERR_UNSUPPORTED;
+    if (mode != ABFT_MODE_NONE && mode != ABFT_MODE_FULL) return mode == ABFT_MODE_SINGLE ? ABFT_ERR_UNSUPPORTED : -4;
+    if (count > 0 && status == nullptr && ws != nullptr) return -6;
+    if (ws_bytes == nullptr) return -9;
+    const bool f64 = dtype == ABFT_F64;
+    const size_t need = align_up(batched_scratch_bytes(batched_grid(), f64)) + 256;
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -9;
+    if (count == 0) return ABFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int* queue = (unsigned int*)((char*)ws + align_up(batched_scratch_bytes(batched_grid(), f64)));
+    if (!use_graph) {
+        ABFT_CUDA_TRY(launch_potrf_batched(items, count, f64, mode, tau_scale, status, ws, queue, s));
+        ABFT_CUDA_TRY(timing_collect(s));
+        return ABFT_OK;
+    }
+    GraphKey key{items, count, dtype, mode, status, ws, stream};
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto itg = g_graphs.find(key);
+        if (itg != g_graphs.end()) exec = itg->second;
+    }
+    if (exec == nullptr) {
+        ABFT_CUDA_TRY(batched_prepare());   // kernel attributes outside the capture
+        (void)batched_grid();
+        cudaStream_t cs;
+        ABFT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        ABFT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = launch_potrf_batched(items, count, f64, mode, tau_scale, status, ws, queue, cs);
+        cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (le != cudaSuccess || ee != cudaSuccess) return ABFT_ERR_CUDA;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return ABFT_ERR_CUDA;
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        g_graphs[key] = exec;
+    }
+    ABFT_CUDA_TRY(cudaGraphLaunch(exec, s));
+    note_launch();
+    ABFT_CUDA_TRY(timing_collect(s));
+    return ABFT_OK;
+}
+
+int abft_batched_graph_reset(void) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second);
+    g_graphs.clear();
     return ABFT_OK;
 }
 

@@ -274,6 +274,14 @@ cudaError_t launch_logdet_backward(const double* L, int64_t ldl, int64_t n, doub
 cudaError_t launch_tril_zero(double* A, int64_t lda, int64_t n, cudaStream_t s);
 cudaError_t launch_symmetrize_half(double* A, int64_t lda, int64_t n, cudaStream_t s);
 
+// Batched kernel (k_batched.cu).
+size_t batched_scratch_bytes(int grid, bool f64);
+int batched_grid();
+cudaError_t batched_prepare();
+cudaError_t launch_potrf_batched(const abft_batch_item* items, int count, bool f64, int mode,
+                                 double tau_scale, abft_batch_status* status, void* scratch,
+                                 unsigned int* queue, cudaStream_t s);
+
 // Kernel launch accounting (every launcher calls note_launch once per kernel).
 void note_launch();
 

@@ -1,0 +1,445 @@
+// k_batched.cu -- batched ABFT Cholesky of many small SPD matrices in one
+// persistent launch (Sec. 2.1 blocked algorithm and Sec. 3.1.2 checksums at
+// the scope of one CTA per matrix).
+//
+// Each CTA repeatedly takes the next matrix from an atomic queue (the host
+// orders the descriptors by decreasing n, so the longest factorizations
+// start first) and factors it with block size B (32 or 64, per descriptor):
+//   PD   the B x B diagonal block in shared memory (right-looking potf2) and
+//        its column-sum check;
+//   PU   one thread per panel row (and per checksum row) solves x L^T = a with
+//        L_kk in shared memory; panel tiles are verified with the weighted
+//        column checksums;
+//   TMU  B x B output tiles of the lower block triangle (diagonal tiles in
+//        full), L_I and L_J staged in shared memory, C read-modify-written in
+//        global memory (L2-resident for these sizes), checksum borders
+//        updated from the carried panel checksums;
+//   then the optional injected fault and the verify / locate / correct of
+//   every trailing tile (full checksums: 0D, 1D, checksum-only, 2D classes).
+// T is the arithmetic type (double or float); the threshold uses its unit
+// roundoff.  There are no spin waits: the only cross-CTA interaction is the
+// atomic queue counter.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace {
+
+constexpr int BT = 256;   // threads per CTA
+constexpr int MAXN = 512;
+constexpr int MAXB = 64;
+constexpr int MAXNT = MAXN / 32;
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < (T)0 ? -x : x; }
+
+// Per-CTA global scratch: checksums and the saved diagonal-block upper triangles.
+template <typename T>
+struct Scratch {
+    T* Cc;    // MAXNT x MAXN column sums (row I: block row I)
+    T* Cw;    // MAXNT x MAXN weighted column sums
+    T* Cr;    // MAXN x MAXNT row sums
+    T* save;  // MAXN x MAXB saved strict upper triangles of the diagonal blocks
+};
+
+template <typename T>
+__device__ void record(abft_batch_status* st, int step, int kind, int row, int col, int* s_first) {
+    if (atomicCAS(s_first, 0, 1) == 0) {
+        st->ev_step = step;
+        st->ev_kind = kind;
+        st->ev_row = row;
+        st->ev_col = col;
+    }
+}
+
+// Sums of one tile (nr x nc at P, ld) into sh: colsum[0..nc), wsum[0..nc), rowsum[0..nr).
+template <typename T>
+__device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* wsum, T* rowsum) {
+    const int t = threadIdx.x;
+    for (int j = t; j < nc; j += BT) {
+        T s = 0, sw = 0;
+        for (int i = 0; i < nr; ++i) {
+            T v = P[(int64_t)i * ld + j];
+            s += v;
+            sw += (T)(i + 1) * v;
+        }
+        colsum[j] = s;
+        wsum[j] = sw;
+    }
+    for (int i = t; i < nr; i += BT) {
+        T s = 0;
+        for (int j = 0; j < nc; ++j) s += P[(int64_t)i * ld + j];
+        rowsum[i] = s;
+    }
+    __syncthreads();
+}
+
+// Verify one tile against its carried checksums and correct it (same rules as
+// the large-matrix kernel).  single = 1: weighted column checksums only.
+template <typename T>
+__device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T* cc, T* cw, T* cr,
+                            int crs, T tau, int single, int step, abft_batch_status* st,
+                            T* colsum, T* wsum, T* rowsum, int* sflag, int* s_first) {
+    tile_sums<T>(P, ld, nr, nc, colsum, wsum, rowsum);
+    const int t = threadIdx.x;
+    if (t == 0) { sflag[0] = 0; sflag[1] = 0; sflag[2] = 1 << 30; sflag[3] = 1 << 30; }
+    __syncthreads();
+    for (int j = t; j < nc; j += BT) {
+        colsum[j] -= cc[j];
+        wsum[j] -= cw[j];
+        if (!(tabs(colsum[j]) <= tau)) { atomicAdd(&sflag[0], 1); atomicMin(&sflag[2], j); }
+    }
+    if (!single)
+        for (int i = t; i < nr; i += BT) {
+            rowsum[i] -= cr[i * crs];
+            if (!(tabs(rowsum[i]) <= tau)) { atomicAdd(&sflag[1], 1); atomicMin(&sflag[3], i); }
+        }
+    __syncthreads();
+    const int nfc = sflag[0], nfr = sflag[1], fc = sflag[2], fr = sflag[3];
+    if (nfc == 0 && nfr == 0) return;
+    if (t == 0) atomicAdd(&st->detected, 1);
+    if (single) {
+        for (int j = t; j < nc; j += BT) {
+            T dc = colsum[j];
+            if (tabs(dc) <= tau) continue;
+            T rho = wsum[j] / dc;
+            T ri = rint(rho);
+            int i = (int)ri - 1;
+            if (tabs(rho - ri) <= (T)0.05 && i >= 0 && i < nr) {
+                P[(int64_t)i * ld + j] -= dc;
+                atomicAdd(&st->corrected, 1);
+                record<T>(st, step, EV_0D, r0 + i, c0 + j, s_first);
+            } else {
+                atomicAdd(&st->uncorrectable, 1);
+                record<T>(st, step, EV_UNCORR, r0, c0 + j, s_first);
+            }
+        }
+    } else if (nfr == 1 && nfc == 1) {
+        if (t == 0) {
+            T dc = colsum[fc], dr = rowsum[fr];
+            if (tabs(dc - dr) <= tau) {
+                P[(int64_t)fr * ld + fc] -= dc;
+                atomicAdd(&st->corrected, 1);
+                record<T>(st, step, EV_0D, r0 + fr, c0 + fc, s_first);
+            } else {
+                atomicAdd(&st->uncorrectable, 1);
+                record<T>(st, step, EV_UNCORR, r0, c0, s_first);
+            }
+        }
+    } else if (nfr == 1 && nfc >= 2) {
+        for (int j = t; j < nc; j += BT)
+            if (!(tabs(colsum[j]) <= tau)) {
+                P[(int64_t)fr * ld + j] -= colsum[j];
+                atomicAdd(&st->corrected, 1);
+                record<T>(st, step, EV_ROW, r0 + fr, c0 + j, s_first);
+            }
+    } else if (nfr >= 2 && nfc == 1) {
+        for (int i = t; i < nr; i += BT)
+            if (!(tabs(rowsum[i]) <= tau)) {
+                P[(int64_t)i * ld + fc] -= rowsum[i];
+                atomicAdd(&st->corrected, 1);
+                record<T>(st, step, EV_COL, r0 + i, c0 + fc, s_first);
+            }
+    } else if (nfr == 0 || nfc == 0) {
+        for (int j = t; j < nc; j += BT) cc[j] += colsum[j];
+        for (int i = t; i < nr; i += BT) cr[i * crs] += rowsum[i];
+        if (t == 0) record<T>(st, step, EV_CKSUM, r0, c0, s_first);
+    } else if (t == 0) {
+        atomicAdd(&st->uncorrectable, 1);
+        record<T>(st, step, EV_UNCORR, r0, c0, s_first);
+    }
+    __syncthreads();
+}
+
+template <typename T, int B>
+__device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scratch<T> S,
+                           abft_batch_status* st, T (*sL)[MAXB + 1], T (*sI)[MAXB + 1],
+                           T (*sJ)[MAXB + 1], T* colsum, T* wsum, T* rowsum, int* sflag,
+                           int* s_first, int* s_fail) {
+    T* A = (T*)it.A;
+    const int64_t lda = it.lda;
+    const int n = it.n;
+    const int nt = (n + B - 1) / B;
+    const int t = threadIdx.x;
+    const bool check = mode != MODE_NONE;
+    const T u = sizeof(T) == 8 ? (T)0x1p-53 : (T)0x1p-24;
+    // an injected fault is used only when it lies inside this matrix
+    const bool fok = it.fstep >= 0 && it.frow >= 0 && it.frow < n && it.fcol >= 0 && it.fcol < n;
+    // threshold tau = tau_scale * 8 u n B max_i a_ii
+    if (t == 0) { *s_first = 0; *s_fail = -1; }
+    T m = 0;
+    for (int i = t; i < n; i += BT) m = fmax(m, A[(int64_t)i * lda + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0) colsum[t >> 5] = m;
+    __syncthreads();
+    T dmax = 0;
+    for (int w = 0; w < BT / 32; ++w) dmax = fmax(dmax, colsum[w]);
+    const T tau = tau_scale * (T)8 * u * (T)n * (T)B * dmax;
+    __syncthreads();
+    // mirror the diagonal blocks (save their strict upper triangles)
+    for (int K = 0; K < nt; ++K) {
+        const int K0 = K * B, kb = min(B, n - K0);
+        for (int e = t; e < kb * kb; e += BT) {
+            int i = e / kb, j = e % kb;
+            if (j > i) {
+                S.save[(K0 + i) * MAXB + j] = A[(int64_t)(K0 + i) * lda + K0 + j];
+                A[(int64_t)(K0 + i) * lda + K0 + j] = A[(int64_t)(K0 + j) * lda + K0 + i];
+            }
+        }
+    }
+    __syncthreads();
+    if (check)
+        for (int I = 0; I < nt; ++I)
+            for (int J = 0; J <= I; ++J) {
+                const int r0 = I * B, c0 = J * B, nr = min(B, n - r0), nc = min(B, n - c0);
+                tile_sums<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, colsum, wsum, rowsum);
+                for (int j = t; j < nc; j += BT) {
+                    S.Cc[I * MAXN + c0 + j] = colsum[j];
+                    S.Cw[I * MAXN + c0 + j] = wsum[j];
+                }
+                for (int i = t; i < nr; i += BT) S.Cr[(r0 + i) * MAXNT + J] = rowsum[i];
+                __syncthreads();
+            }
+    for (int k = 0; k < nt; ++k) {
+        const int K0 = k * B, kb = min(B, n - K0), T0 = K0 + kb, mrows = n - T0;
+        // ---- PD: potf2 of the diagonal block in shared memory
+        for (int e = t; e < kb * kb; e += BT) {
+            int i = e / kb, j = e % kb;
+            if (j <= i) sL[i][j] = A[(int64_t)(K0 + i) * lda + K0 + j];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            if (t == 0) {
+                T d = sL[j][j];
+                if (!(d > (T)0)) *s_fail = j;
+                else sL[j][j] = sqrt(d);
+            }
+            __syncthreads();
+            if (*s_fail >= 0) break;
+            const T djj = sL[j][j];
+            for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] / djj;
+            __syncthreads();
+            const int w = kb - j - 1;
+            for (int e = t; e < w * w; e += BT) {
+                int i = j + 1 + e / w, l = j + 1 + e % w;
+                if (l <= i) sL[i][l] -= sL[i][j] * sL[l][j];
+            }
+            __syncthreads();
+        }
+        if (*s_fail >= 0) {
+            if (t == 0) st->info = K0 + *s_fail + 1;
+            break;
+        }
+        for (int e = t; e < kb * kb; e += BT) {
+            int i = e / kb, j = e % kb;
+            if (j <= i) A[(int64_t)(K0 + i) * lda + K0 + j] = sL[i][j];
+        }
+        if (check) {   // PD check on column sums
+            for (int p = t; p < kb; p += BT) {
+                T s = 0;
+                for (int q = p; q < kb; ++q) s += sL[q][p];
+                colsum[p] = s;
+            }
+            __syncthreads();
+            for (int j = t; j < kb; j += BT) {
+                T y = 0;
+                for (int p = 0; p <= j; ++p) y += colsum[p] * sL[j][p];
+                if (!(tabs(y - S.Cc[k * MAXN + K0 + j]) <= tau)) {
+                    atomicAdd(&st->detected, 1);
+                    atomicAdd(&st->uncorrectable, 1);
+                    record<T>(st, k, EV_PD, K0 + j, K0 + j, s_first);
+                }
+            }
+        }
+        __syncthreads();
+        if (mrows <= 0) break;
+        // ---- PU: x L^T = a for the panel rows and the checksum rows (one thread per row)
+        const int ncs = check ? 2 * (nt - k - 1) : 0;
+        for (int rr = t; rr < mrows + ncs; rr += BT) {
+            T* row;
+            if (rr < mrows) row = A + (int64_t)(T0 + rr) * lda + K0;
+            else {
+                int c = rr - mrows, I = k + 1 + c / 2;
+                row = ((c & 1) ? S.Cw : S.Cc) + I * MAXN + K0;
+            }
+            for (int j = 0; j < kb; ++j) {
+                T v = row[j];
+                for (int p = 0; p < j; ++p) v -= row[p] * sL[j][p];
+                row[j] = v / sL[j][j];
+            }
+        }
+        __syncthreads();
+        if (fok && it.fstep == k && it.fkind == ABFT_FAULT_PANEL && t == 0)
+            A[(int64_t)it.frow * lda + it.fcol] += (T)it.fdelta;
+        __syncthreads();
+        if (check)
+            for (int I = k + 1; I < nt; ++I) {
+                const int r0 = I * B, nr = min(B, n - r0);
+                verify_tile<T>(A + (int64_t)r0 * lda + K0, lda, r0, K0, nr, kb,
+                               S.Cc + I * MAXN + K0, S.Cw + I * MAXN + K0, nullptr, 0, tau, 1, k,
+                               st, colsum, wsum, rowsum, sflag, s_first);
+            }
+        // ---- TMU over the lower block triangle with the checksum borders
+        for (int I = k + 1; I < nt; ++I) {
+            const int r0 = I * B, nr = min(B, n - r0);
+            for (int e = t; e < B * kb; e += BT) {
+                int i = e / kb, p = e % kb;
+                sI[i][p] = (i < nr) ? A[(int64_t)(r0 + i) * lda + K0 + p] : (T)0;
+            }
+            for (int J = k + 1; J <= I; ++J) {
+                const int c0 = J * B, nc = min(B, n - c0);
+                for (int e = t; e < B * kb; e += BT) {
+                    int j = e / kb, p = e % kb;
+                    sJ[j][p] = (j < nc) ? A[(int64_t)(c0 + j) * lda + K0 + p] : (T)0;
+                }
+                __syncthreads();
+                const int tx = t & 15, ty = t >> 4;
+                for (int a = 0; a < B / 16; ++a)
+                    for (int b = 0; b < B / 16; ++b) {
+                        const int i = ty + 16 * a, j = tx + 16 * b;
+                        if (i >= nr || j >= nc) continue;
+                        T acc = 0;
+                        for (int p = 0; p < kb; ++p) acc += sI[i][p] * sJ[j][p];
+                        T* c = A + (int64_t)(r0 + i) * lda + c0 + j;
+                        T v = *c - acc;
+                        if (fok && it.fstep == k && it.fkind == ABFT_FAULT_COMPUTE && it.frow == r0 + i &&
+                            it.fcol == c0 + j)
+                            v += (T)it.fdelta;
+                        *c = v;
+                    }
+                if (check) {
+                    for (int j = t; j < nc; j += BT) {   // c_IJ -= s_I L_J^T, w_IJ likewise
+                        T a1 = 0, a2 = 0;
+                        for (int p = 0; p < kb; ++p) {
+                            a1 += S.Cc[I * MAXN + K0 + p] * sJ[j][p];
+                            a2 += S.Cw[I * MAXN + K0 + p] * sJ[j][p];
+                        }
+                        S.Cc[I * MAXN + c0 + j] -= a1;
+                        S.Cw[I * MAXN + c0 + j] -= a2;
+                    }
+                    for (int i = t; i < nr; i += BT) {   // r_IJ -= L_I s_J^T
+                        T a1 = 0;
+                        for (int p = 0; p < kb; ++p) a1 += sI[i][p] * S.Cc[J * MAXN + K0 + p];
+                        S.Cr[(r0 + i) * MAXNT + J] -= a1;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (fok && it.fstep == k && it.fkind == ABFT_FAULT_MEMORY && t == 0)
+            A[(int64_t)it.frow * lda + it.fcol] += (T)it.fdelta;
+        __syncthreads();
+        if (check)
+            for (int I = k + 1; I < nt; ++I)
+                for (int J = k + 1; J <= I; ++J) {
+                    const int r0 = I * B, c0 = J * B, nr = min(B, n - r0), nc = min(B, n - c0);
+                    verify_tile<T>(A + (int64_t)r0 * lda + c0, lda, r0, c0, nr, nc,
+                                   S.Cc + I * MAXN + c0, S.Cw + I * MAXN + c0,
+                                   S.Cr + r0 * MAXNT + J, MAXNT, tau, 0, k, st, colsum, wsum,
+                                   rowsum, sflag, s_first);
+                }
+    }
+    __syncthreads();
+    for (int K = 0; K < nt; ++K) {   // restore the diagonal blocks' upper triangles
+        const int K0 = K * B, kb = min(B, n - K0);
+        for (int e = t; e < kb * kb; e += BT) {
+            int i = e / kb, j = e % kb;
+            if (j > i) A[(int64_t)(K0 + i) * lda + K0 + j] = S.save[(K0 + i) * MAXB + j];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) k_potrf_batched(const abft_batch_item* items, int count,
+                                                      int mode, double tau_scale,
+                                                      abft_batch_status* status, T* scratch,
+                                                      unsigned int* queue) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    T (*sL)[MAXB + 1] = (T (*)[MAXB + 1])smb;
+    T (*sI)[MAXB + 1] = sL + MAXB;
+    T (*sJ)[MAXB + 1] = sI + MAXB;
+    T* colsum = (T*)(sJ + MAXB);
+    T* wsum = colsum + MAXB;
+    T* rowsum = wsum + MAXB;
+    __shared__ int sflag[4], s_first, s_fail, s_item;
+    const size_t per = (size_t)(3 * MAXNT * MAXN + MAXN * MAXB);
+    Scratch<T> S;
+    T* base = scratch + per * blockIdx.x;
+    S.Cc = base;
+    S.Cw = base + MAXNT * MAXN;
+    S.Cr = base + 2 * MAXNT * MAXN;
+    S.save = base + 3 * MAXNT * MAXN;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int idx = s_item;
+        __syncthreads();
+        if (idx >= count) break;
+        const abft_batch_item it = items[idx];
+        abft_batch_status* st = status + it.id;
+        if (threadIdx.x == 0) {
+            st->info = 0; st->detected = 0; st->corrected = 0; st->uncorrectable = 0;
+            st->ev_step = -1; st->ev_kind = -1; st->ev_row = -1; st->ev_col = -1;
+        }
+        __syncthreads();
+        if (it.n <= 0 || it.n > MAXN) continue;
+        if (it.nb == 64)
+            factor_one<T, 64>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
+                              sflag, &s_first, &s_fail);
+        else
+            factor_one<T, 32>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
+                              sflag, &s_first, &s_fail);
+    }
+}
+
+}  // namespace
+
+size_t batched_smem(bool f64) {
+    return (size_t)(3 * MAXB * (MAXB + 1) + 3 * MAXB) * (f64 ? sizeof(double) : sizeof(float));
+}
+
+size_t batched_scratch_bytes(int grid, bool f64) {
+    const size_t per = (size_t)(3 * MAXNT * MAXN + MAXN * MAXB);
+    return per * (size_t)grid * (f64 ? sizeof(double) : sizeof(float));
+}
+
+int batched_grid() {
+    return 2 * num_sms();
+}
+
+// Kernel attributes (set once, outside any stream capture).
+cudaError_t batched_prepare() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_batched<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem(true));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_potrf_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)batched_smem(false));
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
+cudaError_t launch_potrf_batched(const abft_batch_item* items, int count, bool f64, int mode,
+                                 double tau_scale, abft_batch_status* status, void* scratch,
+                                 unsigned int* queue, cudaStream_t s) {
+    cudaError_t e = batched_prepare();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    const int grid = batched_grid();
+    if (f64)
+        k_potrf_batched<double><<<grid, BT, batched_smem(true), s>>>(items, count, mode, tau_scale,
+                                                                    status, (double*)scratch, queue);
+    else
+        k_potrf_batched<float><<<grid, BT, batched_smem(false), s>>>(items, count, mode, tau_scale,
+                                                                    status, (float*)scratch, queue);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft
