@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
     p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched timings")
     return p.parse_args()
 
 
@@ -353,6 +354,59 @@ def run_ours(args, ws, rank, local):
                            == sorted((f[0], f[2], f[3]) for f in fl)}
         del U0
 
+    batched = None
+    if not args.no_batched:
+        # 4096 SPD matrices, n uniform in [32, 512], one fault per 64 matrices,
+        # one persistent launch replayed from a CUDA graph; FP64 and FP32.
+        from paper_2301_03166_b300 import tune
+        sizes = W.batched_sizes(4096, 32, 512, seed=1005)
+        offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)[:-1]])
+        tot = int((sizes.astype(np.int64) ** 2).sum())
+        g = torch.Generator(device=dev)
+        g.manual_seed(100000)
+        base = torch.empty(tot, dtype=torch.float64, device=dev)
+        for i, nn in enumerate(sizes):
+            nn = int(nn)
+            M = torch.randn(nn, nn, generator=g, dtype=torch.float64, device=dev)
+            Ai = M @ M.T / nn
+            Ai.diagonal().add_(1.0)
+            base[offs[i]:offs[i] + nn * nn] = Ai.reshape(-1)
+        r = W.rng(6000)
+        bflops = float(sum(int(nn) ** 3 / 3.0 for nn in sizes))
+        batched = {"count": 4096, "flops_per_batch": bflops}
+        for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+            table = tune.tune(tdt, dev, per_bucket=64)
+            nbf = tune.chooser(table)
+            faults = {}
+            for q in range(0, 4096, 64):
+                i = q + int(r.integers(0, 64))
+                nn, b = int(sizes[i]), nbf(int(sizes[i]))
+                if nn > b:
+                    row, col = int(r.integers(b, nn)), int(r.integers(b, nn))
+                    if col // b > row // b:
+                        row, col = col, row
+                    faults[i] = (0, abft.F_MEMORY, row, col, 1e3)
+            buf0 = base.to(tdt)
+            buf = buf0.clone()
+            bt = abft.Batch(buf, sizes, offs, nbf, faults)
+            bws = abft.Workspace()
+            def bstep():
+                buf.copy_(buf0)
+                abft.potrf_batched(bt, use_graph=True, workspace=bws)
+            ms_b, _ = timed(bstep, max(1, args.steps), 2)
+            ms_copy, _ = timed(lambda: buf.copy_(buf0), max(1, args.steps), 1)
+            st = bt.statuses()
+            ok = all(s_["info"] == 0 for s_ in st) and all(
+                st[i]["corrected"] == 1 and (st[i]["ev_row"], st[i]["ev_col"]) == f[2:4]
+                for i, f in faults.items())
+            ms_f = ms_b - ms_copy
+            batched[name] = {"ms_per_batch": ms_f, "matrices_per_s": 4096 / (ms_f * 1e-3),
+                             "tflops": bflops / (ms_f * 1e-3) / 1e12, "nb_by_bucket": table,
+                             "faults": len(faults), "all_located_and_corrected": ok}
+            del buf0, buf, bt
+        abft.lib().abft_batched_graph_reset()
+        del base
+
     e2e = None
     if not args.no_e2e:
         A0h = A0.cpu().pin_memory()
@@ -397,7 +451,7 @@ def run_ours(args, ws, rank, local):
             "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
-            "mixed_precision_ir": mixed, "lu_qr": lu_qr,
+            "mixed_precision_ir": mixed, "lu_qr": lu_qr, "batched": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
