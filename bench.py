@@ -145,9 +145,12 @@ def kernel_source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-# ncu-measured DRAM traffic of the FP64 TMU kernel (per step, summed over the
-# step's launches), valid only for the kernel source it was measured on.
-TMU_TRAFFIC = {}   # {source_hash: bytes_per_factorization}
+# ncu-measured DRAM traffic of the FP64 TMU kernel in bytes per updated C
+# element (dram__bytes_read.sum + dram__bytes_write.sum of the step-0 TMU at
+# n = 4096 divided by its 7.86 M updated elements), valid only for the kernel
+# source it was measured on; scaled to the benchmark's launches by the number
+# of updated elements.
+TMU_TRAFFIC = {"4155d564486da839": 83.312640e6 / 7864320}
 
 
 def cpu_baseline(steps=1, warm=0):
@@ -267,13 +270,19 @@ def run_ours(args, ws, rank, local):
     # roofline of the dominant kernel (the FP64 trailing update)
     tmu_ms, tmu_launches = phases["tmu"]
     tmu_achieved = tmu_flops(n, nb) * args.steps / (tmu_ms * 1e-3) / 1e12 if tmu_ms > 0 else None
-    traffic = TMU_TRAFFIC.get(kernel_source_hash())
+    bpe = TMU_TRAFFIC.get(kernel_source_hash())
+    elems = 0
+    for K0 in range(0, n, nb):
+        q = (n - K0 - min(nb, n - K0) + nb - 1) // nb
+        elems += q * (q + 1) // 2 * nb * nb
+    traffic = bpe * elems if bpe else None
     roofline = {"bound": "alu", "kernel": "k_gemm_f64 (FP64 DFMA trailing update)",
                 "achieved": tmu_achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (tmu_achieved / peak) if tmu_achieved else None,
                 "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (B300 has no FP64 tensor path; "
                                "DFMA microbenchmark 1.13 TFLOP/s)",
-                "traffic": (traffic / tmu_launches * args.steps) if traffic else None,
+                "traffic": (traffic * args.steps / tmu_launches) if traffic else None,
+                "traffic_note": "bytes per launch, scaled from an ncu capture at n=4096 by updated C elements",
                 "tmu_share_of_step": tmu_ms / ms if ms > 0 else None,
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
 
@@ -377,7 +386,7 @@ def run_ours(args, ws, rank, local):
         for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
             table = tune.tune(tdt, dev, per_bucket=64)
             nbf = tune.chooser(table)
-            faults = {}
+            bfaults = {}
             for q in range(0, 4096, 64):
                 i = q + int(r.integers(0, 64))
                 nn, b = int(sizes[i]), nbf(int(sizes[i]))
@@ -385,10 +394,10 @@ def run_ours(args, ws, rank, local):
                     row, col = int(r.integers(b, nn)), int(r.integers(b, nn))
                     if col // b > row // b:
                         row, col = col, row
-                    faults[i] = (0, abft.F_MEMORY, row, col, 1e3)
+                    bfaults[i] = (0, abft.F_MEMORY, row, col, 1e3)
             buf0 = base.to(tdt)
             buf = buf0.clone()
-            bt = abft.Batch(buf, sizes, offs, nbf, faults)
+            bt = abft.Batch(buf, sizes, offs, nbf, bfaults)
             bws = abft.Workspace()
             def bstep():
                 buf.copy_(buf0)
@@ -398,11 +407,11 @@ def run_ours(args, ws, rank, local):
             st = bt.statuses()
             ok = all(s_["info"] == 0 for s_ in st) and all(
                 st[i]["corrected"] == 1 and (st[i]["ev_row"], st[i]["ev_col"]) == f[2:4]
-                for i, f in faults.items())
+                for i, f in bfaults.items())
             ms_f = ms_b - ms_copy
             batched[name] = {"ms_per_batch": ms_f, "matrices_per_s": 4096 / (ms_f * 1e-3),
                              "tflops": bflops / (ms_f * 1e-3) / 1e12, "nb_by_bucket": table,
-                             "faults": len(faults), "all_located_and_corrected": ok}
+                             "bfaults": len(bfaults), "all_located_and_corrected": ok}
             del buf0, buf, bt
         abft.lib().abft_batched_graph_reset()
         del base
