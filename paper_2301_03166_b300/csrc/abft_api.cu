@@ -699,20 +699,25 @@ namespace {
 // ------------------------------------------------------------- solves / IR
 constexpr int kSplit = 8;   // split-K factor of the FP64 residual
 
+// potrs scratch: the chunk inverses (sized for FP64) then, for the FP32
+// solve, an n x 16 FP32 copy of the right-hand sides.
 size_t potrs_ws_bytes(int64_t n, int32_t dtype) {
-    const size_t f = (dtype == ABFT_F64) ? 0 : sizeof(float) * (size_t)n * 16;
-    return align_up(std::max<size_t>(f, 256));
+    const size_t inv = align_up(potrs_inv_bytes(n, true));
+    const size_t f = (dtype == ABFT_F64) ? 0 : align_up(sizeof(float) * (size_t)n * 16);
+    return std::max<size_t>(inv + f, 256);
 }
 
 int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
-              double* B, int64_t ldb, float* Yf, cudaStream_t s) {
+              double* B, int64_t ldb, char* ws, cudaStream_t s) {
+    void* inv = ws;
+    float* Yf = (float*)(ws + align_up(potrs_inv_bytes(n, true)));
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         if (dtype == ABFT_F64) {
-            ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, B + r0, ldb, s));
+            ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, B + r0, ldb, (double*)inv, s));
         } else {
             ABFT_CUDA_TRY(launch_copy_d2f(B + r0, ldb, Yf, 16, n, nr, s));
-            ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, s));
+            ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
             ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, B + r0, ldb, n, nr, s));
         }
     }
@@ -720,7 +725,7 @@ int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* 
 }
 
 struct IrWs {
-    size_t chol, yf, R, P, rs, norms, eta, total;
+    size_t chol, solve, R, P, rs, norms, eta, total;
 };
 
 IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
@@ -728,7 +733,7 @@ IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
     size_t off = 0;
     w.chol = off; off = align_up(off + chol_ws(n, nb, mode, mixed).total);
-    w.yf = off; off = align_up(off + sizeof(float) * (size_t)n * 16);
+    w.solve = off; off = align_up(off + potrs_ws_bytes(n, ABFT_F32));
     w.R = off; off = align_up(off + sizeof(double) * (size_t)n * 16);
     w.P = off; off = align_up(off + sizeof(double) * (size_t)kSplit * (size_t)n * 16);
     w.rs = off; off = align_up(off + sizeof(double) * (size_t)n);
@@ -762,7 +767,7 @@ int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double*
     if (n == 0 || nrhs == 0) return ABFT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     timing_mark(PH_SOLVE, 1, s);
-    int rc = potrs_run(n, nrhs, nb, dtype, L, ldl, B, ldb, (float*)ws, s);
+    int rc = potrs_run(n, nrhs, nb, dtype, L, ldl, B, ldb, (char*)ws, s);
     timing_mark(PH_SOLVE, 0, s);
     if (rc != ABFT_OK) return rc;
     ABFT_CUDA_TRY(timing_collect(s));
@@ -812,7 +817,9 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     if (rc > 0 || rc == ABFT_ERR_CUDA || rc == ABFT_ERR_TIMEOUT) return rc;
     const int factor_rc = rc;
     if (n == 0 || nrhs == 0) return factor_rc;
-    float* Yf = (float*)(base + w.yf);
+    char* sws = base + w.solve;
+    void* inv = sws;
+    float* Yf = (float*)(sws + align_up(potrs_inv_bytes(n, true)));
     double* R = (double*)(base + w.R);
     double* P = (double*)(base + w.P);
     double* rs = (double*)(base + w.rs);
@@ -828,7 +835,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
         // X0 = L^{-T} L^{-1} B
         timing_mark(PH_SOLVE, 1, s);
         ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
-        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, Yf, s);
+        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, sws, s);
         if (rc != ABFT_OK) return rc;
         int32_t it = 0;
         double eta = 0.0;
@@ -842,11 +849,11 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
             if (eta <= tol || it >= maxit || !(eta == eta)) break;
             // correction D = L^{-T} L^{-1} R in the solve precision, X += D
             if (dtype == ABFT_F64) {
-                ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, s));
+                ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, (double*)inv, s));
                 ABFT_CUDA_TRY(launch_add_f64(X + r0, ldx, R, 16, n, nr, s));
             } else {
                 ABFT_CUDA_TRY(launch_copy_d2f(R, 16, Yf, 16, n, nr, s));
-                ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, s));
+                ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
                 ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
             }
         }
@@ -984,7 +991,7 @@ int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, in
     if (run && Lbar == nullptr) return -12;
     if (ldlb < std::max<int64_t>(1, n)) return -13;
     if (ws_bytes == nullptr) return -15;
-    const size_t need = align_up(sizeof(double) * (size_t)n * 16) * 4;
+    const size_t need = align_up(sizeof(double) * (size_t)n * 16) * 4 + align_up(potrs_inv_bytes(n, true));
     if (ws == nullptr) {
         *ws_bytes = need;
         return ABFT_OK;
@@ -1000,7 +1007,8 @@ int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, in
     timing_mark(PH_SOLVE, 1, s);
     // Bbar = A^{-1} Xbar
     ABFT_CUDA_TRY(launch_copy_d2d(Xbar, ldxb, Bbar, ldbb, n, (int)nrhs, s));
-    ABFT_CUDA_TRY(launch_potrs_f64(n, (int)nrhs, nb, L, ldl, Bbar, ldbb, s));
+    ABFT_CUDA_TRY(launch_potrs_f64(n, (int)nrhs, nb, L, ldl, Bbar, ldbb,
+                                   (double*)((char*)ws + 4 * blk), s));
     // Lbar -= tril((Bbar X^T + X Bbar^T) L) = tril(Bbar (L^T X)^T + X (L^T Bbar)^T)
     ABFT_CUDA_TRY(launch_copy_d2d(X, ldx, Xc, 16, n, (int)nrhs, s));
     ABFT_CUDA_TRY(launch_copy_d2d(Bbar, ldbb, Bc, 16, n, (int)nrhs, s));

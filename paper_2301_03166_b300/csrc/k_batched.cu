@@ -221,10 +221,12 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             const T djj = sL[j][j];
             for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] / djj;
             __syncthreads();
-            const int w = kb - j - 1;
-            for (int e = t; e < w * w; e += BT) {
-                int i = j + 1 + e / w, l = j + 1 + e % w;
-                if (l <= i) sL[i][l] -= sL[i][j] * sL[l][j];
+            {   // rank-1 update of the remaining lower triangle on a 16 x 16 thread grid
+                const int tx = t & 15, ty = t >> 4;
+                for (int i = j + 1 + ty; i < kb; i += 16) {
+                    const T aij = sL[i][j];
+                    for (int l = j + 1 + tx; l <= i; l += 16) sL[i][l] -= aij * sL[l][j];
+                }
             }
             __syncthreads();
         }

@@ -11,16 +11,18 @@
 // run as an FP32 SIMT GEMM.  The panel solve runs in FP32 (k_trsm_rlt<float>),
 // the diagonal-block factorization, verification and correction stay in FP64.
 //
-// Kernel anatomy (one CTA per 128 x 128 output tile of the lower block
-// triangle, 192 threads, two CTAs per SM):
+// Kernel anatomy: persistent, one CTA per SM (320 threads), the 128 x 128
+// output tiles of the lower block triangle dealt round-robin to the CTAs:
 //   warp 0   TMA producer: 128x64 BF16 boxes of A (rows i0..) and B (rows j0..)
-//            with 128-byte swizzle into a 3-stage ring of shared buffers
-//   warp 1   TMEM allocation (128 columns) and the single-thread MMA issuer;
-//            tcgen05.commit releases each stage and finally signals the epilogue
-//   warps 2-5  tcgen05.ld of the FP32 accumulator (each warp its 32-lane
-//            quarter), staged in shared memory; then all six warps do a
-//            coalesced FP64 read-modify-write of C with the scales, 16 loads
-//            in flight per thread.
+//            with 128-byte swizzle into a 4-stage ring of shared buffers
+//   warp 1   TMEM allocation (2 x 128 columns) and the single-thread MMA
+//            issuer, alternating between the two accumulators so the next
+//            tile's MMAs run while the previous tile drains;
+//            tcgen05.commit releases each stage and signals the epilogue
+//   warps 2-9  tcgen05.ld of the FP32 accumulator (warp w reads lane quarter
+//            w % 4, column half (w - 2) / 4), staged in shared memory, the
+//            accumulator released, then a coalesced FP64 read-modify-write
+//            of C with the scales, 16 loads in flight per thread.
 // Every mbarrier wait is bounded: on timeout the CTA records an error in the
 // status block, skips the rest of its work, frees its TMEM and returns.
 #include <cuda.h>
@@ -36,16 +38,16 @@ namespace abft {
 namespace {
 
 constexpr int TM = 128, TN = 128, KC = 64;
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;
 constexpr int HALF_BYTES = TM * KC * 2;              // one 128 x 64 16-bit box
 constexpr int STAGE_BYTES = 2 * HALF_BYTES;          // A box + B box
-constexpr int MIX_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr int EPI_WARPS = 8;
+constexpr int MIX_THREADS = 64 + EPI_WARPS * 32;     // producer, MMA, 8 epilogue warps
+constexpr uint32_t TMEM_COLS = 256;                  // two 128-column FP32 accumulators
 constexpr int STG_LD = TN + 1;                       // epilogue staging row stride (floats)
-constexpr size_t MIX_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int STG_BYTES = TM * STG_LD * 4;
+constexpr size_t MIX_SMEM = (size_t)STAGES * STAGE_BYTES + STG_BYTES + 1024 + 256;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
-
-static_assert(TM * STG_LD * 4 <= STAGES * STAGE_BYTES, "staging must fit in the stage ring");
 
 struct MixArgs {
     double* C;
@@ -57,7 +59,8 @@ struct MixArgs {
     int ncf;
     ComputeFault cf[MAX_CF];
     DevStatus* st;
-    int64_t tiles_n;
+    int64_t ntiles;     // tiles of the lower block triangle (r x r per block pair)
+    int64_t r;          // 128-tiles per g
     uint32_t idesc;
 };
 
@@ -149,30 +152,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(MIX_THREADS) k_tmu_mixed(const __grid_constant__ CUtensorMap tmap,
-                                                          MixArgs a) {
+// Decode the idx-th tile of the lower block triangle: block pairs (BI >= BJ)
+// in row-major order, r x r 128-tiles inside each g x g block pair.
+__device__ __forceinline__ void lower_tile(int64_t idx, int64_t r, int64_t& ti, int64_t& tj) {
+    const int64_t r2 = r * r, pair = idx / r2, sub = idx % r2;
+    int64_t a = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
+    while (a * (a + 1) / 2 > pair) --a;
+    while ((a + 1) * (a + 2) / 2 <= pair) ++a;
+    const int64_t b = pair - a * (a + 1) / 2;
+    ti = a * r + sub / r;
+    tj = b * r + sub % r;
+}
+
+// Persistent warp-specialized update: CTA c handles tiles c, c + G, c + 2G, ...
+__global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_constant__ CUtensorMap tmap,
+                                                             MixArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    float* stg = (float*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES + STG_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accb = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
-    int* abort_flag = (int*)(tmem_slot + 1);
+    uint64_t* accf = empty + STAGES;   // [2]
+    uint64_t* acce = accf + 2;         // [2]
+    uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     if (a.st->info != 0) return;
-    const int64_t tm = blockIdx.x / a.tiles_n, tn = blockIdx.x % a.tiles_n;
-    const int64_t i0 = tm * TM, j0 = tn * TN;
-    {
-        int64_t rlast = (i0 + TM - 1 < a.M - 1 ? i0 + TM - 1 : a.M - 1) + a.off;
-        if (rlast / a.g < (j0 + a.off) / a.g) return;
-    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -188,107 +203,142 @@ __global__ void __launch_bounds__(MIX_THREADS) k_tmu_mixed(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int nk = (int)(a.K / KC);
+    const int64_t G = gridDim.x;
 
     if (warp == 0) {
-        if (lane == 0) {
-            for (int c = 0; c < nk; ++c) {
-                const int s = c % STAGES;
-                if (c >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((c - STAGES) / STAGES) & 1))) {
-                    *(volatile int*)abort_flag = 1;
-                    atomicExch(&a.st->error, 2);
-                    break;
+        if (lane == 0) {   // TMA producer
+            int64_t c = 0;
+            for (int64_t idx = blockIdx.x; idx < a.ntiles && !*abort_flag; idx += G) {
+                int64_t ti, tj;
+                lower_tile(idx, a.r, ti, tj);
+                if (ti * TM >= a.M || tj * TN >= a.M) continue;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = (int)(c % STAGES);
+                    if (c >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((c - STAGES) / STAGES) & 1))) {
+                        *abort_flag = 1;
+                        atomicExch(&a.st->error, 2);
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    uint8_t* dst = smem + s * STAGE_BYTES;
+                    tma_load_2d(dst, &tmap, &full[s], kc * KC, (int)(ti * TM));
+                    tma_load_2d(dst + HALF_BYTES, &tmap, &full[s], kc * KC, (int)(tj * TN));
                 }
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                uint8_t* dst = smem + s * STAGE_BYTES;
-                tma_load_2d(dst, &tmap, &full[s], c * KC, (int)i0);
-                tma_load_2d(dst + HALF_BYTES, &tmap, &full[s], c * KC, (int)j0);
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            bool ok = true;
-            for (int c = 0; c < nk; ++c) {
-                const int s = c % STAGES;
-                if (!mbar_wait(&full[s], (uint32_t)((c / STAGES) & 1))) {
-                    *(volatile int*)abort_flag = 1;
+        if (lane == 0) {   // MMA issuer
+            int64_t c = 0, it = 0;
+            for (int64_t idx = blockIdx.x; idx < a.ntiles && !*abort_flag; idx += G) {
+                int64_t ti, tj;
+                lower_tile(idx, a.r, ti, tj);
+                if (ti * TM >= a.M || tj * TN >= a.M) continue;
+                const int b = (int)(it & 1);
+                if (it >= 2 && !mbar_wait(&acce[b], (uint32_t)(((it >> 1) - 1) & 1))) {
+                    *abort_flag = 1;
                     atomicExch(&a.st->error, 2);
-                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t abase = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t bbase = abase + HALF_BYTES;
+                const uint32_t dt = tmem + (uint32_t)(b * TN);
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = (int)(c % STAGES);
+                    if (!mbar_wait(&full[s], (uint32_t)((c / STAGES) & 1))) {
+                        *abort_flag = 1;
+                        atomicExch(&a.st->error, 2);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t abase = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t bbase = abase + HALF_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < KC / 16; ++kk)
-                    mma_f16(tmem, smem_desc(abase + kk * 32), smem_desc(bbase + kk * 32), a.idesc,
-                            (c | kk) != 0 ? 1u : 0u);
-                mma_commit(&empty[s]);
+                    for (int kk = 0; kk < KC / 16; ++kk)
+                        mma_f16(dt, smem_desc(abase + kk * 32), smem_desc(bbase + kk * 32), a.idesc,
+                                (kc | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&accf[b]);
+                ++it;
             }
-            if (ok) mma_commit(accb);
+        }
+    } else {
+        // epilogue warps: TMEM lane quarter q = warp % 4, column half h
+        const int ew = warp - 2;               // 0 .. EPI_WARPS-1
+        const int q = warp & 3;
+        const int h = ew >> 2;                 // 0 or 1: columns [64 h, 64 h + 64)
+        int64_t it = 0;
+        for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
+            int64_t ti, tj;
+            lower_tile(idx, a.r, ti, tj);
+            if (ti * TM >= a.M || tj * TN >= a.M) continue;
+            const int b = (int)(it & 1);
+            bool ok = !*abort_flag && mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1));
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(&a.st->error, 2);
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int r = q * 32 + lane;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    uint32_t v[32];
+                    const int col = h * 64 + cc * 32;
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + col), v);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) stg[r * STG_LD + col + u] = __uint_as_float(v[u]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+            if (!*abort_flag) {
+                const int64_t i0 = ti * TM, j0 = tj * TN;
+                // FP64 read-modify-write of the tile, 4 rows x 4 column chunks in flight
+                for (int rb = ew; rb < TM; rb += EPI_WARPS * 4) {
+                    double cv[4][4];
+                    double* ptr[4][4];
+                    double sc[4][4];
+                    int rrv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = rb + u * EPI_WARPS;
+                        rrv[u] = rr;
+                        const int64_t i = i0 + rr;
+                        const bool rowok = rr < TM && i < a.M;
+                        const int64_t bi = rowok ? (i + a.off) / a.g : 0;
+                        const double si = rowok ? a.sig[bi] : 0.0;
+#pragma unroll
+                        for (int t4 = 0; t4 < TN / 32; ++t4) {
+                            const int64_t j = j0 + lane + 32 * t4;
+                            const int64_t bj = (j + a.off) / a.g;
+                            const bool okj = rowok && j < a.M && bi >= bj;
+                            ptr[u][t4] = okj ? a.C + i * a.ldc + j : nullptr;
+                            sc[u][t4] = okj ? si * a.sig[bj] : 0.0;
+                            cv[u][t4] = okj ? *ptr[u][t4] : 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int t4 = 0; t4 < TN / 32; ++t4) {
+                            if (ptr[u][t4] == nullptr) continue;
+                            double v = cv[u][t4] - sc[u][t4] * (double)stg[rrv[u] * STG_LD + lane + 32 * t4];
+                            const int64_t i = i0 + rrv[u], j = j0 + lane + 32 * t4;
+                            for (int f = 0; f < a.ncf; ++f)
+                                if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
+                            *ptr[u][t4] = v;
+                        }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+            ++it;
         }
     }
     __syncwarp();
-    // all warps: wait for the accumulator (bounded)
-    const bool acc_ok = mbar_wait(accb, 0);
-    if (!acc_ok && threadIdx.x == 0) {
-        *(volatile int*)abort_flag = 1;
-        atomicExch(&a.st->error, 2);
-    }
-    float* stg = (float*)smem;   // the stage ring is free once the accumulator is complete
-    if (acc_ok && warp >= 2) {
-        // TMEM -> shared staging: warp w reads its lane quarter q = w % 4
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int q = warp & 3;
-        const int r = q * 32 + lane;
-#pragma unroll
-        for (int cc = 0; cc < TN / 32; ++cc) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
-#pragma unroll
-            for (int u = 0; u < 32; ++u) stg[r * STG_LD + cc * 32 + u] = __uint_as_float(v[u]);
-        }
-    }
-    __syncthreads();
-    if (acc_ok && *(volatile int*)abort_flag == 0) {
-        // FP64 read-modify-write of C by all 6 warps, 4 rows x 4 column chunks
-        // (16 independent loads) in flight per thread
-        constexpr int NW = MIX_THREADS / 32;
-        for (int rb = warp; rb < TM; rb += NW * 4) {
-            double cv[4][4];
-            double* ptr[4][4];
-            double sc[4][4];
-            int rrv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int rr = rb + u * NW;
-                rrv[u] = rr;
-                const int64_t i = i0 + rr;
-                const bool rowok = rr < TM && i < a.M;
-                const int64_t bi = rowok ? (i + a.off) / a.g : 0;
-                const double si = rowok ? a.sig[bi] : 0.0;
-#pragma unroll
-                for (int t = 0; t < TN / 32; ++t) {
-                    const int64_t j = j0 + lane + 32 * t;
-                    const int64_t bj = (j + a.off) / a.g;
-                    const bool ok = rowok && j < a.M && bi >= bj;
-                    ptr[u][t] = ok ? a.C + i * a.ldc + j : nullptr;
-                    sc[u][t] = ok ? si * a.sig[bj] : 0.0;
-                    cv[u][t] = ok ? *ptr[u][t] : 0.0;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int t = 0; t < TN / 32; ++t) {
-                    if (ptr[u][t] == nullptr) continue;
-                    double v = cv[u][t] - sc[u][t] * (double)stg[rrv[u] * STG_LD + lane + 32 * t];
-                    const int64_t i = i0 + rrv[u], j = j0 + lane + 32 * t;
-                    for (int f = 0; f < a.ncf; ++f)
-                        if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
-                    *ptr[u][t] = v;
-                }
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
@@ -490,14 +540,17 @@ cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16
     a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.g = g; a.off = off; a.sig = sig; a.st = st;
     a.ncf = 0;
     for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
-    const int64_t tiles = (m + TM - 1) / TM;
-    a.tiles_n = tiles;
+    const int64_t q = (m + g - 1) / g;
+    a.r = g / TM;
+    a.ntiles = q * (q + 1) / 2 * a.r * a.r;
     // kind::f16 instruction descriptor: D F32 (bits 4-5), A/B format BF16 = 1 or
     // F16 = 0 (bits 7-9, 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
     const uint32_t fmt = bf16 ? 1u : 0u;
     a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) |
               ((uint32_t)(TM >> 4) << 24);
-    k_tmu_mixed<<<(unsigned)(tiles * tiles), MIX_THREADS, MIX_SMEM, s>>>(map, a);
+    int64_t grid = num_sms();
+    if (grid > a.ntiles) grid = a.ntiles;
+    k_tmu_mixed<<<(unsigned)grid, MIX_THREADS, MIX_SMEM, s>>>(map, a);
     note_launch();
     return cudaGetLastError();
 }

@@ -42,10 +42,11 @@ __global__ void __launch_bounds__(256) k_potf2_small(double* A, int64_t lda, int
         const double djj = a[j][j];
         for (int i = j + 1 + t; i < nb; i += blockDim.x) a[i][j] = a[i][j] / djj;
         __syncthreads();
-        const int m = nb - j - 1;
-        for (int e = t; e < m * m; e += blockDim.x) {
-            int i = j + 1 + e / m, l = j + 1 + e % m;
-            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        // rank-1 update of the remaining lower triangle on a 16 x 16 thread grid
+        const int tx = t & 15, ty = t >> 4;
+        for (int i = j + 1 + ty; i < nb; i += 16) {
+            const double aij = a[i][j];
+            for (int l = j + 1 + tx; l <= i; l += 16) a[i][l] -= aij * a[l][j];
         }
         __syncthreads();
     }

@@ -18,18 +18,43 @@ namespace {
 
 constexpr int MAXRHS = 16;
 
+// Inverses of the 32 x 32 diagonal chunks of L (lower), one warp per chunk:
+// lane j computes column j of the inverse by substitution with the chunk in
+// shared memory.  Used by the diagonal-block solves below.
+template <typename T>
+__global__ void __launch_bounds__(32) k_chunk_inv(const double* L, int64_t ldl, int64_t n, T* Inv) {
+    __shared__ T Lc[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int w = (int)((n - c0) < 32 ? (n - c0) : 32);
+    const int lane = threadIdx.x;
+    for (int i = 0; i < 32; ++i)
+        Lc[i][lane] = (i < w && lane <= i) ? (T)L[(c0 + i) * ldl + c0 + lane] : (T)0;
+    __syncwarp();
+    T x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        T v = (i == lane) ? (T)1 : (T)0;
+#pragma unroll
+        for (int p = 0; p < i; ++p) v -= Lc[i][p] * x[p];
+        x[i] = (i < w) ? v / Lc[i][i] : (T)0;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Inv[(c0 + i) * 32 + lane] = (i < w && lane < w) ? x[i] : (T)0;
+}
+
 // Solve the kb x kb diagonal block in place: L Y = Y (TRANS = 0) or
 // L^T X = X (TRANS = 1) for nrhs <= 16 right-hand sides (Y row-major, ld ldy).
-// 32-row chunks: the chunk is first updated from the already solved rows (all
-// threads), then solved by substitution with its 32 x 32 block of L in shared
-// memory, one row per step, every (row, rhs) pair on its own thread.
+// 32-row chunks: the chunk is updated from the already solved rows, then
+// multiplied by its precomputed inverse (Inv: the block's chunks, 32 x 32 each).
 template <typename T, int TRANS>
 __global__ void __launch_bounds__(512) k_trsv_diag(const double* L, int64_t ldl, int kb, T* Y,
-                                                   int64_t ldy, int nrhs) {
+                                                   int64_t ldy, int nrhs, const T* Inv) {
     extern __shared__ __align__(16) unsigned char sb[];
     T* y = (T*)sb;                        // kb x MAXRHS
-    __shared__ T Lc[32][33];
-    __shared__ T xs[32][MAXRHS];
+    T* Lr = y + (size_t)kb * MAXRHS;      // 32 x (kb + 1): the chunk's rows (or columns) of L
+    const int ldr = kb + 1;
+    __shared__ T Ic[32][33];
+    __shared__ T tmp[32][MAXRHS];
     const int t = threadIdx.x;
     for (int e = t; e < kb * nrhs; e += blockDim.x) {
         int i = e / nrhs, r = e % nrhs;
@@ -41,37 +66,44 @@ __global__ void __launch_bounds__(512) k_trsv_diag(const double* L, int64_t ldl,
     for (int ci = 0; ci < nch; ++ci) {
         const int c = TRANS ? nch - 1 - ci : ci;
         const int c0 = c * 32, c1 = (c0 + 32 < kb) ? c0 + 32 : kb, w = c1 - c0;
+        // the chunk's inverse (transposed for the backward solve)
+        for (int e = t; e < 32 * 32; e += blockDim.x) {
+            int a = e >> 5, b = e & 31;
+            Ic[a][b] = TRANS ? Inv[(int64_t)(c0 + b) * 32 + a] : Inv[(int64_t)(c0 + a) * 32 + b];
+        }
+        // stage the part of L that couples the chunk to the solved rows in one
+        // coalesced pass: rows c0..c1 x cols 0..c0 (forward), or rows c1..kb x
+        // cols c0..c1 stored transposed (backward)
+        if (!TRANS) {
+            for (int e = t; e < w * c0; e += blockDim.x) {
+                int a = e / c0, b = e % c0;
+                Lr[a * ldr + b] = (T)L[(int64_t)(c0 + a) * ldl + b];
+            }
+        } else {
+            const int h = kb - c1;
+            for (int e = t; e < h * 32; e += blockDim.x) {
+                int b = e >> 5, a = e & 31;
+                if (a < w) Lr[a * ldr + b] = (T)L[(int64_t)(c1 + b) * ldl + c0 + a];
+            }
+        }
+        __syncthreads();
         // update the chunk from the solved rows
         if (q < w && r < nrhs) {
             const int i = c0 + q;
             T acc = 0;
             if (!TRANS) {
-                for (int p = 0; p < c0; ++p) acc += (T)L[(int64_t)i * ldl + p] * y[p * MAXRHS + r];
+                for (int p = 0; p < c0; ++p) acc += Lr[q * ldr + p] * y[p * MAXRHS + r];
             } else {
-                for (int p = c1; p < kb; ++p) acc += (T)L[(int64_t)p * ldl + i] * y[p * MAXRHS + r];
+                for (int p = c1; p < kb; ++p) acc += Lr[q * ldr + (p - c1)] * y[p * MAXRHS + r];
             }
-            y[i * MAXRHS + r] -= acc;
-        }
-        // the chunk's block of L (transposed for the backward solve)
-        for (int e = t; e < 32 * 32; e += blockDim.x) {
-            int a = e >> 5, b = e & 31;
-            T v = 0;
-            if (a < w && b < w) v = TRANS ? (T)L[(int64_t)(c0 + b) * ldl + c0 + a]
-                                          : (T)L[(int64_t)(c0 + a) * ldl + c0 + b];
-            Lc[a][b] = v;     // row a of the (possibly transposed) chunk
+            tmp[q][r] = y[i * MAXRHS + r] - acc;
         }
         __syncthreads();
-        // substitution: step s fixes row j (ascending, or descending for L^T)
-        for (int st = 0; st < w; ++st) {
-            const int jj = TRANS ? w - 1 - st : st;
-            if (r < nrhs && q < w) {
-                const T xj = y[(c0 + jj) * MAXRHS + r] / Lc[jj][jj];
-                if (q == jj) xs[q][r] = xj;
-                else if (TRANS ? q < jj : q > jj) y[(c0 + q) * MAXRHS + r] -= Lc[q][jj] * xj;
-            }
-            __syncthreads();
+        if (q < w && r < nrhs) {
+            T v = 0;
+            for (int p = 0; p < w; ++p) v += Ic[q][p] * tmp[p][r];
+            y[(c0 + q) * MAXRHS + r] = v;
         }
-        if (q < w && r < nrhs) y[(c0 + q) * MAXRHS + r] = xs[q][r];
         __syncthreads();
     }
     for (int e = t; e < kb * nrhs; e += blockDim.x) {
@@ -260,25 +292,29 @@ template <typename T>
 cudaError_t set_attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
+    const int bytes = (512 * MAXRHS + 32 * 513) * (int)sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_trsv_diag<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         512 * MAXRHS * (int)sizeof(T));
+                                         bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_trsv_diag<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 512 * MAXRHS * (int)sizeof(T));
+                                 bytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
 template <typename T>
 cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl, T* Y,
-                    int64_t ldy, cudaStream_t s) {
+                    int64_t ldy, T* Inv, cudaStream_t s) {
     cudaError_t e = set_attrs<T>();
     if (e != cudaSuccess) return e;
     const int64_t N = (n + nb - 1) / nb;
-    const size_t smem = (size_t)nb * MAXRHS * sizeof(T);
+    const size_t smem = (size_t)(nb * MAXRHS + 32 * (nb + 1)) * sizeof(T);
+    k_chunk_inv<T><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(L, ldl, n, Inv);
+    note_launch();
     for (int64_t k = 0; k < N; ++k) {   // L Y = B
         const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0, T0 = K0 + kb;
-        k_trsv_diag<T, 0><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
+        k_trsv_diag<T, 0><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy,
+                                               nrhs, Inv + K0 * 32);
         note_launch();
         if (T0 < n) {
             k_trsv_update<T, 0><<<(unsigned)((n - T0 + 63) / 64), 256, 0, s>>>(
@@ -288,7 +324,8 @@ cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ld
     }
     for (int64_t k = N - 1; k >= 0; --k) {   // L^T X = Y
         const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0;
-        k_trsv_diag<T, 1><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy, nrhs);
+        k_trsv_diag<T, 1><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy,
+                                               nrhs, Inv + K0 * 32);
         note_launch();
         if (K0 > 0) {
             k_trsv_update<T, 1><<<(unsigned)((K0 + 63) / 64), 256, 0, s>>>(
@@ -304,13 +341,17 @@ cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ld
 int potrs_max_rhs() { return MAXRHS; }
 
 cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             double* B, int64_t ldb, cudaStream_t s) {
-    return potrs_t<double>(n, nrhs, nb, L, ldl, B, ldb, s);
+                             double* B, int64_t ldb, double* inv, cudaStream_t s) {
+    return potrs_t<double>(n, nrhs, nb, L, ldl, B, ldb, inv, s);
 }
 
 cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             float* B, int64_t ldb, cudaStream_t s) {
-    return potrs_t<float>(n, nrhs, nb, L, ldl, B, ldb, s);
+                             float* B, int64_t ldb, float* inv, cudaStream_t s) {
+    return potrs_t<float>(n, nrhs, nb, L, ldl, B, ldb, inv, s);
+}
+
+size_t potrs_inv_bytes(int64_t n, bool f64) {
+    return (size_t)((n + 31) / 32) * 32 * 32 * (f64 ? sizeof(double) : sizeof(float));
 }
 
 cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
