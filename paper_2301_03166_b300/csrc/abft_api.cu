@@ -720,6 +720,10 @@ int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* 
             ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
             ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, B + r0, ldb, n, nr, s));
         }
+        cudaError_t ce = cudaSuccess;
+        const int err = potrs_error(inv, n, dtype == ABFT_F64, s, &ce);
+        ABFT_CUDA_TRY(ce);
+        if (err) return ABFT_ERR_TIMEOUT;
     }
     return ABFT_OK;
 }
@@ -856,6 +860,10 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
                 ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
                 ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
             }
+            cudaError_t ce = cudaSuccess;
+            const int serr = potrs_error(inv, n, dtype == ABFT_F64, s, &ce);
+            ABFT_CUDA_TRY(ce);
+            if (serr) return ABFT_ERR_TIMEOUT;
         }
         timing_mark(PH_SOLVE, 0, s);
         iters_max = std::max(iters_max, it);
@@ -1009,6 +1017,12 @@ int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, in
     ABFT_CUDA_TRY(launch_copy_d2d(Xbar, ldxb, Bbar, ldbb, n, (int)nrhs, s));
     ABFT_CUDA_TRY(launch_potrs_f64(n, (int)nrhs, nb, L, ldl, Bbar, ldbb,
                                    (double*)((char*)ws + 4 * blk), s));
+    {
+        cudaError_t ce = cudaSuccess;
+        const int serr = potrs_error((char*)ws + 4 * blk, n, true, s, &ce);
+        ABFT_CUDA_TRY(ce);
+        if (serr) return ABFT_ERR_TIMEOUT;
+    }
     // Lbar -= tril((Bbar X^T + X Bbar^T) L) = tril(Bbar (L^T X)^T + X (L^T Bbar)^T)
     ABFT_CUDA_TRY(launch_copy_d2d(X, ldx, Xc, 16, n, (int)nrhs, s));
     ABFT_CUDA_TRY(launch_copy_d2d(Bbar, ldbb, Bc, 16, n, (int)nrhs, s));

@@ -230,12 +230,16 @@ cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, c
 
 // Solves and iterative refinement (k_solve.cu).
 int potrs_max_rhs();
-// inv: scratch for the inverses of the 32 x 32 diagonal chunks (potrs_inv_bytes).
+// inv: scratch for the inverses of the 32 x 32 diagonal chunks and the sweep's
+// tickets and ready flags (potrs_inv_bytes).
 cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
                              double* B, int64_t ldb, double* inv, cudaStream_t s);
 cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
                              float* B, int64_t ldb, float* inv, cudaStream_t s);
 size_t potrs_inv_bytes(int64_t n, bool f64);
+// Nonzero when a wait of the last solve using `inv` gave up (reads one word and
+// synchronizes the stream; *ce receives the copy's status).
+int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_t* ce);
 cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
                             int cols, cudaStream_t s);
 cudaError_t launch_copy_d2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,

@@ -19,7 +19,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxG = 512;
-constexpr int kMaxT = kMaxG / 32;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -43,37 +42,49 @@ __device__ __forceinline__ void tile_coords(const TileSet& ts, int64_t idx, int6
 }
 
 // Sums of one tile into shared memory: colsum[j], and when asked wsum[j]
-// (weights 1..nr) and rowsum[i].
-template <bool COLW, bool ROWS>
+// (weights 1..nr) and rowsum[i].  TM = column groups of 32 per lane (g <= 32 TM);
+// each warp loads 32 / TM rows per batch, so a lane has 32 loads in flight.
+template <int TM, bool COLW, bool ROWS>
 __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* colsum,
                           double* wsum, double* rowsum, double (*part)[kMaxG]) {
+    constexpr int U = 32 / TM;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = (nc + 31) >> 5;
-    double acc[kMaxT], wacc[kMaxT];
+    double acc[TM], wacc[TM];
 #pragma unroll
-    for (int t = 0; t < kMaxT; ++t) { acc[t] = 0.0; wacc[t] = 0.0; }
-    for (int i = warp; i < nr; i += kWarps) {
-        const double* row = T + (int64_t)i * ldt;
-        double rs = 0.0;
-        const double wi = (double)(i + 1);
+    for (int t = 0; t < TM; ++t) { acc[t] = 0.0; wacc[t] = 0.0; }
+    for (int i0 = warp; i0 < nr; i0 += U * kWarps) {
+        double v[U][TM];
 #pragma unroll
-        for (int t = 0; t < kMaxT; ++t) {
-            if (t < nt) {
-                int j = lane + 32 * t;
-                double v = (j < nc) ? row[j] : 0.0;
-                acc[t] += v;
-                if (COLW) wacc[t] = fma(wi, v, wacc[t]);
-                rs += v;
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            const double* row = T + (int64_t)i * ldt;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                const int j = lane + 32 * t;
+                v[u][t] = (t < nt && i < nr && j < nc) ? row[j] : 0.0;
             }
         }
-        if (ROWS) {
-            rs = warp_sum(rs);
-            if (lane == 0) rowsum[i] = rs;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            const double wi = (double)(i + 1);
+            double rs = 0.0;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                acc[t] += v[u][t];
+                if (COLW) wacc[t] = fma(wi, v[u][t], wacc[t]);
+                rs += v[u][t];
+            }
+            if (ROWS) {
+                rs = warp_sum(rs);
+                if (lane == 0 && i < nr) rowsum[i] = rs;
+            }
         }
     }
     // combine the per-warp column partial sums in warp order
 #pragma unroll
-    for (int t = 0; t < kMaxT; ++t)
+    for (int t = 0; t < TM; ++t)
         if (t < nt) part[warp][lane + 32 * t] = acc[t];
     __syncthreads();
     for (int j = threadIdx.x; j < nc; j += kThreads) {
@@ -84,7 +95,7 @@ __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* 
     __syncthreads();
     if (COLW) {
 #pragma unroll
-        for (int t = 0; t < kMaxT; ++t)
+        for (int t = 0; t < TM; ++t)
             if (t < nt) part[warp][lane + 32 * t] = wacc[t];
         __syncthreads();
         for (int j = threadIdx.x; j < nc; j += kThreads) {
@@ -104,7 +115,7 @@ __device__ __forceinline__ void tile_extent(const TileSet& ts, int64_t I, int64_
     nc = (int)(b < ts.g ? b : ts.g);
 }
 
-template <bool COLW, bool ROWS>
+template <int TM, bool COLW, bool ROWS>
 __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
     __shared__ double part[kWarps][kMaxG];
     __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
     tile_extent(ts, I, J, nr, nc);
     if (nr <= 0 || nc <= 0) return;
     const double* T = ts.A + I * ts.g * ts.lda + J * ts.g;
-    tile_sums<COLW, ROWS>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    tile_sums<TM, COLW, ROWS>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
     double* cc = ts.cc + I * ts.ccI + J * ts.g;
     for (int j = threadIdx.x; j < nc; j += kThreads) {
         cc[j] = colsum[j];
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
 // checksum is wrong, re-encode it; >=2 rows and >=2 cols -> 2D, uncorrectable.
 // Single mode: each flagged column is located at i = rint(d^w_j / d^c_j) - 1
 // (accepted within 0.05 of an integer and inside the tile) and corrected by d^c_j.
-template <int MODE>
+template <int MODE, int TM>
 __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevStatus* st) {
     __shared__ double part[kWarps][kMaxG];
     __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
@@ -151,7 +162,8 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     double* cw = (MODE == MODE_SINGLE) ? ts.cw + I * ts.ccI + J * ts.g : nullptr;
     double* cr = (MODE == MODE_FULL) ? ts.cr + r0 * ts.crs + J * ts.crJ : nullptr;
     if (threadIdx.x == 0) { s_nfc = 0; s_nfr = 0; s_fc = 1 << 30; s_fr = 1 << 30; }
-    tile_sums<MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum, rowsum, part);
+    tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum, rowsum,
+                                                         part);
     const double tau = st->tau;
     double dmax = 0.0;
     // d = recomputed - carried, kept in place of the sums
@@ -306,15 +318,28 @@ int64_t tile_count(const TileSet& ts) {
     return (ts.I1 - ts.I0) * (ts.J1 - ts.J0);
 }
 
+template <int TM>
+void encode_t(const TileSet& ts, int mode, int64_t nt, cudaStream_t s) {
+    const bool colw = mode == MODE_SINGLE || ts.weighted;
+    if (mode == MODE_FULL && colw) k_encode<TM, true, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    else if (mode == MODE_FULL) k_encode<TM, false, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    else k_encode<TM, true, false><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+}
+
+template <int TM>
+void verify_t(const TileSet& ts, int mode, int step, DevStatus* st, int64_t nt, cudaStream_t s) {
+    if (mode == MODE_FULL) k_verify<MODE_FULL, TM><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
+    else k_verify<MODE_SINGLE, TM><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
+}
+
 }  // namespace
 
 cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s) {
     int64_t nt = tile_count(ts);
     if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
-    const bool colw = mode == MODE_SINGLE || ts.weighted;
-    if (mode == MODE_FULL && colw) k_encode<true, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
-    else if (mode == MODE_FULL) k_encode<false, true><<<(unsigned)nt, kThreads, 0, s>>>(ts);
-    else k_encode<true, false><<<(unsigned)nt, kThreads, 0, s>>>(ts);
+    if (ts.g > kMaxG) return cudaErrorInvalidValue;
+    if (ts.g <= 256) encode_t<8>(ts, mode, nt, s);
+    else encode_t<16>(ts, mode, nt, s);
     note_launch();
     return cudaGetLastError();
 }
@@ -322,8 +347,9 @@ cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s) {
 cudaError_t launch_verify(const TileSet& ts, int mode, int step, DevStatus* st, cudaStream_t s) {
     int64_t nt = tile_count(ts);
     if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
-    if (mode == MODE_FULL) k_verify<MODE_FULL><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
-    else k_verify<MODE_SINGLE><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
+    if (ts.g > kMaxG) return cudaErrorInvalidValue;
+    if (ts.g <= 256) verify_t<8>(ts, mode, step, st, nt, s);
+    else verify_t<16>(ts, mode, step, st, nt, s);
     note_launch();
     return cudaGetLastError();
 }

@@ -29,11 +29,14 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
 
 namespace abft {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -351,35 +354,68 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
 // Quantize the panel per g-row tile: sigma_I = 2^(ceil(log2 max|L_I|) - e_t),
 // Lq = RN(L / sigma_I) in BF16 (e_t = 0) or FP16 (e_t = 14); t_I = 1^T Lq_I
 // and (single-side mode) tw_I = (1..g)^T Lq_I, in FP64.
+// One cluster of QCL CTAs per tile, each CTA a slab of g / QCL rows: the tile
+// maximum and the column sums are combined in rank 0's shared memory (the
+// slab partial sums in rank order).  The panel was just written by the panel
+// solve, so both passes over it are served mostly from L2.
+constexpr int QCL = 8;
+
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_quant_panel(const double* P, int64_t lda, int64_t T0,
-                                                     int64_t n, int kb, int64_t g, int64_t I0,
-                                                     uint16_t* Lq, double* sig, double* tsum,
-                                                     int64_t tstride, int weighted) {
+__global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
+    k_quant_panel(const double* __restrict__ P, int64_t lda, int64_t T0, int64_t n, int kb,
+                  int64_t g, int64_t I0, uint16_t* __restrict__ Lq, double* __restrict__ sig,
+                  double* __restrict__ tsum, int64_t tstride, int weighted) {
+    extern __shared__ double qpart[];     // rank 0: [QCL][2][kb] slab column sums
     __shared__ double red[8];
-    const int64_t I = I0 + blockIdx.x;
+    __shared__ double cmax[QCL];          // rank 0: slab maxima
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int t = threadIdx.x;
+    const int64_t I = I0 + blockIdx.x / QCL;
     const int64_t r0 = I * g, r1 = (r0 + g < n) ? r0 + g : n;
+    const int64_t rps = (g + QCL - 1) / QCL;
+    const int64_t s0 = (r0 + rank * rps < r1) ? r0 + rank * rps : r1;
+    const int64_t s1 = (s0 + rps < r1) ? s0 + rps : r1;
     double m = 0.0;
-    for (int64_t e = threadIdx.x; e < (r1 - r0) * kb; e += blockDim.x) {
-        int64_t r = r0 + e / kb;
-        int p = (int)(e % kb);
-        m = fmax(m, fabs(P[r * lda + p]));
+    for (int p = t; p < kb; p += 256) {
+        for (int64_t r = s0; r < s1; r += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (r + u < s1) ? P[(r + u) * lda + p] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) m = fmax(m, fabs(v[u]));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    if ((t & 31) == 0) red[t >> 5] = m;
     __syncthreads();
-    m = red[0];
-    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    if (t == 0) {
+        double mc = red[0];
+        for (int w = 1; w < 8; ++w) mc = fmax(mc, red[w]);
+        double* rc = cl.map_shared_rank(cmax, 0);
+        rc[rank] = mc;
+    }
+    cl.sync();
+    {
+        const double* rc = cl.map_shared_rank(cmax, 0);
+        m = rc[0];
+        for (int c = 1; c < QCL; ++c) m = fmax(m, rc[c]);
+    }
     int e2 = 0;
-    double f = frexp(m, &e2);          // m = f 2^e2, f in [0.5, 1)
-    int cl = (f == 0.5) ? e2 - 1 : e2; // ceil(log2 m)
-    const double sigma = (m > 0.0) ? ldexp(1.0, cl - (BF16 ? 0 : 14)) : 1.0;
-    if (threadIdx.x == 0) sig[I] = sigma;
-    for (int p = threadIdx.x; p < kb; p += blockDim.x) {
+    const double f = frexp(m, &e2);                 // m = f 2^e2, f in [0.5, 1)
+    const int cexp = (f == 0.5) ? e2 - 1 : e2;      // ceil(log2 m)
+    const int ex = cexp - (BF16 ? 0 : 14);
+    const double sigma = (m > 0.0) ? ldexp(1.0, ex) : 1.0;
+    // x / sigma is exact scaling by a power of two; multiply by the exact
+    // reciprocal unless it would leave the normal range
+    const bool use_mul = m > 0.0 && ex > -1000 && ex < 1000;
+    const double rsig = use_mul ? ldexp(1.0, -ex) : 1.0;
+    double* qp = cl.map_shared_rank(qpart, 0);
+    for (int p = t; p < kb; p += 256) {
         double s = 0.0, sw = 0.0;
-        for (int64_t r = r0; r < r1; ++r) {
-            double x = P[r * lda + p] / sigma;
+        for (int64_t r = s0; r < s1; ++r) {
+            const double x = use_mul ? P[r * lda + p] * rsig : P[r * lda + p] / sigma;
             double xq;
             uint16_t bits;
             if (BF16) {
@@ -394,6 +430,18 @@ __global__ void __launch_bounds__(256) k_quant_panel(const double* P, int64_t ld
             Lq[(r - T0) * kb + p] = bits;
             s += xq;
             sw += (double)(r - r0 + 1) * xq;
+        }
+        qp[(2 * rank) * kb + p] = s;
+        qp[(2 * rank + 1) * kb + p] = sw;
+    }
+    cl.sync();
+    if (rank != 0) return;
+    if (t == 0) sig[I] = sigma;
+    for (int p = t; p < kb; p += 256) {
+        double s = 0.0, sw = 0.0;
+        for (int c = 0; c < QCL; ++c) {
+            s += qpart[(2 * c) * kb + p];
+            sw += qpart[(2 * c + 1) * kb + p];
         }
         tsum[I * tstride + p] = s;
         if (weighted) tsum[I * tstride + kb + p] = sw;
@@ -501,12 +549,26 @@ cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t
                                double* sig, double* tsum, int64_t tstride, int weighted,
                                cudaStream_t s) {
     if (I1 <= I0) return cudaSuccess;
+    if (kb > 512) return cudaErrorInvalidValue;
+    static bool attr = false;
+    const size_t smem = sizeof(double) * 2 * QCL * 512;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_quant_panel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_quant_panel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t need = sizeof(double) * 2 * QCL * (size_t)kb;
+    const unsigned grid = (unsigned)((I1 - I0) * QCL);
     if (bf16)
-        k_quant_panel<true><<<(unsigned)(I1 - I0), 256, 0, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq,
-                                                                  sig, tsum, tstride, weighted);
+        k_quant_panel<true><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
+                                                    tstride, weighted);
     else
-        k_quant_panel<false><<<(unsigned)(I1 - I0), 256, 0, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq,
-                                                                   sig, tsum, tstride, weighted);
+        k_quant_panel<false><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
+                                                     tstride, weighted);
     note_launch();
     return cudaGetLastError();
 }

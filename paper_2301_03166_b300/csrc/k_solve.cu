@@ -2,13 +2,14 @@
 // pieces of iterative refinement: the FP64 residual R = B - A X, the
 // normwise backward error, and X += D.
 //
-// potrs runs block by block: a one-CTA solve of the nb x nb diagonal block
-// (32-row chunks: an update from the solved rows by all threads, then a short
-// substitution inside the chunk), and a many-CTA update of the remaining rows
-// with the just-solved block.  T is the arithmetic type (double for the FP64
-// solve, float for the correction solves of iterative refinement); L is read
-// in FP64 and converted on load.
+// potrs is two launches of a persistent sweep kernel (forward with L, backward
+// with L^T), each covering all 64-row blocks with flag-ordered block solves.
+// T is the arithmetic type (double for the FP64 solve, float for the
+// correction solves of iterative refinement); L is read in FP64 and converted
+// on load.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -42,119 +43,219 @@ __global__ void __launch_bounds__(32) k_chunk_inv(const double* L, int64_t ldl, 
     for (int i = 0; i < 32; ++i) Inv[(c0 + i) * 32 + lane] = (i < w && lane < w) ? x[i] : (T)0;
 }
 
-// Solve the kb x kb diagonal block in place: L Y = Y (TRANS = 0) or
-// L^T X = X (TRANS = 1) for nrhs <= 16 right-hand sides (Y row-major, ld ldy).
-// 32-row chunks: the chunk is updated from the already solved rows, then
-// multiplied by its precomputed inverse (Inv: the block's chunks, 32 x 32 each).
-template <typename T, int TRANS>
-__global__ void __launch_bounds__(512) k_trsv_diag(const double* L, int64_t ldl, int kb, T* Y,
-                                                   int64_t ldy, int nrhs, const T* Inv) {
-    extern __shared__ __align__(16) unsigned char sb[];
-    T* y = (T*)sb;                        // kb x MAXRHS
-    T* Lr = y + (size_t)kb * MAXRHS;      // 32 x (kb + 1): the chunk's rows (or columns) of L
-    const int ldr = kb + 1;
-    __shared__ T Ic[32][33];
-    __shared__ T tmp[32][MAXRHS];
-    const int t = threadIdx.x;
-    for (int e = t; e < kb * nrhs; e += blockDim.x) {
-        int i = e / nrhs, r = e % nrhs;
-        y[i * MAXRHS + r] = Y[(int64_t)i * ldy + r];
-    }
-    __syncthreads();
-    const int nch = (kb + 31) / 32;
-    const int q = t >> 4, r = t & 15;     // this thread's (row in chunk, rhs)
-    for (int ci = 0; ci < nch; ++ci) {
-        const int c = TRANS ? nch - 1 - ci : ci;
-        const int c0 = c * 32, c1 = (c0 + 32 < kb) ? c0 + 32 : kb, w = c1 - c0;
-        // the chunk's inverse (transposed for the backward solve)
-        for (int e = t; e < 32 * 32; e += blockDim.x) {
-            int a = e >> 5, b = e & 31;
-            Ic[a][b] = TRANS ? Inv[(int64_t)(c0 + b) * 32 + a] : Inv[(int64_t)(c0 + a) * 32 + b];
-        }
-        // stage the part of L that couples the chunk to the solved rows in one
-        // coalesced pass: rows c0..c1 x cols 0..c0 (forward), or rows c1..kb x
-        // cols c0..c1 stored transposed (backward)
-        if (!TRANS) {
-            for (int e = t; e < w * c0; e += blockDim.x) {
-                int a = e / c0, b = e % c0;
-                Lr[a * ldr + b] = (T)L[(int64_t)(c0 + a) * ldl + b];
-            }
-        } else {
-            const int h = kb - c1;
-            for (int e = t; e < h * 32; e += blockDim.x) {
-                int b = e >> 5, a = e & 31;
-                if (a < w) Lr[a * ldr + b] = (T)L[(int64_t)(c1 + b) * ldl + c0 + a];
-            }
-        }
-        __syncthreads();
-        // update the chunk from the solved rows
-        if (q < w && r < nrhs) {
-            const int i = c0 + q;
-            T acc = 0;
-            if (!TRANS) {
-                for (int p = 0; p < c0; ++p) acc += Lr[q * ldr + p] * y[p * MAXRHS + r];
-            } else {
-                for (int p = c1; p < kb; ++p) acc += Lr[q * ldr + (p - c1)] * y[p * MAXRHS + r];
-            }
-            tmp[q][r] = y[i * MAXRHS + r] - acc;
-        }
-        __syncthreads();
-        if (q < w && r < nrhs) {
-            T v = 0;
-            for (int p = 0; p < w; ++p) v += Ic[q][p] * tmp[p][r];
-            y[(c0 + q) * MAXRHS + r] = v;
-        }
-        __syncthreads();
-    }
-    for (int e = t; e < kb * nrhs; e += blockDim.x) {
-        int i = e / nrhs, rr = e % nrhs;
-        Y[(int64_t)i * ldy + rr] = y[i * MAXRHS + rr];
-    }
+// One triangular sweep in a single launch: L Y = Y (TRANS = 0) or L^T X = X
+// (TRANS = 1) for nrhs <= 16 right-hand sides, Y row-major (ld ldy), solved in
+// place.  Rows are cut into 64-row blocks.  CTAs take blocks from a ticket
+// counter in solve order (first to last for L, last to first for L^T); the CTA
+// of block i streams the 64 x 64 tiles of L that couple it to the blocks solved
+// before it, waiting on each block's ready flag, then solves its diagonal block
+// with the precomputed 32 x 32 chunk inverses and publishes its rows and flag.
+// A CTA only waits on blocks whose tickets were handed out before its own, so
+// the sweep completes whatever the number of resident CTAs.  Every wait gives
+// up after one second: it sets sync[2] and the remaining CTAs drain.
+// sync: [0] / [1] tickets (L, L^T), [2] error, [4, 4 + NB) flags of the L
+// sweep, [4 + NB, 4 + 2 NB) flags of the L^T sweep; zeroed before the solve.
+constexpr int RB = 64;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Rows update with a solved block: Y[i][r] -= sum_p Lop[i][p] Ys[p][r], i < M,
-// p < K; Lop[i][p] = L[i][p] (TRANS = 0) or L[p][i] (TRANS = 1).
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+size_t sweep_smem_bytes() {
+    return sizeof(T) * ((size_t)RB * (RB + 1) + 2 * (size_t)RB * MAXRHS + 2 * 32 * 33);
+}
+
 template <typename T, int TRANS>
-__global__ void __launch_bounds__(256) k_trsv_update(const double* L, int64_t ldl, int64_t M,
-                                                     int K, const T* Ys, int64_t ldys, T* Y,
-                                                     int64_t ldy, int nrhs) {
-    __shared__ T As[64][65];
-    __shared__ T Bs[64][MAXRHS];
-    const int t = threadIdx.x;
-    const int64_t i0 = blockIdx.x * 64;
-    const int row = t & 63, cg = t >> 6;   // 4 column groups
-    T acc[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < K; k0 += 64) {
-        for (int e = t; e < 64 * 64; e += 256) {
-            int a = e >> 6, b = e & 63;   // coalesced along b
-            if (!TRANS) {   // As[p][i] = L[i0+a][k0+b] stored as As[b][a]
-                int64_t i = i0 + a; int p = k0 + b;
-                As[b][a] = (i < M && p < K) ? (T)L[i * ldl + p] : (T)0;
-            } else {        // As[p][i] = L[k0+a][i0+b]
-                int p = k0 + a; int64_t i = i0 + b;
-                As[a][b] = (i < M && p < K) ? (T)L[(int64_t)p * ldl + i] : (T)0;
-            }
-        }
-        for (int e = t; e < 64 * MAXRHS; e += 256) {
-            int p = e / MAXRHS, r = e % MAXRHS;
-            Bs[p][r] = (k0 + p < K && r < nrhs) ? Ys[(int64_t)(k0 + p) * ldys + r] : (T)0;
+__global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict__ L, int64_t ldl,
+                                                    int64_t n, T* Y, int64_t ldy, int nrhs,
+                                                    const T* __restrict__ Inv, unsigned* sync) {
+    extern __shared__ __align__(16) unsigned char sb[];
+    T* sA = (T*)sb;                         // tile of L^T (or L): sA[p * (RB + 1) + a]
+    T* sY = sA + RB * (RB + 1);             // solved rows of the tile / rhs of the diagonal
+    T* sX = sY + RB * MAXRHS;               // solution of the diagonal block
+    T* sI = sX + RB * MAXRHS;               // two 32 x 32 chunk inverses, ld 33
+    __shared__ int s_blk, s_ok, s_known;
+    const int NB = (int)((n + RB - 1) / RB);
+    const int nchunk = (int)((n + 31) / 32);
+    unsigned* ticket = sync + TRANS;
+    unsigned* err = sync + 2;
+    unsigned* flag = sync + 4 + (TRANS ? NB : 0);
+    const int t = threadIdx.x, row = t & 63, cg = t >> 6;
+    for (;;) {
+        if (t == 0) {
+            const unsigned tk = atomicAdd(ticket, 1u);
+            const bool live = *(volatile unsigned*)err == 0u;
+            s_blk = (live && tk < (unsigned)NB) ? (TRANS ? NB - 1 - (int)tk : (int)tk) : -1;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int p = 0; p < 64; ++p) {
-            T a = As[p][row];
+        const int bi = s_blk;
+        if (bi < 0) return;
+        const int64_t i0 = (int64_t)bi * RB;
+        const int nj = TRANS ? NB - 1 - bi : bi;     // coupling tiles, in solve order
+        auto jblk = [&](int k) { return TRANS ? NB - 1 - k : k; };
+        // this thread's 16 elements of tile (bi, jb) of the operator (jb == bi: diagonal)
+        auto load_tile = [&](int jb, double (&v)[16]) {
+            const int64_t j0 = (int64_t)jb * RB;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] += a * Bs[p][cg + 4 * u];
-        }
-        __syncthreads();
-    }
-    const int64_t i = i0 + row;
-    if (i < M)
+            for (int q = 0; q < 16; ++q) {
+                const int e = t + 256 * q, a = e >> 6, b = e & 63;
+                const int64_t gr = TRANS ? j0 + a : i0 + a, gc = TRANS ? i0 + b : j0 + b;
+                v[q] = (gr < n && gc < n) ? L[gr * ldl + gc] : 0.0;
+            }
+        };
+        auto store_tile = [&](const double (&v)[16]) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = t + 256 * q, a = e >> 6, b = e & 63;
+                if (TRANS) sA[a * (RB + 1) + b] = (T)v[q];    // sA[p][a] = L[j0 + p][i0 + a]
+                else sA[b * (RB + 1) + a] = (T)v[q];          // sA[p][a] = L[i0 + a][j0 + p]
+            }
+        };
+        auto load_y = [&](int jb, T (&v)[4]) {
+            const int64_t j0 = (int64_t)jb * RB;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = t + 256 * q, p = e >> 4, r = e & 15;
+                v[q] = (j0 + p < n && r < nrhs) ? __ldcg(&Y[(j0 + p) * ldy + r]) : (T)0;
+            }
+        };
+        auto store_y = [&](const T (&v)[4]) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sY[t + 256 * q] = v[q];
+        };
+        T acc[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            int r = cg + 4 * u;
-            if (r < nrhs) Y[i * ldy + r] -= acc[u];
+            const int64_t i = i0 + row;
+            const int r = cg + 4 * u;
+            acc[u] = (i < n && r < nrhs) ? __ldcg(&Y[i * ldy + r]) : (T)0;
         }
+        if (t == 0) s_known = (nj > 0 && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) ? nj - 1 : -1;
+        __syncthreads();
+        int known = s_known;
+        double preL[16];
+        T preY[4];
+        load_tile(nj > 0 ? jblk(0) : bi, preL);
+        bool hy = false;
+        if (nj > 0 && known >= 0) { load_y(jblk(0), preY); hy = true; }
+        for (int k = 0; k < nj; ++k) {
+            store_tile(preL);
+            if (hy) store_y(preY);
+            bool next_y = false;
+            if (k + 1 < nj) {
+                load_tile(jblk(k + 1), preL);
+                if (k + 1 <= known) { load_y(jblk(k + 1), preY); next_y = true; }
+            } else {
+                load_tile(bi, preL);                  // the diagonal tile comes next
+            }
+            if (!hy) {
+                if (t == 0) {
+                    int ok = 1;
+                    const unsigned long long t_start = global_ns();
+                    while (ld_acquire_u32(&flag[jblk(k)]) == 0u) {
+                        if (*(volatile unsigned*)err != 0u) { ok = 0; break; }
+                        if (global_ns() - t_start > 1000000000ull) {
+                            atomicExch(err, 1u);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    int kn = k;
+                    if (ok && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) kn = nj - 1;
+                    s_known = kn;
+                    s_ok = ok;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                known = s_known;
+                T v[4];
+                load_y(jblk(k), v);
+                store_y(v);
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int p = 0; p < RB; ++p) {
+                const T a = sA[p * (RB + 1) + row];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] -= a * sY[p * MAXRHS + cg + 4 * u];
+            }
+            __syncthreads();
+            hy = next_y;
+        }
+        // diagonal block
+        store_tile(preL);
+        for (int e = t; e < 2 * 32 * 32; e += 256) {
+            const int c = e >> 10, a = (e >> 5) & 31, b = e & 31;
+            const int ci = (int)(i0 / 32) + c;
+            sI[(c * 32 + a) * 33 + b] = (ci < nchunk) ? Inv[((int64_t)ci * 32 + a) * 32 + b] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sY[row * MAXRHS + cg + 4 * u] = acc[u];
+        __syncthreads();
+        const int q = t >> 3, r0 = t & 7;
+        // first chunk (rows 0..31 for L, 32..63 for L^T)
+        {
+            const int c = TRANS ? 1 : 0, o = 32 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + 8 * h;
+                T v = 0;
+                for (int p = 0; p < 32; ++p) {
+                    const T m = TRANS ? sI[(c * 32 + p) * 33 + q] : sI[(c * 32 + q) * 33 + p];
+                    v += m * sY[(o + p) * MAXRHS + r];
+                }
+                sX[(o + q) * MAXRHS + r] = v;
+            }
+        }
+        __syncthreads();
+        // couple the second chunk to the first
+        {
+            const int o2 = TRANS ? 0 : 32, o1 = TRANS ? 32 : 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + 8 * h;
+                T v = 0;
+                for (int p = 0; p < 32; ++p) {
+                    // L: L[32 + q][p] = sA[p][32 + q];  L^T: L[32 + p][q] = sA[32 + p][q]
+                    const T m = sA[(o1 + p) * (RB + 1) + o2 + q];
+                    v += m * sX[(o1 + p) * MAXRHS + r];
+                }
+                sY[(o2 + q) * MAXRHS + r] -= v;
+            }
+        }
+        __syncthreads();
+        {
+            const int c = TRANS ? 0 : 1, o = 32 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + 8 * h;
+                T v = 0;
+                for (int p = 0; p < 32; ++p) {
+                    const T m = TRANS ? sI[(c * 32 + p) * 33 + q] : sI[(c * 32 + q) * 33 + p];
+                    v += m * sY[(o + p) * MAXRHS + r];
+                }
+                sX[(o + q) * MAXRHS + r] = v;
+            }
+        }
+        __syncthreads();
+        for (int e = t; e < RB * MAXRHS; e += 256) {
+            const int a = e >> 4, r = e & 15;
+            if (i0 + a < n && r < nrhs) Y[(i0 + a) * ldy + r] = sX[e];
+        }
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();
+            st_release_u32(&flag[bi], 1u);
+        }
+    }
 }
 
 template <typename S, typename D>
@@ -292,47 +393,41 @@ template <typename T>
 cudaError_t set_attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
-    const int bytes = (512 * MAXRHS + 32 * 513) * (int)sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_trsv_diag<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
+    const int bytes = (int)sweep_smem_bytes<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_trsv_sweep<T, 0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_trsv_diag<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_trsv_sweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
+size_t inv_region(int64_t n, bool f64) {
+    const size_t b = (size_t)((n + 31) / 32) * 32 * 32 * (f64 ? sizeof(double) : sizeof(float));
+    return (b + 255) / 256 * 256;
+}
+
+size_t sync_words(int64_t n) { return 4 + 2 * (size_t)((n + RB - 1) / RB); }
+
 template <typename T>
-cudaError_t potrs_t(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl, T* Y,
-                    int64_t ldy, T* Inv, cudaStream_t s) {
+cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, T* Y, int64_t ldy, T* Inv,
+                    cudaStream_t s) {
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
     cudaError_t e = set_attrs<T>();
     if (e != cudaSuccess) return e;
-    const int64_t N = (n + nb - 1) / nb;
-    const size_t smem = (size_t)(nb * MAXRHS + 32 * (nb + 1)) * sizeof(T);
+    unsigned* sync = (unsigned*)((char*)Inv + inv_region(n, sizeof(T) == sizeof(double)));
+    e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * sync_words(n), s);
+    if (e != cudaSuccess) return e;
     k_chunk_inv<T><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(L, ldl, n, Inv);
     note_launch();
-    for (int64_t k = 0; k < N; ++k) {   // L Y = B
-        const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0, T0 = K0 + kb;
-        k_trsv_diag<T, 0><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy,
-                                               nrhs, Inv + K0 * 32);
-        note_launch();
-        if (T0 < n) {
-            k_trsv_update<T, 0><<<(unsigned)((n - T0 + 63) / 64), 256, 0, s>>>(
-                L + T0 * ldl + K0, ldl, n - T0, (int)kb, Y + K0 * ldy, ldy, Y + T0 * ldy, ldy, nrhs);
-            note_launch();
-        }
-    }
-    for (int64_t k = N - 1; k >= 0; --k) {   // L^T X = Y
-        const int64_t K0 = k * nb, kb = (K0 + nb < n) ? nb : n - K0;
-        k_trsv_diag<T, 1><<<1, 512, smem, s>>>(L + K0 * ldl + K0, ldl, (int)kb, Y + K0 * ldy, ldy,
-                                               nrhs, Inv + K0 * 32);
-        note_launch();
-        if (K0 > 0) {
-            k_trsv_update<T, 1><<<(unsigned)((K0 + 63) / 64), 256, 0, s>>>(
-                L + K0 * ldl, ldl, K0, (int)kb, Y + K0 * ldy, ldy, Y, ldy, nrhs);
-            note_launch();
-        }
-    }
+    const int NB = (int)((n + RB - 1) / RB);
+    const unsigned grid = (unsigned)std::min<int64_t>(NB, 2 * (int64_t)num_sms());
+    const size_t smem = sweep_smem_bytes<T>();
+    k_trsv_sweep<T, 0><<<grid, 256, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+    note_launch();
+    k_trsv_sweep<T, 1><<<grid, 256, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -342,16 +437,26 @@ int potrs_max_rhs() { return MAXRHS; }
 
 cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
                              double* B, int64_t ldb, double* inv, cudaStream_t s) {
-    return potrs_t<double>(n, nrhs, nb, L, ldl, B, ldb, inv, s);
+    (void)nb;
+    return potrs_t<double>(n, nrhs, L, ldl, B, ldb, inv, s);
 }
 
 cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
                              float* B, int64_t ldb, float* inv, cudaStream_t s) {
-    return potrs_t<float>(n, nrhs, nb, L, ldl, B, ldb, inv, s);
+    (void)nb;
+    return potrs_t<float>(n, nrhs, L, ldl, B, ldb, inv, s);
+}
+
+int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_t* ce) {
+    unsigned h = 0;
+    const unsigned* sync = (const unsigned*)((const char*)inv + inv_region(n, f64));
+    *ce = cudaMemcpyAsync(&h, sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (*ce == cudaSuccess) *ce = cudaStreamSynchronize(s);
+    return (int)h;
 }
 
 size_t potrs_inv_bytes(int64_t n, bool f64) {
-    return (size_t)((n + 31) / 32) * 32 * 32 * (f64 ? sizeof(double) : sizeof(float));
+    return inv_region(n, f64) + sizeof(unsigned) * sync_words(n);
 }
 
 cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
