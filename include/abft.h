@@ -103,6 +103,9 @@ typedef struct {
     int32_t ir_iters;          /* iterative refinement iterations (posv_ir)           */
     int32_t reserved;
     double backward_err;       /* final normwise backward error (posv_ir)             */
+    int32_t gmres_iters;       /* GMRES iterations over all refinement steps          */
+    int32_t attempts;          /* factorizations tried (posv_gmres_ir shift retries)  */
+    double shift;              /* diagonal shift of the factored matrix               */
 } abft_report;
 
 #define ABFT_OK 0
@@ -220,6 +223,40 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
                  int64_t lda, double* L, int64_t ldl, const double* B, int64_t ldb, double* X,
                  int64_t ldx, double tol, int32_t maxit, const abft_fault* faults, int32_t nfaults,
                  double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * abft_posv_gmres_ir -- solve A X = B for SPD A by GMRES-based iterative
+ * refinement (Carson and Higham, SISC 2017 / 2018) preconditioned by an ABFT
+ * Cholesky factor in the given dtype, with the diagonal scaling and shift of
+ * Higham and Pranesh (SISC 2021) for low-precision factorizations.  Not in
+ * the paper: the precision form added on top of it, for ill-conditioned A.
+ *   S = diag(s_i), s_i = 2^-t_i, t_i = e_i / 2 rounded toward zero, with
+ *       a_ii = f 2^e_i, f in [1/2, 1) (scale != 0; else S = I), so S A S is
+ *       formed exactly and its diagonal lies in [1/4, 2);
+ *   L := lower(S A S + delta I) (the upper triangle of L is not written),
+ *       abft_potrf(L) in dtype; with shift < 0 a
+ *       non-positive pivot restarts the factorization with delta = u_f, then
+ *       4 delta (at most 8 attempts; u_f = 2^-8 BF16, 2^-11 FP16, 2^-53 FP64);
+ *       shift >= 0 fixes delta = shift;
+ *   M^{-1} v = S L^{-T} L^{-1} S v (FP64 substitution if precond_f64, else FP32);
+ *   X = M^{-1} B; repeat: R = B - A X in FP64, eta as abft_posv_ir; stop at
+ *       eta <= tol or after maxit refinement steps; else run GMRES (left
+ *       preconditioned, Arnoldi with classical Gram-Schmidt applied twice,
+ *       Givens rotations, FP64) on M^{-1} A D = M^{-1} R from D = 0 until its
+ *       residual falls to inner_tol times the initial one for every
+ *       right-hand side or m iterations, and X += D.
+ *   m          GMRES iterations per refinement step, 1 .. 64
+ * rep (optional) receives the factorization report plus ir_iters, gmres_iters,
+ * attempts, shift (delta) and backward_err.  The call synchronizes the stream
+ * once per GMRES iteration.  Returns as abft_posv_ir; argument errors as
+ * abft_posv_ir plus -16 m; -17 inner_tol; -18 shift NaN; -19 faults.
+ */
+int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mode,
+                       const double* A, int64_t lda, double* L, int64_t ldl, const double* B,
+                       int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit, int32_t m,
+                       double inner_tol, double shift, int32_t scale, int32_t precond_f64,
+                       const abft_fault* faults, int32_t nfaults, double tau_scale,
+                       abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
  * Reverse mode (adjoints) of potrf, potrs and logdet -- not in the paper: the

@@ -32,7 +32,9 @@ class Report(ctypes.Structure):
                 ("nloc", ctypes.c_int32), ("info", ctypes.c_int32),
                 ("loc", Fault * MAX_LOC), ("max_ratio", ctypes.c_double),
                 ("tau", ctypes.c_double), ("ir_iters", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double)]
+                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double),
+                ("gmres_iters", ctypes.c_int32), ("attempts", ctypes.c_int32),
+                ("shift", ctypes.c_double)]
 
 
 class AbftError(RuntimeError):
@@ -57,6 +59,10 @@ _SIGNATURES = {
     "abft_posv_ir": [_i64, _i64, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                      _dbl, _i32, ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp,
                      _sz, _vp],
+    "abft_posv_gmres_ir": [_i64, _i64, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                           _i64, _dbl, _i32, _i32, _dbl, _dbl, _i32, _i32,
+                           ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz,
+                           _vp],
     "abft_geqrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
     "abft_getrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
@@ -122,6 +128,7 @@ def report_dict(r):
         "uncorrectable": r.uncorrectable, "checksum_repaired": r.checksum_repaired,
         "info": r.info, "max_ratio": r.max_ratio, "tau": r.tau,
         "ir_iters": r.ir_iters, "backward_err": r.backward_err,
+        "gmres_iters": r.gmres_iters, "attempts": r.attempts, "shift": r.shift,
         "loc": [(r.loc[i].step, r.loc[i].kind, r.loc[i].row, r.loc[i].col, r.loc[i].delta)
                 for i in range(r.nloc)],
     }
@@ -301,6 +308,40 @@ def posv_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=50, faul
                          B.stride(0), ctypes.c_void_p(X.data_ptr()), X.stride(0), tol, maxit, fa,
                          nf, tau_scale, ctypes.byref(rep), ctypes.c_void_p(ws.data_ptr()),
                          ctypes.byref(size), _stream(stream))
+    if check and rc < 0 and rc != ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    return rc, X, L, report_dict(rep)
+
+
+def posv_gmres_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=20, m=30,
+                  inner_tol=1e-6, shift=-1.0, scale=True, precond_f64=False, faults=(),
+                  tau_scale=1.0, L=None, X=None, workspace=None, stream=None, check=True):
+    """Solve A X = B (A SPD, lower triangle read) by GMRES-based iterative
+    refinement preconditioned by an ABFT Cholesky of the scaled, shifted matrix
+    in `dtype` (shift < 0: automatic).  Returns (code, X, L, report)."""
+    _check_matrix(A)
+    _check_matrix(B, "B")
+    n, nrhs = B.shape
+    L = torch.empty_like(A) if L is None else L
+    X = torch.empty_like(B) if X is None else X
+    Lb = lib()
+    fa, nf = _faults(faults)
+    need = ctypes.c_size_t(0)
+    rc = Lb.abft_posv_gmres_ir(n, nrhs, nb, dtype, mode, None, max(1, A.stride(0)), None,
+                               max(1, L.stride(0)), None, max(1, B.stride(0)), None,
+                               max(1, X.stride(0)), tol, maxit, m, inner_tol, shift, int(scale),
+                               int(precond_f64), fa, nf, tau_scale, None, None,
+                               ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    rep = Report()
+    size = ctypes.c_size_t(ws.numel())
+    rc = Lb.abft_posv_gmres_ir(n, nrhs, nb, dtype, mode, _ptr(A), A.stride(0), _ptr(L),
+                               L.stride(0), _ptr(B), B.stride(0), _ptr(X), X.stride(0), tol,
+                               maxit, m, inner_tol, shift, int(scale), int(precond_f64), fa, nf,
+                               tau_scale, ctypes.byref(rep), _ptr(ws), ctypes.byref(size),
+                               _stream(stream))
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, X, L, report_dict(rep)

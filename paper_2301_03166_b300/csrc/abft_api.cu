@@ -747,6 +747,33 @@ IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
     return w;
 }
 
+constexpr int kGmresMax = 64;       // largest GMRES cycle (basis vectors)
+constexpr int kGmresAttempts = 8;   // factorizations tried with growing shift
+
+struct GmWs {
+    size_t sc, V, W, part, hnew, h2, H, cs, sn, g, res, y, total;
+};
+
+GmWs gm_ws(int64_t n, int m, size_t off) {
+    GmWs w{};
+    const size_t d = sizeof(double);
+    const size_t blk = d * (size_t)n * 16;
+    w.sc = off; off = align_up(off + d * (size_t)std::max<int64_t>(n, 1));
+    w.V = off; off = align_up(off + blk * (size_t)(m + 1));
+    w.W = off; off = align_up(off + blk);
+    w.part = off; off = align_up(off + d * 16 * (size_t)(m + 2) * (size_t)gmres_dot_blocks(n));
+    w.hnew = off; off = align_up(off + d * 16 * (size_t)(m + 2));
+    w.h2 = off; off = align_up(off + d * 16 * (size_t)(m + 2));
+    w.H = off; off = align_up(off + d * 16 * (size_t)m * (size_t)(m + 1));
+    w.cs = off; off = align_up(off + d * 16 * (size_t)m);
+    w.sn = off; off = align_up(off + d * 16 * (size_t)m);
+    w.g = off; off = align_up(off + d * 16 * (size_t)(m + 1));
+    w.res = off; off = align_up(off + d * 16);
+    w.y = off; off = align_up(off + d * 16 * (size_t)m);
+    w.total = off;
+    return w;
+}
+
 }  // namespace
 
 extern "C" {
@@ -875,6 +902,191 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     return factor_rc;
 }
 
+
+int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mode,
+                       const double* A, int64_t lda, double* L, int64_t ldl, const double* B,
+                       int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit, int32_t m,
+                       double inner_tol, double shift, int32_t scale, int32_t precond_f64,
+                       const abft_fault* faults, int32_t nfaults, double tau_scale,
+                       abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
+    if (dtype < 0 || dtype > 3 || dtype == ABFT_F32) return dtype == ABFT_F32 ? ABFT_ERR_UNSUPPORTED : -4;
+    if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -5;
+    const bool needp = ws != nullptr && n > 0;
+    if (needp && A == nullptr) return -6;
+    if (lda < std::max<int64_t>(1, n)) return -7;
+    if (needp && L == nullptr) return -8;
+    if (ldl < std::max<int64_t>(1, n)) return -9;
+    if (needp && nrhs > 0 && B == nullptr) return -10;
+    if (ldb < std::max<int64_t>(1, nrhs)) return -11;
+    if (needp && nrhs > 0 && X == nullptr) return -12;
+    if (ldx < std::max<int64_t>(1, nrhs)) return -13;
+    if (!(tol >= 0.0)) return -14;
+    if (maxit < 0) return -15;
+    if (m < 1 || m > kGmresMax) return -16;
+    if (!(inner_tol >= 0.0)) return -17;
+    if (!(shift >= 0.0) && !(shift < 0.0)) return -18;   // NaN
+    if (ws_bytes == nullptr) return -22;
+    const IrWs w = ir_ws(n, nb, mode, dtype);
+    const GmWs gw = gm_ws(n, m, w.total);
+    size_t pws = 0;
+    int rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, nullptr, nullptr,
+                        &pws, nullptr);
+    if (rc != ABFT_OK) return rc == -7 ? -19 : rc;
+    if (ws == nullptr) {
+        *ws_bytes = gw.total;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < gw.total) return -22;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    abft_report prep;
+    abft_report* pr = rep ? rep : &prep;
+    double* sc = (double*)(base + gw.sc);
+    // scaling (powers of two, exact) and the shifted low-precision factorization;
+    // a non-positive pivot restarts it with a larger shift (automatic when shift < 0)
+    const double ulow = dtype == ABFT_MIXED_F16 ? 0x1p-11 : (dtype == ABFT_F64 ? 0x1p-53 : 0x1p-8);
+    double delta = shift < 0.0 ? 0.0 : shift;
+    int32_t attempts = 0;
+    ABFT_CUDA_TRY(launch_gm_diag_scale(A, lda, n, sc, scale ? 1 : 0, s));
+    for (;;) {
+        ++attempts;
+        ABFT_CUDA_TRY(launch_gm_scaled_copy(A, lda, sc, delta, L, ldl, n, s));
+        size_t have = pws;
+        rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, pr, base + w.chol,
+                        &have, stream);
+        if (rc > 0 && shift < 0.0 && attempts < kGmresAttempts) {
+            delta = delta > 0.0 ? 4.0 * delta : ulow;
+            continue;
+        }
+        break;
+    }
+    if (rc > 0 || rc == ABFT_ERR_CUDA || rc == ABFT_ERR_TIMEOUT) {
+        pr->attempts = attempts;
+        pr->shift = delta;
+        return rc;
+    }
+    const int factor_rc = rc;
+    pr->attempts = attempts;
+    pr->shift = delta;
+    if (n == 0 || nrhs == 0) return factor_rc;
+    char* sws = base + w.solve;
+    void* inv = sws;
+    float* Yf = (float*)(sws + align_up(potrs_inv_bytes(n, true)));
+    double* R = (double*)(base + w.R);
+    double* P = (double*)(base + w.P);
+    double* rs = (double*)(base + w.rs);
+    unsigned long long* nrm = (unsigned long long*)(base + w.norms);
+    unsigned long long *anorm = nrm, *bmax = nrm + 1, *rmax = nrm + 17, *xmax = nrm + 33;
+    double* eta_d = (double*)(base + w.eta);
+    double* V = (double*)(base + gw.V);
+    const int64_t vstride = n * 16;
+    double* Wb = (double*)(base + gw.W);
+    double* part = (double*)(base + gw.part);
+    double* hnew = (double*)(base + gw.hnew);
+    double* h2 = (double*)(base + gw.h2);
+    double* H = (double*)(base + gw.H);
+    double* cs = (double*)(base + gw.cs);
+    double* sn = (double*)(base + gw.sn);
+    double* g = (double*)(base + gw.g);
+    double* res = (double*)(base + gw.res);
+    double* yv = (double*)(base + gw.y);
+    const bool f64 = precond_f64 != 0;
+    // z := M^{-1} z = S L^{-T} L^{-1} S z, in place on an n x 16 block
+    auto precond = [&](double* z) -> int {
+        ABFT_CUDA_TRY(launch_gm_rowscale(sc, z, z, n, s));
+        if (f64) {
+            ABFT_CUDA_TRY(launch_potrs_f64(n, 16, nb, L, ldl, z, 16, (double*)inv, s));
+        } else {
+            ABFT_CUDA_TRY(launch_copy_d2f(z, 16, Yf, 16, n, 16, s));
+            ABFT_CUDA_TRY(launch_potrs_f32(n, 16, nb, L, ldl, Yf, 16, (float*)inv, s));
+            ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, z, 16, n, 16, s));
+        }
+        ABFT_CUDA_TRY(launch_gm_rowscale(sc, z, z, n, s));
+        return ABFT_OK;
+    };
+    auto solve_err = [&]() -> int {
+        cudaError_t ce = cudaSuccess;
+        const int e = potrs_error(inv, n, f64, s, &ce);
+        ABFT_CUDA_TRY(ce);
+        return e ? ABFT_ERR_TIMEOUT : ABFT_OK;
+    };
+    int32_t iters_max = 0, gm_total = 0;
+    double eta_max = 0.0;
+    std::vector<double> hres(16), beta(16);
+    for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
+        const int nr = (int)std::min<int64_t>(16, nrhs - r0);
+        ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
+        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, s));
+        timing_mark(PH_SOLVE, 1, s);
+        // X0 = M^{-1} B (the padding columns stay zero)
+        ABFT_CUDA_TRY(cudaMemsetAsync(Wb, 0, sizeof(double) * (size_t)n * 16, s));
+        ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, Wb, 16, n, nr, s));
+        rc = precond(Wb);
+        if (rc != ABFT_OK) return rc;
+        ABFT_CUDA_TRY(launch_copy_d2d(Wb, 16, X + r0, ldx, n, nr, s));
+        int32_t it = 0;
+        double eta = 0.0;
+        for (;; ++it) {
+            ABFT_CUDA_TRY(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long) * 32, s));
+            ABFT_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * 16, s));
+            ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P, kSplit,
+                                          rmax, xmax, s));
+            ABFT_CUDA_TRY(launch_eta(rmax, xmax, anorm, bmax, nr, eta_d, s));
+            ABFT_CUDA_TRY(cudaMemcpyAsync(&eta, eta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+            rc = solve_err();
+            if (rc != ABFT_OK) return rc;
+            if (eta <= tol || it >= maxit || !(eta == eta)) break;
+            // GMRES on M^{-1} A d = M^{-1} R from d = 0
+            rc = precond(R);
+            if (rc != ABFT_OK) return rc;
+            ABFT_CUDA_TRY(launch_gm_dots(R, 0, 1, R, n, part, hnew, 0, s));
+            ABFT_CUDA_TRY(launch_gm_init_g(hnew, g, m, res, s));
+            ABFT_CUDA_TRY(launch_gm_scale(R, hnew, V, n, s));
+            ABFT_CUDA_TRY(cudaMemcpyAsync(beta.data(), res, sizeof(double) * 16,
+                                          cudaMemcpyDeviceToHost, s));
+            ABFT_CUDA_TRY(cudaStreamSynchronize(s));
+            int k = 0;
+            for (int j = 0; j < m; ++j) {
+                double* Vj = V + (int64_t)j * vstride;
+                ABFT_CUDA_TRY(launch_symv(A, lda, n, Vj, Wb, P, kSplit, s));
+                rc = precond(Wb);
+                if (rc != ABFT_OK) return rc;
+                // classical Gram-Schmidt, twice
+                ABFT_CUDA_TRY(launch_gm_dots(V, vstride, j + 1, Wb, n, part, hnew, 0, s));
+                ABFT_CUDA_TRY(launch_gm_subtract(V, vstride, j + 1, hnew, Wb, n, s));
+                ABFT_CUDA_TRY(launch_gm_dots(V, vstride, j + 1, Wb, n, part, h2, 0, s));
+                ABFT_CUDA_TRY(launch_gm_subtract(V, vstride, j + 1, h2, Wb, n, s));
+                ABFT_CUDA_TRY(launch_add_f64(hnew, 16, h2, 16, j + 1, 16, s));
+                ABFT_CUDA_TRY(launch_gm_dots(Wb, 0, 1, Wb, n, part, hnew + (int64_t)(j + 1) * 16, 0, s));
+                ABFT_CUDA_TRY(launch_gm_givens(H, m, hnew, cs, sn, g, j, res, s));
+                ABFT_CUDA_TRY(launch_gm_scale(Wb, hnew + (int64_t)(j + 1) * 16,
+                                              V + (int64_t)(j + 1) * vstride, n, s));
+                ABFT_CUDA_TRY(cudaMemcpyAsync(hres.data(), res, sizeof(double) * 16,
+                                              cudaMemcpyDeviceToHost, s));
+                rc = solve_err();
+                if (rc != ABFT_OK) return rc;
+                k = j + 1;
+                double worst = 0.0;
+                for (int r = 0; r < nr; ++r)
+                    if (beta[r] > 0.0) worst = std::max(worst, hres[r] / beta[r]);
+                if (!(worst > inner_tol)) break;
+            }
+            ABFT_CUDA_TRY(launch_gm_update(H, m, g, k, yv, V, vstride, X + r0, ldx, nr, n, s));
+            gm_total += k;
+        }
+        timing_mark(PH_SOLVE, 0, s);
+        iters_max = std::max(iters_max, it);
+        eta_max = std::max(eta_max, eta);
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    pr->ir_iters = iters_max;
+    pr->gmres_iters = gm_total;
+    pr->backward_err = eta_max;
+    return factor_rc;
+}
 }  // extern "C"
 
 namespace {

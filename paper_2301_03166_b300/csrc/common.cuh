@@ -248,6 +248,10 @@ cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const doubl
                             const double* B, int64_t ldb, int nrhs, double* R, int64_t ldr,
                             double* P, int nsplit, unsigned long long* rmax,
                             unsigned long long* xmax, cudaStream_t s);
+// Y = A X for symmetric A (lower triangle read), X / Y n x 16 (ld 16), split-K
+// partials in P (nsplit x n x 16).
+cudaError_t launch_symv(const double* A, int64_t lda, int64_t n, const double* X, double* Y,
+                        double* P, int nsplit, cudaStream_t s);
 cudaError_t launch_inf_norms(const double* A, int64_t lda, int64_t n, const double* B, int64_t ldb,
                              int nrhs, double* rs, unsigned long long* anorm,
                              unsigned long long* bmax, cudaStream_t s);
@@ -296,6 +300,28 @@ enum { PH_PD = 0, PH_PU = 1, PH_TMU = 2, PH_VERIFY = 3, PH_OTHER = 4, PH_SOLVE =
 bool timing_on();
 void timing_mark(int phase, int begin, cudaStream_t s);
 cudaError_t timing_collect(cudaStream_t s);
+
+// GMRES-IR pieces (k_gmres.cu); vectors are n x 16 blocks (ld 16), basis
+// vector i at V + i * vstride.
+int gmres_dot_blocks(int64_t n);
+cudaError_t launch_gm_dots(const double* V, int64_t vstride, int nv, const double* W, int64_t n,
+                           double* part, double* h, int acc, cudaStream_t s);
+cudaError_t launch_gm_subtract(const double* V, int64_t vstride, int nv, const double* h,
+                               double* W, int64_t n, cudaStream_t s);
+cudaError_t launch_gm_scale(const double* x, const double* nrm2, double* out, int64_t n,
+                            cudaStream_t s);
+cudaError_t launch_gm_rowscale(const double* sc, const double* x, double* y, int64_t n,
+                               cudaStream_t s);
+cudaError_t launch_gm_givens(double* H, int m, const double* hnew, double* cs, double* sn,
+                             double* g, int j, double* res, cudaStream_t s);
+cudaError_t launch_gm_init_g(const double* nrm2, double* g, int m, double* res, cudaStream_t s);
+cudaError_t launch_gm_update(const double* H, int m, const double* g, int k, double* y,
+                             const double* V, int64_t vstride, double* X, int64_t ldx, int nrhs,
+                             int64_t n, cudaStream_t s);
+cudaError_t launch_gm_diag_scale(const double* A, int64_t lda, int64_t n, double* sc, int on,
+                                 cudaStream_t s);
+cudaError_t launch_gm_scaled_copy(const double* A, int64_t lda, const double* sc, double delta,
+                                  double* L, int64_t ldl, int64_t n, cudaStream_t s);
 
 }  // namespace abft
 

@@ -339,6 +339,17 @@ __global__ void k_resid_reduce(const double* P, int nsplit, int64_t n, const dou
     atomic_max_nonneg(&xmax[r], fabs(X[i * ldx + r]));
 }
 
+// Y = sum_s P[s] (fixed order): the product A X from the split-K partials.
+__global__ void k_symv_reduce(const double* P, int nsplit, int64_t n, double* Y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * MAXRHS) return;
+    const int64_t i = e / MAXRHS;
+    const int r = (int)(e % MAXRHS);
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += P[((int64_t)k * n + i) * MAXRHS + r];
+    Y[e] = s;
+}
+
 // Row sums of |A| for symmetric A read from its lower triangle: the part
 // j <= i of row i (one warp per row) plus the strict column part i > j of
 // column i (one thread per column); both passes are coalesced.
@@ -488,6 +499,18 @@ cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const doubl
     int64_t tot = n * nrhs;
     k_resid_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, B, ldb, X, ldx, nrhs,
                                                                  R, ldr, rmax, xmax);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symv(const double* A, int64_t lda, int64_t n, const double* X, double* Y,
+                        double* P, int nsplit, cudaStream_t s) {
+    const int64_t kchunk = ((n + nsplit - 1) / nsplit + 31) / 32 * 32;
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)nsplit);
+    k_resid_partial<<<grid, 256, 0, s>>>(A, lda, n, X, MAXRHS, MAXRHS, kchunk, P);
+    note_launch();
+    const int64_t tot = n * MAXRHS;
+    k_symv_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, Y);
     note_launch();
     return cudaGetLastError();
 }
