@@ -57,8 +57,11 @@ def lib():
         L.orc_geqrf.argtypes = [i64, i64, ctypes.c_int, dp, i64, dp, ctypes.POINTER(_Event),
                                 ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_Report)]
         L.orc_potrs.argtypes = [i64, i64, dp, i64, dp, i64]
+        L.orc_potrf_sched.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_int32), dp, i64,
+                                      ctypes.POINTER(_Event), ctypes.c_int32, ctypes.c_double,
+                                      ctypes.POINTER(_Report)]
         for f in ("orc_potf2", "orc_getf2", "orc_geqr2", "orc_potrf", "orc_getrf",
-                  "orc_geqrf", "orc_potrs"):
+                  "orc_geqrf", "orc_potrs", "orc_potrf_sched"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -128,6 +131,22 @@ def potrf(A, nb, mode=FULL, faults=(), tau_scale=1.0):
     rep = _Report()
     info = lib().orc_potrf(A.shape[0], nb, mode, _dp(A), max(1, A.shape[1]), fa, nf, tau_scale,
                            ctypes.byref(rep))
+    return A, info, _report(rep)
+
+
+def potrf_sched(A, nb, modes, faults=(), tau_scale=1.0):
+    """Blocked ABFT Cholesky with one checksum mode per step (NONE / SINGLE /
+    FULL; adaptive ABFT, Sec. 3.1.2).  Returns (A', info, report) as potrf."""
+    A = _mat(A)
+    n = A.shape[0]
+    N = max(1, -(-n // nb))
+    m = np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
+    if m.shape != (N,):
+        raise ValueError(f"modes must have {N} entries")
+    fa, nf = _faults(faults)
+    rep = _Report()
+    info = lib().orc_potrf_sched(n, nb, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(A),
+                                 max(1, A.shape[1]), fa, nf, tau_scale, ctypes.byref(rep))
     return A, info, _report(rep)
 
 

@@ -371,16 +371,27 @@ static int chol_fault_ok(const orc_event* f, int64_t n, int64_t nb, int64_t N) {
  * a non-positive pivot, or -(argument index) for an invalid argument.
  * The strict upper triangle of A is left untouched.
  */
-int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
-              const orc_event* faults, int32_t nfaults, double tau_scale,
-              orc_report* rep) {
+/*
+ * orc_potrf_sched -- orc_potrf with a checksum mode per step (the adaptive
+ * ABFT of Sec. 3.1.2, Alg. alg-abft: each iteration runs with no check, the
+ * single-side check or the full check).  modes[k] is the mode of step k
+ * (N = ceil(n / nb) entries).  A step with mode NONE neither carries nor
+ * verifies checksums; when checking starts again, or moves from SINGLE to
+ * FULL, the checksums of the trailing block triangle are encoded afresh from
+ * the current data at the start of that step (so an error that struck during
+ * unchecked steps is part of the new checksums and is not detected).
+ */
+int orc_potrf_sched(int64_t n, int64_t nb, const int* modes, double* A, int64_t lda,
+                    const orc_event* faults, int32_t nfaults, double tau_scale,
+                    orc_report* rep) {
     memset(rep, 0, sizeof(*rep));
     if (n < 0) return -1;
     if (nb <= 0) return -2;
-    if (mode < M_NONE || mode > M_FULL) return -3;
     if (lda < (n > 1 ? n : 1)) return -5;
     if (n == 0) return 0;
     int64_t g = nb, nt = (n + g - 1) / g, N = nt;
+    for (int64_t k = 0; k < N; ++k)
+        if (modes[k] < M_NONE || modes[k] > M_FULL) return -3;
     for (int32_t f = 0; f < nfaults; ++f)
         if (!chol_fault_ok(&faults[f], n, nb, N)) return -6;
 
@@ -389,7 +400,7 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
         for (int64_t j = 0; j <= i; ++j) W[i * n + j] = W[j * n + i] = A[i * lda + j];
     double dmax = 0.0;
     for (int64_t i = 0; i < n; ++i) if (A[i * lda + i] > dmax) dmax = A[i * lda + i];
-    vctx c = { mode, 0, g, threshold(tau_scale, n, g, dmax), rep };
+    vctx c = { M_NONE, 0, g, threshold(tau_scale, n, g, dmax), rep };
     rep->tau = c.tau;
 
     double* Cc = dalloc(nt * n);  /* Cc[I*n + j]: column sums of tile-row I   */
@@ -397,18 +408,23 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
     double* Cr = dalloc(n * nt);  /* Cr[i*nt + J]: row sums of tile-column J   */
     double* xr = dalloc(n);       /* carried row sums of the panel             */
     double* v = dalloc(g);
-    if (mode != M_NONE)
-        for (int64_t I = 0; I < nt; ++I)
-            for (int64_t J = 0; J <= I; ++J) {
-                int64_t r0 = I * g, c0 = J * g;
-                encode_tile(W + r0 * n + c0, n, imin(g, n - r0), imin(g, n - c0),
-                            Cc + I * n + c0, Cw + I * n + c0, Cr + r0 * nt + J, nt);
-            }
     int info = 0;
     for (int64_t k = 0; k < N; ++k) {
+        const int mode = modes[k];
+        const int prev = k > 0 ? modes[k - 1] : M_NONE;
         c.step = (int)k;
+        c.mode = mode;
         int64_t K0 = k * g, kb = imin(g, n - K0), T0 = K0 + kb;
         double* Lkk = W + K0 * n + K0;
+        /* (re-)encode the trailing block triangle when checking starts or
+           moves from single-side to full checksums */
+        if (mode != M_NONE && (prev == M_NONE || (mode == M_FULL && prev != M_FULL)))
+            for (int64_t I = k; I < nt; ++I)
+                for (int64_t J = k; J <= I; ++J) {
+                    int64_t r0 = I * g, c0 = J * g;
+                    encode_tile(W + r0 * n + c0, n, imin(g, n - r0), imin(g, n - c0),
+                                Cc + I * n + c0, Cw + I * n + c0, Cr + r0 * nt + J, nt);
+                }
         /* PD */
         int pinfo = orc_potf2(kb, Lkk, n);
         if (pinfo) { info = (int)(K0 + pinfo); break; }
@@ -500,6 +516,23 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
     qsort(rep->loc, (size_t)rep->nloc, sizeof(orc_event), cmp_event);
     free(W); free(Cc); free(Cw); free(Cr); free(xr); free(v);
     return info;
+}
+
+/* orc_potrf: every step in the same checksum mode (the algorithm described
+ * above orc_potrf_sched). */
+int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
+              const orc_event* faults, int32_t nfaults, double tau_scale,
+              orc_report* rep) {
+    memset(rep, 0, sizeof(*rep));
+    if (n < 0) return -1;
+    if (nb <= 0) return -2;
+    if (mode < M_NONE || mode > M_FULL) return -3;
+    int64_t N = n > 0 ? (n + nb - 1) / nb : 1;
+    int* modes = (int*)malloc(sizeof(int) * (size_t)N);
+    for (int64_t k = 0; k < N; ++k) modes[k] = mode;
+    int r = orc_potrf_sched(n, nb, modes, A, lda, faults, nfaults, tau_scale, rep);
+    free(modes);
+    return r;
 }
 
 /* ------------------------------------------------------ blocked ABFT LU */
