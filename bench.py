@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
     p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
     p.add_argument("--no-batched", action="store_true", help="skip the batched timings")
+    p.add_argument("--conditioned", action="store_true",
+                   help="add the conditioned mixed-precision solves: A = Q diag(sigma) Q^T with "
+                        "kappa 1e2, 1e6, 1e10, block 512, GMRES-IR (BF16 / FP16) vs the FP64 form")
+    p.add_argument("--cond-n", type=int, default=16384)
     return p.parse_args()
 
 
@@ -341,6 +345,49 @@ def run_ours(args, ws, rank, local):
                            "rc": rc_m, "faults_corrected": rep_m["corrected"]}
         del Lbuf, Xb, B
 
+    conditioned = None
+    if args.conditioned:
+        # A = Q diag(sigma) Q^T, sigma geometric with condition kappa, block 512,
+        # 16 N(0,1) right-hand sides, target backward error 1e-12; time to
+        # solution of the FP64 form (FP64 ABFT potrf + potrs) and of GMRES-IR
+        # preconditioned by the BF16 / FP16 ABFT factor (automatic shift), and
+        # the error of each against the FP64 form's solution.
+        nc, nbc = args.cond_n, 512
+        Bc = torch.from_numpy(W.rhs(nc, 16, seed=1003)).to(dev)
+        Xc = torch.empty_like(Bc)
+        conditioned = {"n": nc, "nb": nbc, "tol": 1e-12}
+        for kappa in (1e2, 1e6, 1e10):
+            Ac = W.spd_kappa_torch(nc, kappa, seed=1002, device=dev)
+            Lc = torch.empty_like(Ac)
+            def fp64_form():
+                Lc.copy_(Ac)
+                abft.potrf(Lc, nbc, abft.FULL, workspace=wsp)
+                Xc.copy_(Bc)
+                abft.potrs(Lc, Xc, nbc, abft.F64)
+            ms64, _ = timed(fp64_form, 1, 1)
+            X64 = Xc.clone()
+            R64 = Bc - Ac @ X64
+            eta64 = float((R64.abs().amax(0) / (Ac.abs().sum(1).amax() * X64.abs().amax(0)
+                                                + Bc.abs().amax(0))).max())
+            entry = {"fp64_ms_to_solution": ms64, "fp64_backward_err": eta64}
+            for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
+                maxit = 3 if kappa >= 1e10 else 20
+                def gm():
+                    return abft.posv_gmres_ir(Ac, Bc, nbc, dt, abft.FULL, tol=1e-12, maxit=maxit,
+                                              m=60, inner_tol=1e-6, L=Lc, X=Xc, workspace=wsp)
+                ms_g, res = timed(gm, 1, 1)
+                rc_g, _, _, rep_g = res
+                err = float((Xc - X64).abs().max() / X64.abs().max())
+                entry[name] = {"ms_to_solution": ms_g, "speedup_vs_fp64": ms64 / ms_g,
+                               "rc": rc_g, "backward_err": rep_g["backward_err"],
+                               "reached_tol": rep_g["backward_err"] <= 1e-12,
+                               "ir_iters": rep_g["ir_iters"], "gmres_iters": rep_g["gmres_iters"],
+                               "attempts": rep_g["attempts"], "shift": rep_g["shift"],
+                               "rel_err_vs_fp64_form": err}
+            conditioned[f"{kappa:.0e}"] = entry
+            del Ac, Lc, X64, R64
+        del Bc, Xc
+
     lu_qr = None
     if not args.no_lu_qr:
         lu_qr = {}
@@ -460,7 +507,8 @@ def run_ours(args, ws, rank, local):
             "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
-            "mixed_precision_ir": mixed, "lu_qr": lu_qr, "batched": batched,
+            "mixed_precision_ir": mixed, "conditioned": conditioned, "lu_qr": lu_qr,
+            "batched": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)

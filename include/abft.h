@@ -185,6 +185,50 @@ int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_potrf_sched -- abft_potrf with one checksum mode per step: the
+ * adaptive ABFT of Sec. 3.1.2 (Alg. alg-abft), where each iteration of the
+ * decomposition runs without a check, with the single-side or with the full
+ * check.  modes: host int32[ceil(n / nb)], ABFT_MODE_* per step.  A step in
+ * mode NONE neither carries nor verifies checksums; at a step that checks
+ * after an unchecked one, or that moves from SINGLE to FULL, the checksums of
+ * the trailing block triangle are encoded afresh from the data (so an error
+ * that struck while nothing was checked is not detected).  The workspace is
+ * that of abft_potrf in the strongest mode of the schedule.  Returns and
+ * errors as abft_potrf (-4: modes NULL or an entry out of range).
+ */
+int abft_potrf_sched(int64_t n, int64_t nb, int32_t dtype, const int32_t* modes, double* A,
+                     int64_t lda, const abft_fault* faults, int32_t nfaults, double tau_scale,
+                     abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * Fault coverage of one detection interval (Sec. 3.1.2): the probability
+ * that single-side (abft_fc_single) or full (abft_fc_full) checksums correct
+ * every error, with errors of type 0D / 1D / 2D arriving as independent
+ * Poisson processes with mean counts mu0 / mu1 / mu2 in the interval
+ * (lambda T) and striking S blocks uniformly; a block corrects at most one
+ * error per interval, single-side checksums 0D errors only, full checksums
+ * 0D and 1D.  The product of the paper's formulas is read as
+ * prod_{i=0}^{k-1} (S - i) / S (k errors in k distinct blocks).  Host only
+ * (no GPU needed).  Returns NaN for S <= 0 or a negative or NaN mean.
+ */
+double abft_fc_single(int64_t S, double mu0, double mu1, double mu2);
+double abft_fc_full(int64_t S, double mu0, double mu1, double mu2);
+
+/*
+ * abft_adaptive_modes -- the mode policy of Alg. alg-abft without its clock
+ * loop (changing clocks is out of scope): for step k with predicted duration
+ * step_seconds[k], NONE when every rate is zero, else SINGLE when
+ * FC_single >= fc_desired, else FULL (also when FC_full < fc_desired, where
+ * the paper would lower the clock; coverage[k] then reports the shortfall).
+ * S = ceil(n / nb)^2.  lambda: host double[3], error rates of 0D, 1D, 2D
+ * errors per second; modes: host int32[ceil(n / nb)] out; coverage: host
+ * double[ceil(n / nb)] out or NULL.  Host only.  Errors: -1 n; -2 nb;
+ * -3 lambda; -4 fc_desired outside [0, 1]; -5 step_seconds / modes.
+ */
+int abft_adaptive_modes(int64_t n, int64_t nb, const double* lambda, double fc_desired,
+                        const double* step_seconds, int32_t* modes, double* coverage);
+
+/*
  * abft_potrs -- solve A X = B with the Cholesky factor L of abft_potrf
  * (X = L^{-T} L^{-1} B, forward then backward block substitution).  Not in
  * the paper; the solve that the factorization serves.

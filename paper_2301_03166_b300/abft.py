@@ -8,6 +8,7 @@ not on a CUDA device, the call raises.
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -71,6 +72,8 @@ _SIGNATURES = {
                            ctypes.POINTER(Report), _vp],
     "abft_potrf": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
+    "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
+                         ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }
 
 
@@ -105,6 +108,13 @@ def lib():
         L.abft_version.restype = ctypes.c_char_p
         L.abft_strerror.restype = ctypes.c_char_p
         L.abft_strerror.argtypes = [_i32]
+        for name in ("abft_fc_single", "abft_fc_full"):
+            getattr(L, name).argtypes = [_i64, _dbl, _dbl, _dbl]
+            getattr(L, name).restype = _dbl
+        L.abft_adaptive_modes.argtypes = [_i64, _i64, ctypes.POINTER(_dbl), _dbl,
+                                          ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
+                                          ctypes.POINTER(_dbl)]
+        L.abft_adaptive_modes.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -185,6 +195,71 @@ def potrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, (report_dict(rep) if rep is not None else None)
+
+
+def _modes_array(modes, n, nb):
+    N = max(1, -(-n // nb)) if n > 0 else 0
+    m = np.ascontiguousarray(np.asarray(list(modes), dtype=np.int32))
+    if m.shape != (N,):
+        raise ValueError(f"modes must have {N} entries (one per step)")
+    return m
+
+
+def potrf_sched(A, nb, modes, dtype=F64, faults=(), tau_scale=1.0, workspace=None, stream=None,
+                check=True):
+    """ABFT Cholesky in place with one checksum mode per step (adaptive ABFT).
+    Returns (info_or_code, report dict)."""
+    _check_matrix(A)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    m = _modes_array(modes, n, nb)
+    mp = m.ctypes.data_as(ctypes.POINTER(_i32))
+    L = lib()
+    fa, nf = _faults(faults)
+    need = ctypes.c_size_t(0)
+    rc = L.abft_potrf_sched(n, nb, dtype, mp, None, max(1, A.stride(0)), fa, nf, tau_scale, None,
+                            None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    rep = Report()
+    size = ctypes.c_size_t(ws.numel())
+    rc = L.abft_potrf_sched(n, nb, dtype, mp, ctypes.c_void_p(A.data_ptr()), max(1, A.stride(0)),
+                            fa, nf, tau_scale, ctypes.byref(rep), ctypes.c_void_p(ws.data_ptr()),
+                            ctypes.byref(size), _stream(stream))
+    if check and rc < 0 and rc != ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    return rc, report_dict(rep)
+
+
+def fc_single(S, mu0, mu1, mu2):
+    """Fault coverage of single-side checksums for one interval (host only)."""
+    return lib().abft_fc_single(int(S), float(mu0), float(mu1), float(mu2))
+
+
+def fc_full(S, mu0, mu1, mu2):
+    """Fault coverage of full checksums for one interval (host only)."""
+    return lib().abft_fc_full(int(S), float(mu0), float(mu1), float(mu2))
+
+
+def adaptive_modes(n, nb, lambdas, fc_desired, step_seconds):
+    """Per-step checksum modes of adaptive ABFT (host only).  Returns
+    (modes list, coverage list)."""
+    N = max(0, -(-n // nb))
+    lam = (_dbl * 3)(*[float(x) for x in lambdas])
+    ts = np.ascontiguousarray(np.asarray(step_seconds, dtype=np.float64))
+    if ts.shape != (N,):
+        raise ValueError(f"step_seconds must have {N} entries")
+    modes = np.zeros(max(N, 1), dtype=np.int32)
+    cov = np.zeros(max(N, 1), dtype=np.float64)
+    rc = lib().abft_adaptive_modes(n, nb, lam, float(fc_desired),
+                                   ts.ctypes.data_as(ctypes.POINTER(_dbl)),
+                                   modes.ctypes.data_as(ctypes.POINTER(_i32)),
+                                   cov.ctypes.data_as(ctypes.POINTER(_dbl)))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return modes[:N].tolist(), cov[:N].tolist()
 
 
 PHASES = ("pd", "pu", "tmu", "verify", "other", "solve")

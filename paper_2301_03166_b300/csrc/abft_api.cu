@@ -179,7 +179,11 @@ cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* s
 }
 
 // Blocked ABFT Cholesky step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
-int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
+// modes (nullable, host, one entry per step): the checksum mode of each step
+// (adaptive ABFT); nullptr runs every step in `mode`.  A step in mode NONE
+// neither carries nor verifies checksums; the trailing block triangle is
+// encoded afresh when checking starts again or moves from SINGLE to FULL.
+int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double* A, int64_t lda,
                const abft_fault* faults, int32_t nfaults, double tau_scale, const CholWs& w,
                char* base, cudaStream_t s, int32_t dtype) {
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
@@ -192,7 +196,6 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
     double* Cr = (double*)(base + w.cr);
     double* save = (double*)(base + w.save);
     const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt;
-    const bool full = mode == ABFT_MODE_FULL, check = mode != ABFT_MODE_NONE;
 
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 0, s));
@@ -204,21 +207,27 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
     base_ts.cr = Cr; base_ts.crs = nt; base_ts.crJ = 1;
     base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
     base_ts.weighted = 1;
-    if (check) {
-        TileSet ts = base_ts;
-        ts.I0 = 0; ts.I1 = nt; ts.J0 = 0; ts.J1 = nt; ts.lower = 1;
-        ABFT_CUDA_TRY(launch_encode(ts, mode, s));
-    }
     timing_mark(PH_OTHER, 0, s);
     for (int64_t k = 0; k < N; ++k) {
         const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
         double* Akk = A + K0 * lda + K0;
+        const int32_t mk = modes ? modes[k] : mode;
+        const int32_t mprev = k == 0 ? ABFT_MODE_NONE : (modes ? modes[k - 1] : mode);
+        const bool full = mk == ABFT_MODE_FULL, check = mk != ABFT_MODE_NONE;
+        if (check && (mprev == ABFT_MODE_NONE || (full && mprev != ABFT_MODE_FULL))) {
+            // (re-)encode the trailing block triangle (Sec. 3.1.2 encode)
+            timing_mark(PH_OTHER, 1, s);
+            TileSet ts = base_ts;
+            ts.I0 = k; ts.I1 = nt; ts.J0 = k; ts.J1 = nt; ts.lower = 1;
+            ABFT_CUDA_TRY(launch_encode(ts, mk, s));
+            timing_mark(PH_OTHER, 0, s);
+        }
         // PD and its checksum check
         timing_mark(PH_PD, 1, s);
         ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, st, s));
         if (check)
             ABFT_CUDA_TRY(launch_chol_pd_check(Akk, lda, kb, CS + (k * nc) * n + K0, K0, (int)k,
-                                               nullptr, mode, st, s));
+                                               nullptr, mk, st, s));
         timing_mark(PH_PD, 0, s);
         if (m <= 0) break;
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
@@ -310,7 +319,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda,
         if (check) {
             TileSet ts = base_ts;
             ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 1;
-            ABFT_CUDA_TRY(launch_verify(ts, mode, (int)k, st, s));
+            ABFT_CUDA_TRY(launch_verify(ts, mk, (int)k, st, s));
         }
         timing_mark(PH_VERIFY, 0, s);
     }
@@ -1437,7 +1446,47 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
     DevStatus* st = (DevStatus*)(base + w.st);
     ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
     if (n > 0) {
-        int rc = chol_steps(n, nb, mode, A, lda, faults, nfaults, tau_scale, w, base, s, dtype);
+        int rc = chol_steps(n, nb, mode, nullptr, A, lda, faults, nfaults, tau_scale, w, base,
+                            s, dtype);
+        if (rc != ABFT_OK) return rc;
+    }
+    ABFT_CUDA_TRY(timing_collect(s));
+    if (rep) return finish_report(st, rep, s);
+    return ABFT_OK;
+}
+
+int abft_potrf_sched(int64_t n, int64_t nb, int32_t dtype, const int32_t* modes, double* A,
+                     int64_t lda, const abft_fault* faults, int32_t nfaults, double tau_scale,
+                     abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
+    const int64_t N = (n + nb - 1) / nb;
+    if (N > 0 && modes == nullptr) return -4;
+    int32_t top = ABFT_MODE_NONE;
+    for (int64_t k = 0; k < N; ++k) {
+        if (modes[k] < ABFT_MODE_NONE || modes[k] > ABFT_MODE_FULL) return -4;
+        top = std::max(top, modes[k]);
+    }
+    // argument checks and the workspace size of the strongest mode used
+    size_t need = 0;
+    int rc = abft_potrf(n, nb, dtype, top, nullptr, lda, faults, nfaults, tau_scale, nullptr,
+                        nullptr, &need, nullptr);
+    if (rc != ABFT_OK) return rc;
+    if (ws_bytes == nullptr) return -12;
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (n > 0 && A == nullptr) return -5;
+    if (*ws_bytes < need) return -12;
+    const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    const CholWs w = chol_ws(n, nb, top, mixed);
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    DevStatus* st = (DevStatus*)(base + w.st);
+    ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    if (n > 0) {
+        rc = chol_steps(n, nb, top, modes, A, lda, faults, nfaults, tau_scale, w, base, s, dtype);
         if (rc != ABFT_OK) return rc;
     }
     ABFT_CUDA_TRY(timing_collect(s));

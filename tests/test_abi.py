@@ -73,3 +73,37 @@ def test_gmres_ir_workspace_query_and_arguments_on_host():
     assert L.abft_posv_gmres_ir(*args(65, 1e-6, -1.0)) == -16
     assert L.abft_posv_gmres_ir(*args(30, -1.0, -1.0)) == -17
     assert L.abft_posv_gmres_ir(*args(30, 1e-6, float("nan"))) == -18
+
+
+def test_fault_coverage_and_policy_match_the_oracle():
+    """The library's host-side fault-coverage model and mode policy against the
+    oracle's literal double sums (no GPU needed)."""
+    from oracle import adaptive as ad
+    for S, m0, m1, m2 in ((1, 0.3, 0.0, 0.0), (16, 2.0, 0.5, 0.1), (4096, 3.0, 1e-3, 0.0),
+                          (65536, 40.0, 2.0, 1e-4), (9, 0.0, 0.0, 0.0)):
+        assert abft.fc_single(S, m0, m1, m2) == pytest.approx(ad.fc_single(S, m0, m1, m2), rel=1e-12)
+        assert abft.fc_full(S, m0, m1, m2) == pytest.approx(ad.fc_full(S, m0, m1, m2), rel=1e-12)
+    import math
+    assert math.isnan(abft.fc_single(0, 1.0, 0.0, 0.0))
+    n, nb = 8192, 256
+    T = [2e-4 * (32 - k) ** 2 for k in range(32)]
+    for lam in ((0.0, 0.0, 0.0), (2.0, 0.0, 0.0), (50.0, 0.01, 0.0), (5.0, 1e-3, 1e-4)):
+        got, cov = abft.adaptive_modes(n, nb, lam, 0.999999, T)
+        want, wcov = ad.adaptive_modes(n, nb, lam, 0.999999, T)
+        assert got == want
+        assert cov == pytest.approx(wcov, rel=1e-12)
+
+
+def test_sched_arguments_on_host():
+    L = abft.lib()
+    need = ctypes.c_size_t(0)
+    m = (ctypes.c_int32 * 8)(0, 0, 1, 1, 2, 2, 1, 0)
+    assert L.abft_potrf_sched(1024, 128, 0, m, None, 1024, None, 0, 1.0, None, None,
+                              ctypes.byref(need), None) == 0
+    full = ctypes.c_size_t(0)
+    assert L.abft_potrf(1024, 128, 0, 2, None, 1024, None, 0, 1.0, None, None,
+                        ctypes.byref(full), None) == 0
+    assert need.value == full.value
+    bad = (ctypes.c_int32 * 8)(0, 0, 1, 3, 2, 2, 1, 0)
+    assert L.abft_potrf_sched(1024, 128, 0, bad, None, 1024, None, 0, 1.0, None, None,
+                              ctypes.byref(need), None) == -4
