@@ -235,7 +235,8 @@ int abft_adaptive_modes(int64_t n, int64_t nb, const double* lambda, double fc_d
  *   n, nrhs    order and number of right-hand sides (processed 16 at a time)
  *   nb         block size of the substitution (multiple of 32, <= 512)
  *   dtype      ABFT_F64: FP64 arithmetic; ABFT_F32 / ABFT_MIXED_*: FP32
- *              arithmetic (L is read in FP64 and rounded on load)
+ *              arithmetic (the lower triangle of L is rounded to FP32 once,
+ *              into the workspace, which then holds n x n floats more)
  *   L, ldl     lower factor (device, row-major); the upper triangle is not read
  *   B, ldb     n x nrhs row-major (device); overwritten by X
  * Errors: -1 n; -2 nrhs; -3 nb; -4 dtype; -5 L; -6 ldl; -7 B; -8 ldb;
@@ -283,6 +284,11 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
  *       4 delta (at most 8 attempts; u_f = 2^-8 BF16, 2^-11 FP16, 2^-53 FP64);
  *       shift >= 0 fixes delta = shift;
  *   M^{-1} v = S L^{-T} L^{-1} S v (FP64 substitution if precond_f64, else FP32);
+ *   inner_f32 != 0: GMRES's products with A use an FP32 copy of A and FP32
+ *       arithmetic (the five-precision GMRES-IR of Amestoy, Buttari, Higham,
+ *       L'Excellent, Mary and Vieuble, SIMAX 2024, with GMRES and the
+ *       preconditioner in FP32); the residual R and the update of X stay FP64;
+ *       the workspace then holds n x n floats more;
  *   X = M^{-1} B; repeat: R = B - A X in FP64, eta as abft_posv_ir; stop at
  *       eta <= tol or after maxit refinement steps; else run GMRES (left
  *       preconditioned, Arnoldi with classical Gram-Schmidt applied twice,
@@ -299,8 +305,9 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
                        const double* A, int64_t lda, double* L, int64_t ldl, const double* B,
                        int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit, int32_t m,
                        double inner_tol, double shift, int32_t scale, int32_t precond_f64,
-                       const abft_fault* faults, int32_t nfaults, double tau_scale,
-                       abft_report* rep, void* ws, size_t* ws_bytes, void* stream);
+                       int32_t inner_f32, const abft_fault* faults, int32_t nfaults,
+                       double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes,
+                       void* stream);
 
 /*
  * Reverse mode (adjoints) of potrf, potrs and logdet -- not in the paper: the

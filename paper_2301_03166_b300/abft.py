@@ -61,7 +61,7 @@ _SIGNATURES = {
                      _dbl, _i32, ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp,
                      _sz, _vp],
     "abft_posv_gmres_ir": [_i64, _i64, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
-                           _i64, _dbl, _i32, _i32, _dbl, _dbl, _i32, _i32,
+                           _i64, _dbl, _i32, _i32, _dbl, _dbl, _i32, _i32, _i32,
                            ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz,
                            _vp],
     "abft_geqrf": [_i64, _i64, _i32, _i32, _vp, _i64, _vp, ctypes.POINTER(Fault), _i32, _dbl,
@@ -389,8 +389,9 @@ def posv_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=50, faul
 
 
 def posv_gmres_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=20, m=30,
-                  inner_tol=1e-6, shift=-1.0, scale=True, precond_f64=False, faults=(),
-                  tau_scale=1.0, L=None, X=None, workspace=None, stream=None, check=True):
+                  inner_tol=1e-6, shift=-1.0, scale=True, precond_f64=False, inner_f32=False,
+                  faults=(), tau_scale=1.0, L=None, X=None, workspace=None, stream=None,
+                  check=True):
     """Solve A X = B (A SPD, lower triangle read) by GMRES-based iterative
     refinement preconditioned by an ABFT Cholesky of the scaled, shifted matrix
     in `dtype` (shift < 0: automatic).  Returns (code, X, L, report)."""
@@ -405,7 +406,7 @@ def posv_gmres_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=20
     rc = Lb.abft_posv_gmres_ir(n, nrhs, nb, dtype, mode, None, max(1, A.stride(0)), None,
                                max(1, L.stride(0)), None, max(1, B.stride(0)), None,
                                max(1, X.stride(0)), tol, maxit, m, inner_tol, shift, int(scale),
-                               int(precond_f64), fa, nf, tau_scale, None, None,
+                               int(precond_f64), int(inner_f32), fa, nf, tau_scale, None, None,
                                ctypes.byref(need), None)
     if rc < 0:
         raise AbftError(rc, strerror(rc))
@@ -414,9 +415,9 @@ def posv_gmres_ir(A, B, nb=256, dtype=MIXED_BF16, mode=FULL, tol=1e-12, maxit=20
     size = ctypes.c_size_t(ws.numel())
     rc = Lb.abft_posv_gmres_ir(n, nrhs, nb, dtype, mode, _ptr(A), A.stride(0), _ptr(L),
                                L.stride(0), _ptr(B), B.stride(0), _ptr(X), X.stride(0), tol,
-                               maxit, m, inner_tol, shift, int(scale), int(precond_f64), fa, nf,
-                               tau_scale, ctypes.byref(rep), _ptr(ws), ctypes.byref(size),
-                               _stream(stream))
+                               maxit, m, inner_tol, shift, int(scale), int(precond_f64),
+                               int(inner_f32), fa, nf, tau_scale, ctypes.byref(rep), _ptr(ws),
+                               ctypes.byref(size), _stream(stream))
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, X, L, report_dict(rep)

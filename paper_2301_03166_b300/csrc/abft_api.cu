@@ -708,25 +708,52 @@ namespace {
 // ------------------------------------------------------------- solves / IR
 constexpr int kSplit = 8;   // split-K factor of the FP64 residual
 
-// potrs scratch: the chunk inverses (sized for FP64) then, for the FP32
-// solve, an n x 16 FP32 copy of the right-hand sides.
+// potrs scratch: the inverses of L's diagonal blocks with the sweep's flags
+// (room for either arithmetic), then, for the FP32 solve, an n x 16 FP32 copy
+// of the right-hand sides and the lower triangle of L rounded to FP32 (n x n).
+struct SolvePtrs {
+    void* inv;
+    float* Yf;
+    float* L32;
+};
+
+SolvePtrs solve_ptrs(char* ws, int64_t n) {
+    SolvePtrs p;
+    p.inv = ws;
+    size_t off = align_up(potrs_inv_bytes(n, true));
+    p.Yf = (float*)(ws + off);
+    off += align_up(sizeof(float) * (size_t)n * 16);
+    p.L32 = (float*)(ws + off);
+    return p;
+}
+
 size_t potrs_ws_bytes(int64_t n, int32_t dtype) {
     const size_t inv = align_up(potrs_inv_bytes(n, true));
-    const size_t f = (dtype == ABFT_F64) ? 0 : align_up(sizeof(float) * (size_t)n * 16);
+    const size_t f = (dtype == ABFT_F64) ? 0
+                                         : align_up(sizeof(float) * (size_t)n * 16) +
+                                               align_up(sizeof(float) * (size_t)n * (size_t)n);
     return std::max<size_t>(inv + f, 256);
 }
 
+// prepared: the block inverses (and for FP32 the FP32 copy of L) of this L are
+// already in ws from an earlier call.
 int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
-              double* B, int64_t ldb, char* ws, cudaStream_t s) {
-    void* inv = ws;
-    float* Yf = (float*)(ws + align_up(potrs_inv_bytes(n, true)));
+              double* B, int64_t ldb, char* ws, cudaStream_t s, bool prepared = false) {
+    const SolvePtrs sp = solve_ptrs(ws, n);
+    void* inv = sp.inv;
+    float* Yf = sp.Yf;
+    if (dtype != ABFT_F64 && !prepared && nrhs > 0)
+        ABFT_CUDA_TRY(launch_tril_to_f32(L, ldl, n, sp.L32, s));
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
+        const bool have_inv = prepared || r0 > 0;
         if (dtype == ABFT_F64) {
-            ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, B + r0, ldb, (double*)inv, s));
+            ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, B + r0, ldb, (double*)inv, s,
+                                           have_inv));
         } else {
             ABFT_CUDA_TRY(launch_copy_d2f(B + r0, ldb, Yf, 16, n, nr, s));
-            ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
+            ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s, have_inv,
+                                           sp.L32));
             ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, B + r0, ldb, n, nr, s));
         }
         cudaError_t ce = cudaSuccess;
@@ -760,10 +787,10 @@ constexpr int kGmresMax = 64;       // largest GMRES cycle (basis vectors)
 constexpr int kGmresAttempts = 8;   // factorizations tried with growing shift
 
 struct GmWs {
-    size_t sc, V, W, part, hnew, h2, H, cs, sn, g, res, y, total;
+    size_t sc, V, W, part, hnew, h2, H, cs, sn, g, res, y, a32, total;
 };
 
-GmWs gm_ws(int64_t n, int m, size_t off) {
+GmWs gm_ws(int64_t n, int m, size_t off, bool a32) {
     GmWs w{};
     const size_t d = sizeof(double);
     const size_t blk = d * (size_t)n * 16;
@@ -779,6 +806,7 @@ GmWs gm_ws(int64_t n, int m, size_t off) {
     w.g = off; off = align_up(off + d * 16 * (size_t)(m + 1));
     w.res = off; off = align_up(off + d * 16);
     w.y = off; off = align_up(off + d * 16 * (size_t)m);
+    w.a32 = off; off = align_up(off + (a32 ? sizeof(float) * (size_t)n * (size_t)n : 0));
     w.total = off;
     return w;
 }
@@ -858,8 +886,9 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     const int factor_rc = rc;
     if (n == 0 || nrhs == 0) return factor_rc;
     char* sws = base + w.solve;
-    void* inv = sws;
-    float* Yf = (float*)(sws + align_up(potrs_inv_bytes(n, true)));
+    const SolvePtrs sp = solve_ptrs(sws, n);
+    void* inv = sp.inv;
+    float* Yf = sp.Yf;
     double* R = (double*)(base + w.R);
     double* P = (double*)(base + w.P);
     double* rs = (double*)(base + w.rs);
@@ -868,6 +897,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     double* eta_d = (double*)(base + w.eta);
     int32_t iters_max = 0;
     double eta_max = 0.0;
+    bool prepared = false;   // block inverses (and the FP32 copy of L) formed
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
@@ -875,8 +905,10 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
         // X0 = L^{-T} L^{-1} B
         timing_mark(PH_SOLVE, 1, s);
         ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
-        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, sws, s);
+        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, sws, s,
+                       prepared);
         if (rc != ABFT_OK) return rc;
+        prepared = true;
         int32_t it = 0;
         double eta = 0.0;
         for (;; ++it) {
@@ -888,12 +920,14 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
             ABFT_CUDA_TRY(cudaStreamSynchronize(s));
             if (eta <= tol || it >= maxit || !(eta == eta)) break;
             // correction D = L^{-T} L^{-1} R in the solve precision, X += D
+            // the inverses of L's diagonal blocks are still in inv from potrs_run
             if (dtype == ABFT_F64) {
-                ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, (double*)inv, s));
+                ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, (double*)inv, s, true));
                 ABFT_CUDA_TRY(launch_add_f64(X + r0, ldx, R, 16, n, nr, s));
             } else {
                 ABFT_CUDA_TRY(launch_copy_d2f(R, 16, Yf, 16, n, nr, s));
-                ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s));
+                ABFT_CUDA_TRY(launch_potrs_f32(n, nr, nb, L, ldl, Yf, 16, (float*)inv, s, true,
+                                               sp.L32));
                 ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
             }
             cudaError_t ce = cudaSuccess;
@@ -916,8 +950,9 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
                        const double* A, int64_t lda, double* L, int64_t ldl, const double* B,
                        int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit, int32_t m,
                        double inner_tol, double shift, int32_t scale, int32_t precond_f64,
-                       const abft_fault* faults, int32_t nfaults, double tau_scale,
-                       abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
+                       int32_t inner_f32, const abft_fault* faults, int32_t nfaults,
+                       double tau_scale, abft_report* rep, void* ws, size_t* ws_bytes,
+                       void* stream) {
     if (n < 0) return -1;
     if (nrhs < 0) return -2;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
@@ -939,7 +974,7 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
     if (!(shift >= 0.0) && !(shift < 0.0)) return -18;   // NaN
     if (ws_bytes == nullptr) return -22;
     const IrWs w = ir_ws(n, nb, mode, dtype);
-    const GmWs gw = gm_ws(n, m, w.total);
+    const GmWs gw = gm_ws(n, m, w.total, inner_f32 != 0);
     size_t pws = 0;
     int rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, nullptr, nullptr,
                         &pws, nullptr);
@@ -982,8 +1017,9 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
     pr->shift = delta;
     if (n == 0 || nrhs == 0) return factor_rc;
     char* sws = base + w.solve;
-    void* inv = sws;
-    float* Yf = (float*)(sws + align_up(potrs_inv_bytes(n, true)));
+    const SolvePtrs sp = solve_ptrs(sws, n);
+    void* inv = sp.inv;
+    float* Yf = sp.Yf;
     double* R = (double*)(base + w.R);
     double* P = (double*)(base + w.P);
     double* rs = (double*)(base + w.rs);
@@ -1002,17 +1038,24 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
     double* g = (double*)(base + gw.g);
     double* res = (double*)(base + gw.res);
     double* yv = (double*)(base + gw.y);
+    float* A32 = (float*)(base + gw.a32);
     const bool f64 = precond_f64 != 0;
-    // z := M^{-1} z = S L^{-T} L^{-1} S z, in place on an n x 16 block
+    if (inner_f32) ABFT_CUDA_TRY(launch_copy_d2f(A, lda, A32, n, n, (int)n, s));
+    // z := M^{-1} z = S L^{-T} L^{-1} S z, in place on an n x 16 block; the
+    // inverses of L's diagonal blocks are formed by the first application
+    bool inv_ready = false;
     auto precond = [&](double* z) -> int {
         ABFT_CUDA_TRY(launch_gm_rowscale(sc, z, z, n, s));
         if (f64) {
-            ABFT_CUDA_TRY(launch_potrs_f64(n, 16, nb, L, ldl, z, 16, (double*)inv, s));
+            ABFT_CUDA_TRY(launch_potrs_f64(n, 16, nb, L, ldl, z, 16, (double*)inv, s, inv_ready));
         } else {
+            if (!inv_ready) ABFT_CUDA_TRY(launch_tril_to_f32(L, ldl, n, sp.L32, s));
             ABFT_CUDA_TRY(launch_copy_d2f(z, 16, Yf, 16, n, 16, s));
-            ABFT_CUDA_TRY(launch_potrs_f32(n, 16, nb, L, ldl, Yf, 16, (float*)inv, s));
+            ABFT_CUDA_TRY(launch_potrs_f32(n, 16, nb, L, ldl, Yf, 16, (float*)inv, s, inv_ready,
+                                           sp.L32));
             ABFT_CUDA_TRY(launch_copy_f2d(Yf, 16, z, 16, n, 16, s));
         }
+        inv_ready = true;
         ABFT_CUDA_TRY(launch_gm_rowscale(sc, z, z, n, s));
         return ABFT_OK;
     };
@@ -1060,7 +1103,8 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
             int k = 0;
             for (int j = 0; j < m; ++j) {
                 double* Vj = V + (int64_t)j * vstride;
-                ABFT_CUDA_TRY(launch_symv(A, lda, n, Vj, Wb, P, kSplit, s));
+                if (inner_f32) ABFT_CUDA_TRY(launch_symv_f32(A32, n, n, Vj, Wb, P, kSplit, s));
+                else ABFT_CUDA_TRY(launch_symv(A, lda, n, Vj, Wb, P, kSplit, s));
                 rc = precond(Wb);
                 if (rc != ABFT_OK) return rc;
                 // classical Gram-Schmidt, twice

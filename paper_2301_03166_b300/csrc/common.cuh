@@ -230,12 +230,19 @@ cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, c
 
 // Solves and iterative refinement (k_solve.cu).
 int potrs_max_rhs();
-// inv: scratch for the inverses of the 32 x 32 diagonal chunks and the sweep's
-// tickets and ready flags (potrs_inv_bytes).
+// inv: scratch for the inverses of the diagonal blocks and the sweep's tickets
+// and ready flags (potrs_inv_bytes).  have_inv: the inverses of this L (in this
+// arithmetic) are already in inv from an earlier call.
 cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             double* B, int64_t ldb, double* inv, cudaStream_t s);
+                             double* B, int64_t ldb, double* inv, cudaStream_t s,
+                             bool have_inv = false);
+// L32 (nullable): the lower triangle of L rounded to FP32, n x n with ld n
+// (launch_tril_to_f32); with it the FP32 sweeps stream FP32 tiles.
 cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             float* B, int64_t ldb, float* inv, cudaStream_t s);
+                             float* B, int64_t ldb, float* inv, cudaStream_t s,
+                             bool have_inv = false, const float* L32 = nullptr);
+cudaError_t launch_tril_to_f32(const double* L, int64_t ldl, int64_t n, float* L32,
+                               cudaStream_t s);
 size_t potrs_inv_bytes(int64_t n, bool f64);
 // Nonzero when a wait of the last solve using `inv` gave up (reads one word and
 // synchronizes the stream; *ce receives the copy's status).
@@ -252,6 +259,9 @@ cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const doubl
 // partials in P (nsplit x n x 16).
 cudaError_t launch_symv(const double* A, int64_t lda, int64_t n, const double* X, double* Y,
                         double* P, int nsplit, cudaStream_t s);
+// The same product in FP32 arithmetic from an FP32 copy of A (Y in FP64).
+cudaError_t launch_symv_f32(const float* A, int64_t lda, int64_t n, const double* X, double* Y,
+                            double* P, int nsplit, cudaStream_t s);
 cudaError_t launch_inf_norms(const double* A, int64_t lda, int64_t n, const double* B, int64_t ldb,
                              int nrhs, double* rs, unsigned long long* anorm,
                              unsigned long long* bmax, cudaStream_t s);

@@ -2,8 +2,9 @@
 // pieces of iterative refinement: the FP64 residual R = B - A X, the
 // normwise backward error, and X += D.
 //
-// potrs is two launches of a persistent sweep kernel (forward with L, backward
-// with L^T), each covering all 64-row blocks with flag-ordered block solves.
+// potrs is the inverses of the diagonal blocks (128 rows in FP32, 64 in FP64)
+// and two launches of a persistent sweep kernel (forward with L, backward
+// with L^T), each covering all blocks with flag-ordered block solves.
 // T is the arithmetic type (double for the FP64 solve, float for the
 // correction solves of iterative refinement); L is read in FP64 and converted
 // on load.
@@ -19,44 +20,83 @@ namespace {
 
 constexpr int MAXRHS = 16;
 
-// Inverses of the 32 x 32 diagonal chunks of L (lower), one warp per chunk:
-// lane j computes column j of the inverse by substitution with the chunk in
-// shared memory.  Used by the diagonal-block solves below.
+// Block geometry of the sweeps: 128-row blocks and 512 threads in FP32, 64-row
+// blocks and 256 threads in FP64 (shared memory holds one tile of L and the
+// inverse of the block's diagonal part).
 template <typename T>
-__global__ void __launch_bounds__(32) k_chunk_inv(const double* L, int64_t ldl, int64_t n, T* Inv) {
-    __shared__ T Lc[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32;
-    const int w = (int)((n - c0) < 32 ? (n - c0) : 32);
-    const int lane = threadIdx.x;
-    for (int i = 0; i < 32; ++i)
-        Lc[i][lane] = (i < w && lane <= i) ? (T)L[(c0 + i) * ldl + c0 + lane] : (T)0;
-    __syncwarp();
-    T x[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        T v = (i == lane) ? (T)1 : (T)0;
-#pragma unroll
-        for (int p = 0; p < i; ++p) v -= Lc[i][p] * x[p];
-        x[i] = (i < w) ? v / Lc[i][i] : (T)0;
+struct SweepCfg;
+template <>
+struct SweepCfg<float> {
+    static constexpr int RB = 128;
+};
+template <>
+struct SweepCfg<double> {
+    static constexpr int RB = 64;
+};
+
+template <typename T>
+size_t inv_smem_bytes() {
+    constexpr int RB = SweepCfg<T>::RB;
+    return sizeof(T) * 2 * (size_t)RB * (RB + 1);
+}
+
+// Inverse of each RB x RB diagonal block of L (rows past n are the identity),
+// one CTA of RB threads per block: thread j computes column j by forward
+// substitution with true divisions, X[j][j] = 1 / L[j][j] and
+// X[i][j] = -(sum_{p=j}^{i-1} L[i][p] X[p][j]) / L[i][i].  Inv holds the
+// blocks one after the other, RB x RB row-major each.
+template <typename T>
+__global__ void k_block_inv(const double* L, int64_t ldl, int64_t n, T* Inv) {
+    constexpr int RB = SweepCfg<T>::RB;
+    extern __shared__ __align__(16) unsigned char bsb[];
+    T* Ls = (T*)bsb;                      // RB x (RB + 1)
+    T* Xs = Ls + RB * (RB + 1);           // column j written by thread j
+    const int64_t b0 = (int64_t)blockIdx.x * RB;
+    const int t = threadIdx.x;
+    for (int e = t; e < RB * RB; e += RB) {
+        const int i = e / RB, j = e % RB;
+        const int64_t gi = b0 + i, gj = b0 + j;
+        T v;
+        if (gi < n && gj < n) v = (j <= i) ? (T)L[gi * ldl + gj] : (T)0;
+        else v = (i == j) ? (T)1 : (T)0;
+        Ls[i * (RB + 1) + j] = v;
     }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) Inv[(c0 + i) * 32 + lane] = (i < w && lane < w) ? x[i] : (T)0;
+    __syncthreads();
+    const int j = t;
+    for (int i = 0; i < RB; ++i) {
+        T x = 0;
+        if (i == j) {
+            x = (T)1 / Ls[i * (RB + 1) + i];
+        } else if (i > j) {
+            T s0 = 0, s1 = 0;
+            int p = j;
+            for (; p + 1 < i; p += 2) {
+                s0 += Ls[i * (RB + 1) + p] * Xs[p * (RB + 1) + j];
+                s1 += Ls[i * (RB + 1) + p + 1] * Xs[(p + 1) * (RB + 1) + j];
+            }
+            if (p < i) s0 += Ls[i * (RB + 1) + p] * Xs[p * (RB + 1) + j];
+            x = -(s0 + s1) / Ls[i * (RB + 1) + i];
+        }
+        Xs[i * (RB + 1) + j] = x;
+    }
+    __syncthreads();
+    T* out = Inv + (int64_t)blockIdx.x * RB * RB;
+    for (int e = t; e < RB * RB; e += RB) out[e] = Xs[(e / RB) * (RB + 1) + e % RB];
 }
 
 // One triangular sweep in a single launch: L Y = Y (TRANS = 0) or L^T X = X
 // (TRANS = 1) for nrhs <= 16 right-hand sides, Y row-major (ld ldy), solved in
-// place.  Rows are cut into 64-row blocks.  CTAs take blocks from a ticket
+// place.  Rows are cut into RB-row blocks.  CTAs take blocks from a ticket
 // counter in solve order (first to last for L, last to first for L^T); the CTA
-// of block i streams the 64 x 64 tiles of L that couple it to the blocks solved
-// before it, waiting on each block's ready flag, then solves its diagonal block
-// with the precomputed 32 x 32 chunk inverses and publishes its rows and flag.
-// A CTA only waits on blocks whose tickets were handed out before its own, so
-// the sweep completes whatever the number of resident CTAs.  Every wait gives
-// up after one second: it sets sync[2] and the remaining CTAs drain.
+// of block i loads the block's precomputed inverse, streams the RB x RB tiles
+// of L that couple it to the blocks solved before it, waiting on each block's
+// ready flag, then forms y_i = Inv_i (b_i - sum_j L_ij y_j) (Inv_i^T for L^T)
+// and publishes its rows and flag.  A CTA only waits on blocks whose tickets
+// were handed out before its own, so the sweep completes whatever the number
+// of resident CTAs.  Every wait gives up after one second: it sets sync[2] and
+// the remaining CTAs drain.
 // sync: [0] / [1] tickets (L, L^T), [2] error, [4, 4 + NB) flags of the L
 // sweep, [4 + NB, 4 + 2 NB) flags of the L^T sweep; zeroed before the solve.
-constexpr int RB = 64;
-
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -69,25 +109,29 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 
 template <typename T>
 size_t sweep_smem_bytes() {
-    return sizeof(T) * ((size_t)RB * (RB + 1) + 2 * (size_t)RB * MAXRHS + 2 * 32 * 33);
+    constexpr int RB = SweepCfg<T>::RB;
+    return sizeof(T) * (2 * (size_t)RB * (RB + 1) + (size_t)RB * MAXRHS);
 }
 
-template <typename T, int TRANS>
-__global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict__ L, int64_t ldl,
-                                                    int64_t n, T* Y, int64_t ldy, int nrhs,
-                                                    const T* __restrict__ Inv, unsigned* sync) {
+template <typename T, int TRANS, typename LT>
+__global__ void __launch_bounds__(4 * SweepCfg<T>::RB) k_trsv_sweep(
+    const LT* __restrict__ L, int64_t ldl, int64_t n, T* Y, int64_t ldy, int nrhs,
+    const T* __restrict__ Inv, unsigned* sync) {
+    constexpr int RB = SweepCfg<T>::RB, NT = 4 * RB, PER = RB * RB / NT, YPER = RB * MAXRHS / NT;
     extern __shared__ __align__(16) unsigned char sb[];
-    T* sA = (T*)sb;                         // tile of L^T (or L): sA[p * (RB + 1) + a]
-    T* sY = sA + RB * (RB + 1);             // solved rows of the tile / rhs of the diagonal
-    T* sX = sY + RB * MAXRHS;               // solution of the diagonal block
-    T* sI = sX + RB * MAXRHS;               // two 32 x 32 chunk inverses, ld 33
+    T* sA = (T*)sb;                         // tile, sA[p * (RB + 1) + a] = op(L)[a][p]
+    T* sI = sA + RB * (RB + 1);             // sI[p * (RB + 1) + a] = M[a][p], M = Inv_i or Inv_i^T
+    T* sY = sI + RB * (RB + 1);             // solved rows of the tile / rhs of the diagonal
     __shared__ int s_blk, s_ok, s_known;
     const int NB = (int)((n + RB - 1) / RB);
-    const int nchunk = (int)((n + 31) / 32);
     unsigned* ticket = sync + TRANS;
     unsigned* err = sync + 2;
     unsigned* flag = sync + 4 + (TRANS ? NB : 0);
-    const int t = threadIdx.x, row = t & 63, cg = t >> 6;
+    // compute roles: 4 groups split the RB-long inner dimension into quarters;
+    // in a group, thread (rg, cg) owns rows rg + c RB / 4 (c < 4) and
+    // right-hand sides 4 cg .. 4 cg + 3 (a 4 x 4 register block)
+    constexpr int Q = RB / 4;
+    const int t = threadIdx.x, g = t / RB, rg = t % Q, cg = (t / Q) % 4;
     for (;;) {
         if (t == 0) {
             const unsigned tk = atomicAdd(ticket, 1u);
@@ -100,49 +144,61 @@ __global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict_
         const int64_t i0 = (int64_t)bi * RB;
         const int nj = TRANS ? NB - 1 - bi : bi;     // coupling tiles, in solve order
         auto jblk = [&](int k) { return TRANS ? NB - 1 - k : k; };
-        // this thread's 16 elements of tile (bi, jb) of the operator (jb == bi: diagonal)
-        auto load_tile = [&](int jb, double (&v)[16]) {
+        auto load_tile = [&](int jb, LT (&v)[PER]) {
             const int64_t j0 = (int64_t)jb * RB;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = t + 256 * q, a = e >> 6, b = e & 63;
+            for (int q = 0; q < PER; ++q) {
+                const int e = t + NT * q, a = e / RB, b = e % RB;
                 const int64_t gr = TRANS ? j0 + a : i0 + a, gc = TRANS ? i0 + b : j0 + b;
-                v[q] = (gr < n && gc < n) ? L[gr * ldl + gc] : 0.0;
+                v[q] = (gr < n && gc < n) ? L[gr * ldl + gc] : (LT)0;
             }
         };
-        auto store_tile = [&](const double (&v)[16]) {
+        auto store_tile = [&](const LT (&v)[PER]) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = t + 256 * q, a = e >> 6, b = e & 63;
+            for (int q = 0; q < PER; ++q) {
+                const int e = t + NT * q, a = e / RB, b = e % RB;
                 if (TRANS) sA[a * (RB + 1) + b] = (T)v[q];    // sA[p][a] = L[j0 + p][i0 + a]
                 else sA[b * (RB + 1) + a] = (T)v[q];          // sA[p][a] = L[i0 + a][j0 + p]
             }
         };
-        auto load_y = [&](int jb, T (&v)[4]) {
+        auto load_y = [&](int jb, T (&v)[YPER]) {
             const int64_t j0 = (int64_t)jb * RB;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = t + 256 * q, p = e >> 4, r = e & 15;
+            for (int q = 0; q < YPER; ++q) {
+                const int e = t + NT * q, p = e >> 4, r = e & 15;
                 v[q] = (j0 + p < n && r < nrhs) ? __ldcg(&Y[(j0 + p) * ldy + r]) : (T)0;
             }
         };
-        auto store_y = [&](const T (&v)[4]) {
+        auto store_y = [&](const T (&v)[YPER]) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sY[t + 256 * q] = v[q];
+            for (int q = 0; q < YPER; ++q) sY[t + NT * q] = v[q];
         };
-        T acc[4];
+        // the block's inverse, off the critical path of the sweep
+        {
+            const T* Ib = Inv + (int64_t)bi * RB * RB;
+            for (int e = t; e < RB * RB; e += NT) {
+                const int i = e / RB, j = e % RB;
+                if (TRANS) sI[i * (RB + 1) + j] = Ib[e];     // M[a][p] = Inv[p][a]
+                else sI[j * (RB + 1) + i] = Ib[e];           // M[a][p] = Inv[a][p]
+            }
+        }
+        T acc[4][4];            // partial sum over this group's quarter of every tile
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + row;
-            const int r = cg + 4 * u;
-            acc[u] = (i < n && r < nrhs) ? __ldcg(&Y[i * ldy + r]) : (T)0;
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[c][u] = 0;
+        T bv[RB * MAXRHS / NT];  // this thread's right-hand side entries of block i
+#pragma unroll
+        for (int q = 0; q < RB * MAXRHS / NT; ++q) {
+            const int e = t + NT * q, i = e / MAXRHS, r = e % MAXRHS;
+            bv[q] = (i0 + i < n && r < nrhs) ? __ldcg(&Y[(i0 + i) * ldy + r]) : (T)0;
         }
         if (t == 0) s_known = (nj > 0 && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) ? nj - 1 : -1;
         __syncthreads();
         int known = s_known;
-        double preL[16];
-        T preY[4];
-        load_tile(nj > 0 ? jblk(0) : bi, preL);
+        LT preL[PER];
+        T preY[YPER];
+        if (nj > 0) load_tile(jblk(0), preL);
         bool hy = false;
         if (nj > 0 && known >= 0) { load_y(jblk(0), preY); hy = true; }
         for (int k = 0; k < nj; ++k) {
@@ -152,8 +208,6 @@ __global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict_
             if (k + 1 < nj) {
                 load_tile(jblk(k + 1), preL);
                 if (k + 1 <= known) { load_y(jblk(k + 1), preY); next_y = true; }
-            } else {
-                load_tile(bi, preL);                  // the diagonal tile comes next
             }
             if (!hy) {
                 if (t == 0) {
@@ -166,7 +220,6 @@ __global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict_
                             ok = 0;
                             break;
                         }
-                        __nanosleep(32);
                     }
                     int kn = k;
                     if (ok && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) kn = nj - 1;
@@ -176,84 +229,101 @@ __global__ void __launch_bounds__(256, 2) k_trsv_sweep(const double* __restrict_
                 __syncthreads();
                 if (!s_ok) return;
                 known = s_known;
-                T v[4];
+                T v[YPER];
                 load_y(jblk(k), v);
                 store_y(v);
             }
             __syncthreads();
 #pragma unroll 8
-            for (int p = 0; p < RB; ++p) {
-                const T a = sA[p * (RB + 1) + row];
+            for (int pp = 0; pp < Q; ++pp) {
+                const int p = g * Q + pp;
+                T a[4], yv[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] -= a * sY[p * MAXRHS + cg + 4 * u];
+                for (int c = 0; c < 4; ++c) a[c] = sA[p * (RB + 1) + rg + c * Q];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) yv[u] = sY[p * MAXRHS + 4 * cg + u];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[c][u] += a[c] * yv[u];
             }
             __syncthreads();
             hy = next_y;
         }
-        // diagonal block
-        store_tile(preL);
-        for (int e = t; e < 2 * 32 * 32; e += 256) {
-            const int c = e >> 10, a = (e >> 5) & 31, b = e & 31;
-            const int ci = (int)(i0 / 32) + c;
-            sI[(c * 32 + a) * 33 + b] = (ci < nchunk) ? Inv[((int64_t)ci * 32 + a) * 32 + b] : (T)0;
+        // y_i = M (b_i - sum_j L_ij y_j): combine the groups' partial sums in
+        // group order, then the same split product with M
+        T* red = sA;                             // [4][RB][16], reuses the tile buffer
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                red[(g * RB + rg + c * Q) * MAXRHS + 4 * cg + u] = acc[c][u];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RB * MAXRHS / NT; ++q) {
+            const int e = t + NT * q;
+            T sum = red[e];
+#pragma unroll
+            for (int h = 1; h < 4; ++h) sum += red[h * RB * MAXRHS + e];
+            sY[e] = bv[q] - sum;
+        }
+        __syncthreads();
+        T out[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) out[c][u] = 0;
+#pragma unroll 8
+        for (int pp = 0; pp < Q; ++pp) {
+            const int p = g * Q + pp;
+            T m[4], yv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) m[c] = sI[p * (RB + 1) + rg + c * Q];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) yv[u] = sY[p * MAXRHS + 4 * cg + u];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) out[c][u] += m[c] * yv[u];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sY[row * MAXRHS + cg + 4 * u] = acc[u];
-        __syncthreads();
-        const int q = t >> 3, r0 = t & 7;
-        // first chunk (rows 0..31 for L, 32..63 for L^T)
-        {
-            const int c = TRANS ? 1 : 0, o = 32 * c;
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = r0 + 8 * h;
-                T v = 0;
-                for (int p = 0; p < 32; ++p) {
-                    const T m = TRANS ? sI[(c * 32 + p) * 33 + q] : sI[(c * 32 + q) * 33 + p];
-                    v += m * sY[(o + p) * MAXRHS + r];
-                }
-                sX[(o + q) * MAXRHS + r] = v;
+            for (int u = 0; u < 4; ++u)
+                red[(g * RB + rg + c * Q) * MAXRHS + 4 * cg + u] = out[c][u];
+        __syncthreads();
+        for (int e = t; e < RB * MAXRHS; e += NT) {
+            const int i = e / MAXRHS, r = e % MAXRHS;
+            T sum = red[e];
+#pragma unroll
+            for (int q = 1; q < 4; ++q) sum += red[q * RB * MAXRHS + e];
+            if (i0 + i < n && r < nrhs) Y[(i0 + i) * ldy + r] = sum;
+        }
+        __syncthreads();
+        // the release store orders the CTA's stores of y_i (made visible to
+        // thread 0 by the barrier) before the flag
+        if (t == 0) st_release_u32(&flag[bi], 1u);
+    }
+}
+
+// L32[i][j] = RN(L[i][j]) for j <= i (the strict upper triangle is not
+// written); one CTA per row (grid-stride), four loads in flight per thread.
+__global__ void k_tril_to_f32(const double* L, int64_t ldl, int64_t n, float* L32, int64_t ld32) {
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const double* src = L + i * ldl;
+        float* dst = L32 + i * ld32;
+        for (int64_t j0 = threadIdx.x; j0 <= i; j0 += 4 * (int64_t)blockDim.x) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = j0 + u * (int64_t)blockDim.x;
+                v[u] = j <= i ? src[j] : 0.0;
             }
-        }
-        __syncthreads();
-        // couple the second chunk to the first
-        {
-            const int o2 = TRANS ? 0 : 32, o1 = TRANS ? 32 : 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = r0 + 8 * h;
-                T v = 0;
-                for (int p = 0; p < 32; ++p) {
-                    // L: L[32 + q][p] = sA[p][32 + q];  L^T: L[32 + p][q] = sA[32 + p][q]
-                    const T m = sA[(o1 + p) * (RB + 1) + o2 + q];
-                    v += m * sX[(o1 + p) * MAXRHS + r];
-                }
-                sY[(o2 + q) * MAXRHS + r] -= v;
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = j0 + u * (int64_t)blockDim.x;
+                if (j <= i) dst[j] = (float)v[u];
             }
-        }
-        __syncthreads();
-        {
-            const int c = TRANS ? 0 : 1, o = 32 * c;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = r0 + 8 * h;
-                T v = 0;
-                for (int p = 0; p < 32; ++p) {
-                    const T m = TRANS ? sI[(c * 32 + p) * 33 + q] : sI[(c * 32 + q) * 33 + p];
-                    v += m * sY[(o + p) * MAXRHS + r];
-                }
-                sX[(o + q) * MAXRHS + r] = v;
-            }
-        }
-        __syncthreads();
-        for (int e = t; e < RB * MAXRHS; e += 256) {
-            const int a = e >> 4, r = e & 15;
-            if (i0 + a < n && r < nrhs) Y[(i0 + a) * ldy + r] = sX[e];
-        }
-        __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            st_release_u32(&flag[bi], 1u);
         }
     }
 }
@@ -267,18 +337,21 @@ __global__ void k_copy2d(const S* src, int64_t lds, D* dst, int64_t ldd, int64_t
     dst[i * ldd + j] = (D)src[i * lds + j];
 }
 
-// Split-K partial products of the residual: P[s][i][r] = sum_{p in chunk s} A[i][p] X[p][r].
-__global__ void __launch_bounds__(256) k_resid_partial(const double* A, int64_t lda, int64_t n,
+// Split-K partial products of the residual: P[s][i][r] = sum_{p in chunk s} A[i][p] X[p][r],
+// in the arithmetic of T (double: the FP64 residual and product; float: the
+// FP32 product of GMRES-IR's inner solver, from an FP32 copy of A).
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_partial(const T* A, int64_t lda, int64_t n,
                                                        const double* X, int64_t ldx, int nrhs,
                                                        int64_t kchunk, double* P) {
-    __shared__ double As[32][65];
-    __shared__ double Xs[32][MAXRHS];
+    __shared__ T As[32][65];
+    __shared__ T Xs[32][MAXRHS];
     const int t = threadIdx.x;
     const int64_t i0 = blockIdx.x * 64;
     const int64_t kbeg = blockIdx.y * kchunk;
     const int64_t kend = (kbeg + kchunk < n) ? kbeg + kchunk : n;
     const int row = t & 63, cg = t >> 6;
-    double acc[4] = {0, 0, 0, 0};
+    T acc[4] = {0, 0, 0, 0};
     for (int64_t k0 = kbeg; k0 < kend; k0 += 32) {
         // A is symmetric and only its lower triangle is read: A[i][p] for p <= i,
         // A[p][i] above; whole tiles on one side load coalesced.
@@ -286,29 +359,29 @@ __global__ void __launch_bounds__(256) k_resid_partial(const double* A, int64_t 
             for (int e = t; e < 64 * 32; e += 256) {
                 int a = e >> 5, b = e & 31;
                 int64_t i = i0 + a, p = k0 + b;
-                As[b][a] = (i < n && p < kend) ? A[i * lda + p] : 0.0;
+                As[b][a] = (i < n && p < kend) ? A[i * lda + p] : (T)0;
             }
         } else if (k0 >= i0 + 64) {
             for (int e = t; e < 64 * 32; e += 256) {
                 int b = e >> 6, a = e & 63;
                 int64_t i = i0 + a, p = k0 + b;
-                As[b][a] = (i < n && p < kend) ? A[p * lda + i] : 0.0;
+                As[b][a] = (i < n && p < kend) ? A[p * lda + i] : (T)0;
             }
         } else {
             for (int e = t; e < 64 * 32; e += 256) {
                 int a = e >> 5, b = e & 31;
                 int64_t i = i0 + a, p = k0 + b;
-                As[b][a] = (i < n && p < kend) ? (p <= i ? A[i * lda + p] : A[p * lda + i]) : 0.0;
+                As[b][a] = (i < n && p < kend) ? (p <= i ? A[i * lda + p] : A[p * lda + i]) : (T)0;
             }
         }
         for (int e = t; e < 32 * MAXRHS; e += 256) {
             int p = e / MAXRHS, r = e % MAXRHS;
-            Xs[p][r] = (k0 + p < kend && r < nrhs) ? X[(k0 + p) * ldx + r] : 0.0;
+            Xs[p][r] = (k0 + p < kend && r < nrhs) ? (T)X[(k0 + p) * ldx + r] : (T)0;
         }
         __syncthreads();
 #pragma unroll 8
         for (int p = 0; p < 32; ++p) {
-            double a = As[p][row];
+            const T a = As[p][row];
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] = fma(a, Xs[p][cg + 4 * u], acc[u]);
         }
@@ -319,7 +392,7 @@ __global__ void __launch_bounds__(256) k_resid_partial(const double* A, int64_t 
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int r = cg + 4 * u;
-            if (r < nrhs) P[((int64_t)blockIdx.y * n + i) * MAXRHS + r] = acc[u];
+            if (r < nrhs) P[((int64_t)blockIdx.y * n + i) * MAXRHS + r] = (double)acc[u];
         }
 }
 
@@ -405,40 +478,69 @@ cudaError_t set_attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
     const int bytes = (int)sweep_smem_bytes<T>();
-    cudaError_t e = cudaFuncSetAttribute(k_trsv_sweep<T, 0>,
+    cudaError_t e = cudaFuncSetAttribute(k_trsv_sweep<T, 0, double>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_trsv_sweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
+        e = cudaFuncSetAttribute(k_trsv_sweep<T, 1, double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && sizeof(T) == sizeof(float))
+        e = cudaFuncSetAttribute(k_trsv_sweep<T, 0, float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && sizeof(T) == sizeof(float))
+        e = cudaFuncSetAttribute(k_trsv_sweep<T, 1, float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_block_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)inv_smem_bytes<T>());
     if (e == cudaSuccess) done = true;
     return e;
 }
 
+template <typename T>
+int64_t sweep_blocks(int64_t n) {
+    return (n + SweepCfg<T>::RB - 1) / SweepCfg<T>::RB;
+}
+
 size_t inv_region(int64_t n, bool f64) {
-    const size_t b = (size_t)((n + 31) / 32) * 32 * 32 * (f64 ? sizeof(double) : sizeof(float));
+    const size_t b = f64 ? (size_t)sweep_blocks<double>(n) * 64 * 64 * sizeof(double)
+                         : (size_t)sweep_blocks<float>(n) * 128 * 128 * sizeof(float);
     return (b + 255) / 256 * 256;
 }
 
-size_t sync_words(int64_t n) { return 4 + 2 * (size_t)((n + RB - 1) / RB); }
+size_t sync_words(int64_t n, bool f64) {
+    return 4 + 2 * (size_t)(f64 ? sweep_blocks<double>(n) : sweep_blocks<float>(n));
+}
 
 template <typename T>
-cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, T* Y, int64_t ldy, T* Inv,
-                    cudaStream_t s) {
+cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, const float* L32, T* Y,
+                    int64_t ldy, T* Inv, bool have_inv, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    constexpr bool F64 = sizeof(T) == sizeof(double);
     cudaError_t e = set_attrs<T>();
     if (e != cudaSuccess) return e;
-    unsigned* sync = (unsigned*)((char*)Inv + inv_region(n, sizeof(T) == sizeof(double)));
-    e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * sync_words(n), s);
+    unsigned* sync = (unsigned*)((char*)Inv + inv_region(n, F64));
+    e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * sync_words(n, F64), s);
     if (e != cudaSuccess) return e;
-    k_chunk_inv<T><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(L, ldl, n, Inv);
-    note_launch();
-    const int NB = (int)((n + RB - 1) / RB);
-    const unsigned grid = (unsigned)std::min<int64_t>(NB, 2 * (int64_t)num_sms());
+    const int64_t NB = sweep_blocks<T>(n);
+    if (!have_inv) {
+        k_block_inv<T><<<(unsigned)NB, SweepCfg<T>::RB, inv_smem_bytes<T>(), s>>>(L, ldl, n, Inv);
+        note_launch();
+    }
+    const int per_sm = F64 ? 2 : 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(NB, per_sm * (int64_t)num_sms());
     const size_t smem = sweep_smem_bytes<T>();
-    k_trsv_sweep<T, 0><<<grid, 256, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
-    note_launch();
-    k_trsv_sweep<T, 1><<<grid, 256, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
-    note_launch();
+    constexpr int NT = 4 * SweepCfg<T>::RB;
+    if (!F64 && L32 != nullptr) {   // FP32 tiles: no conversion in the sweep
+        k_trsv_sweep<T, 0, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, sync);
+        note_launch();
+        k_trsv_sweep<T, 1, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, sync);
+        note_launch();
+    } else {
+        k_trsv_sweep<T, 0, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+        note_launch();
+        k_trsv_sweep<T, 1, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+        note_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -447,15 +549,24 @@ cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, T* Y, int
 int potrs_max_rhs() { return MAXRHS; }
 
 cudaError_t launch_potrs_f64(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             double* B, int64_t ldb, double* inv, cudaStream_t s) {
+                             double* B, int64_t ldb, double* inv, cudaStream_t s, bool have_inv) {
     (void)nb;
-    return potrs_t<double>(n, nrhs, L, ldl, B, ldb, inv, s);
+    return potrs_t<double>(n, nrhs, L, ldl, nullptr, B, ldb, inv, have_inv, s);
 }
 
 cudaError_t launch_potrs_f32(int64_t n, int nrhs, int64_t nb, const double* L, int64_t ldl,
-                             float* B, int64_t ldb, float* inv, cudaStream_t s) {
+                             float* B, int64_t ldb, float* inv, cudaStream_t s, bool have_inv,
+                             const float* L32) {
     (void)nb;
-    return potrs_t<float>(n, nrhs, L, ldl, B, ldb, inv, s);
+    return potrs_t<float>(n, nrhs, L, ldl, L32, B, ldb, inv, have_inv, s);
+}
+
+cudaError_t launch_tril_to_f32(const double* L, int64_t ldl, int64_t n, float* L32,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_tril_to_f32<<<(unsigned)std::min<int64_t>(n, 1 << 20), 256, 0, s>>>(L, ldl, n, L32, n);
+    note_launch();
+    return cudaGetLastError();
 }
 
 int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_t* ce) {
@@ -467,7 +578,9 @@ int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_
 }
 
 size_t potrs_inv_bytes(int64_t n, bool f64) {
-    return inv_region(n, f64) + sizeof(unsigned) * sync_words(n);
+    (void)f64;   // room for either arithmetic, so one region serves both
+    return std::max(inv_region(n, true) + sizeof(unsigned) * sync_words(n, true),
+                    inv_region(n, false) + sizeof(unsigned) * sync_words(n, false));
 }
 
 cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
@@ -494,7 +607,7 @@ cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const doubl
                             unsigned long long* xmax, cudaStream_t s) {
     const int64_t kchunk = ((n + nsplit - 1) / nsplit + 31) / 32 * 32;
     dim3 grid((unsigned)((n + 63) / 64), (unsigned)nsplit);
-    k_resid_partial<<<grid, 256, 0, s>>>(A, lda, n, X, ldx, nrhs, kchunk, P);
+    k_resid_partial<double><<<grid, 256, 0, s>>>(A, lda, n, X, ldx, nrhs, kchunk, P);
     note_launch();
     int64_t tot = n * nrhs;
     k_resid_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, B, ldb, X, ldx, nrhs,
@@ -507,7 +620,19 @@ cudaError_t launch_symv(const double* A, int64_t lda, int64_t n, const double* X
                         double* P, int nsplit, cudaStream_t s) {
     const int64_t kchunk = ((n + nsplit - 1) / nsplit + 31) / 32 * 32;
     dim3 grid((unsigned)((n + 63) / 64), (unsigned)nsplit);
-    k_resid_partial<<<grid, 256, 0, s>>>(A, lda, n, X, MAXRHS, MAXRHS, kchunk, P);
+    k_resid_partial<double><<<grid, 256, 0, s>>>(A, lda, n, X, MAXRHS, MAXRHS, kchunk, P);
+    note_launch();
+    const int64_t tot = n * MAXRHS;
+    k_symv_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, Y);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symv_f32(const float* A, int64_t lda, int64_t n, const double* X, double* Y,
+                            double* P, int nsplit, cudaStream_t s) {
+    const int64_t kchunk = ((n + nsplit - 1) / nsplit + 31) / 32 * 32;
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)nsplit);
+    k_resid_partial<float><<<grid, 256, 0, s>>>(A, lda, n, X, MAXRHS, MAXRHS, kchunk, P);
     note_launch();
     const int64_t tot = n * MAXRHS;
     k_symv_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, Y);

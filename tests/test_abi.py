@@ -64,8 +64,8 @@ def test_gmres_ir_workspace_query_and_arguments_on_host():
     L = abft.lib()
     need = ctypes.c_size_t(0)
     args = lambda m, itol, shift: (1024, 16, 128, abft.MIXED_BF16, abft.FULL, None, 1024, None, 1024,
-                                   None, 16, None, 16, 1e-12, 10, m, itol, shift, 1, 0, None, 0,
-                                   1.0, None, None, ctypes.byref(need), None)
+                                   None, 16, None, 16, 1e-12, 10, m, itol, shift, 1, 0, 0, None,
+                                   0, 1.0, None, None, ctypes.byref(need), None)
     assert L.abft_posv_gmres_ir(*args(30, 1e-6, -1.0)) == 0
     # the Krylov basis (m + 1 blocks of n x 16 doubles) is part of the workspace
     assert need.value >= 31 * 1024 * 16 * 8
