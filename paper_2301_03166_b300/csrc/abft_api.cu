@@ -87,8 +87,17 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of the pieces of a Cholesky workspace.
+// Diagonal blocks wider than kPdChunk are factored in chunks with a split-K
+// update between them (chol_pd).
+constexpr int64_t kPdChunk = 256;
+constexpr int kPdSplit = 8;
+
+size_t pd_part_bytes(int64_t nb) {
+    return nb > kPdChunk ? sizeof(double) * kPdSplit * (size_t)kPdChunk * kPdChunk : 0;
+}
+
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, pdpart, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
@@ -110,6 +119,7 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false) {
     w.lq = off; off = align_up(off + (mixed ? sizeof(uint16_t) * (size_t)n * (size_t)nb : 0));
     w.sig = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)w.nt : 0));
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
+    w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.total = off;
     return w;
 }
@@ -154,14 +164,20 @@ int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s, bool l
     return ABFT_OK;
 }
 
-// Factor the kb x kb diagonal block at A (lower) in 64-column chunks.
-cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* st, cudaStream_t s) {
-    for (int64_t c = 0; c < kb; c += 64) {
-        int64_t w = std::min<int64_t>(64, kb - c);
+// Factor the kb x kb diagonal block at A (lower) and check it against the
+// carried column checksum cc (check != 0): one cluster launch for kb <= 256;
+// larger blocks in 256-column chunks (cluster factorization of the chunk,
+// panel solve of the rows below it, split-K update of the rest of the block)
+// followed by the separate check.  part: split-K scratch (pd_part_bytes).
+cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, const double* cc, int check,
+                    int step, double* part, DevStatus* st, cudaStream_t s) {
+    if (kb <= kPdChunk) return launch_potrf_pd_cluster(A, lda, kb, K0, cc, step, check, st, s);
+    for (int64_t c = 0; c < kb; c += kPdChunk) {
+        const int64_t w = std::min(kPdChunk, kb - c);
         double* Lc = A + c * lda + c;
-        cudaError_t e = launch_potf2_small(Lc, lda, w, K0 + c, st, s);
+        cudaError_t e = launch_potrf_pd_cluster(Lc, lda, w, K0 + c, nullptr, step, 0, st, s);
         if (e != cudaSuccess) return e;
-        int64_t r = kb - c - w;
+        const int64_t r = kb - c - w;
         if (r <= 0) continue;
         TrsmSeg seg{Lc + w * lda, lda, r};
         e = launch_trsm_rlt(Lc, lda, w, &seg, 1, nullptr, nullptr, st, s);
@@ -172,9 +188,10 @@ cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, DevStatus* s
         g.C = Lc + w * lda + w; g.ldc = lda;
         g.M = r; g.N = r; g.K = w;
         g.g = 64; g.row0 = 0; g.col0 = 0;
-        e = launch_gemm_f64(&g, 1, 0, 0, nullptr, 0, st, s);
+        e = launch_gemm_f64_splitk(g, 0, 0, kPdSplit, part, st, s);
         if (e != cudaSuccess) return e;
     }
+    if (check) return launch_chol_pd_check(A, lda, kb, cc, K0, step, nullptr, MODE_FULL, st, s);
     return cudaSuccess;
 }
 
@@ -224,10 +241,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
         }
         // PD and its checksum check
         timing_mark(PH_PD, 1, s);
-        ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, st, s));
-        if (check)
-            ABFT_CUDA_TRY(launch_chol_pd_check(Akk, lda, kb, CS + (k * nc) * n + K0, K0, (int)k,
-                                               nullptr, mk, st, s));
+        ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, check ? CS + (k * nc) * n + K0 : nullptr,
+                              check ? 1 : 0, (int)k, (double*)(base + w.pdpart), st, s));
         timing_mark(PH_PD, 0, s);
         if (m <= 0) break;
         // PU: panel rows and the carried checksum rows through X L_kk^T = B

@@ -150,6 +150,12 @@ cudaError_t launch_gemm_f64_splitk(const GemmSeg& seg, int a_kmajor, int b_kmajo
 
 cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_base,
                                DevStatus* st, cudaStream_t s);
+// FP64 factorization of a kb x kb (kb <= 256) diagonal block by one thread-block
+// cluster; check != 0 then tests it against the carried column checksum cc
+// (k_pd_cluster.cu).  A non-positive pivot sets info = K0 + column + 1.
+cudaError_t launch_potrf_pd_cluster(double* A, int64_t lda, int64_t kb, int64_t K0,
+                                    const double* cc, int step, int check, DevStatus* st,
+                                    cudaStream_t s);
 // X L^T = B (nt = false) or X L = B (nt = true, FP64 only) for the rows of up
 // to two row segments (in place); L lower nb x nb.
 // If v != NULL, x[i] = B_i . v is stored for the rows of segment 0 before the solve.

@@ -157,6 +157,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Decode the idx-th tile of the lower block triangle: block pairs (BI >= BJ)
 // in row-major order, r x r 128-tiles inside each g x g block pair.
+// Exact float -> double by bit manipulation for normal values (rebias the
+// exponent, widen the mantissa), so the conversion stays off the FP64 pipe;
+// zero, subnormals, infinities and NaN take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+        const uint32_t lo = (b & 7u) << 29;
+        return __hiloint2double((int)hi, (int)lo);
+    }
+    return (double)x;
+}
+
 __device__ __forceinline__ void lower_tile(int64_t idx, int64_t r, int64_t& ti, int64_t& tj) {
     const int64_t r2 = r * r, pair = idx / r2, sub = idx % r2;
     int64_t a = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
@@ -300,11 +314,14 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
             asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
             if (!*abort_flag) {
                 const int64_t i0 = ti * TM, j0 = tj * TN;
-                // FP64 read-modify-write of the tile, 4 rows x 4 column chunks in flight
+                // a 128 x 128 tile lies in one g x g block (g is a multiple of 128 and
+                // the trailing matrix starts on a block boundary): one scale per tile
+                const double sc = a.sig[(i0 + a.off) / a.g] * a.sig[(j0 + a.off) / a.g];
+                // FP64 read-modify-write of the tile, 4 rows x 4 column chunks in
+                // flight; C - sc * acc is one FMA on the FP64 pipe per element
                 for (int rb = ew; rb < TM; rb += EPI_WARPS * 4) {
                     double cv[4][4];
                     double* ptr[4][4];
-                    double sc[4][4];
                     int rrv[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -312,15 +329,11 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                         rrv[u] = rr;
                         const int64_t i = i0 + rr;
                         const bool rowok = rr < TM && i < a.M;
-                        const int64_t bi = rowok ? (i + a.off) / a.g : 0;
-                        const double si = rowok ? a.sig[bi] : 0.0;
 #pragma unroll
                         for (int t4 = 0; t4 < TN / 32; ++t4) {
                             const int64_t j = j0 + lane + 32 * t4;
-                            const int64_t bj = (j + a.off) / a.g;
-                            const bool okj = rowok && j < a.M && bi >= bj;
+                            const bool okj = rowok && j < a.M;
                             ptr[u][t4] = okj ? a.C + i * a.ldc + j : nullptr;
-                            sc[u][t4] = okj ? si * a.sig[bj] : 0.0;
                             cv[u][t4] = okj ? *ptr[u][t4] : 0.0;
                         }
                     }
@@ -329,7 +342,8 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
 #pragma unroll
                         for (int t4 = 0; t4 < TN / 32; ++t4) {
                             if (ptr[u][t4] == nullptr) continue;
-                            double v = cv[u][t4] - sc[u][t4] * (double)stg[rrv[u] * STG_LD + lane + 32 * t4];
+                            const double x = f32_to_f64_exact(stg[rrv[u] * STG_LD + lane + 32 * t4]);
+                            double v = fma(-sc, x, cv[u][t4]);
                             const int64_t i = i0 + rrv[u], j = j0 + lane + 32 * t4;
                             for (int f = 0; f < a.ncf; ++f)
                                 if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;

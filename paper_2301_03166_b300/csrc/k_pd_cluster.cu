@@ -1,0 +1,286 @@
+// k_pd_cluster.cu -- FP64 factorization of a diagonal block of the blocked
+// Cholesky (Sec. 2.1 PD) by one thread-block cluster, with the PD checksum
+// check (Sec. 3.1.2) fused.
+//
+// B300 runs FP64 at about two lanes per clock per SM, so a kb x kb block
+// (kb <= 256: kb^3 / 6 = 2.8 M FMA) takes most of a millisecond on one SM.
+// Here the block's lower triangle is held as 32 x 32 tiles spread over the
+// shared memory of the CL CTAs of a cluster (tile id = q (q + 1) / 2 + r,
+// home CTA id % CL, slot id / CL; rows past kb are the identity) and factored
+// right-looking by tile columns p = 0 .. NT - 1:
+//   A  the home CTA of tile (p, p) factors it (unblocked, true divisions);
+//   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
+//      per row (lane l holds x_l), spread over every warp of the cluster;
+//   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
+//      of 16 rows, are dealt round-robin to the CTAs; operands are fetched
+//      from their home CTAs through distributed shared memory.
+// The phases are separated by cluster barriers (hardware barriers, no spin).
+// Then every CTA writes its tiles back to A, and CTA 0 checks the PD checksum
+// relation (1^T L) L^T = c^T against the carried column checksum cc.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace abft {
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int PT = 32;             // tile edge
+constexpr int PLD = 33;            // padded row stride (doubles)
+constexpr int PMAXT = 8;           // tiles per side: kb <= 256
+constexpr int PTHREADS = 256;
+constexpr int PWARPS = PTHREADS / 32;
+constexpr int TILE = PT * PLD;
+
+template <int CL>
+__host__ __device__ constexpr int pd_slots() {
+    return (PMAXT * (PMAXT + 1) / 2 + CL - 1) / CL;
+}
+
+template <int CL>
+constexpr size_t pd_smem() {
+    return sizeof(double) * (size_t)TILE * (pd_slots<CL>() + 3);
+}
+
+__device__ __forceinline__ void tile_of(int id, int& q, int& r) {
+    q = 0;
+    while ((q + 1) * (q + 2) / 2 <= id) ++q;
+    r = id - q * (q + 1) / 2;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int64_t lda, int kb,
+                                                                  int64_t K0, const double* cc,
+                                                                  int step, int check,
+                                                                  DevStatus* st) {
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) double pd_sm[];
+    double* home = pd_sm;                              // pd_slots tiles
+    double* sD = pd_sm + pd_slots<CL>() * TILE;        // copy of L(p, p)
+    double* sQ = sD + TILE;                            // operand copies for phase C
+    double* sR = sQ + TILE;
+    __shared__ int s_fail;
+    __shared__ double s_cs[PMAXT * PT];
+    if (st->info != 0) return;                         // same answer in every CTA
+    const int me = (int)cl.block_rank();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int NT = (kb + PT - 1) / PT, NTILE = NT * (NT + 1) / 2;
+    auto tile_ptr = [&](int q, int r) -> double* {
+        const int id = q * (q + 1) / 2 + r;
+        return cl.map_shared_rank(home + (id / CL) * TILE, id % CL);
+    };
+    // this CTA's tiles from A (the strict upper part of diagonal tiles is not
+    // used; rows and columns past kb are the identity)
+    for (int id = me; id < NTILE; id += CL) {
+        int q, r;
+        tile_of(id, q, r);
+        double* T = home + (id / CL) * TILE;
+        for (int e = t; e < PT * PT; e += PTHREADS) {
+            const int i = e >> 5, j = e & 31, gi = q * PT + i, gj = r * PT + j;
+            double v;
+            if (gi < kb && gj < kb) v = (q > r || j <= i) ? A[(int64_t)gi * lda + gj] : 0.0;
+            else v = gi == gj ? 1.0 : 0.0;
+            T[i * PLD + j] = v;
+        }
+    }
+    if (t == 0) s_fail = -1;
+    cl.sync();
+    int fail = -1;
+    for (int p = 0; p < NT; ++p) {
+        const int idp = p * (p + 1) / 2 + p;
+        // A: unblocked Cholesky of the diagonal tile in its home CTA
+        if (me == idp % CL) {
+            double* D = home + (idp / CL) * TILE;
+            for (int j = 0; j < PT; ++j) {
+                if (t == 0) {
+                    const double d = D[j * PLD + j];
+                    if (!(d > 0.0)) s_fail = j;
+                    else D[j * PLD + j] = sqrt(d);
+                }
+                __syncthreads();
+                if (s_fail >= 0) break;
+                const double sj = D[j * PLD + j];
+                if (t > j && t < PT) D[t * PLD + j] = D[t * PLD + j] / sj;
+                __syncthreads();
+                const int m = PT - 1 - j;
+                for (int e = t; e < m * (m + 1) / 2; e += PTHREADS) {
+                    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                    while (a * (a + 1) / 2 > e) --a;
+                    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+                    const int b = e - a * (a + 1) / 2;
+                    const int i = j + 1 + a, l = j + 1 + b;
+                    D[i * PLD + l] -= D[i * PLD + j] * D[l * PLD + j];
+                }
+                __syncthreads();
+            }
+        }
+        cl.sync();
+        {
+            const int f = *cl.map_shared_rank(&s_fail, idp % CL);
+            if (f >= 0) {
+                fail = p * PT + f;
+                break;
+            }
+        }
+        const int below = NT - 1 - p;
+        if (below == 0) break;
+        // B: rows of the panel tiles below, x L_pp^T = a, one warp per row
+        {
+            const double* Dr = tile_ptr(p, p);
+            for (int e = t; e < PT * PT; e += PTHREADS) sD[(e >> 5) * PLD + (e & 31)] = Dr[(e >> 5) * PLD + (e & 31)];
+            __syncthreads();
+            const int rows = below * PT;
+            for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
+                double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
+                double x = X[lane];
+                for (int j = 0; j < PT; ++j) {
+                    if (lane == j) x = x / sD[j * PLD + j];
+                    const double xj = __shfl_sync(0xffffffffu, x, j);
+                    if (lane > j) x -= xj * sD[lane * PLD + j];
+                }
+                X[lane] = x;
+            }
+        }
+        cl.sync();
+        // C: trailing tiles in halves of 16 rows
+        {
+            const int nitem = below * (below + 1);          // tiles x 2 halves
+            for (int w = me; w < nitem; w += CL) {
+                const int tid = w >> 1, half = w & 1;
+                int a, b;
+                tile_of(tid, a, b);
+                const int q = p + 1 + a, r = p + 1 + b;
+                const double* Lq = tile_ptr(q, p);
+                const double* Lr = tile_ptr(r, p);
+                for (int e = t; e < 16 * PT; e += PTHREADS) {
+                    const int i = 16 * half + (e >> 5), j = e & 31;
+                    sQ[(e >> 5) * PLD + j] = Lq[i * PLD + j];
+                }
+                for (int e = t; e < PT * PT; e += PTHREADS) sR[(e >> 5) * PLD + (e & 31)] = Lr[(e >> 5) * PLD + (e & 31)];
+                __syncthreads();
+                double* C = tile_ptr(q, r);
+                // thread: row i (16) x columns l = (t & 15) + 16 c (2)
+                const int i = t >> 4, l0 = t & 15;
+                double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 8
+                for (int k = 0; k < PT; ++k) {
+                    const double lq = sQ[i * PLD + k];
+                    acc0 = fma(lq, sR[l0 * PLD + k], acc0);
+                    acc1 = fma(lq, sR[(l0 + 16) * PLD + k], acc1);
+                }
+                const int ci = 16 * half + i;
+                C[ci * PLD + l0] -= acc0;
+                C[ci * PLD + l0 + 16] -= acc1;
+                __syncthreads();
+            }
+        }
+        cl.sync();
+    }
+    // write back (the strict upper triangle of A is left as it is)
+    if (fail < 0) {
+        for (int id = me; id < NTILE; id += CL) {
+            int q, r;
+            tile_of(id, q, r);
+            const double* T = home + (id / CL) * TILE;
+            for (int e = t; e < PT * PT; e += PTHREADS) {
+                const int i = e >> 5, j = e & 31, gi = q * PT + i, gj = r * PT + j;
+                if (gi < kb && gj < kb && (q > r || j <= i)) A[(int64_t)gi * lda + gj] = T[i * PLD + j];
+            }
+        }
+    } else if (me == 0 && t == 0) {
+        atomicCAS(&st->info, 0, (int)(K0 + fail + 1));
+    }
+    cl.sync();
+    if (fail >= 0 || !check || me != 0) return;
+    // PD check: y_j = sum_{p <= j} (sum_{q >= p} L[q][p]) L[j][p] against cc[j]
+    for (int p = t; p < kb; p += PTHREADS) {
+        double s = 0.0;
+        for (int q = p; q < kb; ++q) s += A[(int64_t)q * lda + p];
+        s_cs[p] = s;
+    }
+    __syncthreads();
+    const double tau = st->tau;
+    for (int j = warp; j < kb; j += PWARPS) {
+        double y = 0.0;
+        for (int p = lane; p <= j; p += 32) y = fma(s_cs[p], A[(int64_t)j * lda + p], y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        if (lane == 0) {
+            const double d = y - cc[j];
+            if (!(fabs(d) <= tau)) {
+                atomicAdd(&st->detected, 1ull);
+                atomicAdd(&st->uncorrectable, 1ull);
+                record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+            }
+        }
+    }
+}
+
+template <int CL>
+cudaError_t launch_cl(double* A, int64_t lda, int kb, int64_t K0, const double* cc, int step,
+                      int check, DevStatus* st, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.blockDim = dim3(PTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = pd_smem<CL>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_potrf_pd_cluster<CL>, A, lda, kb, K0, cc, step, check, st);
+}
+
+// Cluster size: 16 CTAs where the device runs such clusters, else 8.
+int pd_cluster_size() {
+    static int size = 0;
+    if (size) return size;
+    size = 8;
+    if (cudaFuncSetAttribute(k_potrf_pd_cluster<16>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) == cudaSuccess &&
+        cudaFuncSetAttribute(k_potrf_pd_cluster<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pd_smem<16>()) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16, 1, 1);
+        cfg.blockDim = dim3(PTHREADS, 1, 1);
+        cfg.dynamicSmemBytes = pd_smem<16>();
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_pd_cluster<16>, &cfg) == cudaSuccess &&
+            nclusters > 0)
+            size = 16;
+    }
+    cudaGetLastError();   // a refused non-portable size is not an error of the caller
+    if (size == 8)
+        cudaFuncSetAttribute(k_potrf_pd_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pd_smem<8>());
+    return size;
+}
+
+}  // namespace
+
+cudaError_t launch_potrf_pd_cluster(double* A, int64_t lda, int64_t kb, int64_t K0,
+                                    const double* cc, int step, int check, DevStatus* st,
+                                    cudaStream_t s) {
+    if (kb <= 0) return cudaSuccess;
+    if (kb > PMAXT * PT) return cudaErrorInvalidValue;
+    const cudaError_t e = pd_cluster_size() == 16
+                              ? launch_cl<16>(A, lda, (int)kb, K0, cc, step, check, st, s)
+                              : launch_cl<8>(A, lda, (int)kb, K0, cc, step, check, st, s);
+    note_launch();
+    return e;
+}
+
+}  // namespace abft
