@@ -10,7 +10,11 @@
 // right-looking by tile columns p = 0 .. NT - 1:
 //   A  the home CTA of tile (p, p) factors it (unblocked, true divisions);
 //   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
-//      per row (lane l holds x_l), spread over every warp of the cluster;
+//      per row (lane l holds x_l), spread over every warp of the cluster; the
+//      division by L_jj is a multiplication by its reciprocal, formed once per
+//      tile (one FP64 division per column instead of one per row: on B300 a
+//      dependent FP64 division costs hundreds of clocks; the reciprocals of the
+//      power-of-two pivots of exact integer cases are exact);
 //   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
 //      of 16 rows, are dealt round-robin to the CTAs; operands are fetched
 //      from their home CTAs through distributed shared memory.
@@ -63,6 +67,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     double* sQ = sD + TILE;                            // operand copies for phase C
     double* sR = sQ + TILE;
     __shared__ int s_fail;
+    __shared__ double s_rinv[PT];                      // 1 / L_jj of the current diagonal tile
     __shared__ double s_cs[PMAXT * PT];
     if (st->info != 0) return;                         // same answer in every CTA
     const int me = (int)cl.block_rank();
@@ -132,12 +137,14 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             const double* Dr = tile_ptr(p, p);
             for (int e = t; e < PT * PT; e += PTHREADS) sD[(e >> 5) * PLD + (e & 31)] = Dr[(e >> 5) * PLD + (e & 31)];
             __syncthreads();
+            if (t < PT) s_rinv[t] = 1.0 / sD[t * PLD + t];
+            __syncthreads();
             const int rows = below * PT;
             for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
                 double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
                 double x = X[lane];
                 for (int j = 0; j < PT; ++j) {
-                    if (lane == j) x = x / sD[j * PLD + j];
+                    if (lane == j) x *= s_rinv[j];
                     const double xj = __shfl_sync(0xffffffffu, x, j);
                     if (lane > j) x -= xj * sD[lane * PLD + j];
                 }
