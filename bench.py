@@ -51,6 +51,15 @@ def parse():
                    help="add the conditioned mixed-precision solves: A = Q diag(sigma) Q^T with "
                         "kappa 1e2, 1e6, 1e10, block 512, GMRES-IR (BF16 / FP16) vs the FP64 form")
     p.add_argument("--cond-n", type=int, default=16384)
+    p.add_argument("--campaign", action="store_true",
+                   help="add the fault campaign: share of correct factorizations and time per "
+                        "factorization for no / single-side / full / adaptive checksums")
+    p.add_argument("--campaign-trials", type=int, default=60)
+    p.add_argument("--profile-case", default=None,
+                   choices=["fp64", "mixed-bf16", "mixed-f16", "potrs-f32"],
+                   help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
+                        "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
+                        "refinement, or an FP32 two-sweep solve with the FP64 factor; at --n, --nb")
     return p.parse_args()
 
 
@@ -388,6 +397,77 @@ def run_ours(args, ws, rank, local):
             del Ac, Lc, X64, R64
         del Bc, Xc
 
+    campaign = None
+    if args.campaign:
+        # Fault campaign (Sec. 3.1.2 / E5 of the paper, with error rates as
+        # inputs instead of overclocking): errors arrive as Poisson processes
+        # per second of the factorization, with rates that rise through it --
+        # none in steps 0-4, 0D errors in steps 5-9, 0D and 1D errors in steps
+        # 10-14 (expected counts 0.8, then 0.5 + 0.3) -- and strike uniformly
+        # over the trailing block triangle of their step.  Each trial factors
+        # the same matrix under each policy; it is correct when no error is left
+        # in the factor (max |L - L_clean| <= 1e-10 max |L_clean|).
+        ncp, nbp = 4096, 256
+        Np = ncp // nbp
+        Ap = W.spd_mmt_torch(ncp, seed=1000 + ncp, device=dev)
+        Wp = torch.empty_like(Ap)
+        def fact(modes, flist=()):
+            Wp.copy_(Ap)
+            return abft.potrf_sched(Wp, nbp, modes, faults=flist, workspace=wsp, check=False)
+        fact([abft.NONE] * Np)
+        Lclean = torch.tril(Wp).clone()
+        lmax = float(Lclean.abs().max())
+        # per-step time, predicted from the step's share of the update flops
+        t_all, _ = timed(lambda: fact([abft.NONE] * Np), 3, 1)
+        flk = np.array([(ncp - (k + 1) * nbp) ** 2 * nbp + nbp ** 3 for k in range(Np)],
+                       dtype=np.float64)
+        Tk = (t_all * 1e-3) * flk / flk.sum()
+        segments = [(0, 5, 0.0, 0.0), (5, 10, 0.8, 0.0), (10, 15, 0.5, 0.3)]
+        lam_k = np.zeros((Np, 3))
+        modes_ad = [abft.NONE] * Np
+        cov_ad = [1.0] * Np
+        for k0, k1, mu0, mu1 in segments:
+            ts = float(Tk[k0:k1].sum())
+            lam = (mu0 / ts, mu1 / ts, 0.0)
+            lam_k[k0:k1] = lam
+            m_seg, c_seg = abft.adaptive_modes(ncp, nbp, lam, 0.999999, Tk.tolist())
+            modes_ad[k0:k1] = m_seg[k0:k1]
+            cov_ad[k0:k1] = c_seg[k0:k1]
+        policies = {"none": [abft.NONE] * Np, "single": [abft.SINGLE] * Np,
+                    "full": [abft.FULL] * Np, "adaptive": modes_ad}
+        r = W.rng(7000)
+        trials = []
+        for t in range(args.campaign_trials):
+            fl_t = []
+            for k in range(Np - 1):
+                T0 = (k + 1) * nbp
+                for mu, kinds in ((lam_k[k, 0] * Tk[k], (abft.F_MEMORY,)),
+                                  (lam_k[k, 1] * Tk[k], (abft.F_ROW1D, abft.F_COL1D))):
+                    for _ in range(int(r.poisson(mu))):
+                        row = int(r.integers(T0, ncp))
+                        col = int(r.integers(T0, min(ncp, (row // nbp + 1) * nbp)))
+                        kind = kinds[int(r.integers(0, len(kinds)))]
+                        fl_t.append((k, kind, row, col, float(r.choice([-1.0, 1.0]) * 1e2)))
+            trials.append(fl_t)
+        campaign = {"n": ncp, "nb": nbp, "trials": len(trials),
+                    "expected_errors": {"steps_0_4": 0.0, "steps_5_9_0d": 0.8,
+                                        "steps_10_14_0d": 0.5, "steps_10_14_1d": 0.3},
+                    "fc_desired": 0.999999, "adaptive_modes": modes_ad,
+                    "adaptive_min_coverage": float(min(cov_ad)),
+                    "errors_per_trial": float(np.mean([len(x) for x in trials]))}
+        for name, modes in policies.items():
+            ok = 0
+            for fl_t in trials:
+                rc_t, _ = fact(modes, fl_t)
+                good = rc_t == 0 and float((torch.tril(Wp) - Lclean).abs().max()) <= 1e-10 * lmax
+                ok += int(good)
+            ms_p, _ = timed(lambda: fact(modes), 3, 1)
+            campaign[name] = {"correct_pct": 100.0 * ok / len(trials), "ms_clean": ms_p}
+        for name in ("single", "full", "adaptive"):
+            campaign[name]["overhead_pct_vs_none"] = 100.0 * (
+                campaign[name]["ms_clean"] / campaign["none"]["ms_clean"] - 1.0)
+        del Ap, Wp, Lclean
+
     lu_qr = None
     if not args.no_lu_qr:
         lu_qr = {}
@@ -507,15 +587,49 @@ def run_ours(args, ws, rank, local):
             "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
-            "mixed_precision_ir": mixed, "conditioned": conditioned, "lu_qr": lu_qr,
+            "mixed_precision_ir": mixed, "conditioned": conditioned, "campaign": campaign,
+            "lu_qr": lu_qr,
             "batched": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
 
 
+def profile_case(args):
+    """One case, warm-up then once, for a profiler; the same inputs as the
+    benchmark's."""
+    from paper_2301_03166_b300 import abft
+    from paper_2301_03166_b300 import workloads as W
+    dev = torch.device("cuda:0")
+    n, nb = args.n, args.nb
+    A0 = W.spd_mmt_torch(n, seed=1000 + n, device=dev)
+    A = torch.empty_like(A0)
+    faults = W.fault_schedule(n, nb, "cholesky", seed=2000 + n)
+    wsp = abft.Workspace()
+    B = torch.from_numpy(W.rhs(n, 16, seed=1003)).to(dev)
+    X = torch.empty_like(B)
+    if args.profile_case == "potrs-f32":
+        A.copy_(A0)
+        abft.potrf(A, nb, abft.FULL, workspace=wsp)
+    for _ in range(2):
+        if args.profile_case == "fp64":
+            A.copy_(A0)
+            abft.potrf(A, nb, abft.FULL, faults=faults, workspace=wsp)
+        elif args.profile_case == "potrs-f32":
+            X.copy_(B)
+            abft.potrs(A, X, nb, abft.F32)
+        else:
+            dt = abft.MIXED_BF16 if args.profile_case == "mixed-bf16" else abft.MIXED_F16
+            abft.posv_ir(A0, B, nb, dt, abft.FULL, tol=1e-12, maxit=100, faults=faults, L=A,
+                         X=X, workspace=wsp)
+    torch.cuda.synchronize(dev)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -157,18 +157,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Decode the idx-th tile of the lower block triangle: block pairs (BI >= BJ)
 // in row-major order, r x r 128-tiles inside each g x g block pair.
-// Exact float -> double by bit manipulation for normal values (rebias the
-// exponent, widen the mantissa), so the conversion stays off the FP64 pipe;
-// zero, subnormals, infinities and NaN take the hardware conversion.
+// Exact float -> double with integer operations only, so the widening stays
+// off B300's slow FP64 pipe: rebias the exponent and widen the mantissa;
+// subnormals are normalized with a count of leading zeros; zero, infinities
+// and NaN keep their class.
 __device__ __forceinline__ double f32_to_f64_exact(float x) {
     const uint32_t b = __float_as_uint(x);
-    const uint32_t e = (b >> 23) & 0xffu;
-    if (e - 1u < 254u) {
-        const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-        const uint32_t lo = (b & 7u) << 29;
-        return __hiloint2double((int)hi, (int)lo);
+    const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+    uint32_t m = b & 0x7fffffu, ed;
+    if (e == 0xffu) {
+        ed = 0x7ffu;
+    } else if (e != 0u) {
+        ed = e + 896u;                         // (e - 127) + 1023
+    } else if (m == 0u) {
+        ed = 0u;
+    } else {                                   // m 2^-149, leading one at bit 31 - clz
+        const uint32_t sh = (uint32_t)__clz((int)m) - 8u;
+        m = (m << sh) & 0x7fffffu;
+        ed = 897u - sh;                        // (-126 - sh) + 1023
     }
-    return (double)x;
+    const uint32_t hi = sign | (ed << 20) | (m >> 3);
+    const uint32_t lo = m << 29;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ void lower_tile(int64_t idx, int64_t r, int64_t& ti, int64_t& tj) {
