@@ -45,7 +45,11 @@ typedef enum {
     ABFT_F64 = 0,        /* FP64 everywhere */
     ABFT_F32 = 1,        /* reserved */
     ABFT_MIXED_BF16 = 2, /* TMU inputs BF16 with per-tile power-of-two scales, FP32 accumulate */
-    ABFT_MIXED_F16 = 3   /* TMU inputs FP16 with per-tile power-of-two scales, FP32 accumulate */
+    ABFT_MIXED_F16 = 3,  /* TMU inputs FP16 with per-tile power-of-two scales, FP32 accumulate */
+    ABFT_F64_EMU = 4     /* abft_potrf only: FP64-accurate TMU from exact products of BF16
+                            slices on the tensor cores (7 x 7-bit slices per element under
+                            a power-of-two row scale, 28 slice pairs, integer recombination;
+                            nb = 128 or 256); PD, PU, checksum borders and verify in FP64 */
 } abft_dtype;
 
 /* Checksum strength (Sec. 3.1.2: single-side vs full checksum ABFT). */

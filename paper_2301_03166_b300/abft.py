@@ -13,7 +13,7 @@ import torch
 
 from . import build as _build
 
-F64, F32, MIXED_BF16, MIXED_F16 = 0, 1, 2, 3
+F64, F32, MIXED_BF16, MIXED_F16, F64_EMU = 0, 1, 2, 3, 4
 NONE, SINGLE, FULL = 0, 1, 2
 F_MEMORY, F_COMPUTE, F_ROW1D, F_COL1D, F_PANEL = 0, 1, 2, 3, 4
 E_0D, E_ROW, E_COL, E_UNCORR, E_CKSUM, E_PD = 0, 1, 2, 3, 4, 5

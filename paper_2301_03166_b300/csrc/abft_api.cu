@@ -97,12 +97,12 @@ size_t pd_part_bytes(int64_t nb) {
 }
 
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, pdpart, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, pdpart, eslice, eex, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
 
-CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false) {
+CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = false) {
     CholWs w{};
     w.nt = (n + nb - 1) / nb;
     // column sums and weighted column sums of every block row, in both modes
@@ -120,6 +120,8 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false) {
     w.sig = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)w.nt : 0));
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
+    w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
+    w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)n : 0));
     w.total = off;
     return w;
 }
@@ -204,6 +206,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                const abft_fault* faults, int32_t nfaults, double tau_scale, const CholWs& w,
                char* base, cudaStream_t s, int32_t dtype) {
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    const bool emu = dtype == ABFT_F64_EMU;
     const int bf16 = dtype == ABFT_MIXED_BF16 ? 1 : 0;
     uint16_t* Lq = (uint16_t*)(base + w.lq);
     double* sig = (double*)(base + w.sig);
@@ -261,7 +264,39 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ABFT_CUDA_TRY(launch_verify(ts, MODE_SINGLE, (int)k, st, s));
         }
         timing_mark(PH_PU, 0, s);
-        if (mixed) {
+        if (emu) {
+            // FP64-accurate TMU from exact BF16 slice products; checksum borders in FP64
+            timing_mark(PH_TMU, 1, s);
+            uint16_t* Sl = (uint16_t*)(base + w.eslice);
+            int* ex = (int*)(base + w.eex);
+            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, Sl, ex, s));
+            ComputeFault ecf[MAX_CF];
+            int encf = 0;
+            for (int f = 0; f < nfaults && encf < MAX_CF; ++f)
+                if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                    ecf[encf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
+            ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, m, kb, A + T0 * lda + T0, lda, g, ecf, encf, st, s));
+            if (check) {
+                GemmSeg bs[2] = {};
+                int nbs = 0;
+                {   // border rows: c_I -= s_I L_J^T (and the weighted rows)
+                    GemmSeg& b = bs[nbs++];
+                    b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
+                    b.B = A + T0 * lda + K0; b.ldb = lda;
+                    b.C = CS + ((k + 1) * nc) * n + T0; b.ldc = n;
+                    b.M = (nt - k - 1) * nc; b.N = m; b.K = kb;
+                }
+                if (full) {   // border columns: r_I -= L_I s_J^T
+                    GemmSeg& b = bs[nbs++];
+                    b.A = A + T0 * lda + K0; b.lda = lda;
+                    b.B = CS + ((k + 1) * nc) * n + K0; b.ldb = nc * n;
+                    b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
+                    b.M = m; b.N = nt - k - 1; b.K = kb;
+                }
+                ABFT_CUDA_TRY(launch_gemm_f64(bs, nbs, 0, 0, nullptr, 0, st, s));
+            }
+            timing_mark(PH_TMU, 0, s);
+        } else if (mixed) {
             // TMU on the tensor cores: quantized panel, FP32 accumulation, FP64 C
             const int64_t ncq = nc > 0 ? nc : 1;
             timing_mark(PH_TMU, 1, s);
@@ -1476,9 +1511,11 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
                void* ws, size_t* ws_bytes, void* stream) {
     if (n < 0) return -1;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
-    if (dtype < 0 || dtype > 3) return -3;
+    if (dtype < 0 || dtype > 4) return -3;
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
-    if (dtype == ABFT_F32 || (mixed && nb % 128 != 0)) return ABFT_ERR_UNSUPPORTED;
+    const bool emu = dtype == ABFT_F64_EMU;
+    if (dtype == ABFT_F32 || (mixed && nb % 128 != 0) || (emu && nb != 128 && nb != 256))
+        return ABFT_ERR_UNSUPPORTED;
     if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -4;
     if (n > 0 && A == nullptr && ws != nullptr) return -5;
     if (lda < std::max<int64_t>(1, n)) return -6;
@@ -1494,7 +1531,7 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
             same += faults[h].kind == ABFT_FAULT_COMPUTE && faults[h].step == faults[f].step;
         if (same > MAX_CF) return -7;
     }
-    const CholWs w = chol_ws(n, nb, mode, mixed);
+    const CholWs w = chol_ws(n, nb, mode, mixed, emu);
     if (ws == nullptr) {
         *ws_bytes = w.total;
         return ABFT_OK;
@@ -1539,7 +1576,7 @@ int abft_potrf_sched(int64_t n, int64_t nb, int32_t dtype, const int32_t* modes,
     if (n > 0 && A == nullptr) return -5;
     if (*ws_bytes < need) return -12;
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
-    const CholWs w = chol_ws(n, nb, top, mixed);
+    const CholWs w = chol_ws(n, nb, top, mixed, dtype == ABFT_F64_EMU);
     cudaStream_t s = (cudaStream_t)stream;
     char* base = (char*)ws;
     DevStatus* st = (DevStatus*)(base + w.st);

@@ -317,6 +317,14 @@ bool timing_on();
 void timing_mark(int phase, int begin, cudaStream_t s);
 cudaError_t timing_collect(cudaStream_t s);
 
+// FP64-accurate trailing update from BF16 slices (k_emu.cu).
+size_t emu_slice_bytes(int64_t n, int64_t nb);
+cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
+                               int* ex, cudaStream_t s);
+cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
+                           int64_t ldc, int64_t g, const ComputeFault* cf, int ncf, DevStatus* st,
+                           cudaStream_t s);
+
 // GMRES-IR pieces (k_gmres.cu); vectors are n x 16 blocks (ld 16), basis
 // vector i at V + i * vstride.
 int gmres_dot_blocks(int64_t n);

@@ -1,0 +1,414 @@
+// k_emu.cu -- FP64-accurate trailing update of the Cholesky on the BF16
+// tensor cores by splitting the panel into small-integer slices (the Ozaki
+// scheme: Ozaki, Ogita, Oishi, Rump 2012; not in the paper).  B300's FP64 pipe
+// runs the FP64 update at ~1.1 TFLOP/s; the slice products below run on
+// tcgen05 and are exact.
+//
+// Splitting (k_slice_panel, integer operations only): row i of the m x kb
+// panel gets the power-of-two scale sigma_i = 2^e_i, e_i = E_max - 1022 with
+// E_max its largest biased exponent, so |x| < 1 for x = L[i][k] / sigma_i.
+// |x| 2^56 rounded to an integer F is written in balanced base 128:
+// x ~ sign(x) sum_{p=0}^{7} d_p 2^(-7 (p + 1)), d_p in [-64, 63] for p >= 1 and
+// d_0 in [0, 128] (digits taken from the least significant end with a carry),
+// and the eight signed digits are stored as BF16 (exact).
+//
+// Update (k_tmu_emu): C_ij -= sigma_i sigma_j 2^-14 sum_d 2^(-7 d) G_d with
+// G_d = sum_{p + q = d} sum_k s_p(i, k) s_q(j, k) over the 36 pairs with
+// p + q <= 7.  The omitted pairs weigh <= ~2^-47 sigma_i sigma_j and the
+// rounding of F <= 2^-57 sigma per element, both at or below the rounding of
+// the same product in FP64.  For kb <= 256 a slice product is an integer below
+// 2^21 (2^20 unless it involves d_0), so all d + 1 <= 8 pairs of weight d
+// accumulate exactly in one FP32 TMEM accumulator: eight groups per tile.
+// Each group is drained into a 64-bit integer fixed-point sum
+// A = sum_d G_d 2^(40 - 7 d) (exact for d <= 5, truncated for d = 6, 7 below
+// 2^-40), and C_ij -= A 2^(e_i + e_j - 54) is one FP64 update per element.
+//
+// Kernel anatomy as the mixed update (k_mixed.cu), with 128 x 64 tiles: warp 0
+// TMA producer (slice p of rows i0.. and slice q of rows j0.., 64-wide K
+// chunks, 4-stage ring), warp 1 TMEM allocation and the MMA issuer (one group
+// at a time into two alternating 64-column accumulators), warps 2-9 the
+// epilogue (TMEM loads, integer accumulation in registers, FP64 staging and a
+// coalesced read-modify-write of C).  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "tc_util.cuh"
+
+namespace abft {
+
+using namespace tc;
+
+namespace {
+
+constexpr int ES = 8;                       // slices per element
+constexpr int ETM = 128, ETN = 64, EKC = 64;
+constexpr int ESTAGES = 4;
+constexpr int EA_BYTES = ETM * EKC * 2;     // 128 x 64 BF16 box
+constexpr int EB_BYTES = ETN * EKC * 2;     // 64 x 64 BF16 box
+constexpr int ESTAGE = EA_BYTES + EB_BYTES;
+constexpr int EPI_W = 8;
+constexpr int ETHREADS = 64 + EPI_W * 32;
+constexpr uint32_t ETMEM_COLS = 128;        // two 64-column FP32 accumulators
+constexpr int ESTG_LD = ETN + 1;            // staging row stride (doubles)
+constexpr int ESTG_BYTES = ETM * ESTG_LD * 8;
+constexpr size_t E_SMEM = (size_t)ESTAGES * ESTAGE + ESTG_BYTES + 1024 + 256;
+constexpr int NGROUP = 8;
+constexpr int FIXB = 40;                    // fraction bits of the fixed-point sum
+
+// the 36 slice pairs (p, q), p + q <= 7, one group per weight d = p + q
+__constant__ int8_t c_pp[36] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2,
+                                3, 4, 5, 0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 6, 7};
+__constant__ int8_t c_qq[36] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3,
+                                2, 1, 0, 6, 5, 4, 3, 2, 1, 0, 7, 6, 5, 4, 3, 2, 1, 0};
+__constant__ int8_t c_gstart[NGROUP + 1] = {0, 1, 3, 6, 10, 15, 21, 28, 36};
+__constant__ int8_t c_gd[NGROUP] = {0, 1, 2, 3, 4, 5, 6, 7};
+
+struct EmuArgs {
+    double* C;
+    int64_t ldc;
+    int64_t M;          // trailing order (rows of the panel slices)
+    int64_t K;          // panel width, multiple of 64, <= 256
+    const int* ex;      // e_i per panel row
+    int ncf;
+    ComputeFault cf[MAX_CF];
+    DevStatus* st;
+    int64_t ntiles;     // tiles of the lower block triangle (rm x rn per block pair)
+    int64_t rm, rn;     // 128-row and 64-column tiles per g
+    uint32_t idesc;
+};
+
+__device__ __forceinline__ void emu_tile(int64_t idx, int64_t rm, int64_t rn, int64_t& ti,
+                                         int64_t& tj) {
+    const int64_t per = rm * rn, pair = idx / per, sub = idx % per;
+    int64_t a = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
+    while (a * (a + 1) / 2 > pair) --a;
+    while ((a + 1) * (a + 2) / 2 <= pair) ++a;
+    const int64_t b = pair - a * (a + 1) / 2;
+    ti = a * rm + sub / rn;
+    tj = b * rn + sub % rn;
+}
+
+// 2^k as a double for the normal range, 0 below it (k > 1023 does not occur:
+// the scales are bounded by the largest finite double).
+__device__ __forceinline__ double pow2(int k) {
+    if (k < -1022) return 0.0;
+    return __hiloint2double((k + 1023) << 20, 0);
+}
+
+__global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ P, int64_t lda,
+                                                     int64_t m, int kb, uint16_t* __restrict__ S,
+                                                     int* __restrict__ ex) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= m) return;
+    const int nt = kb >> 5;                 // kb <= 256: at most 8 per lane
+    unsigned long long b[8];
+    int emax = 1;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        b[t] = 0ull;
+        if (t < nt) {
+            b[t] = (unsigned long long)__double_as_longlong(P[row * lda + lane + 32 * t]);
+            const int e = (int)((b[t] >> 52) & 0x7ffull);
+            emax = e > emax ? e : emax;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int other = __shfl_xor_sync(0xffffffffu, emax, o);
+        emax = other > emax ? other : emax;
+    }
+    if (lane == 0) ex[row] = emax - 1022;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (t >= nt) continue;
+        const int e = (int)((b[t] >> 52) & 0x7ffull);
+        const unsigned long long mant = (b[t] & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+        // F = round(|x| 2^56) = round(mant 2^(E - E_max + 3)), E of a subnormal taken
+        // as 1: a right shift by E_max - 3 - E (a left shift for the largest elements)
+        const int sh = emax - 3 - (e ? e : 1);
+        unsigned long long F;
+        if (sh <= 0) F = mant << (-sh);
+        else if (sh >= 64) F = 0ull;
+        else F = (mant >> sh) + ((mant >> (sh - 1)) & 1ull);
+        const bool neg = (b[t] >> 63) != 0ull;
+        const int64_t k = lane + 32 * t;
+        int carry = 0;
+#pragma unroll
+        for (int p = ES - 1; p >= 0; --p) {
+            int d = (int)((F >> (7 * (ES - 1 - p))) & 127ull) + carry;
+            carry = 0;
+            if (p > 0 && d >= 64) {
+                d -= 128;
+                carry = 1;
+            }
+            const float v = (float)(neg ? -d : d);
+            S[((int64_t)p * m + row) * kb + k] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__ CUtensorMap mapA,
+                                                         const __grid_constant__ CUtensorMap mapB,
+                                                         EmuArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    double* stg = (double*)(smem + ESTAGES * ESTAGE);
+    uint64_t* full = (uint64_t*)(smem + ESTAGES * ESTAGE + ESTG_BYTES);
+    uint64_t* empty = full + ESTAGES;
+    uint64_t* accf = empty + ESTAGES;   // [2]
+    uint64_t* acce = accf + 2;          // [2]
+    uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    if (a.st->info != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ESTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], EPI_W);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(ETMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int nk = (int)(a.K / EKC);
+    const int64_t G = gridDim.x;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer: per tile, per group, per pair, per K chunk
+            int64_t c = 0;
+            bool ok = true;
+            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
+                int64_t ti, tj;
+                emu_tile(idx, a.rm, a.rn, ti, tj);
+                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
+                for (int pr = 0; pr < c_gstart[NGROUP] && ok; ++pr) {
+                    const int64_t ya = (int64_t)c_pp[pr] * a.M + ti * ETM;
+                    const int64_t yb = (int64_t)c_qq[pr] * a.M + tj * ETN;
+                    for (int kc = 0; kc < nk; ++kc, ++c) {
+                        const int s = (int)(c % ESTAGES);
+                        if (c >= ESTAGES &&
+                            !mbar_wait(&empty[s], (uint32_t)(((c - ESTAGES) / ESTAGES) & 1))) {
+                            *abort_flag = 1;
+                            atomicExch(&a.st->error, 3);
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&full[s], ESTAGE);
+                        uint8_t* dst = smem + s * ESTAGE;
+                        tma_load_2d(dst, &mapA, &full[s], kc * EKC, (int)ya);
+                        tma_load_2d(dst + EA_BYTES, &mapB, &full[s], kc * EKC, (int)yb);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer: one group at a time into alternating accumulators
+            int64_t c = 0, it = 0;
+            bool ok = true;
+            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
+                int64_t ti, tj;
+                emu_tile(idx, a.rm, a.rn, ti, tj);
+                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
+                for (int g = 0; g < NGROUP && ok; ++g, ++it) {
+                    const int b = (int)(it & 1);
+                    if (it >= 2 && !mbar_wait(&acce[b], (uint32_t)(((it >> 1) - 1) & 1))) {
+                        *abort_flag = 1;
+                        atomicExch(&a.st->error, 3);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dt = tmem + (uint32_t)(b * ETN);
+                    bool first = true;
+                    for (int pr = c_gstart[g]; pr < c_gstart[g + 1] && ok; ++pr) {
+                        for (int kc = 0; kc < nk; ++kc, ++c) {
+                            const int s = (int)(c % ESTAGES);
+                            if (!mbar_wait(&full[s], (uint32_t)((c / ESTAGES) & 1))) {
+                                *abort_flag = 1;
+                                atomicExch(&a.st->error, 3);
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t abase = smem_u32(smem + s * ESTAGE);
+                            const uint32_t bbase = abase + EA_BYTES;
+#pragma unroll
+                            for (int kk = 0; kk < EKC / 16; ++kk) {
+                                mma_f16(dt, smem_desc(abase + kk * 32), smem_desc(bbase + kk * 32),
+                                        a.idesc, first ? 0u : 1u);
+                                first = false;
+                            }
+                            mma_commit(&empty[s]);
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&accf[b]);
+                }
+            }
+        }
+    } else {
+        // epilogue: TMEM lane quarter q (rows 32 q ..), column half h (32 columns)
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int h = ew >> 2;
+        const int r = q * 32 + lane;
+        int64_t it = 0;
+        for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
+            int64_t ti, tj;
+            emu_tile(idx, a.rm, a.rn, ti, tj);
+            if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
+            long long acc[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) acc[u] = 0;
+            bool ok = true;
+            for (int g = 0; g < NGROUP; ++g, ++it) {
+                const int b = (int)(it & 1);
+                if (!*abort_flag && ok && mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1))) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * ETN + h * 32), v);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                         smem_u32(&acce[b]))
+                                     : "memory");
+                    const int sh = FIXB - 7 * c_gd[g];
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        // an exact integer below 2^24 in magnitude
+                        const long long iv = (long long)__float2int_rn(__uint_as_float(v[u]));
+                        acc[u] += sh >= 0 ? iv * (1ll << sh) : (iv >> (-sh));
+                    }
+                } else {
+                    ok = false;
+                    if (!*abort_flag) {
+                        *abort_flag = 1;
+                        atomicExch(&a.st->error, 3);
+                    }
+                }
+            }
+            // scale, stage, and read-modify-write C with coalesced accesses
+            const int64_t i0 = ti * ETM, j0 = tj * ETN;
+            if (ok) {
+                const int64_t gi = i0 + r;
+                const int ei = gi < a.M ? a.ex[gi] : 0;
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const int64_t gj = j0 + h * 32 + u;
+                    const int ej = gj < a.M ? a.ex[gj] : 0;
+                    stg[r * ESTG_LD + h * 32 + u] = (double)acc[u] * pow2(ei + ej - 54);
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(EPI_W * 32) : "memory");
+            if (ok && !*abort_flag) {
+                for (int rr = ew; rr < ETM; rr += EPI_W) {
+                    const int64_t i = i0 + rr;
+                    if (i >= a.M) break;
+#pragma unroll
+                    for (int t2 = 0; t2 < ETN / 32; ++t2) {
+                        const int64_t j = j0 + lane + 32 * t2;
+                        if (j >= a.M) continue;
+                        double* cp = a.C + i * a.ldc + j;
+                        double v = *cp - stg[rr * ESTG_LD + lane + 32 * t2];
+                        for (int f = 0; f < a.ncf; ++f)
+                            if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
+                        *cp = v;
+                    }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(EPI_W * 32) : "memory");
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ETMEM_COLS));
+    }
+}
+
+bool encode_slices(CUtensorMap* map, const uint16_t* S, int64_t rows, int64_t kb, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kb, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kb * 2};
+    cuuint32_t box[2] = {(cuuint32_t)EKC, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)S, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t emu_slice_bytes(int64_t n, int64_t nb) {
+    return sizeof(uint16_t) * (size_t)ES * (size_t)n * (size_t)nb;
+}
+
+cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
+                               int* ex, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    if (kb % 32 != 0 || kb > 256) return cudaErrorInvalidValue;
+    k_slice_panel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(P, lda, m, (int)kb, S, ex);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// C (m x m, trailing, FP64) -= L L^T on the lower block triangle (blocks of g),
+// from the slices S (7 x m x kb BF16) and row exponents ex of the panel L.
+cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
+                           int64_t ldc, int64_t g, const ComputeFault* cf, int ncf, DevStatus* st,
+                           cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    if (kb % EKC != 0 || kb > 256 || g % ETM != 0) return cudaErrorInvalidValue;
+    CUtensorMap mapA, mapB;
+    if (!encode_slices(&mapA, S, ES * m, kb, ETM) || !encode_slices(&mapB, S, ES * m, kb, ETN))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tmu_emu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)E_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    EmuArgs a{};
+    a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.ex = ex; a.st = st;
+    a.ncf = 0;
+    for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
+    const int64_t qb = (m + g - 1) / g;
+    a.rm = g / ETM;
+    a.rn = g / ETN;
+    a.ntiles = qb * (qb + 1) / 2 * a.rm * a.rn;
+    // kind::f16 instruction descriptor: D F32, A/B BF16, K-major, N >> 3, M >> 4
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ETN >> 3) << 17) |
+              ((uint32_t)(ETM >> 4) << 24);
+    int64_t grid = num_sms();
+    if (grid > a.ntiles) grid = a.ntiles;
+    k_tmu_emu<<<(unsigned)grid, ETHREADS, E_SMEM, s>>>(mapA, mapB, a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace abft
