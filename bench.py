@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
     p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
     p.add_argument("--no-batched", action="store_true", help="skip the batched timings")
+    p.add_argument("--no-emulated", action="store_true",
+                   help="skip the FP64-accurate factorization with the BF16 tensor-core update")
     p.add_argument("--conditioned", action="store_true",
                    help="add the conditioned mixed-precision solves: A = Q diag(sigma) Q^T with "
                         "kappa 1e2, 1e6, 1e10, block 512, GMRES-IR (BF16 / FP16) vs the FP64 form")
@@ -56,7 +58,7 @@ def parse():
                         "factorization for no / single-side / full / adaptive checksums")
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
-                   choices=["fp64", "mixed-bf16", "mixed-f16", "potrs-f32"],
+                   choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
                         "refinement, or an FP32 two-sweep solve with the FP64 factor; at --n, --nb")
@@ -326,6 +328,48 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize(dev)
         return t0.elapsed_time(t1) / steps, out
 
+    emulated = None
+    if not args.no_emulated:
+        # FP64-accurate factorization with the trailing update on the BF16 tensor
+        # cores (ABFT_F64_EMU): same matrix, faults and checksums as the step;
+        # accuracy against the FP64 factor above and by a probe backward error
+        # ||(L L^T - A) v|| / (||A|| ||v||) with a seeded random v (FP64 on the GPU).
+        Lref = torch.tril(A).clone()
+        def emu_step():
+            A.copy_(A0)
+            return abft.potrf(A, nb, abft.FULL, dtype=abft.F64_EMU, faults=faults, workspace=wsp)
+        for _ in range(max(1, args.warmup)):
+            rc_e, rep_e = emu_step()
+        abft.timing_enable(True)
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            rc_e, rep_e = emu_step()
+        t1.record()
+        torch.cuda.synchronize(dev)
+        ph_e = abft.timing_read()
+        abft.timing_enable(False)
+        ms_e = t0.elapsed_time(t1) / args.steps
+        Le = torch.tril(A)
+        gv = torch.Generator(device=dev)
+        gv.manual_seed(4242)
+        v = torch.randn(n, 1, generator=gv, dtype=torch.float64, device=dev)
+        Av = A0 @ v
+        def probe(Lx):
+            return float(torch.linalg.norm(Lx @ (Lx.T @ v) - Av) /
+                         (torch.linalg.norm(A0, ord=float("inf")) * torch.linalg.norm(v)))
+        emulated = {"ms": ms_e, "tflops": chol_flops(n) / (ms_e * 1e-3) / 1e12,
+                    "pct_of_fp64_peak": 100 * chol_flops(n) / (ms_e * 1e-3) / 1e12 / peak,
+                    "speedup_vs_fp64": ms_step / ms_e, "rc": rc_e,
+                    "events_match_injected": [(e[0], e[1], e[2], e[3]) for e in rep_e["loc"]] == expected,
+                    "probe_backward_err": probe(Le), "probe_backward_err_fp64": probe(Lref),
+                    "max_rel_diff_vs_fp64_factor": float((Le - Lref).abs().max() / Lref.abs().max()),
+                    "phase_ms_per_step": {k: vv[0] / args.steps for k, vv in ph_e.items()},
+                    "tmu_tensor_tflops_equiv": tmu_flops(n, nb) / (ph_e["tmu"][0] / args.steps * 1e-3) / 1e12}
+        del Lref, Le, v, Av
+
     mixed = None
     if not args.no_mixed:
         # time to solution of A X = B (16 right-hand sides) at a 1e-12 backward
@@ -587,6 +631,7 @@ def run_ours(args, ws, rank, local):
             "abft": {"detected": rep["detected"], "corrected": rep["corrected"],
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
+            "fp64_emulated": emulated,
             "mixed_precision_ir": mixed, "conditioned": conditioned, "campaign": campaign,
             "lu_qr": lu_qr,
             "batched": batched,
@@ -612,9 +657,10 @@ def profile_case(args):
         A.copy_(A0)
         abft.potrf(A, nb, abft.FULL, workspace=wsp)
     for _ in range(2):
-        if args.profile_case == "fp64":
+        if args.profile_case in ("fp64", "fp64-emu"):
             A.copy_(A0)
-            abft.potrf(A, nb, abft.FULL, faults=faults, workspace=wsp)
+            dt = abft.F64 if args.profile_case == "fp64" else abft.F64_EMU
+            abft.potrf(A, nb, abft.FULL, dtype=dt, faults=faults, workspace=wsp)
         elif args.profile_case == "potrs-f32":
             X.copy_(B)
             abft.potrs(A, X, nb, abft.F32)

@@ -320,18 +320,31 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
             }
             asm volatile("bar.sync 1, %0;" ::"r"(EPI_W * 32) : "memory");
             if (ok && !*abort_flag) {
-                for (int rr = ew; rr < ETM; rr += EPI_W) {
-                    const int64_t i = i0 + rr;
-                    if (i >= a.M) break;
+                // warp ew owns rows ew, ew + 8, ...: all 32 of its C values per lane
+                // are loaded before any is updated
+                constexpr int RPW = ETM / EPI_W;
+                double cv[RPW][ETN / 32];
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const int64_t i = i0 + ew + u * EPI_W;
 #pragma unroll
                     for (int t2 = 0; t2 < ETN / 32; ++t2) {
                         const int64_t j = j0 + lane + 32 * t2;
-                        if (j >= a.M) continue;
-                        double* cp = a.C + i * a.ldc + j;
-                        double v = *cp - stg[rr * ESTG_LD + lane + 32 * t2];
+                        cv[u][t2] = (i < a.M && j < a.M) ? a.C[i * a.ldc + j] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < RPW; ++u) {
+                    const int rr = ew + u * EPI_W;
+                    const int64_t i = i0 + rr;
+#pragma unroll
+                    for (int t2 = 0; t2 < ETN / 32; ++t2) {
+                        const int64_t j = j0 + lane + 32 * t2;
+                        if (i >= a.M || j >= a.M) continue;
+                        double v = cv[u][t2] - stg[rr * ESTG_LD + lane + 32 * t2];
                         for (int f = 0; f < a.ncf; ++f)
                             if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
-                        *cp = v;
+                        a.C[i * a.ldc + j] = v;
                     }
                 }
             }
