@@ -23,12 +23,19 @@
 // A = sum_d G_d 2^(40 - 7 d) (exact for d <= 5, truncated for d = 6, 7 below
 // 2^-40), and C_ij -= A 2^(e_i + e_j - 54) is one FP64 update per element.
 //
-// Kernel anatomy as the mixed update (k_mixed.cu), with 128 x 64 tiles: warp 0
-// TMA producer (slice p of rows i0.. and slice q of rows j0.., 64-wide K
-// chunks, 4-stage ring), warp 1 TMEM allocation and the MMA issuer (one group
-// at a time into two alternating 64-column accumulators), warps 2-9 the
-// epilogue (TMEM loads, integer accumulation in registers, FP64 staging and a
-// coalesced read-modify-write of C).  Every wait is bounded.
+// Kernel anatomy (persistent, one CTA per SM, 128 x 64 tiles of C): the pairs
+// of a tile run p-major, so slice p of the tile's rows (the A operand, 128 x kb,
+// 64 KB) is loaded once and stays in shared memory (two slots) while slices
+// q = 0 .. 7 - p of the tile's columns (B, 64 x kb, one pair per stage) stream
+// through a 3-stage ring; the eight weight groups accumulate in eight 64-column FP32
+// TMEM accumulators (all 512 columns).  Group d is complete after pair
+// (d, 0), so the epilogue drains it while the MMAs of larger p continue, and
+// the next tile's first MMA into group d waits only for that drain.
+// Warp 0 issues the TMA loads (lane 0 the B chunks, lane 1 the A slices, each
+// running ahead as far as its buffers allow), warp 1 allocates TMEM and
+// issues the MMAs,
+// warps 2-9 drain the groups into 64-bit integers (registers) and update C.
+// Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -44,26 +51,18 @@ namespace {
 
 constexpr int ES = 8;                       // slices per element
 constexpr int ETM = 128, ETN = 64, EKC = 64;
-constexpr int ESTAGES = 4;
-constexpr int EA_BYTES = ETM * EKC * 2;     // 128 x 64 BF16 box
-constexpr int EB_BYTES = ETN * EKC * 2;     // 64 x 64 BF16 box
-constexpr int ESTAGE = EA_BYTES + EB_BYTES;
+constexpr int EKMAX = 256;                  // panel width limit (exact FP32 accumulation)
+constexpr int ACHUNK = ETM * EKC * 2;       // 128 x 64 BF16 box
+constexpr int ASLOT = ACHUNK * (EKMAX / EKC);   // one slice of the tile rows, whole K
+constexpr int BCHUNK = ETN * EKC * 2;       // 64 x 64 BF16 box
+constexpr int BSTAGE = BCHUNK * (EKMAX / EKC);   // one slice of the tile columns, whole K
+constexpr int BSTAGES = 3;
 constexpr int EPI_W = 8;
 constexpr int ETHREADS = 64 + EPI_W * 32;
-constexpr uint32_t ETMEM_COLS = 128;        // two 64-column FP32 accumulators
-constexpr int ESTG_LD = ETN + 1;            // staging row stride (doubles)
-constexpr int ESTG_BYTES = ETM * ESTG_LD * 8;
-constexpr size_t E_SMEM = (size_t)ESTAGES * ESTAGE + ESTG_BYTES + 1024 + 256;
 constexpr int NGROUP = 8;
+constexpr uint32_t ETMEM_COLS = 512;        // eight 64-column FP32 accumulators
+constexpr size_t E_SMEM = 2 * (size_t)ASLOT + (size_t)BSTAGES * BSTAGE + 1024 + 512;
 constexpr int FIXB = 40;                    // fraction bits of the fixed-point sum
-
-// the 36 slice pairs (p, q), p + q <= 7, one group per weight d = p + q
-__constant__ int8_t c_pp[36] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2,
-                                3, 4, 5, 0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 6, 7};
-__constant__ int8_t c_qq[36] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3,
-                                2, 1, 0, 6, 5, 4, 3, 2, 1, 0, 7, 6, 5, 4, 3, 2, 1, 0};
-__constant__ int8_t c_gstart[NGROUP + 1] = {0, 1, 3, 6, 10, 15, 21, 28, 36};
-__constant__ int8_t c_gd[NGROUP] = {0, 1, 2, 3, 4, 5, 6, 7};
 
 struct EmuArgs {
     double* C;
@@ -155,24 +154,31 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                                                          EmuArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    double* stg = (double*)(smem + ESTAGES * ESTAGE);
-    uint64_t* full = (uint64_t*)(smem + ESTAGES * ESTAGE + ESTG_BYTES);
-    uint64_t* empty = full + ESTAGES;
-    uint64_t* accf = empty + ESTAGES;   // [2]
-    uint64_t* acce = accf + 2;          // [2]
-    uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+    uint8_t* abuf = smem;                                  // [2][ASLOT]
+    uint8_t* bring = smem + 2 * ASLOT;                     // [BSTAGES][BSTAGE]
+    uint64_t* fullA = (uint64_t*)(bring + BSTAGES * BSTAGE);
+    uint64_t* emptyA = fullA + 2;
+    uint64_t* fullB = emptyA + 2;
+    uint64_t* emptyB = fullB + BSTAGES;
+    uint64_t* accf = emptyB + BSTAGES;                     // [NGROUP]
+    uint64_t* acce = accf + NGROUP;                        // [NGROUP]
+    uint32_t* tmem_slot = (uint32_t*)(acce + NGROUP);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     if (a.st->info != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ESTAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            mbar_init(&fullA[s2], 1);
+            mbar_init(&emptyA[s2], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], EPI_W);
+        for (int s2 = 0; s2 < BSTAGES; ++s2) {
+            mbar_init(&fullB[s2], 1);
+            mbar_init(&emptyB[s2], 1);
+        }
+        for (int d = 0; d < NGROUP; ++d) {
+            mbar_init(&accf[d], 1);
+            mbar_init(&acce[d], EPI_W);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -190,78 +196,106 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
     const uint32_t tmem = *tmem_slot;
     const int nk = (int)(a.K / EKC);
     const int64_t G = gridDim.x;
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(&a.st->error, 3);
+    };
 
     if (warp == 0) {
-        if (lane == 0) {   // TMA producer: per tile, per group, per pair, per K chunk
-            int64_t c = 0;
+        if (lane == 1) {          // TMA producer of the A slices (tile rows, whole K)
+            int64_t ca = 0;
             bool ok = true;
             for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
                 int64_t ti, tj;
                 emu_tile(idx, a.rm, a.rn, ti, tj);
                 if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
-                for (int pr = 0; pr < c_gstart[NGROUP] && ok; ++pr) {
-                    const int64_t ya = (int64_t)c_pp[pr] * a.M + ti * ETM;
-                    const int64_t yb = (int64_t)c_qq[pr] * a.M + tj * ETN;
-                    for (int kc = 0; kc < nk; ++kc, ++c) {
-                        const int s = (int)(c % ESTAGES);
-                        if (c >= ESTAGES &&
-                            !mbar_wait(&empty[s], (uint32_t)(((c - ESTAGES) / ESTAGES) & 1))) {
-                            *abort_flag = 1;
-                            atomicExch(&a.st->error, 3);
+                for (int p = 0; p < ES; ++p, ++ca) {
+                    const int slot = (int)(ca & 1);
+                    if (ca >= 2 && !mbar_wait(&emptyA[slot], (uint32_t)(((ca >> 1) - 1) & 1))) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&fullA[slot], (uint32_t)(ACHUNK * nk));
+                    const int ya = (int)((int64_t)p * a.M + ti * ETM);
+                    for (int kc = 0; kc < nk; ++kc)
+                        tma_load_2d(abuf + slot * ASLOT + kc * ACHUNK, &mapA, &fullA[slot], kc * EKC, ya);
+                }
+            }
+        } else if (lane == 0) {   // TMA producer of the B chunks (tile columns)
+            int64_t cb = 0;
+            bool ok = true;
+            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
+                int64_t ti, tj;
+                emu_tile(idx, a.rm, a.rn, ti, tj);
+                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
+                for (int p = 0; p < ES && ok; ++p) {
+                    for (int q = 0; q < ES - p; ++q, ++cb) {
+                        const int yb = (int)((int64_t)q * a.M + tj * ETN);
+                        const int s2 = (int)(cb % BSTAGES);
+                        if (cb >= BSTAGES &&
+                            !mbar_wait(&emptyB[s2], (uint32_t)(((cb / BSTAGES) - 1) & 1))) {
+                            fail();
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(&full[s], ESTAGE);
-                        uint8_t* dst = smem + s * ESTAGE;
-                        tma_load_2d(dst, &mapA, &full[s], kc * EKC, (int)ya);
-                        tma_load_2d(dst + EA_BYTES, &mapB, &full[s], kc * EKC, (int)yb);
+                        mbar_expect_tx(&fullB[s2], (uint32_t)(BCHUNK * nk));
+                        for (int kc = 0; kc < nk; ++kc)
+                            tma_load_2d(bring + s2 * BSTAGE + kc * BCHUNK, &mapB, &fullB[s2],
+                                        kc * EKC, yb);
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // MMA issuer: one group at a time into alternating accumulators
-            int64_t c = 0, it = 0;
+        if (lane == 0) {   // MMA issuer
+            int64_t ca = 0, cb = 0, tc = 0;
             bool ok = true;
             for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
                 int64_t ti, tj;
                 emu_tile(idx, a.rm, a.rn, ti, tj);
                 if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
-                for (int g = 0; g < NGROUP && ok; ++g, ++it) {
-                    const int b = (int)(it & 1);
-                    if (it >= 2 && !mbar_wait(&acce[b], (uint32_t)(((it >> 1) - 1) & 1))) {
-                        *abort_flag = 1;
-                        atomicExch(&a.st->error, 3);
+                for (int p = 0; p < ES && ok; ++p, ++ca) {
+                    const int slot = (int)(ca & 1);
+                    if (!mbar_wait(&fullA[slot], (uint32_t)((ca >> 1) & 1))) {
+                        fail();
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t dt = tmem + (uint32_t)(b * ETN);
-                    bool first = true;
-                    for (int pr = c_gstart[g]; pr < c_gstart[g + 1] && ok; ++pr) {
-                        for (int kc = 0; kc < nk; ++kc, ++c) {
-                            const int s = (int)(c % ESTAGES);
-                            if (!mbar_wait(&full[s], (uint32_t)((c / ESTAGES) & 1))) {
-                                *abort_flag = 1;
-                                atomicExch(&a.st->error, 3);
-                                ok = false;
-                                break;
-                            }
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const uint32_t abase = smem_u32(smem + s * ESTAGE);
-                            const uint32_t bbase = abase + EA_BYTES;
-#pragma unroll
-                            for (int kk = 0; kk < EKC / 16; ++kk) {
-                                mma_f16(dt, smem_desc(abase + kk * 32), smem_desc(bbase + kk * 32),
-                                        a.idesc, first ? 0u : 1u);
-                                first = false;
-                            }
-                            mma_commit(&empty[s]);
+                    const uint32_t abase = smem_u32(abuf + slot * ASLOT);
+                    for (int q = 0; q < ES - p && ok; ++q, ++cb) {
+                        const int d = p + q;
+                        // first MMA of group d in this tile: its accumulator must be drained
+                        if (p == 0 && tc >= 1 && !mbar_wait(&acce[d], (uint32_t)((tc - 1) & 1))) {
+                            fail();
+                            ok = false;
+                            break;
                         }
+                        const int s2 = (int)(cb % BSTAGES);
+                        if (!mbar_wait(&fullB[s2], (uint32_t)((cb / BSTAGES) & 1))) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t dt = tmem + (uint32_t)(d * ETN);
+                        // descriptors advance by 32 bytes per K = 16 step (field in 16-byte units)
+                        const uint64_t adesc0 = smem_desc(abase);
+                        const uint64_t bdesc0 = smem_desc(smem_u32(bring + s2 * BSTAGE));
+                        for (int kc = 0; kc < nk; ++kc) {
+#pragma unroll
+                            for (int kk = 0; kk < EKC / 16; ++kk)
+                                mma_f16(dt, adesc0 + (uint64_t)((kc * ACHUNK + kk * 32) >> 4),
+                                        bdesc0 + (uint64_t)((kc * BCHUNK + kk * 32) >> 4), a.idesc,
+                                        (p > 0 || kc > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&emptyB[s2]);
+                        if (q == 0) mma_commit(&accf[p]);   // pair (p, 0) ends group p
                     }
-                    if (!ok) break;
-                    mma_commit(&accf[b]);
+                    if (ok) mma_commit(&emptyA[slot]);
                 }
+                ++tc;
             }
         }
     } else {
@@ -270,7 +304,7 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
         const int q = warp & 3;
         const int h = ew >> 2;
         const int r = q * 32 + lane;
-        int64_t it = 0;
+        int64_t tc = 0;
         for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
             int64_t ti, tj;
             emu_tile(idx, a.rm, a.rn, ti, tj);
@@ -279,19 +313,18 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
 #pragma unroll
             for (int u = 0; u < 32; ++u) acc[u] = 0;
             bool ok = true;
-            for (int g = 0; g < NGROUP; ++g, ++it) {
-                const int b = (int)(it & 1);
-                if (!*abort_flag && ok && mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1))) {
+            for (int d = 0; d < NGROUP; ++d) {
+                if (ok && !*abort_flag && mbar_wait(&accf[d], (uint32_t)(tc & 1))) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * ETN + h * 32), v);
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * ETN + h * 32), v);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                         smem_u32(&acce[b]))
+                                         smem_u32(&acce[d]))
                                      : "memory");
-                    const int sh = FIXB - 7 * c_gd[g];
+                    const int sh = FIXB - 7 * d;
 #pragma unroll
                     for (int u = 0; u < 32; ++u) {
                         // an exact integer below 2^24 in magnitude
@@ -299,56 +332,36 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                         acc[u] += sh >= 0 ? iv * (1ll << sh) : (iv >> (-sh));
                     }
                 } else {
+                    if (ok && !*abort_flag) fail();
                     ok = false;
-                    if (!*abort_flag) {
-                        *abort_flag = 1;
-                        atomicExch(&a.st->error, 3);
-                    }
                 }
             }
-            // scale, stage, and read-modify-write C with coalesced accesses
-            const int64_t i0 = ti * ETM, j0 = tj * ETN;
-            if (ok) {
-                const int64_t gi = i0 + r;
-                const int ei = gi < a.M ? a.ex[gi] : 0;
+            // C[i][j] -= A 2^(e_i + e_j - 54): this thread's row, 32 columns, all
+            // loads first
+            const int64_t gi = ti * ETM + r, jb = tj * ETN + h * 32;
+            if (ok && !*abort_flag && gi < a.M) {
+                double* crow = a.C + gi * a.ldc;
+                const int ei = a.ex[gi];
 #pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    const int64_t gj = j0 + h * 32 + u;
-                    const int ej = gj < a.M ? a.ex[gj] : 0;
-                    stg[r * ESTG_LD + h * 32 + u] = (double)acc[u] * pow2(ei + ej - 54);
-                }
-            }
-            asm volatile("bar.sync 1, %0;" ::"r"(EPI_W * 32) : "memory");
-            if (ok && !*abort_flag) {
-                // warp ew owns rows ew, ew + 8, ...: all 32 of its C values per lane
-                // are loaded before any is updated
-                constexpr int RPW = ETM / EPI_W;
-                double cv[RPW][ETN / 32];
+                for (int half = 0; half < 2; ++half) {
+                    double cv[16];
 #pragma unroll
-                for (int u = 0; u < RPW; ++u) {
-                    const int64_t i = i0 + ew + u * EPI_W;
-#pragma unroll
-                    for (int t2 = 0; t2 < ETN / 32; ++t2) {
-                        const int64_t j = j0 + lane + 32 * t2;
-                        cv[u][t2] = (i < a.M && j < a.M) ? a.C[i * a.ldc + j] : 0.0;
+                    for (int u = 0; u < 16; ++u) {
+                        const int64_t gj = jb + 16 * half + u;
+                        cv[u] = gj < a.M ? crow[gj] : 0.0;
                     }
-                }
 #pragma unroll
-                for (int u = 0; u < RPW; ++u) {
-                    const int rr = ew + u * EPI_W;
-                    const int64_t i = i0 + rr;
-#pragma unroll
-                    for (int t2 = 0; t2 < ETN / 32; ++t2) {
-                        const int64_t j = j0 + lane + 32 * t2;
-                        if (i >= a.M || j >= a.M) continue;
-                        double v = cv[u][t2] - stg[rr * ESTG_LD + lane + 32 * t2];
+                    for (int u = 0; u < 16; ++u) {
+                        const int64_t gj = jb + 16 * half + u;
+                        if (gj >= a.M) continue;
+                        double v = cv[u] - (double)acc[16 * half + u] * pow2(ei + a.ex[gj] - 54);
                         for (int f = 0; f < a.ncf; ++f)
-                            if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
-                        a.C[i * a.ldc + j] = v;
+                            if (a.cf[f].row == gi && a.cf[f].col == gj) v += a.cf[f].delta;
+                        crow[gj] = v;
                     }
                 }
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(EPI_W * 32) : "memory");
+            ++tc;
         }
     }
     __syncwarp();
@@ -395,7 +408,7 @@ cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t 
                            int64_t ldc, int64_t g, const ComputeFault* cf, int ncf, DevStatus* st,
                            cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    if (kb % EKC != 0 || kb > 256 || g % ETM != 0) return cudaErrorInvalidValue;
+    if (kb % EKC != 0 || kb > EKMAX || g % ETM != 0) return cudaErrorInvalidValue;
     CUtensorMap mapA, mapB;
     if (!encode_slices(&mapA, S, ES * m, kb, ETM) || !encode_slices(&mapB, S, ES * m, kb, ETN))
         return cudaErrorInvalidValue;
