@@ -121,7 +121,7 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
-    w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)n : 0));
+    w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)emu_rows(n, nb) : 0));
     w.total = off;
     return w;
 }
@@ -265,36 +265,32 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
         }
         timing_mark(PH_PU, 0, s);
         if (emu) {
-            // FP64-accurate TMU from exact BF16 slice products; checksum borders in FP64
+            // FP64-accurate TMU from exact BF16 slice products; the checksum
+            // rows are sliced behind the panel rows and their border products
+            // (c_I -= s_I L_J^T, and in FULL mode r_I -= L_I s_J^T) run in the
+            // same launch
             timing_mark(PH_TMU, 1, s);
             uint16_t* Sl = (uint16_t*)(base + w.eslice);
             int* ex = (int*)(base + w.eex);
-            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, Sl, ex, s));
+            EmuBorders eb;
+            if (check) {
+                eb.mc = (nt - k - 1) * nc;
+                eb.nc = (int)nc;
+                eb.C2 = CS + ((k + 1) * nc) * n + T0; eb.ldc2 = n;
+                if (full) { eb.C3 = Cr + T0 * nt + (k + 1); eb.ldc3 = nt; }
+            }
+            const int64_t mtot = m + eb.mc;
+            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, Sl, mtot, 0, ex, s));
+            if (check)
+                ABFT_CUDA_TRY(launch_slice_panel(CS + ((k + 1) * nc) * n + K0, n, eb.mc, kb, Sl,
+                                                 mtot, m, ex, s));
             ComputeFault ecf[MAX_CF];
             int encf = 0;
             for (int f = 0; f < nfaults && encf < MAX_CF; ++f)
                 if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
                     ecf[encf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
-            ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, m, kb, A + T0 * lda + T0, lda, g, ecf, encf, st, s));
-            if (check) {
-                GemmSeg bs[2] = {};
-                int nbs = 0;
-                {   // border rows: c_I -= s_I L_J^T (and the weighted rows)
-                    GemmSeg& b = bs[nbs++];
-                    b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
-                    b.B = A + T0 * lda + K0; b.ldb = lda;
-                    b.C = CS + ((k + 1) * nc) * n + T0; b.ldc = n;
-                    b.M = (nt - k - 1) * nc; b.N = m; b.K = kb;
-                }
-                if (full) {   // border columns: r_I -= L_I s_J^T
-                    GemmSeg& b = bs[nbs++];
-                    b.A = A + T0 * lda + K0; b.lda = lda;
-                    b.B = CS + ((k + 1) * nc) * n + K0; b.ldb = nc * n;
-                    b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
-                    b.M = m; b.N = nt - k - 1; b.K = kb;
-                }
-                ABFT_CUDA_TRY(launch_gemm_f64(bs, nbs, 0, 0, nullptr, 0, st, s));
-            }
+            ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, m, kb, A + T0 * lda + T0, lda, g, eb, ecf, encf,
+                                         st, s));
             timing_mark(PH_TMU, 0, s);
         } else if (mixed) {
             // TMU on the tensor cores: quantized panel, FP32 accumulation, FP64 C

@@ -317,13 +317,23 @@ bool timing_on();
 void timing_mark(int phase, int begin, cudaStream_t s);
 cudaError_t timing_collect(cudaStream_t s);
 
-// FP64-accurate trailing update from BF16 slices (k_emu.cu).
+// FP64-accurate trailing update from BF16 slices (k_emu.cu).  The slice
+// tensor holds emu_rows(n, nb) rows: the panel rows, then the checksum rows.
+struct EmuBorders {
+    double* C2 = nullptr;   // checksum rows x panel rows (row-major, ld ldc2), or null
+    int64_t ldc2 = 0;
+    double* C3 = nullptr;   // panel rows x plain checksum rows (ld ldc3), or null
+    int64_t ldc3 = 0;
+    int64_t mc = 0;         // checksum rows sliced behind the panel rows
+    int nc = 0;             // checksum rows per block row (plain ones at i % nc == 0)
+};
+int64_t emu_rows(int64_t n, int64_t nb);
 size_t emu_slice_bytes(int64_t n, int64_t nb);
 cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
-                               int* ex, cudaStream_t s);
+                               int64_t Mtot, int64_t row0, int* ex, cudaStream_t s);
 cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
-                           int64_t ldc, int64_t g, const ComputeFault* cf, int ncf, DevStatus* st,
-                           cudaStream_t s);
+                           int64_t ldc, int64_t g, const EmuBorders& eb, const ComputeFault* cf,
+                           int ncf, DevStatus* st, cudaStream_t s);
 
 // GMRES-IR pieces (k_gmres.cu); vectors are n x 16 blocks (ld 16), basis
 // vector i at V + i * vstride.

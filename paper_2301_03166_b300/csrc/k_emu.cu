@@ -23,18 +23,29 @@
 // A = sum_d G_d 2^(40 - 7 d) (exact for d <= 5, truncated for d = 6, 7 below
 // 2^-40), and C_ij -= A 2^(e_i + e_j - 54) is one FP64 update per element.
 //
-// Kernel anatomy (persistent, one CTA per SM, 128 x 64 tiles of C): the pairs
-// of a tile run p-major, so slice p of the tile's rows (the A operand, 128 x kb,
-// 64 KB) is loaded once and stays in shared memory (two slots) while slices
-// q = 0 .. 7 - p of the tile's columns (B, 64 x kb, one pair per stage) stream
-// through a 3-stage ring; the eight weight groups accumulate in eight 64-column FP32
-// TMEM accumulators (all 512 columns).  Group d is complete after pair
-// (d, 0), so the epilogue drains it while the MMAs of larger p continue, and
-// the next tile's first MMA into group d waits only for that drain.
-// Warp 0 issues the TMA loads (lane 0 the B chunks, lane 1 the A slices, each
-// running ahead as far as its buffers allow), warp 1 allocates TMEM and
-// issues the MMAs,
-// warps 2-9 drain the groups into 64-bit integers (registers) and update C.
+// Tensor-core shape (measured on B300): one tcgen05.mma of M = 128, K = 16
+// takes the same time for every N up to 256, so every MMA here has N = 256.
+// The eight weight groups of a 128 x 64 tile of C fill the 512 TMEM columns
+// (group d at columns 64 d), split into two 256-column windows X (groups 0-3)
+// and Y (groups 4-7).  For slice p of the tile rows, the MMA into a window
+// takes as its 256-row B operand four consecutive 64-row blocks of the stack
+// [0, 0, 0, B_0, B_1, ..., B_7] (B_q = slice q of the tile columns): the block
+// under group c is B_(c - p), or zero when c < p.  X needs slices p = 0..3,
+// Y all eight: 12 MMAs per K step for the 36 pairs (75% of the MMA work useful,
+// against 25% for N = 64 MMAs).
+//
+// Kernel anatomy (persistent, one CTA per SM): the K dimension streams through
+// two 108 KB stages (K = 32 per stage, 64-byte swizzled rows) holding all eight
+// slices of the tile rows (A) and of the tile columns (B, behind its three
+// zero blocks).  Warp 0 lane 0 issues the TMA loads, warp 1 allocates TMEM and
+// issues the MMAs (per stage the X MMAs, then the Y MMAs), warps 2-9 drain X
+// and then Y into 64-bit integers and update C.  The MMAs of the next tile
+// start on X as soon as the epilogue has read X (it does so while the last Y
+// MMAs of the tile run) and on Y once Y has been read; the FP64 update of C
+// overlaps the next tile's MMAs.  One launch also carries the two checksum
+// borders of the ABFT update (Sec. 3.1.2): the checksum rows are sliced into
+// the same tensor behind the panel rows, and their tiles (checksum rows x
+// panel rows, panel rows x checksum rows) join the work list.
 // Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -50,31 +61,41 @@ using namespace tc;
 namespace {
 
 constexpr int ES = 8;                       // slices per element
-constexpr int ETM = 128, ETN = 64, EKC = 64;
+constexpr int ETM = 128, ETN = 64;          // C tile
+constexpr int EKC = 32;                     // K per stage (64-byte rows)
 constexpr int EKMAX = 256;                  // panel width limit (exact FP32 accumulation)
-constexpr int ACHUNK = ETM * EKC * 2;       // 128 x 64 BF16 box
-constexpr int ASLOT = ACHUNK * (EKMAX / EKC);   // one slice of the tile rows, whole K
-constexpr int BCHUNK = ETN * EKC * 2;       // 64 x 64 BF16 box
-constexpr int BSTAGE = BCHUNK * (EKMAX / EKC);   // one slice of the tile columns, whole K
-constexpr int BSTAGES = 3;
+constexpr int A_SL = ETM * EKC * 2;         // 8 KB: one slice of the tile rows
+constexpr int B_BL = ETN * EKC * 2;         // 4 KB: one 64-row block of the B stack
+constexpr int NZ = 3;                       // zero blocks ahead of B_0
+constexpr int ST_A = ES * A_SL;
+constexpr int STAGE = ST_A + (NZ + ES) * B_BL;   // 108 KB
+constexpr int NSTAGE = 2;
+constexpr uint32_t STAGE_TX = (uint32_t)(ES * A_SL + ES * B_BL);
 constexpr int EPI_W = 8;
 constexpr int ETHREADS = 64 + EPI_W * 32;
-constexpr int NGROUP = 8;
-constexpr uint32_t ETMEM_COLS = 512;        // eight 64-column FP32 accumulators
-constexpr size_t E_SMEM = 2 * (size_t)ASLOT + (size_t)BSTAGES * BSTAGE + 1024 + 512;
+constexpr uint32_t ETMEM_COLS = 512;        // eight 64-column FP32 group accumulators
+constexpr size_t E_SMEM = (size_t)NSTAGE * STAGE + 1024 + 256;
 constexpr int FIXB = 40;                    // fraction bits of the fixed-point sum
 
 struct EmuArgs {
-    double* C;
+    double* C;          // trailing matrix (panel rows x panel rows, lower block triangle)
     int64_t ldc;
-    int64_t M;          // trailing order (rows of the panel slices)
-    int64_t K;          // panel width, multiple of 64, <= 256
-    const int* ex;      // e_i per panel row
+    double* C2;         // checksum rows x panel rows (nullable)
+    int64_t ldc2;
+    double* C3;         // panel rows x plain checksum rows, column i / nc (nullable)
+    int64_t ldc3;
+    int64_t M;          // panel rows
+    int64_t MC;         // checksum rows (behind the panel rows in the slices)
+    int64_t Mtot;       // rows per slice: M + MC
+    int64_t K;          // panel width, multiple of 32, <= 256
+    int nc;             // checksum rows per block row; plain rows are i % nc == 0
+    const int* ex;      // e_i per slice row
     int ncf;
     ComputeFault cf[MAX_CF];
     DevStatus* st;
-    int64_t ntiles;     // tiles of the lower block triangle (rm x rn per block pair)
+    int64_t n1, n2, n3; // work items: trailing tiles, border-row tiles, border-column tiles
     int64_t rm, rn;     // 128-row and 64-column tiles per g
+    int64_t c2, c3;     // column tiles of the two border families
     uint32_t idesc;
 };
 
@@ -89,6 +110,52 @@ __device__ __forceinline__ void emu_tile(int64_t idx, int64_t rm, int64_t rn, in
     tj = b * rn + sub % rn;
 }
 
+struct EmuItem {
+    int fam;            // 0 trailing, 1 border rows, 2 border columns
+    int64_t ti, tj;     // tile indices within the family
+    int64_t arow, brow; // first slice row of the A and B tiles
+    bool valid;
+};
+
+__device__ __forceinline__ EmuItem emu_item(int64_t idx, const EmuArgs& a) {
+    EmuItem t;
+    if (idx < a.n1) {
+        emu_tile(idx, a.rm, a.rn, t.ti, t.tj);
+        t.fam = 0;
+        t.arow = t.ti * ETM;
+        t.brow = t.tj * ETN;
+        t.valid = t.arow < a.M && t.brow < a.M;
+    } else if (idx < a.n1 + a.n2) {
+        const int64_t j = idx - a.n1;
+        t.fam = 1;
+        t.ti = j / a.c2;
+        t.tj = j % a.c2;
+        t.arow = a.M + t.ti * ETM;
+        t.brow = t.tj * ETN;
+        t.valid = true;
+    } else {
+        const int64_t j = idx - a.n1 - a.n2;
+        t.fam = 2;
+        t.ti = j / a.c3;
+        t.tj = j % a.c3;
+        t.arow = t.ti * ETM;
+        t.brow = a.M + t.tj * ETN;
+        t.valid = true;
+    }
+    return t;
+}
+
+// K-major operand with 64-byte swizzle: 8-row groups 512 bytes apart (SBO).
+__device__ __forceinline__ uint64_t desc64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
 // 2^k as a double for the normal range, 0 below it (k > 1023 does not occur:
 // the scales are bounded by the largest finite double).
 __device__ __forceinline__ double pow2(int k) {
@@ -98,6 +165,7 @@ __device__ __forceinline__ double pow2(int k) {
 
 __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ P, int64_t lda,
                                                      int64_t m, int kb, uint16_t* __restrict__ S,
+                                                     int64_t Mtot, int64_t row0,
                                                      int* __restrict__ ex) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + warp;
@@ -119,7 +187,7 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
         const int other = __shfl_xor_sync(0xffffffffu, emax, o);
         emax = other > emax ? other : emax;
     }
-    if (lane == 0) ex[row] = emax - 1022;
+    if (lane == 0) ex[row0 + row] = emax - 1022;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         if (t >= nt) continue;
@@ -144,7 +212,34 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
                 carry = 1;
             }
             const float v = (float)(neg ? -d : d);
-            S[((int64_t)p * m + row) * kb + k] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+            S[((int64_t)p * Mtot + row0 + row) * kb + k] =
+                __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        }
+    }
+}
+
+// Drain group accumulators d0 .. d0 + 3 (one window) of this thread's TMEM
+// lane and 32-column half into the 64-bit fixed-point sums acc.
+__device__ __forceinline__ void drain_window(uint32_t taddr, int d0, long long (&acc)[32],
+                                             uint64_t* freed, int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int d = d0 + i;
+        uint32_t v[32];
+        tmem_ld32(taddr + (uint32_t)(d * ETN), v);
+        if (i == 3) {   // the window has been read: the next tile's MMAs may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(freed))
+                             : "memory");
+        }
+        const int sh = FIXB - 7 * d;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            // an exact integer below 2^24 in magnitude
+            const long long iv = (long long)__float2int_rn(__uint_as_float(v[u]));
+            acc[u] += sh >= 0 ? iv * (1ll << sh) : (iv >> (-sh));
         }
     }
 }
@@ -154,36 +249,34 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                                                          EmuArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* abuf = smem;                                  // [2][ASLOT]
-    uint8_t* bring = smem + 2 * ASLOT;                     // [BSTAGES][BSTAGE]
-    uint64_t* fullA = (uint64_t*)(bring + BSTAGES * BSTAGE);
-    uint64_t* emptyA = fullA + 2;
-    uint64_t* fullB = emptyA + 2;
-    uint64_t* emptyB = fullB + BSTAGES;
-    uint64_t* accf = emptyB + BSTAGES;                     // [NGROUP]
-    uint64_t* acce = accf + NGROUP;                        // [NGROUP]
-    uint32_t* tmem_slot = (uint32_t*)(acce + NGROUP);
+    uint64_t* fullS = (uint64_t*)(smem + NSTAGE * STAGE);
+    uint64_t* emptyS = fullS + NSTAGE;
+    uint64_t* xdone = emptyS + NSTAGE;      // tile's X window complete
+    uint64_t* ydone = xdone + 1;
+    uint64_t* xfree = ydone + 1;            // X window read by the epilogue
+    uint64_t* yfree = xfree + 1;
+    uint32_t* tmem_slot = (uint32_t*)(yfree + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     if (a.st->info != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // zero blocks of the B stacks
+    for (int s2 = 0; s2 < NSTAGE; ++s2)
+        for (int i = threadIdx.x; i < NZ * B_BL / 16; i += ETHREADS)
+            *(uint4*)(smem + s2 * STAGE + ST_A + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) {
-        for (int s2 = 0; s2 < 2; ++s2) {
-            mbar_init(&fullA[s2], 1);
-            mbar_init(&emptyA[s2], 1);
+        for (int s2 = 0; s2 < NSTAGE; ++s2) {
+            mbar_init(&fullS[s2], 1);
+            mbar_init(&emptyS[s2], 1);
         }
-        for (int s2 = 0; s2 < BSTAGES; ++s2) {
-            mbar_init(&fullB[s2], 1);
-            mbar_init(&emptyB[s2], 1);
-        }
-        for (int d = 0; d < NGROUP; ++d) {
-            mbar_init(&accf[d], 1);
-            mbar_init(&acce[d], EPI_W);
-        }
+        mbar_init(xdone, 1);
+        mbar_init(ydone, 1);
+        mbar_init(xfree, EPI_W);
+        mbar_init(yfree, EPI_W);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -195,105 +288,81 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int nk = (int)(a.K / EKC);
-    const int64_t G = gridDim.x;
+    const int64_t G = gridDim.x, nitems = a.n1 + a.n2 + a.n3;
     auto fail = [&]() {
         *abort_flag = 1;
         atomicExch(&a.st->error, 3);
     };
 
     if (warp == 0) {
-        if (lane == 1) {          // TMA producer of the A slices (tile rows, whole K)
-            int64_t ca = 0;
+        if (lane == 0) {   // TMA producer: per stage all eight A slices and B blocks
+            int64_t c = 0;
             bool ok = true;
-            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
-                int64_t ti, tj;
-                emu_tile(idx, a.rm, a.rn, ti, tj);
-                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
-                for (int p = 0; p < ES; ++p, ++ca) {
-                    const int slot = (int)(ca & 1);
-                    if (ca >= 2 && !mbar_wait(&emptyA[slot], (uint32_t)(((ca >> 1) - 1) & 1))) {
+            for (int64_t idx = blockIdx.x; idx < nitems && ok && !*abort_flag; idx += G) {
+                const EmuItem t = emu_item(idx, a);
+                if (!t.valid) continue;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s2 = (int)(c % NSTAGE);
+                    if (c >= NSTAGE &&
+                        !mbar_wait(&emptyS[s2], (uint32_t)(((c / NSTAGE) - 1) & 1))) {
                         fail();
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&fullA[slot], (uint32_t)(ACHUNK * nk));
-                    const int ya = (int)((int64_t)p * a.M + ti * ETM);
-                    for (int kc = 0; kc < nk; ++kc)
-                        tma_load_2d(abuf + slot * ASLOT + kc * ACHUNK, &mapA, &fullA[slot], kc * EKC, ya);
-                }
-            }
-        } else if (lane == 0) {   // TMA producer of the B chunks (tile columns)
-            int64_t cb = 0;
-            bool ok = true;
-            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
-                int64_t ti, tj;
-                emu_tile(idx, a.rm, a.rn, ti, tj);
-                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
-                for (int p = 0; p < ES && ok; ++p) {
-                    for (int q = 0; q < ES - p; ++q, ++cb) {
-                        const int yb = (int)((int64_t)q * a.M + tj * ETN);
-                        const int s2 = (int)(cb % BSTAGES);
-                        if (cb >= BSTAGES &&
-                            !mbar_wait(&emptyB[s2], (uint32_t)(((cb / BSTAGES) - 1) & 1))) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        mbar_expect_tx(&fullB[s2], (uint32_t)(BCHUNK * nk));
-                        for (int kc = 0; kc < nk; ++kc)
-                            tma_load_2d(bring + s2 * BSTAGE + kc * BCHUNK, &mapB, &fullB[s2],
-                                        kc * EKC, yb);
-                    }
+                    uint8_t* st = smem + s2 * STAGE;
+                    mbar_expect_tx(&fullS[s2], STAGE_TX);
+                    for (int p = 0; p < ES; ++p)
+                        tma_load_2d(st + p * A_SL, &mapA, &fullS[s2], kc * EKC,
+                                    (int)(p * a.Mtot + t.arow));
+                    for (int q = 0; q < ES; ++q)
+                        tma_load_2d(st + ST_A + (NZ + q) * B_BL, &mapB, &fullS[s2], kc * EKC,
+                                    (int)(q * a.Mtot + t.brow));
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
-            int64_t ca = 0, cb = 0, tc = 0;
+            int64_t c = 0, tc = 0;
             bool ok = true;
-            for (int64_t idx = blockIdx.x; idx < a.ntiles && ok && !*abort_flag; idx += G) {
-                int64_t ti, tj;
-                emu_tile(idx, a.rm, a.rn, ti, tj);
-                if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
-                for (int p = 0; p < ES && ok; ++p, ++ca) {
-                    const int slot = (int)(ca & 1);
-                    if (!mbar_wait(&fullA[slot], (uint32_t)((ca >> 1) & 1))) {
+            const uint32_t tx = tmem, ty = tmem + 4 * ETN;
+            for (int64_t idx = blockIdx.x; idx < nitems && ok && !*abort_flag; idx += G) {
+                const EmuItem t = emu_item(idx, a);
+                if (!t.valid) continue;
+                for (int kc = 0; kc < nk && ok; ++kc, ++c) {
+                    const int s2 = (int)(c % NSTAGE);
+                    if (!mbar_wait(&fullS[s2], (uint32_t)((c / NSTAGE) & 1)) ||
+                        (kc == 0 && tc >= 1 && !mbar_wait(xfree, (uint32_t)((tc - 1) & 1)))) {
                         fail();
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t abase = smem_u32(abuf + slot * ASLOT);
-                    for (int q = 0; q < ES - p && ok; ++q, ++cb) {
-                        const int d = p + q;
-                        // first MMA of group d in this tile: its accumulator must be drained
-                        if (p == 0 && tc >= 1 && !mbar_wait(&acce[d], (uint32_t)((tc - 1) & 1))) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        const int s2 = (int)(cb % BSTAGES);
-                        if (!mbar_wait(&fullB[s2], (uint32_t)((cb / BSTAGES) & 1))) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t dt = tmem + (uint32_t)(d * ETN);
-                        // descriptors advance by 32 bytes per K = 16 step (field in 16-byte units)
-                        const uint64_t adesc0 = smem_desc(abase);
-                        const uint64_t bdesc0 = smem_desc(smem_u32(bring + s2 * BSTAGE));
-                        for (int kc = 0; kc < nk; ++kc) {
+                    const uint32_t sa = smem_u32(smem + s2 * STAGE);
+                    const uint64_t adesc = desc64(sa), bdesc = desc64(sa + ST_A);
+                    // descriptors advance by 32 bytes per K = 16 step (field in 16-byte units)
 #pragma unroll
-                            for (int kk = 0; kk < EKC / 16; ++kk)
-                                mma_f16(dt, adesc0 + (uint64_t)((kc * ACHUNK + kk * 32) >> 4),
-                                        bdesc0 + (uint64_t)((kc * BCHUNK + kk * 32) >> 4), a.idesc,
-                                        (p > 0 || kc > 0 || kk > 0) ? 1u : 0u);
-                        }
-                        mma_commit(&emptyB[s2]);
-                        if (q == 0) mma_commit(&accf[p]);   // pair (p, 0) ends group p
+                    for (int kk = 0; kk < EKC / 16; ++kk)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)   // X: groups 0-3, B blocks from NZ - p
+                            mma_f16(tx, adesc + (uint64_t)((p * A_SL + kk * 32) >> 4),
+                                    bdesc + (uint64_t)(((NZ - p) * B_BL + kk * 32) >> 4), a.idesc,
+                                    (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+                    if (kc == nk - 1) mma_commit(xdone);
+                    if (kc == 0 && tc >= 1 && !mbar_wait(yfree, (uint32_t)((tc - 1) & 1))) {
+                        fail();
+                        ok = false;
+                        break;
                     }
-                    if (ok) mma_commit(&emptyA[slot]);
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int kk = 0; kk < EKC / 16; ++kk)
+#pragma unroll
+                        for (int p = 0; p < ES; ++p)  // Y: groups 4-7, B blocks from NZ + 4 - p
+                            mma_f16(ty, adesc + (uint64_t)((p * A_SL + kk * 32) >> 4),
+                                    bdesc + (uint64_t)(((NZ + 4 - p) * B_BL + kk * 32) >> 4),
+                                    a.idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+                    mma_commit(&emptyS[s2]);
+                    if (kc == nk - 1) mma_commit(ydone);
                 }
                 ++tc;
             }
@@ -304,64 +373,63 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
         const int q = warp & 3;
         const int h = ew >> 2;
         const int r = q * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 32);
         int64_t tc = 0;
-        for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
-            int64_t ti, tj;
-            emu_tile(idx, a.rm, a.rn, ti, tj);
-            if (ti * ETM >= a.M || tj * ETN >= a.M) continue;
+        for (int64_t idx = blockIdx.x; idx < nitems; idx += G) {
+            const EmuItem t = emu_item(idx, a);
+            if (!t.valid) continue;
             long long acc[32];
 #pragma unroll
             for (int u = 0; u < 32; ++u) acc[u] = 0;
-            bool ok = true;
-            for (int d = 0; d < NGROUP; ++d) {
-                if (ok && !*abort_flag && mbar_wait(&accf[d], (uint32_t)(tc & 1))) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * ETN + h * 32), v);
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0)
-                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                         smem_u32(&acce[d]))
-                                     : "memory");
-                    const int sh = FIXB - 7 * d;
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        // an exact integer below 2^24 in magnitude
-                        const long long iv = (long long)__float2int_rn(__uint_as_float(v[u]));
-                        acc[u] += sh >= 0 ? iv * (1ll << sh) : (iv >> (-sh));
-                    }
-                } else {
-                    if (ok && !*abort_flag) fail();
-                    ok = false;
-                }
+            if (*abort_flag || !mbar_wait(xdone, (uint32_t)(tc & 1))) {
+                if (!*abort_flag) fail();
+                break;
             }
-            // C[i][j] -= A 2^(e_i + e_j - 54): this thread's row, 32 columns, all
-            // loads first
-            const int64_t gi = ti * ETM + r, jb = tj * ETN + h * 32;
-            if (ok && !*abort_flag && gi < a.M) {
-                double* crow = a.C + gi * a.ldc;
-                const int ei = a.ex[gi];
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    double cv[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int64_t gj = jb + 16 * half + u;
-                        cv[u] = gj < a.M ? crow[gj] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int64_t gj = jb + 16 * half + u;
-                        if (gj >= a.M) continue;
-                        double v = cv[u] - (double)acc[16 * half + u] * pow2(ei + a.ex[gj] - 54);
-                        for (int f = 0; f < a.ncf; ++f)
-                            if (a.cf[f].row == gi && a.cf[f].col == gj) v += a.cf[f].delta;
-                        crow[gj] = v;
-                    }
-                }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain_window(taddr, 0, acc, xfree, lane);
+            if (*abort_flag || !mbar_wait(ydone, (uint32_t)(tc & 1))) {
+                if (!*abort_flag) fail();
+                break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain_window(taddr, 4, acc, yfree, lane);
             ++tc;
+            // C[i][j] -= A 2^(e_i + e_j - 54) over this thread's row and 32 columns
+            const int64_t ri = t.ti * ETM + r, cb = t.tj * ETN + h * 32;
+            double* crow;
+            int ei;
+            int64_t colmax, ej0, cdiv;
+            if (t.fam == 0) {
+                if (ri >= a.M) continue;
+                crow = a.C + ri * a.ldc; ei = a.ex[ri]; colmax = a.M; ej0 = 0; cdiv = 1;
+            } else if (t.fam == 1) {
+                if (ri >= a.MC) continue;
+                crow = a.C2 + ri * a.ldc2; ei = a.ex[a.M + ri]; colmax = a.M; ej0 = 0; cdiv = 1;
+            } else {
+                if (ri >= a.M) continue;
+                crow = a.C3 + ri * a.ldc3; ei = a.ex[ri]; colmax = a.MC; ej0 = a.M; cdiv = a.nc;
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                double cv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {   // all loads first
+                    const int64_t gj = cb + 16 * half + u;
+                    cv[u] = (gj < colmax && (cdiv == 1 || gj % cdiv == 0))
+                                ? crow[cdiv == 1 ? gj : gj / cdiv]
+                                : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int64_t gj = cb + 16 * half + u;
+                    if (gj >= colmax || (cdiv != 1 && gj % cdiv != 0)) continue;
+                    double v = cv[u] - (double)acc[16 * half + u] * pow2(ei + a.ex[ej0 + gj] - 54);
+                    if (t.fam == 0)
+                        for (int f = 0; f < a.ncf; ++f)
+                            if (a.cf[f].row == ri && a.cf[f].col == gj) v += a.cf[f].delta;
+                    crow[cdiv == 1 ? gj : gj / cdiv] = v;
+                }
+            }
         }
     }
     __syncwarp();
@@ -382,35 +450,45 @@ bool encode_slices(CUtensorMap* map, const uint16_t* S, int64_t rows, int64_t kb
     cuuint32_t box[2] = {(cuuint32_t)EKC, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)S, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
+int64_t emu_rows(int64_t n, int64_t nb) {
+    return n + 2 * ((n + nb - 1) / nb);
+}
+
 size_t emu_slice_bytes(int64_t n, int64_t nb) {
-    return sizeof(uint16_t) * (size_t)ES * (size_t)n * (size_t)nb;
+    return sizeof(uint16_t) * (size_t)ES * (size_t)emu_rows(n, nb) * (size_t)nb;
 }
 
 cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
-                               int* ex, cudaStream_t s) {
+                               int64_t Mtot, int64_t row0, int* ex, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    if (kb % 32 != 0 || kb > 256) return cudaErrorInvalidValue;
-    k_slice_panel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(P, lda, m, (int)kb, S, ex);
+    if (kb % 32 != 0 || kb > 256 || row0 + m > Mtot) return cudaErrorInvalidValue;
+    k_slice_panel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(P, lda, m, (int)kb, S, Mtot, row0, ex);
     note_launch();
     return cudaGetLastError();
 }
 
-// C (m x m, trailing, FP64) -= L L^T on the lower block triangle (blocks of g),
-// from the slices S (7 x m x kb BF16) and row exponents ex of the panel L.
+// C (m x m, trailing, FP64) -= L L^T on the lower block triangle (blocks of g)
+// from the slices S (8 x (m + mc) x kb BF16, the panel L in rows 0 .. m - 1 and
+// the checksum rows in m .. m + mc - 1) and the row exponents ex; with borders:
+// C2 (mc x m) -= L_c L^T and C3[i][c / nc] -= (L L_c^T)[i][c] for the plain
+// checksum rows c.
 cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
-                           int64_t ldc, int64_t g, const ComputeFault* cf, int ncf, DevStatus* st,
-                           cudaStream_t s) {
+                           int64_t ldc, int64_t g, const EmuBorders& eb, const ComputeFault* cf,
+                           int ncf, DevStatus* st, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     if (kb % EKC != 0 || kb > EKMAX || g % ETM != 0) return cudaErrorInvalidValue;
+    if ((eb.C2 || eb.C3) && (eb.mc <= 0 || eb.nc <= 0)) return cudaErrorInvalidValue;
+    const int64_t mc = (eb.C2 || eb.C3) ? eb.mc : 0, mtot = m + mc;
+    if ((int64_t)ES * mtot + ETM > INT32_MAX) return cudaErrorInvalidValue;
     CUtensorMap mapA, mapB;
-    if (!encode_slices(&mapA, S, ES * m, kb, ETM) || !encode_slices(&mapB, S, ES * m, kb, ETN))
+    if (!encode_slices(&mapA, S, ES * mtot, kb, ETM) || !encode_slices(&mapB, S, ES * mtot, kb, ETN))
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -421,17 +499,24 @@ cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t 
     }
     EmuArgs a{};
     a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.ex = ex; a.st = st;
+    a.C2 = eb.C2; a.ldc2 = eb.ldc2; a.C3 = eb.C3; a.ldc3 = eb.ldc3;
+    a.MC = mc; a.Mtot = mtot; a.nc = eb.nc > 0 ? eb.nc : 1;
     a.ncf = 0;
     for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
     const int64_t qb = (m + g - 1) / g;
     a.rm = g / ETM;
     a.rn = g / ETN;
-    a.ntiles = qb * (qb + 1) / 2 * a.rm * a.rn;
-    // kind::f16 instruction descriptor: D F32, A/B BF16, K-major, N >> 3, M >> 4
-    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ETN >> 3) << 17) |
+    a.n1 = qb * (qb + 1) / 2 * a.rm * a.rn;
+    a.c2 = (m + ETN - 1) / ETN;
+    a.n2 = eb.C2 ? (mc + ETM - 1) / ETM * a.c2 : 0;
+    a.c3 = (mc + ETN - 1) / ETN;
+    a.n3 = eb.C3 ? (m + ETM - 1) / ETM * a.c3 : 0;
+    // kind::f16 instruction descriptor: D F32, A/B BF16, K-major, N = 256, M = 128
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
               ((uint32_t)(ETM >> 4) << 24);
+    const int64_t items = a.n1 + a.n2 + a.n3;
     int64_t grid = num_sms();
-    if (grid > a.ntiles) grid = a.ntiles;
+    if (grid > items) grid = items;
     k_tmu_emu<<<(unsigned)grid, ETHREADS, E_SMEM, s>>>(mapA, mapB, a);
     note_launch();
     return cudaGetLastError();
