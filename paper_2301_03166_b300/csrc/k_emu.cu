@@ -38,8 +38,10 @@
 // two 108 KB stages (K = 32 per stage, 64-byte swizzled rows) holding all eight
 // slices of the tile rows (A) and of the tile columns (B, behind its three
 // zero blocks).  Warp 0 lane 0 issues the TMA loads, warp 1 allocates TMEM and
-// issues the MMAs (per stage the X MMAs, then the Y MMAs), warps 2-9 drain X
-// and then Y into 64-bit integers and update C.  The MMAs of the next tile
+// issues the MMAs (per stage the X MMAs, then the Y MMAs), warps 2-17 drain X
+// and then Y into 64-bit integers and update C (each warp a TMEM lane quarter
+// and 16 columns, read in the 16x256b shape so that C moves in 64-byte row
+// segments).  The MMAs of the next tile
 // start on X as soon as the epilogue has read X (it does so while the last Y
 // MMAs of the tile run) and on Y once Y has been read; the FP64 update of C
 // overlaps the next tile's MMAs.  One launch also carries the two checksum
@@ -70,8 +72,9 @@ constexpr int NZ = 3;                       // zero blocks ahead of B_0
 constexpr int ST_A = ES * A_SL;
 constexpr int STAGE = ST_A + (NZ + ES) * B_BL;   // 108 KB
 constexpr int NSTAGE = 2;
+constexpr int ECOLS = ETN / 4;             // columns per epilogue thread
 constexpr uint32_t STAGE_TX = (uint32_t)(ES * A_SL + ES * B_BL);
-constexpr int EPI_W = 8;
+constexpr int EPI_W = 16;                   // 4 TMEM lane quarters x 4 column quarters
 constexpr int ETHREADS = 64 + EPI_W * 32;
 constexpr uint32_t ETMEM_COLS = 512;        // eight 64-column FP32 group accumulators
 constexpr size_t E_SMEM = (size_t)NSTAGE * STAGE + 1024 + 256;
@@ -89,6 +92,7 @@ struct EmuArgs {
     int64_t Mtot;       // rows per slice: M + MC
     int64_t K;          // panel width, multiple of 32, <= 256
     int nc;             // checksum rows per block row; plain rows are i % nc == 0
+    bool vec1, vec2;    // C / C2 rows 16-byte aligned at even columns (double2 access)
     const int* ex;      // e_i per slice row
     int ncf;
     ComputeFault cf[MAX_CF];
@@ -218,15 +222,19 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
     }
 }
 
-// Drain group accumulators d0 .. d0 + 3 (one window) of this thread's TMEM
-// lane and 32-column half into the 64-bit fixed-point sums acc.
-__device__ __forceinline__ void drain_window(uint32_t taddr, int d0, long long (&acc)[32],
+// Drain group accumulators d0 .. d0 + 3 (one window) into the 64-bit
+// fixed-point sums acc.  taddr addresses this warp's 32 TMEM lanes and 16
+// columns; acc[8 hh + k] holds element k of the 16x256b fragment of lanes
+// 16 hh .. 16 hh + 15.
+__device__ __forceinline__ void drain_window(uint32_t taddr, int d0, long long (&acc)[ECOLS],
                                              uint64_t* freed, int lane) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int d = d0 + i;
-        uint32_t v[32];
-        tmem_ld32(taddr + (uint32_t)(d * ETN), v);
+        uint32_t v0[8], v1[8];
+        tmem_ld16x256_x2(taddr + (uint32_t)(d * ETN), v0);
+        tmem_ld16x256_x2(taddr + (16u << 16) + (uint32_t)(d * ETN), v1);
+        tmem_wait_ld();
         if (i == 3) {   // the window has been read: the next tile's MMAs may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -236,9 +244,10 @@ __device__ __forceinline__ void drain_window(uint32_t taddr, int d0, long long (
         }
         const int sh = FIXB - 7 * d;
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
+        for (int u = 0; u < ECOLS; ++u) {
             // an exact integer below 2^24 in magnitude
-            const long long iv = (long long)__float2int_rn(__uint_as_float(v[u]));
+            const float f = __uint_as_float(u < 8 ? v0[u] : v1[u - 8]);
+            const long long iv = (long long)__float2int_rn(f);
             acc[u] += sh >= 0 ? iv * (1ll << sh) : (iv >> (-sh));
         }
     }
@@ -340,9 +349,9 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                     const uint32_t sa = smem_u32(smem + s2 * STAGE);
                     const uint64_t adesc = desc64(sa), bdesc = desc64(sa + ST_A);
                     // descriptors advance by 32 bytes per K = 16 step (field in 16-byte units)
-#pragma unroll
+#pragma unroll 1
                     for (int kk = 0; kk < EKC / 16; ++kk)
-#pragma unroll
+#pragma unroll 1
                         for (int p = 0; p < 4; ++p)   // X: groups 0-3, B blocks from NZ - p
                             mma_f16(tx, adesc + (uint64_t)((p * A_SL + kk * 32) >> 4),
                                     bdesc + (uint64_t)(((NZ - p) * B_BL + kk * 32) >> 4), a.idesc,
@@ -354,9 +363,9 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
+#pragma unroll 1
                     for (int kk = 0; kk < EKC / 16; ++kk)
-#pragma unroll
+#pragma unroll 1
                         for (int p = 0; p < ES; ++p)  // Y: groups 4-7, B blocks from NZ + 4 - p
                             mma_f16(ty, adesc + (uint64_t)((p * A_SL + kk * 32) >> 4),
                                     bdesc + (uint64_t)(((NZ + 4 - p) * B_BL + kk * 32) >> 4),
@@ -368,19 +377,21 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
             }
         }
     } else {
-        // epilogue: TMEM lane quarter q (rows 32 q ..), column half h (32 columns)
+        // epilogue: warp (q, cq) drains TMEM lanes 32 q .. 32 q + 31 (tile rows)
+        // and columns 16 cq .. 16 cq + 15 of every group in the 16x256b shape:
+        // four neighbouring threads hold eight consecutive columns of one row,
+        // so C moves in full 64-byte row segments
         const int ew = warp - 2;
         const int q = warp & 3;
-        const int h = ew >> 2;
-        const int r = q * 32 + lane;
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 32);
+        const int cq = ew >> 2;
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * ECOLS);
         int64_t tc = 0;
         for (int64_t idx = blockIdx.x; idx < nitems; idx += G) {
             const EmuItem t = emu_item(idx, a);
             if (!t.valid) continue;
-            long long acc[32];
+            long long acc[ECOLS];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) acc[u] = 0;
+            for (int u = 0; u < ECOLS; ++u) acc[u] = 0;
             if (*abort_flag || !mbar_wait(xdone, (uint32_t)(tc & 1))) {
                 if (!*abort_flag) fail();
                 break;
@@ -394,40 +405,66 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             drain_window(taddr, 4, acc, yfree, lane);
             ++tc;
-            // C[i][j] -= A 2^(e_i + e_j - 54) over this thread's row and 32 columns
-            const int64_t ri = t.ti * ETM + r, cb = t.tj * ETN + h * 32;
-            double* crow;
-            int ei;
-            int64_t colmax, ej0, cdiv;
-            if (t.fam == 0) {
-                if (ri >= a.M) continue;
-                crow = a.C + ri * a.ldc; ei = a.ex[ri]; colmax = a.M; ej0 = 0; cdiv = 1;
-            } else if (t.fam == 1) {
-                if (ri >= a.MC) continue;
-                crow = a.C2 + ri * a.ldc2; ei = a.ex[a.M + ri]; colmax = a.M; ej0 = 0; cdiv = 1;
-            } else {
-                if (ri >= a.M) continue;
-                crow = a.C3 + ri * a.ldc3; ei = a.ex[ri]; colmax = a.MC; ej0 = a.M; cdiv = a.nc;
-            }
+            // C[i][j] -= A 2^(e_i + e_j - 54) over rows 32 q + 16 hh + 8 rr + lane / 4
+            // and column pairs 16 cq + 8 j + 2 (lane % 4)
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                double cv[16];
+            for (int hr = 0; hr < 4; ++hr) {
+                const int hh = hr >> 1, rr = hr & 1;
+                const int ri = (int)(t.ti * ETM) + 32 * q + 16 * hh + 8 * rr + (lane >> 2);
+                double* crow = nullptr;
+                int ei = 0, colmax = 0, ej0 = 0, cdiv = 1;
+                bool vec = false;
+                if (t.fam == 0) {
+                    if (ri < a.M) {
+                        crow = a.C + ri * a.ldc; ei = a.ex[ri]; colmax = (int)a.M; vec = a.vec1;
+                    }
+                } else if (t.fam == 1) {
+                    if (ri < a.MC) {
+                        crow = a.C2 + ri * a.ldc2; ei = a.ex[a.M + ri]; colmax = (int)a.M;
+                        vec = a.vec2;
+                    }
+                } else if (ri < a.M) {
+                    crow = a.C3 + ri * a.ldc3; ei = a.ex[ri];
+                    colmax = (int)a.MC; ej0 = (int)a.M; cdiv = a.nc;
+                }
+                if (!crow) continue;
+                double2 cv[2];
+                const int gj0 = (int)(t.tj * ETN) + 16 * cq + 2 * (lane & 3);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {   // all loads first
-                    const int64_t gj = cb + 16 * half + u;
-                    cv[u] = (gj < colmax && (cdiv == 1 || gj % cdiv == 0))
-                                ? crow[cdiv == 1 ? gj : gj / cdiv]
-                                : 0.0;
+                for (int j = 0; j < 2; ++j) {   // loads first
+                    const int gj = gj0 + 8 * j;
+                    if (vec && gj + 1 < colmax) {
+                        cv[j] = *(const double2*)(crow + gj);
+                    } else {
+                        cv[j].x = (gj < colmax && (cdiv == 1 || gj % cdiv == 0))
+                                      ? crow[cdiv == 1 ? gj : gj / cdiv] : 0.0;
+                        cv[j].y = (gj + 1 < colmax && (cdiv == 1 || (gj + 1) % cdiv == 0))
+                                      ? crow[cdiv == 1 ? gj + 1 : (gj + 1) / cdiv] : 0.0;
+                    }
                 }
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int64_t gj = cb + 16 * half + u;
-                    if (gj >= colmax || (cdiv != 1 && gj % cdiv != 0)) continue;
-                    double v = cv[u] - (double)acc[16 * half + u] * pow2(ei + a.ex[ej0 + gj] - 54);
-                    if (t.fam == 0)
-                        for (int f = 0; f < a.ncf; ++f)
-                            if (a.cf[f].row == ri && a.cf[f].col == gj) v += a.cf[f].delta;
-                    crow[cdiv == 1 ? gj : gj / cdiv] = v;
+                for (int j = 0; j < 2; ++j) {
+                    const int gj = gj0 + 8 * j;
+                    double v[2] = {cv[j].x, cv[j].y};
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (gj + c >= colmax) continue;
+                        v[c] -= (double)acc[8 * hh + 4 * j + 2 * rr + c] *
+                                pow2(ei + a.ex[ej0 + gj + c] - 54);
+                        if (t.fam == 0)
+#pragma unroll
+                            for (int f = 0; f < MAX_CF; ++f)   // static indices: no local copy
+                                if (f < a.ncf && a.cf[f].row == ri && a.cf[f].col == gj + c)
+                                    v[c] += a.cf[f].delta;
+                    }
+                    if (vec && gj + 1 < colmax) {
+                        *(double2*)(crow + gj) = make_double2(v[0], v[1]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+                            if (gj + c < colmax && (cdiv == 1 || (gj + c) % cdiv == 0))
+                                crow[cdiv == 1 ? gj + c : (gj + c) / cdiv] = v[c];
+                    }
                 }
             }
         }
@@ -501,6 +538,8 @@ cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t 
     a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.ex = ex; a.st = st;
     a.C2 = eb.C2; a.ldc2 = eb.ldc2; a.C3 = eb.C3; a.ldc3 = eb.ldc3;
     a.MC = mc; a.Mtot = mtot; a.nc = eb.nc > 0 ? eb.nc : 1;
+    a.vec1 = ((uintptr_t)C % 16 == 0) && ldc % 2 == 0;
+    a.vec2 = ((uintptr_t)eb.C2 % 16 == 0) && eb.ldc2 % 2 == 0;
     a.ncf = 0;
     for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
     const int64_t qb = (m + g - 1) / g;
