@@ -24,6 +24,7 @@ struct DevStatus {
     double umax;                       // running max |u_ij| (LU)
     int error;                         // internal error code (timeouts)
     int lu_info;                       // LU: 1-based first exactly-zero pivot (factorization continues)
+    int vexp;                          // > 0: biased exponent bound of the verified entries (fixed-point sums)
     unsigned int bar_arrive;           // grid barrier of the cooperative panel kernels
     unsigned int bar_gen;
     abft_fault loc[ABFT_MAX_LOC];

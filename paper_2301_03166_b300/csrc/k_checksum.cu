@@ -8,6 +8,17 @@
 // every global load is a coalesced 256-byte row segment and the tile is read
 // from HBM exactly once.  Row sums use warp shuffles.  All reductions run in a
 // fixed order, so repeated runs give identical sums.
+//
+// Verification sums in fixed point: B300 issues one FP64 instruction per
+// sub-partition every ~64 cycles, so FP64 column / row / weighted sums bound the
+// verify by the FP64 pipe.  When the factorization has a magnitude bound
+// (st->vexp > 0: every entry has biased exponent <= vexp), each entry is
+// rounded to an integer multiple of 2^(vexp - 1075) (at most half a unit,
+// 2^-53 of the bound, per entry) and summed exactly in 64-bit integers on the
+// integer pipes; the weighted sums use units 2^10 larger to stay inside 64
+// bits.  A tile holding an entry above the bound (an injected error, a NaN)
+// is summed again in FP64, so detection, location and correction see the
+// same quantities either way.
 #include <math.h>
 
 #include "common.cuh"
@@ -107,6 +118,102 @@ __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* 
     }
 }
 
+// An entry as a signed multiple of 2^(vexp - 1075), rounded to nearest (half
+// away from zero); bad = true when its exponent exceeds vexp (or it is not
+// finite).
+__device__ __forceinline__ long long to_fixed(double x, int vexp, bool& bad) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    if (e > vexp) {
+        bad = true;
+        return 0;
+    }
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    const int sh = vexp - (e ? e : 1);
+    const unsigned long long q = sh >= 64 ? 0ull : (sh == 0 ? mant : ((mant >> (sh - 1)) + 1ull) >> 1);
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// tile_sums in exact 64-bit fixed point (same outputs, converted to double
+// once per sum).  Returns false, with nothing written, when an entry of the
+// tile exceeds the bound: the caller then sums in FP64.
+template <int TM, bool COLW, bool ROWS>
+__device__ bool tile_sums_fixed(const double* T, int64_t ldt, int nr, int nc, int vexp,
+                                double* colsum, double* wsum, double* rowsum,
+                                double (*part)[kMaxG]) {
+    constexpr int U = 32 / TM;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = (nc + 31) >> 5;
+    long long acc[TM], wacc[TM];
+#pragma unroll
+    for (int t = 0; t < TM; ++t) { acc[t] = 0; wacc[t] = 0; }
+    bool bad = false;
+    long long (*ipart)[kMaxG] = reinterpret_cast<long long (*)[kMaxG]>(part);
+    long long* irow = reinterpret_cast<long long*>(rowsum);
+    for (int i0 = warp; i0 < nr; i0 += U * kWarps) {
+        double v[U][TM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            const double* row = T + (int64_t)i * ldt;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                const int j = lane + 32 * t;
+                v[u][t] = (t < nt && i < nr && j < nc) ? row[j] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            long long rs = 0;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                const long long q = to_fixed(v[u][t], vexp, bad);
+                acc[t] += q;
+                if (COLW) wacc[t] += (long long)(i + 1) * (q >> 10);
+                rs += q;
+            }
+            if (ROWS) {
+                rs = warp_sum_ll(rs);
+                if (lane == 0 && i < nr) irow[i] = rs;
+            }
+        }
+    }
+    if (__syncthreads_or(bad ? 1 : 0)) return false;
+    const double unit = ldexp(1.0, vexp - 1075), wunit = ldexp(1.0, vexp - 1065);
+#pragma unroll
+    for (int t = 0; t < TM; ++t)
+        if (t < nt) ipart[warp][lane + 32 * t] = acc[t];
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        long long s = 0;
+        for (int w = 0; w < kWarps; ++w) s += ipart[w][j];
+        colsum[j] = (double)s * unit;
+    }
+    if (ROWS)
+        for (int i = threadIdx.x; i < nr; i += kThreads) rowsum[i] = (double)irow[i] * unit;
+    __syncthreads();
+    if (COLW) {
+#pragma unroll
+        for (int t = 0; t < TM; ++t)
+            if (t < nt) ipart[warp][lane + 32 * t] = wacc[t];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            long long s = 0;
+            for (int w = 0; w < kWarps; ++w) s += ipart[w][j];
+            wsum[j] = (double)s * wunit;
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
 __device__ __forceinline__ void tile_extent(const TileSet& ts, int64_t I, int64_t J, int& nr,
                                             int& nc) {
     int64_t r0 = I * ts.g, c0 = J * ts.g;
@@ -162,8 +269,12 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     double* cw = (MODE == MODE_SINGLE) ? ts.cw + I * ts.ccI + J * ts.g : nullptr;
     double* cr = (MODE == MODE_FULL) ? ts.cr + r0 * ts.crs + J * ts.crJ : nullptr;
     if (threadIdx.x == 0) { s_nfc = 0; s_nfr = 0; s_fc = 1 << 30; s_fr = 1 << 30; }
-    tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum, rowsum,
-                                                         part);
+    const int vexp = st->vexp;
+    if (vexp <= 0 ||
+        !tile_sums_fixed<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, vexp, colsum,
+                                                                     wsum, rowsum, part))
+        tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum,
+                                                             rowsum, part);
     const double tau = st->tau;
     double dmax = 0.0;
     // d = recomputed - carried, kept in place of the sums
@@ -307,6 +418,10 @@ __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, d
         t *= (double)g;
         t *= m;
         st->tau = t;
+        // entries of the Schur complements are bounded by max a_ii, panel
+        // entries by sqrt(max a_ii): the fixed-point verify bound
+        const double bnd = fmax(m, sqrt(m));
+        st->vexp = (bnd > 0.0 && bnd < 1e300) ? (int)((__double_as_longlong(bnd) >> 52) & 0x7ff) : 0;
     }
 }
 
