@@ -433,6 +433,23 @@ int abft_potrf_noalloc(int64_t n, int64_t nb, int32_t dtype, int32_t mode, doubl
 size_t abft_noalloc_capacity(void);
 
 /*
+ * abft_set_lookahead(on): look-ahead of the blocked Cholesky (Sec. 2.1, the
+ *   look-ahead of Fig. example-lu (b), here on one GPU).  On (the default),
+ *   abft_potrf / abft_posv_* with one checksum mode for all steps split each
+ *   trailing update: the next block column is updated and verified first,
+ *   then the next diagonal block is factored (PD of the next step, with its
+ *   checksum check) on the caller's stream while the rest of the update and
+ *   its verification run on an internal stream of the calling thread; the
+ *   caller's stream waits for both before the next panel solve.  Every kernel
+ *   performs the same arithmetic either way: factors, reports and return codes
+ *   are identical with look-ahead on and off.  Per-step schedules
+ *   (abft_potrf_sched) always run sequentially.  The internal stream and its
+ *   events are created on the first call that uses them on a device (make it
+ *   before any stream capture).  Returns the previous setting (0 or 1).
+ */
+int abft_set_lookahead(int32_t on);
+
+/*
  * Diagnostics (no counterpart in the paper; the paper profiles per-operation
  * times only to predict slack, Sec. 3.2.1).
  * abft_timing_enable(on): when on != 0, every entry point records CUDA events

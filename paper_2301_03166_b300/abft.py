@@ -100,6 +100,8 @@ def lib():
             fn.argtypes = argt
             fn.restype = ctypes.c_int
         L.abft_timing_enable.argtypes = [_i32]
+        L.abft_set_lookahead.argtypes = [_i32]
+        L.abft_set_lookahead.restype = ctypes.c_int
         L.abft_timing_enable.restype = ctypes.c_int
         L.abft_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         L.abft_timing_read.restype = ctypes.c_int
@@ -263,6 +265,13 @@ def adaptive_modes(n, nb, lambdas, fc_desired, step_seconds):
 
 
 PHASES = ("pd", "pu", "tmu", "verify", "other", "solve")
+
+
+def set_lookahead(on=True):
+    """Look-ahead of the blocked Cholesky (next diagonal block factored on a
+    side stream while the rest of the update runs); returns the previous
+    setting.  Results are identical either way."""
+    return bool(lib().abft_set_lookahead(1 if on else 0))
 
 
 def timing_enable(on=True):

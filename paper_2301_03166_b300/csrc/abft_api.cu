@@ -197,11 +197,47 @@ cudaError_t chol_pd(double* A, int64_t lda, int64_t kb, int64_t K0, const double
     return cudaSuccess;
 }
 
+// Side stream and events of the look-ahead, per device and calling thread.
+struct LookAhead {
+    int dev = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ready = nullptr, rest_done = nullptr;
+};
+
+cudaError_t lookahead_streams(LookAhead*& out) {
+    thread_local LookAhead la[16];   // per thread: concurrent callers never share events
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+    LookAhead& l = la[dev];
+    if (l.dev != dev) {
+        e = cudaStreamCreateWithFlags(&l.side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.rest_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        l.dev = dev;
+    }
+    out = &l;
+    return cudaSuccess;
+}
+
+std::atomic<int> g_lookahead{1};
+
 // Blocked ABFT Cholesky step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
 // modes (nullable, host, one entry per step): the checksum mode of each step
 // (adaptive ABFT); nullptr runs every step in `mode`.  A step in mode NONE
 // neither carries nor verifies checksums; the trailing block triangle is
 // encoded afresh when checking starts again or moves from SINGLE to FULL.
+//
+// Look-ahead (Sec. 2.1, Fig. example-lu (b), on one GPU): with a uniform mode
+// and at least two trailing block columns, the update of step k is split.  The
+// next block column is updated and verified first; the factorization of the
+// next diagonal block (PD of step k + 1) then runs on the caller's stream
+// while the rest of the update and its verification run on a side stream
+// (the persistent tensor-core updates leave the PD's SMs free), and the
+// caller's stream waits for both before the next panel solve.  Every kernel
+// does the same arithmetic either way, so the results are identical.
 int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double* A, int64_t lda,
                const abft_fault* faults, int32_t nfaults, double tau_scale, const CholWs& w,
                char* base, cudaStream_t s, int32_t dtype) {
@@ -216,6 +252,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     double* Cr = (double*)(base + w.cr);
     double* save = (double*)(base + w.save);
     const int64_t g = nb, nt = w.nt, nc = w.nc, N = nt;
+    LookAhead* la = nullptr;
+    if (modes == nullptr && g_lookahead.load() && n > 2 * nb) ABFT_CUDA_TRY(lookahead_streams(la));
 
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 0, s));
@@ -228,6 +266,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     base_ts.g = g; base_ts.nrow_end = n; base_ts.ncol_end = n;
     base_ts.weighted = 1;
     timing_mark(PH_OTHER, 0, s);
+    enum { PART_ALL = 0, PART_NEXT = 1, PART_REST = 2 };
+    bool pd_ahead = false;   // PD of this step already run by the previous step's look-ahead
     for (int64_t k = 0; k < N; ++k) {
         const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
         double* Akk = A + K0 * lda + K0;
@@ -243,10 +283,13 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             timing_mark(PH_OTHER, 0, s);
         }
         // PD and its checksum check
-        timing_mark(PH_PD, 1, s);
-        ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, check ? CS + (k * nc) * n + K0 : nullptr,
-                              check ? 1 : 0, (int)k, (double*)(base + w.pdpart), st, s));
-        timing_mark(PH_PD, 0, s);
+        if (!pd_ahead) {
+            timing_mark(PH_PD, 1, s);
+            ABFT_CUDA_TRY(chol_pd(Akk, lda, kb, K0, check ? CS + (k * nc) * n + K0 : nullptr,
+                                  check ? 1 : 0, (int)k, (double*)(base + w.pdpart), st, s));
+            timing_mark(PH_PD, 0, s);
+        }
+        pd_ahead = false;
         if (m <= 0) break;
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
         timing_mark(PH_PU, 1, s);
@@ -264,110 +307,171 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ABFT_CUDA_TRY(launch_verify(ts, MODE_SINGLE, (int)k, st, s));
         }
         timing_mark(PH_PU, 0, s);
-        if (emu) {
-            // FP64-accurate TMU from exact BF16 slice products; the checksum
-            // rows are sliced behind the panel rows and their border products
-            // (c_I -= s_I L_J^T, and in FULL mode r_I -= L_I s_J^T) run in the
-            // same launch
+
+        // TMU of part p: PART_ALL the lower block triangle of the trailing
+        // matrix, PART_NEXT its first block column (w columns), PART_REST the
+        // triangle after it; each with its share of the checksum borders.
+        const bool split = la != nullptr && m > g;
+        const int64_t w1 = std::min(g, m);
+        const int64_t mc = check ? (nt - k - 1) * nc : 0;
+        const int reserve = split ? pd_cluster_size() : 0;
+        ComputeFault cfall[MAX_CF];
+        int ncfall = 0;
+        for (int f = 0; f < nfaults && ncfall < MAX_CF; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                cfall[ncfall++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
+        if (emu) {   // the panel and checksum rows are sliced once for both parts
             timing_mark(PH_TMU, 1, s);
-            uint16_t* Sl = (uint16_t*)(base + w.eslice);
-            int* ex = (int*)(base + w.eex);
-            EmuBorders eb;
-            if (check) {
-                eb.mc = (nt - k - 1) * nc;
-                eb.nc = (int)nc;
-                eb.C2 = CS + ((k + 1) * nc) * n + T0; eb.ldc2 = n;
-                if (full) { eb.C3 = Cr + T0 * nt + (k + 1); eb.ldc3 = nt; }
-            }
-            const int64_t mtot = m + eb.mc;
-            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, Sl, mtot, 0, ex, s));
+            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, (uint16_t*)(base + w.eslice),
+                                             m + mc, 0, (int*)(base + w.eex), s));
             if (check)
-                ABFT_CUDA_TRY(launch_slice_panel(CS + ((k + 1) * nc) * n + K0, n, eb.mc, kb, Sl,
-                                                 mtot, m, ex, s));
-            ComputeFault ecf[MAX_CF];
-            int encf = 0;
-            for (int f = 0; f < nfaults && encf < MAX_CF; ++f)
-                if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
-                    ecf[encf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
-            ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, m, kb, A + T0 * lda + T0, lda, g, eb, ecf, encf,
-                                         st, s));
+                ABFT_CUDA_TRY(launch_slice_panel(CS + ((k + 1) * nc) * n + K0, n, mc, kb,
+                                                 (uint16_t*)(base + w.eslice), m + mc, m,
+                                                 (int*)(base + w.eex), s));
             timing_mark(PH_TMU, 0, s);
         } else if (mixed) {
-            // TMU on the tensor cores: quantized panel, FP32 accumulation, FP64 C
-            const int64_t ncq = nc > 0 ? nc : 1;
             timing_mark(PH_TMU, 1, s);
+            const int64_t ncq = nc > 0 ? nc : 1;
             ABFT_CUDA_TRY(launch_quant_panel(A + K0, lda, T0, n, kb, g, k + 1, nt, bf16, Lq, sig, tq,
                                              ncq * kb, check ? 1 : 0, s));
-            ComputeFault mcf[MAX_CF];
-            int mncf = 0;
-            for (int f = 0; f < nfaults && mncf < MAX_CF; ++f)
-                if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
-                    mcf[mncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
-            ABFT_CUDA_TRY(launch_tmu_mixed(Lq, m, kb, bf16, A + T0 * lda + T0, lda, g, T0, sig, mcf,
-                                           mncf, st, s));
-            if (check) {
-                BorderSegHost bs[2] = {};
-                // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
-                bs[0].A = tq + ((k + 1) * ncq) * kb; bs[0].a_half = 0; bs[0].lda = kb;
-                bs[0].B = Lq; bs[0].b_half = 1; bs[0].ldb = kb;
-                bs[0].C = CS + ((k + 1) * nc) * n + T0; bs[0].ldc = n;
-                bs[0].M = (nt - k - 1) * nc; bs[0].N = m; bs[0].K = kb;
-                bs[0].r_off = 0; bs[0].r_div = nc; bs[0].r_base = k + 1;
-                bs[0].c_off = T0; bs[0].c_div = g; bs[0].c_base = 0;
-                // row-sum columns: r_I -= sigma_I sigma_J (Lq_I t_J^T)
-                bs[1].A = Lq; bs[1].a_half = 1; bs[1].lda = kb;
-                bs[1].B = tq + ((k + 1) * ncq) * kb; bs[1].b_half = 0; bs[1].ldb = ncq * kb;
-                bs[1].C = Cr + T0 * nt + (k + 1); bs[1].ldc = nt;
-                bs[1].M = m; bs[1].N = nt - k - 1; bs[1].K = kb;
-                bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;
-                bs[1].c_off = 0; bs[1].c_div = 1; bs[1].c_base = k + 1;
-                ABFT_CUDA_TRY(launch_border_mixed(bs, full ? 2 : 1, bf16, sig, st, s));
-            }
             timing_mark(PH_TMU, 0, s);
+        }
+        auto tmu = [&](int part, cudaStream_t ss) -> int {
+            // columns [c0, c1) of the trailing matrix, block-column range [J0, J1)
+            const int64_t c0 = part == PART_REST ? w1 : 0, c1 = part == PART_NEXT ? w1 : m;
+            const int64_t J0 = k + 1 + (part == PART_REST ? 1 : 0);
+            const int64_t J1 = part == PART_NEXT ? k + 2 : nt;
+            const int maxg = part == PART_REST ? std::max(1, num_sms() - reserve) : 0;
+            timing_mark(PH_TMU, 1, ss);
+            if (emu) {
+                // FP64-accurate TMU from exact BF16 slice products; the checksum
+                // rows sit behind the panel rows in the slice tensor
+                const uint16_t* Sl = (const uint16_t*)(base + w.eslice);
+                const int* ex = (const int*)(base + w.eex);
+                EmuRectHost rc[3] = {};
+                int nr = 0;
+                int64_t tri_m = 0, tri_o = 0;
+                if (part == PART_NEXT) {
+                    EmuRectHost& r = rc[nr++];
+                    r.C = A + T0 * lda + T0; r.ldc = lda;
+                    r.a0 = 0; r.na = m; r.b0 = 0; r.nb = w1; r.cdiv = 1; r.frow = 0; r.fcol = 0;
+                } else {
+                    tri_m = m;
+                    tri_o = c0;
+                }
+                if (check) {   // border rows: c_I -= s_I L_J^T (and the weighted rows)
+                    EmuRectHost& r = rc[nr++];
+                    r.C = CS + ((k + 1) * nc) * n + T0 + c0; r.ldc = n;
+                    r.a0 = m; r.na = mc; r.b0 = c0; r.nb = c1 - c0; r.cdiv = 1; r.frow = -1;
+                }
+                if (full) {    // border columns: r_I -= L_I s_J^T (plain checksum rows)
+                    EmuRectHost& r = rc[nr++];
+                    r.C = Cr + T0 * nt + J0; r.ldc = nt;
+                    r.a0 = 0; r.na = m; r.b0 = m + (J0 - k - 1) * nc; r.nb = (J1 - J0) * nc;
+                    r.cdiv = (int)nc; r.frow = -1;
+                }
+                ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, m + mc, kb, A + T0 * lda + T0, lda, tri_m,
+                                             tri_o, g, rc, nr, cfall, ncfall, maxg, st, ss));
+            } else if (mixed) {
+                // TMU on the tensor cores: quantized panel, FP32 accumulation, FP64 C
+                const int64_t ncq = nc > 0 ? nc : 1;
+                ABFT_CUDA_TRY(launch_tmu_mixed(Lq, m, kb, bf16, A + T0 * lda + T0, lda, g, T0, sig,
+                                               cfall, ncfall, st, ss, part == PART_REST ? w1 : 0,
+                                               part == PART_NEXT ? 1 : 0, maxg));
+                if (check) {
+                    BorderSegHost bs[2] = {};
+                    // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
+                    bs[0].A = tq + ((k + 1) * ncq) * kb; bs[0].a_half = 0; bs[0].lda = kb;
+                    bs[0].B = Lq + c0 * kb; bs[0].b_half = 1; bs[0].ldb = kb;
+                    bs[0].C = CS + ((k + 1) * nc) * n + T0 + c0; bs[0].ldc = n;
+                    bs[0].M = (nt - k - 1) * nc; bs[0].N = c1 - c0; bs[0].K = kb;
+                    bs[0].r_off = 0; bs[0].r_div = nc; bs[0].r_base = k + 1;
+                    bs[0].c_off = T0 + c0; bs[0].c_div = g; bs[0].c_base = 0;
+                    // row-sum columns: r_I -= sigma_I sigma_J (Lq_I t_J^T)
+                    bs[1].A = Lq; bs[1].a_half = 1; bs[1].lda = kb;
+                    bs[1].B = tq + (J0 * ncq) * kb; bs[1].b_half = 0; bs[1].ldb = ncq * kb;
+                    bs[1].C = Cr + T0 * nt + J0; bs[1].ldc = nt;
+                    bs[1].M = m; bs[1].N = J1 - J0; bs[1].K = kb;
+                    bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;
+                    bs[1].c_off = 0; bs[1].c_div = 1; bs[1].c_base = J0;
+                    ABFT_CUDA_TRY(launch_border_mixed(bs, full ? 2 : 1, bf16, sig, st, ss));
+                }
+            } else {
+                // TMU with the checksum borders folded into the same launch
+                GemmSeg gs[3] = {};
+                ComputeFault cf[MAX_CF];
+                int ncf = 0;
+                if (part == PART_NEXT) {   // the next block column, no mask
+                    gs[0].A = A + T0 * lda + K0; gs[0].lda = lda;
+                    gs[0].B = A + T0 * lda + K0; gs[0].ldb = lda;
+                    gs[0].C = A + T0 * lda + T0; gs[0].ldc = lda;
+                    gs[0].M = m; gs[0].N = w1; gs[0].K = kb;
+                } else {                   // the lower block triangle from column c0
+                    gs[0].A = A + (T0 + c0) * lda + K0; gs[0].lda = lda;
+                    gs[0].B = A + (T0 + c0) * lda + K0; gs[0].ldb = lda;
+                    gs[0].C = A + (T0 + c0) * lda + T0 + c0; gs[0].ldc = lda;
+                    gs[0].M = m - c0; gs[0].N = m - c0; gs[0].K = kb;
+                    gs[0].g = g; gs[0].row0 = T0 + c0; gs[0].col0 = T0 + c0;
+                }
+                for (int f = 0; f < ncfall; ++f)   // faults in segment 0 coordinates
+                    cf[ncf++] = {cfall[f].row - c0, cfall[f].col - c0, cfall[f].delta};
+                int nseg = 1;
+                if (check) {  // border rows: c_I -= s_I L_J^T (and the weighted rows)
+                    GemmSeg& b = gs[nseg++];
+                    b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
+                    b.B = A + (T0 + c0) * lda + K0; b.ldb = lda;
+                    b.C = CS + ((k + 1) * nc) * n + T0 + c0; b.ldc = n;
+                    b.M = (nt - k - 1) * nc; b.N = c1 - c0; b.K = kb;
+                }
+                if (full) {   // border columns: r_I -= L_I s_J^T
+                    GemmSeg& b = gs[nseg++];
+                    b.A = A + T0 * lda + K0; b.lda = lda;
+                    b.B = CS + (J0 * nc) * n + K0; b.ldb = nc * n;
+                    b.C = Cr + T0 * nt + J0; b.ldc = nt;
+                    b.M = m; b.N = J1 - J0; b.K = kb;
+                }
+                ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 0, cf, ncf, st, ss));
+            }
+            timing_mark(PH_TMU, 0, ss);
+            // storage errors of this step in these columns, then the verification
+            timing_mark(PH_VERIFY, 1, ss);
+            for (int f = 0; f < nfaults; ++f)
+                if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
+                                            faults[f].kind == ABFT_FAULT_ROW1D ||
+                                            faults[f].kind == ABFT_FAULT_COL1D) &&
+                    faults[f].col - T0 >= c0 && faults[f].col - T0 < c1)
+                    ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], ss));
+            if (check) {
+                TileSet ts = base_ts;
+                ts.I0 = J0; ts.I1 = nt; ts.J0 = J0; ts.J1 = J1; ts.lower = part == PART_NEXT ? 0 : 1;
+                ABFT_CUDA_TRY(launch_verify(ts, mk, (int)k, st, ss));
+            }
+            timing_mark(PH_VERIFY, 0, ss);
+            return ABFT_OK;
+        };
+        if (!split) {
+            const int rc = tmu(PART_ALL, s);
+            if (rc != ABFT_OK) return rc;
         } else {
-        // TMU with the checksum borders folded into the same launch
-        GemmSeg gs[3] = {};
-        gs[0].A = A + T0 * lda + K0; gs[0].lda = lda;
-        gs[0].B = A + T0 * lda + K0; gs[0].ldb = lda;
-        gs[0].C = A + T0 * lda + T0; gs[0].ldc = lda;
-        gs[0].M = m; gs[0].N = m; gs[0].K = kb;
-        gs[0].g = g; gs[0].row0 = T0; gs[0].col0 = T0;
-        int nseg = 1;
-        if (check) {  // border rows: c_I -= s_I L_J^T (and the weighted rows)
-            GemmSeg& b = gs[nseg++];
-            b.A = CS + ((k + 1) * nc) * n + K0; b.lda = n;
-            b.B = A + T0 * lda + K0; b.ldb = lda;
-            b.C = CS + ((k + 1) * nc) * n + T0; b.ldc = n;
-            b.M = (nt - k - 1) * nc; b.N = m; b.K = kb;
+            int rc = tmu(PART_NEXT, s);
+            if (rc != ABFT_OK) return rc;
+            // the rest of the update on the side stream; PD of step k + 1 next on
+            // the caller's stream, so that the cluster PD is dispatched first and
+            // the capped persistent grid of the update fills the other SMs
+            ABFT_CUDA_TRY(cudaEventRecord(la->ready, s));
+            ABFT_CUDA_TRY(cudaStreamWaitEvent(la->side, la->ready, 0));
+            const int64_t K1 = T0, kb1 = std::min(g, n - K1);
+            timing_mark(PH_PD, 1, s);
+            ABFT_CUDA_TRY(chol_pd(A + K1 * lda + K1, lda, kb1, K1,
+                                  check ? CS + ((k + 1) * nc) * n + K1 : nullptr, check ? 1 : 0,
+                                  (int)(k + 1), (double*)(base + w.pdpart), st, s));
+            timing_mark(PH_PD, 0, s);
+            rc = tmu(PART_REST, la->side);
+            if (rc != ABFT_OK) return rc;
+            ABFT_CUDA_TRY(cudaEventRecord(la->rest_done, la->side));
+            ABFT_CUDA_TRY(cudaStreamWaitEvent(s, la->rest_done, 0));
+            pd_ahead = true;
         }
-        if (full) {   // border columns: r_I -= L_I s_J^T
-            GemmSeg& b = gs[nseg++];
-            b.A = A + T0 * lda + K0; b.lda = lda;
-            b.B = CS + ((k + 1) * nc) * n + K0; b.ldb = nc * n;
-            b.C = Cr + T0 * nt + (k + 1); b.ldc = nt;
-            b.M = m; b.N = nt - k - 1; b.K = kb;
-        }
-        ComputeFault cf[MAX_CF];
-        int ncf = 0;
-        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
-            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
-                cf[ncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
-        timing_mark(PH_TMU, 1, s);
-        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 0, cf, ncf, st, s));
-        timing_mark(PH_TMU, 0, s);
-        }
-        timing_mark(PH_VERIFY, 1, s);
-        for (int f = 0; f < nfaults; ++f)
-            if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
-                                        faults[f].kind == ABFT_FAULT_ROW1D ||
-                                        faults[f].kind == ABFT_FAULT_COL1D))
-                ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));
-        if (check) {
-            TileSet ts = base_ts;
-            ts.I0 = k + 1; ts.I1 = nt; ts.J0 = k + 1; ts.J1 = nt; ts.lower = 1;
-            ABFT_CUDA_TRY(launch_verify(ts, mk, (int)k, st, s));
-        }
-        timing_mark(PH_VERIFY, 0, s);
     }
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 1, s));
@@ -1469,6 +1573,10 @@ extern "C" {
 const char* abft_version(void) { return "abft-b300 0.1 (sm_103a)"; }
 
 int64_t abft_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int abft_set_lookahead(int32_t on) {
+    return g_lookahead.exchange(on != 0 ? 1 : 0);
+}
 
 int abft_timing_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_tmu);

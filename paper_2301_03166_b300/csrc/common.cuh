@@ -154,6 +154,7 @@ cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_
 // FP64 factorization of a kb x kb (kb <= 256) diagonal block by one thread-block
 // cluster; check != 0 then tests it against the carried column checksum cc
 // (k_pd_cluster.cu).  A non-positive pivot sets info = K0 + column + 1.
+int pd_cluster_size();   // CTAs of the cluster PD (16 where supported, else 8)
 cudaError_t launch_potrf_pd_cluster(double* A, int64_t lda, int64_t kb, int64_t K0,
                                     const double* cc, int step, int check, DevStatus* st,
                                     cudaStream_t s);
@@ -231,7 +232,8 @@ cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t
                                cudaStream_t s);
 cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
                              int64_t ldc, int64_t g, int64_t off, const double* sig,
-                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s);
+                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s,
+                             int64_t o = 0, int strip = 0, int max_grid = 0);
 cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
                                 const DevStatus* st, cudaStream_t s);
 
@@ -320,21 +322,22 @@ cudaError_t timing_collect(cudaStream_t s);
 
 // FP64-accurate trailing update from BF16 slices (k_emu.cu).  The slice
 // tensor holds emu_rows(n, nb) rows: the panel rows, then the checksum rows.
-struct EmuBorders {
-    double* C2 = nullptr;   // checksum rows x panel rows (row-major, ld ldc2), or null
-    int64_t ldc2 = 0;
-    double* C3 = nullptr;   // panel rows x plain checksum rows (ld ldc3), or null
-    int64_t ldc3 = 0;
-    int64_t mc = 0;         // checksum rows sliced behind the panel rows
-    int nc = 0;             // checksum rows per block row (plain ones at i % nc == 0)
+struct EmuRectHost {
+    double* C;              // C[i * ldc + j / cdiv] for i < na, j < nb with j % cdiv == 0
+    int64_t ldc;
+    int64_t a0, na;         // A operand: slice rows a0 .. a0 + na - 1
+    int64_t b0, nb;         // B operand: slice rows b0 .. b0 + nb - 1
+    int cdiv;
+    int64_t frow, fcol;     // trailing coordinates of (0, 0) for compute faults (-1: none)
 };
 int64_t emu_rows(int64_t n, int64_t nb);
 size_t emu_slice_bytes(int64_t n, int64_t nb);
 cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
                                int64_t Mtot, int64_t row0, int* ex, cudaStream_t s);
-cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
-                           int64_t ldc, int64_t g, const EmuBorders& eb, const ComputeFault* cf,
-                           int ncf, DevStatus* st, cudaStream_t s);
+cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t mtot, int64_t kb, double* C,
+                           int64_t ldc, int64_t M, int64_t o, int64_t g, const EmuRectHost* rects,
+                           int nrect, const ComputeFault* cf, int ncf, int max_grid, DevStatus* st,
+                           cudaStream_t s);
 
 // GMRES-IR pieces (k_gmres.cu); vectors are n x 16 blocks (ld 16), basis
 // vector i at V + i * vstride.

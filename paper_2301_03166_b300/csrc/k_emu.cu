@@ -47,7 +47,9 @@
 // overlaps the next tile's MMAs.  One launch also carries the two checksum
 // borders of the ABFT update (Sec. 3.1.2): the checksum rows are sliced into
 // the same tensor behind the panel rows, and their tiles (checksum rows x
-// panel rows, panel rows x checksum rows) join the work list.
+// panel rows, panel rows x checksum rows) join the work list as rectangles;
+// a rectangle also carries the next block column alone when the update is
+// split for look-ahead.
 // Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -80,26 +82,33 @@ constexpr uint32_t ETMEM_COLS = 512;        // eight 64-column FP32 group accumu
 constexpr size_t E_SMEM = (size_t)NSTAGE * STAGE + 1024 + 256;
 constexpr int FIXB = 40;                    // fraction bits of the fixed-point sum
 
-struct EmuArgs {
-    double* C;          // trailing matrix (panel rows x panel rows, lower block triangle)
+struct EmuRect {
+    double* C;          // C[i * ldc + j / cdiv] for local row i < na, column j < nb, j % cdiv == 0
     int64_t ldc;
-    double* C2;         // checksum rows x panel rows (nullable)
-    int64_t ldc2;
-    double* C3;         // panel rows x plain checksum rows, column i / nc (nullable)
-    int64_t ldc3;
-    int64_t M;          // panel rows
-    int64_t MC;         // checksum rows (behind the panel rows in the slices)
-    int64_t Mtot;       // rows per slice: M + MC
+    int a0, na;         // A operand: slice rows a0 .. a0 + na - 1
+    int b0, nb;         // B operand: slice rows b0 .. b0 + nb - 1
+    int cdiv;
+    int ntj;            // 64-column tiles
+    int frow, fcol;     // trailing coordinates of local (0, 0) for compute faults (-1: none)
+    bool vec;           // double2 access (cdiv 1, rows 16-byte aligned)
+};
+
+struct EmuArgs {
+    double* C;          // trailing matrix: the triangle covers rows and columns [o, M)
+    int64_t ldc;
+    int64_t M, o;
+    int64_t Mtot;       // rows per slice
     int64_t K;          // panel width, multiple of 32, <= 256
-    int nc;             // checksum rows per block row; plain rows are i % nc == 0
-    bool vec1, vec2;    // C / C2 rows 16-byte aligned at even columns (double2 access)
     const int* ex;      // e_i per slice row
     int ncf;
-    ComputeFault cf[MAX_CF];
+    ComputeFault cf[MAX_CF];   // trailing coordinates
     DevStatus* st;
-    int64_t n1, n2, n3; // work items: trailing tiles, border-row tiles, border-column tiles
+    int64_t n1;         // tiles of the lower block triangle
     int64_t rm, rn;     // 128-row and 64-column tiles per g
-    int64_t c2, c3;     // column tiles of the two border families
+    int nrect;
+    EmuRect rect[3];
+    int64_t rend[3];    // cumulative rectangle tile counts
+    bool vec1;          // triangle rows 16-byte aligned at even columns
     uint32_t idesc;
 };
 
@@ -114,9 +123,15 @@ __device__ __forceinline__ void emu_tile(int64_t idx, int64_t rm, int64_t rn, in
     tj = b * rn + sub % rn;
 }
 
+// rect[r] with static indices (a runtime index into the parameter block would
+// copy it to local memory)
+__device__ __forceinline__ EmuRect rect_of(const EmuArgs& a, int r) {
+    return r == 0 ? a.rect[0] : (r == 1 ? a.rect[1] : a.rect[2]);
+}
+
 struct EmuItem {
-    int fam;            // 0 trailing, 1 border rows, 2 border columns
-    int64_t ti, tj;     // tile indices within the family
+    int seg;            // -1 triangle, else the rectangle
+    int64_t ti, tj;     // tile indices within the segment
     int64_t arow, brow; // first slice row of the A and B tiles
     bool valid;
 };
@@ -125,25 +140,22 @@ __device__ __forceinline__ EmuItem emu_item(int64_t idx, const EmuArgs& a) {
     EmuItem t;
     if (idx < a.n1) {
         emu_tile(idx, a.rm, a.rn, t.ti, t.tj);
-        t.fam = 0;
-        t.arow = t.ti * ETM;
-        t.brow = t.tj * ETN;
+        t.seg = -1;
+        t.arow = a.o + t.ti * ETM;
+        t.brow = a.o + t.tj * ETN;
         t.valid = t.arow < a.M && t.brow < a.M;
-    } else if (idx < a.n1 + a.n2) {
-        const int64_t j = idx - a.n1;
-        t.fam = 1;
-        t.ti = j / a.c2;
-        t.tj = j % a.c2;
-        t.arow = a.M + t.ti * ETM;
-        t.brow = t.tj * ETN;
-        t.valid = true;
     } else {
-        const int64_t j = idx - a.n1 - a.n2;
-        t.fam = 2;
-        t.ti = j / a.c3;
-        t.tj = j % a.c3;
-        t.arow = t.ti * ETM;
-        t.brow = a.M + t.tj * ETN;
+        int64_t j = idx - a.n1;
+        int r = 0;
+        if (a.nrect > 1 && j >= a.rend[0]) r = 1;
+        if (a.nrect > 2 && j >= a.rend[1]) r = 2;
+        j -= r == 0 ? 0 : (r == 1 ? a.rend[0] : a.rend[1]);
+        const EmuRect e = rect_of(a, r);
+        t.seg = r;
+        t.ti = j / e.ntj;
+        t.tj = j % e.ntj;
+        t.arow = e.a0 + t.ti * ETM;
+        t.brow = e.b0 + t.tj * ETN;
         t.valid = true;
     }
     return t;
@@ -297,7 +309,7 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int nk = (int)(a.K / EKC);
-    const int64_t G = gridDim.x, nitems = a.n1 + a.n2 + a.n3;
+    const int64_t G = gridDim.x, nitems = a.n1 + (a.nrect == 0 ? 0 : (a.nrect == 1 ? a.rend[0] : (a.nrect == 2 ? a.rend[1] : a.rend[2])));
     auto fail = [&]() {
         *abort_flag = 1;
         atomicExch(&a.st->error, 3);
@@ -412,20 +424,22 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                 const int hh = hr >> 1, rr = hr & 1;
                 const int ri = (int)(t.ti * ETM) + 32 * q + 16 * hh + 8 * rr + (lane >> 2);
                 double* crow = nullptr;
-                int ei = 0, colmax = 0, ej0 = 0, cdiv = 1;
+                int ei = 0, colmax = 0, ej0 = 0, cdiv = 1, frow = -1, fcol = 0;
                 bool vec = false;
-                if (t.fam == 0) {
-                    if (ri < a.M) {
-                        crow = a.C + ri * a.ldc; ei = a.ex[ri]; colmax = (int)a.M; vec = a.vec1;
+                if (t.seg < 0) {
+                    const int gi = (int)a.o + ri;
+                    if (gi < a.M) {
+                        crow = a.C + (int64_t)gi * a.ldc + a.o; ei = a.ex[gi];
+                        colmax = (int)(a.M - a.o); ej0 = (int)a.o; vec = a.vec1;
+                        frow = gi; fcol = (int)a.o;
                     }
-                } else if (t.fam == 1) {
-                    if (ri < a.MC) {
-                        crow = a.C2 + ri * a.ldc2; ei = a.ex[a.M + ri]; colmax = (int)a.M;
-                        vec = a.vec2;
+                } else {
+                    const EmuRect e = rect_of(a, t.seg);
+                    if (ri < e.na) {
+                        crow = e.C + (int64_t)ri * e.ldc; ei = a.ex[e.a0 + ri];
+                        colmax = e.nb; ej0 = e.b0; cdiv = e.cdiv; vec = e.vec;
+                        frow = e.frow >= 0 ? e.frow + ri : -1; fcol = e.fcol;
                     }
-                } else if (ri < a.M) {
-                    crow = a.C3 + ri * a.ldc3; ei = a.ex[ri];
-                    colmax = (int)a.MC; ej0 = (int)a.M; cdiv = a.nc;
                 }
                 if (!crow) continue;
                 double2 cv[2];
@@ -451,10 +465,10 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                         if (gj + c >= colmax) continue;
                         v[c] -= (double)acc[8 * hh + 4 * j + 2 * rr + c] *
                                 pow2(ei + a.ex[ej0 + gj + c] - 54);
-                        if (t.fam == 0)
+                        if (frow >= 0)
 #pragma unroll
                             for (int f = 0; f < MAX_CF; ++f)   // static indices: no local copy
-                                if (f < a.ncf && a.cf[f].row == ri && a.cf[f].col == gj + c)
+                                if (f < a.ncf && a.cf[f].row == frow && a.cf[f].col == fcol + gj + c)
                                     v[c] += a.cf[f].delta;
                     }
                     if (vec && gj + 1 < colmax) {
@@ -511,19 +525,46 @@ cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t 
     return cudaGetLastError();
 }
 
-// C (m x m, trailing, FP64) -= L L^T on the lower block triangle (blocks of g)
-// from the slices S (8 x (m + mc) x kb BF16, the panel L in rows 0 .. m - 1 and
-// the checksum rows in m .. m + mc - 1) and the row exponents ex; with borders:
-// C2 (mc x m) -= L_c L^T and C3[i][c / nc] -= (L L_c^T)[i][c] for the plain
-// checksum rows c.
-cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t kb, double* C,
-                           int64_t ldc, int64_t g, const EmuBorders& eb, const ComputeFault* cf,
-                           int ncf, DevStatus* st, cudaStream_t s) {
-    if (m <= 0) return cudaSuccess;
-    if (kb % EKC != 0 || kb > EKMAX || g % ETM != 0) return cudaErrorInvalidValue;
-    if ((eb.C2 || eb.C3) && (eb.mc <= 0 || eb.nc <= 0)) return cudaErrorInvalidValue;
-    const int64_t mc = (eb.C2 || eb.C3) ? eb.mc : 0, mtot = m + mc;
+// One launch of the emulated update: the lower block triangle of the trailing
+// matrix C (rows and columns [o, M), blocks of g; M <= o: none) and up to three
+// rectangles, all from the slice tensor S (8 x mtot x kb BF16) and the row
+// exponents ex.  Compute faults are in trailing coordinates.  max_grid > 0
+// caps the persistent grid (SMs left to a concurrent panel factorization).
+cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t mtot, int64_t kb, double* C,
+                           int64_t ldc, int64_t M, int64_t o, int64_t g, const EmuRectHost* rects,
+                           int nrect, const ComputeFault* cf, int ncf, int max_grid, DevStatus* st,
+                           cudaStream_t s) {
+    if (kb % EKC != 0 || kb > EKMAX || g % ETM != 0 || nrect < 0 || nrect > 3 || o % g != 0)
+        return cudaErrorInvalidValue;
     if ((int64_t)ES * mtot + ETM > INT32_MAX) return cudaErrorInvalidValue;
+    EmuArgs a{};
+    a.C = C; a.ldc = ldc; a.M = M; a.o = o; a.K = kb; a.ex = ex; a.st = st; a.Mtot = mtot;
+    a.vec1 = ((uintptr_t)C % 16 == 0) && ldc % 2 == 0;
+    a.ncf = 0;
+    for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
+    const int64_t qb = M > o ? (M - o + g - 1) / g : 0;
+    a.rm = g / ETM;
+    a.rn = g / ETN;
+    a.n1 = qb * (qb + 1) / 2 * a.rm * a.rn;
+    int64_t tot = 0;
+    for (int r = 0; r < nrect; ++r) {
+        const EmuRectHost& h = rects[r];
+        if (h.na <= 0 || h.nb <= 0) continue;
+        if (h.a0 < 0 || h.b0 < 0 || h.a0 + h.na > mtot || h.b0 + h.nb > mtot || h.cdiv < 1)
+            return cudaErrorInvalidValue;
+        EmuRect& e = a.rect[a.nrect];
+        e.C = h.C; e.ldc = h.ldc;
+        e.a0 = (int)h.a0; e.na = (int)h.na; e.b0 = (int)h.b0; e.nb = (int)h.nb;
+        e.cdiv = h.cdiv;
+        e.ntj = (int)((h.nb + ETN - 1) / ETN);
+        e.frow = (int)h.frow; e.fcol = (int)h.fcol;
+        e.vec = h.cdiv == 1 && ((uintptr_t)h.C % 16 == 0) && h.ldc % 2 == 0;
+        tot += (h.na + ETM - 1) / ETM * e.ntj;
+        a.rend[a.nrect] = tot;
+        ++a.nrect;
+    }
+    const int64_t items = a.n1 + tot;
+    if (items == 0) return cudaSuccess;
     CUtensorMap mapA, mapB;
     if (!encode_slices(&mapA, S, ES * mtot, kb, ETM) || !encode_slices(&mapB, S, ES * mtot, kb, ETN))
         return cudaErrorInvalidValue;
@@ -534,27 +575,11 @@ cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t m, int64_t 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    EmuArgs a{};
-    a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.ex = ex; a.st = st;
-    a.C2 = eb.C2; a.ldc2 = eb.ldc2; a.C3 = eb.C3; a.ldc3 = eb.ldc3;
-    a.MC = mc; a.Mtot = mtot; a.nc = eb.nc > 0 ? eb.nc : 1;
-    a.vec1 = ((uintptr_t)C % 16 == 0) && ldc % 2 == 0;
-    a.vec2 = ((uintptr_t)eb.C2 % 16 == 0) && eb.ldc2 % 2 == 0;
-    a.ncf = 0;
-    for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
-    const int64_t qb = (m + g - 1) / g;
-    a.rm = g / ETM;
-    a.rn = g / ETN;
-    a.n1 = qb * (qb + 1) / 2 * a.rm * a.rn;
-    a.c2 = (m + ETN - 1) / ETN;
-    a.n2 = eb.C2 ? (mc + ETM - 1) / ETM * a.c2 : 0;
-    a.c3 = (mc + ETN - 1) / ETN;
-    a.n3 = eb.C3 ? (m + ETM - 1) / ETM * a.c3 : 0;
     // kind::f16 instruction descriptor: D F32, A/B BF16, K-major, N = 256, M = 128
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
               ((uint32_t)(ETM >> 4) << 24);
-    const int64_t items = a.n1 + a.n2 + a.n3;
     int64_t grid = num_sms();
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid > items) grid = items;
     k_tmu_emu<<<(unsigned)grid, ETHREADS, E_SMEM, s>>>(mapA, mapB, a);
     note_launch();

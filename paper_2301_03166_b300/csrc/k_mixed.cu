@@ -63,8 +63,10 @@ struct MixArgs {
     int ncf;
     ComputeFault cf[MAX_CF];
     DevStatus* st;
-    int64_t ntiles;     // tiles of the lower block triangle (r x r per block pair)
+    int64_t ntiles;     // tiles of the block pairs (r x r per block pair)
     int64_t r;          // 128-tiles per g
+    int64_t o;          // triangle origin (a multiple of g)
+    int strip;          // 1: only the first block column (all block rows), no triangle
     uint32_t idesc;
 };
 
@@ -102,6 +104,20 @@ __device__ __forceinline__ void lower_tile(int64_t idx, int64_t r, int64_t& ti, 
     const int64_t b = pair - a * (a + 1) / 2;
     ti = a * r + sub / r;
     tj = b * r + sub % r;
+}
+
+// The idx-th tile: of the lower block triangle of [o, M) (strip = 0), or of the
+// first block column of [0, M) (strip = 1, the look-ahead part).
+__device__ __forceinline__ void mix_tile(const MixArgs& a, int64_t idx, int64_t& ti, int64_t& tj) {
+    if (a.strip) {
+        const int64_t r2 = a.r * a.r, pair = idx / r2, sub = idx % r2;
+        ti = pair * a.r + sub / a.r;
+        tj = sub % a.r;
+    } else {
+        lower_tile(idx, a.r, ti, tj);
+        ti += a.o / TM;
+        tj += a.o / TM;
+    }
 }
 
 // Persistent warp-specialized update: CTA c handles tiles c, c + G, c + 2G, ...
@@ -150,7 +166,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
             int64_t c = 0;
             for (int64_t idx = blockIdx.x; idx < a.ntiles && !*abort_flag; idx += G) {
                 int64_t ti, tj;
-                lower_tile(idx, a.r, ti, tj);
+                mix_tile(a, idx, ti, tj);
                 if (ti * TM >= a.M || tj * TN >= a.M) continue;
                 for (int kc = 0; kc < nk; ++kc, ++c) {
                     const int s = (int)(c % STAGES);
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
             int64_t c = 0, it = 0;
             for (int64_t idx = blockIdx.x; idx < a.ntiles && !*abort_flag; idx += G) {
                 int64_t ti, tj;
-                lower_tile(idx, a.r, ti, tj);
+                mix_tile(a, idx, ti, tj);
                 if (ti * TM >= a.M || tj * TN >= a.M) continue;
                 const int b = (int)(it & 1);
                 if (it >= 2 && !mbar_wait(&acce[b], (uint32_t)(((it >> 1) - 1) & 1))) {
@@ -212,7 +228,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
         int64_t it = 0;
         for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
             int64_t ti, tj;
-            lower_tile(idx, a.r, ti, tj);
+            mix_tile(a, idx, ti, tj);
             if (ti * TM >= a.M || tj * TN >= a.M) continue;
             const int b = (int)(it & 1);
             bool ok = !*abort_flag && mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1));
@@ -510,11 +526,15 @@ cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t
     return cudaGetLastError();
 }
 
-// C (m x m, trailing, FP64) -= sigma sigma^T o (Lq Lq^T) on the lower block triangle.
+// C (m x m, trailing, FP64) -= sigma sigma^T o (Lq Lq^T) on the lower block
+// triangle of [o, m) (strip = 0) or on the first block column (strip = 1);
+// max_grid > 0 caps the persistent grid.
 cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
                              int64_t ldc, int64_t g, int64_t off, const double* sig,
-                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s) {
-    if (m <= 0) return cudaSuccess;
+                             const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s,
+                             int64_t o, int strip, int max_grid) {
+    if (m <= 0 || (!strip && o >= m)) return cudaSuccess;
+    if (o % g != 0 || (strip && o != 0)) return cudaErrorInvalidValue;
     if (kb % KC != 0) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
@@ -539,15 +559,22 @@ cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16
     a.C = C; a.ldc = ldc; a.M = m; a.K = kb; a.g = g; a.off = off; a.sig = sig; a.st = st;
     a.ncf = 0;
     for (int f = 0; f < ncf && f < MAX_CF; ++f) a.cf[a.ncf++] = cf[f];
-    const int64_t q = (m + g - 1) / g;
     a.r = g / TM;
-    a.ntiles = q * (q + 1) / 2 * a.r * a.r;
+    a.o = o;
+    a.strip = strip;
+    if (strip) {
+        a.ntiles = (m + g - 1) / g * a.r * a.r;
+    } else {
+        const int64_t q = (m - o + g - 1) / g;
+        a.ntiles = q * (q + 1) / 2 * a.r * a.r;
+    }
     // kind::f16 instruction descriptor: D F32 (bits 4-5), A/B format BF16 = 1 or
     // F16 = 0 (bits 7-9, 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
     const uint32_t fmt = bf16 ? 1u : 0u;
     a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) |
               ((uint32_t)(TM >> 4) << 24);
     int64_t grid = num_sms();
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid > a.ntiles) grid = a.ntiles;
     k_tmu_mixed<<<(unsigned)grid, MIX_THREADS, MIX_SMEM, s>>>(map, a);
     note_launch();

@@ -244,6 +244,8 @@ cudaError_t launch_cl(double* A, int64_t lda, int kb, int64_t K0, const double* 
     return cudaLaunchKernelEx(&cfg, k_potrf_pd_cluster<CL>, A, lda, kb, K0, cc, step, check, st);
 }
 
+}  // namespace
+
 // Cluster size: 16 CTAs where the device runs such clusters, else 8.
 int pd_cluster_size() {
     static int size = 0;
@@ -276,7 +278,6 @@ int pd_cluster_size() {
     return size;
 }
 
-}  // namespace
 
 cudaError_t launch_potrf_pd_cluster(double* A, int64_t lda, int64_t kb, int64_t K0,
                                     const double* cc, int step, int check, DevStatus* st,
