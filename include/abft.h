@@ -463,6 +463,35 @@ int abft_set_lookahead(int32_t on);
  */
 int abft_timing_enable(int32_t on);
 int abft_timing_read(double* ms, int64_t* count, int32_t nphase);
+
+/*
+ * abft_timing_marks(phase, step, ms, max): the timed intervals recorded since
+ *   the last abft_timing_enable, in recording order: phase (as above), the
+ *   Cholesky iteration the interval belongs to (-1 outside the step loop;
+ *   the look-ahead PD is attributed to the iteration it factors) and its
+ *   milliseconds.  Writes at most max entries (host arrays); returns the
+ *   number of intervals, or -1 on bad arguments.
+ *
+ * abft_predict_step_times(T, W, nsteps, pred): the enhanced algorithmic
+ *   per-iteration time prediction of Sec. 3.2.1 (host only):
+ *   pred[k] = sum_i w_i (W[k] / W[k-i]) T[k-i], i = 1 .. 4, w = 1/2, 1/4,
+ *   1/8, 1/8, over the previous iterations j = k - i with W[j] > 0 and
+ *   T[j] >= 0; when fewer than four are usable their weights are
+ *   renormalized to sum to one (the paper is silent on the first
+ *   iterations); pred[k] = NaN when none is.  T: measured times, W: the
+ *   operation's work per iteration (any unit).  Returns 0, or -1 on bad
+ *   arguments.
+ *
+ * abft_chol_step_work(n, nb, phase, k): the work of one operation of
+ *   iteration k of the blocked Cholesky as this library performs it, for
+ *   abft_predict_step_times: PD kb^3/3, PU m kb^2, TMU 2 kb E (flops), verify
+ *   E + m kb (elements), with kb the block width, m the trailing order and E
+ *   the elements of the trailing lower block triangle (diagonal blocks
+ *   full); phase as in abft_timing_read; 0 for other phases or past the end.
+ */
+int abft_timing_marks(int32_t* phase, int64_t* step, double* ms, int32_t max);
+int abft_predict_step_times(const double* T, const double* W, int64_t nsteps, double* pred);
+double abft_chol_step_work(int64_t n, int64_t nb, int32_t phase, int64_t k);
 int64_t abft_launch_count(void);
 
 /* Library version string. */

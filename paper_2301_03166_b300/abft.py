@@ -102,6 +102,15 @@ def lib():
         L.abft_timing_enable.argtypes = [_i32]
         L.abft_set_lookahead.argtypes = [_i32]
         L.abft_set_lookahead.restype = ctypes.c_int
+        L.abft_timing_marks.argtypes = [ctypes.POINTER(_i32), ctypes.POINTER(_i64),
+                                        ctypes.POINTER(ctypes.c_double), _i32]
+        L.abft_timing_marks.restype = ctypes.c_int
+        L.abft_predict_step_times.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), _i64,
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.abft_predict_step_times.restype = ctypes.c_int
+        L.abft_chol_step_work.argtypes = [_i64, _i64, _i32, _i64]
+        L.abft_chol_step_work.restype = ctypes.c_double
         L.abft_timing_enable.restype = ctypes.c_int
         L.abft_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         L.abft_timing_read.restype = ctypes.c_int
@@ -284,6 +293,40 @@ def timing_read():
     cnt = (ctypes.c_int64 * len(PHASES))()
     lib().abft_timing_read(ms, cnt, len(PHASES))
     return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def timing_marks():
+    """Timed intervals since timing_enable: list of (phase name, iteration, ms)."""
+    L = lib()
+    n = L.abft_timing_marks(None, None, None, 0)
+    if n <= 0:
+        return []
+    ph = (_i32 * n)()
+    st = (_i64 * n)()
+    ms = (ctypes.c_double * n)()
+    L.abft_timing_marks(ph, st, ms, n)
+    return [(PHASES[ph[i]], st[i], ms[i]) for i in range(n)]
+
+
+def predict_step_times(T, W):
+    """Per-iteration time prediction from the last four iterations (Sec. 3.2.1),
+    computed by the library: pred[k] = sum_i w_i (W[k] / W[k-i]) T[k-i]."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    if T.shape != W.shape or T.ndim != 1:
+        raise ValueError("T and W must be 1-D arrays of the same length")
+    out = np.empty_like(T)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().abft_predict_step_times(T.ctypes.data_as(dp), W.ctypes.data_as(dp), T.size,
+                                       out.ctypes.data_as(dp))
+    if rc != 0:
+        raise AbftError(rc, "bad arguments")
+    return out
+
+
+def chol_step_work(n, nb, phase, k):
+    """Work of operation `phase` ('pd', 'pu', 'tmu', 'verify') at iteration k."""
+    return lib().abft_chol_step_work(n, nb, PHASES.index(phase), k)
 
 
 def launch_count():

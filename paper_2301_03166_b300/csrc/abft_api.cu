@@ -4,6 +4,7 @@
 // locate, correct).  No host synchronization happens inside the step loop;
 // the only device-to-host copy is the final status when a report is wanted.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -23,7 +24,15 @@ namespace {
 struct Mark {
     int phase;
     cudaEvent_t a, b;
+    int64_t step;
 };
+struct Interval {
+    int phase;
+    int64_t step;
+    double ms;
+};
+std::vector<Interval> g_intervals;    // timed intervals since the last enable, in order
+thread_local int64_t g_step = -1;     // iteration the next marks belong to
 std::mutex g_tmu;
 bool g_timing = false;
 std::vector<cudaEvent_t> g_pool;      // reusable events
@@ -43,6 +52,8 @@ cudaEvent_t next_event() {
 
 bool timing_on() { return g_timing; }
 
+void timing_step(int64_t k) { g_step = k; }
+
 void timing_mark(int phase, int begin, cudaStream_t s) {
     if (!g_timing) return;
     std::lock_guard<std::mutex> lk(g_tmu);
@@ -50,7 +61,7 @@ void timing_mark(int phase, int begin, cudaStream_t s) {
     if (!e) return;
     cudaEventRecord(e, s);
     if (begin) {
-        g_marks.push_back({phase, e, nullptr});
+        g_marks.push_back({phase, e, nullptr, g_step});
     } else {
         for (auto it = g_marks.rbegin(); it != g_marks.rend(); ++it)
             if (it->phase == phase && it->b == nullptr) { it->b = e; break; }
@@ -68,6 +79,7 @@ cudaError_t timing_collect(cudaStream_t s) {
         if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
             g_ms[m.phase] += ms;
             g_calls[m.phase] += 1;
+            g_intervals.push_back({m.phase, m.step, (double)ms});
         }
     }
     g_marks.clear();
@@ -271,6 +283,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     for (int64_t k = 0; k < N; ++k) {
         const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
         double* Akk = A + K0 * lda + K0;
+        timing_step(k);
         const int32_t mk = modes ? modes[k] : mode;
         const int32_t mprev = k == 0 ? ABFT_MODE_NONE : (modes ? modes[k - 1] : mode);
         const bool full = mk == ABFT_MODE_FULL, check = mk != ABFT_MODE_NONE;
@@ -461,11 +474,13 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ABFT_CUDA_TRY(cudaEventRecord(la->ready, s));
             ABFT_CUDA_TRY(cudaStreamWaitEvent(la->side, la->ready, 0));
             const int64_t K1 = T0, kb1 = std::min(g, n - K1);
+            timing_step(k + 1);
             timing_mark(PH_PD, 1, s);
             ABFT_CUDA_TRY(chol_pd(A + K1 * lda + K1, lda, kb1, K1,
                                   check ? CS + ((k + 1) * nc) * n + K1 : nullptr, check ? 1 : 0,
                                   (int)(k + 1), (double*)(base + w.pdpart), st, s));
             timing_mark(PH_PD, 0, s);
+            timing_step(k);
             rc = tmu(PART_REST, la->side);
             if (rc != ABFT_OK) return rc;
             ABFT_CUDA_TRY(cudaEventRecord(la->rest_done, la->side));
@@ -473,6 +488,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             pd_ahead = true;
         }
     }
+    timing_step(-1);
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 1, s));
     timing_mark(PH_OTHER, 0, s);
@@ -1583,8 +1599,65 @@ int abft_timing_enable(int32_t on) {
     g_timing = on != 0;
     for (int i = 0; i < PH_COUNT; ++i) { g_ms[i] = 0.0; g_calls[i] = 0; }
     g_marks.clear();
+    g_intervals.clear();
     g_pool_used = 0;
     return ABFT_OK;
+}
+
+int abft_timing_marks(int32_t* phase, int64_t* step, double* ms, int32_t max) {
+    if (max < 0 || (max > 0 && (phase == nullptr || step == nullptr || ms == nullptr))) return -1;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    const int32_t n = (int32_t)std::min<size_t>(g_intervals.size(), (size_t)INT32_MAX);
+    for (int32_t i = 0; i < n && i < max; ++i) {
+        phase[i] = g_intervals[i].phase;
+        step[i] = g_intervals[i].step;
+        ms[i] = g_intervals[i].ms;
+    }
+    return n;
+}
+
+// Enhanced algorithmic slack prediction (Sec. 3.2.1): the time of an
+// operation at iteration k from its profiled times at the last p = 4
+// iterations, each scaled by the ratio of the operation's work between the
+// two iterations and weighted 1/2, 1/4, 1/8, 1/8 (nearest first).
+int abft_predict_step_times(const double* T, const double* W, int64_t nsteps, double* pred) {
+    if (nsteps < 0 || (nsteps > 0 && (T == nullptr || W == nullptr || pred == nullptr))) return -1;
+    static const double wt[4] = {0.5, 0.25, 0.125, 0.125};
+    for (int64_t k = 0; k < nsteps; ++k) {
+        double num = 0.0, wsum = 0.0;
+        for (int i = 1; i <= 4 && k - i >= 0; ++i) {
+            const int64_t j = k - i;
+            if (!(W[j] > 0.0) || !(T[j] >= 0.0)) continue;   // no work, or not measured
+            num += wt[i - 1] * (W[k] / W[j]) * T[j];
+            wsum += wt[i - 1];
+        }
+        // fewer than four usable neighbours: their weights are renormalized
+        pred[k] = wsum > 0.0 ? num / wsum : std::nan("");
+    }
+    return ABFT_OK;
+}
+
+// Work of one operation of iteration k of the blocked Cholesky as this
+// implementation performs it (flops; elements for the verification):
+// PD kb^3 / 3, PU m kb^2, TMU 2 kb E (E = elements of the lower block
+// triangle of the trailing matrix, diagonal blocks full), verify E + m kb.
+double abft_chol_step_work(int64_t n, int64_t nb, int32_t phase, int64_t k) {
+    if (n <= 0 || nb <= 0 || k < 0) return 0.0;
+    const int64_t K0 = k * nb;
+    if (K0 >= n) return 0.0;
+    const int64_t kb = std::min(nb, n - K0), T0 = K0 + kb, m = n - T0;
+    double E = 0.0;
+    for (int64_t r0 = 0; r0 < m; r0 += nb) {
+        const int64_t rows = std::min(nb, m - r0);
+        E += (double)rows * (double)(r0 + rows);
+    }
+    switch (phase) {
+        case PH_PD: return (double)kb * kb * kb / 3.0;
+        case PH_PU: return (double)m * kb * kb;
+        case PH_TMU: return 2.0 * kb * E;
+        case PH_VERIFY: return E + (double)m * kb;
+        default: return 0.0;
+    }
 }
 
 int abft_timing_read(double* ms, int64_t* count, int32_t nphase) {

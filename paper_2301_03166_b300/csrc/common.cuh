@@ -318,6 +318,7 @@ void note_launch();
 enum { PH_PD = 0, PH_PU = 1, PH_TMU = 2, PH_VERIFY = 3, PH_OTHER = 4, PH_SOLVE = 5, PH_COUNT = 6 };
 bool timing_on();
 void timing_mark(int phase, int begin, cudaStream_t s);
+void timing_step(int64_t k);   // iteration index recorded with the next marks (-1: none)
 cudaError_t timing_collect(cudaStream_t s);
 
 // FP64-accurate trailing update from BF16 slices (k_emu.cu).  The slice

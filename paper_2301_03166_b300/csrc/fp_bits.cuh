@@ -1,0 +1,40 @@
+// fp_bits.cuh -- conversions built from the IEEE-754 binary64 definition with
+// integer operations only.  B300 issues every FP64 instruction, conversions
+// included, at about one warp instruction per 64 clocks per sub-partition, so
+// epilogues that would otherwise convert on the FP64 pipe assemble the bits
+// themselves.
+#pragma once
+
+#include <stdint.h>
+
+namespace abft {
+
+// acc * 2^s rounded to nearest (ties to even), as a double: the magnitude is
+// normalized with a count of leading zeros, its top 53 bits are rounded on the
+// 11 bits below them, and s is folded into the exponent field.  ok = false
+// when the result would be subnormal or overflow (the caller converts on the
+// FP64 pipe).
+__device__ __forceinline__ double i64_scaled_to_f64(long long acc, int s, bool& ok) {
+    ok = true;
+    if (acc == 0) return 0.0;
+    const unsigned long long sign = acc < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long u = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    const int lz = __clzll((long long)u);
+    u <<= lz;                                          // leading one at bit 63
+    unsigned long long mant = u >> 11;                 // 53 bits, leading one at bit 52
+    const unsigned long long rem = u & 0x7ffull;
+    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+    int e = 1086 - lz + s;                             // biased exponent of mant 2^(11 - lz + s)
+    if (mant >> 53) {                                  // rounding carried into bit 53
+        mant >>= 1;
+        ++e;
+    }
+    if (e <= 0 || e >= 2047) {
+        ok = false;
+        return 0.0;
+    }
+    return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) |
+                                            (mant & 0xfffffffffffffull)));
+}
+
+}  // namespace abft

@@ -56,6 +56,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 #include "tc_util.cuh"
 
 namespace abft {
@@ -170,13 +171,6 @@ __device__ __forceinline__ uint64_t desc64(uint32_t saddr) {
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)4 << 61;
     return d;
-}
-
-// 2^k as a double for the normal range, 0 below it (k > 1023 does not occur:
-// the scales are bounded by the largest finite double).
-__device__ __forceinline__ double pow2(int k) {
-    if (k < -1022) return 0.0;
-    return __hiloint2double((k + 1023) << 20, 0);
 }
 
 __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ P, int64_t lda,
@@ -463,8 +457,14 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         if (gj + c >= colmax) continue;
-                        v[c] -= (double)acc[8 * hh + 4 * j + 2 * rr + c] *
-                                pow2(ei + a.ex[ej0 + gj + c] - 54);
+                        // A 2^(e_i + e_j - 54) assembled with integer operations
+                        // (one FP64 instruction per element: the subtraction)
+                        const long long av = acc[8 * hh + 4 * j + 2 * rr + c];
+                        const int sc = ei + a.ex[ej0 + gj + c] - 54;
+                        bool normal;
+                        double y = i64_scaled_to_f64(av, sc, normal);
+                        if (!normal) y = ldexp((double)av, sc);
+                        v[c] -= y;
                         if (frow >= 0)
 #pragma unroll
                             for (int f = 0; f < MAX_CF; ++f)   // static indices: no local copy
