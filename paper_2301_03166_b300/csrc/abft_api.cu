@@ -306,10 +306,44 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
         if (m <= 0) break;
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
         timing_mark(PH_PU, 1, s);
-        TrsmSeg segs[2] = {{A + T0 * lda + K0, lda, m},
-                           {CS + ((k + 1) * nc) * n + K0, n, (nt - k - 1) * nc}};
-        ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, nullptr, nullptr, st, s,
-                                      mixed));
+        if (emu && kb % 64 == 0 && kb >= 128) {
+            // blocked by 64 columns: X_c L_cc^T = B_c - X_<c L_c,<c^T.  The 64-wide
+            // diagonal solves run one thread per row (k_trsm_rows); the products
+            // run FP64-accurate from BF16 slices on the tensor cores (the panel rows, the checksum rows and the
+            // rows L_c,<c re-sliced with one scale per row over the columns < c)
+            constexpr int64_t CW = 64;
+            uint16_t* Sl = (uint16_t*)(base + w.eslice);
+            int* ex = (int*)(base + w.eex);
+            const int64_t mcp = check ? (nt - k - 1) * nc : 0, mrows = m + mcp;
+            double* Xp = A + T0 * lda + K0;
+            double* Xc = CS + ((k + 1) * nc) * n + K0;
+            for (int64_t c = 0; c < kb / CW; ++c) {
+                if (c > 0) {
+                    const int64_t K = c * CW, Mt = mrows + CW;
+                    ABFT_CUDA_TRY(launch_slice_panel(Xp, lda, m, K, Sl, Mt, 0, ex, s));
+                    if (check) ABFT_CUDA_TRY(launch_slice_panel(Xc, n, mcp, K, Sl, Mt, m, ex, s));
+                    ABFT_CUDA_TRY(launch_slice_panel(Akk + c * CW * lda, lda, CW, K, Sl, Mt, mrows,
+                                                     ex, s));
+                    EmuRectHost rc[2] = {};
+                    rc[0].C = Xp + c * CW; rc[0].ldc = lda;
+                    rc[0].a0 = 0; rc[0].na = m; rc[0].b0 = mrows; rc[0].nb = CW; rc[0].cdiv = 1;
+                    rc[0].frow = -1;
+                    rc[1].C = Xc + c * CW; rc[1].ldc = n;
+                    rc[1].a0 = m; rc[1].na = mcp; rc[1].b0 = mrows; rc[1].nb = CW; rc[1].cdiv = 1;
+                    rc[1].frow = -1;
+                    ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, Mt, K, nullptr, 0, 0, 0, 128, rc,
+                                                 check ? 2 : 1, nullptr, 0, 0, st, s));
+                }
+                TrsmSeg sg[2] = {{Xp + c * CW, lda, m}, {Xc + c * CW, n, mcp}};
+                ABFT_CUDA_TRY(launch_trsm_rows(Akk + c * CW * lda + c * CW, lda, CW, sg,
+                                               check ? 2 : 1, st, s, false));
+            }
+        } else {
+            TrsmSeg segs[2] = {{A + T0 * lda + K0, lda, m},
+                               {CS + ((k + 1) * nc) * n + K0, n, (nt - k - 1) * nc}};
+            ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, nullptr, nullptr, st,
+                                          s, mixed));
+        }
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)
                 ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));

@@ -166,6 +166,8 @@ struct TrsmSeg {
     int64_t ldb;
     int64_t rows;
 };
+cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
+                             int nseg, const DevStatus* st, cudaStream_t s, bool f32 = false);
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
                             cudaStream_t s, bool f32 = false, bool nt = false);

@@ -177,6 +177,61 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     }
 }
 
+// Solve X L^T = B in place for a narrow L (nb <= 64), one thread per row:
+// four warps of 32 rows per CTA (one per SM sub-partition), each thread
+// substituting its own row once L and the reciprocals of its diagonal are in
+// shared memory; one warp per sub-partition keeps its FP64 unit busy
+// (k_trsm_rlt's one-warp substitution next to seven waiting warps left most
+// of it idle).  x_j = (b_j - sum_{p<j} x_p L_jp) / L_jj
+// with the division by L_jj a multiplication by its reciprocal, formed once per
+// CTA (exact for the power-of-two pivots of exact integer cases).  Two
+// partial sums per row shorten the dependent chain.
+constexpr int RW_ROWS = 128;
+constexpr int RW_MAXNB = 64;
+constexpr int RW_LD = RW_MAXNB + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(RW_ROWS) k_trsm_rows(TrsmArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_bytes[];
+    T* X = (T*)smem_bytes;                 // RW_ROWS x RW_LD
+    T* Ls = X + RW_ROWS * RW_LD;           // nb x RW_LD
+    T* rinv = Ls + RW_MAXNB * RW_LD;       // nb
+    if (a.st && a.st->info != 0) return;
+    const int64_t bid = blockIdx.x;
+    const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    const TrsmSeg g = s ? a.seg[1] : a.seg[0];   // static indices: no local copy
+    const int64_t r0 = (bid - (s ? a.start[1] : a.start[0])) * RW_ROWS;
+    const int nr = (int)((g.rows - r0) < RW_ROWS ? (g.rows - r0) : RW_ROWS);
+    const int nb = a.nb, t = threadIdx.x;
+    for (int e = t; e < RW_ROWS * nb; e += RW_ROWS) {
+        const int r = e / nb, p = e % nb;
+        X[r * RW_LD + p] = r < nr ? (T)g.B[(r0 + r) * g.ldb + p] : (T)0;
+    }
+    for (int e = t; e < nb * nb; e += RW_ROWS) {
+        const int j = e / nb, p = e % nb;
+        Ls[j * RW_LD + p] = p <= j ? (T)a.L[(int64_t)j * a.ldl + p] : (T)0;
+    }
+    for (int j = t; j < nb; j += RW_ROWS) rinv[j] = (T)1 / (T)a.L[(int64_t)j * a.ldl + j];
+    __syncthreads();
+    T* xr = X + t * RW_LD;
+    for (int j = 0; j < nb; ++j) {
+        const T* lj = Ls + j * RW_LD;
+        T v0 = xr[j], v1 = 0;
+        int p = 0;
+        for (; p + 1 < j; p += 2) {
+            v0 -= xr[p] * lj[p];
+            v1 -= xr[p + 1] * lj[p + 1];
+        }
+        if (p < j) v0 -= xr[p] * lj[p];
+        xr[j] = (v0 + v1) * rinv[j];
+    }
+    __syncthreads();
+    for (int e = t; e < nr * nb; e += RW_ROWS) {
+        const int r = e / nb, p = e % nb;
+        g.B[(r0 + r) * g.ldb + p] = (double)X[r * RW_LD + p];
+    }
+}
+
 // PD check on column sums: 1^T A_kk (carried, cc) vs (1^T L) L^T, and, when
 // v != NULL, v = L^{-T} 1 (blocked back substitution, chunks of 32).
 __global__ void __launch_bounds__(512) k_chol_pd_check(const double* L, int64_t ldl, int nb,
@@ -287,6 +342,45 @@ cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const Trsm
     if (nt) k_trsm_rlt<double, true><<<(unsigned)total, TT, sd, s>>>(a);
     else if (f32) k_trsm_rlt<float, false><<<(unsigned)total, TT, sf, s>>>(a);
     else k_trsm_rlt<double, false><<<(unsigned)total, TT, sd, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// X L^T = B for nb <= 64 with k_trsm_rows (f32: in FP32, the FP64 B and L
+// rounded on load).
+cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
+                             int nseg, const DevStatus* st, cudaStream_t s, bool f32) {
+    if (nb <= 0) return cudaSuccess;
+    if (nb > RW_MAXNB || nseg < 1 || nseg > 2) return cudaErrorInvalidValue;
+    TrsmArgs a{};
+    a.L = L;
+    a.ldl = ldl;
+    a.nb = (int)nb;
+    int64_t total = 0;
+    for (int i = 0; i < nseg; ++i) {
+        if (segs[i].rows <= 0) continue;
+        a.seg[a.nseg] = segs[i];
+        a.start[a.nseg] = total;
+        total += (segs[i].rows + RW_ROWS - 1) / RW_ROWS;
+        a.nseg++;
+    }
+    if (total == 0) return cudaSuccess;
+    a.start[a.nseg] = total;
+    a.st = st;
+    const size_t sd = (size_t)(RW_ROWS * RW_LD + RW_MAXNB * RW_LD + RW_MAXNB) * sizeof(double);
+    const size_t sf = (size_t)(RW_ROWS * RW_LD + RW_MAXNB * RW_LD + RW_MAXNB) * sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_rows<double>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sf);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (f32) k_trsm_rows<float><<<(unsigned)total, RW_ROWS, sf, s>>>(a);
+    else k_trsm_rows<double><<<(unsigned)total, RW_ROWS, sd, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }
