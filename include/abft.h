@@ -254,7 +254,11 @@ int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double*
  * dtype followed by iterative refinement (not in the paper: the precision
  * form added on top of it).  L := A (lower triangle copied), abft_potrf(L),
  * X = L^{-T} L^{-1} B, then repeat: R = B - A X in FP64 (A symmetric, read
- * from its lower triangle), eta = max_r ||R_r||_inf / (||A||_inf ||X_r||_inf +
+ * from its lower triangle; for the 16-bit dtypes with n a multiple of 32 the
+ * products A X are FP64-accurate sums of exact BF16 slice products on the
+ * tensor cores -- A split once per call into 8 slices of its full rows, n^2
+ * 16 bytes of workspace -- with an error below that of the same dot products
+ * in FP64 arithmetic), eta = max_r ||R_r||_inf / (||A||_inf ||X_r||_inf +
  * ||B_r||_inf); stop when eta <= tol or after maxit corrections; otherwise
  * D = L^{-T} L^{-1} R (FP32 for the mixed dtypes, FP64 for ABFT_F64) and
  * X += D.  rep (optional) receives the factorization report plus ir_iters and

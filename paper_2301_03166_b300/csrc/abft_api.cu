@@ -965,7 +965,8 @@ int potrs_run(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* 
 }
 
 struct IrWs {
-    size_t chol, solve, R, P, rs, norms, eta, total;
+    size_t chol, solve, R, P, rs, norms, eta, re, total;
+    bool emu_resid;   // residual from BF16 slices of A on the tensor cores
 };
 
 IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
@@ -979,6 +980,10 @@ IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
     w.rs = off; off = align_up(off + sizeof(double) * (size_t)n);
     w.norms = off; off = align_up(off + sizeof(unsigned long long) * 64);
     w.eta = off; off = align_up(off + sizeof(double));
+    // the 16-bit factorizations refine with an FP64-accurate residual from
+    // BF16 slices of A (FP64 factorizations keep the FP64 residual)
+    w.emu_resid = mixed && resid_emu_supported(n);
+    w.re = off; off = align_up(off + (w.emu_resid ? resid_emu_bytes(n) : 0));
     w.total = off;
     return w;
 }
@@ -1098,6 +1103,11 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     int32_t iters_max = 0;
     double eta_max = 0.0;
     bool prepared = false;   // block inverses (and the FP32 copy of L) formed
+    if (w.emu_resid) {       // slices of A, once per solve
+        timing_mark(PH_SOLVE, 1, s);
+        ABFT_CUDA_TRY(launch_resid_emu_prepare(A, lda, n, base + w.re, s));
+        timing_mark(PH_SOLVE, 0, s);
+    }
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
@@ -1113,8 +1123,12 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
         double eta = 0.0;
         for (;; ++it) {
             ABFT_CUDA_TRY(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long) * 32, s));
-            ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P, kSplit,
-                                          rmax, xmax, s));
+            if (w.emu_resid)
+                ABFT_CUDA_TRY(launch_resid_emu(n, X + r0, ldx, B + r0, ldb, nr, R, 16, base + w.re,
+                                               rmax, xmax, s));
+            else
+                ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P,
+                                              kSplit, rmax, xmax, s));
             ABFT_CUDA_TRY(launch_eta(rmax, xmax, anorm, bmax, nr, eta_d, s));
             ABFT_CUDA_TRY(cudaMemcpyAsync(&eta, eta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
             ABFT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1268,6 +1282,11 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
     int32_t iters_max = 0, gm_total = 0;
     double eta_max = 0.0;
     std::vector<double> hres(16), beta(16);
+    if (w.emu_resid) {   // slices of A for the residuals and products, once per solve
+        timing_mark(PH_SOLVE, 1, s);
+        ABFT_CUDA_TRY(launch_resid_emu_prepare(A, lda, n, base + w.re, s));
+        timing_mark(PH_SOLVE, 0, s);
+    }
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
@@ -1284,7 +1303,11 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
         for (;; ++it) {
             ABFT_CUDA_TRY(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long) * 32, s));
             ABFT_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * 16, s));
-            ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P, kSplit,
+            if (w.emu_resid)
+                ABFT_CUDA_TRY(launch_resid_emu(n, X + r0, ldx, B + r0, ldb, nr, R, 16, base + w.re,
+                                               rmax, xmax, s));
+            else
+                ABFT_CUDA_TRY(launch_residual(A, lda, n, X + r0, ldx, B + r0, ldb, nr, R, 16, P, kSplit,
                                           rmax, xmax, s));
             ABFT_CUDA_TRY(launch_eta(rmax, xmax, anorm, bmax, nr, eta_d, s));
             ABFT_CUDA_TRY(cudaMemcpyAsync(&eta, eta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1304,6 +1327,9 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
             for (int j = 0; j < m; ++j) {
                 double* Vj = V + (int64_t)j * vstride;
                 if (inner_f32) ABFT_CUDA_TRY(launch_symv_f32(A32, n, n, Vj, Wb, P, kSplit, s));
+                else if (w.emu_resid)
+                    ABFT_CUDA_TRY(launch_resid_emu(n, Vj, 16, nullptr, 0, 16, Wb, 16, base + w.re,
+                                                   nullptr, nullptr, s));
                 else ABFT_CUDA_TRY(launch_symv(A, lda, n, Vj, Wb, P, kSplit, s));
                 rc = precond(Wb);
                 if (rc != ABFT_OK) return rc;

@@ -342,6 +342,21 @@ cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t mtot, int64
                            int nrect, const ComputeFault* cf, int ncf, int max_grid, DevStatus* st,
                            cudaStream_t s);
 
+// FP64-accurate refinement residual on the tensor cores (k_resid_emu.cu).
+bool resid_emu_supported(int64_t n);
+size_t resid_emu_bytes(int64_t n);
+cudaError_t launch_resid_emu_prepare(const double* A, int64_t lda, int64_t n, void* ws,
+                                     cudaStream_t s);
+// B == nullptr: R = A X (n x 16, ld 16) instead of the residual.
+cudaError_t launch_resid_emu(int64_t n, const double* X, int64_t ldx, const double* B, int64_t ldb,
+                             int nr, double* R, int64_t ldr, void* ws, unsigned long long* rmax,
+                             unsigned long long* xmax, cudaStream_t s);
+cudaError_t launch_symv_reduce(const double* P, int nsplit, int64_t n, double* Y, cudaStream_t s);
+cudaError_t launch_resid_reduce(const double* P, int nsplit, int64_t n, const double* B,
+                                int64_t ldb, const double* X, int64_t ldx, int nrhs, double* R,
+                                int64_t ldr, unsigned long long* rmax, unsigned long long* xmax,
+                                cudaStream_t s);
+
 // GMRES-IR pieces (k_gmres.cu); vectors are n x 16 blocks (ld 16), basis
 // vector i at V + i * vstride.
 int gmres_dot_blocks(int64_t n);

@@ -56,6 +56,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "emu_slice.cuh"
 #include "fp_bits.cuh"
 #include "tc_util.cuh"
 
@@ -162,17 +163,6 @@ __device__ __forceinline__ EmuItem emu_item(int64_t idx, const EmuArgs& a) {
     return t;
 }
 
-// K-major operand with 64-byte swizzle: 8-row groups 512 bytes apart (SBO).
-__device__ __forceinline__ uint64_t desc64(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
-    return d;
-}
-
 __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ P, int64_t lda,
                                                      int64_t m, int kb, uint16_t* __restrict__ S,
                                                      int64_t Mtot, int64_t row0,
@@ -201,30 +191,11 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         if (t >= nt) continue;
-        const int e = (int)((b[t] >> 52) & 0x7ffull);
-        const unsigned long long mant = (b[t] & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-        // F = round(|x| 2^56) = round(mant 2^(E - E_max + 3)), E of a subnormal taken
-        // as 1: a right shift by E_max - 3 - E (a left shift for the largest elements)
-        const int sh = emax - 3 - (e ? e : 1);
-        unsigned long long F;
-        if (sh <= 0) F = mant << (-sh);
-        else if (sh >= 64) F = 0ull;
-        else F = (mant >> sh) + ((mant >> (sh - 1)) & 1ull);
-        const bool neg = (b[t] >> 63) != 0ull;
+        uint16_t d[EMU_SLICES];
+        slice_digits(b[t], emax, d);
         const int64_t k = lane + 32 * t;
-        int carry = 0;
 #pragma unroll
-        for (int p = ES - 1; p >= 0; --p) {
-            int d = (int)((F >> (7 * (ES - 1 - p))) & 127ull) + carry;
-            carry = 0;
-            if (p > 0 && d >= 64) {
-                d -= 128;
-                carry = 1;
-            }
-            const float v = (float)(neg ? -d : d);
-            S[((int64_t)p * Mtot + row0 + row) * kb + k] =
-                __bfloat16_as_ushort(__float2bfloat16_rn(v));
-        }
+        for (int p = 0; p < ES; ++p) S[((int64_t)p * Mtot + row0 + row) * kb + k] = d[p];
     }
 }
 
@@ -353,7 +324,7 @@ __global__ void __launch_bounds__(ETHREADS, 1) k_tmu_emu(const __grid_constant__
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t sa = smem_u32(smem + s2 * STAGE);
-                    const uint64_t adesc = desc64(sa), bdesc = desc64(sa + ST_A);
+                    const uint64_t adesc = smem_desc64(sa), bdesc = smem_desc64(sa + ST_A);
                     // descriptors advance by 32 bytes per K = 16 step (field in 16-byte units)
 #pragma unroll 1
                     for (int kk = 0; kk < EKC / 16; ++kk)

@@ -616,6 +616,26 @@ cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_symv_reduce(const double* P, int nsplit, int64_t n, double* Y, cudaStream_t s) {
+    const int64_t tot = n * MAXRHS;
+    if (tot <= 0) return cudaSuccess;
+    k_symv_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, Y);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_reduce(const double* P, int nsplit, int64_t n, const double* B,
+                                int64_t ldb, const double* X, int64_t ldx, int nrhs, double* R,
+                                int64_t ldr, unsigned long long* rmax, unsigned long long* xmax,
+                                cudaStream_t s) {
+    const int64_t tot = n * nrhs;
+    if (tot <= 0) return cudaSuccess;
+    k_resid_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, nsplit, n, B, ldb, X, ldx, nrhs,
+                                                                 R, ldr, rmax, xmax);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_symv(const double* A, int64_t lda, int64_t n, const double* X, double* Y,
                         double* P, int nsplit, cudaStream_t s) {
     const int64_t kchunk = ((n + nsplit - 1) / nsplit + 31) / 32 * 32;
