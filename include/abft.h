@@ -250,6 +250,28 @@ int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double*
                double* B, int64_t ldb, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_symm_emu -- Y = A X for symmetric A (lower triangle read), FP64-accurate
+ * on the BF16 tensor cores (the product of the refinement residuals; not in the
+ * paper).  A is split into 8 BF16 slices of its full rows (a power-of-two
+ * scale per row, balanced base-128 digits), each block of up to 16 columns of
+ * X into 8 slices per column; the 36 slice pairs whose weights add up to at
+ * most 7 are summed exactly (FP32 accumulation over 256 terms, 64-bit integer
+ * combination), the 256-term chunks in FP64.  Error per element at most about
+ * n 2^-55 (row scale of A)(column scale of X), below the rounding of the same
+ * dot product in FP64; exact when every product and partial sum is an integer
+ * below 2^53 whose digits fit the slices (e.g. small integers).
+ *   n          order, a multiple of 32 (ABFT_ERR_UNSUPPORTED otherwise)
+ *   A, lda     device, row-major, lower triangle read, not modified
+ *   X, ldx     n x nrhs device, row-major;  Y, ldy  n x nrhs device output
+ *   ws, ws_bytes   workspace query protocol (ws = NULL: *ws_bytes = the
+ *              size, 16 n^2 + O(n) bytes)
+ * Returns 0 or an argument error: -1 n; -2 nrhs; -3 A; -4 lda; -5 X; -6 ldx;
+ * -7 Y; -8 ldy; -10 workspace.
+ */
+int abft_symm_emu(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X,
+                  int64_t ldx, double* Y, int64_t ldy, void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * abft_posv_ir -- solve A X = B for SPD A by an ABFT Cholesky in the given
  * dtype followed by iterative refinement (not in the paper: the precision
  * form added on top of it).  L := A (lower triangle copied), abft_potrf(L),

@@ -72,6 +72,7 @@ _SIGNATURES = {
                            ctypes.POINTER(Report), _vp],
     "abft_potrf": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
+    "abft_symm_emu": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
     "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
                          ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }
@@ -206,6 +207,33 @@ def potrf(A, nb, mode=FULL, dtype=F64, faults=(), tau_scale=1.0, report=True,
     if check and rc < 0 and rc != ERR_UNCORRECTABLE:
         raise AbftError(rc, strerror(rc))
     return rc, (report_dict(rep) if rep is not None else None)
+
+
+def symm_emu(A, X, Y=None, workspace=None, stream=None):
+    """Y = A X for symmetric A (lower triangle read), FP64-accurate on the BF16
+    tensor cores (n a multiple of 32).  Returns Y."""
+    _check_matrix(A)
+    _check_matrix(X, "X")
+    n, nrhs = X.shape
+    if A.shape != (n, n):
+        raise ValueError("A must be n x n")
+    if Y is None:
+        Y = torch.empty_like(X)
+    L = lib()
+    need = ctypes.c_size_t(0)
+    rc = L.abft_symm_emu(n, nrhs, None, max(1, A.stride(0)), None, max(1, X.stride(0)), None,
+                         max(1, Y.stride(0)), None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, A.device)
+    size = ctypes.c_size_t(ws.numel())
+    rc = L.abft_symm_emu(n, nrhs, ctypes.c_void_p(A.data_ptr()), max(1, A.stride(0)),
+                         ctypes.c_void_p(X.data_ptr()), max(1, X.stride(0)),
+                         ctypes.c_void_p(Y.data_ptr()), max(1, Y.stride(0)),
+                         ctypes.c_void_p(ws.data_ptr()), ctypes.byref(size), _stream(stream))
+    if rc != 0:
+        raise AbftError(rc, strerror(rc))
+    return Y
 
 
 def _modes_array(modes, n, nb):

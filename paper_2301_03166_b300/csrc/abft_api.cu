@@ -1020,6 +1020,40 @@ GmWs gm_ws(int64_t n, int m, size_t off, bool a32) {
 
 extern "C" {
 
+int abft_symm_emu(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X,
+                  int64_t ldx, double* Y, int64_t ldy, void* ws, size_t* ws_bytes, void* stream) {
+    if (n < 0 || (n > 0 && !resid_emu_supported(n))) return n < 0 ? -1 : ABFT_ERR_UNSUPPORTED;
+    if (nrhs < 0) return -2;
+    if (lda < std::max<int64_t>(1, n)) return -4;
+    if (ldx < std::max<int64_t>(1, nrhs)) return -6;
+    if (ldy < std::max<int64_t>(1, nrhs)) return -8;
+    if (ws_bytes == nullptr) return -10;
+    const size_t need = n > 0 ? align_up(resid_emu_bytes(n)) + align_up(sizeof(double) * n * 16) : 0;
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -10;
+    if (n == 0 || nrhs == 0) return ABFT_OK;
+    if (A == nullptr) return -3;
+    if (X == nullptr) return -5;
+    if (Y == nullptr) return -7;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    double* Y16 = (double*)(base + align_up(resid_emu_bytes(n)));
+    timing_mark(PH_SOLVE, 1, s);
+    ABFT_CUDA_TRY(launch_resid_emu_prepare(A, lda, n, base, s));
+    for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
+        const int nr = (int)std::min<int64_t>(16, nrhs - r0);
+        ABFT_CUDA_TRY(launch_resid_emu(n, X + r0, ldx, nullptr, 0, nr, Y16, 16, base, nullptr,
+                                       nullptr, s));
+        ABFT_CUDA_TRY(launch_copy_d2d(Y16, 16, Y + r0, ldy, n, nr, s));
+    }
+    timing_mark(PH_SOLVE, 0, s);
+    ABFT_CUDA_TRY(timing_collect(s));
+    return ABFT_OK;
+}
+
 int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
                double* B, int64_t ldb, void* ws, size_t* ws_bytes, void* stream) {
     if (n < 0) return -1;
