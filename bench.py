@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
     p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
     p.add_argument("--no-batched", action="store_true", help="skip the batched timings")
+    p.add_argument("--no-lookahead", action="store_true",
+                   help="skip the look-ahead section (BF16 factorization with and without "
+                        "look-ahead, per-iteration time prediction as a self-check)")
     p.add_argument("--no-emulated", action="store_true",
                    help="skip the FP64-accurate factorization with the BF16 tensor-core update")
     p.add_argument("--conditioned", action="store_true",
@@ -398,6 +401,43 @@ def run_ours(args, ws, rank, local):
                            "rc": rc_m, "faults_corrected": rep_m["corrected"]}
         del Lbuf, Xb, B
 
+    lookahead = None
+    if not args.no_lookahead:
+        # Look-ahead (Sec. 2.1, Fig. example-lu (b), on one GPU): the BF16 ABFT
+        # factorization of the benchmark matrix with and without it, and, as a
+        # self-check of the per-step costs it trades, the per-iteration time
+        # prediction of Sec. 3.2.1 (last four iterations weighted 1/2, 1/4, 1/8,
+        # 1/8, scaled by the operations' work ratios) against the measured
+        # per-iteration times of PD, PU, TMU and verification.
+        def bf16_factor():
+            A.copy_(A0)
+            return abft.potrf(A, nb, abft.FULL, dtype=abft.MIXED_BF16, faults=faults, workspace=wsp)
+        lookahead = {}
+        for on in (False, True):
+            abft.set_lookahead(on)
+            ms_la, _ = timed(bf16_factor, max(1, args.steps), 1)
+            lookahead["ms_on" if on else "ms_off"] = ms_la
+        lookahead["speedup"] = lookahead["ms_off"] / lookahead["ms_on"]
+        abft.timing_enable(True)
+        bf16_factor()
+        torch.cuda.synchronize(dev)
+        marks = abft.timing_marks()
+        abft.timing_enable(False)
+        nsteps = (n + nb - 1) // nb
+        pred_err = {}
+        for op in ("pd", "pu", "tmu", "verify"):
+            T = np.zeros(nsteps)
+            for ph, k, ms in marks:
+                if ph == op and 0 <= k < nsteps:
+                    T[k] += ms
+            Wk = np.array([abft.chol_step_work(n, nb, op, k) for k in range(nsteps)])
+            pr = abft.predict_step_times(T, Wk)
+            sel = [k for k in range(4, nsteps) if Wk[k] > 0 and T[k] > 0 and np.isfinite(pr[k])]
+            rel = np.abs(pr[sel] - T[sel]) / T[sel]
+            pred_err[op] = {"mean_rel_err": float(rel.mean()), "max_rel_err": float(rel.max()),
+                            "steps": len(sel)}
+        lookahead["prediction"] = pred_err
+
     conditioned = None
     if args.conditioned:
         # A = Q diag(sigma) Q^T, sigma geometric with condition kappa, block 512,
@@ -632,7 +672,8 @@ def run_ours(args, ws, rank, local):
                      "uncorrectable": rep["uncorrectable"], "events_match_injected": events_ok,
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
             "fp64_emulated": emulated,
-            "mixed_precision_ir": mixed, "conditioned": conditioned, "campaign": campaign,
+            "mixed_precision_ir": mixed, "lookahead": lookahead, "conditioned": conditioned,
+            "campaign": campaign,
             "lu_qr": lu_qr,
             "batched": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
