@@ -8,7 +8,9 @@
 // shared memory of the CL CTAs of a cluster (tile id = q (q + 1) / 2 + r,
 // home CTA id % CL, slot id / CL; rows past kb are the identity) and factored
 // right-looking by tile columns p = 0 .. NT - 1:
-//   A  the home CTA of tile (p, p) factors it (unblocked, true divisions);
+//   A  the home CTA of tile (p, p) factors it square-root free (L D L^T, one
+//      reciprocal per pivot on the dependent chain, the 32 square roots and
+//      the column scalings, true divisions, at the end);
 //   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
 //      per row (lane l holds x_l), spread over every warp of the cluster; the
 //      division by L_jj is a multiplication by its reciprocal, formed once per
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     double* sQ = sD + TILE;                            // operand copies for phase C
     double* sR = sQ + TILE;
     __shared__ int s_fail;
-    __shared__ double s_rinv[PT];                      // 1 / L_jj of the current diagonal tile
+    __shared__ double s_rinv[PT];                      // 1 / L_jj (B); 1 / d_j, then sqrt(d_j) (A)
     __shared__ double s_cs[PMAXT * PT];
     if (st->info != 0) return;                         // same answer in every CTA
     const int me = (int)cl.block_rank();
@@ -96,20 +98,24 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     int fail = -1;
     for (int p = 0; p < NT; ++p) {
         const int idp = p * (p + 1) / 2 + p;
-        // A: unblocked Cholesky of the diagonal tile in its home CTA
+        // A: the diagonal tile in its home CTA, square-root free (L D L^T,
+        // right-looking): per pivot one reciprocal of d_j on the dependent
+        // chain (an FP64 square root and a division per pivot cost 675 and 431
+        // clocks on B300); the trailing entries take D[i][j] D[l][j] / d_j.
+        // Then L = L_unit D^(1/2): column j is D[i][j] / sqrt(d_j), all 32
+        // square roots at once.  A non-positive d_j fails at the same pivot as
+        // the Cholesky recurrence (d_j is the value under its square root).
         if (me == idp % CL) {
             double* D = home + (idp / CL) * TILE;
             for (int j = 0; j < PT; ++j) {
                 if (t == 0) {
                     const double d = D[j * PLD + j];
                     if (!(d > 0.0)) s_fail = j;
-                    else D[j * PLD + j] = sqrt(d);
+                    else s_rinv[j] = 1.0 / d;
                 }
                 __syncthreads();
                 if (s_fail >= 0) break;
-                const double sj = D[j * PLD + j];
-                if (t > j && t < PT) D[t * PLD + j] = D[t * PLD + j] / sj;
-                __syncthreads();
+                const double rj = s_rinv[j];
                 const int m = PT - 1 - j;
                 for (int e = t; e < m * (m + 1) / 2; e += PTHREADS) {
                     int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -117,9 +123,19 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
                     while ((a + 1) * (a + 2) / 2 <= e) ++a;
                     const int b = e - a * (a + 1) / 2;
                     const int i = j + 1 + a, l = j + 1 + b;
-                    D[i * PLD + l] -= D[i * PLD + j] * D[l * PLD + j];
+                    D[i * PLD + l] -= D[i * PLD + j] * (D[l * PLD + j] * rj);
                 }
                 __syncthreads();
+            }
+            if (s_fail < 0) {
+                if (t < PT) s_rinv[t] = sqrt(D[t * PLD + t]);   // sqrt(d_j)
+                __syncthreads();
+                for (int e = t; e < PT * PT; e += PTHREADS) {
+                    const int i = e >> 5, jj = e & 31;
+                    if (i > jj) D[i * PLD + jj] = D[i * PLD + jj] / s_rinv[jj];
+                }
+                __syncthreads();
+                if (t < PT) D[t * PLD + t] = s_rinv[t];
             }
         }
         cl.sync();
