@@ -1145,7 +1145,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
-        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, s));
+        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, P, s));
         // X0 = L^{-T} L^{-1} B
         timing_mark(PH_SOLVE, 1, s);
         ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
@@ -1324,7 +1324,7 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
     for (int64_t r0 = 0; r0 < nrhs; r0 += 16) {
         const int nr = (int)std::min<int64_t>(16, nrhs - r0);
         ABFT_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * 64, s));
-        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, s));
+        ABFT_CUDA_TRY(launch_inf_norms(A, lda, n, B + r0, ldb, nr, rs, anorm, bmax, P, s));
         timing_mark(PH_SOLVE, 1, s);
         // X0 = M^{-1} B (the padding columns stay zero)
         ABFT_CUDA_TRY(cudaMemsetAsync(Wb, 0, sizeof(double) * (size_t)n * 16, s));

@@ -275,7 +275,7 @@ cudaError_t launch_symv_f32(const float* A, int64_t lda, int64_t n, const double
                             double* P, int nsplit, cudaStream_t s);
 cudaError_t launch_inf_norms(const double* A, int64_t lda, int64_t n, const double* B, int64_t ldb,
                              int nrhs, double* rs, unsigned long long* anorm,
-                             unsigned long long* bmax, cudaStream_t s);
+                             unsigned long long* bmax, double* scratch, cudaStream_t s);   // scratch: 16 n doubles
 cudaError_t launch_eta(const unsigned long long* rmax, const unsigned long long* xmax,
                        const unsigned long long* anorm, const unsigned long long* bmax, int nrhs,
                        double* eta, cudaStream_t s);

@@ -1,5 +1,5 @@
-// fp_bits.cuh -- conversions built from the IEEE-754 binary64 definition with
-// integer operations only.  B300 issues every FP64 instruction, conversions
+// fp_bits.cuh -- conversions built from the IEEE-754 binary64 / binary32
+// definitions with integer operations only.  B300 issues every FP64 instruction, conversions
 // included, at about one warp instruction per 64 clocks per sub-partition, so
 // epilogues that would otherwise convert on the FP64 pipe assemble the bits
 // themselves.
@@ -35,6 +35,29 @@ __device__ __forceinline__ double i64_scaled_to_f64(long long acc, int s, bool& 
     }
     return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) |
                                             (mant & 0xfffffffffffffull)));
+}
+
+// Exact float -> double with integer operations only: rebias the exponent and
+// widen the mantissa; subnormals are normalized with a count of leading
+// zeros; zero, infinities and NaN keep their class.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+    uint32_t m = b & 0x7fffffu, ed;
+    if (e == 0xffu) {
+        ed = 0x7ffu;
+    } else if (e != 0u) {
+        ed = e + 896u;                         // (e - 127) + 1023
+    } else if (m == 0u) {
+        ed = 0u;
+    } else {                                   // m 2^-149, leading one at bit 31 - clz
+        const uint32_t sh = (uint32_t)__clz((int)m) - 8u;
+        m = (m << sh) & 0x7fffffu;
+        ed = 897u - sh;                        // (-126 - sh) + 1023
+    }
+    const uint32_t hi = sign | (ed << 20) | (m >> 3);
+    const uint32_t lo = m << 29;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 }  // namespace abft

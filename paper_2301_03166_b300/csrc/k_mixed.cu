@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 #include "tc_util.cuh"
 
 namespace abft {
@@ -71,31 +72,8 @@ struct MixArgs {
 };
 
 // Decode the idx-th tile of the lower block triangle: block pairs (BI >= BJ)
-// in row-major order, r x r 128-tiles inside each g x g block pair.
-// Exact float -> double with integer operations only, so the widening stays
-// off B300's slow FP64 pipe: rebias the exponent and widen the mantissa;
-// subnormals are normalized with a count of leading zeros; zero, infinities
-// and NaN keep their class.
-__device__ __forceinline__ double f32_to_f64_exact(float x) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
-    uint32_t m = b & 0x7fffffu, ed;
-    if (e == 0xffu) {
-        ed = 0x7ffu;
-    } else if (e != 0u) {
-        ed = e + 896u;                         // (e - 127) + 1023
-    } else if (m == 0u) {
-        ed = 0u;
-    } else {                                   // m 2^-149, leading one at bit 31 - clz
-        const uint32_t sh = (uint32_t)__clz((int)m) - 8u;
-        m = (m << sh) & 0x7fffffu;
-        ed = 897u - sh;                        // (-126 - sh) + 1023
-    }
-    const uint32_t hi = sign | (ed << 20) | (m >> 3);
-    const uint32_t lo = m << 29;
-    return __hiloint2double((int)hi, (int)lo);
-}
-
+// in row-major order, r x r 128-tiles inside each g x g block pair.  (The
+// epilogue widens FP32 to FP64 without the FP64 pipe: f32_to_f64_exact.)
 __device__ __forceinline__ void lower_tile(int64_t idx, int64_t r, int64_t& ti, int64_t& tj) {
     const int64_t r2 = r * r, pair = idx / r2, sub = idx % r2;
     int64_t a = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);

@@ -437,13 +437,33 @@ __global__ void k_abs_rowsum_lower(const double* A, int64_t lda, int64_t n, doub
     if (lane == 0) rs[i] = s;
 }
 
-__global__ void k_abs_colsum_strict(const double* A, int64_t lda, int64_t n, const double* rs,
-                                    const double* B, int64_t ldb, int nrhs,
-                                    unsigned long long* anorm, unsigned long long* bmax) {
+// The strict column part of the row sums of |A| (i > j of column j) in
+// kNormChunks row ranges per column (P[c][j]), so that many threads stream
+// each column; then ||A||_inf = max_j (rs[j] + sum_c P[c][j]) in a fixed order.
+constexpr int kNormChunks = 16;
+
+__global__ void k_abs_colsum_part(const double* A, int64_t lda, int64_t n, double* P) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t chunk = (n + kNormChunks - 1) / kNormChunks;
+    const int64_t i0 = blockIdx.y * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t i = i0 > j + 1 ? i0 : j + 1;
+    for (; i + 1 < i1; i += 2) {
+        s0 += fabs(A[i * lda + j]);
+        s1 += fabs(A[(i + 1) * lda + j]);
+    }
+    if (i < i1) s0 += fabs(A[i * lda + j]);
+    P[blockIdx.y * n + j] = s0 + s1;
+}
+
+__global__ void k_abs_colsum_strict(const double* rs, const double* P, int64_t n, const double* B,
+                                    int64_t ldb, int nrhs, unsigned long long* anorm,
+                                    unsigned long long* bmax) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     double s = rs[j];
-    for (int64_t i = j + 1; i < n; ++i) s += fabs(A[i * lda + j]);
+    for (int c = 0; c < kNormChunks; ++c) s += P[c * n + j];
     atomic_max_nonneg(anorm, s);
     for (int r = 0; r < nrhs; ++r) atomic_max_nonneg(&bmax[r], fabs(B[j * ldb + r]));
 }
@@ -662,10 +682,14 @@ cudaError_t launch_symv_f32(const float* A, int64_t lda, int64_t n, const double
 
 cudaError_t launch_inf_norms(const double* A, int64_t lda, int64_t n, const double* B, int64_t ldb,
                              int nrhs, double* rs, unsigned long long* anorm,
-                             unsigned long long* bmax, cudaStream_t s) {
+                             unsigned long long* bmax, double* scratch, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     k_abs_rowsum_lower<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(A, lda, n, rs);
     note_launch();
-    k_abs_colsum_strict<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, lda, n, rs, B, ldb, nrhs,
+    k_abs_colsum_part<<<dim3((unsigned)((n + 255) / 256), kNormChunks), 256, 0, s>>>(A, lda, n,
+                                                                                  scratch);
+    note_launch();
+    k_abs_colsum_strict<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rs, scratch, n, B, ldb, nrhs,
                                                                    anorm, bmax);
     note_launch();
     return cudaGetLastError();
