@@ -561,10 +561,14 @@ def run_ours(args, ws, rank, local):
         def lu_step():
             A.copy_(U0)
             return abft.getrf(A, nb, abft.FULL, faults=lu_f, workspace=wsp)
+        def lu_emu_step():   # the trailing update FP64-accurate on the BF16 tensor cores
+            A.copy_(U0)
+            return abft.getrf(A, nb, abft.FULL, dtype=abft.F64_EMU, faults=lu_f, workspace=wsp)
         def qr_step():
             A.copy_(U0)
             return abft.geqrf(A, nb, abft.FULL, faults=qr_f, workspace=wsp)
         for name, fn, fl, flops in (("lu", lu_step, lu_f, 2 * n ** 3 / 3),
+                                    ("lu_fp64_emulated", lu_emu_step, lu_f, 2 * n ** 3 / 3),
                                     ("qr", qr_step, qr_f, 4 * n ** 3 / 3)):
             ms_x, res = timed(fn, 1, 1)
             rep_x = res[-1]

@@ -158,7 +158,11 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
  *              block row of U: step nb <= row < (step+1) nb, col >= (step+1) nb
  *   tau_scale  tau_k = tau_scale * 8 u n nb max(max|a_ij|, max|u_ij| so far)
  * Returns as abft_potrf; info > 0 is the first exactly-zero pivot (the
- * factorization is completed, as LAPACK).  Errors: -1 n; -2 nb; -3 dtype;
+ * factorization is completed, as LAPACK).  dtype ABFT_F64 or ABFT_F64_EMU
+ * (nb <= 256: the trailing update and its checksum borders FP64-accurate from
+ * BF16 slices on the tensor cores, the rows of L21 and the columns of U12
+ * sliced each step; the panel, pivoting and verification stay FP64); other
+ * dtypes ABFT_ERR_UNSUPPORTED.  Errors: -1 n; -2 nb; -3 dtype;
  * -4 mode; -5 A; -6 lda; -7 ipiv NULL; -8 faults; -9 nfaults; -10 tau_scale;
  * -13 workspace.
  */

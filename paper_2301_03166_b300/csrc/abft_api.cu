@@ -531,11 +531,15 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
 
 // ------------------------------------------------------------------ LU
 struct LuWs {
-    size_t st, cs, cr, colchk, colchkw, ptot, part, z, zw, pv, pi, total;
+    size_t st, cs, cr, colchk, colchkw, ptot, part, z, zw, pv, pi, eslice, eex, total;
     int64_t nc, nt;
 };
 
-LuWs lu_ws(int64_t n, int64_t nb, int mode) {
+// rows of the LU's slice tensor: L21, the checksum panel rows, the columns of
+// U12 and the row-checksum columns
+int64_t lu_emu_rows(int64_t n, int64_t nt) { return 2 * n + 3 * nt; }
+
+LuWs lu_ws(int64_t n, int64_t nb, int mode, bool emu = false) {
     LuWs w{};
     w.nt = (n + nb - 1) / nb;
     w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
@@ -552,6 +556,9 @@ LuWs lu_ws(int64_t n, int64_t nb, int mode) {
     w.zw = off; off = align_up(off + d * (size_t)nb);
     w.pv = off; off = align_up(off + d * 1024);
     w.pi = off; off = align_up(off + sizeof(int64_t) * 1024);
+    const int64_t er = emu ? lu_emu_rows(n, w.nt) : 0;
+    w.eslice = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)er * (size_t)nb);
+    w.eex = off; off = align_up(off + sizeof(int) * (size_t)er);
     w.total = off;
     return w;
 }
@@ -568,7 +575,7 @@ bool lu_fault_ok(const abft_fault& f, int64_t n, int64_t nb, int64_t N) {
 // Blocked ABFT LU step loop (Sec. 2.1 PD / PU / TMU; Sec. 3.1.2).
 int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_t* ipiv,
              const abft_fault* faults, int32_t nfaults, double tau_scale, const LuWs& w,
-             char* base, cudaStream_t s) {
+             char* base, cudaStream_t s, bool emu = false) {
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
     double* Cr = (double*)(base + w.cr);
@@ -656,7 +663,44 @@ int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
                 cf[ncf++] = {faults[f].row - T0, faults[f].col - T0, faults[f].delta};
         timing_mark(PH_TMU, 1, s);
-        ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 1, cf, ncf, st, s));
+        if (emu) {
+            // FP64-accurate TMU from exact BF16 slice products (as the Cholesky's):
+            // slice tensor rows [L21 | checksum panel rows | columns of U12 |
+            // row-checksum columns t_J], the update and both borders as rectangles
+            uint16_t* Sl = (uint16_t*)(base + w.eslice);
+            int* ex = (int*)(base + w.eex);
+            const int64_t mc = check ? (nt - k - 1) * nc : 0, q = full ? nt - k - 1 : 0;
+            const int64_t mt = 2 * m + mc + q;
+            ABFT_CUDA_TRY(launch_slice_panel(A + T0 * lda + K0, lda, m, kb, Sl, mt, 0, ex, s));
+            if (check)
+                ABFT_CUDA_TRY(launch_slice_panel(CS + ((k + 1) * nc) * n + K0, n, mc, kb, Sl, mt, m,
+                                                 ex, s));
+            ABFT_CUDA_TRY(launch_slice_cols(A + K0 * lda + T0, lda, kb, m, Sl, mt, m + mc, ex, s));
+            if (full)
+                ABFT_CUDA_TRY(launch_slice_cols(Cr + K0 * nt + (k + 1), nt, kb, q, Sl, mt,
+                                                2 * m + mc, ex, s));
+            EmuRectHost rc[3] = {};
+            int nr = 0;
+            {
+                EmuRectHost& r = rc[nr++];
+                r.C = A + T0 * lda + T0; r.ldc = lda;
+                r.a0 = 0; r.na = m; r.b0 = m + mc; r.nb = m; r.cdiv = 1; r.frow = 0; r.fcol = 0;
+            }
+            if (check) {
+                EmuRectHost& r = rc[nr++];
+                r.C = CS + ((k + 1) * nc) * n + T0; r.ldc = n;
+                r.a0 = m; r.na = mc; r.b0 = m + mc; r.nb = m; r.cdiv = 1; r.frow = -1;
+            }
+            if (full) {
+                EmuRectHost& r = rc[nr++];
+                r.C = Cr + T0 * nt + (k + 1); r.ldc = nt;
+                r.a0 = 0; r.na = m; r.b0 = 2 * m + mc; r.nb = q; r.cdiv = 1; r.frow = -1;
+            }
+            ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, mt, kb, nullptr, 0, 0, 0, 128, rc, nr, cf, ncf, 0,
+                                         st, s));
+        } else {
+            ABFT_CUDA_TRY(launch_gemm_f64(gs, nseg, 0, 1, cf, ncf, st, s));
+        }
         timing_mark(PH_TMU, 0, s);
         timing_mark(PH_VERIFY, 1, s);
         for (int f = 0; f < nfaults; ++f)
@@ -676,10 +720,11 @@ int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_
 
 int check_common(int64_t n, int64_t nb, int32_t dtype, int32_t mode, const void* A, int64_t lda,
                  const abft_fault* faults, int32_t nfaults, double tau_scale, const void* ws,
-                 size_t* ws_bytes) {
+                 size_t* ws_bytes, bool allow_emu = false) {
     if (n < 0) return -1;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
-    if (dtype != ABFT_F64) return dtype < 0 || dtype > 3 ? -3 : ABFT_ERR_UNSUPPORTED;
+    const bool emu_ok = allow_emu && dtype == ABFT_F64_EMU && nb <= 256;
+    if (dtype != ABFT_F64 && !emu_ok) return dtype < 0 || dtype > 4 ? -3 : ABFT_ERR_UNSUPPORTED;
     if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -4;
     if (n > 0 && A == nullptr && ws != nullptr) return -5;
     if (lda < std::max<int64_t>(1, n)) return -6;
@@ -703,13 +748,15 @@ extern "C" {
 int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                int64_t* ipiv, const abft_fault* faults, int32_t nfaults, double tau_scale,
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
-    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes);
+    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes,
+                          true);
     if (rc != ABFT_OK) return rc;
     if (n > 0 && ipiv == nullptr && ws != nullptr) return -7;
     const int64_t N = (n + nb - 1) / nb;
     for (int f = 0; f < nfaults; ++f)
         if (!lu_fault_ok(faults[f], n, nb, N)) return -8;
-    const LuWs w = lu_ws(n, nb, mode);
+    const bool emu = dtype == ABFT_F64_EMU;
+    const LuWs w = lu_ws(n, nb, mode, emu);
     if (ws == nullptr) {
         *ws_bytes = w.total;
         return ABFT_OK;
@@ -720,7 +767,7 @@ int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
     DevStatus* st = (DevStatus*)(base + w.st);
     ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
     if (n > 0) {
-        rc = lu_steps(n, nb, mode, A, lda, ipiv, faults, nfaults, tau_scale, w, base, s);
+        rc = lu_steps(n, nb, mode, A, lda, ipiv, faults, nfaults, tau_scale, w, base, s, emu);
         if (rc != ABFT_OK) return rc;
     }
     ABFT_CUDA_TRY(timing_collect(s));

@@ -199,6 +199,42 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
     }
 }
 
+// Slices of the columns of a row-major K x ncols matrix P (K <= 256, a
+// multiple of 32) as rows row0 .. row0 + ncols - 1 of S (row stride K): the
+// B operand of an update whose right factor is stored by rows (the LU's
+// U12).  One CTA per 32 columns: the K x 32 tile goes through shared memory
+// so that the reads (along rows of P) and the writes (along rows of S) are
+// coalesced; one scale per column.
+constexpr int SC_COLS = 32;
+__global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ P, int64_t ld,
+                                                    int K, int64_t ncols, uint16_t* __restrict__ S,
+                                                    int64_t Mtot, int64_t row0,
+                                                    int* __restrict__ ex) {
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    double* T = (double*)sc_smem;                     // K x (SC_COLS + 1)
+    __shared__ int emax_s[SC_COLS];
+    const int64_t c0 = (int64_t)blockIdx.x * SC_COLS;
+    const int nc = (int)(ncols - c0 < SC_COLS ? ncols - c0 : SC_COLS);
+    if (threadIdx.x < SC_COLS) emax_s[threadIdx.x] = 1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * SC_COLS; e += blockDim.x) {
+        const int k = e / SC_COLS, j = e % SC_COLS;
+        const double v = j < nc ? P[(int64_t)k * ld + c0 + j] : 0.0;
+        T[k * (SC_COLS + 1) + j] = v;
+        atomicMax(&emax_s[j], (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffull));
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) ex[row0 + c0 + threadIdx.x] = emax_s[threadIdx.x] - 1022;
+    for (int e = threadIdx.x; e < nc * K; e += blockDim.x) {
+        const int j = e / K, k = e % K;
+        uint16_t d[EMU_SLICES];
+        slice_digits((unsigned long long)__double_as_longlong(T[k * (SC_COLS + 1) + j]),
+                     emax_s[j], d);
+#pragma unroll
+        for (int p = 0; p < ES; ++p) S[((int64_t)p * Mtot + row0 + c0 + j) * K + k] = d[p];
+    }
+}
+
 // Drain group accumulators d0 .. d0 + 3 (one window) into the 64-bit
 // fixed-point sums acc.  taddr addresses this warp's 32 TMEM lanes and 16
 // columns; acc[8 hh + k] holds element k of the 16x256b fragment of lanes
@@ -485,6 +521,24 @@ int64_t emu_rows(int64_t n, int64_t nb) {
 
 size_t emu_slice_bytes(int64_t n, int64_t nb) {
     return sizeof(uint16_t) * (size_t)ES * (size_t)emu_rows(n, nb) * (size_t)nb;
+}
+
+cudaError_t launch_slice_cols(const double* P, int64_t ld, int64_t K, int64_t ncols, uint16_t* S,
+                              int64_t Mtot, int64_t row0, int* ex, cudaStream_t s) {
+    if (ncols <= 0) return cudaSuccess;
+    if (K % 32 != 0 || K > 256 || row0 + ncols > Mtot) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * (size_t)K * (SC_COLS + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_slice_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(double) * 256 * (SC_COLS + 1)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_slice_cols<<<(unsigned)((ncols + SC_COLS - 1) / SC_COLS), 256, smem, s>>>(P, ld, (int)K, ncols,
+                                                                             S, Mtot, row0, ex);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
