@@ -531,7 +531,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
 
 // ------------------------------------------------------------------ LU
 struct LuWs {
-    size_t st, cs, cr, colchk, colchkw, ptot, part, z, zw, pv, pi, eslice, eex, total;
+    size_t st, cs, cr, colchk, colchkw, ptot, part, z, zw, pv, pi, stage, eslice, eex, total;
     int64_t nc, nt;
 };
 
@@ -556,6 +556,7 @@ LuWs lu_ws(int64_t n, int64_t nb, int mode, bool emu = false) {
     w.zw = off; off = align_up(off + d * (size_t)nb);
     w.pv = off; off = align_up(off + d * 1024);
     w.pi = off; off = align_up(off + sizeof(int64_t) * 1024);
+    w.stage = off; off = align_up(off + getf2_stage_bytes(nb));
     const int64_t er = emu ? lu_emu_rows(n, w.nt) : 0;
     w.eslice = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)er * (size_t)nb);
     w.eex = off; off = align_up(off + sizeof(int) * (size_t)er);
@@ -608,7 +609,8 @@ int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_
         double* P = A + K0 * lda + K0;
         timing_mark(PH_PD, 1, s);
         if (check) ABFT_CUDA_TRY(launch_coltot(CS, n, nc, k, nt, K0, kb, ptot, s));
-        ABFT_CUDA_TRY(launch_getf2_coop(P, lda, n - K0, kb, K0, ipiv, st, pv, pi, s));
+        ABFT_CUDA_TRY(launch_getf2_coop(P, lda, n - K0, kb, K0, ipiv, st, pv, pi,
+                                        (double*)(base + w.stage), s));
         ABFT_CUDA_TRY(launch_laswp(A, lda, n, K0, kb, ipiv, CS, n, nc, g, Cr, nt, mode, s));
         if (check) {
             ABFT_CUDA_TRY(launch_lu_colsums(P, lda, n - K0, kb, g, k, nt, K0, CS, n, nc, mode,

@@ -177,9 +177,10 @@ cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const
 
 // LU kernels (k_lu.cu).
 int num_sms();
+size_t getf2_stage_bytes(int64_t kb);   // pivot-row copies of launch_getf2_coop
 cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int64_t K0,
                               int64_t* ipiv, DevStatus* st, double* part_v, int64_t* part_i,
-                              cudaStream_t s);
+                              double* stage, cudaStream_t s);
 cudaError_t launch_laswp(double* A, int64_t lda, int64_t n, int64_t K0, int64_t kb,
                          const int64_t* ipiv, double* CS, int64_t ldcs, int64_t nc, int64_t g,
                          double* Cr, int64_t nt, int mode, cudaStream_t s);

@@ -3,11 +3,18 @@
 // Sec. 3.1.2: checksums carried through each operation).
 //
 // The panel factorization (getf2 on the (n - K0) x kb panel) is one
-// cooperative launch: each CTA owns a contiguous block of panel rows; per
-// column the CTAs publish their local (max |a|, first index), meet at a
-// bounded grid barrier, CTA 0 picks the pivot and swaps the two panel rows,
-// they meet again, and every CTA scales and updates its own rows.  The panel
-// (<= 32 MB at n = 16384) stays in L2 across the column loop.
+// cooperative launch: each CTA owns a contiguous block of panel rows.  Per
+// column the CTAs publish their local (max |a|, first index) together with a
+// copy of that candidate row (and the owner of row j a copy of row j), meet
+// at one bounded grid barrier, and then every CTA picks the same pivot from
+// the published values, the owners of rows j and p write the interchange
+// from the copies, and every CTA scales and updates its own rows with the
+// pivot row's copy.  The copies alternate between two slots by column parity:
+// slot j % 2 is rewritten only at column j + 2, after the barrier of column
+// j + 1, which every CTA reaches only once it has finished reading it.  (The
+// earlier scheme met twice per column, the pivot chosen and the rows swapped
+// by one CTA between the barriers.)  The panel (<= 32 MB at n = 16384)
+// stays in L2 across the column loop.
 #include <math.h>
 
 #include "common.cuh"
@@ -47,45 +54,64 @@ __device__ void block_argmax(double& v, int64_t& idx) {
 
 __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64_t m, int kb,
                                                    int64_t K0, int64_t* ipiv, DevStatus* st,
-                                                   double* part_v, int64_t* part_i) {
+                                                   double* part_v, int64_t* part_i,
+                                                   double* stage) {
     __shared__ double urow[512];
     __shared__ double lcol[MAXR];
     const unsigned G = gridDim.x;
     const int64_t R = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
+    // stage: [2][G + 1][kb]: candidate row per CTA, then row j (slot G)
     for (int j = 0; j < kb; ++j) {
-        // A: local first-max of |P[i][j]| over my rows i >= j
+        const int par = j & 1;
+        double* slot = stage + (size_t)par * (G + 1) * kb;
+        // A: local first-max of |P[i][j]| over my rows i >= j, published with a
+        // copy of the candidate row; the owner of row j publishes row j
         double bv = -1.0;
         int64_t bi = INT64_MAX;
         for (int64_t i = (r0 > j ? r0 : j) + threadIdx.x; i < r1; i += PT)
             better(bv, bi, fabs(P[i * lda + j]), i);
         block_argmax(bv, bi);
-        if (threadIdx.x == 0) { part_v[blockIdx.x] = bv; part_i[blockIdx.x] = bi; }
-        if (!grid_barrier(st, G)) return;
-        // B: CTA 0 picks the pivot and swaps the two panel rows
-        if (blockIdx.x == 0) {
-            double v = -1.0;
-            int64_t idx = INT64_MAX;
-            for (unsigned b = threadIdx.x; b < G; b += PT) better(v, idx, part_v[b], part_i[b]);
-            block_argmax(v, idx);
-            int64_t p = (idx == INT64_MAX) ? j : idx;
-            if (threadIdx.x == 0) ipiv[K0 + j] = K0 + p;
-            double piv = P[p * lda + j];
-            if (piv == 0.0) {
-                if (threadIdx.x == 0) atomicCAS(&st->lu_info, 0, (int)(K0 + j + 1));
-            } else if (p != j) {
-                for (int c = threadIdx.x; c < kb; c += PT) {
-                    double a = P[(int64_t)j * lda + c];
-                    P[(int64_t)j * lda + c] = P[p * lda + c];
-                    P[p * lda + c] = a;
-                }
-            }
+        if (threadIdx.x == 0) {
+            part_v[par * G + blockIdx.x] = bv;
+            part_i[par * G + blockIdx.x] = bi;
         }
+        if (bi != INT64_MAX)
+            for (int c = threadIdx.x; c < kb; c += PT)
+                slot[(size_t)blockIdx.x * kb + c] = P[bi * lda + c];
+        if (j >= r0 && j < r1)
+            for (int c = threadIdx.x; c < kb; c += PT) slot[(size_t)G * kb + c] = P[(int64_t)j * lda + c];
         if (!grid_barrier(st, G)) return;
+        // B: every CTA picks the pivot from the published values (same order,
+        // same result); the pivot row comes from its owner's copy
+        double v = -1.0;
+        int64_t idx = INT64_MAX;
+        unsigned win = 0;
+        for (unsigned b = threadIdx.x; b < G; b += PT) {
+            const double pv = part_v[par * G + b];
+            const int64_t pi = part_i[par * G + b];
+            if (pv > v || (pv == v && pi < idx)) { v = pv; idx = pi; }
+        }
+        block_argmax(v, idx);
+        const int64_t p = (idx == INT64_MAX) ? j : idx;
+        if (idx != INT64_MAX) win = (unsigned)(idx / R);   // the CTA that owns row p
+        if (blockIdx.x == 0 && threadIdx.x == 0) ipiv[K0 + j] = K0 + p;
+        for (int c = threadIdx.x; c < kb; c += PT)
+            urow[c] = p == j ? slot[(size_t)G * kb + c] : slot[(size_t)win * kb + c];
+        __syncthreads();
+        const double piv = urow[j];
+        if (piv == 0.0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->lu_info, 0, (int)(K0 + j + 1));
+            continue;
+        }
+        if (p != j) {   // the interchange, written by the owners of the two rows
+            if (j >= r0 && j < r1)
+                for (int c = threadIdx.x; c < kb; c += PT) P[(int64_t)j * lda + c] = urow[c];
+            if (p >= r0 && p < r1)
+                for (int c = threadIdx.x; c < kb; c += PT) P[p * lda + c] = slot[(size_t)G * kb + c];
+            __syncthreads();
+        }
         // C: scale and rank-1 update of my rows below the pivot
-        const double piv = P[(int64_t)j * lda + j];
-        if (piv == 0.0) continue;
-        for (int c = j + 1 + threadIdx.x; c < kb; c += PT) urow[c] = P[(int64_t)j * lda + c];
         const int64_t ibeg = (r0 > j + 1 ? r0 : j + 1);
         for (int64_t i = ibeg + threadIdx.x; i < r1; i += PT) {
             double l = P[i * lda + j] / piv;
@@ -93,14 +119,19 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
             lcol[i - r0] = l;
         }
         __syncthreads();
-        const int w = kb - j - 1;
-        if (w > 0 && ibeg < r1) {
-            const int64_t nrow = r1 - ibeg;
-            for (int64_t e = threadIdx.x; e < nrow * w; e += PT) {
-                int64_t i = ibeg + e / w;
-                int c = j + 1 + (int)(e % w);
-                double* a = P + i * lda + c;
-                *a = __dsub_rn(*a, __dmul_rn(lcol[i - r0], urow[c]));
+        // one column per thread, eight rows at a time: loads coalesced along the
+        // rows and eight of them in flight per thread
+        for (int c = j + 1 + threadIdx.x; c < kb; c += PT) {
+            const double uc = urow[c];
+            for (int64_t i = ibeg; i < r1; i += 8) {
+                double av[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i + u < r1) av[u] = P[(i + u) * lda + c];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i + u < r1)
+                        P[(i + u) * lda + c] = __dsub_rn(av[u], __dmul_rn(lcol[i + u - r0], uc));
             }
         }
         __syncthreads();
@@ -412,16 +443,20 @@ int num_sms() {
     return g_num_sms;
 }
 
+size_t getf2_stage_bytes(int64_t kb) {
+    return sizeof(double) * 2 * ((size_t)num_sms() + 1) * (size_t)kb;
+}
+
 cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int64_t K0,
                               int64_t* ipiv, DevStatus* st, double* part_v, int64_t* part_i,
-                              cudaStream_t s) {
+                              double* stage, cudaStream_t s) {
     int64_t want = (m + 63) / 64;
     int64_t G = want < num_sms() ? want : num_sms();
     if (G < 1) G = 1;
     while ((m + G - 1) / G > MAXR) ++G;   // rows per CTA must fit the shared buffer
     if (G > num_sms()) return cudaErrorInvalidValue;
     int kbi = (int)kb;
-    void* args[] = {&P, &lda, &m, &kbi, &K0, &ipiv, &st, &part_v, &part_i};
+    void* args[] = {&P, &lda, &m, &kbi, &K0, &ipiv, &st, &part_v, &part_i, &stage};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_getf2_coop, dim3((unsigned)G), dim3(PT),
                                                 args, 0, s);
     note_launch();
