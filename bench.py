@@ -61,10 +61,12 @@ def parse():
                         "factorization for no / single-side / full / adaptive checksums")
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
-                   choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32"],
+                   choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32", "lu",
+                            "lu-emu", "qr"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
-                        "refinement, or an FP32 two-sweep solve with the FP64 factor; at --n, --nb")
+                        "refinement, an FP32 two-sweep solve with the FP64 factor, or the ABFT "
+                        "LU (FP64 / FP64-accurate update) or QR of the uniform matrix; at --n, --nb")
     return p.parse_args()
 
 
@@ -698,6 +700,19 @@ def profile_case(args):
     wsp = abft.Workspace()
     B = torch.from_numpy(W.rhs(n, 16, seed=1003)).to(dev)
     X = torch.empty_like(B)
+    if args.profile_case in ("lu", "lu-emu", "qr"):
+        U0 = W.uniform_torch(n, seed=1001 + n, device=dev)
+        for _ in range(2):
+            A.copy_(U0)
+            if args.profile_case == "qr":
+                abft.geqrf(A, nb, abft.FULL, faults=W.fault_schedule(n, nb, "qr", seed=4000 + n),
+                           workspace=wsp)
+            else:
+                dt = abft.F64 if args.profile_case == "lu" else abft.F64_EMU
+                abft.getrf(A, nb, abft.FULL, dtype=dt,
+                           faults=W.fault_schedule(n, nb, "lu", seed=3000 + n), workspace=wsp)
+        torch.cuda.synchronize(dev)
+        return
     if args.profile_case == "potrs-f32":
         A.copy_(A0)
         abft.potrf(A, nb, abft.FULL, workspace=wsp)

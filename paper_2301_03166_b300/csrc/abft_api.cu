@@ -857,26 +857,25 @@ int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double
         if (T0 >= n) { timing_mark(PH_PD, 0, s); break; }
         ABFT_CUDA_TRY(launch_qr_prep_v(P, lda, m, kb, V, s));
         if (check) ABFT_CUDA_TRY(launch_qr_vsums(V, m, kb, g, k, nt, K0, CS, n, nc, mode, s));
-        ABFT_CUDA_TRY(cudaMemsetAsync(Gn, 0, sizeof(double) * kb * kb, s));
-        {
-            GemmSeg gg{};   // Gn = -V^T V
-            gg.A = V; gg.lda = kb; gg.B = V; gg.ldb = kb; gg.C = Gn; gg.ldc = kb;
-            gg.M = kb; gg.N = kb; gg.K = m;
-            ABFT_CUDA_TRY(launch_gemm_f64(&gg, 1, 1, 1, nullptr, 0, st, s));
-        }
-        ABFT_CUDA_TRY(launch_larft(Gn, kb, tau + K0, T, s));
         timing_mark(PH_PD, 0, s);
-        // TMU (larfb): W = -V^T [C, r]; X = -T^T W; [C, r] -= V X; c_I -= (1^T V_I) X
+        // TMU (larfb): W = -V^T [C, r]; X = -T^T W; [C, r] -= V X; c_I -= (1^T V_I) X.
+        // Gn = -V^T V (for T) shares the operand V^T and the reduction length m with
+        // W, so it is one more segment of the same launch (its 64x64 tiles alone
+        // would occupy only (kb/64)^2 SMs for the whole length m).
         const int64_t ncs = full ? nt - k - 1 : 0, nd = n - T0, ncol = nd + ncs;
         timing_mark(PH_TMU, 1, s);
+        ABFT_CUDA_TRY(cudaMemsetAsync(Gn, 0, sizeof(double) * kb * kb, s));
         ABFT_CUDA_TRY(cudaMemsetAsync(Wb, 0, sizeof(double) * kb * ldw, s));
         ABFT_CUDA_TRY(cudaMemsetAsync(Xb, 0, sizeof(double) * kb * ldw, s));
-        GemmSeg g1[2] = {};
-        g1[0].A = V; g1[0].lda = kb; g1[0].B = A + K0 * lda + T0; g1[0].ldb = lda;
-        g1[0].C = Wb; g1[0].ldc = ldw; g1[0].M = kb; g1[0].N = nd; g1[0].K = m;
-        g1[1].A = V; g1[1].lda = kb; g1[1].B = Cr + K0 * nt + (k + 1); g1[1].ldb = nt;
-        g1[1].C = Wb + nd; g1[1].ldc = ldw; g1[1].M = kb; g1[1].N = ncs; g1[1].K = m;
-        ABFT_CUDA_TRY(launch_gemm_f64(g1, full ? 2 : 1, 1, 1, nullptr, 0, st, s));
+        GemmSeg g1[3] = {};
+        g1[0].A = V; g1[0].lda = kb; g1[0].B = V; g1[0].ldb = kb;
+        g1[0].C = Gn; g1[0].ldc = kb; g1[0].M = kb; g1[0].N = kb; g1[0].K = m;
+        g1[1].A = V; g1[1].lda = kb; g1[1].B = A + K0 * lda + T0; g1[1].ldb = lda;
+        g1[1].C = Wb; g1[1].ldc = ldw; g1[1].M = kb; g1[1].N = nd; g1[1].K = m;
+        g1[2].A = V; g1[2].lda = kb; g1[2].B = Cr + K0 * nt + (k + 1); g1[2].ldb = nt;
+        g1[2].C = Wb + nd; g1[2].ldc = ldw; g1[2].M = kb; g1[2].N = ncs; g1[2].K = m;
+        ABFT_CUDA_TRY(launch_gemm_f64(g1, full ? 3 : 2, 1, 1, nullptr, 0, st, s));
+        ABFT_CUDA_TRY(launch_larft(Gn, kb, tau + K0, T, s));
         GemmSeg g2{};
         g2.A = T; g2.lda = kb; g2.B = Wb; g2.ldb = ldw; g2.C = Xb; g2.ldc = ldw;
         g2.M = kb; g2.N = ncol; g2.K = kb;

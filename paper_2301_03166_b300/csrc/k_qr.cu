@@ -29,12 +29,43 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Cooperative geqr2 on the panel P (m x kb, row-major, ld lda).  part is a
 // G x (kb + 1) scratch of per-CTA partial sums, wv a kb scratch for the
 // reflector's row vector w, nrm receives the column norms before the PD.
+// sum_{b<G} p[b * stride] in the order b = 0, 1, ..., with eight loads in
+// flight (the partials live in L2; a load-add chain would pay its latency G times)
+__device__ __forceinline__ double ordered_sum(const double* p, int64_t stride, unsigned G) {
+    double s = 0.0;
+    for (unsigned b = 0; b < G; b += 8) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = (b + u < G) ? p[(int64_t)(b + u) * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (b + u < G) s += x[u];
+    }
+    return s;
+}
+
+// The same sum taken by one warp: lane l adds b = l, l + 32, ... in order, then
+// an xor butterfly (a + b == b + a, so every lane ends with the same value, and
+// every CTA that calls it on the same data gets the same bits).  The dependent
+// FP64 chain is ceil(G/32) + 5 adds instead of G: on this FP64 pipe one
+// warp-instruction occupies a sub-partition for tens of cycles, so a G-long
+// chain per column was a large part of the panel's time.
+__device__ __forceinline__ double warp_tree_sum(const double* p, int64_t stride, unsigned G) {
+    const unsigned lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (unsigned b = lane; b < G; b += 32) s += p[(int64_t)b * stride];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64_t m, int kb,
                                                    double* tau, double* nrm, double* part,
                                                    double* wv, DevStatus* st) {
     __shared__ double red[QT / 32];
     __shared__ double wl[512];
     __shared__ double vloc[QMAXR];
+    __shared__ double s_sst;
     const unsigned G = gridDim.x;
     const int64_t R = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
@@ -49,9 +80,7 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
     if (!grid_barrier(st, G)) return;
     if (blockIdx.x == 0)
         for (int c = threadIdx.x; c < kb; c += QT) {
-            double s = 0.0;
-            for (unsigned b = 0; b < G; ++b) s += part[(int64_t)b * ld + c];
-            nrm[c] = sqrt(s);
+            nrm[c] = sqrt(ordered_sum(part + c, ld, G));
         }
     if (!grid_barrier(st, G)) return;
     for (int j = 0; j < kb; ++j) {
@@ -65,14 +94,28 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
         ss = block_sum(ss, red);
         if (threadIdx.x == 0) mypart[0] = ss;
         for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
+            // eight rows of operands loaded ahead, accumulated in row order
             double d = 0.0;
-            for (int64_t i = ibeg; i < r1; ++i) d += P[i * lda + j] * P[i * lda + c];
+            for (int64_t i = ibeg; i < r1; i += 8) {
+                double xv[8], av[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i + u < r1) { xv[u] = P[(i + u) * lda + j]; av[u] = P[(i + u) * lda + c]; }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i + u < r1) d += xv[u] * av[u];
+            }
             mypart[1 + c] = d;
         }
         if (!grid_barrier(st, G)) return;
-        // B: every CTA forms beta, tau; CTA b reduces the dots of columns c = j+1+b, +G, ...
-        double sst = 0.0;
-        for (unsigned b = 0; b < G; ++b) sst += part[(int64_t)b * ld];
+        // B: every CTA forms beta, tau; warp q of CTA b reduces the dots of
+        // columns c = j + 1 + 8 b + q, then + 8 G, ...
+        if (threadIdx.x < 32) {
+            const double t = warp_tree_sum(part, ld, G);
+            if (threadIdx.x == 0) s_sst = t;
+        }
+        __syncthreads();
+        const double sst = s_sst;
         const double alpha = P[(int64_t)j * lda + j];
         double tj = 0.0, beta = alpha, scal = 1.0;
         if (sst != 0.0) {
@@ -82,12 +125,14 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
             scal = alpha - beta;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) tau[j] = tj;
-        if (tj != 0.0)
-            for (int c = j + 1 + blockIdx.x * QT + threadIdx.x; c < kb; c += G * QT) {
-                double d = 0.0;
-                for (unsigned b = 0; b < G; ++b) d += part[(int64_t)b * ld + 1 + c];
-                wv[c] = P[(int64_t)j * lda + c] + d / scal;
+        if (tj != 0.0) {
+            const int nw = QT / 32;
+            for (int c = j + 1 + (int)blockIdx.x * nw + (int)(threadIdx.x >> 5); c < kb;
+                 c += (int)G * nw) {
+                const double d = warp_tree_sum(part + 1 + c, ld, G);
+                if ((threadIdx.x & 31) == 0) wv[c] = P[(int64_t)j * lda + c] + d / scal;
             }
+        }
         if (!grid_barrier(st, G)) return;
         // C: v_i = x_i / (alpha - beta); a -= tau v w on my rows
         if (tj == 0.0) continue;
@@ -95,18 +140,24 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
         for (int64_t i = ibeg + threadIdx.x; i < r1; i += QT) {
             double v = P[i * lda + j] / scal;
             P[i * lda + j] = v;
-            vloc[i - r0] = v;
+            vloc[i - r0] = __dmul_rn(tj, v);  // tau_j v_i, once per row
         }
         __syncthreads();
         const int w = kb - j - 1;
         if (w > 0) {
-            if (ibeg < r1) {
-                const int64_t nrow = r1 - ibeg;
-                for (int64_t e = threadIdx.x; e < nrow * w; e += QT) {
-                    int64_t i = ibeg + e / w;
-                    int c = j + 1 + (int)(e % w);
-                    double* a = P + i * lda + c;
-                    *a = __dsub_rn(*a, __dmul_rn(__dmul_rn(tj, vloc[i - r0]), wl[c]));
+            // one column per thread, eight rows at a time (coalesced along the
+            // rows, eight loads in flight)
+            for (int c = j + 1 + threadIdx.x; c < kb && ibeg < r1; c += QT) {
+                const double wc = wl[c];
+                for (int64_t i = ibeg; i < r1; i += 8) {
+                    double av[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < r1) av[u] = P[(i + u) * lda + c];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < r1)
+                            P[(i + u) * lda + c] = fma(-vloc[i + u - r0], wc, av[u]);
                 }
             }
             if (j >= r0 && j < r1)
@@ -166,22 +217,41 @@ __global__ void k_qr_vsums(const double* V, int64_t m, int kb, int64_t g, int64_
 
 // larft (forward, columnwise) from Gneg = -V^T V: T[j][j] = tau_j,
 // T[0:j, j] = -tau_j T[0:j, 0:j] (V^T v_j)[0:j].  One CTA, columns in order.
-__global__ void __launch_bounds__(512) k_larft(const double* Gneg, int kb, const double* tau,
-                                               double* T) {
-    __shared__ double y[512];
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) T[e] = 0.0;
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-        const double tj = tau[j];
-        for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = -Gneg[(int64_t)i * kb + j];
-        __syncthreads();
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            double s = 0.0;
-            for (int q = i; q < j; ++q) s += T[(int64_t)i * kb + q] * y[q];
-            T[(int64_t)i * kb + j] = -tj * s;
+// T of the compact WY form: T(j, j) = tau_j and, for i < j,
+// T(i, j) = -tau_j sum_{q=i}^{j-1} T(i, q) (V^T V)(q, j)  (Gneg = -V^T V).
+// Row i depends on nothing but its own earlier entries, so one warp takes one
+// row: lane l keeps the running sums S_j of the columns j = l, l + 32, ...
+// and, as soon as T(i, q) is final, adds T(i, q) (V^T V)(q, j) to every S_j,
+// j > q -- the terms of each sum in the order q = i, i + 1, ..., as a
+// column-by-column evaluation takes them, and row q of Gneg read contiguously.
+constexpr int LARFT_W = 4;   // rows (warps) per CTA
+__global__ void __launch_bounds__(32 * LARFT_W) k_larft(const double* Gneg, int kb,
+                                                       const double* tau, double* T) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * LARFT_W + (threadIdx.x >> 5);
+    if (i >= kb) return;
+    double S[16];   // kb <= 512
+#pragma unroll
+    for (int t = 0; t < 16; ++t) S[t] = 0.0;
+    double* Ti = T + (int64_t)i * kb;
+    for (int j = lane; j < i; j += 32) Ti[j] = 0.0;
+    for (int q = i; q < kb; ++q) {
+        // T(i, q): the diagonal, or -tau_q times the finished sum S_q
+        const int own = q & 31, slot = q >> 5;
+        double mine = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            if (t == slot) mine = S[t];
+        const double sq = __shfl_sync(0xffffffffu, mine, own);
+        const double tq = tau[q];
+        const double tiq = (q == i) ? tq : -tq * sq;
+        if (lane == own) Ti[q] = tiq;
+        const double* Gq = Gneg + (int64_t)q * kb;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int j = lane + 32 * t;
+            if (j > q && j < kb) S[t] = fma(tiq, -Gq[j], S[t]);
         }
-        if (threadIdx.x == 0) T[(int64_t)j * kb + j] = tj;
-        __syncthreads();
     }
 }
 
@@ -249,7 +319,9 @@ cudaError_t launch_qr_vsums(const double* V, int64_t m, int64_t kb, int64_t g, i
 
 cudaError_t launch_larft(const double* Gneg, int64_t kb, const double* tau, double* T,
                          cudaStream_t s) {
-    k_larft<<<1, 512, 0, s>>>(Gneg, (int)kb, tau, T);
+    if (kb > 512) return cudaErrorInvalidValue;
+    k_larft<<<(unsigned)((kb + LARFT_W - 1) / LARFT_W), 32 * LARFT_W, 0, s>>>(Gneg, (int)kb, tau,
+                                                                           T);
     note_launch();
     return cudaGetLastError();
 }
