@@ -25,8 +25,8 @@ struct DevStatus {
     int error;                         // internal error code (timeouts)
     int lu_info;                       // LU: 1-based first exactly-zero pivot (factorization continues)
     int vexp;                          // > 0: biased exponent bound of the verified entries (fixed-point sums)
-    unsigned int bar_arrive;           // grid barrier of the cooperative panel kernels
-    unsigned int bar_gen;
+    unsigned long long bar_count;      // grid barrier of the cooperative panel kernels:
+                                       // arrivals since the launch (zeroed by the launcher)
     abft_fault loc[ABFT_MAX_LOC];
 };
 
@@ -39,32 +39,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks,
+                                             unsigned long long& passed) {
+    // bar_count only grows during a launch: barrier number `passed` (1, 2, ...)
+    // is complete once every CTA has added its arrival, i.e. at passed * nblocks,
+    // so the last arrival's own increment releases the waiters (no reset and no
+    // generation flag on the critical path).  A CTA that gives up never arrives
+    // again, so the others give up at their next wait as well.
     __shared__ int s_ok;
     __syncthreads();
+    ++passed;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int* vgen = &st->bar_gen;
-        unsigned int gen = *vgen;
+        const unsigned long long target = passed * nblocks;
         __threadfence();
-        unsigned int ticket = atomicAdd(&st->bar_arrive, 1u);
-        if (ticket == nblocks - 1) {
-            atomicExch(&st->bar_arrive, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            unsigned long long t0 = global_ns();
-            while (*vgen == gen) {
+        const unsigned long long seen = atomicAdd(&st->bar_count, 1ull) + 1ull;
+        if (seen < target) {
+            volatile unsigned long long* vc = &st->bar_count;
+            const unsigned long long t0 = global_ns();
+            while (*vc < target) {
                 if (global_ns() - t0 > kBarrierNs) {
                     atomicExch(&st->error, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
-        s_ok = ok && (*(volatile int*)&st->error == 0);
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;

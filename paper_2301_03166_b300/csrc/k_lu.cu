@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
     const unsigned G = gridDim.x;
     const int64_t R = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
+    unsigned long long nbar = 0;   // grid barriers passed
     // stage: [2][G + 1][kb]: candidate row per CTA, then row j (slot G)
     for (int j = 0; j < kb; ++j) {
         const int par = j & 1;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
                 slot[(size_t)blockIdx.x * kb + c] = P[bi * lda + c];
         if (j >= r0 && j < r1)
             for (int c = threadIdx.x; c < kb; c += PT) slot[(size_t)G * kb + c] = P[(int64_t)j * lda + c];
-        if (!grid_barrier(st, G)) return;
+        if (!grid_barrier(st, G, nbar)) return;
         // B: every CTA picks the pivot from the published values (same order,
         // same result); the pivot row comes from its owner's copy
         double v = -1.0;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (i + u < r1)
-                        P[(i + u) * lda + c] = __dsub_rn(av[u], __dmul_rn(lcol[i + u - r0], uc));
+                        P[(i + u) * lda + c] = fma(-lcol[i + u - r0], uc, av[u]);
             }
         }
         __syncthreads();
@@ -456,6 +457,8 @@ cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int
     while ((m + G - 1) / G > MAXR) ++G;   // rows per CTA must fit the shared buffer
     if (G > num_sms()) return cudaErrorInvalidValue;
     int kbi = (int)kb;
+    cudaError_t e0 = cudaMemsetAsync(&st->bar_count, 0, sizeof(st->bar_count), s);
+    if (e0 != cudaSuccess) return e0;
     void* args[] = {&P, &lda, &m, &kbi, &K0, &ipiv, &st, &part_v, &part_i, &stage};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_getf2_coop, dim3((unsigned)G), dim3(PT),
                                                 args, 0, s);

@@ -71,18 +71,19 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
     const int64_t r0 = blockIdx.x * R, r1 = (r0 + R < m) ? r0 + R : m;
     const int ld = kb + 1;
     double* mypart = part + (int64_t)blockIdx.x * ld;
+    unsigned long long nbar = 0;   // grid barriers passed
     // column norms before the PD (for the norm-preservation check)
     for (int c = threadIdx.x; c < kb; c += QT) {
         double s = 0.0;
         for (int64_t i = r0; i < r1; ++i) s += P[i * lda + c] * P[i * lda + c];
         mypart[c] = s;
     }
-    if (!grid_barrier(st, G)) return;
+    if (!grid_barrier(st, G, nbar)) return;
     if (blockIdx.x == 0)
         for (int c = threadIdx.x; c < kb; c += QT) {
             nrm[c] = sqrt(ordered_sum(part + c, ld, G));
         }
-    if (!grid_barrier(st, G)) return;
+    if (!grid_barrier(st, G, nbar)) return;
     for (int j = 0; j < kb; ++j) {
         // A: partial |x(2:)|^2 and partial dots x(2:)^T P[:, c] over my rows i > j
         const int64_t ibeg = r0 > j + 1 ? r0 : j + 1;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
             }
             mypart[1 + c] = d;
         }
-        if (!grid_barrier(st, G)) return;
+        if (!grid_barrier(st, G, nbar)) return;
         // B: every CTA forms beta, tau; warp q of CTA b reduces the dots of
         // columns c = j + 1 + 8 b + q, then + 8 G, ...
         if (threadIdx.x < 32) {
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
                 if ((threadIdx.x & 31) == 0) wv[c] = P[(int64_t)j * lda + c] + d / scal;
             }
         }
-        if (!grid_barrier(st, G)) return;
+        if (!grid_barrier(st, G, nbar)) return;
         // C: v_i = x_i / (alpha - beta); a -= tau v w on my rows
         if (tj == 0.0) continue;
         for (int c = j + 1 + threadIdx.x; c < kb; c += QT) wl[c] = wv[c];
@@ -286,6 +287,8 @@ cudaError_t launch_geqr2_coop(double* P, int64_t lda, int64_t m, int64_t kb, dou
     while ((m + G - 1) / G > QMAXR) ++G;
     if (G > num_sms()) return cudaErrorInvalidValue;
     int kbi = (int)kb;
+    cudaError_t e0 = cudaMemsetAsync(&st->bar_count, 0, sizeof(st->bar_count), s);
+    if (e0 != cudaSuccess) return e0;
     void* args[] = {&P, &lda, &m, &kbi, &tau, &nrm, &part, &wv, &st};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_geqr2_coop, dim3((unsigned)G), dim3(QT),
                                                 args, 0, s);
