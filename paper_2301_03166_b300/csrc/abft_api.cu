@@ -783,11 +783,15 @@ namespace {
 
 // ------------------------------------------------------------------ QR
 struct QrWs {
-    size_t st, cs, cr, nrm, part, wv, V, G, T, W, X, total;
+    size_t st, cs, cr, nrm, part, wv, V, G, T, W, X, sw, exw, su, exu, total;
     int64_t nc, nt, ldw;
 };
 
-QrWs qr_ws(int64_t n, int64_t nb, int mode) {
+// FP64-accurate QR update: the reduction of V^T [C, r] over the m panel rows
+// runs in QR_KC-row pieces (K of one slice product)
+constexpr int64_t QR_KC = 256;
+
+QrWs qr_ws(int64_t n, int64_t nb, int mode, bool emu = false) {
     QrWs w{};
     w.nt = (n + nb - 1) / nb;
     w.nc = mode == ABFT_MODE_FULL ? 1 : (mode == ABFT_MODE_SINGLE ? 2 : 0);
@@ -805,6 +809,14 @@ QrWs qr_ws(int64_t n, int64_t nb, int mode) {
     w.T = off; off = align_up(off + d * (size_t)nb * (size_t)nb);
     w.W = off; off = align_up(off + d * (size_t)nb * (size_t)w.ldw);
     w.X = off; off = align_up(off + d * (size_t)nb * (size_t)w.ldw);
+    // slices: pieces of [V | C | r] columns (first step the largest), and
+    // [V rows | checksum panel rows | columns of X]
+    const int64_t rw = emu ? (n + QR_KC - 1) / QR_KC * (n + w.nt) : 0;
+    const int64_t ru = emu ? 2 * n + w.nt * (w.nc + 1) : 0;
+    w.sw = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)rw * (size_t)QR_KC);
+    w.exw = off; off = align_up(off + sizeof(int) * (size_t)rw);
+    w.su = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)ru * (size_t)nb);
+    w.exu = off; off = align_up(off + sizeof(int) * (size_t)ru);
     w.total = off;
     return w;
 }
@@ -820,7 +832,7 @@ bool qr_fault_ok(const abft_fault& f, int64_t n, int64_t nb, int64_t N) {
 // Blocked ABFT Householder QR step loop.
 int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double* tau,
              const abft_fault* faults, int32_t nfaults, double tau_scale, const QrWs& w,
-             char* base, cudaStream_t s) {
+             char* base, cudaStream_t s, bool emu) {
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
     double* Cr = (double*)(base + w.cr);
@@ -867,6 +879,84 @@ int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double
         ABFT_CUDA_TRY(cudaMemsetAsync(Gn, 0, sizeof(double) * kb * kb, s));
         ABFT_CUDA_TRY(cudaMemsetAsync(Wb, 0, sizeof(double) * kb * ldw, s));
         ABFT_CUDA_TRY(cudaMemsetAsync(Xb, 0, sizeof(double) * kb * ldw, s));
+        ComputeFault cf[MAX_CF];
+        int ncf = 0;
+        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
+            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
+                cf[ncf++] = {faults[f].row - K0, faults[f].col - T0, faults[f].delta};
+        if (emu) {
+            // FP64-accurate larfb from exact BF16 slice products.  Gn and W:
+            // the reduction over the m panel rows in QR_KC-row pieces, piece p
+            // holding the slices of columns p of [V | C | r] (one scale per
+            // column and piece); one launch per piece subtracts its exact
+            // product from Gn and W in turn (fixed order, FP64 sums).
+            uint16_t* Sw = (uint16_t*)(base + w.sw);
+            int* exw = (int*)(base + w.exw);
+            const int64_t R = kb + ncol, npc = (m + QR_KC - 1) / QR_KC, MW = npc * R;
+            ABFT_CUDA_TRY(launch_slice_cols_chunked(V, kb, QR_KC, m, kb, Sw, MW, 0, R, exw, s));
+            ABFT_CUDA_TRY(launch_slice_cols_chunked(A + K0 * lda + T0, lda, QR_KC, m, nd, Sw, MW,
+                                                    kb, R, exw, s));
+            if (ncs > 0)
+                ABFT_CUDA_TRY(launch_slice_cols_chunked(Cr + K0 * nt + (k + 1), nt, QR_KC, m, ncs,
+                                                        Sw, MW, kb + nd, R, exw, s));
+            for (int64_t pc = 0; pc < npc; ++pc) {
+                const int64_t r0 = pc * R;
+                EmuRectHost rw[3] = {};
+                int nr = 0;
+                {   // W[:, :nd] -= V_p^T C_p
+                    EmuRectHost& r = rw[nr++];
+                    r.C = Wb; r.ldc = ldw; r.a0 = r0; r.na = kb; r.b0 = r0 + kb; r.nb = nd;
+                    r.cdiv = 1; r.frow = -1;
+                }
+                if (ncs > 0) {   // W[:, nd:] -= V_p^T r_p
+                    EmuRectHost& r = rw[nr++];
+                    r.C = Wb + nd; r.ldc = ldw; r.a0 = r0; r.na = kb; r.b0 = r0 + kb + nd;
+                    r.nb = ncs; r.cdiv = 1; r.frow = -1;
+                }
+                {   // Gn -= V_p^T V_p
+                    EmuRectHost& r = rw[nr++];
+                    r.C = Gn; r.ldc = kb; r.a0 = r0; r.na = kb; r.b0 = r0; r.nb = kb;
+                    r.cdiv = 1; r.frow = -1;
+                }
+                ABFT_CUDA_TRY(launch_tmu_emu(Sw, exw, MW, QR_KC, nullptr, 0, 0, 0, 128, rw, nr,
+                                             nullptr, 0, 0, st, s));
+            }
+            ABFT_CUDA_TRY(launch_larft(Gn, kb, tau + K0, T, s));
+            GemmSeg g2{};   // X = -T^T W (K = kb: FP64)
+            g2.A = T; g2.lda = kb; g2.B = Wb; g2.ldb = ldw; g2.C = Xb; g2.ldc = ldw;
+            g2.M = kb; g2.N = ncol; g2.K = kb;
+            ABFT_CUDA_TRY(launch_gemm_f64(&g2, 1, 1, 1, nullptr, 0, st, s));
+            // [C, r] -= V X and c_I -= (1^T V_I) X: rows of V and of the
+            // checksum panel against the columns of X
+            uint16_t* Su = (uint16_t*)(base + w.su);
+            int* exu = (int*)(base + w.exu);
+            const int64_t mcs = check ? (nt - k) * nc : 0, MU = m + mcs + ncol;
+            ABFT_CUDA_TRY(launch_slice_panel(V, kb, m, kb, Su, MU, 0, exu, s));
+            if (mcs > 0)
+                ABFT_CUDA_TRY(launch_slice_panel(CS + (k * nc) * n + K0, n, mcs, kb, Su, MU, m,
+                                                 exu, s));
+            ABFT_CUDA_TRY(launch_slice_cols(Xb, ldw, kb, ncol, Su, MU, m + mcs, exu, s));
+            EmuRectHost ru[3] = {};
+            int nr = 0;
+            {
+                EmuRectHost& r = ru[nr++];
+                r.C = A + K0 * lda + T0; r.ldc = lda; r.a0 = 0; r.na = m; r.b0 = m + mcs;
+                r.nb = nd; r.cdiv = 1; r.frow = 0; r.fcol = 0;
+            }
+            if (check) {
+                EmuRectHost& r = ru[nr++];
+                r.C = CS + (k * nc) * n + T0; r.ldc = n; r.a0 = m; r.na = mcs; r.b0 = m + mcs;
+                r.nb = nd; r.cdiv = 1; r.frow = -1;
+            }
+            if (full && ncs > 0) {
+                EmuRectHost& r = ru[nr++];
+                r.C = Cr + K0 * nt + (k + 1); r.ldc = nt; r.a0 = 0; r.na = m;
+                r.b0 = m + mcs + nd; r.nb = ncs; r.cdiv = 1; r.frow = -1;
+            }
+            ABFT_CUDA_TRY(launch_tmu_emu(Su, exu, MU, kb, nullptr, 0, 0, 0, 128, ru, nr, cf, ncf,
+                                         0, st, s));
+            timing_mark(PH_TMU, 0, s);
+        } else {
         GemmSeg g1[3] = {};
         g1[0].A = V; g1[0].lda = kb; g1[0].B = V; g1[0].ldb = kb;
         g1[0].C = Gn; g1[0].ldc = kb; g1[0].M = kb; g1[0].N = kb; g1[0].K = m;
@@ -894,13 +984,9 @@ int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double
             b.A = V; b.lda = kb; b.B = Xb + nd; b.ldb = ldw;
             b.C = Cr + K0 * nt + (k + 1); b.ldc = nt; b.M = m; b.N = ncs; b.K = kb;
         }
-        ComputeFault cf[MAX_CF];
-        int ncf = 0;
-        for (int f = 0; f < nfaults && ncf < MAX_CF; ++f)
-            if (faults[f].step == k && faults[f].kind == ABFT_FAULT_COMPUTE)
-                cf[ncf++] = {faults[f].row - K0, faults[f].col - T0, faults[f].delta};
         ABFT_CUDA_TRY(launch_gemm_f64(g3, nseg, 0, 1, cf, ncf, st, s));
         timing_mark(PH_TMU, 0, s);
+        }
         timing_mark(PH_VERIFY, 1, s);
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && (faults[f].kind == ABFT_FAULT_MEMORY ||
@@ -924,13 +1010,15 @@ extern "C" {
 int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                double* tau, const abft_fault* faults, int32_t nfaults, double tau_scale,
                abft_report* rep, void* ws, size_t* ws_bytes, void* stream) {
-    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes);
+    int rc = check_common(n, nb, dtype, mode, A, lda, faults, nfaults, tau_scale, ws, ws_bytes,
+                          true);
     if (rc != ABFT_OK) return rc;
     if (n > 0 && tau == nullptr && ws != nullptr) return -7;
     const int64_t N = (n + nb - 1) / nb;
     for (int f = 0; f < nfaults; ++f)
         if (!qr_fault_ok(faults[f], n, nb, N)) return -8;
-    const QrWs w = qr_ws(n, nb, mode);
+    const bool emu = dtype == ABFT_F64_EMU;
+    const QrWs w = qr_ws(n, nb, mode, emu);
     if (ws == nullptr) {
         *ws_bytes = w.total;
         return ABFT_OK;
@@ -941,7 +1029,7 @@ int abft_geqrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
     DevStatus* st = (DevStatus*)(base + w.st);
     ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
     if (n > 0) {
-        rc = qr_steps(n, nb, mode, A, lda, tau, faults, nfaults, tau_scale, w, base, s);
+        rc = qr_steps(n, nb, mode, A, lda, tau, faults, nfaults, tau_scale, w, base, s, emu);
         if (rc != ABFT_OK) return rc;
     }
     ABFT_CUDA_TRY(timing_collect(s));

@@ -341,6 +341,11 @@ int64_t emu_rows(int64_t n, int64_t nb);
 size_t emu_slice_bytes(int64_t n, int64_t nb);
 cudaError_t launch_slice_cols(const double* P, int64_t ld, int64_t K, int64_t ncols, uint16_t* S,
                               int64_t Mtot, int64_t row0, int* ex, cudaStream_t s);
+// The columns of an mrows x ncols matrix in K-row pieces (zero past mrows):
+// piece c at slice rows row0 + c rstride .. + ncols - 1, one scale per column and piece.
+cudaError_t launch_slice_cols_chunked(const double* P, int64_t ld, int64_t K, int64_t mrows,
+                                      int64_t ncols, uint16_t* S, int64_t Mtot, int64_t row0,
+                                      int64_t rstride, int* ex, cudaStream_t s);
 cudaError_t launch_slice_panel(const double* P, int64_t lda, int64_t m, int64_t kb, uint16_t* S,
                                int64_t Mtot, int64_t row0, int* ex, cudaStream_t s);
 cudaError_t launch_tmu_emu(const uint16_t* S, const int* ex, int64_t mtot, int64_t kb, double* C,

@@ -205,21 +205,30 @@ __global__ void __launch_bounds__(256) k_slice_panel(const double* __restrict__ 
 // U12).  One CTA per 32 columns: the K x 32 tile goes through shared memory
 // so that the reads (along rows of P) and the writes (along rows of S) are
 // coalesced; one scale per column.
+// Chunked form (blockIdx.y = chunk c): rows c K .. c K + K - 1 of an
+// mrows-row matrix, rows past mrows taken as zero, written at row0 + c rstride:
+// the operands of a product whose reduction runs over the rows of P (the
+// QR's V^T C), cut into K-long pieces with a scale per column and piece.
 constexpr int SC_COLS = 32;
 __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ P, int64_t ld,
-                                                    int K, int64_t ncols, uint16_t* __restrict__ S,
-                                                    int64_t Mtot, int64_t row0,
+                                                    int K, int64_t mrows, int64_t ncols,
+                                                    uint16_t* __restrict__ S, int64_t Mtot,
+                                                    int64_t row0, int64_t rstride,
                                                     int* __restrict__ ex) {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     double* T = (double*)sc_smem;                     // K x (SC_COLS + 1)
     __shared__ int emax_s[SC_COLS];
     const int64_t c0 = (int64_t)blockIdx.x * SC_COLS;
     const int nc = (int)(ncols - c0 < SC_COLS ? ncols - c0 : SC_COLS);
+    P += (int64_t)blockIdx.y * K * ld;
+    row0 += (int64_t)blockIdx.y * rstride;
+    const int64_t left = mrows - (int64_t)blockIdx.y * K;
+    const int kv = (int)(left < K ? left : K);
     if (threadIdx.x < SC_COLS) emax_s[threadIdx.x] = 1;
     __syncthreads();
     for (int e = threadIdx.x; e < K * SC_COLS; e += blockDim.x) {
         const int k = e / SC_COLS, j = e % SC_COLS;
-        const double v = j < nc ? P[(int64_t)k * ld + c0 + j] : 0.0;
+        const double v = (j < nc && k < kv) ? P[(int64_t)k * ld + c0 + j] : 0.0;
         T[k * (SC_COLS + 1) + j] = v;
         atomicMax(&emax_s[j], (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffull));
     }
@@ -525,8 +534,16 @@ size_t emu_slice_bytes(int64_t n, int64_t nb) {
 
 cudaError_t launch_slice_cols(const double* P, int64_t ld, int64_t K, int64_t ncols, uint16_t* S,
                               int64_t Mtot, int64_t row0, int* ex, cudaStream_t s) {
-    if (ncols <= 0) return cudaSuccess;
-    if (K % 32 != 0 || K > 256 || row0 + ncols > Mtot) return cudaErrorInvalidValue;
+    return launch_slice_cols_chunked(P, ld, K, K, ncols, S, Mtot, row0, 0, ex, s);
+}
+
+cudaError_t launch_slice_cols_chunked(const double* P, int64_t ld, int64_t K, int64_t mrows,
+                                      int64_t ncols, uint16_t* S, int64_t Mtot, int64_t row0,
+                                      int64_t rstride, int* ex, cudaStream_t s) {
+    if (ncols <= 0 || mrows <= 0) return cudaSuccess;
+    const int64_t nch = (mrows + K - 1) / K;
+    if (K % 32 != 0 || K > 256 || nch > 65535 || row0 + (nch - 1) * rstride + ncols > Mtot)
+        return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * (size_t)K * (SC_COLS + 1);
     static bool attr = false;
     if (!attr) {
@@ -535,8 +552,8 @@ cudaError_t launch_slice_cols(const double* P, int64_t ld, int64_t K, int64_t nc
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_slice_cols<<<(unsigned)((ncols + SC_COLS - 1) / SC_COLS), 256, smem, s>>>(P, ld, (int)K, ncols,
-                                                                             S, Mtot, row0, ex);
+    const dim3 grid((unsigned)((ncols + SC_COLS - 1) / SC_COLS), (unsigned)nch);
+    k_slice_cols<<<grid, 256, smem, s>>>(P, ld, (int)K, mrows, ncols, S, Mtot, row0, rstride, ex);
     note_launch();
     return cudaGetLastError();
 }
