@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
                    choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32", "lu",
-                            "lu-emu", "qr"],
+                            "lu-emu", "qr", "qr-emu"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
                         "refinement, an FP32 two-sweep solve with the FP64 factor, or the ABFT "
@@ -569,9 +569,13 @@ def run_ours(args, ws, rank, local):
         def qr_step():
             A.copy_(U0)
             return abft.geqrf(A, nb, abft.FULL, faults=qr_f, workspace=wsp)
+        def qr_emu_step():   # V^T [C, r] and C -= V X FP64-accurate on the BF16 tensor cores
+            A.copy_(U0)
+            return abft.geqrf(A, nb, abft.FULL, dtype=abft.F64_EMU, faults=qr_f, workspace=wsp)
         for name, fn, fl, flops in (("lu", lu_step, lu_f, 2 * n ** 3 / 3),
                                     ("lu_fp64_emulated", lu_emu_step, lu_f, 2 * n ** 3 / 3),
-                                    ("qr", qr_step, qr_f, 4 * n ** 3 / 3)):
+                                    ("qr", qr_step, qr_f, 4 * n ** 3 / 3),
+                                    ("qr_fp64_emulated", qr_emu_step, qr_f, 4 * n ** 3 / 3)):
             ms_x, res = timed(fn, 1, 1)
             rep_x = res[-1]
             lu_qr[name] = {"ms": ms_x, "tflops": flops / (ms_x * 1e-3) / 1e12,
@@ -700,13 +704,14 @@ def profile_case(args):
     wsp = abft.Workspace()
     B = torch.from_numpy(W.rhs(n, 16, seed=1003)).to(dev)
     X = torch.empty_like(B)
-    if args.profile_case in ("lu", "lu-emu", "qr"):
+    if args.profile_case in ("lu", "lu-emu", "qr", "qr-emu"):
         U0 = W.uniform_torch(n, seed=1001 + n, device=dev)
         for _ in range(2):
             A.copy_(U0)
-            if args.profile_case == "qr":
-                abft.geqrf(A, nb, abft.FULL, faults=W.fault_schedule(n, nb, "qr", seed=4000 + n),
-                           workspace=wsp)
+            if args.profile_case in ("qr", "qr-emu"):
+                dt = abft.F64 if args.profile_case == "qr" else abft.F64_EMU
+                abft.geqrf(A, nb, abft.FULL, dtype=dt,
+                           faults=W.fault_schedule(n, nb, "qr", seed=4000 + n), workspace=wsp)
             else:
                 dt = abft.F64 if args.profile_case == "lu" else abft.F64_EMU
                 abft.getrf(A, nb, abft.FULL, dtype=dt,

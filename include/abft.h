@@ -46,10 +46,12 @@ typedef enum {
     ABFT_F32 = 1,        /* reserved */
     ABFT_MIXED_BF16 = 2, /* TMU inputs BF16 with per-tile power-of-two scales, FP32 accumulate */
     ABFT_MIXED_F16 = 3,  /* TMU inputs FP16 with per-tile power-of-two scales, FP32 accumulate */
-    ABFT_F64_EMU = 4     /* abft_potrf only: FP64-accurate TMU from exact products of BF16
-                            slices on the tensor cores (7 x 7-bit slices per element under
-                            a power-of-two row scale, 28 slice pairs, integer recombination;
-                            nb = 128 or 256); PD, PU, checksum borders and verify in FP64 */
+    ABFT_F64_EMU = 4     /* abft_potrf / getrf / geqrf (and posv_ir's residual): FP64-accurate
+                            TMU from exact products of BF16 slices on the tensor cores (8
+                            balanced base-128 digits per element under a power-of-two row
+                            scale, the 36 digit pairs of weight <= 7, FP32 group sums exact
+                            for K <= 256, integer recombination; nb <= 256); PD, pivoting,
+                            checksum verification and correction in FP64 */
 } abft_dtype;
 
 /* Checksum strength (Sec. 3.1.2: single-side vs full checksum ABFT). */
@@ -177,6 +179,12 @@ int abft_getrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
  * reflector applied to the trailing columns, C -= V T^T V^T C); Sec. 3.1.2
  * (the row checksums ride through the update as extra columns, the column
  * checksums of each block row are updated by (1^T V_I) T^T V^T C).
+ * dtype ABFT_F64, or ABFT_F64_EMU with nb <= 256: V^T V and V^T [C, r]
+ * (reduced over the panel rows in 256-row pieces, one exact slice product
+ * per piece, summed in FP64 in piece order) and [C, r] -= V X with the
+ * checksum rows FP64-accurate from BF16 slices on the tensor cores; the
+ * panel, T, X = T^T W and verification in FP64.  Other dtypes
+ * ABFT_ERR_UNSUPPORTED.
  *   A, lda     n x n row-major; on return R on and above the diagonal and the
  *              reflectors v (unit leading entry implicit) below, LAPACK
  *              geqrf layout; reflectors follow LAPACK larfg:
