@@ -922,14 +922,21 @@ int qr_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, double
                                              nullptr, 0, 0, st, s));
             }
             ABFT_CUDA_TRY(launch_larft(Gn, kb, tau + K0, T, s));
-            GemmSeg g2{};   // X = -T^T W (K = kb: FP64)
-            g2.A = T; g2.lda = kb; g2.B = Wb; g2.ldb = ldw; g2.C = Xb; g2.ldc = ldw;
-            g2.M = kb; g2.N = ncol; g2.K = kb;
-            ABFT_CUDA_TRY(launch_gemm_f64(&g2, 1, 1, 1, nullptr, 0, st, s));
-            // [C, r] -= V X and c_I -= (1^T V_I) X: rows of V and of the
-            // checksum panel against the columns of X
             uint16_t* Su = (uint16_t*)(base + w.su);
             int* exu = (int*)(base + w.exu);
+            {   // X = -T^T W: the columns of T against the columns of W
+                const int64_t MX = kb + ncol;
+                ABFT_CUDA_TRY(launch_slice_cols(T, kb, kb, kb, Su, MX, 0, exu, s));
+                ABFT_CUDA_TRY(launch_slice_cols(Wb, ldw, kb, ncol, Su, MX, kb, exu, s));
+                EmuRectHost rx{};
+                rx.C = Xb; rx.ldc = ldw; rx.a0 = 0; rx.na = kb; rx.b0 = kb; rx.nb = ncol;
+                rx.cdiv = 1; rx.frow = -1;
+                ABFT_CUDA_TRY(launch_tmu_emu(Su, exu, MX, kb, nullptr, 0, 0, 0, 128, &rx, 1,
+                                             nullptr, 0, 0, st, s));
+            }
+            // [C, r] -= V X and c_I -= (1^T V_I) X: rows of V and of the
+            // checksum panel against the columns of X (the slices of T and W
+            // above are consumed before these overwrite them: same stream)
             const int64_t mcs = check ? (nt - k) * nc : 0, MU = m + mcs + ncol;
             ABFT_CUDA_TRY(launch_slice_panel(V, kb, m, kb, Su, MU, 0, exu, s));
             if (mcs > 0)

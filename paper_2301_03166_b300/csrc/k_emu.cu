@@ -226,21 +226,45 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ P
     const int kv = (int)(left < K ? left : K);
     if (threadIdx.x < SC_COLS) emax_s[threadIdx.x] = 1;
     __syncthreads();
-    for (int e = threadIdx.x; e < K * SC_COLS; e += blockDim.x) {
-        const int k = e / SC_COLS, j = e % SC_COLS;
-        const double v = (j < nc && k < kv) ? P[(int64_t)k * ld + c0 + j] : 0.0;
-        T[k * (SC_COLS + 1) + j] = v;
-        atomicMax(&emax_s[j], (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffull));
+    {   // lane j of warp w reads rows w, w + 8, ... of column c0 + j (a warp: 32
+        // consecutive doubles of one row), eight loads in flight; the largest
+        // exponent is kept in a register and merged once per thread
+        const int j = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        int em = 1;
+        for (int k0 = w; k0 < K; k0 += 8 * nw) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * nw;
+                v[u] = (j < nc && k < kv) ? P[(int64_t)k * ld + c0 + j] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * nw;
+                if (k < K) {
+                    T[k * (SC_COLS + 1) + j] = v[u];
+                    const int e = (int)(((unsigned long long)__double_as_longlong(v[u]) >> 52) & 0x7ffull);
+                    em = e > em ? e : em;
+                }
+            }
+        }
+        atomicMax(&emax_s[j], em);
     }
     __syncthreads();
     if (threadIdx.x < nc) ex[row0 + c0 + threadIdx.x] = emax_s[threadIdx.x] - 1022;
-    for (int e = threadIdx.x; e < nc * K; e += blockDim.x) {
-        const int j = e / K, k = e % K;
-        uint16_t d[EMU_SLICES];
+    // two consecutive k per thread: each digit pair leaves in one 32-bit store
+    const int kh = K >> 1;
+    for (int e = threadIdx.x; e < nc * kh; e += blockDim.x) {
+        const int j = e / kh, k = 2 * (e % kh);
+        uint16_t d0[EMU_SLICES], d1[EMU_SLICES];
         slice_digits((unsigned long long)__double_as_longlong(T[k * (SC_COLS + 1) + j]),
-                     emax_s[j], d);
+                     emax_s[j], d0);
+        slice_digits((unsigned long long)__double_as_longlong(T[(k + 1) * (SC_COLS + 1) + j]),
+                     emax_s[j], d1);
 #pragma unroll
-        for (int p = 0; p < ES; ++p) S[((int64_t)p * Mtot + row0 + c0 + j) * K + k] = d[p];
+        for (int p = 0; p < ES; ++p)
+            *(uint32_t*)(S + ((int64_t)p * Mtot + row0 + c0 + j) * K + k) =
+                (uint32_t)d0[p] | ((uint32_t)d1[p] << 16);
     }
 }
 
