@@ -109,7 +109,7 @@ size_t pd_part_bytes(int64_t nb) {
 }
 
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, pdpart, eslice, eex, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, l32, pdpart, eslice, eex, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
@@ -131,6 +131,7 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     w.lq = off; off = align_up(off + (mixed ? sizeof(uint16_t) * (size_t)n * (size_t)nb : 0));
     w.sig = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)w.nt : 0));
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
+    w.l32 = off; off = align_up(off + (mixed ? sizeof(float) * (size_t)nb * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
     w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)emu_rows(n, nb) : 0));
@@ -341,8 +342,10 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
         } else {
             TrsmSeg segs[2] = {{A + T0 * lda + K0, lda, m},
                                {CS + ((k + 1) * nc) * n + K0, n, (nt - k - 1) * nc}};
+            float* l32 = mixed ? (float*)(base + w.l32) : nullptr;
+            if (mixed) ABFT_CUDA_TRY(launch_l_to_f32(Akk, lda, kb, l32, s));
             ABFT_CUDA_TRY(launch_trsm_rlt(Akk, lda, kb, segs, check ? 2 : 1, nullptr, nullptr, st,
-                                          s, mixed));
+                                          s, mixed, false, l32));
         }
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)

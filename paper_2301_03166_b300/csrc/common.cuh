@@ -171,9 +171,12 @@ struct TrsmSeg {
 };
 cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                              int nseg, const DevStatus* st, cudaStream_t s, bool f32 = false);
+// lf (FP32 X L^T = B only): L rounded to FP32 beforehand by launch_l_to_f32.
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s, bool f32 = false, bool nt = false);
+                            cudaStream_t s, bool f32 = false, bool nt = false,
+                            const float* lf = nullptr);
+cudaError_t launch_l_to_f32(const double* L, int64_t ldl, int64_t nb, float* Lf, cudaStream_t s);
 cudaError_t launch_chol_pd_check(const double* L, int64_t ldl, int64_t nb, const double* cc,
                                  int64_t K0, int step, double* v, int mode, DevStatus* st,
                                  cudaStream_t s);

@@ -8,7 +8,10 @@
 // by the diagonal, never a reciprocal, so integer inputs stay exact.
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "fp_bits.cuh"
 
 namespace abft {
 
@@ -74,7 +77,17 @@ struct TrsmArgs {
     const double* v;
     double* x;
     const DevStatus* st;
+    const float* Lf;    // FP32 solves: L rounded to FP32 once (nb x nb, ld nb), or null
 };
+
+// The lower triangle of L rounded to FP32 (ld nb), once per panel solve
+// instead of once per CTA (an FP64 -> FP32 conversion runs on the FP64 pipe).
+__global__ void k_l_to_f32(const double* L, int64_t ldl, int nb, float* Lf) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * nb) return;
+    const int i = (int)(e / nb), j = (int)(e % nb);
+    Lf[e] = j <= i ? (float)L[(int64_t)i * ldl + j] : 0.f;
+}
 
 // Solve X L^T = B (NT = false) or X L = B (NT = true) for RB rows at a time
 // (in place), L lower nb x nb.  Columns are processed in chunks of 32, left to
@@ -124,9 +137,13 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
             for (int e = t; e < CW * CW; e += TT) {
                 int q = e / CW, pp = e % CW;
                 T v = 0;
-                if (q < w && p0 + pp < pend)
-                    v = NT ? (T)a.L[(int64_t)(p0 + pp) * a.ldl + c0 + q]
-                           : (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp];
+                if (q < w && p0 + pp < pend) {
+                    if (std::is_same<T, float>::value && !NT && a.Lf)
+                        v = (T)a.Lf[(c0 + q) * nb + p0 + pp];
+                    else
+                        v = NT ? (T)a.L[(int64_t)(p0 + pp) * a.ldl + c0 + q]
+                               : (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp];
+                }
                 Ls[q * (CW + 1) + pp] = v;
             }
             __syncthreads();
@@ -147,7 +164,10 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
             int q = e / CW, pp = e % CW;
             T v = 0;
             if (q < w && pp < w) {
-                if (!NT && pp <= q) v = (T)a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp];
+                if (!NT && pp <= q)
+                    v = (std::is_same<T, float>::value && a.Lf)
+                            ? (T)a.Lf[(c0 + q) * nb + c0 + pp]
+                            : (T)a.L[(int64_t)(c0 + q) * a.ldl + c0 + pp];
                 if (NT && pp >= q) v = (T)a.L[(int64_t)(c0 + pp) * a.ldl + c0 + q];
             }
             Ls[q * (CW + 1) + pp] = v;
@@ -155,7 +175,20 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
         __syncthreads();
         if (t < RB) {
             T* xr = X + t * ldx + c0;
-            if (!NT) {
+            if (std::is_same<T, float>::value && !NT && w == CW) {
+                // FP32, a full chunk: the row's 32 unknowns in registers (fully
+                // unrolled; the same terms, order and division as the loop below)
+                T xv[CW];
+#pragma unroll
+                for (int jj = 0; jj < CW; ++jj) {
+                    T v = xr[jj];
+#pragma unroll
+                    for (int p = 0; p < jj; ++p) v -= xv[p] * Ls[jj * (CW + 1) + p];
+                    xv[jj] = v / Ls[jj * (CW + 1) + jj];
+                }
+#pragma unroll
+                for (int jj = 0; jj < CW; ++jj) xr[jj] = xv[jj];
+            } else if (!NT) {
                 for (int jj = 0; jj < w; ++jj) {
                     T v = xr[jj];
                     for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
@@ -173,7 +206,11 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     }
     for (int e = t; e < nr * nb; e += TT) {
         int r = e / nb, p = e % nb;
-        g.B[(r0 + r) * g.ldb + p] = (double)X[r * ldx + p];
+        // FP32 results widen with integer operations (off the FP64 pipe)
+        if (std::is_same<T, float>::value)
+            g.B[(r0 + r) * g.ldb + p] = f32_to_f64_exact((float)X[r * ldx + p]);
+        else
+            g.B[(r0 + r) * g.ldb + p] = (double)X[r * ldx + p];
     }
 }
 
@@ -300,11 +337,21 @@ cudaError_t launch_potf2_small(double* A, int64_t lda, int64_t nb, int64_t info_
     return cudaGetLastError();
 }
 
+cudaError_t launch_l_to_f32(const double* L, int64_t ldl, int64_t nb, float* Lf,
+                            cudaStream_t s) {
+    const int64_t tot = nb * nb;
+    if (tot <= 0) return cudaSuccess;
+    k_l_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L, ldl, (int)nb, Lf);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
-                            cudaStream_t s, bool f32, bool nt) {
+                            cudaStream_t s, bool f32, bool nt, const float* lf) {
     TrsmArgs a{};
     a.L = L;
+    a.Lf = (f32 && !nt) ? lf : nullptr;
     a.ldl = ldl;
     a.nb = (int)nb;
     a.nseg = 0;
