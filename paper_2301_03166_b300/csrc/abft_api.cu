@@ -109,7 +109,7 @@ size_t pd_part_bytes(int64_t nb) {
 }
 
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, l32, pdpart, eslice, eex, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, tq32, l32, pdpart, eslice, eex, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
@@ -131,6 +131,7 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     w.lq = off; off = align_up(off + (mixed ? sizeof(uint16_t) * (size_t)n * (size_t)nb : 0));
     w.sig = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)w.nt : 0));
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
+    w.tq32 = off; off = align_up(off + (mixed ? sizeof(float) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.l32 = off; off = align_up(off + (mixed ? sizeof(float) * (size_t)nb * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
@@ -260,6 +261,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     uint16_t* Lq = (uint16_t*)(base + w.lq);
     double* sig = (double*)(base + w.sig);
     double* tq = (double*)(base + w.tq);
+    float* tq32 = (float*)(base + w.tq32);
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
     double* Cr = (double*)(base + w.cr);
@@ -383,7 +385,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             timing_mark(PH_TMU, 1, s);
             const int64_t ncq = nc > 0 ? nc : 1;
             ABFT_CUDA_TRY(launch_quant_panel(A + K0, lda, T0, n, kb, g, k + 1, nt, bf16, Lq, sig, tq,
-                                             ncq * kb, check ? 1 : 0, s));
+                                             ncq * kb, check ? 1 : 0, s, tq32));
             timing_mark(PH_TMU, 0, s);
         }
         auto tmu = [&](int part, cudaStream_t ss) -> int {
@@ -431,7 +433,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                 if (check) {
                     BorderSegHost bs[2] = {};
                     // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
-                    bs[0].A = tq + ((k + 1) * ncq) * kb; bs[0].a_half = 0; bs[0].lda = kb;
+                    bs[0].A = tq32 + ((k + 1) * ncq) * kb; bs[0].a_half = 2; bs[0].lda = kb;
                     bs[0].B = Lq + c0 * kb; bs[0].b_half = 1; bs[0].ldb = kb;
                     bs[0].C = CS + ((k + 1) * nc) * n + T0 + c0; bs[0].ldc = n;
                     bs[0].M = (nt - k - 1) * nc; bs[0].N = c1 - c0; bs[0].K = kb;
@@ -439,7 +441,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                     bs[0].c_off = T0 + c0; bs[0].c_div = g; bs[0].c_base = 0;
                     // row-sum columns: r_I -= sigma_I sigma_J (Lq_I t_J^T)
                     bs[1].A = Lq; bs[1].a_half = 1; bs[1].lda = kb;
-                    bs[1].B = tq + (J0 * ncq) * kb; bs[1].b_half = 0; bs[1].ldb = ncq * kb;
+                    bs[1].B = tq32 + (J0 * ncq) * kb; bs[1].b_half = 2; bs[1].ldb = ncq * kb;
                     bs[1].C = Cr + T0 * nt + J0; bs[1].ldc = nt;
                     bs[1].M = m; bs[1].N = J1 - J0; bs[1].K = kb;
                     bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;

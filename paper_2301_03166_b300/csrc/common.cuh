@@ -225,7 +225,7 @@ cudaError_t launch_qr_tau(const double* A, int64_t lda, int64_t n, int64_t g, do
 // Mixed-precision TMU kernels (k_mixed.cu).
 struct BorderSegHost {
     const void* A;
-    int a_half;          // 1: 16-bit quantized operand, 0: FP64
+    int a_half;          // 1: 16-bit quantized operand, 0: FP64, 2: FP32
     int64_t lda;
     const void* B;
     int b_half;
@@ -238,7 +238,7 @@ struct BorderSegHost {
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
                                int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
                                double* sig, double* tsum, int64_t tstride, int weighted,
-                               cudaStream_t s);
+                               cudaStream_t s, float* tsum32 = nullptr);
 cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
                              int64_t ldc, int64_t g, int64_t off, const double* sig,
                              const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s,

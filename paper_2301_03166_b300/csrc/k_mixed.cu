@@ -295,7 +295,8 @@ template <bool BF16>
 __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     k_quant_panel(const double* __restrict__ P, int64_t lda, int64_t T0, int64_t n, int kb,
                   int64_t g, int64_t I0, uint16_t* __restrict__ Lq, double* __restrict__ sig,
-                  double* __restrict__ tsum, int64_t tstride, int weighted) {
+                  double* __restrict__ tsum, int64_t tstride, int weighted,
+                  float* __restrict__ tsum32) {
     extern __shared__ double qpart[];     // rank 0: [QCL][2][kb] slab column sums
     __shared__ double red[8];
     __shared__ double cmax[QCL];          // rank 0: slab maxima
@@ -376,6 +377,10 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
         }
         tsum[I * tstride + p] = s;
         if (weighted) tsum[I * tstride + kb + p] = sw;
+        if (tsum32) {   // the FP32 operand of the border products, rounded once here
+            tsum32[I * tstride + p] = (float)s;
+            if (weighted) tsum32[I * tstride + kb + p] = (float)sw;
+        }
     }
 }
 
@@ -384,7 +389,7 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
 // 16-bit (the quantized panel), B likewise; sr / sc are tile scales.
 struct BorderSeg {
     const void* A;      // rows of K
-    int a_half;         // 1: A is 16-bit (BF16 / FP16 per `bf16`), 0: FP64
+    int a_half;         // 1: A is 16-bit (BF16 / FP16 per `bf16`), 0: FP64, 2: FP32
     int64_t lda;
     const void* B;
     int b_half;
@@ -405,6 +410,7 @@ struct BorderArgs {
 };
 
 __device__ __forceinline__ float ld_op(const void* p, int half, int bf16, int64_t idx) {
+    if (half == 2) return ((const float*)p)[idx];
     if (!half) return (float)((const double*)p)[idx];
     uint16_t b = ((const uint16_t*)p)[idx];
     return bf16 ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
@@ -421,15 +427,26 @@ __global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const int lr = t >> 2, lk = (t & 3) * 4;
     float acc[4][4] = {};
+    // the next K chunk's operands are loaded into registers while the current
+    // chunk is multiplied from shared memory
+    float pa[4], pb[4];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + lk + u, i = i0 + lr, j = j0 + lr;
+            pa[u] = (i < g.M && k < g.K) ? ld_op(g.A, g.a_half, a.bf16, i * g.lda + k) : 0.f;
+            pb[u] = (j < g.N && k < g.K) ? ld_op(g.B, g.b_half, a.bf16, j * g.ldb + k) : 0.f;
+        }
+    };
+    fetch(0);
     for (int64_t k0 = 0; k0 < g.K; k0 += 16) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            int64_t k = k0 + lk + u;
-            int64_t i = i0 + lr, j = j0 + lr;
-            As[lk + u][lr] = (i < g.M && k < g.K) ? ld_op(g.A, g.a_half, a.bf16, i * g.lda + k) : 0.f;
-            Bs[lk + u][lr] = (j < g.N && k < g.K) ? ld_op(g.B, g.b_half, a.bf16, j * g.ldb + k) : 0.f;
+            As[lk + u][lr] = pa[u];
+            Bs[lk + u][lr] = pb[u];
         }
         __syncthreads();
+        if (k0 + 16 < g.K) fetch(k0 + 16);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             float av[4], bv[4];
@@ -478,7 +495,7 @@ cudaError_t get_encoder() {
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
                                int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
                                double* sig, double* tsum, int64_t tstride, int weighted,
-                               cudaStream_t s) {
+                               cudaStream_t s, float* tsum32) {
     if (I1 <= I0) return cudaSuccess;
     if (kb > 512) return cudaErrorInvalidValue;
     static bool attr = false;
@@ -496,10 +513,10 @@ cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t
     const unsigned grid = (unsigned)((I1 - I0) * QCL);
     if (bf16)
         k_quant_panel<true><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
-                                                    tstride, weighted);
+                                                    tstride, weighted, tsum32);
     else
         k_quant_panel<false><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
-                                                     tstride, weighted);
+                                                     tstride, weighted, tsum32);
     note_launch();
     return cudaGetLastError();
 }
