@@ -448,6 +448,9 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
  * the memory their keys refer to, if the same addresses may be reused). */
 int abft_batched_graph_reset(void);
 
+/* Size of the built-in device scratch array used by abft_potrf_noalloc. */
+#define ABFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)   /* 16 MiB per GPU */
+
 /*
  * abft_potrf_noalloc -- abft_potrf for callers that cannot allocate device
  * memory.  The paper has no counterpart: it exists for host programs whose
@@ -455,20 +458,23 @@ int abft_batched_graph_reset(void);
  * process's device footprint) and therefore can neither call cudaMalloc nor
  * pass a workspace.  Arguments and results are those of abft_potrf without
  * ws / ws_bytes; A is still the caller's.  The workspace is a built-in device
- * array of abft_noalloc_capacity() bytes (16 MiB), present on every GPU where
+ * array of ABFT_NOALLOC_SCRATCH_BYTES (16 MiB), present on every GPU where
  * the library's device code is loaded and kept there until the process
  * exits; a problem whose abft_potrf workspace would exceed it is rejected with
- * ABFT_ERR_TOO_LARGE (for example, FULL mode fits n = 4096 with nb <= 256).
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call reuses the same array, so calls whose GPU work overlaps (on different
- * streams, or from different threads) race; serialize them.  The function
- * itself performs no device allocation.
+ * ABFT_ERR_TOO_LARGE before anything is launched (for example, FULL mode fits
+ * n = 4096 with nb <= 256).  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Every call reuses the same array and it keeps the previous
+ * call's contents (the status block at its start is cleared by each call,
+ * everything else is written before it is read), so calls whose GPU work
+ * overlaps (on different streams, or from different threads) race; serialize
+ * them.  The call makes no cudaMalloc, cudaFree or other device-memory
+ * allocation; like abft_potrf, a thread's first factorization on a device
+ * creates the look-ahead's side stream and its two events once.
  */
 int abft_potrf_noalloc(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                        const abft_fault* faults, int32_t nfaults, double tau_scale,
                        abft_report* rep, void* stream);
-size_t abft_noalloc_capacity(void);
 
 /*
  * abft_set_lookahead(on): look-ahead of the blocked Cholesky (Sec. 2.1, the

@@ -18,6 +18,7 @@ NONE, SINGLE, FULL = 0, 1, 2
 F_MEMORY, F_COMPUTE, F_ROW1D, F_COL1D, F_PANEL = 0, 1, 2, 3, 4
 E_0D, E_ROW, E_COL, E_UNCORR, E_CKSUM, E_PD = 0, 1, 2, 3, 4, 5
 ERR_UNCORRECTABLE, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_TOO_LARGE = -1000, -1001, -1002, -1003, -1004
+NOALLOC_SCRATCH_BYTES = 16 << 20   # ABFT_NOALLOC_SCRATCH_BYTES: abft_potrf_noalloc's built-in scratch
 MAX_LOC = 64
 
 
@@ -116,7 +117,6 @@ def lib():
         L.abft_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         L.abft_timing_read.restype = ctypes.c_int
         L.abft_launch_count.restype = _i64
-        L.abft_noalloc_capacity.restype = ctypes.c_size_t
         L.abft_version.restype = ctypes.c_char_p
         L.abft_strerror.restype = ctypes.c_char_p
         L.abft_strerror.argtypes = [_i32]

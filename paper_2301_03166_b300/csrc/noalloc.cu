@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr size_t kScratchBytes = ABFT_NOALLOC_SCRATCH_BYTES;   // 16 MiB per device
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -45,8 +45,6 @@ int scratch_address(void** out) {
 }  // namespace
 
 extern "C" {
-
-size_t abft_noalloc_capacity(void) { return kScratchBytes; }
 
 int abft_potrf_noalloc(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                        const abft_fault* faults, int32_t nfaults, double tau_scale,
