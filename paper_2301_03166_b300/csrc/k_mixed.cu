@@ -234,38 +234,44 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                 // a 128 x 128 tile lies in one g x g block (g is a multiple of 128 and
                 // the trailing matrix starts on a block boundary): one scale per tile
                 const double sc = a.sig[(i0 + a.off) / a.g] * a.sig[(j0 + a.off) / a.g];
-                // FP64 read-modify-write of the tile, 4 rows x 4 column chunks in
-                // flight; C - sc * acc is one FMA on the FP64 pipe per element
-                for (int rb = ew; rb < TM; rb += EPI_WARPS * 4) {
-                    double cv[4][4];
-                    double* ptr[4][4];
-                    int rrv[4];
+                // FP64 read-modify-write of the tile: warp ew takes rows
+                // ew + 32 g + 8 u (groups g < 4, u < 4) x 128 columns; the next
+                // group's 16 loads are issued before this group's FMAs and
+                // stores (32 loads in flight per thread); C - sc * acc is one
+                // FMA on the FP64 pipe per element
+                constexpr int NG = TM / (EPI_WARPS * 4);
+                double cv[2][4][TN / 32];
+                auto load_group = [&](int gq, double (&c)[4][TN / 32]) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int rr = rb + u * EPI_WARPS;
-                        rrv[u] = rr;
-                        const int64_t i = i0 + rr;
-                        const bool rowok = rr < TM && i < a.M;
+                        const int64_t i = i0 + ew + 32 * gq + 8 * u;
 #pragma unroll
                         for (int t4 = 0; t4 < TN / 32; ++t4) {
                             const int64_t j = j0 + lane + 32 * t4;
-                            const bool okj = rowok && j < a.M;
-                            ptr[u][t4] = okj ? a.C + i * a.ldc + j : nullptr;
-                            cv[u][t4] = okj ? *ptr[u][t4] : 0.0;
+                            c[u][t4] = (i < a.M && j < a.M) ? a.C[i * a.ldc + j] : 0.0;
                         }
                     }
+                };
+                load_group(0, cv[0]);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                for (int gq = 0; gq < NG; ++gq) {
+                    if (gq + 1 < NG) load_group(gq + 1, cv[(gq + 1) & 1]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = ew + 32 * gq + 8 * u;
+                        const int64_t i = i0 + rr;
+                        if (i >= a.M) continue;
 #pragma unroll
                         for (int t4 = 0; t4 < TN / 32; ++t4) {
-                            if (ptr[u][t4] == nullptr) continue;
-                            const double x = f32_to_f64_exact(stg[rrv[u] * STG_LD + lane + 32 * t4]);
-                            double v = fma(-sc, x, cv[u][t4]);
-                            const int64_t i = i0 + rrv[u], j = j0 + lane + 32 * t4;
+                            const int64_t j = j0 + lane + 32 * t4;
+                            if (j >= a.M) continue;
+                            const double x = f32_to_f64_exact(stg[rr * STG_LD + lane + 32 * t4]);
+                            double v = fma(-sc, x, cv[gq & 1][u][t4]);
                             for (int f = 0; f < a.ncf; ++f)
                                 if (a.cf[f].row == i && a.cf[f].col == j) v += a.cf[f].delta;
-                            *ptr[u][t4] = v;
+                            a.C[i * a.ldc + j] = v;
                         }
+                    }
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
