@@ -283,6 +283,17 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     timing_mark(PH_OTHER, 0, s);
     enum { PART_ALL = 0, PART_NEXT = 1, PART_REST = 2 };
     bool pd_ahead = false;   // PD of this step already run by the previous step's look-ahead
+    // The previous step's rest of the update (side stream) writes only block
+    // columns >= k + 1 of this step's trailing matrix (and their checksums), so
+    // this step's PD and panel solve may run beside it; the caller's stream
+    // joins it before the first operation that touches what it writes or reads
+    // (the panel's slices or quantized copy, or the trailing update).
+    bool rest_pending = false;
+    auto join_rest = [&]() -> cudaError_t {
+        if (!rest_pending) return cudaSuccess;
+        rest_pending = false;
+        return cudaStreamWaitEvent(s, la->rest_done, 0);
+    };
     for (int64_t k = 0; k < N; ++k) {
         const int64_t K0 = k * g, kb = std::min(g, n - K0), T0 = K0 + kb, m = n - T0;
         double* Akk = A + K0 * lda + K0;
@@ -306,7 +317,12 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             timing_mark(PH_PD, 0, s);
         }
         pd_ahead = false;
-        if (m <= 0) break;
+        if (m <= 0) {
+            ABFT_CUDA_TRY(join_rest());
+            break;
+        }
+        // the emulated panel solve reuses the slice tensor the rest still reads
+        if (emu) ABFT_CUDA_TRY(join_rest());
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
         timing_mark(PH_PU, 1, s);
         if (emu && kb % 64 == 0 && kb >= 128) {
@@ -359,6 +375,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ABFT_CUDA_TRY(launch_verify(ts, MODE_SINGLE, (int)k, st, s));
         }
         timing_mark(PH_PU, 0, s);
+        ABFT_CUDA_TRY(join_rest());
 
         // TMU of part p: PART_ALL the lower block triangle of the trailing
         // matrix, PART_NEXT its first block column (w columns), PART_REST the
@@ -523,7 +540,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             rc = tmu(PART_REST, la->side);
             if (rc != ABFT_OK) return rc;
             ABFT_CUDA_TRY(cudaEventRecord(la->rest_done, la->side));
-            ABFT_CUDA_TRY(cudaStreamWaitEvent(s, la->rest_done, 0));
+            rest_pending = true;
             pd_ahead = true;
         }
     }
