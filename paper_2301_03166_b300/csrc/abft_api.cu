@@ -109,7 +109,7 @@ size_t pd_part_bytes(int64_t nb) {
 }
 
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, tq32, l32, pdpart, eslice, eex, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, tq32, l32, pdpart, eslice, eex, pslice, pex, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
@@ -136,6 +136,10 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
     w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)emu_rows(n, nb) : 0));
+    // the blocked panel solve's own slices (it runs beside the previous step's
+    // update, which still reads eslice)
+    w.pslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
+    w.pex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)emu_rows(n, nb) : 0));
     w.total = off;
     return w;
 }
@@ -321,8 +325,6 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ABFT_CUDA_TRY(join_rest());
             break;
         }
-        // the emulated panel solve reuses the slice tensor the rest still reads
-        if (emu) ABFT_CUDA_TRY(join_rest());
         // PU: panel rows and the carried checksum rows through X L_kk^T = B
         timing_mark(PH_PU, 1, s);
         if (emu && kb % 64 == 0 && kb >= 128) {
@@ -331,8 +333,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             // run FP64-accurate from BF16 slices on the tensor cores (the panel rows, the checksum rows and the
             // rows L_c,<c re-sliced with one scale per row over the columns < c)
             constexpr int64_t CW = 64;
-            uint16_t* Sl = (uint16_t*)(base + w.eslice);
-            int* ex = (int*)(base + w.eex);
+            uint16_t* Sl = (uint16_t*)(base + w.pslice);
+            int* ex = (int*)(base + w.pex);
             const int64_t mcp = check ? (nt - k - 1) * nc : 0, mrows = m + mcp;
             double* Xp = A + T0 * lda + K0;
             double* Xc = CS + ((k + 1) * nc) * n + K0;
