@@ -120,18 +120,30 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
             lcol[i - r0] = l;
         }
         __syncthreads();
-        // one column per thread, eight rows at a time: loads coalesced along the
-        // rows and eight of them in flight per thread
-        for (int c = j + 1 + threadIdx.x; c < kb; c += PT) {
+        // thread t: column j + 1 + t % w, row chunk t / w (with fewer columns
+        // than threads the rows are split so that every thread works and the
+        // dependent load rounds per thread shrink), eight rows at a time:
+        // loads coalesced along the rows, eight in flight per thread
+        const int w = kb - j - 1;
+        const int64_t nrow = r1 - ibeg;
+        int rsp = w > 0 ? PT / w : 1;
+        if (rsp < 1) rsp = 1;
+        if ((int64_t)rsp > (nrow + 7) / 8) rsp = (int)((nrow + 7) / 8);
+        if (rsp < 1) rsp = 1;
+        const int64_t rch = (nrow + rsp - 1) / rsp;
+        for (int t = threadIdx.x; t < w * rsp; t += PT) {
+            const int c = j + 1 + t % w;
+            const int64_t ia = ibeg + (int64_t)(t / w) * rch;
+            const int64_t ie = ia + rch < r1 ? ia + rch : r1;
             const double uc = urow[c];
-            for (int64_t i = ibeg; i < r1; i += 8) {
+            for (int64_t i = ia; i < ie; i += 8) {
                 double av[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (i + u < r1) av[u] = P[(i + u) * lda + c];
+                    if (i + u < ie) av[u] = P[(i + u) * lda + c];
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (i + u < r1)
+                    if (i + u < ie)
                         P[(i + u) * lda + c] = fma(-lcol[i + u - r0], uc, av[u]);
             }
         }

@@ -146,18 +146,27 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
         __syncthreads();
         const int w = kb - j - 1;
         if (w > 0) {
-            // one column per thread, eight rows at a time (coalesced along the
-            // rows, eight loads in flight)
-            for (int c = j + 1 + threadIdx.x; c < kb && ibeg < r1; c += QT) {
+            // thread t: column j + 1 + t % w, row chunk t / w (rows split when
+            // there are fewer columns than threads), eight rows at a time
+            // (coalesced along the rows, eight loads in flight)
+            const int64_t nrow = r1 - ibeg;
+            int rsp = QT / w;
+            if ((int64_t)rsp > (nrow + 7) / 8) rsp = (int)((nrow + 7) / 8);
+            if (rsp < 1) rsp = 1;
+            const int64_t rch = (nrow + rsp - 1) / rsp;
+            for (int t = threadIdx.x; t < w * rsp && ibeg < r1; t += QT) {
+                const int c = j + 1 + t % w;
+                const int64_t ia = ibeg + (int64_t)(t / w) * rch;
+                const int64_t ie = ia + rch < r1 ? ia + rch : r1;
                 const double wc = wl[c];
-                for (int64_t i = ibeg; i < r1; i += 8) {
+                for (int64_t i = ia; i < ie; i += 8) {
                     double av[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        if (i + u < r1) av[u] = P[(i + u) * lda + c];
+                        if (i + u < ie) av[u] = P[(i + u) * lda + c];
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        if (i + u < r1)
+                        if (i + u < ie)
                             P[(i + u) * lda + c] = fma(-vloc[i + u - r0], wc, av[u]);
                 }
             }
