@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
     __shared__ double red[QT / 32];
     __shared__ double wl[512];
     __shared__ double vloc[QMAXR];
+    __shared__ double dpart[512];   // (row chunk, column) partial dot products
     __shared__ double s_sst;
     const unsigned G = gridDim.x;
     const int64_t R = (m + G - 1) / G;
@@ -94,19 +95,39 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
         }
         ss = block_sum(ss, red);
         if (threadIdx.x == 0) mypart[0] = ss;
-        for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
-            // eight rows of operands loaded ahead, accumulated in row order
-            double d = 0.0;
-            for (int64_t i = ibeg; i < r1; i += 8) {
-                double xv[8], av[8];
+        {
+            // x(2:)^T a_c: thread t takes column j + 1 + t % w over row chunk t / w
+            // (rows split when fewer columns than threads remain), eight rows of
+            // operands loaded ahead and accumulated in row order; the chunks'
+            // partial sums are then added in chunk order
+            const int w = kb - j - 1;
+            const int64_t nrow = r1 - ibeg;
+            int rsp = w > 0 ? QT / w : 1;
+            if ((int64_t)rsp > (nrow + 7) / 8) rsp = (int)((nrow + 7) / 8);
+            if (rsp < 1) rsp = 1;
+            const int64_t rch = (nrow + rsp - 1) / rsp;
+            for (int t = threadIdx.x; t < w * rsp; t += QT) {
+                const int c = j + 1 + t % w;
+                const int64_t ia = ibeg + (int64_t)(t / w) * rch;
+                const int64_t ie = ia + rch < r1 ? ia + rch : r1;
+                double d = 0.0;
+                for (int64_t i = ia; i < ie; i += 8) {
+                    double xv[8], av[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i + u < r1) { xv[u] = P[(i + u) * lda + j]; av[u] = P[(i + u) * lda + c]; }
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < ie) { xv[u] = P[(i + u) * lda + j]; av[u] = P[(i + u) * lda + c]; }
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i + u < r1) d += xv[u] * av[u];
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < ie) d += xv[u] * av[u];
+                }
+                dpart[t] = d;
             }
-            mypart[1 + c] = d;
+            __syncthreads();
+            for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
+                double d = 0.0;
+                for (int q = 0; q < rsp; ++q) d += dpart[q * w + (c - j - 1)];
+                mypart[1 + c] = d;
+            }
         }
         if (!grid_barrier(st, G, nbar)) return;
         // B: every CTA forms beta, tau; warp q of CTA b reduces the dots of
