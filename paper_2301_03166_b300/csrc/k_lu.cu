@@ -291,27 +291,43 @@ __global__ void __launch_bounds__(512) k_lu_pd_check(const double* P, int64_t ld
     __syncthreads();
     for (int c1 = kb; c1 > 0; c1 -= 32) {
         const int c0 = c1 - 32 > 0 ? c1 - 32 : 0;
+        // (the chunk's entries of L are loaded into registers first, so that
+        // the substitution and the update wait for memory once per chunk, not
+        // once per term; the terms and their order are unchanged)
         if (warp == 0) {
             const int p = c0 + lane;
+            double lv[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int j = c0 + u;
+                lv[u] = (j < c1 && p < j) ? P[(int64_t)j * lda + p] : 0.0;
+            }
             double a = (p < c1) ? tz[p] : 0.0, b = (p < c1) ? tw[p] : 0.0;
-            for (int j = c1 - 1; j >= c0; --j) {
-                double zj = __shfl_sync(0xffffffffu, a, j - c0);
-                double wj = __shfl_sync(0xffffffffu, b, j - c0);
+#pragma unroll
+            for (int u = 31; u >= 0; --u) {
+                const int j = c0 + u;
+                if (j >= c1) continue;
+                double zj = __shfl_sync(0xffffffffu, a, u);
+                double wj = __shfl_sync(0xffffffffu, b, u);
                 if (p < j) {
-                    double l = P[(int64_t)j * lda + p];
-                    a -= l * zj;
-                    b -= l * wj;
+                    a -= lv[u] * zj;
+                    b -= lv[u] * wj;
                 }
             }
             if (p < c1) { tz[p] = a; tw[p] = b; }
         }
         __syncthreads();
         for (int p = t; p < c0; p += blockDim.x) {
+            double lv[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+                lv[u] = (c0 + u < c1) ? P[(int64_t)(c0 + u) * lda + p] : 0.0;
             double a = tz[p], b = tw[p];
-            for (int j = c0; j < c1; ++j) {
-                double l = P[(int64_t)j * lda + p];
-                a -= l * tz[j];
-                b -= l * tw[j];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                if (c0 + u >= c1) continue;
+                a -= lv[u] * tz[c0 + u];
+                b -= lv[u] * tw[c0 + u];
             }
             tz[p] = a; tw[p] = b;
         }
