@@ -422,11 +422,20 @@ __global__ void __launch_bounds__(256) k_trsm_llu(TrsmLArgs a) {
             Ls[q * 33 + pp] = (q < w && pp < q) ? a.L[(int64_t)(r0 + q) * a.ldl + r0 + pp] : 0.0;
         }
         __syncthreads();
-        if (t < CB) {
-            for (int jj = 0; jj < w; ++jj) {
-                double v = X[(r0 + jj) * (CB + 1) + t];
-                for (int p = 0; p < jj; ++p) v -= Ls[jj * 33 + p] * X[(r0 + p) * (CB + 1) + t];
-                X[(r0 + jj) * (CB + 1) + t] = v;
+        {
+            // substitution inside the chunk, right-looking over all eight warps:
+            // once row p is final its value updates the rows below it (lane =
+            // column, warp wq owns rows q = wq mod 8); every row receives its
+            // terms in the order p = 0, 1, ..., as in a row-by-row substitution
+            const int lane = t & 31, wq = t >> 5;
+            for (int p = 0; p < w; ++p) {
+                const double xp = X[(r0 + p) * (CB + 1) + lane];
+                for (int q = wq; q < w; q += 8)
+                    if (q > p) {
+                        double* xq = X + (r0 + q) * (CB + 1) + lane;
+                        *xq = fma(-Ls[q * 33 + p], xp, *xq);
+                    }
+                __syncthreads();
             }
         }
         __syncthreads();
