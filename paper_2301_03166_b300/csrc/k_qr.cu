@@ -2,7 +2,9 @@
 // Sec. 3.1.2 checksums).  PD = geqr2 on the (n - K0) x kb panel (LAPACK larfg
 // convention) as one cooperative launch, then the triangular factor T of the
 // block reflector I - V T V^T; the TMU is three FP64 GEMM launches of
-// k_gemm_f64 (W = V^T C, X = T^T W, C -= V X) issued by the host.
+// k_gemm_f64 (W = V^T C, X = T^T W, C -= V X) issued by the host, or, in the
+// FP64-accurate form, the same three products as exact BF16 slice products
+// on the tensor cores (k_emu.cu).
 #include <math.h>
 
 #include "common.cuh"
@@ -26,9 +28,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-// Cooperative geqr2 on the panel P (m x kb, row-major, ld lda).  part is a
-// G x (kb + 1) scratch of per-CTA partial sums, wv a kb scratch for the
-// reflector's row vector w, nrm receives the column norms before the PD.
 // sum_{b<G} p[b * stride] in the order b = 0, 1, ..., with eight loads in
 // flight (the partials live in L2; a load-add chain would pay its latency G times)
 __device__ __forceinline__ double ordered_sum(const double* p, int64_t stride, unsigned G) {
@@ -59,6 +58,17 @@ __device__ __forceinline__ double warp_tree_sum(const double* p, int64_t stride,
     return s;
 }
 
+// Cooperative geqr2 on the panel P (m x kb, row-major, ld lda).  part is a
+// G x (kb + 1) scratch of per-CTA partial sums, wv a kb scratch for the
+// reflector's row vector w, nrm receives the column norms before the PD.
+// Each CTA owns a contiguous block of panel rows.  Per column j: (A) every
+// CTA forms its partial |x(2:)|^2 and x(2:)^T a_c for c > j; grid barrier;
+// (B) every CTA forms beta and tau from the partials (one warp tree, the
+// same bits in every CTA), and the CTAs' warps share the reductions of the
+// dot products into w; grid barrier; (C) every CTA scales its part of v and
+// applies a_c -= tau v w_c to its rows.  The dot products and the update map
+// threads to (column, row chunk) pairs, so that late columns keep every
+// thread busy.
 __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64_t m, int kb,
                                                    double* tau, double* nrm, double* part,
                                                    double* wv, DevStatus* st) {
