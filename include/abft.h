@@ -461,8 +461,8 @@ int abft_batched_graph_reset(void);
  * array of ABFT_NOALLOC_SCRATCH_BYTES (16 MiB), present on every GPU where
  * the library's device code is loaded and kept there until the process
  * exits; a problem whose abft_potrf workspace would exceed it is rejected with
- * ABFT_ERR_TOO_LARGE before anything is launched (for example, FULL mode fits
- * n = 4096 with nb <= 256).  The first call on a device looks up the array's
+ * ABFT_ERR_TOO_LARGE before anything is launched (for example, ABFT_F64 in
+ * FULL mode fits n = 4096 with nb <= 256; the other dtypes need more).  The first call on a device looks up the array's
  * device address (with that device current); make that first call before any
  * stream capture.  Every call reuses the same array and it keeps the previous
  * call's contents (the status block at its start is cleared by each call,
