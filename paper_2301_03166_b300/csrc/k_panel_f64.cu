@@ -251,16 +251,36 @@ __global__ void __launch_bounds__(RW_ROWS) k_trsm_rows(TrsmArgs a) {
     for (int j = t; j < nb; j += RW_ROWS) rinv[j] = (T)1 / (T)a.L[(int64_t)j * a.ldl + j];
     __syncthreads();
     T* xr = X + t * RW_LD;
-    for (int j = 0; j < nb; ++j) {
-        const T* lj = Ls + j * RW_LD;
-        T v0 = xr[j], v1 = 0;
-        int p = 0;
-        for (; p + 1 < j; p += 2) {
-            v0 -= xr[p] * lj[p];
-            v1 -= xr[p + 1] * lj[p + 1];
+    if (nb == RW_MAXNB) {
+        // full width: the row's unknowns in registers (fully unrolled; the same
+        // terms, pairing and order as the loop below), one shared load per term
+        T xv[RW_MAXNB];
+#pragma unroll
+        for (int j = 0; j < RW_MAXNB; ++j) {
+            const T* lj = Ls + j * RW_LD;
+            T v0 = xr[j], v1 = 0;
+#pragma unroll
+            for (int p = 0; p + 1 < j; p += 2) {
+                v0 -= xv[p] * lj[p];
+                v1 -= xv[p + 1] * lj[p + 1];
+            }
+            if (j & 1) v0 -= xv[j - 1] * lj[j - 1];
+            xv[j] = (v0 + v1) * rinv[j];
         }
-        if (p < j) v0 -= xr[p] * lj[p];
-        xr[j] = (v0 + v1) * rinv[j];
+#pragma unroll
+        for (int j = 0; j < RW_MAXNB; ++j) xr[j] = xv[j];
+    } else {
+        for (int j = 0; j < nb; ++j) {
+            const T* lj = Ls + j * RW_LD;
+            T v0 = xr[j], v1 = 0;
+            int p = 0;
+            for (; p + 1 < j; p += 2) {
+                v0 -= xr[p] * lj[p];
+                v1 -= xr[p + 1] * lj[p + 1];
+            }
+            if (p < j) v0 -= xr[p] * lj[p];
+            xr[j] = (v0 + v1) * rinv[j];
+        }
     }
     __syncthreads();
     for (int e = t; e < nr * nb; e += RW_ROWS) {
