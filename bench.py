@@ -86,6 +86,66 @@ def tmu_flops(n, nb):
     return tot
 
 
+# ------------------------------------------------------------- energy
+class BoardEnergy:
+    """NVML's total-energy counter of the board this process runs on, read
+    only (mJ since the driver loaded), for the context figure "board energy
+    per factorization".  NVML is reached through pynvml or, where that module
+    is missing, through the driver's libnvidia-ml by ctypes (the documented C
+    entry points); the board is found by the CUDA device's PCI address, else
+    its UUID.  Reads return None where NVML or the counter is unavailable."""
+
+    def __init__(self, dev):
+        self.h = None
+        self.c = None
+        p = torch.cuda.get_device_properties(dev)
+        bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+        uuid = f"GPU-{p.uuid}".encode()
+        try:
+            import pynvml
+            self.nv = pynvml
+            pynvml.nvmlInit()
+            try:
+                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+            except Exception:
+                self.h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
+            pynvml.nvmlDeviceGetTotalEnergyConsumption(self.h)
+            return
+        except Exception:
+            self.h = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+                if lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(h)) != 0:
+                    return
+            e = ctypes.c_ulonglong()
+            if lib.nvmlDeviceGetTotalEnergyConsumption(h, ctypes.byref(e)) == 0:
+                self.c = (lib, h)
+        except Exception:
+            self.c = None
+
+    def read(self):
+        try:
+            if self.h is not None:
+                return float(self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h))
+            if self.c is not None:
+                e = ctypes.c_ulonglong()
+                if self.c[0].nvmlDeviceGetTotalEnergyConsumption(self.c[1], ctypes.byref(e)) == 0:
+                    return float(e.value)
+        except Exception:
+            pass
+        return None
+
+    @staticmethod
+    def joules(e0, e1, calls):
+        if e0 is None or e1 is None or e1 <= e0 or calls <= 0:
+            return None
+        return (e1 - e0) * 1e-3 / calls
+
+
 # ------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -121,7 +181,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, reasons, watts = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -132,12 +192,17 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                watts.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_mean": statistics.mean(watts) if watts else None}
 
 
 # ------------------------------------------------------------- helpers
@@ -264,12 +329,14 @@ def run_ours(args, ws, rank, local):
     assert rc == 0, f"potrf returned {rc}"
     events_ok = [(e[0], e[1], e[2], e[3]) for e in rep["loc"]] == expected
 
+    energy = BoardEnergy(dev)
     clocks = ClockSampler(local)
     clocks.start()
     abft.timing_enable(True)
     launches0 = abft.launch_count()
     barrier(ws)
     torch.cuda.synchronize(dev)
+    en0 = energy.read()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -277,6 +344,7 @@ def run_ours(args, ws, rank, local):
         rc, rep = step()
     e1.record()
     torch.cuda.synchronize(dev)
+    en1 = energy.read()
     barrier(ws)
     ms = e0.elapsed_time(e1)
     launches = abft.launch_count() - launches0
@@ -285,6 +353,18 @@ def run_ours(args, ws, rank, local):
     clk = clocks.stop()
     ms = max_over_ranks(ms, ws, dev)
     ms_step = ms / args.steps
+    j_fact = BoardEnergy.joules(en0, en1, args.steps)
+    src = ("NVML total-energy counter of this rank's board over the timed region, divided "
+           "by the steps (read only; context)")
+    if j_fact is None and clk.get("power_w_mean"):
+        # no energy counter: the mean of the board power samples taken during
+        # the timed region, times the time per factorization
+        j_fact = clk["power_w_mean"] * ms_step * 1e-3
+        src = ("mean board power (nvidia-smi power.draw, 200 ms samples over the timed "
+               "region) x time per factorization (read only; context)")
+    energy_line = {"board_joules_per_factorization": j_fact,
+                   "board_watts_avg": (j_fact / (ms_step * 1e-3)) if j_fact else None,
+                   "source": src}
     value = ws * chol_flops(n) / (ms_step * 1e-3) / 1e12
 
     # roofline of the dominant kernel (the FP64 trailing update)
@@ -319,10 +399,13 @@ def run_ours(args, ws, rank, local):
         overhead = {"ms_full": ms_step, "ms_none": ms_none,
                     "abft_overhead_pct": 100.0 * (ms_step / ms_none - 1.0)}
 
+    last_joules = [None]   # board energy per call of the last timed() (NVML, context)
+
     def timed(fn, steps, warm):
         for _ in range(warm):
             fn()
         torch.cuda.synchronize(dev)
+        j0 = energy.read()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
@@ -331,6 +414,7 @@ def run_ours(args, ws, rank, local):
             out = fn()
         t1.record()
         torch.cuda.synchronize(dev)
+        last_joules[0] = BoardEnergy.joules(j0, energy.read(), steps)
         return t0.elapsed_time(t1) / steps, out
 
     emulated = None
@@ -390,7 +474,7 @@ def run_ours(args, ws, rank, local):
             abft.potrs(A, Xb, nb, abft.F64)
             return None
         ms_fp64, _ = timed(fp64_solve, 1, 1)
-        mixed = {"fp64_ms_to_solution": ms_fp64}
+        mixed = {"fp64_ms_to_solution": ms_fp64, "fp64_board_joules": last_joules[0]}
         for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
             def mixed_solve():
                 return abft.posv_ir(A0, B, nb, dt, abft.FULL, tol=1e-12, maxit=100, faults=faults,
@@ -400,7 +484,8 @@ def run_ours(args, ws, rank, local):
             mixed[name] = {"ms_to_solution": ms_mix, "speedup_vs_fp64": ms_fp64 / ms_mix,
                            "tflops_equiv": chol_flops(n) / (ms_mix * 1e-3) / 1e12,
                            "ir_iters": rep_m["ir_iters"], "backward_err": rep_m["backward_err"],
-                           "rc": rc_m, "faults_corrected": rep_m["corrected"]}
+                           "rc": rc_m, "faults_corrected": rep_m["corrected"],
+                           "board_joules": last_joules[0]}
         del Lbuf, Xb, B
 
     lookahead = None
@@ -688,6 +773,7 @@ def run_ours(args, ws, rank, local):
             "batched": batched,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
+            "energy": energy_line,
         }), flush=True)
 
 
