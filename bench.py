@@ -98,9 +98,12 @@ class BoardEnergy:
     def __init__(self, dev):
         self.h = None
         self.c = None
-        p = torch.cuda.get_device_properties(dev)
-        bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
-        uuid = f"GPU-{p.uuid}".encode()
+        try:
+            p = torch.cuda.get_device_properties(dev)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            uuid = f"GPU-{p.uuid}".encode()
+        except Exception:
+            return
         try:
             import pynvml
             self.nv = pynvml
