@@ -8,6 +8,14 @@ the working copy is reset from a pristine copy and factored; the report
 (events, counters) is read back.  The matrix (2.1 GB) is larger than L2, so
 no separate L2 flush is needed between steps.
 
+Besides the contract's keys, the line reports the context figures:
+- `energy`: board joules per factorization, from NVML's energy counter
+  (read only);
+- `cpu_lapack`: LAPACK dpotrf on all host cores on the same matrix,
+  without checksums, a stronger CPU baseline than the oracle;
+- sections for the FP64-accurate and 16-bit forms, the look-ahead, LU / QR
+  and the batched factorization.
+
 --impl reference times the CPU oracle (plain C, one core) on a bounded
 sample of the same workload instead (rank 0 only).
 """
