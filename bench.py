@@ -158,6 +158,21 @@ class BoardEnergy:
 
 
 # ------------------------------------------------------------- clocks
+def board_id(dev):
+    """The board behind CUDA device `dev` as nvidia-smi names it: its PCI bus
+    id (nvidia-smi ignores CUDA_VISIBLE_DEVICES, so a CUDA index can name
+    another board), else its UUID, else the CUDA index."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except Exception:
+        pass
+    try:
+        return f"GPU-{torch.cuda.get_device_properties(dev).uuid}"
+    except Exception:
+        return str(dev)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -361,7 +376,7 @@ def run_ours(args, ws, rank, local):
     events_ok = [(e[0], e[1], e[2], e[3]) for e in rep["loc"]] == expected
 
     energy = BoardEnergy(dev)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(board_id(local))
     clocks.start()
     abft.timing_enable(True)
     launches0 = abft.launch_count()

@@ -470,7 +470,8 @@ int abft_batched_graph_reset(void);
  * overlaps (on different streams, or from different threads) race; serialize
  * them.  The call makes no cudaMalloc, cudaFree or other device-memory
  * allocation; like abft_potrf, a thread's first factorization on a device
- * creates the look-ahead's side stream and its two events once.
+ * creates the look-ahead's side stream and its two events once.  Like the
+ * rest of the library it assumes one GPU per process (device index < 16).
  */
 int abft_potrf_noalloc(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, int64_t lda,
                        const abft_fault* faults, int32_t nfaults, double tau_scale,

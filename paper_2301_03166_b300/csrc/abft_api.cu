@@ -1760,15 +1760,21 @@ int abft_tril(int64_t n, double* A, int64_t lda, void* stream) {
 namespace {
 
 // -------------------------------------------------------------- batched
+// A captured graph holds every kernel argument, so the key holds them all:
+// the buffers, the sizes and modes, the threshold scale (as its bit pattern)
+// and the device the graph was instantiated on.
 struct GraphKey {
     const void* items;
     int count, dtype, mode;
+    uint64_t tau_bits;
+    int device;
     const void* status;
     const void* ws;
     void* stream;
     bool operator<(const GraphKey& o) const {
-        return std::tie(items, count, dtype, mode, status, ws, stream) <
-               std::tie(o.items, o.count, o.dtype, o.mode, o.status, o.ws, o.stream);
+        return std::tie(items, count, dtype, mode, tau_bits, device, status, ws, stream) <
+               std::tie(o.items, o.count, o.dtype, o.mode, o.tau_bits, o.device, o.status, o.ws,
+                        o.stream);
     }
 };
 std::mutex g_graph_mu;
@@ -1802,7 +1808,11 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
         ABFT_CUDA_TRY(timing_collect(s));
         return ABFT_OK;
     }
-    GraphKey key{items, count, dtype, mode, status, ws, stream};
+    int device = 0;
+    ABFT_CUDA_TRY(cudaGetDevice(&device));
+    uint64_t tau_bits = 0;
+    std::memcpy(&tau_bits, &tau_scale, sizeof(tau_bits));
+    GraphKey key{items, count, dtype, mode, tau_bits, device, status, ws, stream};
     cudaGraphExec_t exec = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_graph_mu);

@@ -24,7 +24,10 @@ namespace {
 constexpr size_t kScratchBytes = ABFT_NOALLOC_SCRATCH_BYTES;   // 16 MiB per device
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// The library drives one GPU per process (its launchers set per-device kernel
+// attributes once per process, and the look-ahead keeps state for device
+// indices below 16), so the address cache covers the same 16 indices.
+constexpr int kMaxDevices = 16;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 

@@ -104,3 +104,23 @@ def test_batched_config_4096():
         Lo, _, _ = oracle.potrf(mats[i], 64, oracle.FULL)
         assert np.abs(np.tril(batch.matrix(i).cpu().numpy()) - np.tril(Lo)).max() <= 1e-12
     abft.lib().abft_batched_graph_reset()
+
+
+def test_batched_graph_key_holds_tau_scale():
+    """A replayed graph must use the threshold of the call that replays it: the
+    same buffers with a threshold scale large enough to hide the injected
+    fault report nothing, and the original scale finds it again."""
+    batch, mats, faults = make_batch(64, torch.float64, nb=64, fault_every=16)
+    assert faults
+    buf0 = batch.buf.clone()
+    ws = abft.Workspace()
+    abft.potrf_batched(batch, use_graph=True, workspace=ws)
+    torch.cuda.synchronize()
+    assert sum(s["detected"] for s in batch.statuses()) == len(faults)
+    for scale, expect in ((1e30, 0), (1.0, len(faults))):
+        batch.buf.copy_(buf0)
+        batch.status.zero_()
+        abft.potrf_batched(batch, tau_scale=scale, use_graph=True, workspace=ws)
+        torch.cuda.synchronize()
+        assert sum(s["detected"] for s in batch.statuses()) == expect
+    abft.lib().abft_batched_graph_reset()
