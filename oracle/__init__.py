@@ -60,8 +60,22 @@ def lib():
         L.orc_potrf_sched.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_int32), dp, i64,
                                       ctypes.POINTER(_Event), ctypes.c_int32, ctypes.c_double,
                                       ctypes.POINTER(_Report)]
+        u16p = ctypes.POINTER(ctypes.c_uint16)
+        L.orc_round16.argtypes = [ctypes.c_double, ctypes.c_int, u16p]
+        L.orc_round16.restype = ctypes.c_double
+        L.orc_tile_sigma.argtypes = [ctypes.c_double, ctypes.c_int]
+        L.orc_tile_sigma.restype = ctypes.c_double
+        L.orc_mixed_coef.argtypes = [ctypes.c_double, i64]
+        L.orc_mixed_coef.restype = ctypes.c_double
+        L.orc_quantize.argtypes = [i64, i64, dp, i64, ctypes.c_int, dp, u16p, dp]
+        L.orc_quantize.restype = None
+        L.orc_syrk_mixed.argtypes = [i64, i64, i64, ctypes.c_int, dp, i64, dp, i64, u16p, dp]
+        L.orc_syrk_mixed.restype = None
+        L.orc_potrf_mixed.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, dp,
+                                      i64, ctypes.POINTER(_Event), ctypes.c_int32,
+                                      ctypes.c_double, ctypes.POINTER(_Report)]
         for f in ("orc_potf2", "orc_getf2", "orc_geqr2", "orc_potrf", "orc_getrf",
-                  "orc_geqrf", "orc_potrs", "orc_potrf_sched"):
+                  "orc_geqrf", "orc_potrs", "orc_potrf_sched", "orc_potrf_mixed"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -147,6 +161,70 @@ def potrf_sched(A, nb, modes, faults=(), tau_scale=1.0):
     rep = _Report()
     info = lib().orc_potrf_sched(n, nb, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(A),
                                  max(1, A.shape[1]), fa, nf, tau_scale, ctypes.byref(rep))
+    return A, info, _report(rep)
+
+
+# ----------------------------------------- mixed precision (16-bit TMU)
+BF16, FP16 = 1, 0
+
+
+def round16(x, bf16=True):
+    """x rounded to BF16 or FP16 (nearest, ties to even) from the format
+    definitions; returns (value, 16-bit encoding)."""
+    b = ctypes.c_uint16(0)
+    v = lib().orc_round16(float(x), 1 if bf16 else 0, ctypes.byref(b))
+    return v, b.value
+
+
+def tile_sigma(m, bf16=True):
+    """Per-tile scale 2^(ceil(log2 m) - e_t) of a tile with maximum |x| = m."""
+    return lib().orc_tile_sigma(float(m), 1 if bf16 else 0)
+
+
+def mixed_coef(tau_scale, g):
+    """tau_scale * 4 * gamma_g(2^-24): the factor of the abs-checksum thresholds."""
+    return lib().orc_mixed_coef(float(tau_scale), int(g))
+
+
+def quantize(P, bf16=True):
+    """One tile quantized: (sigma, 16-bit encodings, their values)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    r, c = P.shape
+    bits = np.zeros((r, c), dtype=np.uint16)
+    q = np.zeros((r, c))
+    sig = ctypes.c_double(0.0)
+    lib().orc_quantize(r, c, _dp(P), c, 1 if bf16 else 0, ctypes.byref(sig),
+                       bits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), _dp(q))
+    return sig.value, bits, q
+
+
+def syrk_mixed(P, C, g, bf16=True):
+    """The mixed trailing update alone: returns (C - sigma_I sigma_J Lq_I Lq_J^T
+    on the lower block triangle, the encodings of Lq, sigma per tile-row)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    C = np.array(C, dtype=np.float64, order="C", copy=True)
+    m, k = P.shape
+    bits = np.zeros((m, k), dtype=np.uint16)
+    sig = np.zeros(-(-m // g))
+    lib().orc_syrk_mixed(m, k, g, 1 if bf16 else 0, _dp(P), k, _dp(C), m,
+                         bits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), _dp(sig))
+    return C, bits, sig
+
+
+def potrf_mixed(A, nb, mode=FULL, bf16=True, faults=(), tau_scale=1.0, modes=None):
+    """Blocked ABFT Cholesky in the mixed form (16-bit quantized TMU operands,
+    FP32 panel solve, abs-checksum thresholds).  Returns (A', info, report);
+    report["tau"] is the largest threshold applied to a trailing tile."""
+    A = _mat(A)
+    n = A.shape[0]
+    N = max(1, -(-n // nb))
+    m = np.full(N, mode, dtype=np.int32) if modes is None else \
+        np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
+    fa, nf = _faults(faults)
+    rep = _Report()
+    info = lib().orc_potrf_mixed(n, nb, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 1 if bf16 else 0, _dp(A), max(1, A.shape[1]), fa, nf, tau_scale,
+                                 ctypes.byref(rep))
     return A, info, _report(rep)
 
 

@@ -157,6 +157,7 @@ typedef struct {
     int64_t g;
     double tau;
     orc_report* rep;
+    double tau_used;   /* largest per-component threshold applied (mixed form) */
 } vctx;
 
 static void add_event(vctx* c, int kind, int64_t row, int64_t col, double d) {
@@ -182,11 +183,13 @@ static void add_event(vctx* c, int kind, int64_t row, int64_t col, double d) {
  * Single mode: every flagged column j is located at row
  * i = round(d^w_j / d^c_j) - 1 (accepted when within 0.05 of an integer and
  * inside the tile) and corrected by d^c_j; otherwise uncorrectable. */
-static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
-                        int64_t nr, int64_t nc, double* cc, double* cw,
-                        double* cr, int64_t crs) {
+static void verify_tile_t(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
+                          int64_t nr, int64_t nc, double* cc, double* cw,
+                          double* cr, int64_t crs, const double* tc, const double* tr) {
     if (c->mode == M_NONE || nr <= 0 || nc <= 0) return;
     double tau = c->tau;
+#define TC(j) (tc ? tc[j] : tau)
+#define TR(i) (tr ? tr[(i) * crs] : tau)
     double* dc = dalloc(nc);
     double* dw = dalloc(nc);
     double* dr = dalloc(nr);
@@ -206,21 +209,25 @@ static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
             dr[i] = s - cr[i * crs];
         }
     int64_t nfc = 0, nfr = 0, fc = -1, fr = -1;
-    double dmax = 0.0;
+    double dmax = 0.0, rmax = 0.0;   /* largest |d|; largest |d| / threshold */
     for (int64_t j = 0; j < nc; ++j) {
         double a = fabs(dc[j]);
-        if (!(a <= tau)) { ++nfc; if (fc < 0) fc = j; }
+        if (!(a <= TC(j))) { ++nfc; if (fc < 0) fc = j; }
         if (a > dmax) dmax = a;
+        if (tc && tc[j] > 0.0 && a / tc[j] > rmax) rmax = a / tc[j];
+        if (tc && tc[j] > c->tau_used) c->tau_used = tc[j];
     }
     if (c->mode == M_FULL)
         for (int64_t i = 0; i < nr; ++i) {
             double a = fabs(dr[i]);
-            if (!(a <= tau)) { ++nfr; if (fr < 0) fr = i; }
+            if (!(a <= TR(i))) { ++nfr; if (fr < 0) fr = i; }
             if (a > dmax) dmax = a;
+            if (tr && tr[i * crs] > 0.0 && a / tr[i * crs] > rmax) rmax = a / tr[i * crs];
+            if (tr && tr[i * crs] > c->tau_used) c->tau_used = tr[i * crs];
         }
     orc_report* rep = c->rep;
     if (nfc == 0 && nfr == 0) {
-        double ratio = tau > 0.0 ? dmax / tau : 0.0;
+        double ratio = tc ? rmax : (tau > 0.0 ? dmax / tau : 0.0);
         if (ratio > rep->max_ratio) rep->max_ratio = ratio;
         free(dc); free(dw); free(dr);
         return;
@@ -228,7 +235,7 @@ static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
     rep->detected += 1;
     if (c->mode == M_SINGLE) {
         for (int64_t j = 0; j < nc; ++j) {
-            if (fabs(dc[j]) <= tau) continue;
+            if (fabs(dc[j]) <= TC(j)) continue;
             double rho = dw[j] / dc[j];
             double ri = nearbyint(rho);
             int64_t i = (int64_t)ri - 1;
@@ -242,7 +249,7 @@ static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
             }
         }
     } else if (nfr == 1 && nfc == 1) {
-        if (fabs(dc[fc] - dr[fr]) <= tau) {
+        if (fabs(dc[fc] - dr[fr]) <= (tc ? TC(fc) + TR(fr) : tau)) {
             T[fr * ldt + fc] -= dc[fc];
             rep->corrected += 1;
             add_event(c, E_0D, r0 + fr, c0 + fc, dc[fc]);
@@ -252,14 +259,14 @@ static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
         }
     } else if (nfr == 1 && nfc >= 2) {
         for (int64_t j = 0; j < nc; ++j) {
-            if (fabs(dc[j]) <= tau) continue;
+            if (fabs(dc[j]) <= TC(j)) continue;
             T[fr * ldt + j] -= dc[j];
             rep->corrected += 1;
             add_event(c, E_ROW, r0 + fr, c0 + j, dc[j]);
         }
     } else if (nfr >= 2 && nfc == 1) {
         for (int64_t i = 0; i < nr; ++i) {
-            if (fabs(dr[i]) <= tau) continue;
+            if (fabs(dr[i]) <= TR(i)) continue;
             T[i * ldt + fc] -= dr[i];
             rep->corrected += 1;
             add_event(c, E_COL, r0 + i, c0 + fc, dr[i]);
@@ -282,6 +289,14 @@ static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
         add_event(c, E_UNCORR, r0, c0, 0.0);
     }
     free(dc); free(dw); free(dr);
+#undef TC
+#undef TR
+}
+
+static void verify_tile(vctx* c, double* T, int64_t ldt, int64_t r0, int64_t c0,
+                        int64_t nr, int64_t nc, double* cc, double* cw,
+                        double* cr, int64_t crs) {
+    verify_tile_t(c, T, ldt, r0, c0, nr, nc, cc, cw, cr, crs, NULL, NULL);
 }
 
 /* Encode the checksums of one tile (Sec. 3.1.2: encode before the operation). */
@@ -533,6 +548,335 @@ int orc_potrf(int64_t n, int64_t nb, int mode, double* A, int64_t lda,
     int r = orc_potrf_sched(n, nb, modes, A, lda, faults, nfaults, tau_scale, rep);
     free(modes);
     return r;
+}
+
+/* ------------------------------------ mixed-precision ABFT Cholesky (16-bit TMU) */
+/*
+ * The mixed form is not in the paper.  It keeps the blocked skeleton of
+ * Sec. 2.1 and the checksum scheme of Sec. 3.1.2, and runs the trailing
+ * matrix update on 16-bit operands whose products are accumulated in FP32
+ * (what a tensor core computes).  Readings, written out in this section:
+ *  - the 16-bit formats: BF16 (8 significand bits, exponents -126..127) and
+ *    FP16 (11 significand bits, exponents -14..15), both with subnormals;
+ *    rounding to nearest, ties to the even significand, overflow to infinity;
+ *  - per g-row tile I of the panel L_Ik: sigma_I = 2^(ceil(log2 max|L_I|) - e_t),
+ *    e_t = 0 (BF16, the tile maximum maps to at most 1) or 14 (FP16, at most
+ *    2^14); sigma_I = 1 for an all-zero tile; Lq_I = RN16(L_I / sigma_I);
+ *  - TMU: A_IJ -= sigma_I sigma_J (Lq_I Lq_J^T).  Here the products of the
+ *    16-bit operands are summed in FP64 (exact products, p in order); the GPU
+ *    accumulates them in FP32, which the thresholds below allow for;
+ *  - the checksums are carried with the same quantized operands, so that the
+ *    quantization cancels from the checksum relation: with t_I = 1^T Lq_I and
+ *    tw_I = (1..g)^T Lq_I, c_IJ -= sigma_I sigma_J t_I Lq_J^T (and the weighted
+ *    rows with tw_I), r_IJ -= sigma_I sigma_J Lq_I t_J^T;
+ *  - abs-checksums bound what the FP32 accumulation can do to that relation:
+ *    |c|_IJ += sigma_I sigma_J (1^T |Lq_I|) |Lq_J|^T and
+ *    |r|_IJ += sigma_I sigma_J |Lq_I| (1^T |Lq_J|)^T, zero when the tile is
+ *    encoded; the threshold of column j (row i) of tile IJ is
+ *    tau_j = coef |c|_IJ,j + tau64, coef = tau_scale * 4 * gamma_g(2^-24),
+ *    gamma_g(u) = g u / (1 - g u), and tau64 the FP64 threshold
+ *    tau_scale * 8 * 2^-53 * n * g * max a_ii (the FP64 rounding of the
+ *    FP64 parts: C, the checksums, the verification sums).  The factor 4
+ *    covers both sides of the relation (data and checksum products) and a
+ *    factor 2 for an accumulation that does not round to nearest;
+ *  - PD in FP64; PU in FP32: L_kk and each right-hand side rounded to FP32,
+ *    x_j = (b_j - sum_{p<j} x_p l_jp) / l_jj with the sum one fused
+ *    multiply-add chain in p order starting from b_j, correctly rounded
+ *    division; the checksum rows (plain and weighted) go through the same
+ *    solve;
+ *  - the PD check and the panel verification use the scalar threshold
+ *    tau_scale * 8 * 2^-24 * n * g * max a_ii (the FP32 panel solve).
+ */
+#define U32 (0x1p-24)
+
+/* x rounded to BF16 (is_bf16 != 0) or FP16, to nearest with ties to even;
+ * *bits receives the 16-bit encoding (sign, biased exponent, fraction). */
+double orc_round16(double x, int is_bf16, uint16_t* bits) {
+    const int p = is_bf16 ? 8 : 11;          /* significand bits, hidden bit included */
+    const int emin = is_bf16 ? -126 : -14;   /* smallest normal exponent */
+    const int emax = is_bf16 ? 127 : 15;
+    const int fbits = p - 1, bias = emax;
+    const uint16_t sign = signbit(x) ? 0x8000u : 0u;
+    const uint16_t expall = (uint16_t)(((1u << (is_bf16 ? 8 : 5)) - 1u) << fbits);
+    if (isnan(x)) { *bits = (uint16_t)(sign | expall | (1u << (fbits - 1))); return x; }
+    if (isinf(x)) { *bits = (uint16_t)(sign | expall); return x; }
+    double a = fabs(x);
+    if (a == 0.0) { *bits = sign; return x; }
+    int E;
+    frexp(a, &E);                             /* a = f 2^E, f in [0.5, 1): exponent E - 1 */
+    int e = E - 1;
+    int qe = (e < emin ? emin : e) - fbits;   /* spacing of the format around a: 2^qe */
+    double r = nearbyint(ldexp(a, -qe));      /* default mode: nearest, ties to even */
+    double v = ldexp(r, qe);
+    double maxf = ldexp(ldexp(1.0, p) - 1.0, emax - fbits);
+    if (v > maxf) { *bits = (uint16_t)(sign | expall); return sign ? -INFINITY : INFINITY; }
+    uint16_t code;
+    if (v < ldexp(1.0, emin)) {               /* subnormal: fraction = v / 2^(emin - fbits) */
+        code = (uint16_t)ldexp(v, -(emin - fbits));
+    } else {
+        int E2;
+        frexp(v, &E2);
+        int e2 = E2 - 1;
+        uint16_t frac = (uint16_t)(ldexp(v, fbits - e2) - ldexp(1.0, fbits));
+        code = (uint16_t)(((unsigned)(e2 + bias) << fbits) | frac);
+    }
+    *bits = (uint16_t)(sign | code);
+    return sign ? -v : v;
+}
+
+/* sigma = 2^(ceil(log2 m) - et) for the tile maximum m = max |x| > 0, else 1. */
+double orc_tile_sigma(double m, int is_bf16) {
+    const int et = is_bf16 ? 0 : 14;
+    if (!(m > 0.0)) return 1.0;
+    int E;
+    double f = frexp(m, &E);                  /* m = f 2^E, f in [0.5, 1) */
+    int c = (f == 0.5) ? E - 1 : E;           /* ceil(log2 m) */
+    return ldexp(1.0, c - et);
+}
+
+/* Quantize one tile (rows x cols, leading dimension ldp): *sigma, the 16-bit
+ * encodings (bits, rows x cols, may be NULL) and their values (q, rows x cols). */
+void orc_quantize(int64_t rows, int64_t cols, const double* P, int64_t ldp, int is_bf16,
+                  double* sigma, uint16_t* bits, double* q) {
+    double m = 0.0;
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < cols; ++j)
+            if (fabs(P[i * ldp + j]) > m) m = fabs(P[i * ldp + j]);
+    double s = orc_tile_sigma(m, is_bf16);
+    *sigma = s;
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < cols; ++j) {
+            uint16_t b;
+            q[i * cols + j] = orc_round16(P[i * ldp + j] / s, is_bf16, &b);
+            if (bits) bits[i * cols + j] = b;
+        }
+}
+
+/* The mixed trailing update on its own: the m x k panel P quantized per g-row
+ * tile (sigma[I], bits m x k), then C -= sigma_I sigma_J (Lq_I Lq_J^T) on the
+ * lower block triangle of the m x m matrix C (blocks g x g, J <= I); each
+ * entry's products summed in FP64 in p order, then subtracted once. */
+void orc_syrk_mixed(int64_t m, int64_t k, int64_t g, int is_bf16, const double* P, int64_t ldp,
+                    double* C, int64_t ldc, uint16_t* bits, double* sigma) {
+    int64_t nt = (m + g - 1) / g;
+    double* q = dalloc(m * k);
+    for (int64_t I = 0; I < nt; ++I) {
+        int64_t r0 = I * g, rows = imin(g, m - r0);
+        orc_quantize(rows, k, P + r0 * ldp, ldp, is_bf16, &sigma[I], bits ? bits + r0 * k : NULL,
+                     q + r0 * k);
+    }
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j) {
+            if (j / g > i / g) continue;
+            double s = 0.0;
+            for (int64_t p = 0; p < k; ++p) s += q[i * k + p] * q[j * k + p];
+            C[i * ldc + j] = C[i * ldc + j] - (sigma[i / g] * sigma[j / g]) * s;
+        }
+    free(q);
+}
+
+/* One right-hand side of x L^T = b in FP32 (the mixed form's panel solve):
+ * Lf holds L (kb x kb, lower) rounded to FP32; b is overwritten with x. */
+static void solve_row_f32(double* b, const float* Lf, int64_t kb) {
+    float x[512];
+    for (int64_t j = 0; j < kb; ++j) {
+        float v = (float)b[j];
+        for (int64_t p = 0; p < j; ++p) v = fmaf(-x[p], Lf[j * kb + p], v);
+        x[j] = v / Lf[j * kb + j];
+    }
+    for (int64_t j = 0; j < kb; ++j) b[j] = (double)x[j];
+}
+
+static double threshold_u(double tau_scale, double u, int64_t n, int64_t g, double M) {
+    double t = tau_scale * 8.0;
+    t *= u;
+    t *= (double)n;
+    t *= (double)g;
+    t *= M;
+    return t;
+}
+
+/* coef of the abs-checksum thresholds: tau_scale * 4 * gamma_g(2^-24). */
+double orc_mixed_coef(double tau_scale, int64_t g) {
+    double gam = ((double)g * U32) / (1.0 - (double)g * U32);
+    double t = tau_scale * 4.0;
+    t *= gam;
+    return t;
+}
+
+/*
+ * orc_potrf_mixed -- the blocked ABFT Cholesky in the mixed form described
+ * above, with a checksum mode per step (modes[k], N = ceil(n / nb) entries,
+ * the same schedule semantics as orc_potrf_sched).  is_bf16 selects BF16 or
+ * FP16 operands.  rep->tau is the largest threshold applied to a trailing
+ * tile (an error larger than it plus the clean |d| is always flagged);
+ * rep->max_ratio the largest |d| / threshold over tiles without flags.
+ */
+int orc_potrf_mixed(int64_t n, int64_t nb, const int* modes, int is_bf16, double* A, int64_t lda,
+                    const orc_event* faults, int32_t nfaults, double tau_scale,
+                    orc_report* rep) {
+    memset(rep, 0, sizeof(*rep));
+    if (n < 0) return -1;
+    if (nb <= 0 || nb > 512) return -2;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (n == 0) return 0;
+    int64_t g = nb, nt = (n + g - 1) / g, N = nt;
+    for (int64_t k = 0; k < N; ++k)
+        if (modes[k] < M_NONE || modes[k] > M_FULL) return -3;
+    for (int32_t f = 0; f < nfaults; ++f)
+        if (!chol_fault_ok(&faults[f], n, nb, N)) return -6;
+
+    double* W = dalloc(n * n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j <= i; ++j) W[i * n + j] = W[j * n + i] = A[i * lda + j];
+    double dmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (A[i * lda + i] > dmax) dmax = A[i * lda + i];
+    const double tau64 = threshold_u(tau_scale, U64, n, g, dmax);
+    const double coef = orc_mixed_coef(tau_scale, g);
+    vctx c = { M_NONE, 0, g, threshold_u(tau_scale, U32, n, g, dmax), rep, 0.0 };
+
+    double* Cc = dalloc(nt * n);   /* column sums of tile-row I: Cc[I*n + j]      */
+    double* Cw = dalloc(nt * n);   /* weighted column sums                          */
+    double* Cr = dalloc(n * nt);   /* row sums of tile-column J: Cr[i*nt + J]      */
+    double* Ca = dalloc(nt * n);   /* abs-checksums of the column sums             */
+    double* Ra = dalloc(n * nt);   /* abs-checksums of the row sums                */
+    double* Tc = dalloc(g);        /* thresholds of one tile's columns             */
+    double* Tr = dalloc(n * nt);   /* thresholds of the row sums (laid out as Cr)  */
+    double* xr = dalloc(n);
+    double* q = dalloc(n * g);     /* quantized panel values, row i at q[i*g]      */
+    double* sig = dalloc(nt);
+    double* t = dalloc(nt * g);    /* t_I = 1^T Lq_I                               */
+    double* tw = dalloc(nt * g);   /* tw_I = (1..g)^T Lq_I                         */
+    double* ta = dalloc(nt * g);   /* 1^T |Lq_I|                                   */
+    float* Lf = (float*)calloc((size_t)(g * g), sizeof(float));
+    int info = 0;
+    for (int64_t k = 0; k < N; ++k) {
+        const int mode = modes[k];
+        const int prev = k > 0 ? modes[k - 1] : M_NONE;
+        c.step = (int)k;
+        c.mode = mode;
+        int64_t K0 = k * g, kb = imin(g, n - K0), T0 = K0 + kb;
+        double* Lkk = W + K0 * n + K0;
+        if (mode != M_NONE && (prev == M_NONE || (mode == M_FULL && prev != M_FULL)))
+            for (int64_t I = k; I < nt; ++I)
+                for (int64_t J = k; J <= I; ++J) {
+                    int64_t r0 = I * g, c0 = J * g, nr = imin(g, n - r0), ncl = imin(g, n - c0);
+                    encode_tile(W + r0 * n + c0, n, nr, ncl, Cc + I * n + c0, Cw + I * n + c0,
+                                Cr + r0 * nt + J, nt);
+                    for (int64_t j = 0; j < ncl; ++j) Ca[I * n + c0 + j] = 0.0;
+                    for (int64_t i = 0; i < nr; ++i) Ra[(r0 + i) * nt + J] = 0.0;
+                }
+        /* PD (FP64) and its check */
+        int pinfo = orc_potf2(kb, Lkk, n);
+        if (pinfo) { info = (int)(K0 + pinfo); break; }
+        if (mode != M_NONE) {
+            for (int64_t j = 0; j < kb; ++j) {
+                double y = 0.0;
+                for (int64_t p = 0; p <= j; ++p) {
+                    double colsum = 0.0;
+                    for (int64_t r = p; r < kb; ++r) colsum += Lkk[r * n + p];
+                    y += colsum * Lkk[j * n + p];
+                }
+                double d = y - Cc[k * n + K0 + j];
+                if (!(fabs(d) <= c.tau)) {
+                    rep->detected += 1; rep->uncorrectable += 1;
+                    add_event(&c, E_PD, K0 + j, K0 + j, d);
+                }
+            }
+        }
+        if (T0 >= n) break;
+        /* PU in FP32: checksum rows and panel rows through x L_kk^T = b */
+        for (int64_t i = 0; i < kb; ++i)
+            for (int64_t j = 0; j < kb; ++j) Lf[i * kb + j] = j <= i ? (float)Lkk[i * n + j] : 0.0f;
+        if (mode != M_NONE)
+            for (int64_t I = k + 1; I < nt; ++I) {
+                solve_row_f32(Cc + I * n + K0, Lf, kb);
+                solve_row_f32(Cw + I * n + K0, Lf, kb);
+            }
+        for (int64_t i = T0; i < n; ++i) solve_row_f32(W + i * n + K0, Lf, kb);
+        for (int32_t f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && faults[f].kind == F_PANEL) apply_fault(W, n, g, &faults[f]);
+        {
+            vctx cp = c;   /* panel tiles: single-side rule, scalar FP32 threshold */
+            if (cp.mode == M_FULL) cp.mode = M_SINGLE;
+            for (int64_t I = k + 1; I < nt; ++I) {
+                int64_t r0 = I * g;
+                verify_tile(&cp, W + r0 * n + K0, n, r0, K0, imin(g, n - r0), kb,
+                            Cc + I * n + K0, Cw + I * n + K0, xr + r0, 1);
+            }
+        }
+        /* quantize the panel per tile-row, with the sums the checksums use */
+        for (int64_t I = k + 1; I < nt; ++I) {
+            int64_t r0 = I * g, rows = imin(g, n - r0);
+            orc_quantize(rows, kb, W + r0 * n + K0, n, is_bf16, &sig[I], NULL, q + r0 * g);
+            for (int64_t p = 0; p < kb; ++p) {
+                double s = 0.0, sw = 0.0, sa = 0.0;
+                for (int64_t r = 0; r < rows; ++r) {
+                    double v = q[(r0 + r) * g + p];
+                    s += v;
+                    sw += (double)(r + 1) * v;
+                    sa += fabs(v);
+                }
+                t[I * g + p] = s; tw[I * g + p] = sw; ta[I * g + p] = sa;
+            }
+        }
+        /* TMU on the quantized operands (products summed in FP64) */
+        for (int64_t i = T0; i < n; ++i)
+            for (int64_t j = T0; j < n; ++j) {
+                if (j / g > i / g) break;   /* lower block triangle, diagonal blocks full */
+                double s = 0.0;
+                for (int64_t p = 0; p < kb; ++p) s += q[i * g + p] * q[j * g + p];
+                W[i * n + j] = W[i * n + j] - (sig[i / g] * sig[j / g]) * s;
+            }
+        /* checksum carries with the same operands, abs-checksums beside them */
+        if (mode != M_NONE) {
+            for (int64_t I = k + 1; I < nt; ++I)
+                for (int64_t j = T0; j < n; ++j) {
+                    if (j / g > I) break;
+                    double sc = sig[I] * sig[j / g], s = 0.0, sw = 0.0, sa = 0.0;
+                    for (int64_t p = 0; p < kb; ++p) {
+                        s += t[I * g + p] * q[j * g + p];
+                        sw += tw[I * g + p] * q[j * g + p];
+                        sa += ta[I * g + p] * fabs(q[j * g + p]);
+                    }
+                    Cc[I * n + j] = Cc[I * n + j] - sc * s;
+                    Cw[I * n + j] = Cw[I * n + j] - sc * sw;
+                    Ca[I * n + j] = Ca[I * n + j] + sc * sa;
+                }
+            if (mode == M_FULL)
+                for (int64_t i = T0; i < n; ++i)
+                    for (int64_t J = k + 1; J <= i / g; ++J) {
+                        double sc = sig[i / g] * sig[J], s = 0.0, sa = 0.0;
+                        for (int64_t p = 0; p < kb; ++p) {
+                            s += q[i * g + p] * t[J * g + p];
+                            sa += fabs(q[i * g + p]) * ta[J * g + p];
+                        }
+                        Cr[i * nt + J] = Cr[i * nt + J] - sc * s;
+                        Ra[i * nt + J] = Ra[i * nt + J] + sc * sa;
+                    }
+        }
+        for (int32_t f = 0; f < nfaults; ++f)
+            if (faults[f].step == k && faults[f].kind != F_PANEL) apply_fault(W, n, g, &faults[f]);
+        /* verify every trailing tile against per-column / per-row thresholds */
+        if (mode != M_NONE)
+            for (int64_t I = k + 1; I < nt; ++I)
+                for (int64_t J = k + 1; J <= I; ++J) {
+                    int64_t r0 = I * g, c0 = J * g, nr = imin(g, n - r0), ncl = imin(g, n - c0);
+                    for (int64_t j = 0; j < ncl; ++j) Tc[j] = coef * Ca[I * n + c0 + j] + tau64;
+                    for (int64_t i = 0; i < nr; ++i)
+                        Tr[(r0 + i) * nt + J] = coef * Ra[(r0 + i) * nt + J] + tau64;
+                    verify_tile_t(&c, W + r0 * n + c0, n, r0, c0, nr, ncl, Cc + I * n + c0,
+                                  Cw + I * n + c0, Cr + r0 * nt + J, nt, Tc, Tr + r0 * nt + J);
+                }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j <= i; ++j) A[i * lda + j] = W[i * n + j];
+    rep->info = info;
+    rep->tau = c.tau_used;
+    qsort(rep->loc, (size_t)rep->nloc, sizeof(orc_event), cmp_event);
+    free(W); free(Cc); free(Cw); free(Cr); free(Ca); free(Ra); free(Tc); free(Tr); free(xr);
+    free(q); free(sig); free(t); free(tw); free(ta); free(Lf);
+    return info;
 }
 
 /* ------------------------------------------------------ blocked ABFT LU */
