@@ -521,6 +521,7 @@ def run_ours(args, ws, rank, local):
             return None
         ms_fp64, _ = timed(fp64_solve, 1, 1)
         mixed = {"fp64_ms_to_solution": ms_fp64, "fp64_board_joules": last_joules[0]}
+        amax_diag = float(A0.diagonal().max().item())
         for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
             def mixed_solve():
                 return abft.posv_ir(A0, B, nb, dt, abft.FULL, tol=1e-12, maxit=100, faults=faults,
@@ -531,7 +532,15 @@ def run_ours(args, ws, rank, local):
                            "tflops_equiv": chol_flops(n) / (ms_mix * 1e-3) / 1e12,
                            "ir_iters": rep_m["ir_iters"], "backward_err": rep_m["backward_err"],
                            "rc": rc_m, "faults_corrected": rep_m["corrected"],
-                           "board_joules": last_joules[0]}
+                           "board_joules": last_joules[0],
+                           # the trailing-tile detector: per-column thresholds
+                           # tau_j = 4 gamma_g(2^-24) |c|_j + tau64 from the
+                           # abs-checksums; an error above tau_max (1 + max_ratio)
+                           # is flagged at every step and column
+                           "detector": {
+                               "max_ratio_clean": rep_m["max_ratio"], "tau_max": rep_m["tau"],
+                               "smallest_detectable_delta": rep_m["tau"] * (1 + rep_m["max_ratio"]),
+                               "scalar_fp32_tau_it_replaces": 8 * 2.0 ** -24 * n * nb * amax_diag}}
         del Lbuf, Xb, B
 
     lookahead = None

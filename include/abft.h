@@ -262,6 +262,38 @@ int abft_potrs(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, const double*
                double* B, int64_t ldb, void* ws, size_t* ws_bytes, void* stream);
 
 /*
+ * abft_syrk_mixed -- the trailing-matrix update (TMU, Sec. 2.1) of abft_potrf
+ * in its mixed-precision form (ABFT_MIXED_BF16 / ABFT_MIXED_F16; the form is
+ * not in the paper), on its own and without checksums, so that it can be
+ * checked element by element.  For each g-row tile I of the m x k panel P:
+ * sigma_I = 2^(ceil(log2 max|P_I|) - e_t) (e_t = 0 for BF16, 14 for FP16;
+ * 1 for an all-zero tile) and Pq_I = P_I / sigma_I rounded to the 16-bit
+ * format (nearest, ties to even); then C -= sigma_I sigma_J (Pq_I Pq_J^T) on
+ * the lower block triangle of the m x m matrix C (g x g blocks with J <= I,
+ * diagonal blocks in full), the products of the 16-bit operands accumulated
+ * in FP32 on the tensor cores and subtracted from C in FP64 (one rounding).
+ * Entries outside the lower block triangle are not touched.
+ *   m, k       panel rows and width; k a multiple of 64, at most 512
+ *   g          tile order, a multiple of 128
+ *   dtype      ABFT_MIXED_BF16 or ABFT_MIXED_F16
+ *   P, ldp     m x k FP64 row-major (device), read only
+ *   C, ldc     m x m FP64 row-major (device), updated in place
+ *   Pq         m x k 16-bit codes (device, row-major with ld k, 16-byte
+ *              aligned), written
+ *   sigma      ceil(m / g) doubles (device), written
+ *   timed_out  host int32 or NULL; when given, the call synchronizes its
+ *              stream and sets it to 1 if a bounded wait of the update kernel
+ *              gave up (then ABFT_ERR_TIMEOUT is returned), else 0
+ *   ws, ws_bytes   workspace query protocol as abft_potrf (a status block and
+ *              ceil(m / g) x k doubles)
+ * Asynchronous on stream unless timed_out is given.  Errors: -1 m; -2 k;
+ * -3 g; -4 dtype; -5 P; -6 ldp; -7 C; -8 ldc; -9 Pq; -10 sigma; -13 workspace.
+ */
+int abft_syrk_mixed(int64_t m, int64_t k, int64_t g, int32_t dtype, const double* P, int64_t ldp,
+                    double* C, int64_t ldc, uint16_t* Pq, double* sigma, int32_t* timed_out,
+                    void* ws, size_t* ws_bytes, void* stream);
+
+/*
  * abft_symm_emu -- Y = A X for symmetric A (lower triangle read), FP64-accurate
  * on the BF16 tensor cores (the product of the refinement residuals; not in the
  * paper).  A is split into 8 BF16 slices of its full rows (a power-of-two

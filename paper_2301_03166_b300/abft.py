@@ -74,6 +74,8 @@ _SIGNATURES = {
     "abft_potrf": [_i64, _i64, _i32, _i32, _vp, _i64, ctypes.POINTER(Fault), _i32, _dbl,
                    ctypes.POINTER(Report), _vp, _sz, _vp],
     "abft_symm_emu": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
+    "abft_syrk_mixed": [_i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _vp,
+                        ctypes.POINTER(_i32), _vp, _sz, _vp],
     "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
                          ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }
@@ -234,6 +236,39 @@ def symm_emu(A, X, Y=None, workspace=None, stream=None):
     if rc != 0:
         raise AbftError(rc, strerror(rc))
     return Y
+
+
+def syrk_mixed(P, C, g, dtype=MIXED_BF16, workspace=None, stream=None, sync=True):
+    """The mixed-precision trailing update on its own: C -= sigma_I sigma_J
+    (Pq_I Pq_J^T) on the lower block triangle (in place).  Returns (the 16-bit
+    codes of Pq as a uint16 numpy array, sigma as a numpy array) when sync,
+    else (Pq, sigma) as device tensors."""
+    _check_matrix(P, "P")
+    _check_matrix(C, "C")
+    m, k = P.shape
+    if C.shape != (m, m):
+        raise ValueError("C must be m x m")
+    Pq = torch.empty((m, k), dtype=torch.int16, device=P.device)
+    sig = torch.empty(max(1, -(-m // g)), dtype=torch.float64, device=P.device)
+    L = lib()
+    need = ctypes.c_size_t(0)
+    rc = L.abft_syrk_mixed(m, k, g, dtype, None, max(1, P.stride(0)), None, max(1, C.stride(0)),
+                           None, None, None, None, ctypes.byref(need), None)
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    ws = (workspace or Workspace()).get(need.value, P.device)
+    size = ctypes.c_size_t(ws.numel())
+    tout = _i32(0)
+    rc = L.abft_syrk_mixed(m, k, g, dtype, ctypes.c_void_p(P.data_ptr()), max(1, P.stride(0)),
+                           ctypes.c_void_p(C.data_ptr()), max(1, C.stride(0)),
+                           ctypes.c_void_p(Pq.data_ptr()), ctypes.c_void_p(sig.data_ptr()),
+                           ctypes.byref(tout) if sync else None,
+                           ctypes.c_void_p(ws.data_ptr()), ctypes.byref(size), _stream(stream))
+    if rc != 0:
+        raise AbftError(rc, strerror(rc))
+    if not sync:
+        return Pq, sig
+    return Pq.cpu().numpy().view(np.uint16), sig.cpu().numpy()
 
 
 def _modes_array(modes, n, nb):

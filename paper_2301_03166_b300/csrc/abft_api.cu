@@ -109,7 +109,8 @@ size_t pd_part_bytes(int64_t nb) {
 }
 
 struct CholWs {
-    size_t st, cs, cr, xr, v, save, lq, sig, tq, tq32, l32, pdpart, eslice, eex, pslice, pex, total;
+    size_t st, cs, cr, xr, v, save, lq, sig, tq, tq32, l32, ca, ra, ta32, pdpart, eslice, eex,
+        pslice, pex, total;
     int64_t nc;   // checksum rows per tile-row in CS (0, 1 or 2)
     int64_t nt;
 };
@@ -133,6 +134,12 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     w.tq = off; off = align_up(off + (mixed ? sizeof(double) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.tq32 = off; off = align_up(off + (mixed ? sizeof(float) * (size_t)(ncq * w.nt) * (size_t)nb : 0));
     w.l32 = off; off = align_up(off + (mixed ? sizeof(float) * (size_t)nb * (size_t)nb : 0));
+    // abs-checksums of the mixed form (thresholds per column / row) and the
+    // panel tiles' sums 1^T |Lq_I| that carry them
+    const bool absc = mixed && mode != ABFT_MODE_NONE;
+    w.ca = off; off = align_up(off + (absc ? sizeof(double) * (size_t)w.nt * (size_t)n : 0));
+    w.ra = off; off = align_up(off + (absc && mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n * (size_t)w.nt : 0));
+    w.ta32 = off; off = align_up(off + (absc ? sizeof(float) * (size_t)w.nt * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
     w.eex = off; off = align_up(off + (emu ? sizeof(int) * (size_t)emu_rows(n, nb) : 0));
@@ -178,6 +185,11 @@ int finish_report(const DevStatus* dst, abft_report* rep, cudaStream_t s, bool l
     std::memcpy(&r, &h.max_ratio_bits, sizeof(r));
     rep->max_ratio = r;
     rep->tau = h.tau;
+    if (h.tau_coef > 0.0 && h.tau_max_bits != 0) {   // mixed form: largest per-column threshold
+        double t;
+        std::memcpy(&t, &h.tau_max_bits, sizeof(t));
+        rep->tau = t;
+    }
     if (h.error) return ABFT_ERR_TIMEOUT;
     if (rep->info) return rep->info;
     if (h.uncorrectable) return ABFT_ERR_UNCORRECTABLE;
@@ -266,6 +278,9 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     double* sig = (double*)(base + w.sig);
     double* tq = (double*)(base + w.tq);
     float* tq32 = (float*)(base + w.tq32);
+    double* Ca = (double*)(base + w.ca);
+    double* Ra = (double*)(base + w.ra);
+    float* ta32 = (float*)(base + w.ta32);
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
     double* Cr = (double*)(base + w.cr);
@@ -276,7 +291,15 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
 
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_mirror_diag(A, lda, n, nb, save, 0, s));
-    ABFT_CUDA_TRY(launch_tau_chol(A, lda, n, g, tau_scale, st, s, mixed ? 0x1p-24 : 0x1p-53));
+    // mixed form: tau_scale * 4 * gamma_g(2^-24), the factor of the per-column
+    // thresholds (the same expression and order as the oracle)
+    double mcoef = 0.0;
+    if (mixed) {
+        const double gam = ((double)g * 0x1p-24) / (1.0 - (double)g * 0x1p-24);
+        mcoef = tau_scale * 4.0;
+        mcoef *= gam;
+    }
+    ABFT_CUDA_TRY(launch_tau_chol(A, lda, n, g, tau_scale, st, s, mixed ? 0x1p-24 : 0x1p-53, mcoef));
     // checksum tile sets (Sec. 3.1.2: per matrix block)
     TileSet base_ts{};
     base_ts.A = A; base_ts.lda = lda;
@@ -311,6 +334,11 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             TileSet ts = base_ts;
             ts.I0 = k; ts.I1 = nt; ts.J0 = k; ts.J1 = nt; ts.lower = 1;
             ABFT_CUDA_TRY(launch_encode(ts, mk, s));
+            if (mixed) {   // abs-checksums start at zero with the encoded checksums
+                ABFT_CUDA_TRY(cudaMemsetAsync(Ca, 0, sizeof(double) * (size_t)nt * (size_t)n, s));
+                if (full)
+                    ABFT_CUDA_TRY(cudaMemsetAsync(Ra, 0, sizeof(double) * (size_t)n * (size_t)nt, s));
+            }
             timing_mark(PH_OTHER, 0, s);
         }
         // PD and its checksum check
@@ -404,7 +432,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             timing_mark(PH_TMU, 1, s);
             const int64_t ncq = nc > 0 ? nc : 1;
             ABFT_CUDA_TRY(launch_quant_panel(A + K0, lda, T0, n, kb, g, k + 1, nt, bf16, Lq, sig, tq,
-                                             ncq * kb, check ? 1 : 0, s, tq32));
+                                             ncq * kb, check ? 1 : 0, s, tq32,
+                                             check ? ta32 : nullptr));
             timing_mark(PH_TMU, 0, s);
         }
         auto tmu = [&](int part, cudaStream_t ss) -> int {
@@ -450,7 +479,7 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                                                cfall, ncfall, st, ss, part == PART_REST ? w1 : 0,
                                                part == PART_NEXT ? 1 : 0, maxg));
                 if (check) {
-                    BorderSegHost bs[2] = {};
+                    BorderSegHost bs[4] = {};
                     // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
                     bs[0].A = tq32 + ((k + 1) * ncq) * kb; bs[0].a_half = 2; bs[0].lda = kb;
                     bs[0].B = Lq + c0 * kb; bs[0].b_half = 1; bs[0].ldb = kb;
@@ -465,7 +494,20 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                     bs[1].M = m; bs[1].N = J1 - J0; bs[1].K = kb;
                     bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;
                     bs[1].c_off = 0; bs[1].c_div = 1; bs[1].c_base = J0;
-                    ABFT_CUDA_TRY(launch_border_mixed(bs, full ? 2 : 1, bf16, sig, st, ss));
+                    // abs-checksum rows: |c|_I += sigma_I sigma_J ((1^T |Lq_I|) |Lq_J|^T)
+                    bs[2] = bs[0];
+                    bs[2].A = ta32 + (k + 1) * kb; bs[2].lda = kb;
+                    bs[2].C = Ca + (k + 1) * n + T0 + c0;
+                    bs[2].M = nt - k - 1; bs[2].r_div = 1;
+                    bs[2].b_abs = 1; bs[2].plus = 1;
+                    // abs-checksum columns: |r|_I += sigma_I sigma_J (|Lq_I| (1^T |Lq_J|)^T)
+                    bs[3] = bs[1];
+                    bs[3].B = ta32 + J0 * kb; bs[3].ldb = kb;
+                    bs[3].C = Ra + T0 * nt + J0;
+                    bs[3].a_abs = 1; bs[3].plus = 1;
+                    // segments: checksum rows, abs rows, then (full) checksum and abs columns
+                    BorderSegHost ord[4] = {bs[0], bs[2], bs[1], bs[3]};
+                    ABFT_CUDA_TRY(launch_border_mixed(ord, full ? 4 : 2, bf16, sig, st, ss));
                 }
             } else {
                 // TMU with the checksum borders folded into the same launch
@@ -515,6 +557,10 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             if (check) {
                 TileSet ts = base_ts;
                 ts.I0 = J0; ts.I1 = nt; ts.J0 = J0; ts.J1 = J1; ts.lower = part == PART_NEXT ? 0 : 1;
+                if (mixed) {   // per-column / per-row thresholds from the abs-checksums
+                    ts.ca = Ca; ts.caI = n;
+                    ts.ra = full ? Ra : nullptr;
+                }
                 ABFT_CUDA_TRY(launch_verify(ts, mk, (int)k, st, ss));
             }
             timing_mark(PH_VERIFY, 0, ss);
@@ -1996,6 +2042,46 @@ int abft_potrf(int64_t n, int64_t nb, int32_t dtype, int32_t mode, double* A, in
     }
     ABFT_CUDA_TRY(timing_collect(s));
     if (rep) return finish_report(st, rep, s);
+    return ABFT_OK;
+}
+
+int abft_syrk_mixed(int64_t m, int64_t k, int64_t g, int32_t dtype, const double* P, int64_t ldp,
+                    double* C, int64_t ldc, uint16_t* Pq, double* sigma, int32_t* timed_out,
+                    void* ws, size_t* ws_bytes, void* stream) {
+    if (m < 0) return -1;
+    if (k <= 0 || k % 64 != 0 || k > 512) return -2;
+    if (g <= 0 || g % 128 != 0) return -3;
+    if (dtype != ABFT_MIXED_BF16 && dtype != ABFT_MIXED_F16) return -4;
+    if (m > 0 && P == nullptr && ws != nullptr) return -5;
+    if (ldp < k) return -6;
+    if (m > 0 && C == nullptr && ws != nullptr) return -7;
+    if (ldc < std::max<int64_t>(1, m)) return -8;
+    if (m > 0 && ws != nullptr && (Pq == nullptr || ((uintptr_t)Pq & 15) != 0)) return -9;
+    if (m > 0 && sigma == nullptr && ws != nullptr) return -10;
+    if (ws_bytes == nullptr) return -13;
+    const int64_t nt = (m + g - 1) / g;
+    const size_t st_off = 0, ts_off = align_up(sizeof(DevStatus));
+    const size_t need = ts_off + align_up(sizeof(double) * (size_t)std::max<int64_t>(1, nt) * (size_t)k);
+    if (ws == nullptr) {
+        *ws_bytes = need;
+        return ABFT_OK;
+    }
+    if (*ws_bytes < need) return -13;
+    if (m == 0) return ABFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus* st = (DevStatus*)((char*)ws + st_off);
+    double* tsum = (double*)((char*)ws + ts_off);
+    const int bf16 = dtype == ABFT_MIXED_BF16 ? 1 : 0;
+    ABFT_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    ABFT_CUDA_TRY(launch_quant_panel(P, ldp, 0, m, k, g, 0, nt, bf16, Pq, sigma, tsum, k, 0, s));
+    ABFT_CUDA_TRY(launch_tmu_mixed(Pq, m, k, bf16, C, ldc, g, 0, sigma, nullptr, 0, st, s, 0, 0, 0));
+    if (timed_out) {
+        int err = 0;
+        ABFT_CUDA_TRY(cudaMemcpyAsync(&err, &st->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ABFT_CUDA_TRY(cudaStreamSynchronize(s));
+        *timed_out = err != 0;
+        if (err) return ABFT_ERR_TIMEOUT;
+    }
     return ABFT_OK;
 }
 

@@ -27,6 +27,11 @@ struct DevStatus {
     int vexp;                          // > 0: biased exponent bound of the verified entries (fixed-point sums)
     unsigned long long bar_count;      // grid barrier of the cooperative panel kernels:
                                        // arrivals since the launch (zeroed by the launcher)
+    // mixed-precision Cholesky: trailing tiles are checked against per-column
+    // (per-row) thresholds tau_coef |c| + tau64 from the abs-checksums
+    double tau64;                      // FP64 part of those thresholds
+    double tau_coef;                   // tau_scale * 4 * gamma_g(2^-24); 0 = scalar tau
+    unsigned long long tau_max_bits;   // largest such threshold applied (bits of a double >= 0)
     abft_fault loc[ABFT_MAX_LOC];
 };
 
@@ -114,6 +119,13 @@ struct TileSet {
     int lower;
     int64_t nrow_end, ncol_end;
     int weighted;   // encode also writes the weighted column sums (cw)
+    // verify only, mixed-precision Cholesky: abs-checksums laid out as cc and cr
+    // (ca(I,J) = ca + I caI + J g, ra(I,J) = ra + (I g) crs + J crJ); when set,
+    // column j is flagged above tau_coef ca_j + tau64 and row i above
+    // tau_coef ra_i + tau64 instead of the scalar tau
+    const double* ca;
+    int64_t caI;
+    const double* ra;
 };
 
 cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s);
@@ -122,8 +134,11 @@ cudaError_t launch_inject(double* A, int64_t lda, int64_t n, int64_t g, const ab
                           cudaStream_t s);
 cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, double* save,
                                int restore, cudaStream_t s);
+// tau_coef > 0 (mixed precision): also stores tau64 (the FP64 threshold) and
+// tau_coef for the per-column thresholds.
 cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                            DevStatus* st, cudaStream_t s, double unit_roundoff = 0x1p-53);
+                            DevStatus* st, cudaStream_t s, double unit_roundoff = 0x1p-53,
+                            double tau_coef = 0.0);
 
 // FP64 update C -= A_op * B_op^T (NT) or A_op * B_op (NN), over up to three
 // segments (the main tiles and the checksum border rows / columns).
@@ -234,11 +249,14 @@ struct BorderSegHost {
     int64_t ldc;
     int64_t M, N, K;
     int64_t r_off, r_div, r_base, c_off, c_div, c_base;
+    int a_abs = 0, b_abs = 0;   // use |A| / |B| (the abs-checksum products)
+    int plus = 0;               // C += ... instead of C -= ...
 };
+// tabs32 (nullable): 1^T |Lq_I| per tile-row, FP32, at tabs32[I kb + p].
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
                                int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
                                double* sig, double* tsum, int64_t tstride, int weighted,
-                               cudaStream_t s, float* tsum32 = nullptr);
+                               cudaStream_t s, float* tsum32 = nullptr, float* tabs32 = nullptr);
 cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16, double* C,
                              int64_t ldc, int64_t g, int64_t off, const double* sig,
                              const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s,

@@ -276,23 +276,50 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
         tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum,
                                                              rowsum, part);
     const double tau = st->tau;
-    double dmax = 0.0;
+    // thresholds per column and row: the scalar tau, or (mixed precision)
+    // tau_coef |c|_j + tau64 from the abs-checksums; part[] is free again
+    const bool pc = ts.ca != nullptr;
+    double* tcol = part[0];
+    double* trow = part[1];
+    const double coef = st->tau_coef, t64 = st->tau64;
+    double tmax = 0.0;
+    if (pc) {
+        const double* ca = ts.ca + I * ts.caI + J * ts.g;
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            tcol[j] = __dadd_rn(__dmul_rn(coef, ca[j]), t64);
+            tmax = fmax(tmax, tcol[j]);
+        }
+        if (MODE == MODE_FULL) {
+            const double* ra = ts.ra + r0 * ts.crs + J * ts.crJ;
+            for (int i = threadIdx.x; i < nr; i += kThreads) {
+                trow[i] = __dadd_rn(__dmul_rn(coef, ra[(int64_t)i * ts.crs]), t64);
+                tmax = fmax(tmax, trow[i]);
+            }
+        }
+        atomic_max_nonneg(&st->tau_max_bits, tmax);
+        __syncthreads();
+    }
+#define TCOL(j) (pc ? tcol[j] : tau)
+#define TROW(i) (pc ? trow[i] : tau)
+    double dmax = 0.0;   // largest |d| / threshold
     // d = recomputed - carried, kept in place of the sums
     for (int j = threadIdx.x; j < nc; j += kThreads) {
         double d = colsum[j] - cc[j];
         colsum[j] = d;
         if (MODE == MODE_SINGLE) wsum[j] = wsum[j] - cw[j];
-        double a = fabs(d);
-        if (!(a <= tau)) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
-        if (a > dmax) dmax = a;
+        double a = fabs(d), t = TCOL(j);
+        if (!(a <= t)) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
+        const double q = t > 0.0 ? a / t : 0.0;
+        if (q > dmax) dmax = q;
     }
     if (MODE == MODE_FULL)
         for (int i = threadIdx.x; i < nr; i += kThreads) {
             double d = rowsum[i] - cr[(int64_t)i * ts.crs];
             rowsum[i] = d;
-            double a = fabs(d);
-            if (!(a <= tau)) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
-            if (a > dmax) dmax = a;
+            double a = fabs(d), t = TROW(i);
+            if (!(a <= t)) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
+            const double q = t > 0.0 ? a / t : 0.0;
+            if (q > dmax) dmax = q;
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -303,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
         if (threadIdx.x == 0) {
             double m = 0.0;
             for (int w = 0; w < kWarps; ++w) m = fmax(m, s_dmax[w]);
-            if (tau > 0.0) atomic_max_nonneg(&st->max_ratio_bits, m / tau);
+            atomic_max_nonneg(&st->max_ratio_bits, m);
         }
         return;
     }
@@ -311,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     if (MODE == MODE_SINGLE) {
         for (int j = threadIdx.x; j < nc; j += kThreads) {
             double dc = colsum[j];
-            if (fabs(dc) <= tau) continue;
+            if (fabs(dc) <= TCOL(j)) continue;
             double rho = wsum[j] / dc;
             double ri = rint(rho);
             int64_t i = (int64_t)ri - 1;
@@ -329,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     if (nfr == 1 && nfc == 1) {
         if (threadIdx.x == 0) {
             double dc = colsum[fc], dr = rowsum[fr];
-            if (fabs(dc - dr) <= tau) {
+            if (fabs(dc - dr) <= (pc ? __dadd_rn(tcol[fc], trow[fr]) : tau)) {
                 T[(int64_t)fr * ts.lda + fc] -= dc;
                 atomicAdd(&st->corrected, 1ull);
                 record_event(st, step, EV_0D, r0 + fr, c0 + fc, dc);
@@ -341,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     } else if (nfr == 1 && nfc >= 2) {
         for (int j = threadIdx.x; j < nc; j += kThreads) {
             double dc = colsum[j];
-            if (fabs(dc) <= tau) continue;
+            if (fabs(dc) <= TCOL(j)) continue;
             T[(int64_t)fr * ts.lda + j] -= dc;
             atomicAdd(&st->corrected, 1ull);
             record_event(st, step, EV_ROW, r0 + fr, c0 + j, dc);
@@ -349,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     } else if (nfr >= 2 && nfc == 1) {
         for (int i = threadIdx.x; i < nr; i += kThreads) {
             double dr = rowsum[i];
-            if (fabs(dr) <= tau) continue;
+            if (fabs(dr) <= TROW(i)) continue;
             T[(int64_t)i * ts.lda + fc] -= dr;
             atomicAdd(&st->corrected, 1ull);
             record_event(st, step, EV_COL, r0 + i, c0 + fc, dr);
@@ -366,6 +393,8 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
         atomicAdd(&st->uncorrectable, 1ull);
         record_event(st, step, EV_UNCORR, r0, c0, 0.0);
     }
+#undef TCOL
+#undef TROW
 }
 
 __global__ void k_inject(double* A, int64_t lda, int64_t row, int64_t col, int64_t len, int along_row,
@@ -399,7 +428,7 @@ __global__ void k_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, dou
 // tau = tau_scale * 8 * u * n * g * max_i a_ii (left to right); u = 2^-53 for the
 // FP64 update, 2^-24 when the update accumulates in FP32 (mixed precision).
 __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                           double u, DevStatus* st) {
+                           double u, double coef, DevStatus* st) {
     __shared__ double red[32];
     double m = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -418,6 +447,15 @@ __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, d
         t *= (double)g;
         t *= m;
         st->tau = t;
+        if (coef > 0.0) {   // mixed precision: the FP64 term of the per-column thresholds
+            double t64 = tau_scale * 8.0;
+            t64 *= 0x1p-53;
+            t64 *= (double)n;
+            t64 *= (double)g;
+            t64 *= m;
+            st->tau64 = t64;
+            st->tau_coef = coef;
+        }
         // entries of the Schur complements are bounded by max a_ii, panel
         // entries by sqrt(max a_ii): the fixed-point verify bound
         const double bnd = fmax(m, sqrt(m));
@@ -499,8 +537,8 @@ cudaError_t launch_mirror_diag(double* A, int64_t lda, int64_t n, int64_t nb, do
 }
 
 cudaError_t launch_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, double tau_scale,
-                            DevStatus* st, cudaStream_t s, double unit_roundoff) {
-    k_tau_chol<<<1, 1024, 0, s>>>(A, lda, n, g, tau_scale, unit_roundoff, st);
+                            DevStatus* st, cudaStream_t s, double unit_roundoff, double tau_coef) {
+    k_tau_chol<<<1, 1024, 0, s>>>(A, lda, n, g, tau_scale, unit_roundoff, tau_coef, st);
     note_launch();
     return cudaGetLastError();
 }

@@ -302,8 +302,8 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     k_quant_panel(const double* __restrict__ P, int64_t lda, int64_t T0, int64_t n, int kb,
                   int64_t g, int64_t I0, uint16_t* __restrict__ Lq, double* __restrict__ sig,
                   double* __restrict__ tsum, int64_t tstride, int weighted,
-                  float* __restrict__ tsum32) {
-    extern __shared__ double qpart[];     // rank 0: [QCL][2][kb] slab column sums
+                  float* __restrict__ tsum32, float* __restrict__ tabs32) {
+    extern __shared__ double qpart[];     // rank 0: [QCL][3][kb] slab column sums
     __shared__ double red[8];
     __shared__ double cmax[QCL];          // rank 0: slab maxima
     cg::cluster_group cl = cg::this_cluster();
@@ -351,7 +351,7 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     const double rsig = use_mul ? ldexp(1.0, -ex) : 1.0;
     double* qp = cl.map_shared_rank(qpart, 0);
     for (int p = t; p < kb; p += 256) {
-        double s = 0.0, sw = 0.0;
+        double s = 0.0, sw = 0.0, sa = 0.0;
         for (int64_t r = s0; r < s1; ++r) {
             const double x = use_mul ? P[r * lda + p] * rsig : P[r * lda + p] / sigma;
             double xq;
@@ -368,19 +368,23 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
             Lq[(r - T0) * kb + p] = bits;
             s += xq;
             sw += (double)(r - r0 + 1) * xq;
+            sa += fabs(xq);
         }
-        qp[(2 * rank) * kb + p] = s;
-        qp[(2 * rank + 1) * kb + p] = sw;
+        qp[(3 * rank) * kb + p] = s;
+        qp[(3 * rank + 1) * kb + p] = sw;
+        qp[(3 * rank + 2) * kb + p] = sa;
     }
     cl.sync();
     if (rank != 0) return;
     if (t == 0) sig[I] = sigma;
     for (int p = t; p < kb; p += 256) {
-        double s = 0.0, sw = 0.0;
+        double s = 0.0, sw = 0.0, sa = 0.0;
         for (int c = 0; c < QCL; ++c) {
-            s += qpart[(2 * c) * kb + p];
-            sw += qpart[(2 * c + 1) * kb + p];
+            s += qpart[(3 * c) * kb + p];
+            sw += qpart[(3 * c + 1) * kb + p];
+            sa += qpart[(3 * c + 2) * kb + p];
         }
+        if (tabs32) tabs32[I * kb + p] = (float)sa;
         tsum[I * tstride + p] = s;
         if (weighted) tsum[I * tstride + kb + p] = sw;
         if (tsum32) {   // the FP32 operand of the border products, rounded once here
@@ -405,10 +409,13 @@ struct BorderSeg {
     int64_t M, N, K;
     // scale index of row i: (i + r_off) / r_div + r_base; of column j likewise
     int64_t r_off, r_div, r_base, c_off, c_div, c_base;
+    int a_abs, b_abs;   // the abs-checksum products use |A| and |B|
+    int plus;           // abs-checksums grow: C += instead of C -=
 };
+constexpr int MAX_BSEG = 4;
 struct BorderArgs {
-    BorderSeg seg[2];
-    int64_t tn[2], start[3];
+    BorderSeg seg[MAX_BSEG];
+    int64_t tn[MAX_BSEG], start[MAX_BSEG + 1];
     int nseg;
     int bf16;
     const double* sig;
@@ -426,7 +433,8 @@ __global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
     __shared__ float As[16][65], Bs[16][65];
     if (a.st->info != 0) return;
     const int64_t bid = blockIdx.x;
-    const int s = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    int s = 0;
+    while (s + 1 < a.nseg && bid >= a.start[s + 1]) ++s;
     const BorderSeg& g = a.seg[s];
     const int64_t local = bid - a.start[s];
     const int64_t i0 = (local / a.tn[s]) * 64, j0 = (local % a.tn[s]) * 64;
@@ -442,6 +450,8 @@ __global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
             const int64_t k = k0 + lk + u, i = i0 + lr, j = j0 + lr;
             pa[u] = (i < g.M && k < g.K) ? ld_op(g.A, g.a_half, a.bf16, i * g.lda + k) : 0.f;
             pb[u] = (j < g.N && k < g.K) ? ld_op(g.B, g.b_half, a.bf16, j * g.ldb + k) : 0.f;
+            if (g.a_abs) pa[u] = fabsf(pa[u]);
+            if (g.b_abs) pb[u] = fabsf(pb[u]);
         }
     };
     fetch(0);
@@ -477,7 +487,9 @@ __global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
             const int64_t j = j0 + tx + 16 * c;
             if (j >= g.N) continue;
             const double sc = a.sig[(j + g.c_off) / g.c_div + g.c_base];
-            g.C[i * g.ldc + j] -= (sr * sc) * (double)acc[r][c];
+            const double v = (sr * sc) * (double)acc[r][c];
+            if (g.plus) g.C[i * g.ldc + j] += v;
+            else g.C[i * g.ldc + j] -= v;
         }
     }
 }
@@ -501,11 +513,11 @@ cudaError_t get_encoder() {
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
                                int64_t g, int64_t I0, int64_t I1, int bf16, uint16_t* Lq,
                                double* sig, double* tsum, int64_t tstride, int weighted,
-                               cudaStream_t s, float* tsum32) {
+                               cudaStream_t s, float* tsum32, float* tabs32) {
     if (I1 <= I0) return cudaSuccess;
     if (kb > 512) return cudaErrorInvalidValue;
     static bool attr = false;
-    const size_t smem = sizeof(double) * 2 * QCL * 512;
+    const size_t smem = sizeof(double) * 3 * QCL * 512;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_quant_panel<true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -515,14 +527,14 @@ cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t need = sizeof(double) * 2 * QCL * (size_t)kb;
+    const size_t need = sizeof(double) * 3 * QCL * (size_t)kb;
     const unsigned grid = (unsigned)((I1 - I0) * QCL);
     if (bf16)
         k_quant_panel<true><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
-                                                    tstride, weighted, tsum32);
+                                                    tstride, weighted, tsum32, tabs32);
     else
         k_quant_panel<false><<<grid, 256, need, s>>>(P, lda, T0, n, (int)kb, g, I0, Lq, sig, tsum,
-                                                     tstride, weighted, tsum32);
+                                                     tstride, weighted, tsum32, tabs32);
     note_launch();
     return cudaGetLastError();
 }
@@ -590,6 +602,7 @@ cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, c
     a.st = st;
     int64_t total = 0;
     a.nseg = 0;
+    if (nseg > MAX_BSEG) return cudaErrorInvalidValue;
     for (int i = 0; i < nseg; ++i) {
         const BorderSegHost& h = segs[i];
         if (h.M <= 0 || h.N <= 0 || h.K <= 0) continue;
@@ -599,6 +612,7 @@ cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, c
         b.C = h.C; b.ldc = h.ldc; b.M = h.M; b.N = h.N; b.K = h.K;
         b.r_off = h.r_off; b.r_div = h.r_div; b.r_base = h.r_base;
         b.c_off = h.c_off; b.c_div = h.c_div; b.c_base = h.c_base;
+        b.a_abs = h.a_abs; b.b_abs = h.b_abs; b.plus = h.plus;
         a.tn[a.nseg] = (h.N + 63) / 64;
         a.start[a.nseg] = total;
         total += ((h.M + 63) / 64) * a.tn[a.nseg];

@@ -130,7 +130,12 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
         const int c0 = (NT ? nch - 1 - ci : ci) * CW;
         const int w = (nb - c0) < CW ? (nb - c0) : CW;
         const int c1 = c0 + w;
-        T acc[4] = {0, 0, 0, 0};
+        // each unknown's terms form one fused multiply-add chain in p order,
+        // starting from its right-hand side: the chunk's columns continue here
+        // from X and the substitution inside the chunk continues from them
+        T acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = (gq + u < w) ? X[gr * ldx + c0 + gq + u] : (T)0;
         const int pbeg = NT ? c1 : 0, pend = NT ? nb : c0;
         for (int p0 = pbeg; p0 < pend; p0 += CW) {
             __syncthreads();
@@ -151,13 +156,13 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
             for (int pp = 0; pp < CW; ++pp) {
                 T xv = (p0 + pp < pend) ? X[gr * ldx + p0 + pp] : (T)0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] = fma(xv, Ls[(gq + u) * (CW + 1) + pp], acc[u]);
+                for (int u = 0; u < 4; ++u) acc[u] = fma(-xv, Ls[(gq + u) * (CW + 1) + pp], acc[u]);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (gq + u < w) X[gr * ldx + c0 + gq + u] -= acc[u];
+            if (gq + u < w) X[gr * ldx + c0 + gq + u] = acc[u];
         // the chunk's diagonal block: Ls[q][p] = L[c0+q][c0+p] (p <= q) for L^T,
         // L[c0+p][c0+q] (p >= q) for L
         for (int e = t; e < CW * CW; e += TT) {
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
                 for (int jj = 0; jj < CW; ++jj) {
                     T v = xr[jj];
 #pragma unroll
-                    for (int p = 0; p < jj; ++p) v -= xv[p] * Ls[jj * (CW + 1) + p];
+                    for (int p = 0; p < jj; ++p) v = fma(-xv[p], Ls[jj * (CW + 1) + p], v);
                     xv[jj] = v / Ls[jj * (CW + 1) + jj];
                 }
 #pragma unroll
@@ -191,13 +196,13 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
             } else if (!NT) {
                 for (int jj = 0; jj < w; ++jj) {
                     T v = xr[jj];
-                    for (int p = 0; p < jj; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
+                    for (int p = 0; p < jj; ++p) v = fma(-xr[p], Ls[jj * (CW + 1) + p], v);
                     xr[jj] = v / Ls[jj * (CW + 1) + jj];
                 }
             } else {
                 for (int jj = w - 1; jj >= 0; --jj) {
                     T v = xr[jj];
-                    for (int p = jj + 1; p < w; ++p) v -= xr[p] * Ls[jj * (CW + 1) + p];
+                    for (int p = jj + 1; p < w; ++p) v = fma(-xr[p], Ls[jj * (CW + 1) + p], v);
                     xr[jj] = v / Ls[jj * (CW + 1) + jj];
                 }
             }
