@@ -480,6 +480,25 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
  * the memory their keys refer to, if the same addresses may be reused). */
 int abft_batched_graph_reset(void);
 
+/*
+ * abft_batched_partition -- split a batch of independent factorizations
+ * (abft_potrf_batched) over G GPUs, one process per GPU, so that every GPU
+ * gets about the same work.  Not in the paper (the batched form's multi-GPU
+ * split; the matrices are independent, so nothing is exchanged on the data
+ * path: each GPU factors its share, the statuses are gathered on the host).
+ * Longest processing time first on the work n_i^3 / 3: the matrices in
+ * decreasing work (ties: lower index first), each to the GPU with the least
+ * work so far (ties: lower GPU index).  The largest share exceeds the
+ * smallest by at most one matrix's work.  Host only, deterministic.
+ *   count, n   number of matrices and their orders (host, n_i >= 0)
+ *   G          number of GPUs (>= 1)
+ *   owner      host int32[count] out: the GPU of each matrix
+ *   load       host double[G] out, or NULL: each GPU's work in flops
+ * Errors: -1 count; -2 n; -3 G; -4 owner.
+ */
+int abft_batched_partition(int32_t count, const int64_t* n, int32_t G, int32_t* owner,
+                           double* load);
+
 /* Size of the built-in device scratch array used by abft_potrf_noalloc. */
 #define ABFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)   /* 16 MiB per GPU */
 

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "abft_symm_emu": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
     "abft_syrk_mixed": [_i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _vp,
                         ctypes.POINTER(_i32), _vp, _sz, _vp],
+    "abft_batched_partition": [_i32, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32),
+                               ctypes.POINTER(_dbl)],
     "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
                          ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }

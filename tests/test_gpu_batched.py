@@ -124,3 +124,33 @@ def test_batched_graph_key_holds_tau_scale():
         torch.cuda.synchronize()
         assert sum(s["detected"] for s in batch.statuses()) == expect
     abft.lib().abft_batched_graph_reset()
+
+
+def test_sharded_batch_equals_one_launch():
+    """The multi-GPU split run shard after shard on one GPU: each share of
+    abft_batched_partition factored by its own launch gives the same factors
+    and, gathered by matrix index, the same statuses as one launch over all."""
+    from paper_2301_03166_b300 import shard
+    count, G = 300, 3
+    batch, mats, faults = make_batch(count, torch.float64, nb=64, fault_every=20)
+    abft.potrf_batched(batch)
+    torch.cuda.synchronize()
+    ref = batch.status.cpu().numpy()
+    owner, load = shard.partition(batch.sizes, G)
+    assert load.max() / load.min() < 1.05
+    parts_ids, parts_st = [], []
+    for g in range(G):
+        ids = shard.shard_ids(owner, g)
+        sz = [batch.sizes[i] for i in ids]
+        offs = np.concatenate([[0], np.cumsum(np.asarray(sz, dtype=np.int64) ** 2)[:-1]])
+        buf = torch.cat([torch.from_numpy(mats[i].reshape(-1)) for i in ids]).to(DEV)
+        loc = {int(i): k for k, i in enumerate(ids)}
+        sb = abft.Batch(buf, sz, offs, 64, {loc[i]: f for i, f in faults.items() if i in loc})
+        abft.potrf_batched(sb)
+        torch.cuda.synchronize()
+        for k, i in enumerate(ids):
+            assert torch.equal(sb.matrix(k), batch.matrix(int(i)))
+        parts_ids.append(ids)
+        parts_st.append(sb.status.cpu().numpy())
+    full = shard.gather_statuses(np.concatenate(parts_ids), np.concatenate(parts_st), count)
+    assert np.array_equal(full, ref)
