@@ -499,6 +499,27 @@ int abft_batched_graph_reset(void);
 int abft_batched_partition(int32_t count, const int64_t* n, int32_t G, int32_t* owner,
                            double* load);
 
+/*
+ * abft_wait_selftest -- exercises the give-up path of the library's bounded
+ * waits on purpose-built cases (no counterpart in the paper; the failure
+ * path of every persistent and cooperative kernel).  Every device-side wait
+ * of the library is bounded: the cooperative kernels' grid barrier gives up
+ * after 2 s, the tensor-core kernels' mbarrier waits after 1 s; a CTA that
+ * gives up records a timeout in the call's status block, releases its tensor
+ * memory and returns, and the call returns ABFT_ERR_TIMEOUT.  Here the limit
+ * is limit_ns (1 .. 2e9) and the case is one of
+ *   0  two CTAs at one grid barrier, one never arrives  -> ABFT_ERR_TIMEOUT
+ *   1  one CTA holding 32 TMEM columns waits on an mbarrier that gets one of
+ *      its two arrivals (it frees the columns after giving up) -> ABFT_ERR_TIMEOUT
+ *   2, 3  the same with every arrival (the waits complete)  -> 0
+ * error_out (host, nullable) receives the status block's error code (0 none,
+ * 1 grid barrier, 2 mbarrier).  Synchronizes the stream.  Workspace query
+ * protocol as abft_potrf (one status block).  Errors: -1 which; -2 limit_ns;
+ * -5 workspace.
+ */
+int abft_wait_selftest(int32_t which, int64_t limit_ns, int32_t* error_out, void* ws,
+                       size_t* ws_bytes, void* stream);
+
 /* Size of the built-in device scratch array used by abft_potrf_noalloc. */
 #define ABFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)   /* 16 MiB per GPU */
 

@@ -78,6 +78,7 @@ _SIGNATURES = {
                         ctypes.POINTER(_i32), _vp, _sz, _vp],
     "abft_batched_partition": [_i32, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32),
                                ctypes.POINTER(_dbl)],
+    "abft_wait_selftest": [_i32, _i64, ctypes.POINTER(_i32), _vp, _sz, _vp],
     "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
                          ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }
@@ -271,6 +272,21 @@ def syrk_mixed(P, C, g, dtype=MIXED_BF16, workspace=None, stream=None, sync=True
     if not sync:
         return Pq, sig
     return Pq.cpu().numpy().view(np.uint16), sig.cpu().numpy()
+
+
+def wait_selftest(which, limit_ns=1000000, device="cuda", stream=None):
+    """Run one case of abft_wait_selftest; returns (return code, error code)."""
+    L = lib()
+    need = ctypes.c_size_t(0)
+    rc = L.abft_wait_selftest(which, limit_ns, None, None, ctypes.byref(need), None)
+    if rc < 0 and rc > ERR_UNCORRECTABLE:
+        raise AbftError(rc, strerror(rc))
+    ws = torch.zeros(max(256, need.value), dtype=torch.uint8, device=device)
+    size = ctypes.c_size_t(ws.numel())
+    err = _i32(0)
+    rc = L.abft_wait_selftest(which, limit_ns, ctypes.byref(err), ctypes.c_void_p(ws.data_ptr()),
+                              ctypes.byref(size), _stream(stream))
+    return rc, err.value
 
 
 def _modes_array(modes, n, nb):

@@ -45,7 +45,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks,
-                                             unsigned long long& passed) {
+                                             unsigned long long& passed,
+                                             unsigned long long limit_ns = kBarrierNs) {
     // bar_count only grows during a launch: barrier number `passed` (1, 2, ...)
     // is complete once every CTA has added its arrival, i.e. at passed * nblocks,
     // so the last arrival's own increment releases the waiters (no reset and no
@@ -63,7 +64,7 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks
             volatile unsigned long long* vc = &st->bar_count;
             const unsigned long long t0 = global_ns();
             while (*vc < target) {
-                if (global_ns() - t0 > kBarrierNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicExch(&st->error, 1);
                     ok = 0;
                     break;

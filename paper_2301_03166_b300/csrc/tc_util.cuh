@@ -30,8 +30,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Bounded parity wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded parity wait; false on timeout (after limit_ns, kWaitNs by default).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
     const uint32_t addr = smem_u32(bar);
     unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
@@ -47,7 +48,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         if ((it & 255u) == 0) {
             unsigned long long t = global_ns();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > kWaitNs) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
 }

@@ -107,3 +107,26 @@ def test_sched_arguments_on_host():
     bad = (ctypes.c_int32 * 8)(0, 0, 1, 3, 2, 2, 1, 0)
     assert L.abft_potrf_sched(1024, 128, 0, bad, None, 1024, None, 0, 1.0, None, None,
                               ctypes.byref(need), None) == -4
+
+
+def test_added_entry_points_check_arguments_on_host():
+    L = abft.lib()
+    need = ctypes.c_size_t(0)
+    # abft_syrk_mixed: workspace query and argument checks
+    assert L.abft_syrk_mixed(300, 64, 128, abft.MIXED_BF16, None, 64, None, 300, None, None, None,
+                             None, ctypes.byref(need), None) == 0 and need.value > 0
+    assert L.abft_syrk_mixed(300, 48, 128, abft.MIXED_BF16, None, 64, None, 300, None, None, None,
+                             None, ctypes.byref(need), None) == -2
+    assert L.abft_syrk_mixed(300, 64, 96, abft.MIXED_BF16, None, 64, None, 300, None, None, None,
+                             None, ctypes.byref(need), None) == -3
+    assert L.abft_syrk_mixed(300, 64, 128, abft.F64, None, 64, None, 300, None, None, None,
+                             None, ctypes.byref(need), None) == -4
+    # abft_wait_selftest: host-side checks only (the cases themselves need a GPU)
+    assert L.abft_wait_selftest(0, 1000, None, None, ctypes.byref(need), None) == 0
+    assert L.abft_wait_selftest(4, 1000, None, None, ctypes.byref(need), None) == -1
+    assert L.abft_wait_selftest(0, 0, None, None, ctypes.byref(need), None) == -2
+    # abft_batched_partition: host only
+    n = (ctypes.c_int64 * 3)(10, 20, 30)
+    own = (ctypes.c_int32 * 3)()
+    assert L.abft_batched_partition(3, n, 0, own, None) == -3
+    assert L.abft_batched_partition(3, n, 2, own, None) == 0 and list(own) == [1, 1, 0]
