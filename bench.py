@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the BF16/FP16 + IR solve")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the GP forward + backward timings (n = 4096, 16384)")
     p.add_argument("--no-lu-qr", action="store_true", help="skip the LU and QR timings")
     p.add_argument("--no-batched", action="store_true", help="skip the batched timings")
     p.add_argument("--no-lookahead", action="store_true",
@@ -430,7 +432,27 @@ def run_ours(args, ws, rank, local):
                 "traffic": (traffic * args.steps / tmu_launches) if traffic else None,
                 "traffic_note": "bytes per launch, scaled from an ncu capture at n=4096 by updated C elements",
                 "tmu_share_of_step": tmu_ms / ms if ms > 0 else None,
-                "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
+                # event pairs of the timed steps; with look-ahead the PD and panel
+                # solve run on the caller's stream beside the rest of the update
+                # on a side stream, so these intervals overlap (their sum can
+                # exceed the step) and PD / PU include waiting for SMs
+                "phase_stream_ms_per_step_overlapping": {k: v[0] / args.steps
+                                                         for k, v in phases.items()}}
+    # a truthful breakdown: one more step with look-ahead off (every phase on
+    # the caller's stream, one after another), its phases and its wall time
+    prev_la = abft.set_lookahead(False)
+    abft.timing_enable(True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    seq = abft.timing_read()
+    abft.timing_enable(False)
+    abft.set_lookahead(prev_la)
+    roofline["phase_ms_sequential_step"] = {k: v[0] for k, v in seq.items()}
+    roofline["sequential_step_ms"] = e0.elapsed_time(e1)
+    roofline["tmu_share_of_sequential_step"] = seq["tmu"][0] / e0.elapsed_time(e1)
 
     overhead = None
     if not args.no_overhead:
@@ -501,7 +523,9 @@ def run_ours(args, ws, rank, local):
                     "events_match_injected": [(e[0], e[1], e[2], e[3]) for e in rep_e["loc"]] == expected,
                     "probe_backward_err": probe(Le), "probe_backward_err_fp64": probe(Lref),
                     "max_rel_diff_vs_fp64_factor": float((Le - Lref).abs().max() / Lref.abs().max()),
-                    "phase_ms_per_step": {k: vv[0] / args.steps for k, vv in ph_e.items()},
+                    # overlapping stream intervals (look-ahead on), as in the roofline
+                    "phase_stream_ms_per_step_overlapping": {k: vv[0] / args.steps
+                                                             for k, vv in ph_e.items()},
                     "tmu_tensor_tflops_equiv": tmu_flops(n, nb) / (ph_e["tmu"][0] / args.steps * 1e-3) / 1e12}
         del Lref, Le, v, Av
 
@@ -803,6 +827,61 @@ def run_ours(args, ws, rank, local):
         abft.lib().abft_batched_graph_reset()
         del base
 
+    adjoint = None
+    if not args.no_adjoint:
+        # GP configuration: X n x 8 iid N(0,1), K = exp(-|xi - xj|^2 / 2) + 1e-2 I,
+        # y iid N(0,1), loss = y^T K^{-1} y / 2 + logdet K / 2; forward (ABFT
+        # Cholesky, solve, logdet) and backward (the hand-written adjoints)
+        # through torch.autograd, timed with CUDA events.  Gradient error: against
+        # the FP64 closed form (K^{-1} - alpha alpha^T)/2 on the host (n = 4096),
+        # and d loss / d lengthscale against central differences (n = 16384).
+        from paper_2301_03166_b300 import autograd as ag
+        adjoint = {}
+        for na in (4096, 16384):
+            Xn, yn = W.gp_inputs(na, 8, seed=1004)
+            Xg = torch.from_numpy(Xn).to(dev)
+            yg = torch.from_numpy(yn).to(dev)
+            def kernel(ell):
+                sq = (Xg * Xg).sum(1)
+                D = torch.clamp(sq[:, None] + sq[None, :] - 2.0 * Xg @ Xg.T, min=0.0)
+                return torch.exp(-D / (2.0 * ell ** 2)) + 1e-2 * torch.eye(na, dtype=torch.float64,
+                                                                          device=dev)
+            K0 = kernel(1.0)
+            entry = {}
+            for tag, dt in (("fp64", abft.F64), ("fp64_emulated", abft.F64_EMU)):
+                Kr = K0.clone().requires_grad_(True)
+                def fwd():
+                    return ag.gp_negative_log_likelihood_terms(Kr, yg, 256, dtype=dt)
+                def fwd_bwd():
+                    Kr.grad = None
+                    loss = fwd()
+                    loss.backward()
+                    return loss
+                ms_f, _ = timed(lambda: fwd().detach(), 1, 1)
+                ms_fb, loss = timed(fwd_bwd, 1, 1)
+                e = {"ms_forward": ms_f, "ms_forward_backward": ms_fb, "ms_backward": ms_fb - ms_f,
+                     "loss": float(loss.item())}
+                if na == 4096:
+                    Kh = K0.cpu().numpy()
+                    Kinv = np.linalg.inv(Kh)
+                    al = Kinv @ yn
+                    Gc = 0.5 * (Kinv - np.outer(al, al))
+                    e["grad_rel_err_vs_closed_form"] = float(
+                        np.linalg.norm(Kr.grad.cpu().numpy() - Gc) / np.linalg.norm(Gc))
+                else:
+                    ell = torch.tensor(1.0, dtype=torch.float64, device=dev, requires_grad=True)
+                    ag.gp_negative_log_likelihood_terms(kernel(ell), yg, 256, dtype=dt).backward()
+                    h = 1e-6
+                    with torch.no_grad():
+                        lp = ag.gp_negative_log_likelihood_terms(kernel(1.0 + h), yg, 256, dtype=dt)
+                        lm = ag.gp_negative_log_likelihood_terms(kernel(1.0 - h), yg, 256, dtype=dt)
+                    fd = (lp.item() - lm.item()) / (2 * h)
+                    e["dloss_dlengthscale_rel_err_vs_fd"] = abs(ell.grad.item() - fd) / max(1.0, abs(fd))
+                entry[tag] = e
+                del Kr
+            adjoint[f"n{na}"] = entry
+            del K0, Xg, yg
+
     e2e = None
     if not args.no_e2e:
         A0h = A0.cpu().pin_memory()
@@ -858,6 +937,7 @@ def run_ours(args, ws, rank, local):
                      "max_ratio": rep["max_ratio"], **(overhead or {})},
             "fp64_emulated": emulated,
             "mixed_precision_ir": mixed, "lookahead": lookahead, "conditioned": conditioned,
+            "adjoint": adjoint,
             "campaign": campaign,
             "lu_qr": lu_qr,
             "batched": batched,

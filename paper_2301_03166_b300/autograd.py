@@ -14,9 +14,9 @@ class Cholesky(torch.autograd.Function):
     """L = chol(A) (lower, zero above the diagonal) with ABFT checksums."""
 
     @staticmethod
-    def forward(ctx, A, nb=256, mode=abft.FULL):
+    def forward(ctx, A, nb=256, mode=abft.FULL, dtype=abft.F64):
         L = A.detach().contiguous().clone()
-        rc, rep = abft.potrf(L, nb, mode)
+        rc, rep = abft.potrf(L, nb, mode, dtype=dtype)
         if rc != 0:
             raise abft.AbftError(rc, abft.strerror(rc))
         abft.tril_(L)
@@ -28,7 +28,7 @@ class Cholesky(torch.autograd.Function):
     def backward(ctx, Lbar):
         (L,) = ctx.saved_tensors
         G = abft.potrf_backward(L, Lbar.contiguous(), ctx.nb, sym=True)
-        return G, None, None
+        return G, None, None, None
 
 
 class CholeskySolve(torch.autograd.Function):
@@ -67,8 +67,10 @@ class LogdetFromCholesky(torch.autograd.Function):
         return Lbar
 
 
-def cholesky(A, nb=256, mode=abft.FULL):
-    return Cholesky.apply(A, nb, mode)
+def cholesky(A, nb=256, mode=abft.FULL, dtype=abft.F64):
+    """dtype ABFT_F64 (FP64 update) or ABFT_F64_EMU (FP64-accurate update on
+    the BF16 tensor cores, nb 128 or 256)."""
+    return Cholesky.apply(A, nb, mode, dtype)
 
 
 def cholesky_solve(L, B, nb=256):
@@ -79,8 +81,8 @@ def logdet_from_cholesky(L):
     return LogdetFromCholesky.apply(L)
 
 
-def gp_negative_log_likelihood_terms(K, y, nb=256):
+def gp_negative_log_likelihood_terms(K, y, nb=256, dtype=abft.F64):
     """loss = y^T K^{-1} y / 2 + logdet(K) / 2 through the ABFT Cholesky."""
-    L = cholesky(K, nb)
+    L = cholesky(K, nb, dtype=dtype)
     alpha = cholesky_solve(L, y.reshape(-1, 1), nb)
     return 0.5 * (y.reshape(-1, 1) * alpha).sum() + 0.5 * logdet_from_cholesky(L)
