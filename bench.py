@@ -62,10 +62,12 @@ def parse():
                         "look-ahead, per-iteration time prediction as a self-check)")
     p.add_argument("--no-emulated", action="store_true",
                    help="skip the FP64-accurate factorization with the BF16 tensor-core update")
-    p.add_argument("--conditioned", action="store_true",
-                   help="add the conditioned mixed-precision solves: A = Q diag(sigma) Q^T with "
-                        "kappa 1e2, 1e6, 1e10, block 512, GMRES-IR (BF16 / FP16) vs the FP64 form")
-    p.add_argument("--cond-n", type=int, default=16384)
+    p.add_argument("--no-conditioned", action="store_true",
+                   help="skip the conditioned solves: A = Q diag(sigma) Q^T with kappa 1e2, 1e6, "
+                        "1e10, n = --cond-n, block 512, 16 right-hand sides; GMRES-IR on the "
+                        "BF16 / FP16 factor and refinement on the FP64-accurate factor, against "
+                        "the FP64 form")
+    p.add_argument("--cond-n", type=int, default=32768)
     p.add_argument("--campaign", action="store_true",
                    help="add the fault campaign: share of correct factorizations and time per "
                         "factorization for no / single-side / full / adaptive checksums")
@@ -605,46 +607,69 @@ def run_ours(args, ws, rank, local):
         lookahead["prediction"] = pred_err
 
     conditioned = None
-    if args.conditioned:
-        # A = Q diag(sigma) Q^T, sigma geometric with condition kappa, block 512,
-        # 16 N(0,1) right-hand sides, target backward error 1e-12; time to
-        # solution of the FP64 form (FP64 ABFT potrf + potrs) and of GMRES-IR
-        # preconditioned by the BF16 / FP16 ABFT factor (automatic shift), and
-        # the error of each against the FP64 form's solution.
+    if not args.no_conditioned:
+        # Conditioned solves: A = Q diag(sigma) Q^T, sigma_i = kappa^(-i/(n-1)),
+        # 16 N(0,1) right-hand sides, target backward error 1e-12, block 512.
+        # At n = 32768 Q is a product of random butterfly networks (the QR of a
+        # Gaussian matrix would take minutes on the FP64 pipe; same spectrum).
+        # Time to solution of the FP64 form (FP64 ABFT potrf + potrs), of
+        # GMRES-IR preconditioned by the BF16 / FP16 ABFT factor (automatic
+        # shift), and of refinement on the FP64-accurate factor (ABFT_F64_EMU,
+        # block 256: the slice update takes at most 256 columns), each with its
+        # backward error and its error against the FP64 form's solution.
         nc, nbc = args.cond_n, 512
         Bc = torch.from_numpy(W.rhs(nc, 16, seed=1003)).to(dev)
         Xc = torch.empty_like(Bc)
-        conditioned = {"n": nc, "nb": nbc, "tol": 1e-12}
+        conditioned = {"n": nc, "nb": nbc, "tol": 1e-12, "nrhs": 16,
+                       "matrix": ("Q diag(sigma) Q^T, Q = 2 random butterfly networks"
+                                  if nc & (nc - 1) == 0 else "Q diag(sigma) Q^T, Q from QR(N(0,1))")}
         for kappa in (1e2, 1e6, 1e10):
-            Ac = W.spd_kappa_torch(nc, kappa, seed=1002, device=dev)
+            if nc & (nc - 1) == 0:
+                Ac = W.spd_kappa_butterfly_torch(nc, kappa, seed=1002, device=dev)
+            else:
+                Ac = W.spd_kappa_torch(nc, kappa, seed=1002, device=dev)
             Lc = torch.empty_like(Ac)
+            anorm = float(Ac.abs().sum(1).amax())
+            def eta_of(X):
+                R = Bc - Ac @ X
+                return float((R.abs().amax(0) / (anorm * X.abs().amax(0) + Bc.abs().amax(0))).max())
             def fp64_form():
                 Lc.copy_(Ac)
                 abft.potrf(Lc, nbc, abft.FULL, workspace=wsp)
                 Xc.copy_(Bc)
                 abft.potrs(Lc, Xc, nbc, abft.F64)
-            ms64, _ = timed(fp64_form, 1, 1)
+            ms64, _ = timed(fp64_form, 1, 0)   # one run (about 12 s at n = 32768)
             X64 = Xc.clone()
-            R64 = Bc - Ac @ X64
-            eta64 = float((R64.abs().amax(0) / (Ac.abs().sum(1).amax() * X64.abs().amax(0)
-                                                + Bc.abs().amax(0))).max())
-            entry = {"fp64_ms_to_solution": ms64, "fp64_backward_err": eta64}
-            for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
-                maxit = 3 if kappa >= 1e10 else 20
-                def gm():
-                    return abft.posv_gmres_ir(Ac, Bc, nbc, dt, abft.FULL, tol=1e-12, maxit=maxit,
-                                              m=60, inner_tol=1e-6, L=Lc, X=Xc, workspace=wsp)
-                ms_g, res = timed(gm, 1, 1)
+            entry = {"fp64_ms_to_solution": ms64, "fp64_backward_err": eta_of(X64)}
+            runs = [("bf16", abft.MIXED_BF16, nbc, True), ("f16", abft.MIXED_F16, nbc, True),
+                    ("fp64_emulated_ir", abft.F64_EMU, 256, False)]
+            for name, dt, nbr, gmres in runs:
+                if gmres:
+                    maxit = 3 if kappa >= 1e10 else 20
+                    def run():
+                        return abft.posv_gmres_ir(Ac, Bc, nbr, dt, abft.FULL, tol=1e-12,
+                                                  maxit=maxit, m=60, inner_tol=1e-6, L=Lc, X=Xc,
+                                                  workspace=wsp)
+                else:
+                    def run():
+                        return abft.posv_ir(Ac, Bc, nbr, dt, abft.FULL, tol=1e-12, maxit=10,
+                                            L=Lc, X=Xc, workspace=wsp)
+                ms_g, res = timed(run, 1, 1)
                 rc_g, _, _, rep_g = res
                 err = float((Xc - X64).abs().max() / X64.abs().max())
-                entry[name] = {"ms_to_solution": ms_g, "speedup_vs_fp64": ms64 / ms_g,
-                               "rc": rc_g, "backward_err": rep_g["backward_err"],
-                               "reached_tol": rep_g["backward_err"] <= 1e-12,
-                               "ir_iters": rep_g["ir_iters"], "gmres_iters": rep_g["gmres_iters"],
-                               "attempts": rep_g["attempts"], "shift": rep_g["shift"],
-                               "rel_err_vs_fp64_form": err}
+                e = {"ms_to_solution": ms_g, "speedup_vs_fp64": ms64 / ms_g, "nb": nbr,
+                     "rc": rc_g, "backward_err": rep_g["backward_err"],
+                     "reached_tol": rep_g["backward_err"] <= 1e-12,
+                     "ir_iters": rep_g["ir_iters"], "rel_err_vs_fp64_form": err}
+                if gmres:
+                    e.update({"gmres_iters": rep_g["gmres_iters"], "attempts": rep_g["attempts"],
+                              "shift": rep_g["shift"]})
+                entry[name] = e
+            emu_ms = entry["fp64_emulated_ir"]["ms_to_solution"]
+            for name in ("bf16", "f16"):
+                entry[name]["speedup_vs_fp64_emulated_ir"] = emu_ms / entry[name]["ms_to_solution"]
             conditioned[f"{kappa:.0e}"] = entry
-            del Ac, Lc, X64, R64
+            del Ac, Lc, X64
         del Bc, Xc
 
     campaign = None

@@ -320,14 +320,17 @@ int abft_symm_emu(int64_t n, int64_t nrhs, const double* A, int64_t lda, const d
  * dtype followed by iterative refinement (not in the paper: the precision
  * form added on top of it).  L := A (lower triangle copied), abft_potrf(L),
  * X = L^{-T} L^{-1} B, then repeat: R = B - A X in FP64 (A symmetric, read
- * from its lower triangle; for the 16-bit dtypes with n a multiple of 32 the
- * products A X are FP64-accurate sums of exact BF16 slice products on the
+ * from its lower triangle; for the 16-bit dtypes and ABFT_F64_EMU with n a
+ * multiple of 32 the products A X are FP64-accurate sums of exact BF16 slice
+ * products on the
  * tensor cores -- A split once per call into 8 slices of its full rows, n^2
  * 16 bytes of workspace -- with an error below that of the same dot products
  * in FP64 arithmetic), eta = max_r ||R_r||_inf / (||A||_inf ||X_r||_inf +
  * ||B_r||_inf); stop when eta <= tol or after maxit corrections; otherwise
- * D = L^{-T} L^{-1} R (FP32 for the mixed dtypes, FP64 for ABFT_F64) and
- * X += D.  rep (optional) receives the factorization report plus ir_iters and
+ * D = L^{-T} L^{-1} R (FP32 for the mixed dtypes, FP64 for ABFT_F64 and
+ * ABFT_F64_EMU, whose factor an FP32 solve would not use) and X += D.
+ * ABFT_F64_EMU (nb 128 or 256) suits ill-conditioned A: its factor is as
+ * accurate as the FP64 one, so refinement converges while kappa u64 << 1.  rep (optional) receives the factorization report plus ir_iters and
  * backward_err (max over right-hand sides).  The call synchronizes the stream
  * once per refinement step (to read eta).
  *   A, lda     SPD matrix (device, lower triangle read, not modified)

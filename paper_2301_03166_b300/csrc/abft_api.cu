@@ -1185,17 +1185,18 @@ struct IrWs {
 IrWs ir_ws(int64_t n, int64_t nb, int mode, int32_t dtype) {
     IrWs w{};
     const bool mixed = dtype == ABFT_MIXED_BF16 || dtype == ABFT_MIXED_F16;
+    const bool emu = dtype == ABFT_F64_EMU;
     size_t off = 0;
-    w.chol = off; off = align_up(off + chol_ws(n, nb, mode, mixed).total);
+    w.chol = off; off = align_up(off + chol_ws(n, nb, mode, mixed, emu).total);
     w.solve = off; off = align_up(off + potrs_ws_bytes(n, ABFT_F32));
     w.R = off; off = align_up(off + sizeof(double) * (size_t)n * 16);
     w.P = off; off = align_up(off + sizeof(double) * (size_t)kSplit * (size_t)n * 16);
     w.rs = off; off = align_up(off + sizeof(double) * (size_t)n);
     w.norms = off; off = align_up(off + sizeof(unsigned long long) * 64);
     w.eta = off; off = align_up(off + sizeof(double));
-    // the 16-bit factorizations refine with an FP64-accurate residual from
-    // BF16 slices of A (FP64 factorizations keep the FP64 residual)
-    w.emu_resid = mixed && resid_emu_supported(n);
+    // the 16-bit and FP64-accurate factorizations refine with an FP64-accurate
+    // residual from BF16 slices of A (FP64 factorizations keep the FP64 residual)
+    w.emu_resid = (mixed || emu) && resid_emu_supported(n);
     w.re = off; off = align_up(off + (w.emu_resid ? resid_emu_bytes(n) : 0));
     w.total = off;
     return w;
@@ -1301,7 +1302,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     if (n < 0) return -1;
     if (nrhs < 0) return -2;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -3;
-    if (dtype < 0 || dtype > 3 || dtype == ABFT_F32) return dtype == ABFT_F32 ? ABFT_ERR_UNSUPPORTED : -4;
+    if (dtype < 0 || dtype > 4 || dtype == ABFT_F32) return dtype == ABFT_F32 ? ABFT_ERR_UNSUPPORTED : -4;
     if (mode < ABFT_MODE_NONE || mode > ABFT_MODE_FULL) return -5;
     const bool needp = ws != nullptr && n > 0;
     if (needp && A == nullptr) return -6;
@@ -1315,6 +1316,9 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
     if (!(tol >= 0.0)) return -14;
     if (maxit < 0) return -15;
     if (ws_bytes == nullptr) return -22;
+    // the solves run in FP64 for the FP64 and FP64-accurate factors (their
+    // accuracy would be lost in FP32 solves), in FP32 for the 16-bit ones
+    const int32_t sdt = (dtype == ABFT_F64 || dtype == ABFT_F64_EMU) ? ABFT_F64 : ABFT_F32;
     const IrWs w = ir_ws(n, nb, mode, dtype);
     size_t pws = 0;
     int rc = abft_potrf(n, nb, dtype, mode, L, ldl, faults, nfaults, tau_scale, nullptr, nullptr,
@@ -1362,8 +1366,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
         // X0 = L^{-T} L^{-1} B
         timing_mark(PH_SOLVE, 1, s);
         ABFT_CUDA_TRY(launch_copy_d2d(B + r0, ldb, X + r0, ldx, n, nr, s));
-        rc = potrs_run(n, nr, nb, dtype == ABFT_F64 ? ABFT_F64 : ABFT_F32, L, ldl, X + r0, ldx, sws, s,
-                       prepared);
+        rc = potrs_run(n, nr, nb, sdt, L, ldl, X + r0, ldx, sws, s, prepared);
         if (rc != ABFT_OK) return rc;
         prepared = true;
         int32_t it = 0;
@@ -1382,7 +1385,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
             if (eta <= tol || it >= maxit || !(eta == eta)) break;
             // correction D = L^{-T} L^{-1} R in the solve precision, X += D
             // the inverses of L's diagonal blocks are still in inv from potrs_run
-            if (dtype == ABFT_F64) {
+            if (sdt == ABFT_F64) {
                 ABFT_CUDA_TRY(launch_potrs_f64(n, nr, nb, L, ldl, R, 16, (double*)inv, s, true));
                 ABFT_CUDA_TRY(launch_add_f64(X + r0, ldx, R, 16, n, nr, s));
             } else {
@@ -1392,7 +1395,7 @@ int abft_posv_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32_t mod
                 ABFT_CUDA_TRY(launch_add_f32(X + r0, ldx, Yf, 16, n, nr, s));
             }
             cudaError_t ce = cudaSuccess;
-            const int serr = potrs_error(inv, n, dtype == ABFT_F64, s, &ce);
+            const int serr = potrs_error(inv, n, sdt == ABFT_F64, s, &ce);
             ABFT_CUDA_TRY(ce);
             if (serr) return ABFT_ERR_TIMEOUT;
         }

@@ -110,6 +110,48 @@ def spd_kappa_torch(n, kappa, seed=1002, device="cuda"):
     return 0.5 * (A + A.T)
 
 
+def spd_kappa_butterfly_torch(n, kappa, seed=1002, device="cuda", passes=2):
+    """A = Q diag(sigma) Q^T with sigma_i = kappa^(-i/(n-1)) for the largest
+    orders (n a power of two), where the QR of an n x n Gaussian matrix would
+    cost minutes on the FP64 pipe.  Q is a product of `passes` random butterfly
+    networks -- log2(n) levels of Givens rotations pairing index i with
+    i + 2^l, angles uniform in [0, 2 pi) -- with a random symmetric
+    permutation after each; the eigenvalues start in a random order on the
+    diagonal.  Dense, with exactly the spectrum sigma up to FP64 rounding, in
+    O(passes n^2 log n) operations (input construction, float64, on `device`)."""
+    import math
+    import torch
+    lv = n.bit_length() - 1
+    if n < 2 or (1 << lv) != n:
+        raise ValueError("n must be a power of two")
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    sig = kappa ** (-torch.arange(n, device=device, dtype=torch.float64) / (n - 1))
+    A = torch.diag(sig[torch.randperm(n, generator=g, device=device)])
+    for _ in range(passes):
+        for l in range(lv):
+            h = 1 << l
+            th = torch.rand(n // 2, generator=g, device=device, dtype=torch.float64) * (2 * math.pi)
+            c, s = torch.cos(th).view(n // (2 * h), h), torch.sin(th).view(n // (2 * h), h)
+            # rows i and i + h of each pair: A <- G A
+            V = A.view(n // (2 * h), 2, h, n)
+            a0 = V[:, 0].clone()
+            a1 = V[:, 1].clone()
+            V[:, 0] = c[:, :, None] * a0 - s[:, :, None] * a1
+            V[:, 1] = s[:, :, None] * a0 + c[:, :, None] * a1
+            # the same rotation on the columns: A <- A G^T
+            Wc = A.view(n, n // (2 * h), 2, h)
+            b0 = Wc[:, :, 0].clone()
+            b1 = Wc[:, :, 1].clone()
+            Wc[:, :, 0] = c[None] * b0 - s[None] * b1
+            Wc[:, :, 1] = s[None] * b0 + c[None] * b1
+            del a0, a1, b0, b1
+        p = torch.randperm(n, generator=g, device=device)
+        A = A.index_select(0, p).index_select(1, p)
+    A = 0.5 * (A + A.T)
+    return A
+
+
 def rhs(n, nrhs=16, seed=1003):
     return rng(seed).standard_normal((n, nrhs))
 
