@@ -257,7 +257,13 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         }
         __syncthreads();
         if (mrows <= 0) break;
-        // ---- PU: x L^T = a for the panel rows and the checksum rows (one thread per row)
+        // ---- PU: x L^T = a for the panel rows and the checksum rows, one thread
+        // per row.  A block with rows below it is never ragged (kb = B, a
+        // multiple of 32), so the row's unknowns are solved 32 at a time in
+        // registers: each chunk first takes the terms of the earlier chunks
+        // (re-read from the row, which this thread wrote), then substitutes
+        // inside the chunk; every unknown's terms form one fused multiply-add
+        // chain in p order.
         const int ncs = check ? 2 * (nt - k - 1) : 0;
         for (int rr = t; rr < mrows + ncs; rr += BT) {
             T* row;
@@ -266,10 +272,24 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 int c = rr - mrows, I = k + 1 + c / 2;
                 row = ((c & 1) ? S.Cw : S.Cc) + I * MAXN + K0;
             }
-            for (int j = 0; j < kb; ++j) {
-                T v = row[j];
-                for (int p = 0; p < j; ++p) v -= row[p] * sL[j][p];
-                row[j] = v / sL[j][j];
+            for (int c0 = 0; c0 < B; c0 += 32) {
+                T x[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) x[q] = row[c0 + q];
+                for (int p = 0; p < c0; ++p) {
+                    const T xp = row[p];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) x[q] = fma(-xp, sL[c0 + q][p], x[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    T v = x[q];
+#pragma unroll
+                    for (int pp = 0; pp < q; ++pp) v = fma(-x[pp], sL[c0 + q][c0 + pp], v);
+                    x[q] = v / sL[c0 + q][c0 + q];
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) row[c0 + q] = x[q];
             }
         }
         __syncthreads();
@@ -297,15 +317,35 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     sJ[j][p] = (j < nc) ? A[(int64_t)(c0 + j) * lda + K0 + p] : (T)0;
                 }
                 __syncthreads();
+                // register tile: thread (tx, ty) owns rows ty + 16 a and columns
+                // tx + 16 b (a, b < B / 16); per p, B / 8 shared loads feed
+                // (B / 16)^2 fused multiply-adds
+                constexpr int R = B / 16;
                 const int tx = t & 15, ty = t >> 4;
-                for (int a = 0; a < B / 16; ++a)
-                    for (int b = 0; b < B / 16; ++b) {
+                T acc[R][R];
+#pragma unroll
+                for (int a = 0; a < R; ++a)
+#pragma unroll
+                    for (int b = 0; b < R; ++b) acc[a][b] = 0;
+                for (int p = 0; p < kb; ++p) {
+                    T av[R], bv[R];
+#pragma unroll
+                    for (int a = 0; a < R; ++a) av[a] = sI[ty + 16 * a][p];
+#pragma unroll
+                    for (int b = 0; b < R; ++b) bv[b] = sJ[tx + 16 * b][p];
+#pragma unroll
+                    for (int a = 0; a < R; ++a)
+#pragma unroll
+                        for (int b = 0; b < R; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < R; ++a)
+#pragma unroll
+                    for (int b = 0; b < R; ++b) {
                         const int i = ty + 16 * a, j = tx + 16 * b;
                         if (i >= nr || j >= nc) continue;
-                        T acc = 0;
-                        for (int p = 0; p < kb; ++p) acc += sI[i][p] * sJ[j][p];
                         T* c = A + (int64_t)(r0 + i) * lda + c0 + j;
-                        T v = *c - acc;
+                        T v = *c - acc[a][b];
                         if (fok && it.fstep == k && it.fkind == ABFT_FAULT_COMPUTE && it.frow == r0 + i &&
                             it.fcol == c0 + j)
                             v += (T)it.fdelta;
@@ -355,7 +395,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BT) k_potrf_batched(const abft_batch_item* items, int count,
+__global__ void __launch_bounds__(BT, 2) k_potrf_batched(const abft_batch_item* items, int count,
                                                       int mode, double tau_scale,
                                                       abft_batch_status* status, T* scratch,
                                                       unsigned int* queue) {
