@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
                    choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32", "lu",
-                            "lu-emu", "qr", "qr-emu"],
+                            "lu-emu", "qr", "qr-emu", "batched-f64", "batched-f32"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
                         "refinement, an FP32 two-sweep solve with the FP64 factor, or the ABFT "
@@ -985,6 +985,29 @@ def profile_case(args):
     wsp = abft.Workspace()
     B = torch.from_numpy(W.rhs(n, 16, seed=1003)).to(dev)
     X = torch.empty_like(B)
+    if args.profile_case in ("batched-f64", "batched-f32"):
+        # 1024 matrices of the batched configuration's size mix (n in [32, 512]),
+        # block 64, one fault per 64 matrices: 0.77 GB in FP64, above L2
+        sizes = W.batched_sizes(1024, 32, 512, seed=1005)
+        offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)[:-1]])
+        tdt = torch.float64 if args.profile_case == "batched-f64" else torch.float32
+        buf0 = torch.cat([torch.from_numpy(W.spd_mmt(int(m), seed=100000 + i).reshape(-1))
+                          for i, m in enumerate(sizes)]).to(dev).to(tdt)
+        buf = buf0.clone()
+        r = W.rng(6000)
+        bf = {}
+        for q in range(0, 1024, 64):
+            i = q + int(r.integers(0, 64))
+            m = int(sizes[i])
+            if m > 64:
+                row, col = int(r.integers(64, m)), int(r.integers(64, m))
+                bf[i] = (0, abft.F_MEMORY, max(row, col), min(row, col), 1e3)
+        bt = abft.Batch(buf, sizes, offs, 64, bf)
+        for _ in range(2):
+            buf.copy_(buf0)
+            abft.potrf_batched(bt, workspace=wsp)
+        torch.cuda.synchronize(dev)
+        return
     if args.profile_case in ("lu", "lu-emu", "qr", "qr-emu"):
         U0 = W.uniform_torch(n, seed=1001 + n, device=dev)
         for _ in range(2):

@@ -1843,7 +1843,7 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     if (count > 0 && status == nullptr && ws != nullptr) return -6;
     if (ws_bytes == nullptr) return -9;
     const bool f64 = dtype == ABFT_F64;
-    const size_t need = align_up(batched_scratch_bytes(batched_grid(), f64)) + 256;
+    const size_t need = align_up(batched_scratch_bytes(batched_grid(f64), f64)) + 256;
     if (ws == nullptr) {
         *ws_bytes = need;
         return ABFT_OK;
@@ -1851,7 +1851,7 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     if (*ws_bytes < need) return -9;
     if (count == 0) return ABFT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned int* queue = (unsigned int*)((char*)ws + align_up(batched_scratch_bytes(batched_grid(), f64)));
+    unsigned int* queue = (unsigned int*)((char*)ws + align_up(batched_scratch_bytes(batched_grid(f64), f64)));
     if (!use_graph) {
         ABFT_CUDA_TRY(launch_potrf_batched(items, count, f64, mode, tau_scale, status, ws, queue, s));
         ABFT_CUDA_TRY(timing_collect(s));
@@ -1870,7 +1870,7 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     }
     if (exec == nullptr) {
         ABFT_CUDA_TRY(batched_prepare());   // kernel attributes outside the capture
-        (void)batched_grid();
+        (void)batched_grid(f64);
         cudaStream_t cs;
         ABFT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t graph;

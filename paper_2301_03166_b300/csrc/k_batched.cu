@@ -54,24 +54,46 @@ __device__ void record(abft_batch_status* st, int step, int kind, int row, int c
     }
 }
 
-// Sums of one tile (nr x nc at P, ld) into sh: colsum[0..nc), wsum[0..nc), rowsum[0..nr).
+// Sums of one tile (nr x nc at P, ld; nc <= 64) into shared memory: colsum[j],
+// wsum[j] (weights 1..nr) and rowsum[i].  Warp w takes rows w, w + 8, ...;
+// lane l holds columns l and l + 32, so each row is one coalesced load per
+// warp and its sum is a warp shuffle reduction; the eight warps' column
+// partials are added in warp order through shared memory (part: 8 x 64).
 template <typename T>
-__device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* wsum, T* rowsum) {
-    const int t = threadIdx.x;
+__device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* wsum, T* rowsum,
+                          T* part) {
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    T c0 = 0, c1 = 0, w0 = 0, w1 = 0;
+#pragma unroll 4
+    for (int i = w; i < nr; i += BT / 32) {
+        const T* row = P + (int64_t)i * ld;
+        const T v0 = l < nc ? row[l] : (T)0;
+        const T v1 = l + 32 < nc ? row[l + 32] : (T)0;
+        const T wi = (T)(i + 1);
+        c0 += v0;
+        c1 += v1;
+        w0 = fma(wi, v0, w0);
+        w1 = fma(wi, v1, w1);
+        T rs = v0 + v1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (l == 0) rowsum[i] = rs;
+    }
+    T* pc = part;            // [8][64] column partials
+    T* pw = part + 8 * 64;   // [8][64] weighted partials
+    pc[w * 64 + l] = c0;
+    pc[w * 64 + l + 32] = c1;
+    pw[w * 64 + l] = w0;
+    pw[w * 64 + l + 32] = w1;
+    __syncthreads();
     for (int j = t; j < nc; j += BT) {
         T s = 0, sw = 0;
-        for (int i = 0; i < nr; ++i) {
-            T v = P[(int64_t)i * ld + j];
-            s += v;
-            sw += (T)(i + 1) * v;
+        for (int q = 0; q < BT / 32; ++q) {
+            s += pc[q * 64 + j];
+            sw += pw[q * 64 + j];
         }
         colsum[j] = s;
         wsum[j] = sw;
-    }
-    for (int i = t; i < nr; i += BT) {
-        T s = 0;
-        for (int j = 0; j < nc; ++j) s += P[(int64_t)i * ld + j];
-        rowsum[i] = s;
     }
     __syncthreads();
 }
@@ -81,8 +103,8 @@ __device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* 
 template <typename T>
 __device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T* cc, T* cw, T* cr,
                             int crs, T tau, int single, int step, abft_batch_status* st,
-                            T* colsum, T* wsum, T* rowsum, int* sflag, int* s_first) {
-    tile_sums<T>(P, ld, nr, nc, colsum, wsum, rowsum);
+                            T* colsum, T* wsum, T* rowsum, T* part, int* sflag, int* s_first) {
+    tile_sums<T>(P, ld, nr, nc, colsum, wsum, rowsum, part);
     const int t = threadIdx.x;
     if (t == 0) { sflag[0] = 0; sflag[1] = 0; sflag[2] = 1 << 30; sflag[3] = 1 << 30; }
     __syncthreads();
@@ -156,7 +178,7 @@ __device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T*
 template <typename T, int B>
 __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scratch<T> S,
                            abft_batch_status* st, T (*sL)[MAXB + 1], T (*sI)[MAXB + 1],
-                           T (*sJ)[MAXB + 1], T* colsum, T* wsum, T* rowsum, int* sflag,
+                           T (*sJ)[MAXB + 1], T* colsum, T* wsum, T* rowsum, T* rdiag, int* sflag,
                            int* s_first, int* s_fail) {
     T* A = (T*)it.A;
     const int64_t lda = it.lda;
@@ -194,7 +216,8 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         for (int I = 0; I < nt; ++I)
             for (int J = 0; J <= I; ++J) {
                 const int r0 = I * B, c0 = J * B, nr = min(B, n - r0), nc = min(B, n - c0);
-                tile_sums<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, colsum, wsum, rowsum);
+                tile_sums<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, colsum, wsum, rowsum,
+                             &sJ[0][0]);
                 for (int j = t; j < nc; j += BT) {
                     S.Cc[I * MAXN + c0 + j] = colsum[j];
                     S.Cw[I * MAXN + c0 + j] = wsum[j];
@@ -218,8 +241,8 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             }
             __syncthreads();
             if (*s_fail >= 0) break;
-            const T djj = sL[j][j];
-            for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] / djj;
+            const T rjj = (T)1 / sL[j][j];   // one division per column, products below
+            for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] * rjj;
             __syncthreads();
             {   // rank-1 update of the remaining lower triangle on a 16 x 16 thread grid
                 const int tx = t & 15, ty = t >> 4;
@@ -238,6 +261,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             int i = e / kb, j = e % kb;
             if (j <= i) A[(int64_t)(K0 + i) * lda + K0 + j] = sL[i][j];
         }
+        for (int j = t; j < kb; j += BT) rdiag[j] = (T)1 / sL[j][j];   // the panel solve's reciprocals
         if (check) {   // PD check on column sums
             for (int p = t; p < kb; p += BT) {
                 T s = 0;
@@ -286,7 +310,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     T v = x[q];
 #pragma unroll
                     for (int pp = 0; pp < q; ++pp) v = fma(-x[pp], sL[c0 + q][c0 + pp], v);
-                    x[q] = v / sL[c0 + q][c0 + q];
+                    x[q] = v * rdiag[c0 + q];
                 }
 #pragma unroll
                 for (int q = 0; q < 32; ++q) row[c0 + q] = x[q];
@@ -301,21 +325,38 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 const int r0 = I * B, nr = min(B, n - r0);
                 verify_tile<T>(A + (int64_t)r0 * lda + K0, lda, r0, K0, nr, kb,
                                S.Cc + I * MAXN + K0, S.Cw + I * MAXN + K0, nullptr, 0, tau, 1, k,
-                               st, colsum, wsum, rowsum, sflag, s_first);
+                               st, colsum, wsum, rowsum, &sJ[0][0], sflag, s_first);
             }
-        // ---- TMU over the lower block triangle with the checksum borders
+        // ---- TMU over the lower block triangle with the checksum borders.
+        // sL is free from here to the next PD: it holds the carried checksum
+        // rows of the panel (c_I, w_I of block row I; c_J of block row J) and
+        // the border dot products' partial sums.
+        T* sCI = &sL[0][0];
+        T* sWI = sCI + MAXB;
+        T* sCJ = sWI + MAXB;
+        T* red = sCJ + MAXB;   // [3][BT / B][MAXB] partial sums of the border products
         for (int I = k + 1; I < nt; ++I) {
             const int r0 = I * B, nr = min(B, n - r0);
-            for (int e = t; e < B * kb; e += BT) {
-                int i = e / kb, p = e % kb;
+            // a block with rows below it is full: kb = B from here on
+#pragma unroll
+            for (int e = t; e < B * B; e += BT) {
+                const int i = e / B, p = e % B;
                 sI[i][p] = (i < nr) ? A[(int64_t)(r0 + i) * lda + K0 + p] : (T)0;
             }
+            if (check)
+                for (int p = t; p < kb; p += BT) {
+                    sCI[p] = S.Cc[I * MAXN + K0 + p];
+                    sWI[p] = S.Cw[I * MAXN + K0 + p];
+                }
             for (int J = k + 1; J <= I; ++J) {
                 const int c0 = J * B, nc = min(B, n - c0);
-                for (int e = t; e < B * kb; e += BT) {
-                    int j = e / kb, p = e % kb;
+#pragma unroll
+                for (int e = t; e < B * B; e += BT) {
+                    const int j = e / B, p = e % B;
                     sJ[j][p] = (j < nc) ? A[(int64_t)(c0 + j) * lda + K0 + p] : (T)0;
                 }
+                if (check)
+                    for (int p = t; p < kb; p += BT) sCJ[p] = S.Cc[J * MAXN + K0 + p];
                 __syncthreads();
                 // register tile: thread (tx, ty) owns rows ty + 16 a and columns
                 // tx + 16 b (a, b < B / 16); per p, B / 8 shared loads feed
@@ -327,7 +368,11 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 for (int a = 0; a < R; ++a)
 #pragma unroll
                     for (int b = 0; b < R; ++b) acc[a][b] = 0;
-                for (int p = 0; p < kb; ++p) {
+                // row / column groups of 16 beyond the tile's edge are skipped
+                // (the same branch for every thread)
+                const int ra = (nr + 15) / 16, rb = (nc + 15) / 16;
+#pragma unroll 8
+                for (int p = 0; p < B; ++p) {
                     T av[R], bv[R];
 #pragma unroll
                     for (int a = 0; a < R; ++a) av[a] = sI[ty + 16 * a][p];
@@ -335,8 +380,10 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     for (int b = 0; b < R; ++b) bv[b] = sJ[tx + 16 * b][p];
 #pragma unroll
                     for (int a = 0; a < R; ++a)
+                        if (a < ra)
 #pragma unroll
-                        for (int b = 0; b < R; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                            for (int b = 0; b < R; ++b)
+                                if (b < rb) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
                 }
 #pragma unroll
                 for (int a = 0; a < R; ++a)
@@ -352,19 +399,38 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                         *c = v;
                     }
                 if (check) {
-                    for (int j = t; j < nc; j += BT) {   // c_IJ -= s_I L_J^T, w_IJ likewise
-                        T a1 = 0, a2 = 0;
-                        for (int p = 0; p < kb; ++p) {
-                            a1 += S.Cc[I * MAXN + K0 + p] * sJ[j][p];
-                            a2 += S.Cw[I * MAXN + K0 + p] * sJ[j][p];
-                        }
-                        S.Cc[I * MAXN + c0 + j] -= a1;
-                        S.Cw[I * MAXN + c0 + j] -= a2;
+                    // border products on every thread: column j (or row j) and
+                    // a quarter q of the panel's columns; the quarters are
+                    // then added in order.  c_IJ -= s_I L_J^T, w_IJ likewise,
+                    // r_IJ -= L_I s_J^T.
+                    constexpr int NQ = BT / B;   // parts of the panel's columns
+                    constexpr int np = B / NQ;
+                    const int j = t % B, q = t / B;
+                    const int p0 = q * np;
+                    T a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+                    for (int p = p0; p < p0 + np; ++p) {
+                        a1 = fma(sCI[p], sJ[j][p], a1);
+                        a2 = fma(sWI[p], sJ[j][p], a2);
+                        a3 = fma(sI[j][p], sCJ[p], a3);
                     }
-                    for (int i = t; i < nr; i += BT) {   // r_IJ -= L_I s_J^T
-                        T a1 = 0;
-                        for (int p = 0; p < kb; ++p) a1 += sI[i][p] * S.Cc[J * MAXN + K0 + p];
-                        S.Cr[(r0 + i) * MAXNT + J] -= a1;
+                    red[(0 * NQ + q) * MAXB + j] = a1;
+                    red[(1 * NQ + q) * MAXB + j] = a2;
+                    red[(2 * NQ + q) * MAXB + j] = a3;
+                    __syncthreads();
+                    if (t < nc) {
+                        T s1 = 0, s2 = 0;
+                        for (int qq = 0; qq < NQ; ++qq) {
+                            s1 += red[(0 * NQ + qq) * MAXB + t];
+                            s2 += red[(1 * NQ + qq) * MAXB + t];
+                        }
+                        S.Cc[I * MAXN + c0 + t] -= s1;
+                        S.Cw[I * MAXN + c0 + t] -= s2;
+                    }
+                    if (t < nr) {
+                        T s3 = 0;
+                        for (int qq = 0; qq < NQ; ++qq) s3 += red[(2 * NQ + qq) * MAXB + t];
+                        S.Cr[(r0 + t) * MAXNT + J] -= s3;
                     }
                 }
                 __syncthreads();
@@ -380,7 +446,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     verify_tile<T>(A + (int64_t)r0 * lda + c0, lda, r0, c0, nr, nc,
                                    S.Cc + I * MAXN + c0, S.Cw + I * MAXN + c0,
                                    S.Cr + r0 * MAXNT + J, MAXNT, tau, 0, k, st, colsum, wsum,
-                                   rowsum, sflag, s_first);
+                                   rowsum, &sJ[0][0], sflag, s_first);
                 }
     }
     __syncthreads();
@@ -394,8 +460,13 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     __syncthreads();
 }
 
+// CTAs per SM: two for FP64 (the FP64 pipe is the limit), four for FP32
+// (shorter arithmetic: more CTAs hide the barriers and load latencies)
 template <typename T>
-__global__ void __launch_bounds__(BT, 2) k_potrf_batched(const abft_batch_item* items, int count,
+struct CtasPerSm { static constexpr int v = sizeof(T) == 8 ? 2 : 4; };
+
+template <typename T>
+__global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abft_batch_item* items, int count,
                                                       int mode, double tau_scale,
                                                       abft_batch_status* status, T* scratch,
                                                       unsigned int* queue) {
@@ -406,6 +477,7 @@ __global__ void __launch_bounds__(BT, 2) k_potrf_batched(const abft_batch_item* 
     T* colsum = (T*)(sJ + MAXB);
     T* wsum = colsum + MAXB;
     T* rowsum = wsum + MAXB;
+    T* rdiag = rowsum + MAXB;
     __shared__ int sflag[4], s_first, s_fail, s_item;
     const size_t per = (size_t)(3 * MAXNT * MAXN + MAXN * MAXB);
     Scratch<T> S;
@@ -430,17 +502,17 @@ __global__ void __launch_bounds__(BT, 2) k_potrf_batched(const abft_batch_item* 
         if (it.n <= 0 || it.n > MAXN) continue;
         if (it.nb == 64)
             factor_one<T, 64>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
-                              sflag, &s_first, &s_fail);
+                              rdiag, sflag, &s_first, &s_fail);
         else
             factor_one<T, 32>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
-                              sflag, &s_first, &s_fail);
+                              rdiag, sflag, &s_first, &s_fail);
     }
 }
 
 }  // namespace
 
 size_t batched_smem(bool f64) {
-    return (size_t)(3 * MAXB * (MAXB + 1) + 3 * MAXB) * (f64 ? sizeof(double) : sizeof(float));
+    return (size_t)(3 * MAXB * (MAXB + 1) + 4 * MAXB) * (f64 ? sizeof(double) : sizeof(float));
 }
 
 size_t batched_scratch_bytes(int grid, bool f64) {
@@ -448,8 +520,8 @@ size_t batched_scratch_bytes(int grid, bool f64) {
     return per * (size_t)grid * (f64 ? sizeof(double) : sizeof(float));
 }
 
-int batched_grid() {
-    return 2 * num_sms();
+int batched_grid(bool f64) {
+    return (f64 ? CtasPerSm<double>::v : CtasPerSm<float>::v) * num_sms();
 }
 
 // Kernel attributes (set once, outside any stream capture).
@@ -473,7 +545,7 @@ cudaError_t launch_potrf_batched(const abft_batch_item* items, int count, bool f
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    const int grid = batched_grid();
+    const int grid = batched_grid(f64);
     if (f64)
         k_potrf_batched<double><<<grid, BT, batched_smem(true), s>>>(items, count, mode, tau_scale,
                                                                     status, (double*)scratch, queue);
