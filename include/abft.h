@@ -405,6 +405,19 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
  * diagonal.  Only L and Lbar are read: no forward intermediates are stored.
  * Errors: -1 n; -2 nb; -3 L; -4 ldl; -5 Lbar; -6 ldlb; -7 Abar; -8 ldab; -11 ws.
  *
+ * abft_potrf_backward_ex: the same with the arithmetic of the dominant
+ * product chosen by dtype: ABFT_F64 (FP64 FMA; abft_potrf_backward) or
+ * ABFT_F64_EMU, where Lbar21 -= (Abar22 + Abar22^T) L21 -- about two thirds
+ * of the sweep's flops -- is FP64-accurate from exact BF16 slice products on
+ * the tensor cores (the splitting of abft_potrf's ABFT_F64_EMU: per block
+ * column of Abar22 + Abar22^T, sliced once when the sweep finalizes it, and
+ * per block row of L21; error per term below the FP64 rounding of the same
+ * product).  ABFT_F64_EMU needs nb = 128 or 256 and n a multiple of nb
+ * (ABFT_ERR_UNSUPPORTED otherwise) and 16 n (n + nb) more bytes of workspace;
+ * it synchronizes the stream once at the end (to read the status of its
+ * bounded waits; ABFT_ERR_TIMEOUT if one gave up).  Errors as
+ * abft_potrf_backward, plus -12 dtype.
+ *
  * abft_potrs_backward: for X = A^{-1} B computed with the factor L and the
  * adjoint Xbar of X (n x nrhs, nrhs <= 16): Bbar = A^{-1} Xbar, and
  * Lbar -= tril((Bbar X^T + X Bbar^T) L) (accumulated into Lbar's lower
@@ -419,6 +432,9 @@ int abft_posv_gmres_ir(int64_t n, int64_t nrhs, int64_t nb, int32_t dtype, int32
 int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, const double* Lbar,
                         int64_t ldlb, double* Abar, int64_t ldab, int32_t sym, void* ws,
                         size_t* ws_bytes, void* stream);
+int abft_potrf_backward_ex(int64_t n, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
+                           const double* Lbar, int64_t ldlb, double* Abar, int64_t ldab,
+                           int32_t sym, void* ws, size_t* ws_bytes, void* stream);
 int abft_potrs_backward(int64_t n, int64_t nrhs, int64_t nb, const double* L, int64_t ldl,
                         const double* X, int64_t ldx, const double* Xbar, int64_t ldxb,
                         double* Bbar, int64_t ldbb, double* Lbar, int64_t ldlb, void* ws,

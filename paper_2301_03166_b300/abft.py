@@ -52,6 +52,8 @@ _sz = ctypes.POINTER(ctypes.c_size_t)
 _SIGNATURES = {
     "abft_potrf_batched": [_i32, _vp, _i32, _i32, _dbl, _vp, _i32, _vp, _sz, _vp],
     "abft_potrf_backward": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz, _vp],
+    "abft_potrf_backward_ex": [_i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz,
+                               _vp],
     "abft_potrs_backward": [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
                             _i64, _vp, _sz, _vp],
     "abft_logdet": [_i64, _vp, _i64, _vp, _vp],
@@ -570,24 +572,28 @@ def _ws_call(fn, query_args, run_args, device, workspace):
     return run_args, ws, size
 
 
-def potrf_backward(L, Lbar, nb=256, sym=True, Abar=None, workspace=None, stream=None):
+def potrf_backward(L, Lbar, nb=256, sym=True, Abar=None, workspace=None, stream=None,
+                   dtype=F64):
     """Adjoint of the Cholesky factorization: Abar from L and Lbar (lower
-    triangles read).  sym=True returns the symmetric gradient."""
+    triangles read).  sym=True returns the symmetric gradient.  dtype F64_EMU
+    runs the dominant product FP64-accurate on the BF16 tensor cores (nb 128
+    or 256, n a multiple of nb)."""
     _check_matrix(L, "L")
     _check_matrix(Lbar, "Lbar")
     n = L.shape[0]
     Abar = torch.empty_like(L) if Abar is None else Abar
     Lb = lib()
     need = ctypes.c_size_t(0)
-    rc = Lb.abft_potrf_backward(n, nb, None, max(1, L.stride(0)), None, max(1, Lbar.stride(0)), None,
-                                max(1, Abar.stride(0)), 1 if sym else 0, None, ctypes.byref(need), None)
+    rc = Lb.abft_potrf_backward_ex(n, nb, dtype, None, max(1, L.stride(0)), None,
+                                   max(1, Lbar.stride(0)), None, max(1, Abar.stride(0)),
+                                   1 if sym else 0, None, ctypes.byref(need), None)
     if rc < 0:
         raise AbftError(rc, strerror(rc))
     ws = (workspace or Workspace()).get(need.value, L.device)
     size = ctypes.c_size_t(ws.numel())
-    rc = Lb.abft_potrf_backward(n, nb, _ptr(L), L.stride(0), _ptr(Lbar), Lbar.stride(0), _ptr(Abar),
-                                Abar.stride(0), 1 if sym else 0, _ptr(ws), ctypes.byref(size),
-                                _stream(stream))
+    rc = Lb.abft_potrf_backward_ex(n, nb, dtype, _ptr(L), L.stride(0), _ptr(Lbar), Lbar.stride(0),
+                                   _ptr(Abar), Abar.stride(0), 1 if sym else 0, _ptr(ws),
+                                   ctypes.byref(size), _stream(stream))
     if rc < 0:
         raise AbftError(rc, strerror(rc))
     return Abar

@@ -22,12 +22,17 @@ class Cholesky(torch.autograd.Function):
         abft.tril_(L)
         ctx.save_for_backward(L)
         ctx.nb = nb
+        # the FP64-accurate forward keeps its arithmetic in the reverse sweep
+        # where the sweep supports it (nb 128 or 256, n a multiple of nb)
+        n = L.shape[0]
+        ctx.bdtype = abft.F64_EMU if (dtype == abft.F64_EMU and nb in (128, 256) and n % nb == 0) \
+            else abft.F64
         return L
 
     @staticmethod
     def backward(ctx, Lbar):
         (L,) = ctx.saved_tensors
-        G = abft.potrf_backward(L, Lbar.contiguous(), ctx.nb, sym=True)
+        G = abft.potrf_backward(L, Lbar.contiguous(), ctx.nb, sym=True, dtype=ctx.bdtype)
         return G, None, None, None
 
 

@@ -1623,19 +1623,58 @@ namespace {
 // -------------------------------------------------------------- adjoint
 constexpr int kAdjSplit = 16;
 
-size_t adj_ws_bytes(int64_t nb) {
+size_t adj_base_bytes(int64_t nb) {
     const size_t d = sizeof(double);
     return align_up(d * nb * nb) * 3 + align_up(d * (size_t)kAdjSplit * nb * nb);
 }
 
+// FP64-accurate sweep: per block column J of F = Abar_L + Abar_L^T a slice
+// tensor region of R = n + nb rows (F's rows, then the columns of the current
+// L21 cut to block row J), 8 BF16 slices of nb columns each; one exponent per
+// slice row; a status block for the tensor-core kernel; the symmetric diagonal block.
+struct AdjEmu {
+    size_t st, S, ex, D, total;
+    int64_t N, R;
+};
+AdjEmu adj_emu_layout(int64_t n, int64_t nb) {
+    AdjEmu a{};
+    a.N = (n + nb - 1) / nb;
+    a.R = n + nb;
+    size_t off = adj_base_bytes(nb);
+    a.st = off; off = align_up(off + sizeof(DevStatus));
+    a.S = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)a.N * (size_t)a.R * (size_t)nb);
+    a.ex = off; off = align_up(off + sizeof(int) * (size_t)a.N * (size_t)a.R);
+    a.D = off; off = align_up(off + sizeof(double) * (size_t)nb * (size_t)nb);
+    a.total = off;
+    return a;
+}
+
+size_t adj_ws_bytes(int64_t n, int64_t nb, bool emu) {
+    return emu ? adj_emu_layout(n, nb).total : adj_base_bytes(nb);
+}
+
 // Blocked reverse sweep of the right-looking Cholesky (lower convention).
+// emu: the dominant product Lbar21 -= F22 L21 (F = Abar_L + Abar_L^T) runs
+// FP64-accurate from exact BF16 slice products on the tensor cores, one
+// launch per block column J of F22 (block J's rows of L21 as the other
+// operand), the launches subtracting into Lbar21 in order of J.  F's block
+// column k is sliced once, when the sweep has finalized it (its rows below
+// the diagonal from Abar21, the diagonal block in full, and Abar21^T as rows
+// of the later block columns' tensors); F never changes afterwards.
 int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, double* Ab,
-                       int64_t ldab, char* ws, cudaStream_t s) {
+                       int64_t ldab, char* ws, cudaStream_t s, bool emu) {
     double* P = (double*)ws;
     double* Y = (double*)(ws + align_up(sizeof(double) * nb * nb));
     double* Lc = (double*)(ws + 2 * align_up(sizeof(double) * nb * nb));
     double* part = (double*)(ws + 3 * align_up(sizeof(double) * nb * nb));
     const int64_t N = (n + nb - 1) / nb;
+    const AdjEmu ae = adj_emu_layout(n, nb);
+    DevStatus* est = (DevStatus*)(ws + ae.st);
+    uint16_t* S = (uint16_t*)(ws + ae.S);
+    int* ex = (int*)(ws + ae.ex);
+    double* D = (double*)(ws + ae.D);
+    const int64_t R = ae.R, Mtot = N * R;
+    if (emu) ABFT_CUDA_TRY(cudaMemsetAsync(est, 0, sizeof(DevStatus), s));
     for (int64_t k = N - 1; k >= 0; --k) {
         const int64_t K0 = k * nb, kb = std::min(nb, n - K0), T0 = K0 + kb, m = n - T0;
         const double* L11 = L + K0 * ldl + K0;
@@ -1643,12 +1682,27 @@ int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, doub
         if (m > 0) {
             // trailing update A22' = A22 - L21 L21^T  =>  Lbar21 -= (Abar22 + Abar22^T) L21
             timing_mark(PH_TMU, 1, s);
-            GemmSeg g1{};
-            g1.A = Ab + T0 * ldab + T0; g1.lda = ldab;
-            g1.B = L + T0 * ldl + K0; g1.ldb = ldl;
-            g1.C = Ab + T0 * ldab + K0; g1.ldc = ldab;
-            g1.M = m; g1.N = kb; g1.K = m;
-            ABFT_CUDA_TRY(launch_gemm_f64(&g1, 1, 2, 1, nullptr, 0, nullptr, s));
+            if (emu) {
+                // the columns of L21, block row J's piece as rows n .. n + kb of tensor J
+                ABFT_CUDA_TRY(launch_slice_cols_chunked(L + T0 * ldl + K0, ldl, nb, m, kb, S, Mtot,
+                                                        (k + 1) * R + n, R, ex, s));
+                for (int64_t J = k + 1; J < N; ++J) {
+                    EmuRectHost rc{};
+                    rc.C = Ab + T0 * ldab + K0; rc.ldc = ldab;
+                    rc.a0 = J * R + T0; rc.na = m;     // F's rows T0 .. n, block column J
+                    rc.b0 = J * R + n; rc.nb = kb;     // L21's columns, block row J
+                    rc.cdiv = 1; rc.frow = -1; rc.fcol = -1;
+                    ABFT_CUDA_TRY(launch_tmu_emu(S, ex, Mtot, nb, nullptr, 0, 0, 0, 128, &rc, 1,
+                                                 nullptr, 0, 0, est, s));
+                }
+            } else {
+                GemmSeg g1{};
+                g1.A = Ab + T0 * ldab + T0; g1.lda = ldab;
+                g1.B = L + T0 * ldl + K0; g1.ldb = ldl;
+                g1.C = Ab + T0 * ldab + K0; g1.ldc = ldab;
+                g1.M = m; g1.N = kb; g1.K = m;
+                ABFT_CUDA_TRY(launch_gemm_f64(&g1, 1, 2, 1, nullptr, 0, nullptr, s));
+            }
             timing_mark(PH_TMU, 0, s);
             // L21 = A21 L11^{-T}  =>  Abar21 = Lbar21 L11^{-1}, Lbar11 -= tril(Abar21^T L21)
             timing_mark(PH_PU, 1, s);
@@ -1682,6 +1736,24 @@ int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, doub
         ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &sy, 1, nullptr, nullptr, nullptr, s, false, true));
         ABFT_CUDA_TRY(launch_assemble_diag(Y, kb, A11, ldab, kb, s));
         timing_mark(PH_PD, 0, s);
+        if (emu) {   // block column k of F is final: slice it for the steps still to come
+            timing_mark(PH_OTHER, 1, s);
+            if (m > 0) {
+                ABFT_CUDA_TRY(launch_slice_panel(Ab + T0 * ldab + K0, ldab, m, kb, S, Mtot,
+                                                 k * R + T0, ex, s));
+                ABFT_CUDA_TRY(launch_slice_cols_chunked(Ab + T0 * ldab + K0, ldab, nb, m, kb, S,
+                                                        Mtot, (k + 1) * R + K0, R, ex, s));
+            }
+            ABFT_CUDA_TRY(launch_sym_diag(A11, ldab, kb, D, s));
+            ABFT_CUDA_TRY(launch_slice_panel(D, kb, kb, kb, S, Mtot, k * R + K0, ex, s));
+            timing_mark(PH_OTHER, 0, s);
+        }
+    }
+    if (emu) {
+        int err = 0;
+        ABFT_CUDA_TRY(cudaMemcpyAsync(&err, &est->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ABFT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (err) return ABFT_ERR_TIMEOUT;
     }
     return ABFT_OK;
 }
@@ -1693,8 +1765,19 @@ extern "C" {
 int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, const double* Lbar,
                         int64_t ldlb, double* Abar, int64_t ldab, int32_t sym, void* ws,
                         size_t* ws_bytes, void* stream) {
+    return abft_potrf_backward_ex(n, nb, ABFT_F64, L, ldl, Lbar, ldlb, Abar, ldab, sym, ws,
+                                  ws_bytes, stream);
+}
+
+int abft_potrf_backward_ex(int64_t n, int64_t nb, int32_t dtype, const double* L, int64_t ldl,
+                           const double* Lbar, int64_t ldlb, double* Abar, int64_t ldab,
+                           int32_t sym, void* ws, size_t* ws_bytes, void* stream) {
     if (n < 0) return -1;
     if (nb <= 0 || nb % 32 != 0 || nb > 512) return -2;
+    if (dtype != ABFT_F64 && dtype != ABFT_F64_EMU)
+        return dtype < 0 || dtype > 4 ? -12 : ABFT_ERR_UNSUPPORTED;
+    const bool emu = dtype == ABFT_F64_EMU;
+    if (emu && ((nb != 128 && nb != 256) || n % nb != 0)) return ABFT_ERR_UNSUPPORTED;
     const bool run = ws != nullptr && n > 0;
     if (run && L == nullptr) return -3;
     if (ldl < std::max<int64_t>(1, n)) return -4;
@@ -1703,7 +1786,7 @@ int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, con
     if (run && Abar == nullptr) return -7;
     if (ldab < std::max<int64_t>(1, n)) return -8;
     if (ws_bytes == nullptr) return -11;
-    const size_t need = adj_ws_bytes(nb);
+    const size_t need = adj_ws_bytes(n, nb, emu);
     if (ws == nullptr) {
         *ws_bytes = need;
         return ABFT_OK;
@@ -1714,7 +1797,7 @@ int abft_potrf_backward(int64_t n, int64_t nb, const double* L, int64_t ldl, con
     timing_mark(PH_OTHER, 1, s);
     ABFT_CUDA_TRY(launch_copy_lower(Lbar, ldlb, Abar, ldab, n, s));
     timing_mark(PH_OTHER, 0, s);
-    int rc = potrf_backward_run(n, nb, L, ldl, Abar, ldab, (char*)ws, s);
+    int rc = potrf_backward_run(n, nb, L, ldl, Abar, ldab, (char*)ws, s, emu);
     if (rc != ABFT_OK) return rc;
     if (sym) ABFT_CUDA_TRY(launch_symmetrize_half(Abar, ldab, n, s));
     ABFT_CUDA_TRY(timing_collect(s));

@@ -316,6 +316,8 @@ cudaError_t launch_copy_f2d(const float* src, int64_t lds, double* dst, int64_t 
 cudaError_t launch_copy_lower(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n,
                               cudaStream_t s);
 cudaError_t launch_phi_neg(double* P, int64_t ld, int64_t kb, cudaStream_t s);
+// D (kb x kb, ld kb) = A + A^T for the lower-stored block A (diagonal doubled).
+cudaError_t launch_sym_diag(const double* A, int64_t lda, int64_t kb, double* D, cudaStream_t s);
 cudaError_t launch_transpose(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t kb,
                              cudaStream_t s);
 cudaError_t launch_assemble_diag(const double* St, int64_t lds, double* A, int64_t lda, int64_t kb,

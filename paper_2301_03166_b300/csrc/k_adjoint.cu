@@ -52,6 +52,15 @@ __global__ void k_assemble_diag(const double* St, int64_t lds, double* A, int64_
     A[(int64_t)i * lda + j] = v;
 }
 
+// D = A + A^T of a lower-stored kb x kb block A (the diagonal doubled): the
+// diagonal block of F = Abar_L + Abar_L^T, in full, for the FP64-accurate sweep.
+__global__ void k_sym_diag(const double* A, int64_t lda, int kb, double* D) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kb * kb) return;
+    const int i = e / kb, j = e % kb;
+    D[e] = i > j ? A[(int64_t)i * lda + j] : (i < j ? A[(int64_t)j * lda + i] : 2.0 * A[(int64_t)i * lda + i]);
+}
+
 // U = L^T X for lower L (only p >= i of column i used): U[i][r] = sum_{p >= i} L[p][i] X[p][r].
 __global__ void __launch_bounds__(256) k_ltx(const double* L, int64_t ldl, int64_t n,
                                              const double* X, int64_t ldx, int nrhs, double* U,
@@ -171,6 +180,13 @@ cudaError_t launch_copy_lower(const double* src, int64_t lds, double* dst, int64
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_copy_lower<<<blocks_for(n * n), 256, 0, s>>>(src, lds, dst, ldd, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_diag(const double* A, int64_t lda, int64_t kb, double* D, cudaStream_t s) {
+    if (kb <= 0) return cudaSuccess;
+    k_sym_diag<<<blocks_for(kb * kb), 256, 0, s>>>(A, lda, (int)kb, D);
     note_launch();
     return cudaGetLastError();
 }

@@ -123,3 +123,39 @@ def test_potrs_backward_vs_fd():
     G_ref = -0.5 * (Bb @ Xe.T + Xe @ Bb.T)
     np.testing.assert_allclose(Gt, G_ref, rtol=1e-9, atol=1e-11)
     np.testing.assert_allclose(Bt.grad.cpu().numpy(), Bb, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,nb", [(256, 128), (768, 256), (1280, 128), (2048, 256)])
+def test_potrf_backward_fp64_accurate_vs_oracle(n, nb):
+    """The reverse sweep with its dominant product from BF16 slices on the
+    tensor cores: the same adjoint as the oracle's to FP64 accuracy."""
+    A = W.spd_mmt(n, seed=800 + n)
+    L = np.linalg.cholesky(A)
+    Lbar = np.tril(W.rng(n + 1).standard_normal((n, n)))
+    G_o = oracle.potrf_backward(L, Lbar)
+    G = abft.potrf_backward(T(L), T(Lbar), nb, sym=True, dtype=abft.F64_EMU).cpu().numpy()
+    assert np.abs(G - G_o).max() <= 1e-11 * max(1.0, np.abs(G_o).max())
+    G64 = abft.potrf_backward(T(L), T(Lbar), nb, sym=True).cpu().numpy()
+    assert np.abs(G - G64).max() <= 1e-11 * max(1.0, np.abs(G64).max())
+
+
+def test_potrf_backward_fp64_accurate_unsupported_shapes():
+    L = T(np.eye(300))
+    with pytest.raises(abft.AbftError):
+        abft.potrf_backward(L, L, 128, dtype=abft.F64_EMU)      # n not a multiple of nb
+    with pytest.raises(abft.AbftError):
+        abft.potrf_backward(T(np.eye(256)), T(np.eye(256)), 64, dtype=abft.F64_EMU)
+
+
+def test_gp_gradient_fp64_accurate_forward_and_backward():
+    """GP configuration at n = 4096 with the FP64-accurate factorization and
+    reverse sweep: the gradient within 1e-8 of the CPU closed form."""
+    n = 4096
+    Xn, yn = W.gp_inputs(n, 8, seed=1004)
+    Kn = W.gp_kernel(Xn)
+    K = T(Kn).requires_grad_(True)
+    loss = ag.gp_negative_log_likelihood_terms(K, T(yn), 256, dtype=abft.F64_EMU)
+    loss.backward()
+    loss_o, G_o = oracle.gp_loss_grad(Kn, yn)
+    assert abs(loss.item() - loss_o) <= 1e-10 * abs(loss_o)
+    assert np.linalg.norm(K.grad.cpu().numpy() - G_o) <= 1e-8 * np.linalg.norm(G_o)
