@@ -137,8 +137,8 @@ CholWs chol_ws(int64_t n, int64_t nb, int mode, bool mixed = false, bool emu = f
     // abs-checksums of the mixed form (thresholds per column / row) and the
     // panel tiles' sums 1^T |Lq_I| that carry them
     const bool absc = mixed && mode != ABFT_MODE_NONE;
-    w.ca = off; off = align_up(off + (absc ? sizeof(double) * (size_t)w.nt * (size_t)n : 0));
-    w.ra = off; off = align_up(off + (absc && mode == ABFT_MODE_FULL ? sizeof(double) * (size_t)n * (size_t)w.nt : 0));
+    w.ca = off; off = align_up(off + (absc ? sizeof(float) * (size_t)w.nt * (size_t)n : 0));
+    w.ra = off; off = align_up(off + (absc && mode == ABFT_MODE_FULL ? sizeof(float) * (size_t)n * (size_t)w.nt : 0));
     w.ta32 = off; off = align_up(off + (absc ? sizeof(float) * (size_t)w.nt * (size_t)nb : 0));
     w.pdpart = off; off = align_up(off + pd_part_bytes(nb));
     w.eslice = off; off = align_up(off + (emu ? emu_slice_bytes(n, nb) : 0));
@@ -278,8 +278,8 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
     double* sig = (double*)(base + w.sig);
     double* tq = (double*)(base + w.tq);
     float* tq32 = (float*)(base + w.tq32);
-    double* Ca = (double*)(base + w.ca);
-    double* Ra = (double*)(base + w.ra);
+    float* Ca = (float*)(base + w.ca);
+    float* Ra = (float*)(base + w.ra);
     float* ta32 = (float*)(base + w.ta32);
     DevStatus* st = (DevStatus*)(base + w.st);
     double* CS = (double*)(base + w.cs);
@@ -335,9 +335,9 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
             ts.I0 = k; ts.I1 = nt; ts.J0 = k; ts.J1 = nt; ts.lower = 1;
             ABFT_CUDA_TRY(launch_encode(ts, mk, s));
             if (mixed) {   // abs-checksums start at zero with the encoded checksums
-                ABFT_CUDA_TRY(cudaMemsetAsync(Ca, 0, sizeof(double) * (size_t)nt * (size_t)n, s));
+                ABFT_CUDA_TRY(cudaMemsetAsync(Ca, 0, sizeof(float) * (size_t)nt * (size_t)n, s));
                 if (full)
-                    ABFT_CUDA_TRY(cudaMemsetAsync(Ra, 0, sizeof(double) * (size_t)n * (size_t)nt, s));
+                    ABFT_CUDA_TRY(cudaMemsetAsync(Ra, 0, sizeof(float) * (size_t)n * (size_t)nt, s));
             }
             timing_mark(PH_OTHER, 0, s);
         }
@@ -497,13 +497,13 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                     // abs-checksum rows: |c|_I += sigma_I sigma_J ((1^T |Lq_I|) |Lq_J|^T)
                     bs[2] = bs[0];
                     bs[2].A = ta32 + (k + 1) * kb; bs[2].lda = kb;
-                    bs[2].C = Ca + (k + 1) * n + T0 + c0;
+                    bs[2].C = nullptr; bs[2].C32 = Ca + (k + 1) * n + T0 + c0;
                     bs[2].M = nt - k - 1; bs[2].r_div = 1;
                     bs[2].b_abs = 1; bs[2].plus = 1;
                     // abs-checksum columns: |r|_I += sigma_I sigma_J (|Lq_I| (1^T |Lq_J|)^T)
                     bs[3] = bs[1];
                     bs[3].B = ta32 + J0 * kb; bs[3].ldb = kb;
-                    bs[3].C = Ra + T0 * nt + J0;
+                    bs[3].C = nullptr; bs[3].C32 = Ra + T0 * nt + J0;
                     bs[3].a_abs = 1; bs[3].plus = 1;
                     // segments: checksum rows, abs rows, then (full) checksum and abs columns
                     BorderSegHost ord[4] = {bs[0], bs[2], bs[1], bs[3]};

@@ -120,13 +120,13 @@ struct TileSet {
     int lower;
     int64_t nrow_end, ncol_end;
     int weighted;   // encode also writes the weighted column sums (cw)
-    // verify only, mixed-precision Cholesky: abs-checksums laid out as cc and cr
-    // (ca(I,J) = ca + I caI + J g, ra(I,J) = ra + (I g) crs + J crJ); when set,
-    // column j is flagged above tau_coef ca_j + tau64 and row i above
-    // tau_coef ra_i + tau64 instead of the scalar tau
-    const double* ca;
+    // verify only, mixed-precision Cholesky: abs-checksums (FP32) laid out as
+    // cc and cr (ca(I,J) = ca + I caI + J g, ra(I,J) = ra + (I g) crs + J crJ);
+    // when set, column j is flagged above tau_coef ca_j + tau64 and row i above
+    // tau_coef ra_i + tau64 (formed in FP32) instead of the scalar tau
+    const float* ca;
     int64_t caI;
-    const double* ra;
+    const float* ra;
 };
 
 cudaError_t launch_encode(const TileSet& ts, int mode, cudaStream_t s);
@@ -252,6 +252,7 @@ struct BorderSegHost {
     int64_t r_off, r_div, r_base, c_off, c_div, c_base;
     int a_abs = 0, b_abs = 0;   // use |A| / |B| (the abs-checksum products)
     int plus = 0;               // C += ... instead of C -= ...
+    float* C32 = nullptr;       // FP32 output (C unused): the abs-checksums
 };
 // tabs32 (nullable): 1^T |Lq_I| per tile-row, FP32, at tabs32[I kb + p].
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,

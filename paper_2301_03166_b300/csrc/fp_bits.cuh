@@ -60,4 +60,16 @@ __device__ __forceinline__ double f32_to_f64_exact(float x) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// |x| as a float by integer operations, the mantissa truncated (for
+// diagnostics such as ratios, where a relative error below 2^-23 does not
+// matter): 0 below the float range, infinity above it and for Inf / NaN.
+__device__ __forceinline__ float f64_abs_to_f32_trunc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    const int e = (int)(b >> 52);
+    if (e >= 2047 || e > 1023 + 127) return __uint_as_float(0x7f800000u);
+    if (e < 1023 - 126) return 0.0f;
+    const uint32_t m = (uint32_t)((b >> 29) & 0x7fffffull);
+    return __uint_as_float(((uint32_t)(e - 896) << 23) | m);
+}
+
 }  // namespace abft

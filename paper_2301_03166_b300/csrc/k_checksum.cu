@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 
 namespace abft {
 
@@ -277,50 +278,65 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
                                                              rowsum, part);
     const double tau = st->tau;
     // thresholds per column and row: the scalar tau, or (mixed precision)
-    // tau_coef |c|_j + tau64 from the abs-checksums; part[] is free again
+    // tau_coef |c|_j + tau64 from the FP32 abs-checksums, formed with one FP32
+    // fused multiply-add and widened to FP64 by integer operations (the flag
+    // test itself stays one FP64 comparison); part[] is free again
     const bool pc = ts.ca != nullptr;
     double* tcol = part[0];
     double* trow = part[1];
-    const double coef = st->tau_coef, t64 = st->tau64;
-    double tmax = 0.0;
+    float* tcol32 = reinterpret_cast<float*>(part[2]);
+    float* trow32 = tcol32 + kMaxG;
     if (pc) {
-        const double* ca = ts.ca + I * ts.caI + J * ts.g;
+        const float c32 = (float)st->tau_coef, t32 = (float)st->tau64;
+        const float* ca = ts.ca + I * ts.caI + J * ts.g;
+        float tmax = 0.0f;
         for (int j = threadIdx.x; j < nc; j += kThreads) {
-            tcol[j] = __dadd_rn(__dmul_rn(coef, ca[j]), t64);
-            tmax = fmax(tmax, tcol[j]);
+            const float t = fmaf(c32, ca[j], t32);
+            tcol32[j] = t;
+            tcol[j] = f32_to_f64_exact(t);
+            tmax = fmaxf(tmax, t);
         }
         if (MODE == MODE_FULL) {
-            const double* ra = ts.ra + r0 * ts.crs + J * ts.crJ;
+            const float* ra = ts.ra + r0 * ts.crs + J * ts.crJ;
             for (int i = threadIdx.x; i < nr; i += kThreads) {
-                trow[i] = __dadd_rn(__dmul_rn(coef, ra[(int64_t)i * ts.crs]), t64);
-                tmax = fmax(tmax, trow[i]);
+                const float t = fmaf(c32, ra[(int64_t)i * ts.crs], t32);
+                trow32[i] = t;
+                trow[i] = f32_to_f64_exact(t);
+                tmax = fmaxf(tmax, t);
             }
         }
-        atomic_max_nonneg(&st->tau_max_bits, tmax);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if ((threadIdx.x & 31) == 0 && tmax > 0.0f)
+            atomic_max_nonneg(&st->tau_max_bits, f32_to_f64_exact(tmax));
         __syncthreads();
     }
 #define TCOL(j) (pc ? tcol[j] : tau)
 #define TROW(i) (pc ? trow[i] : tau)
-    double dmax = 0.0;   // largest |d| / threshold
+    // largest |d| (scalar threshold) or largest |d| / threshold in FP32
+    // (per-column thresholds; a diagnostic, so truncated operands suffice)
+    double dmax = 0.0;
+    float rmax = 0.0f;
     // d = recomputed - carried, kept in place of the sums
     for (int j = threadIdx.x; j < nc; j += kThreads) {
         double d = colsum[j] - cc[j];
         colsum[j] = d;
         if (MODE == MODE_SINGLE) wsum[j] = wsum[j] - cw[j];
-        double a = fabs(d), t = TCOL(j);
-        if (!(a <= t)) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
-        const double q = t > 0.0 ? a / t : 0.0;
-        if (q > dmax) dmax = q;
+        double a = fabs(d);
+        if (!(a <= TCOL(j))) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
+        if (pc) rmax = fmaxf(rmax, __fdividef(f64_abs_to_f32_trunc(a), tcol32[j]));
+        else if (a > dmax) dmax = a;
     }
     if (MODE == MODE_FULL)
         for (int i = threadIdx.x; i < nr; i += kThreads) {
             double d = rowsum[i] - cr[(int64_t)i * ts.crs];
             rowsum[i] = d;
-            double a = fabs(d), t = TROW(i);
-            if (!(a <= t)) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
-            const double q = t > 0.0 ? a / t : 0.0;
-            if (q > dmax) dmax = q;
+            double a = fabs(d);
+            if (!(a <= TROW(i))) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
+            if (pc) rmax = fmaxf(rmax, __fdividef(f64_abs_to_f32_trunc(a), trow32[i]));
+            else if (a > dmax) dmax = a;
         }
+    if (pc) dmax = f32_to_f64_exact(rmax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((threadIdx.x & 31) == 0) s_dmax[threadIdx.x >> 5] = dmax;
@@ -330,7 +346,8 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
         if (threadIdx.x == 0) {
             double m = 0.0;
             for (int w = 0; w < kWarps; ++w) m = fmax(m, s_dmax[w]);
-            atomic_max_nonneg(&st->max_ratio_bits, m);
+            if (pc) atomic_max_nonneg(&st->max_ratio_bits, m);
+            else if (tau > 0.0) atomic_max_nonneg(&st->max_ratio_bits, m / tau);
         }
         return;
     }

@@ -411,6 +411,7 @@ struct BorderSeg {
     int64_t r_off, r_div, r_base, c_off, c_div, c_base;
     int a_abs, b_abs;   // the abs-checksum products use |A| and |B|
     int plus;           // abs-checksums grow: C += instead of C -=
+    float* C32;         // FP32 output instead of C (the abs-checksums)
 };
 constexpr int MAX_BSEG = 4;
 struct BorderArgs {
@@ -487,6 +488,10 @@ __global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
             const int64_t j = j0 + tx + 16 * c;
             if (j >= g.N) continue;
             const double sc = a.sig[(j + g.c_off) / g.c_div + g.c_base];
+            if (g.C32) {   // abs-checksums: FP32 (they only scale a threshold)
+                g.C32[i * g.ldc + j] += (float)(sr * sc) * acc[r][c];
+                continue;
+            }
             const double v = (sr * sc) * (double)acc[r][c];
             if (g.plus) g.C[i * g.ldc + j] += v;
             else g.C[i * g.ldc + j] -= v;
@@ -612,7 +617,7 @@ cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, c
         b.C = h.C; b.ldc = h.ldc; b.M = h.M; b.N = h.N; b.K = h.K;
         b.r_off = h.r_off; b.r_div = h.r_div; b.r_base = h.r_base;
         b.c_off = h.c_off; b.c_div = h.c_div; b.c_base = h.c_base;
-        b.a_abs = h.a_abs; b.b_abs = h.b_abs; b.plus = h.plus;
+        b.a_abs = h.a_abs; b.b_abs = h.b_abs; b.plus = h.plus; b.C32 = h.C32;
         a.tn[a.nseg] = (h.N + 63) / 64;
         a.start[a.nseg] = total;
         total += ((h.M + 63) / 64) * a.tn[a.nseg];
