@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
                    choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32", "lu",
-                            "lu-emu", "qr", "qr-emu", "batched-f64", "batched-f32"],
+                            "lu-emu", "qr", "qr-emu", "batched-f64", "batched-f32", "fp64-pipes"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
                         "refinement, an FP32 two-sweep solve with the FP64 factor, or the ABFT "
@@ -978,6 +978,15 @@ def profile_case(args):
     from paper_2301_03166_b300 import abft
     from paper_2301_03166_b300 import workloads as W
     dev = torch.device("cuda:0")
+    if args.profile_case == "fp64-pipes":
+        # the FP64 FMA against the FP64 tensor-core MMA, with the SM clock seen
+        clocks = ClockSampler(board_id(0))
+        clocks.start()
+        r = {"dfma_tflops": abft.fp64_pipe_probe(0, 200000),
+             "dmma_m8n8k4_tflops": abft.fp64_pipe_probe(1, 200000)}
+        r["clocks"] = clocks.stop()
+        print(json.dumps(r), flush=True)
+        return
     n, nb = args.n, args.nb
     A0 = W.spd_mmt_torch(n, seed=1000 + n, device=dev)
     A = torch.empty_like(A0)

@@ -539,6 +539,18 @@ int abft_batched_partition(int32_t count, const int64_t* n, int32_t G, int32_t* 
 int abft_wait_selftest(int32_t which, int64_t limit_ns, int32_t* error_out, void* ws,
                        size_t* ws_bytes, void* stream);
 
+/*
+ * abft_fp64_pipe_probe -- diagnostics (no counterpart in the paper): the
+ * FP64 multiply-add rate of this GPU measured two ways, which = 0 the FP64
+ * FMA of the CUDA cores, which = 1 the FP64 tensor-core MMA (mma.sync
+ * m8n8k4); four CTAs of 256 threads per SM, 8 independent chains per thread
+ * (4 accumulators per warp for the MMA), iters steps each.  *tflops_out
+ * receives the rate of the second of two launches (CUDA events).  Behind the
+ * library's choice of the FMA for its FP64 arithmetic.  Synchronizes the
+ * stream.  Errors: -1 which; -2 iters (1 .. 2^24); -3 tflops_out.
+ */
+int abft_fp64_pipe_probe(int32_t which, int64_t iters, double* tflops_out, void* stream);
+
 /* Size of the built-in device scratch array used by abft_potrf_noalloc. */
 #define ABFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)   /* 16 MiB per GPU */
 

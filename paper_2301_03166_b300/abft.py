@@ -81,6 +81,7 @@ _SIGNATURES = {
     "abft_batched_partition": [_i32, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32),
                                ctypes.POINTER(_dbl)],
     "abft_wait_selftest": [_i32, _i64, ctypes.POINTER(_i32), _vp, _sz, _vp],
+    "abft_fp64_pipe_probe": [_i32, _i64, ctypes.POINTER(_dbl), _vp],
     "abft_potrf_sched": [_i64, _i64, _i32, ctypes.POINTER(_i32), _vp, _i64,
                          ctypes.POINTER(Fault), _i32, _dbl, ctypes.POINTER(Report), _vp, _sz, _vp],
 }
@@ -289,6 +290,15 @@ def wait_selftest(which, limit_ns=1000000, device="cuda", stream=None):
     rc = L.abft_wait_selftest(which, limit_ns, ctypes.byref(err), ctypes.c_void_p(ws.data_ptr()),
                               ctypes.byref(size), _stream(stream))
     return rc, err.value
+
+
+def fp64_pipe_probe(which, iters=20000, stream=None):
+    """FP64 multiply-add rate in TFLOP/s: which 0 = FMA, 1 = tensor-core MMA."""
+    out = _dbl(0.0)
+    rc = lib().abft_fp64_pipe_probe(which, iters, ctypes.byref(out), _stream(stream))
+    if rc != 0:
+        raise AbftError(rc, strerror(rc))
+    return out.value
 
 
 def _modes_array(modes, n, nb):
