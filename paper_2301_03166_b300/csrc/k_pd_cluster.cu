@@ -9,8 +9,8 @@
 // home CTA id % CL, slot id / CL; rows past kb are the identity) and factored
 // right-looking by tile columns p = 0 .. NT - 1:
 //   A  the home CTA of tile (p, p) factors it square-root free (L D L^T, one
-//      reciprocal per pivot on the dependent chain, the 32 square roots and
-//      the column scalings, true divisions, at the end);
+//      reciprocal per pivot on the dependent chain; the 32 square roots and
+//      the column scalings by their reciprocals at the end);
 //   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
 //      per row (lane l holds x_l), spread over every warp of the cluster; the
 //      division by L_jj is a multiplication by its reciprocal, formed once per
@@ -18,11 +18,15 @@
 //      dependent FP64 division costs hundreds of clocks; the reciprocals of the
 //      power-of-two pivots of exact integer cases are exact);
 //   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
-//      of 16 rows, are dealt round-robin to the CTAs; operands are fetched
-//      from their home CTAs through distributed shared memory.
+//      of 16 rows; operands are fetched from their home CTAs through
+//      distributed shared memory.  Look-ahead: the home CTA of tile
+//      (p + 1, p + 1) updates that tile first and factors it (A of the next
+//      step) while the other CTAs share the rest of the tiles.
 // The phases are separated by cluster barriers (hardware barriers, no spin).
-// Then every CTA writes its tiles back to A, and CTA 0 checks the PD checksum
-// relation (1^T L) L^T = c^T against the carried column checksum cc.
+// Then the PD checksum relation (1^T L) L^T = c^T is checked against the
+// carried column checksum cc from the tiles in shared memory (per-tile
+// partial sums in every CTA, added in a fixed order by CTA 0), and every CTA
+// writes its tiles back to A.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -93,59 +97,100 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             T[i * PLD + j] = v;
         }
     }
+    // (a, b), b <= a, of a trailing triangle in row-major order: the first
+    // m (m + 1) / 2 entries are the triangle of order m
+    __shared__ unsigned char s_ta[PT * (PT - 1) / 2], s_tb[PT * (PT - 1) / 2];
+    __shared__ double s_sc[PT];
+    __shared__ double s_sq[PT];
+    for (int e = t; e < PT * (PT - 1) / 2; e += PTHREADS) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        s_ta[e] = (unsigned char)a;
+        s_tb[e] = (unsigned char)(e - a * (a + 1) / 2);
+    }
     if (t == 0) s_fail = -1;
-    cl.sync();
-    int fail = -1;
-    for (int p = 0; p < NT; ++p) {
+    // A: diagonal tile (p, p) in its home CTA, square-root free (L D L^T,
+    // right-looking): per pivot one reciprocal of d_j on the dependent chain
+    // (an FP64 square root and a division per pivot cost 675 and 431 clocks on
+    // B300); the trailing entries take D[i][j] (D[l][j] / d_j), the quotient
+    // formed once per row l.  Then L = L_unit D^(1/2): column j is
+    // D[i][j] / sqrt(d_j), taken as a product with 1 / sqrt(d_j).  A
+    // non-positive d_j fails at the same pivot as the Cholesky recurrence
+    // (d_j is the value under its square root).
+    auto factor_diag = [&](int p) {
         const int idp = p * (p + 1) / 2 + p;
-        // A: the diagonal tile in its home CTA, square-root free (L D L^T,
-        // right-looking): per pivot one reciprocal of d_j on the dependent
-        // chain (an FP64 square root and a division per pivot cost 675 and 431
-        // clocks on B300); the trailing entries take D[i][j] D[l][j] / d_j.
-        // Then L = L_unit D^(1/2): column j is D[i][j] / sqrt(d_j), all 32
-        // square roots at once.  A non-positive d_j fails at the same pivot as
-        // the Cholesky recurrence (d_j is the value under its square root).
-        if (me == idp % CL) {
-            double* D = home + (idp / CL) * TILE;
-            for (int j = 0; j < PT; ++j) {
-                if (t == 0) {
-                    const double d = D[j * PLD + j];
-                    if (!(d > 0.0)) s_fail = j;
-                    else s_rinv[j] = 1.0 / d;
-                }
-                __syncthreads();
-                if (s_fail >= 0) break;
-                const double rj = s_rinv[j];
-                const int m = PT - 1 - j;
-                for (int e = t; e < m * (m + 1) / 2; e += PTHREADS) {
-                    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-                    while (a * (a + 1) / 2 > e) --a;
-                    while ((a + 1) * (a + 2) / 2 <= e) ++a;
-                    const int b = e - a * (a + 1) / 2;
-                    const int i = j + 1 + a, l = j + 1 + b;
-                    D[i * PLD + l] -= D[i * PLD + j] * (D[l * PLD + j] * rj);
-                }
-                __syncthreads();
+        double* D = home + (idp / CL) * TILE;
+        for (int j = 0; j < PT; ++j) {
+            if (t == 0) {
+                const double d = D[j * PLD + j];
+                if (!(d > 0.0)) s_fail = j;
+                else s_rinv[j] = 1.0 / d;
             }
-            if (s_fail < 0) {
-                if (t < PT) s_rinv[t] = sqrt(D[t * PLD + t]);   // sqrt(d_j)
-                __syncthreads();
-                for (int e = t; e < PT * PT; e += PTHREADS) {
-                    const int i = e >> 5, jj = e & 31;
-                    if (i > jj) D[i * PLD + jj] = D[i * PLD + jj] / s_rinv[jj];
-                }
-                __syncthreads();
-                if (t < PT) D[t * PLD + t] = s_rinv[t];
+            __syncthreads();
+            if (s_fail >= 0) return;
+            const double rj = s_rinv[j];
+            if (t > j && t < PT) s_sc[t] = D[t * PLD + j] * rj;
+            __syncthreads();
+            const int m = PT - 1 - j;
+            for (int e = t; e < m * (m + 1) / 2; e += PTHREADS) {
+                const int i = j + 1 + s_ta[e], l = j + 1 + s_tb[e];
+                D[i * PLD + l] -= D[i * PLD + j] * s_sc[l];
             }
+            __syncthreads();
         }
-        cl.sync();
-        {
-            const int f = *cl.map_shared_rank(&s_fail, idp % CL);
-            if (f >= 0) {
-                fail = p * PT + f;
-                break;
-            }
+        if (t < PT) {
+            const double sq = sqrt(D[t * PLD + t]);
+            s_sq[t] = sq;
+            s_rinv[t] = 1.0 / sq;
         }
+        __syncthreads();
+        for (int e = t; e < PT * PT; e += PTHREADS) {
+            const int i = e >> 5, jj = e & 31;
+            if (i > jj) D[i * PLD + jj] = D[i * PLD + jj] * s_rinv[jj];
+        }
+        __syncthreads();
+        if (t < PT) D[t * PLD + t] = s_sq[t];
+        __syncthreads();
+    };
+    // C item w of step p: half (w & 1) of the 16-row halves of trailing tile
+    // number w >> 1 (row-major over the lower triangle of the tiles below p):
+    // C(q, r) -= L(q, p) L(r, p)^T with the operands from their home CTAs
+    auto c_item = [&](int w, int p) {
+        const int tid = w >> 1, half = w & 1;
+        int a, b;
+        tile_of(tid, a, b);
+        const int q = p + 1 + a, r = p + 1 + b;
+        const double* Lq = tile_ptr(q, p);
+        const double* Lr = tile_ptr(r, p);
+        for (int e = t; e < 16 * PT; e += PTHREADS) {
+            const int i = 16 * half + (e >> 5), j = e & 31;
+            sQ[(e >> 5) * PLD + j] = Lq[i * PLD + j];
+        }
+        for (int e = t; e < PT * PT; e += PTHREADS) sR[(e >> 5) * PLD + (e & 31)] = Lr[(e >> 5) * PLD + (e & 31)];
+        __syncthreads();
+        double* C = tile_ptr(q, r);
+        // thread: row i (16) x columns l = (t & 15) + 16 c (2)
+        const int i = t >> 4, l0 = t & 15;
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < PT; ++k) {
+            const double lq = sQ[i * PLD + k];
+            acc0 = fma(lq, sR[l0 * PLD + k], acc0);
+            acc1 = fma(lq, sR[(l0 + 16) * PLD + k], acc1);
+        }
+        const int ci = 16 * half + i;
+        C[ci * PLD + l0] -= acc0;
+        C[ci * PLD + l0 + 16] -= acc1;
+        __syncthreads();
+    };
+    int fail = -1;
+    if (me == 0) factor_diag(0);   // tile 0 lives in CTA 0
+    cl.sync();
+    {
+        const int f = *cl.map_shared_rank(&s_fail, 0);
+        if (f >= 0) fail = f;
+    }
+    for (int p = 0; p < NT && fail < 0; ++p) {
         const int below = NT - 1 - p;
         if (below == 0) break;
         // B: rows of the panel tiles below, x L_pp^T = a, one warp per row
@@ -168,39 +213,91 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             }
         }
         cl.sync();
-        // C: trailing tiles in halves of 16 rows
+        // C with look-ahead: the home CTA of the next diagonal tile updates it
+        // first (items 0 and 1) and factors it (A of step p + 1) while the
+        // other CTAs share the rest of the trailing tiles (nothing else reads
+        // or writes that tile in this step)
         {
-            const int nitem = below * (below + 1);          // tiles x 2 halves
-            for (int w = me; w < nitem; w += CL) {
-                const int tid = w >> 1, half = w & 1;
-                int a, b;
-                tile_of(tid, a, b);
-                const int q = p + 1 + a, r = p + 1 + b;
-                const double* Lq = tile_ptr(q, p);
-                const double* Lr = tile_ptr(r, p);
-                for (int e = t; e < 16 * PT; e += PTHREADS) {
-                    const int i = 16 * half + (e >> 5), j = e & 31;
-                    sQ[(e >> 5) * PLD + j] = Lq[i * PLD + j];
-                }
-                for (int e = t; e < PT * PT; e += PTHREADS) sR[(e >> 5) * PLD + (e & 31)] = Lr[(e >> 5) * PLD + (e & 31)];
-                __syncthreads();
-                double* C = tile_ptr(q, r);
-                // thread: row i (16) x columns l = (t & 15) + 16 c (2)
-                const int i = t >> 4, l0 = t & 15;
-                double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll 8
-                for (int k = 0; k < PT; ++k) {
-                    const double lq = sQ[i * PLD + k];
-                    acc0 = fma(lq, sR[l0 * PLD + k], acc0);
-                    acc1 = fma(lq, sR[(l0 + 16) * PLD + k], acc1);
-                }
-                const int ci = 16 * half + i;
-                C[ci * PLD + l0] -= acc0;
-                C[ci * PLD + l0 + 16] -= acc1;
-                __syncthreads();
+            const int idn = (p + 1) * (p + 2) / 2 + p + 1, hn = idn % CL;
+            const int nitem = below * (below + 1);           // tiles x 2 halves
+            if (me == hn) {
+                c_item(0, p);
+                c_item(1, p);
+                factor_diag(p + 1);
+            } else {
+                const int rk = (me - hn - 1 + CL) % CL;     // 0 .. CL - 2
+                for (int w = 2 + rk; w < nitem; w += CL - 1) c_item(w, p);
+            }
+            cl.sync();
+            const int f = *cl.map_shared_rank(&s_fail, hn);
+            if (f >= 0) fail = (p + 1) * PT + f;
+        }
+    }
+    // PD check inputs while the tiles are in shared memory: every CTA adds the
+    // column sums of its tiles, part[(tile id) * PT + c] (rows past kb are
+    // identity rows, not part of L: skipped); CTA 0 then adds them per
+    // column in tile order
+    const bool do_check = fail < 0 && check;
+    __shared__ double s_part[PMAXT * (PMAXT + 1) / 2 * PT];   // rank 0: per-tile partials
+    if (do_check) {
+        for (int id = me; id < NTILE; id += CL) {
+            int q, r;
+            tile_of(id, q, r);
+            const double* T = home + (id / CL) * TILE;
+            double* dst = cl.map_shared_rank(s_part, 0) + id * PT;
+            if (t < PT) {
+                double sum = 0.0;
+                const int c = t;
+                for (int i = (q == r ? c : 0); i < PT && q * PT + i < kb; ++i) sum += T[i * PLD + c];
+                dst[c] = sum;
             }
         }
-        cl.sync();
+    }
+    cl.sync();
+    if (do_check && me == 0) {
+        for (int p = t; p < kb; p += PTHREADS) {
+            const int r = p / PT, c = p % PT;
+            double sum = 0.0;
+            for (int q = r; q < NT; ++q) sum += s_part[(q * (q + 1) / 2 + r) * PT + c];
+            s_cs[p] = sum;
+        }
+    }
+    cl.sync();
+    // y_j = sum_{p <= j} s_cs[p] L[j][p]: every CTA the rows of its tiles
+    // (partials per tile, reusing s_part in rank 0), CTA 0 adds them per row
+    if (do_check) {
+        const double* cs0 = cl.map_shared_rank(s_cs, 0);
+        for (int id = me; id < NTILE; id += CL) {
+            int q, r;
+            tile_of(id, q, r);
+            const double* T = home + (id / CL) * TILE;
+            for (int i = warp; i < PT; i += PWARPS) {
+                double y = 0.0;
+                const int c = lane;
+                if (q * PT + i < kb && (q > r || c <= i)) y = cs0[r * PT + c] * T[i * PLD + c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+                if (lane == 0) sD[id * PT + i] = y;   // sD, sQ, sR: free; gathered below
+            }
+        }
+    }
+    cl.sync();
+    if (do_check && me == 0) {
+        const double tau = st->tau;
+        for (int j = t; j < kb; j += PTHREADS) {
+            const int q = j / PT, i = j % PT;
+            double y = 0.0;
+            for (int r = 0; r <= q; ++r) {
+                const int id = q * (q + 1) / 2 + r;
+                y += cl.map_shared_rank(sD, id % CL)[id * PT + i];
+            }
+            const double d = y - cc[j];
+            if (!(fabs(d) <= tau)) {
+                atomicAdd(&st->detected, 1ull);
+                atomicAdd(&st->uncorrectable, 1ull);
+                record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+            }
+        }
     }
     // write back (the strict upper triangle of A is left as it is)
     if (fail < 0) {
@@ -216,30 +313,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     } else if (me == 0 && t == 0) {
         atomicCAS(&st->info, 0, (int)(K0 + fail + 1));
     }
-    cl.sync();
-    if (fail >= 0 || !check || me != 0) return;
-    // PD check: y_j = sum_{p <= j} (sum_{q >= p} L[q][p]) L[j][p] against cc[j]
-    for (int p = t; p < kb; p += PTHREADS) {
-        double s = 0.0;
-        for (int q = p; q < kb; ++q) s += A[(int64_t)q * lda + p];
-        s_cs[p] = s;
-    }
-    __syncthreads();
-    const double tau = st->tau;
-    for (int j = warp; j < kb; j += PWARPS) {
-        double y = 0.0;
-        for (int p = lane; p <= j; p += 32) y = fma(s_cs[p], A[(int64_t)j * lda + p], y);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-        if (lane == 0) {
-            const double d = y - cc[j];
-            if (!(fabs(d) <= tau)) {
-                atomicAdd(&st->detected, 1ull);
-                atomicAdd(&st->uncorrectable, 1ull);
-                record_event(st, step, EV_PD, K0 + j, K0 + j, d);
-            }
-        }
-    }
+    cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 template <int CL>
