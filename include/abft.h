@@ -29,6 +29,12 @@
  *  - Checksum block size g equals the block size nb (one checksum tile per
  *    matrix block, Sec. 3.1.2).  nb must be a positive multiple of 32 and at
  *    most 512.
+ *  - One GPU per process: several launchers raise their kernels' dynamic
+ *    shared-memory limit once per process (a per-device attribute), and the
+ *    look-ahead and the no-allocation entry point keep per-device state for
+ *    device indices below 16.  Several GPUs are driven by one process each
+ *    (the batched form splits its matrices over them with
+ *    abft_batched_partition).
  */
 #ifndef ABFT_H
 #define ABFT_H

@@ -118,3 +118,21 @@ def test_small_faults_located_like_the_oracle(dtype, bf16, mode):
     assert rep["tau"] < 5e-3
     Lo = np.tril(Lo)
     assert np.linalg.norm(L - Lo) <= 0.3 * np.linalg.norm(Lo - np.linalg.cholesky(A))
+
+
+def test_n4096_mixed_vs_oracle():
+    """n = 4096, block 256 (16 block columns, the look-ahead splits of the
+    full-size runs), BF16, faults at 1 per 10 steps: events equal to the mixed
+    oracle's, the first panel bit for bit, the factor within the same fraction
+    of the quantization's own effect as at the smaller orders."""
+    n, nb = 4096, 256
+    A = W.spd_mmt(n, seed=1000 + n)
+    faults = W.fault_schedule(n, nb, "cholesky", seed=2000 + n)
+    rc, L, rep = run(A, nb, abft.FULL, abft.MIXED_BF16, faults)
+    Lo, info, rep_o = oracle.potrf_mixed(A, nb, oracle.FULL, True, faults=faults)
+    Lo = np.tril(Lo)
+    assert rc == 0 and info == 0
+    assert ev(rep) == ev(rep_o) and len(ev(rep)) == len(faults)
+    assert np.array_equal(L[nb:, :nb], Lo[nb:, :nb])
+    L64 = np.linalg.cholesky(A)
+    assert np.linalg.norm(L - Lo) <= 0.3 * np.linalg.norm(Lo - L64)

@@ -166,3 +166,22 @@ def test_full_size_sampled(n):
     Lj = L[torch.as_tensor(jj, device=DEV)].cpu().numpy()
     recon = np.einsum("ij,ij->i", Li, Lj)
     assert np.abs(recon - A_lower_samples).max() <= 1e-13 * n
+
+
+def test_n4096_every_entry_vs_oracle():
+    """n = 4096, block 256, faults at 1 per 10 steps: the whole factor, not a
+    sample, against the oracle's, for the FP64 update and for the FP64-accurate
+    tensor-core update (the tile counts of the full-size runs: 16 block columns,
+    every look-ahead split); events equal to the oracle's."""
+    n, nb = 4096, 256
+    A = W.spd_mmt(n, seed=1000 + n)
+    faults = W.fault_schedule(n, nb, "cholesky", seed=2000 + n)
+    Lo, info_o, rep_o = oracle.potrf(A, nb, oracle.FULL, faults)
+    Lo = np.tril(Lo)
+    for dt in (abft.F64, abft.F64_EMU):
+        T = torch.from_numpy(A).to(DEV)
+        rc, rep = abft.potrf(T, nb, abft.FULL, dtype=dt, faults=faults)
+        torch.cuda.synchronize()
+        assert rc == 0 and info_o == 0
+        assert events(rep) == events(rep_o)
+        assert np.abs(np.tril(T.cpu().numpy()) - Lo).max() <= 1e-12 * np.abs(Lo).max()
