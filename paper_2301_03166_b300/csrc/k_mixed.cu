@@ -11,7 +11,7 @@
 // run as an FP32 SIMT GEMM.  The panel solve runs in FP32 (k_trsm_rlt<float>),
 // the diagonal-block factorization, verification and correction stay in FP64.
 //
-// Kernel anatomy: persistent, one CTA per SM (320 threads), the 128 x 128
+// Kernel anatomy: persistent, one CTA per SM (576 threads), the 128 x 128
 // output tiles of the lower block triangle dealt round-robin to the CTAs:
 //   warp 0   TMA producer: 128x64 BF16 boxes of A (rows i0..) and B (rows j0..)
 //            with 128-byte swizzle into a 4-stage ring of shared buffers
@@ -19,10 +19,12 @@
 //            issuer, alternating between the two accumulators so the next
 //            tile's MMAs run while the previous tile drains;
 //            tcgen05.commit releases each stage and signals the epilogue
-//   warps 2-9  tcgen05.ld of the FP32 accumulator (warp w reads lane quarter
-//            w % 4, column half (w - 2) / 4), staged in shared memory, the
+//   warps 2-17 tcgen05.ld of the FP32 accumulator (warp w reads lane quarter
+//            w % 4, column quarter (w - 2) / 4), staged in shared memory, the
 //            accumulator released, then a coalesced FP64 read-modify-write
-//            of C with the scales, 16 loads in flight per thread.
+//            of C with the scales, 16 loads in flight per thread (sixteen
+//            epilogue warps: the read-modify-write is latency-bound; eight
+//            had made the BF16 solve at n = 16384 1.7 ms slower).
 // Every mbarrier wait is bounded: on timeout the CTA records an error in the
 // status block, skips the rest of its work, frees its TMEM and returns.
 #include <cuda.h>
@@ -47,8 +49,8 @@ constexpr int TM = 128, TN = 128, KC = 64;
 constexpr int STAGES = 4;
 constexpr int HALF_BYTES = TM * KC * 2;              // one 128 x 64 16-bit box
 constexpr int STAGE_BYTES = 2 * HALF_BYTES;          // A box + B box
-constexpr int EPI_WARPS = 8;
-constexpr int MIX_THREADS = 64 + EPI_WARPS * 32;     // producer, MMA, 8 epilogue warps
+constexpr int EPI_WARPS = 16;
+constexpr int MIX_THREADS = 64 + EPI_WARPS * 32;     // producer, MMA, 16 epilogue warps
 constexpr uint32_t TMEM_COLS = 256;                  // two 128-column FP32 accumulators
 constexpr int STG_LD = TN + 1;                       // epilogue staging row stride (floats)
 constexpr int STG_BYTES = TM * STG_LD * 4;
@@ -202,7 +204,8 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
         // epilogue warps: TMEM lane quarter q = warp % 4, column half h
         const int ew = warp - 2;               // 0 .. EPI_WARPS-1
         const int q = warp & 3;
-        const int h = ew >> 2;                 // 0 or 1: columns [64 h, 64 h + 64)
+        constexpr int CPW = TN / (EPI_WARPS / 4);   // accumulator columns drained per warp
+        const int h = ew >> 2;                 // columns [CPW h, CPW h + CPW)
         int64_t it = 0;
         for (int64_t idx = blockIdx.x; idx < a.ntiles; idx += G) {
             int64_t ti, tj;
@@ -217,9 +220,9 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int r = q * 32 + lane;
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
+                for (int cc = 0; cc < CPW / 32; ++cc) {
                     uint32_t v[32];
-                    const int col = h * 64 + cc * 32;
+                    const int col = h * CPW + cc * 32;
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + col), v);
 #pragma unroll
                     for (int u = 0; u < 32; ++u) stg[r * STG_LD + col + u] = __uint_as_float(v[u]);
@@ -235,7 +238,8 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                 // the trailing matrix starts on a block boundary): one scale per tile
                 const double sc = a.sig[(i0 + a.off) / a.g] * a.sig[(j0 + a.off) / a.g];
                 // FP64 read-modify-write of the tile: warp ew takes rows
-                // ew + 32 g + 8 u (groups g < 4, u < 4) x 128 columns; the next
+                // ew + 4 E g + E u (E = EPI_WARPS; groups g < NG, u < 4) x 128
+                // columns; the next
                 // group's 16 loads are issued before this group's FMAs and
                 // stores (32 loads in flight per thread); C - sc * acc is one
                 // FMA on the FP64 pipe per element
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                 auto load_group = [&](int gq, double (&c)[4][TN / 32]) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int64_t i = i0 + ew + 32 * gq + 8 * u;
+                        const int64_t i = i0 + ew + 4 * EPI_WARPS * gq + EPI_WARPS * u;
 #pragma unroll
                         for (int t4 = 0; t4 < TN / 32; ++t4) {
                             const int64_t j = j0 + lane + 32 * t4;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
                     if (gq + 1 < NG) load_group(gq + 1, cv[(gq + 1) & 1]);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int rr = ew + 32 * gq + 8 * u;
+                        const int rr = ew + 4 * EPI_WARPS * gq + EPI_WARPS * u;
                         const int64_t i = i0 + rr;
                         if (i >= a.M) continue;
 #pragma unroll
