@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 
 namespace abft {
 
@@ -98,13 +99,73 @@ __device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* 
     __syncthreads();
 }
 
+// tile_sums for FP64 tiles in exact 64-bit fixed point: every entry rounded to
+// a multiple of 2^(vexp - 1075) (vexp bounds every entry's biased exponent:
+// the Schur complements of an SPD matrix are bounded by max a_ii, the panel by
+// its square root), the weighted sums in units 2^10 larger so that they stay
+// inside 64 bits; the integer pipes instead of the FP64 pipe, which the
+// update needs.  Returns false, with nothing written, when an entry exceeds
+// the bound (an injected error, a NaN): the caller then sums in FP64.
+__device__ bool tile_sums_fixed(const double* P, int64_t ld, int nr, int nc, int vexp,
+                                double* colsum, double* wsum, double* rowsum, double* part) {
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    long long c0 = 0, c1 = 0, w0 = 0, w1 = 0;
+    bool bad = false;
+    long long* irow = reinterpret_cast<long long*>(rowsum);
+#pragma unroll 4
+    for (int i = w; i < nr; i += BT / 32) {
+        const double* row = P + (int64_t)i * ld;
+        const long long q0 = l < nc ? to_fixed(row[l], vexp, bad) : 0ll;
+        const long long q1 = l + 32 < nc ? to_fixed(row[l + 32], vexp, bad) : 0ll;
+        c0 += q0;
+        c1 += q1;
+        w0 += (long long)(i + 1) * (q0 >> 10);
+        w1 += (long long)(i + 1) * (q1 >> 10);
+        const long long rs = warp_sum_ll(q0 + q1);
+        if (l == 0) irow[i] = rs;
+    }
+    if (__syncthreads_or(bad ? 1 : 0)) return false;
+    long long* pc = reinterpret_cast<long long*>(part);   // [8][64] column partials
+    long long* pw = pc + 8 * 64;                          // [8][64] weighted partials
+    pc[w * 64 + l] = c0;
+    pc[w * 64 + l + 32] = c1;
+    pw[w * 64 + l] = w0;
+    pw[w * 64 + l + 32] = w1;
+    __syncthreads();
+    const double unit = ldexp(1.0, vexp - 1075), wunit = ldexp(1.0, vexp - 1065);
+    for (int j = t; j < nc; j += BT) {
+        long long s = 0, sw = 0;
+        for (int q = 0; q < BT / 32; ++q) {
+            s += pc[q * 64 + j];
+            sw += pw[q * 64 + j];
+        }
+        colsum[j] = (double)s * unit;
+        wsum[j] = (double)sw * wunit;
+    }
+    for (int i = t; i < nr; i += BT) rowsum[i] = (double)irow[i] * unit;
+    __syncthreads();
+    return true;
+}
+
+template <typename T>
+__device__ void tile_sums_any(const T* P, int64_t ld, int nr, int nc, int vexp, T* colsum, T* wsum,
+                              T* rowsum, T* part) {
+    if constexpr (sizeof(T) == 8) {
+        if (vexp > 0 && tile_sums_fixed((const double*)P, ld, nr, nc, vexp, (double*)colsum,
+                                        (double*)wsum, (double*)rowsum, (double*)part))
+            return;
+    }
+    tile_sums<T>(P, ld, nr, nc, colsum, wsum, rowsum, part);
+}
+
 // Verify one tile against its carried checksums and correct it (same rules as
 // the large-matrix kernel).  single = 1: weighted column checksums only.
 template <typename T>
 __device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T* cc, T* cw, T* cr,
                             int crs, T tau, int single, int step, abft_batch_status* st,
-                            T* colsum, T* wsum, T* rowsum, T* part, int* sflag, int* s_first) {
-    tile_sums<T>(P, ld, nr, nc, colsum, wsum, rowsum, part);
+                            T* colsum, T* wsum, T* rowsum, T* part, int* sflag, int* s_first,
+                            int vexp) {
+    tile_sums_any<T>(P, ld, nr, nc, vexp, colsum, wsum, rowsum, part);
     const int t = threadIdx.x;
     if (t == 0) { sflag[0] = 0; sflag[1] = 0; sflag[2] = 1 << 30; sflag[3] = 1 << 30; }
     __syncthreads();
@@ -199,6 +260,12 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     T dmax = 0;
     for (int w = 0; w < BT / 32; ++w) dmax = fmax(dmax, colsum[w]);
     const T tau = tau_scale * (T)8 * u * (T)n * (T)B * dmax;
+    // fixed-point bound of the FP64 sums: max(max a_ii, sqrt(max a_ii))
+    int vexp = 0;
+    if (sizeof(T) == 8) {
+        const double bnd = fmax((double)dmax, sqrt((double)dmax));
+        if (bnd > 0.0 && bnd < 1e300) vexp = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+    }
     __syncthreads();
     // mirror the diagonal blocks (save their strict upper triangles)
     for (int K = 0; K < nt; ++K) {
@@ -216,8 +283,8 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         for (int I = 0; I < nt; ++I)
             for (int J = 0; J <= I; ++J) {
                 const int r0 = I * B, c0 = J * B, nr = min(B, n - r0), nc = min(B, n - c0);
-                tile_sums<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, colsum, wsum, rowsum,
-                             &sJ[0][0]);
+                tile_sums_any<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, vexp, colsum, wsum,
+                                 rowsum, &sJ[0][0]);
                 for (int j = t; j < nc; j += BT) {
                     S.Cc[I * MAXN + c0 + j] = colsum[j];
                     S.Cw[I * MAXN + c0 + j] = wsum[j];
@@ -325,7 +392,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 const int r0 = I * B, nr = min(B, n - r0);
                 verify_tile<T>(A + (int64_t)r0 * lda + K0, lda, r0, K0, nr, kb,
                                S.Cc + I * MAXN + K0, S.Cw + I * MAXN + K0, nullptr, 0, tau, 1, k,
-                               st, colsum, wsum, rowsum, &sJ[0][0], sflag, s_first);
+                               st, colsum, wsum, rowsum, &sJ[0][0], sflag, s_first, vexp);
             }
         // ---- TMU over the lower block triangle with the checksum borders.
         // sL is free from here to the next PD: it holds the carried checksum
@@ -446,7 +513,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     verify_tile<T>(A + (int64_t)r0 * lda + c0, lda, r0, c0, nr, nc,
                                    S.Cc + I * MAXN + c0, S.Cw + I * MAXN + c0,
                                    S.Cr + r0 * MAXNT + J, MAXNT, tau, 0, k, st, colsum, wsum,
-                                   rowsum, &sJ[0][0], sflag, s_first);
+                                   rowsum, &sJ[0][0], sflag, s_first, vexp);
                 }
     }
     __syncthreads();

@@ -119,28 +119,6 @@ __device__ void tile_sums(const double* T, int64_t ldt, int nr, int nc, double* 
     }
 }
 
-// An entry as a signed multiple of 2^(vexp - 1075), rounded to nearest (half
-// away from zero); bad = true when its exponent exceeds vexp (or it is not
-// finite).
-__device__ __forceinline__ long long to_fixed(double x, int vexp, bool& bad) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ffull);
-    if (e > vexp) {
-        bad = true;
-        return 0;
-    }
-    const unsigned long long mant = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-    const int sh = vexp - (e ? e : 1);
-    const unsigned long long q = sh >= 64 ? 0ull : (sh == 0 ? mant : ((mant >> (sh - 1)) + 1ull) >> 1);
-    return (b >> 63) ? -(long long)q : (long long)q;
-}
-
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // tile_sums in exact 64-bit fixed point (same outputs, converted to double
 // once per sum).  Returns false, with nothing written, when an entry of the
 // tile exceeds the bound: the caller then sums in FP64.
