@@ -548,6 +548,7 @@ def run_ours(args, ws, rank, local):
         ms_fp64, _ = timed(fp64_solve, 1, 1)
         mixed = {"fp64_ms_to_solution": ms_fp64, "fp64_board_joules": last_joules[0]}
         amax_diag = float(A0.diagonal().max().item())
+        small = [(f[0], f[1], f[2], f[3], 1e-2) for f in faults]   # the same places, delta 1e-2
         for name, dt in (("bf16", abft.MIXED_BF16), ("f16", abft.MIXED_F16)):
             def mixed_solve():
                 return abft.posv_ir(A0, B, nb, dt, abft.FULL, tol=1e-12, maxit=100, faults=faults,
@@ -567,6 +568,14 @@ def run_ours(args, ws, rank, local):
                                "max_ratio_clean": rep_m["max_ratio"], "tau_max": rep_m["tau"],
                                "smallest_detectable_delta": rep_m["tau"] * (1 + rep_m["max_ratio"]),
                                "scalar_fp32_tau_it_replaces": 8 * 2.0 ** -24 * n * nb * amax_diag}}
+            # the same factorization with errors of 1e-2 (below the scalar bound it
+            # replaces) at the same places: each located and corrected
+            Lbuf.copy_(A0)
+            rc_s, rep_s = abft.potrf(Lbuf, nb, abft.FULL, dtype=dt, faults=small, workspace=wsp)
+            mixed[name]["detector"]["small_faults"] = {
+                "delta": 1e-2, "injected": len(small), "corrected": rep_s["corrected"],
+                "located_at_injected": [(e[0], e[2], e[3]) for e in rep_s["loc"]] ==
+                sorted((f[0], f[2], f[3]) for f in small)}
         del Lbuf, Xb, B
 
     lookahead = None

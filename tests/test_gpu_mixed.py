@@ -88,3 +88,21 @@ def test_full_size_n16384(dtype):
     Lj = L[torch.as_tensor(jj, device=DEV)].cpu().numpy()
     u = U_BF16 if dtype == abft.MIXED_BF16 else U_F16
     assert np.abs(np.einsum("ij,ij->i", Li, Lj) - Aij).max() <= 8 * u
+
+
+@pytest.mark.parametrize("dtype", [abft.MIXED_BF16, abft.MIXED_F16])
+def test_full_size_small_faults(dtype):
+    """n = 16384: errors of 1e-2 -- four hundred times below the scalar FP32
+    bound 8 u32 n g max a_ii (about 4.1) that the abs-checksum thresholds
+    replace -- at 1 per 10 steps are each located at the injected position
+    and corrected; the clean tiles stay far below their thresholds."""
+    n, nb = 16384, 256
+    Ad = W.spd_mmt_torch(n, seed=1000 + n, device=DEV)
+    faults = [(f[0], f[1], f[2], f[3], 1e-2) for f in W.fault_schedule(n, nb, "cholesky", seed=2000 + n)]
+    rc, rep = abft.potrf(Ad, nb, abft.FULL, dtype=dtype, faults=faults)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert events(rep) == sorted((f[0], 0, f[2], f[3]) for f in faults)
+    assert rep["corrected"] == len(faults) and rep["uncorrectable"] == 0
+    assert all(abs(e[4] - 1e-2) < 1e-4 for e in rep["loc"])
+    assert rep["tau"] < 5e-3 and rep["max_ratio"] < 1e-2
