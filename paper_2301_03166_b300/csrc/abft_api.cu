@@ -483,35 +483,16 @@ int chol_steps(int64_t n, int64_t nb, int32_t mode, const int32_t* modes, double
                                                cfall, ncfall, st, ss, part == PART_REST ? w1 : 0,
                                                part == PART_NEXT ? 1 : 0, maxg));
                 if (check) {
-                    BorderSegHost bs[4] = {};
-                    // column-sum rows: c_I -= sigma_I sigma_J (t_I Lq_J^T)
-                    bs[0].A = tq32 + ((k + 1) * ncq) * kb; bs[0].a_half = 2; bs[0].lda = kb;
-                    bs[0].B = Lq + c0 * kb; bs[0].b_half = 1; bs[0].ldb = kb;
-                    bs[0].C = CS + ((k + 1) * nc) * n + T0 + c0; bs[0].ldc = n;
-                    bs[0].M = (nt - k - 1) * nc; bs[0].N = c1 - c0; bs[0].K = kb;
-                    bs[0].r_off = 0; bs[0].r_div = nc; bs[0].r_base = k + 1;
-                    bs[0].c_off = T0 + c0; bs[0].c_div = g; bs[0].c_base = 0;
-                    // row-sum columns: r_I -= sigma_I sigma_J (Lq_I t_J^T)
-                    bs[1].A = Lq; bs[1].a_half = 1; bs[1].lda = kb;
-                    bs[1].B = tq32 + (J0 * ncq) * kb; bs[1].b_half = 2; bs[1].ldb = ncq * kb;
-                    bs[1].C = Cr + T0 * nt + J0; bs[1].ldc = nt;
-                    bs[1].M = m; bs[1].N = J1 - J0; bs[1].K = kb;
-                    bs[1].r_off = T0; bs[1].r_div = g; bs[1].r_base = 0;
-                    bs[1].c_off = 0; bs[1].c_div = 1; bs[1].c_base = J0;
-                    // abs-checksum rows: |c|_I += sigma_I sigma_J ((1^T |Lq_I|) |Lq_J|^T)
-                    bs[2] = bs[0];
-                    bs[2].A = ta32 + (k + 1) * kb; bs[2].lda = kb;
-                    bs[2].C = nullptr; bs[2].C32 = Ca + (k + 1) * n + T0 + c0;
-                    bs[2].M = nt - k - 1; bs[2].r_div = 1;
-                    bs[2].b_abs = 1; bs[2].plus = 1;
-                    // abs-checksum columns: |r|_I += sigma_I sigma_J (|Lq_I| (1^T |Lq_J|)^T)
-                    bs[3] = bs[1];
-                    bs[3].B = ta32 + J0 * kb; bs[3].ldb = kb;
-                    bs[3].C = nullptr; bs[3].C32 = Ra + T0 * nt + J0;
-                    bs[3].a_abs = 1; bs[3].plus = 1;
-                    // segments: checksum rows, abs rows, then (full) checksum and abs columns
-                    BorderSegHost ord[4] = {bs[0], bs[2], bs[1], bs[3]};
-                    ABFT_CUDA_TRY(launch_border_mixed(ord, full ? 4 : 2, bf16, sig, st, ss));
+                    // checksum borders from the same quantized panel (one product
+                    // per panel row and checksum vector, written to both borders)
+                    BorderSymHost bh{};
+                    bh.Lq = Lq; bh.m = m; bh.K = kb; bh.bf16 = bf16;
+                    bh.tq = tq32; bh.ta = ta32; bh.nc = (int)ncq; bh.Jb = k + 1; bh.Je = nt;
+                    bh.CS = CS; bh.Ca = Ca; bh.ldcs = n; bh.T0 = T0;
+                    bh.Cr = full ? Cr : nullptr; bh.Ra = full ? Ra : nullptr; bh.ldr = nt;
+                    bh.c0 = c0; bh.c1 = c1; bh.J0 = J0; bh.J1 = J1;
+                    bh.g = g; bh.sig = sig;
+                    ABFT_CUDA_TRY(launch_border_sym(bh, st, ss));
                 }
             } else {
                 // TMU with the checksum borders folded into the same launch

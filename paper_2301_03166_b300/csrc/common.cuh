@@ -239,20 +239,28 @@ cudaError_t launch_qr_tau(const double* A, int64_t lda, int64_t n, int64_t g, do
                           DevStatus* st, cudaStream_t s);
 
 // Mixed-precision TMU kernels (k_mixed.cu).
-struct BorderSegHost {
-    const void* A;
-    int a_half;          // 1: 16-bit quantized operand, 0: FP64, 2: FP32
-    int64_t lda;
-    const void* B;
-    int b_half;
-    int64_t ldb;
-    double* C;
-    int64_t ldc;
-    int64_t M, N, K;
-    int64_t r_off, r_div, r_base, c_off, c_div, c_base;
-    int a_abs = 0, b_abs = 0;   // use |A| / |B| (the abs-checksum products)
-    int plus = 0;               // C += ... instead of C -= ...
-    float* C32 = nullptr;       // FP32 output (C unused): the abs-checksums
+// Checksum borders of the mixed update of trailing rows T0 + [0, m): the
+// products of the quantized panel rows Lq_j with the FP32 checksum vectors of
+// blocks [Jb, Je) (nc signed sums per block in tq, one abs sum in ta).  Rows
+// j in [c0, c1) update the column-checksum rows CS / Ca; blocks J in [J0, J1)
+// update the row-checksum columns Cr / Ra (null: single-side checksums).
+struct BorderSymHost {
+    const uint16_t* Lq;
+    int64_t m, K;
+    int bf16;
+    const float* tq;
+    const float* ta;
+    int nc;
+    int64_t Jb, Je;
+    double* CS;
+    float* Ca;
+    int64_t ldcs, T0;
+    double* Cr;
+    float* Ra;
+    int64_t ldr;
+    int64_t c0, c1, J0, J1;
+    int64_t g;
+    const double* sig;
 };
 // tabs32 (nullable): 1^T |Lq_I| per tile-row, FP32, at tabs32[I kb + p].
 cudaError_t launch_quant_panel(const double* P, int64_t lda, int64_t T0, int64_t n, int64_t kb,
@@ -263,8 +271,7 @@ cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16
                              int64_t ldc, int64_t g, int64_t off, const double* sig,
                              const ComputeFault* cf, int ncf, DevStatus* st, cudaStream_t s,
                              int64_t o = 0, int strip = 0, int max_grid = 0);
-cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
-                                const DevStatus* st, cudaStream_t s);
+cudaError_t launch_border_sym(const BorderSymHost& h, const DevStatus* st, cudaStream_t s);
 
 // Solves and iterative refinement (k_solve.cu).
 int potrs_max_rhs();

@@ -32,6 +32,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cooperative_groups.h>
+#include <algorithm>
+#include <climits>
 #include <math.h>
 
 #include "common.cuh"
@@ -398,109 +400,300 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     }
 }
 
-// Small FP32 GEMM for the checksum borders of the mixed update:
-// C_f64[i][j] -= sr(i) sc(j) sum_p A[i][p] B[j][p], A rows FP64 (t sums) or
-// 16-bit (the quantized panel), B likewise; sr / sc are tile scales.
-struct BorderSeg {
-    const void* A;      // rows of K
-    int a_half;         // 1: A is 16-bit (BF16 / FP16 per `bf16`), 0: FP64, 2: FP32
-    int64_t lda;
-    const void* B;
-    int b_half;
-    int64_t ldb;
-    double* C;
-    int64_t ldc;
-    int64_t M, N, K;
-    // scale index of row i: (i + r_off) / r_div + r_base; of column j likewise
-    int64_t r_off, r_div, r_base, c_off, c_div, c_base;
-    int a_abs, b_abs;   // the abs-checksum products use |A| and |B|
-    int plus;           // abs-checksums grow: C += instead of C -=
-    float* C32;         // FP32 output instead of C (the abs-checksums)
+// Checksum borders of the mixed update.  Every border product is a dot
+// product of one trailing panel row Lq_j (16-bit, K values) with one checksum
+// vector of a block J: the column sums t_J and weighted sums tw_J (FP32,
+// signed) or the abs sums 1^T |Lq_J| (FP32, against |Lq_j|).  By the symmetry
+// of L L^T the column-checksum rows (c_J -= sigma_J sigma_I t_J Lq_j^T, for
+// the columns j of the part) and the row-checksum columns (r_I -= sigma_I
+// sigma_J Lq_j t_J^T, for the blocks J of the part) are the same dot
+// products, so each is computed once and written to both borders.
+// A job is a range of panel rows times a range of vectors of one kind; a CTA
+// computes an RT x VC tile of it as an FP32 SIMT GEMM over K in chunks of 32
+// (the next chunk copied by cp.async while this one is multiplied, the 16-bit
+// rows widened to FP32 in shared memory), every dot product summed with fmaf
+// in order of increasing k.
+// The scales are powers of two: sigma_I sigma_J acc is formed by exponent
+// arithmetic, so the epilogue's only FP64 operation is the update of C.
+struct BJob {
+    int64_t r0, r1;     // panel rows [r0, r1)
+    int v0, v1;         // vectors [v0, v1) of the kind's list
+    int vstep;          // list index v is vector u = v vstep (2: plain sums only)
+    int kind;           // 0: signed (t, tw), 1: abs
+    int cfg;            // tile shape (BCfg)
+    int64_t nvc;        // vector chunks
+    int64_t cta0;       // first CTA of the job
 };
-constexpr int MAX_BSEG = 4;
-struct BorderArgs {
-    BorderSeg seg[MAX_BSEG];
-    int64_t tn[MAX_BSEG], start[MAX_BSEG + 1];
-    int nseg;
+constexpr int MAX_BJOB = 6;
+struct BSymArgs {
+    const uint16_t* Lq;
+    int64_t m, K;
     int bf16;
+    const float* tq;    // signed vectors: u-th at tq + (Jb nc + u) K
+    const float* ta;    // abs vectors: u-th at ta + (Jb + u) K
+    int nc;             // signed vectors per block
+    int64_t Jb;         // block of vector 0
+    double* CS;         // column-checksum rows: (J nc + s, T0 + j), leading dimension ldcs
+    float* Ca;          // abs-checksum rows: (J, T0 + j), leading dimension ldcs
+    int64_t ldcs, T0;
+    double* Cr;         // row-checksum columns: (T0 + j, J), leading dimension ldr; null: none
+    float* Ra;          // abs row-checksum columns
+    int64_t ldr;
+    int64_t c0, c1;     // rows j in [c0, c1) update the column-checksum rows
+    int64_t J0, J1;     // blocks J in [J0, J1) update the row-checksum columns
+    int64_t g;
     const double* sig;
     const DevStatus* st;
+    int njob;
+    BJob job[MAX_BJOB];
 };
 
-__device__ __forceinline__ float ld_op(const void* p, int half, int bf16, int64_t idx) {
-    if (half == 2) return ((const float*)p)[idx];
-    if (!half) return (float)((const double*)p)[idx];
-    uint16_t b = ((const uint16_t*)p)[idx];
-    return bf16 ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+constexpr int BKC = 32;            // K chunk
+constexpr int BLD = BKC + 4;       // shared row stride (floats): conflict-free float4 reads
+constexpr int BTHREADS = 256;
+// Tile shapes: TR x TV threads, each RPT rows x VPT vectors.  Per 4 k a thread
+// reads RPT + VPT float4 from shared memory (a 128-bit shared load costs four
+// wavefronts even when broadcast) for 4 RPT VPT FMAs, so the bulk shape 8 x 4
+// keeps the shared pipe at two thirds of the FMA rate; its 128 x 64 tile does
+// 16 FMAs per byte brought from L2.
+template <int TR_, int TV_, int RPT_, int VPT_>
+struct BShape {
+    static constexpr int TR = TR_, TV = TV_, RPT = RPT_, VPT = VPT_;
+    static constexpr int RT = TR * RPT, VC = TV * VPT;
+    static_assert(TR * TV == BTHREADS, "threads");
+    static constexpr int LU = RT * BKC / 8;           // 8-value units of the Lq chunk
+    static constexpr int TU = VC * BKC / 4;           // float4 units of the vector chunk
+    static constexpr int LPT = (LU + BTHREADS - 1) / BTHREADS, TPT = (TU + BTHREADS - 1) / BTHREADS;
+};
+using BBulk = BShape<16, 16, 8, 4>;    // 128 rows x 64 vectors
+using BTiny = BShape<16, 16, 2, 1>;    // 32 x 16: jobs too small to fill the GPU in bulk tiles
+using BSkinny = BShape<64, 4, 2, 1>;   // 128 x 4: a handful of vectors (the look-ahead's row sums)
+constexpr int BLR = BKC + 8;       // raw 16-bit row stride (elements): 16-byte aligned rows
+// widened rows, two vector buffers and the raw rows, in floats
+constexpr int bsmem(int rt, int vc) { return (rt + 2 * vc) * BLD + rt * BLR / 2; }
+constexpr int BSMEM_FLOATS = bsmem(128, 64);   // the largest shape (BBulk)
+static_assert(bsmem(128, 4) <= BSMEM_FLOATS && bsmem(32, 16) <= BSMEM_FLOATS, "shared");
+constexpr int bcfg_rt(int c) { return c == 0 ? BBulk::RT : (c == 1 ? BTiny::RT : BSkinny::RT); }
+constexpr int bcfg_vc(int c) { return c == 0 ? BBulk::VC : (c == 1 ? BTiny::VC : BSkinny::VC); }
+
+// exponent of a power of two (sigma), or INT_MIN for 0 / Inf / NaN / subnormal
+__device__ __forceinline__ int pow2_exp(double s) {
+    const int e = (__double2hiint(s) >> 20) & 0x7ff;
+    return (e == 0 || e == 0x7ff) ? INT_MIN : e - 1023;
 }
 
-__global__ void __launch_bounds__(256) k_border_mixed(BorderArgs a) {
-    __shared__ float As[16][65], Bs[16][65];
-    if (a.st->info != 0) return;
-    const int64_t bid = blockIdx.x;
-    int s = 0;
-    while (s + 1 < a.nseg && bid >= a.start[s + 1]) ++s;
-    const BorderSeg& g = a.seg[s];
-    const int64_t local = bid - a.start[s];
-    const int64_t i0 = (local / a.tn[s]) * 64, j0 = (local % a.tn[s]) * 64;
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int lr = t >> 2, lk = (t & 3) * 4;
-    float acc[4][4] = {};
-    // the next K chunk's operands are loaded into registers while the current
-    // chunk is multiplied from shared memory
-    float pa[4], pb[4];
-    auto fetch = [&](int64_t k0) {
+// x 2^e (|e| < 1000, so 2^e is a normal double): by exponent arithmetic when
+// x and the result are normal, else as the FP64 product with 2^e
+__device__ __forceinline__ double scale_f64(double x, int e) {
+    const int hi = __double2hiint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex != 0 && ex != 0x7ff && ex + e > 0 && ex + e < 0x7ff)
+        return __hiloint2double(hi + (e << 20), __double2loint(x));
+    return x * __hiloint2double((e + 1023) << 20, 0);
+}
+
+// 16-byte global -> shared copy (cp.async), zero-filled when !pred
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <class S>
+__device__ __forceinline__ void border_tile(const BSymArgs& a, const BJob& jb, int64_t rtile,
+                                            int64_t vchunk, float* sm) {
+    float* const Ls = sm;                               // [RT][BLD] FP32 (widened, |.| for abs jobs)
+    float* const Tb = sm + S::RT * BLD;                 // [2][VC][BLD] FP32 vectors
+    uint16_t* const Lr = (uint16_t*)(Tb + 2 * S::VC * BLD);   // [RT][BLR] raw 16-bit rows
+    const int t = threadIdx.x, tv = t % S::TV, tr = t / S::TV;
+    const int64_t r0 = jb.r0 + rtile * S::RT;
+    const int vbase = jb.v0 + (int)vchunk * S::VC;
+    const int ncK = jb.kind ? 1 : a.nc;
+    const float* vecs = jb.kind ? a.ta + a.Jb * a.K : a.tq + a.Jb * a.nc * a.K;
+    const bool absl = jb.kind != 0;
+    // chunk k0 -> shared memory by cp.async: raw panel rows to Lr, vectors to Td
+    auto fetch = [&](int64_t k0, float* Td) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t k = k0 + lk + u, i = i0 + lr, j = j0 + lr;
-            pa[u] = (i < g.M && k < g.K) ? ld_op(g.A, g.a_half, a.bf16, i * g.lda + k) : 0.f;
-            pb[u] = (j < g.N && k < g.K) ? ld_op(g.B, g.b_half, a.bf16, j * g.ldb + k) : 0.f;
-            if (g.a_abs) pa[u] = fabsf(pa[u]);
-            if (g.b_abs) pb[u] = fabsf(pb[u]);
-        }
-    };
-    fetch(0);
-    for (int64_t k0 = 0; k0 < g.K; k0 += 16) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            As[lk + u][lr] = pa[u];
-            Bs[lk + u][lr] = pb[u];
-        }
-        __syncthreads();
-        if (k0 + 16 < g.K) fetch(k0 + 16);
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int64_t i = i0 + ty + 16 * r;
-        if (i >= g.M) continue;
-        const double sr = a.sig[(i + g.r_off) / g.r_div + g.r_base];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t j = j0 + tx + 16 * c;
-            if (j >= g.N) continue;
-            const double sc = a.sig[(j + g.c_off) / g.c_div + g.c_base];
-            if (g.C32) {   // abs-checksums: FP32 (they only scale a threshold)
-                g.C32[i * g.ldc + j] += (float)(sr * sc) * acc[r][c];
-                continue;
+        for (int q = 0; q < S::LPT; ++q) {
+            const int u = t + BTHREADS * q;
+            if (u < S::LU) {
+                const int64_t row = r0 + u / (BKC / 8);
+                const bool ok = row < jb.r1;
+                const uint16_t* src = a.Lq + (ok ? row : jb.r0) * a.K + k0 + (u % (BKC / 8)) * 8;
+                cp_async16(Lr + (u / (BKC / 8)) * BLR + (u % (BKC / 8)) * 8, src, ok);
             }
-            const double v = (sr * sc) * (double)acc[r][c];
-            if (g.plus) g.C[i * g.ldc + j] += v;
-            else g.C[i * g.ldc + j] -= v;
+        }
+#pragma unroll
+        for (int q = 0; q < S::TPT; ++q) {
+            const int u = t + BTHREADS * q;
+            if (u < S::TU) {
+                const int v = vbase + u / (BKC / 4);
+                const bool ok = v < jb.v1;
+                const float* src = vecs + (int64_t)(ok ? v : jb.v0) * jb.vstep * a.K + k0 + (u % (BKC / 4)) * 4;
+                cp_async16(Td + (u / (BKC / 4)) * BLD + (u % (BKC / 4)) * 4, src, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    auto widen = [&](uint32_t h) -> float {
+        const uint16_t b = (uint16_t)h;
+        const float f = a.bf16 ? __uint_as_float((uint32_t)b << 16) : __half2float(__ushort_as_half(b));
+        return absl ? fabsf(f) : f;
+    };
+    float acc[S::RPT][S::VPT];
+#pragma unroll
+    for (int i = 0; i < S::RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < S::VPT; ++j) acc[i][j] = 0.f;
+    fetch(0, Tb);
+    int buf = 0;
+    for (int64_t k0 = 0; k0 < a.K; k0 += BKC, buf ^= 1) {
+        cp_async_wait_all();
+        __syncthreads();   // chunk k0 landed; the previous chunk's products are done
+#pragma unroll
+        for (int q = 0; q < S::LPT; ++q) {
+            const int u = t + BTHREADS * q;
+            if (u < S::LU) {
+                const int row = u / (BKC / 8), c8 = (u % (BKC / 8)) * 8;
+                const uint4 raw = *(const uint4*)(Lr + row * BLR + c8);
+                const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    f[2 * e] = widen(w[e] & 0xffffu);
+                    f[2 * e + 1] = widen(w[e] >> 16);
+                }
+                float* d = Ls + row * BLD + c8;
+                *(float4*)d = make_float4(f[0], f[1], f[2], f[3]);
+                *(float4*)(d + 4) = make_float4(f[4], f[5], f[6], f[7]);
+            }
+        }
+        __syncthreads();   // Ls ready, Lr free
+        if (k0 + BKC < a.K) fetch(k0 + BKC, Tb + (buf ^ 1) * (S::VC * BLD));
+        const float* Ts = Tb + buf * (S::VC * BLD);
+#pragma unroll
+        for (int k4 = 0; k4 < BKC; k4 += 4) {
+            float4 tt[S::VPT];
+#pragma unroll
+            for (int j = 0; j < S::VPT; ++j) tt[j] = *(const float4*)(Ts + (tv + S::TV * j) * BLD + k4);
+#pragma unroll
+            for (int i = 0; i < S::RPT; ++i) {
+                const float4 l = *(const float4*)(Ls + (tr + S::TR * i) * BLD + k4);
+#pragma unroll
+                for (int j = 0; j < S::VPT; ++j) {
+                    acc[i][j] = fmaf(tt[j].x, l.x, acc[i][j]);
+                    acc[i][j] = fmaf(tt[j].y, l.y, acc[i][j]);
+                    acc[i][j] = fmaf(tt[j].z, l.z, acc[i][j]);
+                    acc[i][j] = fmaf(tt[j].w, l.w, acc[i][j]);
+                }
+            }
         }
     }
+    // epilogue: scatter each product to the borders that hold it.  The
+    // read-modify-writes go in groups of G rows: all loads of a group are
+    // issued before its first store (the borders may alias as far as the
+    // compiler knows, so one load per store would serialize on latency).
+    const bool rowsums = a.Cr != nullptr;
+    int64_t Jv[S::VPT];
+    int sv[S::VPT], eJ[S::VPT];
+    bool vok[S::VPT];
+#pragma unroll
+    for (int j = 0; j < S::VPT; ++j) {
+        const int v = vbase + tv + S::TV * j;
+        vok[j] = v < jb.v1;
+        const int uu = (vok[j] ? v : jb.v0) * jb.vstep;
+        Jv[j] = a.Jb + uu / ncK;
+        sv[j] = uu % ncK;
+        eJ[j] = pow2_exp(a.sig[Jv[j]]);
+    }
+    constexpr int G = S::RPT < 2 ? S::RPT : 2;
+#pragma unroll
+    for (int i0 = 0; i0 < S::RPT; i0 += G) {
+        int64_t jr[G];
+        int eI[G];
+        bool rok[G], toc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            jr[g] = r0 + tr + S::TR * (i0 + g);
+            rok[g] = jr[g] < jb.r1;
+            eI[g] = rok[g] ? pow2_exp(a.sig[(a.T0 + jr[g]) / a.g]) : 0;
+            toc[g] = rok[g] && jr[g] >= a.c0 && jr[g] < a.c1;
+        }
+        auto cpos = [&](int g, int j) -> int64_t {
+            return (jb.kind ? Jv[j] : Jv[j] * a.nc + sv[j]) * a.ldcs + a.T0 + jr[g];
+        };
+        auto rpos = [&](int g, int j) -> int64_t { return (a.T0 + jr[g]) * a.ldr + Jv[j]; };
+        auto wc = [&](int g, int j) { return toc[g] && vok[j]; };
+        auto wr = [&](int g, int j) {
+            return rok[g] && vok[j] && rowsums && sv[j] == 0 && Jv[j] >= a.J0 && Jv[j] < a.J1;
+        };
+        // sigma_I sigma_J acc: exponent arithmetic, else the FP64 product
+        auto exact_e = [&](int g, int j) {
+            return (eI[g] != INT_MIN && eJ[j] != INT_MIN) ? eI[g] + eJ[j] : 4096;
+        };
+        auto s2 = [&](int g, int j) {
+            return a.sig[(a.T0 + jr[g]) / a.g] * a.sig[Jv[j]];
+        };
+        if (jb.kind == 0) {
+            double cv[G][S::VPT], rv[G][S::VPT];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int j = 0; j < S::VPT; ++j) {
+                    cv[g][j] = wc(g, j) ? a.CS[cpos(g, j)] : 0.0;
+                    rv[g][j] = wr(g, j) ? a.Cr[rpos(g, j)] : 0.0;
+                }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int j = 0; j < S::VPT; ++j) {
+                    if (!rok[g] || !vok[j]) continue;
+                    const int e = exact_e(g, j);
+                    const double x = f32_to_f64_exact(acc[i0 + g][j]);
+                    const double val = (e > -1000 && e < 1000) ? scale_f64(x, e) : s2(g, j) * x;
+                    if (wc(g, j)) a.CS[cpos(g, j)] = cv[g][j] - val;
+                    if (wr(g, j)) a.Cr[rpos(g, j)] = rv[g][j] - val;
+                }
+        } else {
+            float cv[G][S::VPT], rv[G][S::VPT];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int j = 0; j < S::VPT; ++j) {
+                    cv[g][j] = wc(g, j) ? a.Ca[cpos(g, j)] : 0.f;
+                    rv[g][j] = wr(g, j) ? a.Ra[rpos(g, j)] : 0.f;
+                }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int j = 0; j < S::VPT; ++j) {
+                    if (!rok[g] || !vok[j]) continue;
+                    const int e = exact_e(g, j);
+                    const float f = (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23)
+                                                            : (float)s2(g, j);
+                    const float val = f * acc[i0 + g][j];
+                    if (wc(g, j)) a.Ca[cpos(g, j)] = cv[g][j] + val;
+                    if (wr(g, j)) a.Ra[rpos(g, j)] = rv[g][j] + val;
+                }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BTHREADS, 2) k_border_sym(BSymArgs a) {
+    __shared__ __align__(16) float sm[BSMEM_FLOATS];
+    if (a.st->info != 0) return;
+    const int64_t b = blockIdx.x;
+    int q = 0;
+    while (q + 1 < a.njob && b >= a.job[q + 1].cta0) ++q;
+    const BJob& jb = a.job[q];
+    const int64_t loc = b - jb.cta0;
+    const int64_t rtile = loc / jb.nvc, vchunk = loc % jb.nvc;
+    if (jb.cfg == 0) border_tile<BBulk>(a, jb, rtile, vchunk, sm);
+    else if (jb.cfg == 1) border_tile<BTiny>(a, jb, rtile, vchunk, sm);
+    else border_tile<BSkinny>(a, jb, rtile, vchunk, sm);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -603,33 +796,42 @@ cudaError_t launch_tmu_mixed(const uint16_t* Lq, int64_t m, int64_t kb, int bf16
     return cudaGetLastError();
 }
 
-cudaError_t launch_border_mixed(const BorderSegHost* segs, int nseg, int bf16, const double* sig,
-                                const DevStatus* st, cudaStream_t s) {
-    BorderArgs a{};
-    a.bf16 = bf16;
-    a.sig = sig;
-    a.st = st;
+cudaError_t launch_border_sym(const BorderSymHost& h, const DevStatus* st, cudaStream_t s) {
+    if (h.m <= 0 || h.K <= 0 || h.Je <= h.Jb) return cudaSuccess;
+    if (h.K % BKC != 0 || h.nc < 1 || h.nc > 2) return cudaErrorInvalidValue;
+    BSymArgs a{};
+    a.Lq = h.Lq; a.m = h.m; a.K = h.K; a.bf16 = h.bf16;
+    a.tq = h.tq; a.ta = h.ta; a.nc = h.nc; a.Jb = h.Jb;
+    a.CS = h.CS; a.Ca = h.Ca; a.ldcs = h.ldcs; a.T0 = h.T0;
+    a.Cr = h.Cr; a.Ra = h.Ra; a.ldr = h.ldr;
+    a.c0 = std::max<int64_t>(0, h.c0); a.c1 = std::min(h.m, h.c1);
+    a.J0 = h.J0; a.J1 = h.J1; a.g = h.g; a.sig = h.sig; a.st = st;
+    const int nblk = (int)(h.Je - h.Jb);
     int64_t total = 0;
-    a.nseg = 0;
-    if (nseg > MAX_BSEG) return cudaErrorInvalidValue;
-    for (int i = 0; i < nseg; ++i) {
-        const BorderSegHost& h = segs[i];
-        if (h.M <= 0 || h.N <= 0 || h.K <= 0) continue;
-        BorderSeg& b = a.seg[a.nseg];
-        b.A = h.A; b.a_half = h.a_half; b.lda = h.lda;
-        b.B = h.B; b.b_half = h.b_half; b.ldb = h.ldb;
-        b.C = h.C; b.ldc = h.ldc; b.M = h.M; b.N = h.N; b.K = h.K;
-        b.r_off = h.r_off; b.r_div = h.r_div; b.r_base = h.r_base;
-        b.c_off = h.c_off; b.c_div = h.c_div; b.c_base = h.c_base;
-        b.a_abs = h.a_abs; b.b_abs = h.b_abs; b.plus = h.plus; b.C32 = h.C32;
-        a.tn[a.nseg] = (h.N + 63) / 64;
-        a.start[a.nseg] = total;
-        total += ((h.M + 63) / 64) * a.tn[a.nseg];
-        a.nseg++;
+    auto add = [&](int64_t r0, int64_t r1, int v0, int v1, int vstep, int kind) {
+        if (r1 <= r0 || v1 <= v0) return;
+        BJob& j = a.job[a.njob++];
+        j.r0 = r0; j.r1 = r1; j.v0 = v0; j.v1 = v1; j.vstep = vstep; j.kind = kind;
+        const int nv = v1 - v0;
+        const int64_t bulk = ((r1 - r0 + BBulk::RT - 1) / BBulk::RT) * ((nv + BBulk::VC - 1) / BBulk::VC);
+        j.cfg = nv <= BSkinny::VC ? 2 : (bulk < num_sms() ? 1 : 0);
+        const int rt = bcfg_rt(j.cfg), vc = bcfg_vc(j.cfg);
+        j.nvc = (nv + vc - 1) / vc;
+        j.cta0 = total;
+        total += ((r1 - r0 + rt - 1) / rt) * j.nvc;
+    };
+    // rows of the part: every vector; the other rows: the row sums of blocks [J0, J1)
+    add(a.c0, a.c1, 0, nblk * h.nc, 1, 0);
+    add(a.c0, a.c1, 0, nblk, 1, 1);
+    if (h.Cr && h.J1 > h.J0) {
+        const int v0 = (int)(h.J0 - h.Jb), v1 = (int)(h.J1 - h.Jb);
+        add(0, a.c0, v0, v1, h.nc, 0);
+        add(0, a.c0, v0, v1, 1, 1);
+        add(a.c1, h.m, v0, v1, h.nc, 0);
+        add(a.c1, h.m, v0, v1, 1, 1);
     }
     if (total == 0) return cudaSuccess;
-    a.start[a.nseg] = total;
-    k_border_mixed<<<(unsigned)total, 256, 0, s>>>(a);
+    k_border_sym<<<(unsigned)total, BTHREADS, 0, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }
