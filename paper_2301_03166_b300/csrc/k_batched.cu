@@ -36,6 +36,119 @@ constexpr int MAXNT = MAXN / 32;
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < (T)0 ? -x : x; }
 
+// 1 / sqrt(x) (CUDA's rsqrtf / rsqrt)
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+// Element e of a lower triangle enumerated row by row ((0,0), (1,0), (1,1),
+// (2,0), ...) as (row << 8) | column.
+__device__ __forceinline__ int tri_pair(int e) {
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if ((i + 1) * (i + 2) / 2 <= e) ++i;
+    if (i * (i + 1) / 2 > e) --i;
+    return (i << 8) | (e - i * (i + 1) / 2);
+}
+
+// Transposed panels in shared memory: element (j, p) of a block's panel rows
+// at p LDT + j, rows of LDT values (16-byte aligned for the vector reads).
+constexpr int LDT = MAXB + 4;
+// J panels staged per CTA.  One buffer: four FP32 CTAs per SM (measured
+// faster than three CTAs whose next tile's rows are copied while this one is
+// multiplied), two FP64 CTAs per SM.
+constexpr int NBUF_F32 = 1;
+
+// Register tile of the update, R = B / 16 outputs per thread and direction.
+// FP32: thread (tx, ty) owns rows R ty + a and columns R tx + b, so that each
+// operand row is one R-wide vector read per p (scalar reads would make the
+// shared-memory pipe, not the FMA pipe, the bound); C is loaded before the
+// product.  FP64: rows ty + 16 a and columns tx + 16 b, so that whole 16 x 16
+// groups can be skipped (the FP64 pipe is the bound).
+template <typename T, int B>
+struct TileMap {
+    static constexpr int R = B / 16;
+    static constexpr bool CONTIG = sizeof(T) == 4;
+    static constexpr bool PREF_C = sizeof(T) == 4;
+    static constexpr int NBUF = sizeof(T) == 4 ? NBUF_F32 : 1;
+    __device__ static int row(int ty, int a) { return CONTIG ? R * ty + a : ty + 16 * a; }
+    __device__ static int col(int tx, int b) { return CONTIG ? R * tx + b : tx + 16 * b; }
+    __device__ static void load(const T* rowp, int tt, T (&v)[R]) {
+        if constexpr (CONTIG && R == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(rowp + 4 * tt);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else if constexpr (CONTIG && R == 2) {
+            const float2 q = *reinterpret_cast<const float2*>(rowp + 2 * tt);
+            v[0] = q.x; v[1] = q.y;
+        } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a) v[a] = rowp[tt + 16 * a];
+        }
+    }
+};
+
+// acc[a][b] += sum_p sA[p][row a] sB[p][col b] over the thread's register
+// tile, p in increasing order.  SEL picks the 16 x 16 groups (FP64 mapping):
+// 0 every group, 1 those on or below the diagonal (b <= a: a full diagonal
+// tile), 2 those inside the tile's edge (a < ra, b < rb) and, on a diagonal
+// tile, on or below it.  The choice is made once per tile, outside the loop.
+template <typename Map, int SEL, typename T, int R>
+__device__ __forceinline__ void tile_product(const T* sA, const T* sB, int tx, int ty, int ra, int rb,
+                                             bool diag, T (&acc)[R][R]) {
+    constexpr int B = 16 * R;
+#pragma unroll 8
+    for (int p = 0; p < B; ++p) {
+        T av[R], bv[R];
+        Map::load(sA + p * LDT, ty, av);
+        Map::load(sB + p * LDT, tx, bv);
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+                if (SEL == 1 && b > a) continue;
+                if (SEL == 2 && !(a < ra && b < rb && !(diag && b > a))) continue;
+                acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
+    }
+}
+
+// Four consecutive values from 16-byte aligned shared memory.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// 4- or 8-byte global -> shared copy (cp.async), zero-filled when !pred
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool pred) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src),
+                 "n"((int)sizeof(T)), "r"(pred ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Panel rows q0 + [0, nq) of block column K0 (B values each) into dst,
+// transposed: dst[p LDT + j] = A[(q0 + j) lda + K0 + p], zero for j >= nq.  A
+// warp copies 4 rows x 8 consecutive values (a 32-byte stretch of each row);
+// for FP32 its transposed stores fall in 32 distinct banks (LDT = 4 mod 32).
+template <typename T, int B>
+__device__ __forceinline__ void stage_panel_t(T* dst, const T* A, int64_t lda, int q0, int nq, int K0) {
+#pragma unroll
+    for (int e = threadIdx.x; e < B * B; e += BT) {
+        const int lane = e & 31, grp = e >> 5;
+        const int j = (grp / (B / 8)) * 4 + (lane >> 3);
+        const int p = (grp % (B / 8)) * 8 + (lane & 7);
+        const bool ok = j < nq;
+        cp_async_elem<T>(dst + p * LDT + j, A + (int64_t)(q0 + (ok ? j : 0)) * lda + K0 + p, ok);
+    }
+}
+
 // Per-CTA global scratch: checksums and the saved diagonal-block upper triangles.
 template <typename T>
 struct Scratch {
@@ -238,8 +351,7 @@ __device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T*
 
 template <typename T, int B>
 __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scratch<T> S,
-                           abft_batch_status* st, T (*sL)[MAXB + 1], T (*sI)[MAXB + 1],
-                           T (*sJ)[MAXB + 1], T* colsum, T* wsum, T* rowsum, T* rdiag, int* sflag,
+                           abft_batch_status* st, T (*sL)[MAXB + 1], T* sIt, T* sJt, T* colsum, T* wsum, T* rowsum, T* rdiag, int* sflag,
                            int* s_first, int* s_fail) {
     T* A = (T*)it.A;
     const int64_t lda = it.lda;
@@ -247,6 +359,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     const int nt = (n + B - 1) / B;
     const int t = threadIdx.x;
     const bool check = mode != MODE_NONE;
+    using Map = TileMap<T, B>;
     const T u = sizeof(T) == 8 ? (T)0x1p-53 : (T)0x1p-24;
     // an injected fault is used only when it lies inside this matrix
     const bool fok = it.fstep >= 0 && it.frow >= 0 && it.frow < n && it.fcol >= 0 && it.fcol < n;
@@ -284,7 +397,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             for (int J = 0; J <= I; ++J) {
                 const int r0 = I * B, c0 = J * B, nr = min(B, n - r0), nc = min(B, n - c0);
                 tile_sums_any<T>(A + (int64_t)r0 * lda + c0, lda, nr, nc, vexp, colsum, wsum,
-                                 rowsum, &sJ[0][0]);
+                                 rowsum, sJt);
                 for (int j = t; j < nc; j += BT) {
                     S.Cc[I * MAXN + c0 + j] = colsum[j];
                     S.Cw[I * MAXN + c0 + j] = wsum[j];
@@ -294,32 +407,88 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             }
     for (int k = 0; k < nt; ++k) {
         const int K0 = k * B, kb = min(B, n - K0), T0 = K0 + kb, mrows = n - T0;
-        // ---- PD: potf2 of the diagonal block in shared memory
+        // ---- PD: right-looking potf2 of the diagonal block in shared memory.
+        // Phase j updates the lower triangle of rows and columns j + 1 .. kb - 1
+        // with column j.  The pivot's reciprocal square root r is taken once
+        // (CUDA's rsqrt), l_jj = d r, and r scales the column: one long
+        // operation per column on the dependent chain instead of a square
+        // root and a division.  Thread 0 updates the next pivot first and
+        // publishes l_jj and r for the next phase.
+        //   FP32: one barrier per phase on a 16 x 16 thread grid; column j is
+        //   scaled where it is used (l_ij = a_ij r_j, the same product
+        //   wherever it is formed) and stored scaled in the next phase, which
+        //   no longer reads it.
+        //   FP64: column j is scaled first (one FP64 multiply per element
+        //   instead of two per update), then a second barrier; the update's
+        //   elements are spread over all threads in row-major order (thread t
+        //   takes elements t, t + BT, ...: full warps, which is what the FP64
+        //   pipe charges for; the pairs are recomputed per phase, which keeps
+        //   registers free).
         for (int e = t; e < kb * kb; e += BT) {
             int i = e / kb, j = e % kb;
             if (j <= i) sL[i][j] = A[(int64_t)(K0 + i) * lda + K0 + j];
         }
         __syncthreads();
+        if (t == 0) {
+            const T d = sL[0][0];
+            if (!(d > (T)0)) *s_fail = 0;
+            else { const T r = rsqrt_t(d); sL[0][0] = d * r; rdiag[0] = r; }
+        }
         for (int j = 0; j < kb; ++j) {
-            if (t == 0) {
-                T d = sL[j][j];
-                if (!(d > (T)0)) *s_fail = j;
-                else sL[j][j] = sqrt(d);
-            }
             __syncthreads();
             if (*s_fail >= 0) break;
-            const T rjj = (T)1 / sL[j][j];   // one division per column, products below
-            for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] * rjj;
-            __syncthreads();
-            {   // rank-1 update of the remaining lower triangle on a 16 x 16 thread grid
+            const T rj = rdiag[j];
+            if constexpr (sizeof(T) == 4) {
+                if (j > 0) {
+                    const T rp = rdiag[j - 1];
+                    for (int i = j + t; i < kb; i += BT) sL[i][j - 1] = sL[i][j - 1] * rp;
+                }
                 const int tx = t & 15, ty = t >> 4;
-                for (int i = j + 1 + ty; i < kb; i += 16) {
-                    const T aij = sL[i][j];
-                    for (int l = j + 1 + tx; l <= i; l += 16) sL[i][l] -= aij * sL[l][j];
+                if (t == 0 && j + 1 < kb) {
+                    const T l = sL[j + 1][j] * rj;
+                    const T d = sL[j + 1][j + 1] - l * l;
+                    if (!(d > (T)0)) *s_fail = j + 1;
+                    else { const T r = rsqrt_t(d); sL[j + 1][j + 1] = d * r; rdiag[j + 1] = r; }
+                }
+                T lv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int l = j + 1 + tx + 16 * u;
+                    lv[u] = l < kb ? sL[l][j] * rj : (T)0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = j + 1 + ty + 16 * q;
+                    if (i >= kb) break;
+                    if (i == j + 1) continue;
+                    const T li = sL[i][j] * rj;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int l = j + 1 + tx + 16 * u;
+                        if (l > i) break;
+                        sL[i][l] -= li * lv[u];
+                    }
+                }
+            } else {
+                for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] * rj;
+                const int m = kb - j - 1, M = m * (m + 1) / 2;
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (t + BT * q >= M) break;
+                    const int pq = tri_pair(t + BT * q);
+                    const int i = j + 1 + (pq >> 8), l = j + 1 + (pq & 255);
+                    if (t + BT * q == 0) {
+                        const T d = sL[i][i] - sL[i][j] * sL[i][j];
+                        if (!(d > (T)0)) *s_fail = j + 1;
+                        else { const T r = rsqrt_t(d); sL[i][i] = d * r; rdiag[i] = r; }
+                    } else {
+                        sL[i][l] -= sL[i][j] * sL[l][j];
+                    }
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (*s_fail >= 0) {
             if (t == 0) st->info = K0 + *s_fail + 1;
             break;
@@ -328,7 +497,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             int i = e / kb, j = e % kb;
             if (j <= i) A[(int64_t)(K0 + i) * lda + K0 + j] = sL[i][j];
         }
-        for (int j = t; j < kb; j += BT) rdiag[j] = (T)1 / sL[j][j];   // the panel solve's reciprocals
+        // rdiag holds the pivots' reciprocals for the panel solve
         if (check) {   // PD check on column sums
             for (int p = t; p < kb; p += BT) {
                 T s = 0;
@@ -346,6 +515,13 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 }
             }
         }
+        // L_kk row by row at stride LDT (16-byte aligned rows) for the panel
+        // solve's vector reads; sIt is free until the update
+        T* const sLr = sIt;
+        for (int e = t; e < kb * kb; e += BT) {
+            const int i = e / kb, j = e % kb;
+            sLr[i * LDT + j] = j <= i ? sL[i][j] : (T)0;
+        }
         __syncthreads();
         if (mrows <= 0) break;
         // ---- PU: x L^T = a for the panel rows and the checksum rows, one thread
@@ -354,7 +530,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         // registers: each chunk first takes the terms of the earlier chunks
         // (re-read from the row, which this thread wrote), then substitutes
         // inside the chunk; every unknown's terms form one fused multiply-add
-        // chain in p order.
+        // chain in p order.  L_kk's rows are read four values at a time.
         const int ncs = check ? 2 * (nt - k - 1) : 0;
         for (int rr = t; rr < mrows + ncs; rr += BT) {
             T* row;
@@ -367,16 +543,29 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 T x[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) x[q] = row[c0 + q];
-                for (int p = 0; p < c0; ++p) {
-                    const T xp = row[p];
+                for (int p = 0; p < c0; p += 4) {
+                    const T x0 = row[p], x1 = row[p + 1], x2 = row[p + 2], x3 = row[p + 3];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) x[q] = fma(-xp, sL[c0 + q][p], x[q]);
+                    for (int q = 0; q < 32; ++q) {
+                        T l[4];
+                        ld4(sLr + (c0 + q) * LDT + p, l);
+                        x[q] = fma(-x0, l[0], x[q]);
+                        x[q] = fma(-x1, l[1], x[q]);
+                        x[q] = fma(-x2, l[2], x[q]);
+                        x[q] = fma(-x3, l[3], x[q]);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     T v = x[q];
 #pragma unroll
-                    for (int pp = 0; pp < q; ++pp) v = fma(-x[pp], sL[c0 + q][c0 + pp], v);
+                    for (int p4 = 0; p4 < q; p4 += 4) {
+                        T l[4];
+                        ld4(sLr + (c0 + q) * LDT + c0 + p4, l);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (p4 + u < q) v = fma(-x[p4 + u], l[u], v);
+                    }
                     x[q] = v * rdiag[c0 + q];
                 }
 #pragma unroll
@@ -392,78 +581,107 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 const int r0 = I * B, nr = min(B, n - r0);
                 verify_tile<T>(A + (int64_t)r0 * lda + K0, lda, r0, K0, nr, kb,
                                S.Cc + I * MAXN + K0, S.Cw + I * MAXN + K0, nullptr, 0, tau, 1, k,
-                               st, colsum, wsum, rowsum, &sJ[0][0], sflag, s_first, vexp);
+                               st, colsum, wsum, rowsum, sJt, sflag, s_first, vexp);
             }
         // ---- TMU over the lower block triangle with the checksum borders.
         // sL is free from here to the next PD: it holds the carried checksum
         // rows of the panel (c_I, w_I of block row I; c_J of block row J) and
-        // the border dot products' partial sums.
+        // the border dot products' partial sums.  The panel rows of blocks I
+        // and J sit transposed in sIt / sJt (element (j, p) at p LDT + j),
+        // copied by cp.async; with two J buffers the next tile's rows are in
+        // flight while this tile is multiplied.  A diagonal tile (J = I) takes
+        // its B operand from sIt.
         T* sCI = &sL[0][0];
         T* sWI = sCI + MAXB;
         T* sCJ = sWI + MAXB;
         T* red = sCJ + MAXB;   // [3][BT / B][MAXB] partial sums of the border products
+        constexpr int NB = Map::NBUF;
         for (int I = k + 1; I < nt; ++I) {
             const int r0 = I * B, nr = min(B, n - r0);
             // a block with rows below it is full: kb = B from here on
-#pragma unroll
-            for (int e = t; e < B * B; e += BT) {
-                const int i = e / B, p = e % B;
-                sI[i][p] = (i < nr) ? A[(int64_t)(r0 + i) * lda + K0 + p] : (T)0;
-            }
+            stage_panel_t<T, B>(sIt, A, lda, r0, nr, K0);
+            if (NB == 2 && k + 1 < I) stage_panel_t<T, B>(sJt, A, lda, (k + 1) * B, B, K0);
+            cp_async_commit();
             if (check)
                 for (int p = t; p < kb; p += BT) {
                     sCI[p] = S.Cc[I * MAXN + K0 + p];
                     sWI[p] = S.Cw[I * MAXN + K0 + p];
                 }
+            int cur = 0;
             for (int J = k + 1; J <= I; ++J) {
                 const int c0 = J * B, nc = min(B, n - c0);
-#pragma unroll
-                for (int e = t; e < B * B; e += BT) {
-                    const int j = e / B, p = e % B;
-                    sJ[j][p] = (j < nc) ? A[(int64_t)(c0 + j) * lda + K0 + p] : (T)0;
+                const bool diag = J == I;
+                if (NB == 1) {
+                    if (!diag) stage_panel_t<T, B>(sJt, A, lda, c0, nc, K0);
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                } else if (J + 1 < I) {
+                    stage_panel_t<T, B>(sJt + (cur ^ 1) * (MAXB * LDT), A, lda, c0 + B, B, K0);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
                 if (check)
                     for (int p = t; p < kb; p += BT) sCJ[p] = S.Cc[J * MAXN + K0 + p];
-                __syncthreads();
-                // register tile: thread (tx, ty) owns rows ty + 16 a and columns
-                // tx + 16 b (a, b < B / 16); per p, B / 8 shared loads feed
-                // (B / 16)^2 fused multiply-adds
+                const T* sB = diag ? sIt : sJt + cur * (MAXB * LDT);
                 constexpr int R = B / 16;
                 const int tx = t & 15, ty = t >> 4;
+                // the tile's C values, loaded before the product so that their
+                // latency is hidden behind it (FP32)
+                T cv[R][R];
+                if (Map::PREF_C) {
+#pragma unroll
+                    for (int a = 0; a < R; ++a)
+#pragma unroll
+                        for (int b = 0; b < R; ++b) {
+                            const int i = Map::row(ty, a), j = Map::col(tx, b);
+                            cv[a][b] = (i < nr && j < nc) ? A[(int64_t)(r0 + i) * lda + c0 + j] : (T)0;
+                        }
+                }
+                __syncthreads();
+                // register tile: thread (tx, ty) owns R x R outputs (Map); per p
+                // it reads R values of each operand row of the transposed panels
+                // and does R^2 fused multiply-adds in p order.  FP64 skips the
+                // 16-row / 16-column groups beyond the tile's edge and, on a
+                // diagonal tile, the groups above the diagonal, whose values the
+                // mirrored groups below write (the same products: C is
+                // symmetric there and a b = b a).
                 T acc[R][R];
 #pragma unroll
                 for (int a = 0; a < R; ++a)
 #pragma unroll
                     for (int b = 0; b < R; ++b) acc[a][b] = 0;
-                // row / column groups of 16 beyond the tile's edge are skipped
-                // (the same branch for every thread)
                 const int ra = (nr + 15) / 16, rb = (nc + 15) / 16;
-#pragma unroll 8
-                for (int p = 0; p < B; ++p) {
-                    T av[R], bv[R];
-#pragma unroll
-                    for (int a = 0; a < R; ++a) av[a] = sI[ty + 16 * a][p];
-#pragma unroll
-                    for (int b = 0; b < R; ++b) bv[b] = sJ[tx + 16 * b][p];
-#pragma unroll
-                    for (int a = 0; a < R; ++a)
-                        if (a < ra)
-#pragma unroll
-                            for (int b = 0; b < R; ++b)
-                                if (b < rb) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                if constexpr (Map::CONTIG) {
+                    tile_product<Map, 0>(sIt, sB, tx, ty, ra, rb, diag, acc);
+                } else {
+                    const bool full = ra == R && rb == R;
+                    if (full && !diag) tile_product<Map, 0>(sIt, sB, tx, ty, ra, rb, diag, acc);
+                    else if (full) tile_product<Map, 1>(sIt, sB, tx, ty, ra, rb, diag, acc);
+                    else tile_product<Map, 2>(sIt, sB, tx, ty, ra, rb, diag, acc);
                 }
 #pragma unroll
                 for (int a = 0; a < R; ++a)
 #pragma unroll
                     for (int b = 0; b < R; ++b) {
-                        const int i = ty + 16 * a, j = tx + 16 * b;
+                        if (!Map::CONTIG && diag && b > a) continue;
+                        const int i = Map::row(ty, a), j = Map::col(tx, b);
                         if (i >= nr || j >= nc) continue;
                         T* c = A + (int64_t)(r0 + i) * lda + c0 + j;
-                        T v = *c - acc[a][b];
+                        const T v = (Map::PREF_C ? cv[a][b] : *c) - acc[a][b];
+                        T w = v;
                         if (fok && it.fstep == k && it.fkind == ABFT_FAULT_COMPUTE && it.frow == r0 + i &&
                             it.fcol == c0 + j)
-                            v += (T)it.fdelta;
-                        *c = v;
+                            w += (T)it.fdelta;
+                        *c = w;
+                        if (!Map::CONTIG && diag && b < a) {   // the mirrored element (j, i)
+                            T wm = v;
+                            if (fok && it.fstep == k && it.fkind == ABFT_FAULT_COMPUTE &&
+                                it.frow == r0 + j && it.fcol == c0 + i)
+                                wm += (T)it.fdelta;
+                            A[(int64_t)(r0 + j) * lda + c0 + i] = wm;
+                        }
                     }
                 if (check) {
                     // border products on every thread: column j (or row j) and
@@ -477,9 +695,9 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     T a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
                     for (int p = p0; p < p0 + np; ++p) {
-                        a1 = fma(sCI[p], sJ[j][p], a1);
-                        a2 = fma(sWI[p], sJ[j][p], a2);
-                        a3 = fma(sI[j][p], sCJ[p], a3);
+                        a1 = fma(sCI[p], sB[p * LDT + j], a1);
+                        a2 = fma(sWI[p], sB[p * LDT + j], a2);
+                        a3 = fma(sIt[p * LDT + j], sCJ[p], a3);
                     }
                     red[(0 * NQ + q) * MAXB + j] = a1;
                     red[(1 * NQ + q) * MAXB + j] = a2;
@@ -501,6 +719,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     }
                 }
                 __syncthreads();
+                if (NB == 2) cur ^= 1;
             }
         }
         if (fok && it.fstep == k && it.fkind == ABFT_FAULT_MEMORY && t == 0)
@@ -513,7 +732,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     verify_tile<T>(A + (int64_t)r0 * lda + c0, lda, r0, c0, nr, nc,
                                    S.Cc + I * MAXN + c0, S.Cw + I * MAXN + c0,
                                    S.Cr + r0 * MAXNT + J, MAXNT, tau, 0, k, st, colsum, wsum,
-                                   rowsum, &sJ[0][0], sflag, s_first, vexp);
+                                   rowsum, sJt, sflag, s_first, vexp);
                 }
     }
     __syncthreads();
@@ -527,10 +746,10 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     __syncthreads();
 }
 
-// CTAs per SM: two for FP64 (the FP64 pipe is the limit), four for FP32
-// (shorter arithmetic: more CTAs hide the barriers and load latencies)
+// CTAs per SM: two for FP64 (the FP64 pipe is the limit); for FP32 as many as
+// the shared memory holds (three with double-buffered J panels)
 template <typename T>
-struct CtasPerSm { static constexpr int v = sizeof(T) == 8 ? 2 : 4; };
+struct CtasPerSm { static constexpr int v = sizeof(T) == 8 ? 2 : (NBUF_F32 == 2 ? 3 : 4); };
 
 template <typename T>
 __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abft_batch_item* items, int count,
@@ -538,10 +757,11 @@ __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abf
                                                       abft_batch_status* status, T* scratch,
                                                       unsigned int* queue) {
     extern __shared__ __align__(16) unsigned char smb[];
+    constexpr int NBUF = TileMap<T, 64>::NBUF;
     T (*sL)[MAXB + 1] = (T (*)[MAXB + 1])smb;
-    T (*sI)[MAXB + 1] = sL + MAXB;
-    T (*sJ)[MAXB + 1] = sI + MAXB;
-    T* colsum = (T*)(sJ + MAXB);
+    T* sIt = (T*)(sL + MAXB);
+    T* sJt = sIt + MAXB * LDT;
+    T* colsum = sJt + NBUF * MAXB * LDT;
     T* wsum = colsum + MAXB;
     T* rowsum = wsum + MAXB;
     T* rdiag = rowsum + MAXB;
@@ -568,10 +788,10 @@ __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abf
         __syncthreads();
         if (it.n <= 0 || it.n > MAXN) continue;
         if (it.nb == 64)
-            factor_one<T, 64>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
+            factor_one<T, 64>(it, mode, (T)tau_scale, S, st, sL, sIt, sJt, colsum, wsum, rowsum,
                               rdiag, sflag, &s_first, &s_fail);
         else
-            factor_one<T, 32>(it, mode, (T)tau_scale, S, st, sL, sI, sJ, colsum, wsum, rowsum,
+            factor_one<T, 32>(it, mode, (T)tau_scale, S, st, sL, sIt, sJt, colsum, wsum, rowsum,
                               rdiag, sflag, &s_first, &s_fail);
     }
 }
@@ -579,7 +799,9 @@ __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abf
 }  // namespace
 
 size_t batched_smem(bool f64) {
-    return (size_t)(3 * MAXB * (MAXB + 1) + 4 * MAXB) * (f64 ? sizeof(double) : sizeof(float));
+    const int nbuf = f64 ? TileMap<double, 64>::NBUF : TileMap<float, 64>::NBUF;
+    return (size_t)(MAXB * (MAXB + 1) + (1 + nbuf) * MAXB * LDT + 4 * MAXB) *
+           (f64 ? sizeof(double) : sizeof(float));
 }
 
 size_t batched_scratch_bytes(int grid, bool f64) {
