@@ -178,11 +178,20 @@ __device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* 
                           T* part) {
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
     T c0 = 0, c1 = 0, w0 = 0, w1 = 0;
-#pragma unroll 4
-    for (int i = w; i < nr; i += BT / 32) {
+    // all of the warp's rows (at most MAXB / 8) loaded before they are summed
+    T va[MAXB / 8], vb[MAXB / 8];
+#pragma unroll
+    for (int q = 0; q < MAXB / 8; ++q) {
+        const int i = w + 8 * q;
         const T* row = P + (int64_t)i * ld;
-        const T v0 = l < nc ? row[l] : (T)0;
-        const T v1 = l + 32 < nc ? row[l + 32] : (T)0;
+        va[q] = (i < nr && l < nc) ? row[l] : (T)0;
+        vb[q] = (i < nr && l + 32 < nc) ? row[l + 32] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < MAXB / 8; ++q) {
+        const int i = w + 8 * q;
+        if (i >= nr) break;
+        const T v0 = va[q], v1 = vb[q];
         const T wi = (T)(i + 1);
         c0 += v0;
         c1 += v1;
@@ -278,20 +287,23 @@ __device__ void verify_tile(T* P, int64_t ld, int r0, int c0, int nr, int nc, T*
                             int crs, T tau, int single, int step, abft_batch_status* st,
                             T* colsum, T* wsum, T* rowsum, T* part, int* sflag, int* s_first,
                             int vexp) {
-    tile_sums_any<T>(P, ld, nr, nc, vexp, colsum, wsum, rowsum, part);
     const int t = threadIdx.x;
+    // the carried checksums of this thread's column / row (nr, nc <= MAXB <= BT),
+    // loaded before the sums so that their latency overlaps them
+    const T ccv = t < nc ? cc[t] : (T)0, cwv = t < nc ? cw[t] : (T)0;
+    const T crv = (!single && t < nr) ? cr[t * crs] : (T)0;
+    tile_sums_any<T>(P, ld, nr, nc, vexp, colsum, wsum, rowsum, part);
     if (t == 0) { sflag[0] = 0; sflag[1] = 0; sflag[2] = 1 << 30; sflag[3] = 1 << 30; }
     __syncthreads();
-    for (int j = t; j < nc; j += BT) {
-        colsum[j] -= cc[j];
-        wsum[j] -= cw[j];
-        if (!(tabs(colsum[j]) <= tau)) { atomicAdd(&sflag[0], 1); atomicMin(&sflag[2], j); }
+    if (t < nc) {
+        colsum[t] -= ccv;
+        wsum[t] -= cwv;
+        if (!(tabs(colsum[t]) <= tau)) { atomicAdd(&sflag[0], 1); atomicMin(&sflag[2], t); }
     }
-    if (!single)
-        for (int i = t; i < nr; i += BT) {
-            rowsum[i] -= cr[i * crs];
-            if (!(tabs(rowsum[i]) <= tau)) { atomicAdd(&sflag[1], 1); atomicMin(&sflag[3], i); }
-        }
+    if (!single && t < nr) {
+        rowsum[t] -= crv;
+        if (!(tabs(rowsum[t]) <= tau)) { atomicAdd(&sflag[1], 1); atomicMin(&sflag[3], t); }
+    }
     __syncthreads();
     const int nfc = sflag[0], nfr = sflag[1], fc = sflag[2], fr = sflag[3];
     if (nfc == 0 && nfr == 0) return;
@@ -526,11 +538,14 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         if (mrows <= 0) break;
         // ---- PU: x L^T = a for the panel rows and the checksum rows, one thread
         // per row.  A block with rows below it is never ragged (kb = B, a
-        // multiple of 32), so the row's unknowns are solved 32 at a time in
-        // registers: each chunk first takes the terms of the earlier chunks
-        // (re-read from the row, which this thread wrote), then substitutes
-        // inside the chunk; every unknown's terms form one fused multiply-add
-        // chain in p order.  L_kk's rows are read four values at a time.
+        // multiple of 32), so the row's unknowns are solved CH at a time in
+        // registers (16 for FP32, whose 64 registers per thread cannot hold
+        // 32 of them without spilling; 32 for FP64): each chunk first takes
+        // the terms of the earlier chunks (re-read from the row, which this
+        // thread wrote), then substitutes inside the chunk; every unknown's
+        // terms form one fused multiply-add chain in p order.  L_kk's rows are
+        // read four values at a time.
+        constexpr int CH = sizeof(T) == 4 ? 16 : 32;
         const int ncs = check ? 2 * (nt - k - 1) : 0;
         for (int rr = t; rr < mrows + ncs; rr += BT) {
             T* row;
@@ -539,14 +554,14 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 int c = rr - mrows, I = k + 1 + c / 2;
                 row = ((c & 1) ? S.Cw : S.Cc) + I * MAXN + K0;
             }
-            for (int c0 = 0; c0 < B; c0 += 32) {
-                T x[32];
+            for (int c0 = 0; c0 < B; c0 += CH) {
+                T x[CH];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) x[q] = row[c0 + q];
+                for (int q = 0; q < CH; ++q) x[q] = row[c0 + q];
                 for (int p = 0; p < c0; p += 4) {
                     const T x0 = row[p], x1 = row[p + 1], x2 = row[p + 2], x3 = row[p + 3];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
+                    for (int q = 0; q < CH; ++q) {
                         T l[4];
                         ld4(sLr + (c0 + q) * LDT + p, l);
                         x[q] = fma(-x0, l[0], x[q]);
@@ -556,7 +571,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
+                for (int q = 0; q < CH; ++q) {
                     T v = x[q];
 #pragma unroll
                     for (int p4 = 0; p4 < q; p4 += 4) {
@@ -569,7 +584,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     x[q] = v * rdiag[c0 + q];
                 }
 #pragma unroll
-                for (int q = 0; q < 32; ++q) row[c0 + q] = x[q];
+                for (int q = 0; q < CH; ++q) row[c0 + q] = x[q];
             }
         }
         __syncthreads();
