@@ -820,6 +820,8 @@ def run_ours(args, ws, rank, local):
         for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
             table = tune.tune(tdt, dev, per_bucket=64)
             nbf = tune.chooser(table)
+            cps = tune.tune_launch(tdt, dev, table=table, sizes=msz)
+            abft.set_batched_ctas_per_sm(cps)
             bfaults, gfaults = {}, {}
             fr = W.rng(6001)
             for gi in sorted(fpos):
@@ -847,7 +849,7 @@ def run_ours(args, ws, rank, local):
             st = shard.gather_statuses(mine, bt.status.cpu().numpy(), 4096, hgroup)
             entry = {"ms_per_batch": ms_f, "matrices_per_s": 4096 / (ms_f * 1e-3),
                      "tflops": bflops / (ms_f * 1e-3) / 1e12, "nb_by_bucket": table,
-                     "bfaults": len(gfaults)}
+                     "ctas_per_sm": cps, "bfaults": len(gfaults)}
             if st is not None:   # rank 0: every matrix once, every fault located and corrected
                 F = {f: i for i, f in enumerate(abft._STATUS_FIELDS)}
                 entry["all_located_and_corrected"] = bool(
@@ -858,6 +860,7 @@ def run_ours(args, ws, rank, local):
                         for gi, f in gfaults.items()))
             batched[name] = entry
             del buf0, buf, bt
+        abft.set_batched_ctas_per_sm(0)
         abft.lib().abft_batched_graph_reset()
         del base
 

@@ -506,6 +506,18 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
 int abft_batched_graph_reset(void);
 
 /*
+ * abft_batched_set_ctas_per_sm: how many persistent CTAs per SM the next
+ * abft_potrf_batched launches use (the launch-level knob of the tuner in
+ * tune.py; the per-matrix knob is the block size item.nb).  0 restores the
+ * default, the most that fit (FP64 2, FP32 4); larger values are clamped to
+ * it.  Process-wide; a cached graph is keyed by the grid it was captured
+ * with.  The factors do not depend on it (each matrix is factored by one
+ * CTA).  Not in the paper.  Returns the previous setting, or -1 for a
+ * negative argument.
+ */
+int abft_batched_set_ctas_per_sm(int32_t ctas);
+
+/*
  * abft_batched_partition -- split a batch of independent factorizations
  * (abft_potrf_batched) over G GPUs, one process per GPU, so that every GPU
  * gets about the same work.  Not in the paper (the batched form's multi-GPU

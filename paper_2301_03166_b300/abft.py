@@ -51,6 +51,7 @@ _sz = ctypes.POINTER(ctypes.c_size_t)
 
 _SIGNATURES = {
     "abft_potrf_batched": [_i32, _vp, _i32, _i32, _dbl, _vp, _i32, _vp, _sz, _vp],
+    "abft_batched_set_ctas_per_sm": [_i32],
     "abft_potrf_backward": [_i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz, _vp],
     "abft_potrf_backward_ex": [_i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _sz,
                                _vp],
@@ -696,6 +697,15 @@ class Batch:
     def statuses(self):
         st = self.status.cpu().numpy()
         return [dict(zip(_STATUS_FIELDS, map(int, row))) for row in st]
+
+
+def set_batched_ctas_per_sm(ctas):
+    """Persistent CTAs per SM of the batched launch (0: the default, the most
+    that fit); returns the previous setting."""
+    rc = lib().abft_batched_set_ctas_per_sm(int(ctas))
+    if rc < 0:
+        raise AbftError(rc, strerror(rc))
+    return rc
 
 
 def potrf_batched(batch, mode=FULL, tau_scale=1.0, use_graph=False, workspace=None, stream=None):

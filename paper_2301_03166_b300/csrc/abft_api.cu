@@ -1882,16 +1882,16 @@ namespace {
 // and the device the graph was instantiated on.
 struct GraphKey {
     const void* items;
-    int count, dtype, mode;
+    int count, dtype, mode, grid;
     uint64_t tau_bits;
     int device;
     const void* status;
     const void* ws;
     void* stream;
     bool operator<(const GraphKey& o) const {
-        return std::tie(items, count, dtype, mode, tau_bits, device, status, ws, stream) <
-               std::tie(o.items, o.count, o.dtype, o.mode, o.tau_bits, o.device, o.status, o.ws,
-                        o.stream);
+        return std::tie(items, count, dtype, mode, grid, tau_bits, device, status, ws, stream) <
+               std::tie(o.items, o.count, o.dtype, o.mode, o.grid, o.tau_bits, o.device, o.status,
+                        o.ws, o.stream);
     }
 };
 std::mutex g_graph_mu;
@@ -1911,7 +1911,9 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     if (count > 0 && status == nullptr && ws != nullptr) return -6;
     if (ws_bytes == nullptr) return -9;
     const bool f64 = dtype == ABFT_F64;
-    const size_t need = align_up(batched_scratch_bytes(batched_grid(f64), f64)) + 256;
+    // sized for the largest grid, so that a workspace stays valid whatever
+    // abft_batched_set_ctas_per_sm chooses later
+    const size_t need = align_up(batched_scratch_bytes(batched_max_grid(f64), f64)) + 256;
     if (ws == nullptr) {
         *ws_bytes = need;
         return ABFT_OK;
@@ -1919,7 +1921,7 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     if (*ws_bytes < need) return -9;
     if (count == 0) return ABFT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned int* queue = (unsigned int*)((char*)ws + align_up(batched_scratch_bytes(batched_grid(f64), f64)));
+    unsigned int* queue = (unsigned int*)((char*)ws + align_up(batched_scratch_bytes(batched_max_grid(f64), f64)));
     if (!use_graph) {
         ABFT_CUDA_TRY(launch_potrf_batched(items, count, f64, mode, tau_scale, status, ws, queue, s));
         ABFT_CUDA_TRY(timing_collect(s));
@@ -1929,7 +1931,7 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     ABFT_CUDA_TRY(cudaGetDevice(&device));
     uint64_t tau_bits = 0;
     std::memcpy(&tau_bits, &tau_scale, sizeof(tau_bits));
-    GraphKey key{items, count, dtype, mode, tau_bits, device, status, ws, stream};
+    GraphKey key{items, count, dtype, mode, batched_grid(f64), tau_bits, device, status, ws, stream};
     cudaGraphExec_t exec = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -1957,6 +1959,11 @@ int abft_potrf_batched(int32_t count, const abft_batch_item* items, int32_t dtyp
     note_launch();
     ABFT_CUDA_TRY(timing_collect(s));
     return ABFT_OK;
+}
+
+int abft_batched_set_ctas_per_sm(int32_t ctas) {
+    if (ctas < 0) return -1;
+    return batched_set_ctas_per_sm(ctas);
 }
 
 int abft_batched_graph_reset(void) {

@@ -343,7 +343,9 @@ cudaError_t launch_symmetrize_half(double* A, int64_t lda, int64_t n, cudaStream
 
 // Batched kernel (k_batched.cu).
 size_t batched_scratch_bytes(int grid, bool f64);
-int batched_grid(bool f64);   // CTAs of the persistent batched launch
+int batched_grid(bool f64);       // CTAs of the persistent batched launch
+int batched_max_grid(bool f64);   // the most CTAs it can have (workspace sizing)
+int batched_set_ctas_per_sm(int c);   // returns the previous setting
 cudaError_t batched_prepare();
 cudaError_t launch_potrf_batched(const abft_batch_item* items, int count, bool f64, int mode,
                                  double tau_scale, abft_batch_status* status, void* scratch,

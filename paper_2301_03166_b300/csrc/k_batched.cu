@@ -21,6 +21,8 @@
 // atomic queue counter.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "fp_bits.cuh"
 
@@ -824,9 +826,21 @@ size_t batched_scratch_bytes(int grid, bool f64) {
     return per * (size_t)grid * (f64 ? sizeof(double) : sizeof(float));
 }
 
+// CTAs per SM of the persistent launch, set by abft_batched_set_ctas_per_sm
+// (0: as many as fit, which the kernel's launch bounds fix).
+std::atomic<int> g_batched_cps{0};
+
+int batched_max_ctas_per_sm(bool f64) { return f64 ? CtasPerSm<double>::v : CtasPerSm<float>::v; }
+
+int batched_set_ctas_per_sm(int c) { return g_batched_cps.exchange(c); }
+
 int batched_grid(bool f64) {
-    return (f64 ? CtasPerSm<double>::v : CtasPerSm<float>::v) * num_sms();
+    const int mx = batched_max_ctas_per_sm(f64);
+    const int c = g_batched_cps.load();
+    return (c <= 0 || c > mx ? mx : c) * num_sms();
 }
+
+int batched_max_grid(bool f64) { return batched_max_ctas_per_sm(f64) * num_sms(); }
 
 // Kernel attributes (set once, outside any stream capture).
 cudaError_t batched_prepare() {

@@ -130,3 +130,7 @@ def test_added_entry_points_check_arguments_on_host():
     own = (ctypes.c_int32 * 3)()
     assert L.abft_batched_partition(3, n, 0, own, None) == -3
     assert L.abft_batched_partition(3, n, 2, own, None) == 0 and list(own) == [1, 1, 0]
+    # abft_batched_set_ctas_per_sm: host only, returns the previous setting
+    assert L.abft_batched_set_ctas_per_sm(-1) == -1
+    prev = L.abft_batched_set_ctas_per_sm(3)
+    assert L.abft_batched_set_ctas_per_sm(prev) == 3

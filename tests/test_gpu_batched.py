@@ -89,6 +89,33 @@ def test_batched_graph_replay_and_tuner(tmp_path):
     abft.lib().abft_batched_graph_reset()
 
 
+def test_batched_ctas_per_sm_tuner(tmp_path):
+    """The launch-level knob: the tuner picks a CTA count in range, and the
+    factors and statuses do not depend on it (one CTA per matrix), eager or
+    replayed from a graph keyed by the grid."""
+    cache = str(tmp_path / "tune.json")
+    for dt in (torch.float64, torch.float32):
+        c = tune.tune_launch(dt, DEV, table={0: 64, 1: 64, 2: 64}, count=160, cache=cache, reps=1)
+        assert 1 <= c <= tune.MAX_CTAS_PER_SM["f64" if dt == torch.float64 else "f32"]
+        assert tune.tune_launch(dt, DEV, count=160, cache=cache) == c          # cached
+    batch, mats, faults = make_batch(200, torch.float32, nb=64, fault_every=20)
+    buf0 = batch.buf.clone()
+    abft.potrf_batched(batch)
+    ref, ref_st = batch.buf.clone(), batch.status.clone()
+    try:
+        for c in (1, 3):
+            assert abft.set_batched_ctas_per_sm(c) in (0, 1)
+            for graph in (False, True):
+                batch.buf.copy_(buf0)
+                batch.status.zero_()
+                abft.potrf_batched(batch, use_graph=graph)
+                torch.cuda.synchronize()
+                assert torch.equal(batch.buf, ref) and torch.equal(batch.status, ref_st)
+    finally:
+        abft.set_batched_ctas_per_sm(0)
+        abft.lib().abft_batched_graph_reset()
+
+
 def test_batched_config_4096():
     """The batched configuration: 4096 matrices, n uniform in [32, 512], one
     fault per 64 matrices, FP64, one persistent launch."""
