@@ -428,10 +428,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         // operation per column on the dependent chain instead of a square
         // root and a division.  Thread 0 updates the next pivot first and
         // publishes l_jj and r for the next phase.
-        //   FP32: one barrier per phase on a 16 x 16 thread grid; column j is
-        //   scaled where it is used (l_ij = a_ij r_j, the same product
-        //   wherever it is formed) and stored scaled in the next phase, which
-        //   no longer reads it.
+        //   FP32: two columns per barrier on a 16 x 16 thread grid (below).
         //   FP64: column j is scaled first (one FP64 multiply per element
         //   instead of two per update), then a second barrier; the update's
         //   elements are spread over all threads in row-major order (thread t
@@ -443,47 +440,110 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
             if (j <= i) sL[i][j] = A[(int64_t)(K0 + i) * lda + K0 + j];
         }
         __syncthreads();
-        if (t == 0) {
-            const T d = sL[0][0];
-            if (!(d > (T)0)) *s_fail = 0;
-            else { const T r = rsqrt_t(d); sL[0][0] = d * r; rdiag[0] = r; }
-        }
-        for (int j = 0; j < kb; ++j) {
-            __syncthreads();
-            if (*s_fail >= 0) break;
-            const T rj = rdiag[j];
-            if constexpr (sizeof(T) == 4) {
-                if (j > 0) {
-                    const T rp = rdiag[j - 1];
-                    for (int i = j + t; i < kb; i += BT) sL[i][j - 1] = sL[i][j - 1] * rp;
+        if constexpr (sizeof(T) == 4) {
+            // Two columns per barrier.  Phase j (columns j and j + 1, whose
+            // 2 x 2 diagonal block thread 0 has factored: r_j, r_j+1 and the
+            // scaled l_j+1,j published) applies the rank-2 update to rows and
+            // columns from j + 2 with both columns scaled where they are used
+            // (l_i,j+1 = (a_i,j+1 - l_ij l_j+1,j) r_j+1), stores the previous
+            // pair scaled, and thread 0 updates and factors the next 2 x 2
+            // block itself.  Every element sees the same fused multiply-adds
+            // in the same order as with one column per barrier.
+            const int tx = t & 15, ty = t >> 4;
+            if (t == 0) {
+                const T d = sL[0][0];
+                if (!(d > (T)0)) *s_fail = 0;
+                else {
+                    const T r = rsqrt_t(d);
+                    sL[0][0] = d * r;
+                    rdiag[0] = r;
+                    if (kb > 1) {
+                        const T l = sL[1][0] * r;
+                        sL[1][0] = l;
+                        const T e = fma(-l, l, sL[1][1]);
+                        if (!(e > (T)0)) *s_fail = 1;
+                        else { const T r1 = rsqrt_t(e); sL[1][1] = e * r1; rdiag[1] = r1; }
+                    }
                 }
-                const int tx = t & 15, ty = t >> 4;
-                if (t == 0 && j + 1 < kb) {
-                    const T l = sL[j + 1][j] * rj;
-                    const T d = sL[j + 1][j + 1] - l * l;
-                    if (!(d > (T)0)) *s_fail = j + 1;
-                    else { const T r = rsqrt_t(d); sL[j + 1][j + 1] = d * r; rdiag[j + 1] = r; }
+            }
+            for (int j = 0; j < kb; j += 2) {
+                __syncthreads();
+                if (*s_fail >= 0) break;
+                const bool two = j + 1 < kb;
+                const T r0 = rdiag[j];
+                const T r1 = two ? rdiag[j + 1] : (T)0;
+                const T l10 = two ? sL[j + 1][j] : (T)0;
+                if (j > 0) {   // the previous pair, rows >= j, stored scaled
+                    const T p0 = rdiag[j - 2], p1 = rdiag[j - 1], pl = sL[j - 1][j - 2];
+                    for (int i = j + t; i < kb; i += BT) {
+                        const T a0 = sL[i][j - 2] * p0;
+                        sL[i][j - 1] = fma(-a0, pl, sL[i][j - 1]) * p1;
+                        sL[i][j - 2] = a0;
+                    }
                 }
-                T lv[4];
+                if (!two) continue;
+                if (t == 0 && j + 2 < kb) {   // the next diagonal block, rows j + 2 (.. j + 3)
+                    const int g = j + 2;
+                    const T c0 = sL[g][j] * r0;
+                    const T c1 = fma(-c0, l10, sL[g][j + 1]) * r1;
+                    T d = fma(-c0, c0, sL[g][g]);
+                    d = fma(-c1, c1, d);
+                    if (!(d > (T)0)) *s_fail = g;
+                    else {
+                        const T r = rsqrt_t(d);
+                        sL[g][g] = d * r;
+                        rdiag[g] = r;
+                        if (g + 1 < kb) {
+                            const T e0 = sL[g + 1][j] * r0;
+                            const T e1 = fma(-e0, l10, sL[g + 1][j + 1]) * r1;
+                            T x = fma(-e0, c0, sL[g + 1][g]);
+                            x = fma(-e1, c1, x);
+                            const T l32 = x * r;
+                            sL[g + 1][g] = l32;
+                            T y = fma(-e0, e0, sL[g + 1][g + 1]);
+                            y = fma(-e1, e1, y);
+                            y = fma(-l32, l32, y);
+                            if (!(y > (T)0)) *s_fail = g + 1;
+                            else { const T r3 = rsqrt_t(y); sL[g + 1][g + 1] = y * r3; rdiag[g + 1] = r3; }
+                        }
+                    }
+                }
+                // rank-2 update of rows j + 4 .. kb - 1 (rows j + 2, j + 3 belong
+                // to thread 0's block), columns j + 2 .. i
+                T lv0[4], lv1[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int l = j + 1 + tx + 16 * u;
-                    lv[u] = l < kb ? sL[l][j] * rj : (T)0;
+                    const int l = j + 2 + tx + 16 * u;
+                    const T v0 = l < kb ? sL[l][j] * r0 : (T)0;
+                    lv0[u] = v0;
+                    lv1[u] = l < kb ? fma(-v0, l10, sL[l][j + 1]) * r1 : (T)0;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int i = j + 1 + ty + 16 * q;
+                    const int i = j + 2 + ty + 16 * q;
                     if (i >= kb) break;
-                    if (i == j + 1) continue;
-                    const T li = sL[i][j] * rj;
+                    if (i < j + 4) continue;
+                    const T li0 = sL[i][j] * r0;
+                    const T li1 = fma(-li0, l10, sL[i][j + 1]) * r1;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int l = j + 1 + tx + 16 * u;
+                        const int l = j + 2 + tx + 16 * u;
                         if (l > i) break;
-                        sL[i][l] -= li * lv[u];
+                        T v = fma(-li0, lv0[u], sL[i][l]);
+                        sL[i][l] = fma(-li1, lv1[u], v);
                     }
                 }
-            } else {
+            }
+        } else {
+            if (t == 0) {
+                const T d = sL[0][0];
+                if (!(d > (T)0)) *s_fail = 0;
+                else { const T r = rsqrt_t(d); sL[0][0] = d * r; rdiag[0] = r; }
+            }
+            for (int j = 0; j < kb; ++j) {
+                __syncthreads();
+                if (*s_fail >= 0) break;
+                const T rj = rdiag[j];
                 for (int i = j + 1 + t; i < kb; i += BT) sL[i][j] = sL[i][j] * rj;
                 const int m = kb - j - 1, M = m * (m + 1) / 2;
                 __syncthreads();
@@ -631,21 +691,15 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 if (NB == 1) {
                     if (!diag) stage_panel_t<T, B>(sJt, A, lda, c0, nc, K0);
                     cp_async_commit();
-                    cp_async_wait<0>();
                 } else if (J + 1 < I) {
                     stage_panel_t<T, B>(sJt + (cur ^ 1) * (MAXB * LDT), A, lda, c0 + B, B, K0);
                     cp_async_commit();
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
                 }
-                if (check)
-                    for (int p = t; p < kb; p += BT) sCJ[p] = S.Cc[J * MAXN + K0 + p];
                 const T* sB = diag ? sIt : sJt + cur * (MAXB * LDT);
                 constexpr int R = B / 16;
                 const int tx = t & 15, ty = t >> 4;
                 // the tile's C values, loaded before the product so that their
-                // latency is hidden behind it (FP32)
+                // latency is hidden behind it and the staging (FP32)
                 T cv[R][R];
                 if (Map::PREF_C) {
 #pragma unroll
@@ -656,6 +710,10 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                             cv[a][b] = (i < nr && j < nc) ? A[(int64_t)(r0 + i) * lda + c0 + j] : (T)0;
                         }
                 }
+                if (check)
+                    for (int p = t; p < kb; p += BT) sCJ[p] = S.Cc[J * MAXN + K0 + p];
+                if (NB == 2 && J + 1 < I) cp_async_wait<1>();
+                else cp_async_wait<0>();
                 __syncthreads();
                 // register tile: thread (tx, ty) owns R x R outputs (Map); per p
                 // it reads R values of each operand row of the transposed panels
