@@ -54,10 +54,6 @@ __device__ __forceinline__ int tri_pair(int e) {
 // Transposed panels in shared memory: element (j, p) of a block's panel rows
 // at p LDT + j, rows of LDT values (16-byte aligned for the vector reads).
 constexpr int LDT = MAXB + 4;
-// J panels staged per CTA.  One buffer: four FP32 CTAs per SM (measured
-// faster than three CTAs whose next tile's rows are copied while this one is
-// multiplied), two FP64 CTAs per SM.
-constexpr int NBUF_F32 = 1;
 
 // Register tile of the update, R = B / 16 outputs per thread and direction.
 // FP32: thread (tx, ty) owns rows R ty + a and columns R tx + b, so that each
@@ -70,7 +66,6 @@ struct TileMap {
     static constexpr int R = B / 16;
     static constexpr bool CONTIG = sizeof(T) == 4;
     static constexpr bool PREF_C = sizeof(T) == 4;
-    static constexpr int NBUF = sizeof(T) == 4 ? NBUF_F32 : 1;
     __device__ static int row(int ty, int a) { return CONTIG ? R * ty + a : ty + 16 * a; }
     __device__ static int col(int tx, int b) { return CONTIG ? R * tx + b : tx + 16 * b; }
     __device__ static void load(const T* rowp, int tt, T (&v)[R]) {
@@ -665,37 +660,28 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         // rows of the panel (c_I, w_I of block row I; c_J of block row J) and
         // the border dot products' partial sums.  The panel rows of blocks I
         // and J sit transposed in sIt / sJt (element (j, p) at p LDT + j),
-        // copied by cp.async; with two J buffers the next tile's rows are in
-        // flight while this tile is multiplied.  A diagonal tile (J = I) takes
-        // its B operand from sIt.
+        // copied by cp.async.  A diagonal tile (J = I) takes its B operand
+        // from sIt.
         T* sCI = &sL[0][0];
         T* sWI = sCI + MAXB;
         T* sCJ = sWI + MAXB;
         T* red = sCJ + MAXB;   // [3][BT / B][MAXB] partial sums of the border products
-        constexpr int NB = Map::NBUF;
         for (int I = k + 1; I < nt; ++I) {
             const int r0 = I * B, nr = min(B, n - r0);
             // a block with rows below it is full: kb = B from here on
             stage_panel_t<T, B>(sIt, A, lda, r0, nr, K0);
-            if (NB == 2 && k + 1 < I) stage_panel_t<T, B>(sJt, A, lda, (k + 1) * B, B, K0);
             cp_async_commit();
             if (check)
                 for (int p = t; p < kb; p += BT) {
                     sCI[p] = S.Cc[I * MAXN + K0 + p];
                     sWI[p] = S.Cw[I * MAXN + K0 + p];
                 }
-            int cur = 0;
             for (int J = k + 1; J <= I; ++J) {
                 const int c0 = J * B, nc = min(B, n - c0);
                 const bool diag = J == I;
-                if (NB == 1) {
-                    if (!diag) stage_panel_t<T, B>(sJt, A, lda, c0, nc, K0);
-                    cp_async_commit();
-                } else if (J + 1 < I) {
-                    stage_panel_t<T, B>(sJt + (cur ^ 1) * (MAXB * LDT), A, lda, c0 + B, B, K0);
-                    cp_async_commit();
-                }
-                const T* sB = diag ? sIt : sJt + cur * (MAXB * LDT);
+                if (!diag) stage_panel_t<T, B>(sJt, A, lda, c0, nc, K0);
+                cp_async_commit();
+                const T* sB = diag ? sIt : sJt;
                 constexpr int R = B / 16;
                 const int tx = t & 15, ty = t >> 4;
                 // the tile's C values, loaded before the product so that their
@@ -712,8 +698,7 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                 }
                 if (check)
                     for (int p = t; p < kb; p += BT) sCJ[p] = S.Cc[J * MAXN + K0 + p];
-                if (NB == 2 && J + 1 < I) cp_async_wait<1>();
-                else cp_async_wait<0>();
+                cp_async_wait<0>();
                 __syncthreads();
                 // register tile: thread (tx, ty) owns R x R outputs (Map); per p
                 // it reads R values of each operand row of the transposed panels
@@ -794,7 +779,6 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
                     }
                 }
                 __syncthreads();
-                if (NB == 2) cur ^= 1;
             }
         }
         if (fok && it.fstep == k && it.fkind == ABFT_FAULT_MEMORY && t == 0)
@@ -821,10 +805,12 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     __syncthreads();
 }
 
-// CTAs per SM: two for FP64 (the FP64 pipe is the limit); for FP32 as many as
-// the shared memory holds (three with double-buffered J panels)
+// CTAs per SM: two for FP64 (the FP64 pipe is the limit), four for FP32 (as
+// many as the shared memory holds; measured faster than three CTAs with a
+// second J panel buffer, whose next tile's rows would be copied during the
+// product)
 template <typename T>
-struct CtasPerSm { static constexpr int v = sizeof(T) == 8 ? 2 : (NBUF_F32 == 2 ? 3 : 4); };
+struct CtasPerSm { static constexpr int v = sizeof(T) == 8 ? 2 : 4; };
 
 template <typename T>
 __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abft_batch_item* items, int count,
@@ -832,11 +818,10 @@ __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abf
                                                       abft_batch_status* status, T* scratch,
                                                       unsigned int* queue) {
     extern __shared__ __align__(16) unsigned char smb[];
-    constexpr int NBUF = TileMap<T, 64>::NBUF;
     T (*sL)[MAXB + 1] = (T (*)[MAXB + 1])smb;
     T* sIt = (T*)(sL + MAXB);
     T* sJt = sIt + MAXB * LDT;
-    T* colsum = sJt + NBUF * MAXB * LDT;
+    T* colsum = sJt + MAXB * LDT;
     T* wsum = colsum + MAXB;
     T* rowsum = wsum + MAXB;
     T* rdiag = rowsum + MAXB;
@@ -874,8 +859,7 @@ __global__ void __launch_bounds__(BT, CtasPerSm<T>::v) k_potrf_batched(const abf
 }  // namespace
 
 size_t batched_smem(bool f64) {
-    const int nbuf = f64 ? TileMap<double, 64>::NBUF : TileMap<float, 64>::NBUF;
-    return (size_t)(MAXB * (MAXB + 1) + (1 + nbuf) * MAXB * LDT + 4 * MAXB) *
+    return (size_t)(MAXB * (MAXB + 1) + 2 * MAXB * LDT + 4 * MAXB) *
            (f64 ? sizeof(double) : sizeof(float));
 }
 
