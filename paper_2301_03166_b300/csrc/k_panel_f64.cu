@@ -294,6 +294,68 @@ __global__ void __launch_bounds__(RW_ROWS) k_trsm_rows(TrsmArgs a) {
     }
 }
 
+// The full-width FP64 case (nb = 64) with two threads per row, lanes 2 r and
+// 2 r + 1: thread h sums the terms p = h (mod 2) of every unknown, in two
+// partial sums, and keeps those x_p in registers; one shuffle per unknown adds
+// the pair's sums (even + odd, the same order on both threads).  Twice the
+// warps of k_trsm_rows and half the dependent chain per thread: at these
+// orders one thread per row leaves a quarter of the sub-partitions without a
+// warp and the rest waiting on dependent FP64 FMAs.
+constexpr int RW2_ROWS = 64;   // rows per CTA (128 threads)
+
+__global__ void __launch_bounds__(2 * RW2_ROWS) k_trsm_rows2(TrsmArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_bytes[];
+    double* X = (double*)smem_bytes;             // RW2_ROWS x RW_LD
+    double* Ls = X + RW2_ROWS * RW_LD;           // 64 x RW_LD
+    double* rinv = Ls + RW_MAXNB * RW_LD;        // 64
+    if (a.st && a.st->info != 0) return;
+    const int64_t bid = blockIdx.x;
+    const int sg = (a.nseg > 1 && bid >= a.start[1]) ? 1 : 0;
+    const TrsmSeg g = sg ? a.seg[1] : a.seg[0];   // static indices: no local copy
+    const int64_t r0 = (bid - (sg ? a.start[1] : a.start[0])) * RW2_ROWS;
+    const int nr = (int)((g.rows - r0) < RW2_ROWS ? (g.rows - r0) : RW2_ROWS);
+    const int t = threadIdx.x;
+    for (int e = t; e < RW2_ROWS * RW_MAXNB; e += 2 * RW2_ROWS) {
+        const int r = e / RW_MAXNB, p = e % RW_MAXNB;
+        X[r * RW_LD + p] = r < nr ? g.B[(r0 + r) * g.ldb + p] : 0.0;
+    }
+    for (int e = t; e < RW_MAXNB * RW_MAXNB; e += 2 * RW2_ROWS) {
+        const int j = e / RW_MAXNB, p = e % RW_MAXNB;
+        Ls[j * RW_LD + p] = p <= j ? a.L[(int64_t)j * a.ldl + p] : 0.0;
+    }
+    for (int j = t; j < RW_MAXNB; j += 2 * RW2_ROWS) rinv[j] = 1.0 / a.L[(int64_t)j * a.ldl + j];
+    __syncthreads();
+    const int r = t >> 1, h = t & 1;
+    double* xr = X + r * RW_LD;
+    double xv[RW_MAXNB / 2];   // x_p, p = 2 q + h
+#pragma unroll
+    for (int j = 0; j < RW_MAXNB; ++j) {
+        const double* lj = Ls + j * RW_LD;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int q = 0; 2 * q < j; ++q) {
+            const int p = 2 * q + h;
+            if (p < j) {
+                if (q & 1) s1 = fma(xv[q], lj[p], s1);
+                else s0 = fma(xv[q], lj[p], s0);
+            }
+        }
+        const double sh = s0 + s1;
+        const double so = __shfl_xor_sync(0xffffffffu, sh, 1);
+        const double tot = h == 0 ? sh + so : so + sh;
+        const double xj = (xr[j] - tot) * rinv[j];
+        if ((j & 1) == h) xv[j >> 1] = xj;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RW_MAXNB / 2; ++q) xr[2 * q + h] = xv[q];
+    __syncthreads();
+    for (int e = t; e < nr * RW_MAXNB; e += 2 * RW2_ROWS) {
+        const int rr = e / RW_MAXNB, p = e % RW_MAXNB;
+        g.B[(r0 + rr) * g.ldb + p] = X[rr * RW_LD + p];
+    }
+}
+
 // PD check on column sums: 1^T A_kk (carried, cc) vs (1^T L) L^T, and, when
 // v != NULL, v = L^{-T} 1 (blocked back substitution, chunks of 32).
 __global__ void __launch_bounds__(512) k_chol_pd_check(const double* L, int64_t ldl, int nb,
@@ -439,6 +501,25 @@ cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const Trs
     if (total == 0) return cudaSuccess;
     a.start[a.nseg] = total;
     a.st = st;
+    if (!f32 && nb == RW_MAXNB) {   // two threads per row
+        int64_t t2 = 0;
+        for (int i = 0; i < a.nseg; ++i) {
+            a.start[i] = t2;
+            t2 += (a.seg[i].rows + RW2_ROWS - 1) / RW2_ROWS;
+        }
+        a.start[a.nseg] = t2;
+        const size_t s2 = (size_t)(RW2_ROWS * RW_LD + RW_MAXNB * RW_LD + RW_MAXNB) * sizeof(double);
+        static bool attr2 = false;
+        if (!attr2) {
+            cudaError_t e = cudaFuncSetAttribute(k_trsm_rows2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)s2);
+            if (e != cudaSuccess) return e;
+            attr2 = true;
+        }
+        k_trsm_rows2<<<(unsigned)t2, 2 * RW2_ROWS, s2, s>>>(a);
+        note_launch();
+        return cudaGetLastError();
+    }
     const size_t sd = (size_t)(RW_ROWS * RW_LD + RW_MAXNB * RW_LD + RW_MAXNB) * sizeof(double);
     const size_t sf = (size_t)(RW_ROWS * RW_LD + RW_MAXNB * RW_LD + RW_MAXNB) * sizeof(float);
     static bool attr_set = false;
