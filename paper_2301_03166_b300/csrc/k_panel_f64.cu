@@ -137,21 +137,36 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u] = (gq + u < w) ? X[gr * ldx + c0 + gq + u] : (T)0;
         const int pbeg = NT ? c1 : 0, pend = NT ? nb : c0;
-        for (int p0 = pbeg; p0 < pend; p0 += CW) {
-            __syncthreads();
-            for (int e = t; e < CW * CW; e += TT) {
-                int q = e / CW, pp = e % CW;
-                T v = 0;
+        // the L piece of columns p0 .. p0 + CW - 1 of the chunk's rows: each
+        // thread's CW * CW / TT values, loaded into registers one piece ahead
+        // (the next piece's loads are in flight during this piece's products)
+        constexpr int PPT = CW * CW / TT;
+        auto load_piece = [&](int p0, T (&v)[PPT]) {
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int e = t + TT * i, q = e / CW, pp = e % CW;
+                T x = 0;
                 if (q < w && p0 + pp < pend) {
                     if (std::is_same<T, float>::value && !NT && a.Lf)
-                        v = (T)a.Lf[(c0 + q) * nb + p0 + pp];
+                        x = (T)a.Lf[(c0 + q) * nb + p0 + pp];
                     else
-                        v = NT ? (T)a.L[(int64_t)(p0 + pp) * a.ldl + c0 + q]
+                        x = NT ? (T)a.L[(int64_t)(p0 + pp) * a.ldl + c0 + q]
                                : (T)a.L[(int64_t)(c0 + q) * a.ldl + p0 + pp];
                 }
-                Ls[q * (CW + 1) + pp] = v;
+                v[i] = x;
+            }
+        };
+        T lnext[PPT];
+        if (pbeg < pend) load_piece(pbeg, lnext);
+        for (int p0 = pbeg; p0 < pend; p0 += CW) {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int e = t + TT * i;
+                Ls[(e / CW) * (CW + 1) + e % CW] = lnext[i];
             }
             __syncthreads();
+            if (p0 + CW < pend) load_piece(p0 + CW, lnext);
 #pragma unroll 8
             for (int pp = 0; pp < CW; ++pp) {
                 T xv = (p0 + pp < pend) ? X[gr * ldx + p0 + pp] : (T)0;
