@@ -181,3 +181,41 @@ def test_sharded_batch_equals_one_launch():
         parts_st.append(sb.status.cpu().numpy())
     full = shard.gather_statuses(np.concatenate(parts_ids), np.concatenate(parts_st), count)
     assert np.array_equal(full, ref)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("mode", [abft.NONE, abft.FULL])
+def test_batched_edge_orders_and_failure(dtype, nb, mode):
+    """Orders below, at and just past the block sizes (single-column PD
+    phases, odd last blocks, ragged edge tiles), FP64 against the oracle and
+    FP32 against LAPACK, and one indefinite matrix in the middle of the batch:
+    its info is the 1-based column of the first non-positive pivot and the
+    matrices around it are unaffected."""
+    sizes = np.array([1, 2, 3, 7, 31, 32, 33, 63, 64, 65, 97, 127, 129, 200])
+    bad = 9                                   # n = 65: pivot 40 made negative
+    mats = [W.spd_mmt(int(n), 7000 + i) for i, n in enumerate(sizes)]
+    mats[bad] = mats[bad].copy()
+    mats[bad][39, 39] = -10.0
+    offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)[:-1]])
+    buf = torch.from_numpy(np.concatenate([m.reshape(-1) for m in mats])).to(DEV).to(dtype)
+    batch = abft.Batch(buf, sizes, offs, nb)
+    abft.potrf_batched(batch, mode=mode)
+    torch.cuda.synchronize()
+    st = batch.statuses()
+    for i, n in enumerate(sizes):
+        if i == bad:
+            assert st[i]["info"] == 40
+            continue
+        assert st[i]["info"] == 0 and st[i]["detected"] == 0, (i, st[i])
+        L = np.tril(batch.matrix(i).cpu().numpy().astype(np.float64))
+        if dtype == torch.float64:
+            Lo, info, _ = oracle.potrf(mats[i], nb, oracle.FULL if mode == abft.FULL else oracle.NONE)
+            assert info == 0
+            assert np.abs(L - np.tril(Lo)).max() <= 1e-12 * max(1.0, np.abs(Lo).max())
+        else:
+            Lf = np.linalg.cholesky(mats[i])
+            assert np.abs(L - Lf).max() <= 64 * 2.0 ** -24 * np.abs(Lf).max()
+        # the strict upper triangle is left as it was
+        U = np.triu(batch.matrix(i).cpu().numpy().astype(np.float64), 1)
+        assert np.array_equal(U, np.triu(mats[i].astype(np.float32 if dtype == torch.float32 else np.float64).astype(np.float64), 1))
