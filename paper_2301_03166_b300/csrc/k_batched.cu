@@ -5,15 +5,17 @@
 // Each CTA repeatedly takes the next matrix from an atomic queue (the host
 // orders the descriptors by decreasing n, so the longest factorizations
 // start first) and factors it with block size B (32 or 64, per descriptor):
-//   PD   the B x B diagonal block in shared memory (right-looking potf2) and
-//        its column-sum check;
+//   PD   the B x B diagonal block in shared memory (right-looking potf2 with
+//        one reciprocal square root per pivot; FP32 two columns per barrier,
+//        FP64 full-warp packed updates) and its column-sum check;
 //   PU   one thread per panel row (and per checksum row) solves x L^T = a with
-//        L_kk in shared memory; panel tiles are verified with the weighted
-//        column checksums;
-//   TMU  B x B output tiles of the lower block triangle (diagonal tiles in
-//        full), L_I and L_J staged in shared memory, C read-modify-written in
-//        global memory (L2-resident for these sizes), checksum borders
-//        updated from the carried panel checksums;
+//        L_kk's rows read four values at a time from shared memory; panel
+//        tiles are verified with the weighted column checksums;
+//   TMU  B x B output tiles of the lower block triangle (diagonal tiles kept
+//        full: FP64 computes the groups on and below the diagonal and mirrors
+//        them), L_I and L_J staged transposed in shared memory by cp.async, C
+//        read-modify-written in global memory (L2-resident for these sizes),
+//        checksum borders updated from the carried panel checksums;
 //   then the optional injected fault and the verify / locate / correct of
 //   every trailing tile (full checksums: 0D, 1D, checksum-only, 2D classes).
 // T is the arithmetic type (double or float); the threshold uses its unit
