@@ -84,6 +84,47 @@ __global__ void k_block_inv(const double* L, int64_t ldl, int64_t n, T* Inv) {
     for (int e = t; e < RB * RB; e += RB) out[e] = Xs[(e / RB) * (RB + 1) + e % RB];
 }
 
+// Coupling of each block with the block solved just before it, folded with
+// the block's inverse: P_i = Inv_i L_{i,i-1} for the L sweep (block 0 has
+// none) and P_i = Inv_i^T L_{i+1,i}^T for the L^T sweep (the last block has
+// none); RB x RB row-major per block, at P + i RB^2.  With them the last step
+// of a block's solve is y_i = w_i - P_i y_prev, w_i = M_i (b_i - the older
+// couplings) formed before y_prev is ready: one product on the sweep's
+// critical path instead of two.  One CTA of RB threads per block; thread b
+// forms column b, each entry one FMA chain over p in order.
+template <typename T, int TRANS>
+__global__ void k_block_couple(const double* L, int64_t ldl, int64_t n, const T* Inv, T* P) {
+    constexpr int RB = SweepCfg<T>::RB;
+    extern __shared__ __align__(16) unsigned char csb[];
+    T* Ms = (T*)csb;                      // RB x (RB + 1): M[a][p]
+    T* Cs = Ms + RB * (RB + 1);           // RB x (RB + 1): C[p][b]
+    const int NB = (int)((n + RB - 1) / RB);
+    const int i = blockIdx.x;
+    const bool has = TRANS ? i + 1 < NB : i > 0;
+    T* out = P + (int64_t)i * RB * RB;
+    const int t = threadIdx.x;
+    if (!has) {
+        for (int e = t; e < RB * RB; e += RB) out[e] = (T)0;
+        return;
+    }
+    const int64_t i0 = (int64_t)i * RB, jn0 = (int64_t)(TRANS ? i + 1 : i - 1) * RB;
+    const T* Ib = Inv + (int64_t)i * RB * RB;
+    for (int e = t; e < RB * RB; e += RB) {
+        const int a = e / RB, q = e % RB;
+        Ms[a * (RB + 1) + q] = TRANS ? Ib[q * RB + a] : Ib[e];   // M = Inv_i^T or Inv_i
+        // C[p][b]: L_{i,i-1}[p][b] = L[i0 + p][jn0 + b], or L_{i+1,i}^T[p][b] = L[jn0 + b][i0 + p]
+        const int64_t gr = TRANS ? jn0 + q : i0 + a, gc = TRANS ? i0 + a : jn0 + q;
+        Cs[a * (RB + 1) + q] = (gr < n && gc < n) ? (T)L[gr * ldl + gc] : (T)0;
+    }
+    __syncthreads();
+    const int b = t;
+    for (int a = 0; a < RB; ++a) {
+        T acc = 0;
+        for (int q = 0; q < RB; ++q) acc = fma(Ms[a * (RB + 1) + q], Cs[q * (RB + 1) + b], acc);
+        out[a * RB + b] = acc;
+    }
+}
+
 // One triangular sweep in a single launch: L Y = Y (TRANS = 0) or L^T X = X
 // (TRANS = 1) for nrhs <= 16 right-hand sides, Y row-major (ld ldy), solved in
 // place.  Rows are cut into RB-row blocks.  CTAs take blocks from a ticket
@@ -116,7 +157,7 @@ size_t sweep_smem_bytes() {
 template <typename T, int TRANS, typename LT>
 __global__ void __launch_bounds__(4 * SweepCfg<T>::RB) k_trsv_sweep(
     const LT* __restrict__ L, int64_t ldl, int64_t n, T* Y, int64_t ldy, int nrhs,
-    const T* __restrict__ Inv, unsigned* sync) {
+    const T* __restrict__ Inv, const T* __restrict__ Pc, unsigned* sync) {
     constexpr int RB = SweepCfg<T>::RB, NT = 4 * RB, PER = RB * RB / NT, YPER = RB * MAXRHS / NT;
     extern __shared__ __align__(16) unsigned char sb[];
     T* sA = (T*)sb;                         // tile, sA[p * (RB + 1) + a] = op(L)[a][p]
@@ -196,44 +237,34 @@ __global__ void __launch_bounds__(4 * SweepCfg<T>::RB) k_trsv_sweep(
         if (t == 0) s_known = (nj > 0 && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) ? nj - 1 : -1;
         __syncthreads();
         int known = s_known;
-        LT preL[PER];
-        T preY[YPER];
-        if (nj > 0) load_tile(jblk(0), preL);
-        bool hy = false;
-        if (nj > 0 && known >= 0) { load_y(jblk(0), preY); hy = true; }
-        for (int k = 0; k < nj; ++k) {
-            store_tile(preL);
-            if (hy) store_y(preY);
-            bool next_y = false;
-            if (k + 1 < nj) {
-                load_tile(jblk(k + 1), preL);
-                if (k + 1 <= known) { load_y(jblk(k + 1), preY); next_y = true; }
-            }
-            if (!hy) {
-                if (t == 0) {
-                    int ok = 1;
-                    const unsigned long long t_start = global_ns();
-                    while (ld_acquire_u32(&flag[jblk(k)]) == 0u) {
-                        if (*(volatile unsigned*)err != 0u) { ok = 0; break; }
-                        if (global_ns() - t_start > 1000000000ull) {
-                            atomicExch(err, 1u);
-                            ok = 0;
-                            break;
-                        }
+        // with the coupling products, the block solved just before this one
+        // (the last in solve order) is taken through P_i at the end
+        const bool usep = Pc != nullptr && nj > 0;
+        const int nk = usep ? nj - 1 : nj;
+        // wait until block jblk(k) is solved; false when the sweep gives up
+        auto wait_block = [&](int k) -> bool {
+            if (t == 0) {
+                int ok = 1;
+                const unsigned long long t_start = global_ns();
+                while (ld_acquire_u32(&flag[jblk(k)]) == 0u) {
+                    if (*(volatile unsigned*)err != 0u) { ok = 0; break; }
+                    if (global_ns() - t_start > 1000000000ull) {
+                        atomicExch(err, 1u);
+                        ok = 0;
+                        break;
                     }
-                    int kn = k;
-                    if (ok && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) kn = nj - 1;
-                    s_known = kn;
-                    s_ok = ok;
                 }
-                __syncthreads();
-                if (!s_ok) return;
-                known = s_known;
-                T v[YPER];
-                load_y(jblk(k), v);
-                store_y(v);
+                int kn = k;
+                if (ok && ld_acquire_u32(&flag[jblk(nj - 1)]) != 0u) kn = nj - 1;
+                s_known = kn;
+                s_ok = ok;
             }
             __syncthreads();
+            known = s_known;
+            return s_ok != 0;
+        };
+        // acc += sA^T sY over this group's quarter of the inner dimension
+        auto tile_product = [&]() {
 #pragma unroll 8
             for (int pp = 0; pp < Q; ++pp) {
                 const int p = g * Q + pp;
@@ -247,6 +278,28 @@ __global__ void __launch_bounds__(4 * SweepCfg<T>::RB) k_trsv_sweep(
 #pragma unroll
                     for (int u = 0; u < 4; ++u) acc[c][u] += a[c] * yv[u];
             }
+        };
+        LT preL[PER];
+        T preY[YPER];
+        if (nk > 0) load_tile(jblk(0), preL);
+        bool hy = false;
+        if (nk > 0 && known >= 0) { load_y(jblk(0), preY); hy = true; }
+        for (int k = 0; k < nk; ++k) {
+            store_tile(preL);
+            if (hy) store_y(preY);
+            bool next_y = false;
+            if (k + 1 < nk) {
+                load_tile(jblk(k + 1), preL);
+                if (k + 1 <= known) { load_y(jblk(k + 1), preY); next_y = true; }
+            }
+            if (!hy) {
+                if (!wait_block(k)) return;
+                T v[YPER];
+                load_y(jblk(k), v);
+                store_y(v);
+            }
+            __syncthreads();
+            tile_product();
             __syncthreads();
             hy = next_y;
         }
@@ -292,12 +345,57 @@ __global__ void __launch_bounds__(4 * SweepCfg<T>::RB) k_trsv_sweep(
             for (int u = 0; u < 4; ++u)
                 red[(g * RB + rg + c * Q) * MAXRHS + 4 * cg + u] = out[c][u];
         __syncthreads();
-        for (int e = t; e < RB * MAXRHS; e += NT) {
-            const int i = e / MAXRHS, r = e % MAXRHS;
+        T wv[YPER];   // w_i (usep) or y_i, entries t + NT q of the block's RB x 16
+#pragma unroll
+        for (int q = 0; q < YPER; ++q) {
+            const int e = t + NT * q;
             T sum = red[e];
 #pragma unroll
-            for (int q = 1; q < 4; ++q) sum += red[q * RB * MAXRHS + e];
-            if (i0 + i < n && r < nrhs) Y[(i0 + i) * ldy + r] = sum;
+            for (int h = 1; h < 4; ++h) sum += red[h * RB * MAXRHS + e];
+            wv[q] = sum;
+        }
+        if (usep) {
+            // y_i = w_i - P_i y_prev: P_i in the tile buffer as a tile
+            // (sA[p][a] = P_i[a][p]), y_prev once its block is solved
+            __syncthreads();   // red (the tile buffer) has been read
+            const T* Pb = Pc + (int64_t)bi * RB * RB;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int e = t + NT * q, aa = e / RB, pq = e % RB;
+                sA[pq * (RB + 1) + aa] = Pb[e];
+            }
+            if (known < nj - 1 && !wait_block(nj - 1)) return;
+            {
+                T v[YPER];
+                load_y(jblk(nj - 1), v);
+                store_y(v);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[c][u] = 0;
+            __syncthreads();
+            tile_product();
+            __syncthreads();   // P_i (the tile buffer) has been read: reuse it for the sums
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    red[(g * RB + rg + c * Q) * MAXRHS + 4 * cg + u] = acc[c][u];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < YPER; ++q) {
+                const int e = t + NT * q;
+                T sum = red[e];
+#pragma unroll
+                for (int h = 1; h < 4; ++h) sum += red[h * RB * MAXRHS + e];
+                wv[q] -= sum;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < YPER; ++q) {
+            const int e = t + NT * q, i = e / MAXRHS, r = e % MAXRHS;
+            if (i0 + i < n && r < nrhs) Y[(i0 + i) * ldy + r] = wv[q];
         }
         __syncthreads();
         // the release store orders the CTA's stores of y_i (made visible to
@@ -512,6 +610,12 @@ cudaError_t set_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_block_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)inv_smem_bytes<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_block_couple<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)inv_smem_bytes<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_block_couple<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)inv_smem_bytes<T>());
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -527,6 +631,11 @@ size_t inv_region(int64_t n, bool f64) {
     return (b + 255) / 256 * 256;
 }
 
+// The solve's precomputed region: the diagonal blocks' inverses, then the
+// coupling products of the L sweep and of the L^T sweep (each the size of the
+// inverses), then the sweeps' tickets and flags.
+size_t pre_region(int64_t n, bool f64) { return 3 * inv_region(n, f64); }
+
 size_t sync_words(int64_t n, bool f64) {
     return 4 + 2 * (size_t)(f64 ? sweep_blocks<double>(n) : sweep_blocks<float>(n));
 }
@@ -538,12 +647,18 @@ cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, const flo
     constexpr bool F64 = sizeof(T) == sizeof(double);
     cudaError_t e = set_attrs<T>();
     if (e != cudaSuccess) return e;
-    unsigned* sync = (unsigned*)((char*)Inv + inv_region(n, F64));
+    unsigned* sync = (unsigned*)((char*)Inv + pre_region(n, F64));
+    T* P0 = (T*)((char*)Inv + inv_region(n, F64));
+    T* P1 = (T*)((char*)Inv + 2 * inv_region(n, F64));
     e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * sync_words(n, F64), s);
     if (e != cudaSuccess) return e;
     const int64_t NB = sweep_blocks<T>(n);
     if (!have_inv) {
         k_block_inv<T><<<(unsigned)NB, SweepCfg<T>::RB, inv_smem_bytes<T>(), s>>>(L, ldl, n, Inv);
+        note_launch();
+        k_block_couple<T, 0><<<(unsigned)NB, SweepCfg<T>::RB, inv_smem_bytes<T>(), s>>>(L, ldl, n, Inv, P0);
+        note_launch();
+        k_block_couple<T, 1><<<(unsigned)NB, SweepCfg<T>::RB, inv_smem_bytes<T>(), s>>>(L, ldl, n, Inv, P1);
         note_launch();
     }
     const int per_sm = F64 ? 2 : 1;
@@ -551,14 +666,14 @@ cudaError_t potrs_t(int64_t n, int nrhs, const double* L, int64_t ldl, const flo
     const size_t smem = sweep_smem_bytes<T>();
     constexpr int NT = 4 * SweepCfg<T>::RB;
     if (!F64 && L32 != nullptr) {   // FP32 tiles: no conversion in the sweep
-        k_trsv_sweep<T, 0, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, sync);
+        k_trsv_sweep<T, 0, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, P0, sync);
         note_launch();
-        k_trsv_sweep<T, 1, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, sync);
+        k_trsv_sweep<T, 1, float><<<grid, NT, smem, s>>>(L32, n, n, Y, ldy, nrhs, Inv, P1, sync);
         note_launch();
     } else {
-        k_trsv_sweep<T, 0, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+        k_trsv_sweep<T, 0, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, P0, sync);
         note_launch();
-        k_trsv_sweep<T, 1, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, sync);
+        k_trsv_sweep<T, 1, double><<<grid, NT, smem, s>>>(L, ldl, n, Y, ldy, nrhs, Inv, P1, sync);
         note_launch();
     }
     return cudaGetLastError();
@@ -591,7 +706,7 @@ cudaError_t launch_tril_to_f32(const double* L, int64_t ldl, int64_t n, float* L
 
 int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_t* ce) {
     unsigned h = 0;
-    const unsigned* sync = (const unsigned*)((const char*)inv + inv_region(n, f64));
+    const unsigned* sync = (const unsigned*)((const char*)inv + pre_region(n, f64));
     *ce = cudaMemcpyAsync(&h, sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (*ce == cudaSuccess) *ce = cudaStreamSynchronize(s);
     return (int)h;
@@ -599,8 +714,8 @@ int potrs_error(const void* inv, int64_t n, bool f64, cudaStream_t s, cudaError_
 
 size_t potrs_inv_bytes(int64_t n, bool f64) {
     (void)f64;   // room for either arithmetic, so one region serves both
-    return std::max(inv_region(n, true) + sizeof(unsigned) * sync_words(n, true),
-                    inv_region(n, false) + sizeof(unsigned) * sync_words(n, false));
+    return std::max(pre_region(n, true) + sizeof(unsigned) * sync_words(n, true),
+                    pre_region(n, false) + sizeof(unsigned) * sync_words(n, false));
 }
 
 cudaError_t launch_copy_d2f(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
