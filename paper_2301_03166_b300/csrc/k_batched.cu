@@ -391,18 +391,26 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
         if (bnd > 0.0 && bnd < 1e300) vexp = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
     }
     __syncthreads();
-    // mirror the diagonal blocks (save their strict upper triangles)
+    // mirror the diagonal blocks (save their strict upper triangles), each
+    // block through shared memory: read row by row, the mirrored upper
+    // triangle written row by row
     for (int K = 0; K < nt; ++K) {
         const int K0 = K * B, kb = min(B, n - K0);
+#pragma unroll 4
         for (int e = t; e < kb * kb; e += BT) {
-            int i = e / kb, j = e % kb;
+            const int i = e / kb, j = e % kb;
+            sL[i][j] = A[(int64_t)(K0 + i) * lda + K0 + j];
+        }
+        __syncthreads();
+        for (int e = t; e < kb * kb; e += BT) {
+            const int i = e / kb, j = e % kb;
             if (j > i) {
-                S.save[(K0 + i) * MAXB + j] = A[(int64_t)(K0 + i) * lda + K0 + j];
-                A[(int64_t)(K0 + i) * lda + K0 + j] = A[(int64_t)(K0 + j) * lda + K0 + i];
+                S.save[(K0 + i) * MAXB + j] = sL[i][j];
+                A[(int64_t)(K0 + i) * lda + K0 + j] = sL[j][i];
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (check)
         for (int I = 0; I < nt; ++I)
             for (int J = 0; J <= I; ++J) {
