@@ -294,6 +294,22 @@ __global__ void __launch_bounds__(MIX_THREADS, 1) k_tmu_mixed(const __grid_const
     }
 }
 
+// exponent of a power of two (sigma), or INT_MIN for 0 / Inf / NaN / subnormal
+__device__ __forceinline__ int pow2_exp(double s) {
+    const int e = (__double2hiint(s) >> 20) & 0x7ff;
+    return (e == 0 || e == 0x7ff) ? INT_MIN : e - 1023;
+}
+
+// x 2^e (|e| < 1000, so 2^e is a normal double): by exponent arithmetic when
+// x and the result are normal, else as the FP64 product with 2^e
+__device__ __forceinline__ double scale_f64(double x, int e) {
+    const int hi = __double2hiint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex != 0 && ex != 0x7ff && ex + e > 0 && ex + e < 0x7ff)
+        return __hiloint2double(hi + (e << 20), __double2loint(x));
+    return x * __hiloint2double((e + 1023) << 20, 0);
+}
+
 // Quantize the panel per g-row tile: sigma_I = 2^(ceil(log2 max|L_I|) - e_t),
 // Lq = RN(L / sigma_I) in BF16 (e_t = 0) or FP16 (e_t = 14); t_I = 1^T Lq_I
 // and (single-side mode) tw_I = (1..g)^T Lq_I, in FP64.
@@ -351,29 +367,33 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     const int cexp = (f == 0.5) ? e2 - 1 : e2;      // ceil(log2 m)
     const int ex = cexp - (BF16 ? 0 : 14);
     const double sigma = (m > 0.0) ? ldexp(1.0, ex) : 1.0;
-    // x / sigma is exact scaling by a power of two; multiply by the exact
-    // reciprocal unless it would leave the normal range
+    // x / sigma is exact scaling by a power of two: x 2^-ex (exponent
+    // arithmetic, scale_f64) unless 2^-ex would leave the normal range
     const bool use_mul = m > 0.0 && ex > -1000 && ex < 1000;
-    const double rsig = use_mul ? ldexp(1.0, -ex) : 1.0;
     double* qp = cl.map_shared_rank(qpart, 0);
+    // FP64-pipe work per element (slow on B300): the rounding to 16 bits and
+    // the sums.  The power-of-two scaling is an exponent addition and the
+    // 16-bit value is widened to FP64 with integer operations (the same
+    // values as the FP64 product and conversion); the weighted sums are formed
+    // only where they are kept.
     for (int p = t; p < kb; p += 256) {
         double s = 0.0, sw = 0.0, sa = 0.0;
         for (int64_t r = s0; r < s1; ++r) {
-            const double x = use_mul ? P[r * lda + p] * rsig : P[r * lda + p] / sigma;
+            const double x = use_mul ? scale_f64(P[r * lda + p], -ex) : P[r * lda + p] / sigma;
             double xq;
             uint16_t bits;
             if (BF16) {
                 __nv_bfloat16 h = __double2bfloat16(x);
                 bits = __bfloat16_as_ushort(h);
-                xq = (double)__bfloat162float(h);
+                xq = f32_to_f64_exact(__bfloat162float(h));
             } else {
                 __half h = __double2half(x);
                 bits = __half_as_ushort(h);
-                xq = (double)__half2float(h);
+                xq = f32_to_f64_exact(__half2float(h));
             }
             Lq[(r - T0) * kb + p] = bits;
             s += xq;
-            sw += (double)(r - r0 + 1) * xq;
+            if (weighted) sw += (double)(r - r0 + 1) * xq;
             sa += fabs(xq);
         }
         qp[(3 * rank) * kb + p] = s;
@@ -475,22 +495,6 @@ constexpr int BSMEM_FLOATS = bsmem(128, 64);   // the largest shape (BBulk)
 static_assert(bsmem(128, 4) <= BSMEM_FLOATS && bsmem(32, 16) <= BSMEM_FLOATS, "shared");
 constexpr int bcfg_rt(int c) { return c == 0 ? BBulk::RT : (c == 1 ? BTiny::RT : BSkinny::RT); }
 constexpr int bcfg_vc(int c) { return c == 0 ? BBulk::VC : (c == 1 ? BTiny::VC : BSkinny::VC); }
-
-// exponent of a power of two (sigma), or INT_MIN for 0 / Inf / NaN / subnormal
-__device__ __forceinline__ int pow2_exp(double s) {
-    const int e = (__double2hiint(s) >> 20) & 0x7ff;
-    return (e == 0 || e == 0x7ff) ? INT_MIN : e - 1023;
-}
-
-// x 2^e (|e| < 1000, so 2^e is a normal double): by exponent arithmetic when
-// x and the result are normal, else as the FP64 product with 2^e
-__device__ __forceinline__ double scale_f64(double x, int e) {
-    const int hi = __double2hiint(x);
-    const int ex = (hi >> 20) & 0x7ff;
-    if (ex != 0 && ex != 0x7ff && ex + e > 0 && ex + e < 0x7ff)
-        return __hiloint2double(hi + (e << 20), __double2loint(x));
-    return x * __hiloint2double((e + 1023) << 20, 0);
-}
 
 // 16-byte global -> shared copy (cp.async), zero-filled when !pred
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
