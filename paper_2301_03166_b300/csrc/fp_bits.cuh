@@ -72,21 +72,36 @@ __device__ __forceinline__ float f64_abs_to_f32_trunc(double x) {
     return __uint_as_float(((uint32_t)(e - 896) << 23) | m);
 }
 
-// An entry as a signed multiple of 2^(vexp - 1075), rounded to nearest (half
-// away from zero); bad = true when its exponent exceeds vexp (or it is not
-// finite).
-__device__ __forceinline__ long long to_fixed(double x, int vexp, bool& bad) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ffull);
-    if (e > vexp) {
-        bad = true;
-        return 0;
-    }
-    const unsigned long long mant = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-    const int sh = vexp - (e ? e : 1);
-    const unsigned long long q = sh >= 64 ? 0ull : (sh == 0 ? mant : ((mant >> (sh - 1)) + 1ull) >> 1);
-    return (b >> 63) ? -(long long)q : (long long)q;
+// a >> s for any s; PTX clamps shift amounts above 31 to 32 (a result of 0)
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t a, uint32_t s) {
+    uint32_t d;
+    asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(s));
+    return d;
 }
+
+// An entry as a signed multiple of 2^(vexp - 1075), truncated toward zero (less
+// than one unit off): its 53-bit significand shifted right by vexp - e in two
+// 32-bit words (a funnel shift for the low word, clamped shifts for the rest),
+// the sign applied as (q ^ s) - s.  emax collects the biased exponents e: an
+// entry above the bound, or not finite, leaves emax > vexp, which the caller
+// checks once per tile.  Zeros and subnormals (e = 0) are read with the
+// implicit bit set, which is below one unit for vexp >= 64: callers take the
+// fixed-point sums only for such bounds.
+__device__ __forceinline__ long long to_fixed(double x, int vexp, int& emax) {
+    const uint32_t lo = (uint32_t)__double2loint(x), hi = (uint32_t)__double2hiint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    emax = e > emax ? e : emax;
+    const uint32_t mh = (hi & 0xfffffu) | 0x100000u;
+    const uint32_t sh = (uint32_t)(vexp - e);
+    const uint32_t ql = sh < 32u ? __funnelshift_rc(lo, mh, sh) : shr_clamp(mh, sh - 32u);
+    const uint32_t qh = shr_clamp(mh, sh);
+    const long long q = (long long)(((unsigned long long)qh << 32) | ql);
+    const long long sg = (long long)((int)hi >> 31);
+    return (q ^ sg) - sg;
+}
+
+// Smallest bound exponent for which to_fixed reads zeros correctly.
+constexpr int kFixedMinExp = 64;
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll

@@ -220,7 +220,7 @@ __device__ void tile_sums(const T* P, int64_t ld, int nr, int nc, T* colsum, T* 
     __syncthreads();
 }
 
-// tile_sums for FP64 tiles in exact 64-bit fixed point: every entry rounded to
+// tile_sums for FP64 tiles in exact 64-bit fixed point: every entry truncated to
 // a multiple of 2^(vexp - 1075) (vexp bounds every entry's biased exponent:
 // the Schur complements of an SPD matrix are bounded by max a_ii, the panel by
 // its square root), the weighted sums in units 2^10 larger so that they stay
@@ -231,13 +231,13 @@ __device__ bool tile_sums_fixed(const double* P, int64_t ld, int nr, int nc, int
                                 double* colsum, double* wsum, double* rowsum, double* part) {
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
     long long c0 = 0, c1 = 0, w0 = 0, w1 = 0;
-    bool bad = false;
+    int emax = 0;
     long long* irow = reinterpret_cast<long long*>(rowsum);
 #pragma unroll 4
     for (int i = w; i < nr; i += BT / 32) {
         const double* row = P + (int64_t)i * ld;
-        const long long q0 = l < nc ? to_fixed(row[l], vexp, bad) : 0ll;
-        const long long q1 = l + 32 < nc ? to_fixed(row[l + 32], vexp, bad) : 0ll;
+        const long long q0 = l < nc ? to_fixed(row[l], vexp, emax) : 0ll;
+        const long long q1 = l + 32 < nc ? to_fixed(row[l + 32], vexp, emax) : 0ll;
         c0 += q0;
         c1 += q1;
         w0 += (long long)(i + 1) * (q0 >> 10);
@@ -245,7 +245,7 @@ __device__ bool tile_sums_fixed(const double* P, int64_t ld, int nr, int nc, int
         const long long rs = warp_sum_ll(q0 + q1);
         if (l == 0) irow[i] = rs;
     }
-    if (__syncthreads_or(bad ? 1 : 0)) return false;
+    if (__syncthreads_or(emax > vexp ? 1 : 0)) return false;
     long long* pc = reinterpret_cast<long long*>(part);   // [8][64] column partials
     long long* pw = pc + 8 * 64;                          // [8][64] weighted partials
     pc[w * 64 + l] = c0;
@@ -388,7 +388,8 @@ __device__ void factor_one(const abft_batch_item& it, int mode, T tau_scale, Scr
     int vexp = 0;
     if (sizeof(T) == 8) {
         const double bnd = fmax((double)dmax, sqrt((double)dmax));
-        if (bnd > 0.0 && bnd < 1e300) vexp = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+        const int ve = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+        if (bnd > 0.0 && bnd < 1e300 && ve >= kFixedMinExp) vexp = ve;
     }
     __syncthreads();
     // mirror the diagonal blocks (save their strict upper triangles), each

@@ -13,8 +13,8 @@
 // sub-partition every ~64 cycles, so FP64 column / row / weighted sums bound the
 // verify by the FP64 pipe.  When the factorization has a magnitude bound
 // (st->vexp > 0: every entry has biased exponent <= vexp), each entry is
-// rounded to an integer multiple of 2^(vexp - 1075) (at most half a unit,
-// 2^-53 of the bound, per entry) and summed exactly in 64-bit integers on the
+// truncated to an integer multiple of 2^(vexp - 1075) (less than one unit,
+// 2^-52 of the bound, per entry) and summed exactly in 64-bit integers on the
 // integer pipes; the weighted sums use units 2^10 larger to stay inside 64
 // bits.  A tile holding an entry above the bound (an injected error, a NaN)
 // is summed again in FP64, so detection, location and correction see the
@@ -132,7 +132,7 @@ __device__ bool tile_sums_fixed(const double* T, int64_t ldt, int nr, int nc, in
     long long acc[TM], wacc[TM];
 #pragma unroll
     for (int t = 0; t < TM; ++t) { acc[t] = 0; wacc[t] = 0; }
-    bool bad = false;
+    int emax = 0;
     long long (*ipart)[kMaxG] = reinterpret_cast<long long (*)[kMaxG]>(part);
     long long* irow = reinterpret_cast<long long*>(rowsum);
     for (int i0 = warp; i0 < nr; i0 += U * kWarps) {
@@ -153,7 +153,7 @@ __device__ bool tile_sums_fixed(const double* T, int64_t ldt, int nr, int nc, in
             long long rs = 0;
 #pragma unroll
             for (int t = 0; t < TM; ++t) {
-                const long long q = to_fixed(v[u][t], vexp, bad);
+                const long long q = to_fixed(v[u][t], vexp, emax);
                 acc[t] += q;
                 if (COLW) wacc[t] += (long long)(i + 1) * (q >> 10);
                 rs += q;
@@ -164,7 +164,7 @@ __device__ bool tile_sums_fixed(const double* T, int64_t ldt, int nr, int nc, in
             }
         }
     }
-    if (__syncthreads_or(bad ? 1 : 0)) return false;
+    if (__syncthreads_or(emax > vexp ? 1 : 0)) return false;
     const double unit = ldexp(1.0, vexp - 1075), wunit = ldexp(1.0, vexp - 1065);
 #pragma unroll
     for (int t = 0; t < TM; ++t)
@@ -454,7 +454,8 @@ __global__ void k_tau_chol(const double* A, int64_t lda, int64_t n, int64_t g, d
         // entries of the Schur complements are bounded by max a_ii, panel
         // entries by sqrt(max a_ii): the fixed-point verify bound
         const double bnd = fmax(m, sqrt(m));
-        st->vexp = (bnd > 0.0 && bnd < 1e300) ? (int)((__double_as_longlong(bnd) >> 52) & 0x7ff) : 0;
+        const int ve = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+        st->vexp = (bnd > 0.0 && bnd < 1e300 && ve >= kFixedMinExp) ? ve : 0;
     }
 }
 
