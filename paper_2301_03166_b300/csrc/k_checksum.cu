@@ -19,7 +19,10 @@
 // bits.  A tile holding an entry above the bound (an injected error, a NaN)
 // is summed again in FP64, so detection, location and correction see the
 // same quantities either way.
+#include <cooperative_groups.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "fp_bits.cuh"
@@ -27,6 +30,8 @@
 namespace abft {
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -230,30 +235,18 @@ __global__ void __launch_bounds__(kThreads) k_encode(TileSet ts) {
 // checksum is wrong, re-encode it; >=2 rows and >=2 cols -> 2D, uncorrectable.
 // Single mode: each flagged column is located at i = rint(d^w_j / d^c_j) - 1
 // (accepted within 0.05 of an integer and inside the tile) and corrected by d^c_j.
-template <int MODE, int TM>
-__global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevStatus* st) {
-    __shared__ double part[kWarps][kMaxG];
-    __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
-    __shared__ int s_nfc, s_nfr, s_fc, s_fr;
-    __shared__ double s_dmax[kWarps];
-    if (st->info != 0) return;
-    int64_t I, J;
-    tile_coords(ts, blockIdx.x, I, J);
-    int nr, nc;
-    tile_extent(ts, I, J, nr, nc);
-    if (nr <= 0 || nc <= 0) return;
+// The classification after the sums (colsum, wsum, rowsum hold the recomputed
+// sums of the tile at T); part[] is scratch that aliases none of them.  sf: four
+// shared ints, s_dmax: kWarps shared doubles.  Called by every thread of one CTA.
+__device__ void verify_classify(const TileSet& ts, int MODE, int step, DevStatus* st, int64_t I,
+                                int64_t J, int nr, int nc, double* T, double* colsum, double* wsum,
+                                double* rowsum, double (*part)[kMaxG], int* sf, double* s_dmax) {
     const int64_t r0 = I * ts.g, c0 = J * ts.g;
-    double* T = ts.A + r0 * ts.lda + c0;
     double* cc = ts.cc + I * ts.ccI + J * ts.g;
     double* cw = (MODE == MODE_SINGLE) ? ts.cw + I * ts.ccI + J * ts.g : nullptr;
     double* cr = (MODE == MODE_FULL) ? ts.cr + r0 * ts.crs + J * ts.crJ : nullptr;
-    if (threadIdx.x == 0) { s_nfc = 0; s_nfr = 0; s_fc = 1 << 30; s_fr = 1 << 30; }
-    const int vexp = st->vexp;
-    if (vexp <= 0 ||
-        !tile_sums_fixed<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, vexp, colsum,
-                                                                     wsum, rowsum, part))
-        tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum,
-                                                             rowsum, part);
+    if (threadIdx.x == 0) { sf[0] = 0; sf[1] = 0; sf[2] = 1 << 30; sf[3] = 1 << 30; }
+    __syncthreads();
     const double tau = st->tau;
     // thresholds per column and row: the scalar tau, or (mixed precision)
     // tau_coef |c|_j + tau64 from the FP32 abs-checksums, formed with one FP32
@@ -301,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
         colsum[j] = d;
         if (MODE == MODE_SINGLE) wsum[j] = wsum[j] - cw[j];
         double a = fabs(d);
-        if (!(a <= TCOL(j))) { atomicAdd(&s_nfc, 1); atomicMin(&s_fc, j); }
+        if (!(a <= TCOL(j))) { atomicAdd(&sf[0], 1); atomicMin(&sf[2], j); }
         if (pc) rmax = fmaxf(rmax, __fdividef(f64_abs_to_f32_trunc(a), tcol32[j]));
         else if (a > dmax) dmax = a;
     }
@@ -310,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
             double d = rowsum[i] - cr[(int64_t)i * ts.crs];
             rowsum[i] = d;
             double a = fabs(d);
-            if (!(a <= TROW(i))) { atomicAdd(&s_nfr, 1); atomicMin(&s_fr, i); }
+            if (!(a <= TROW(i))) { atomicAdd(&sf[1], 1); atomicMin(&sf[3], i); }
             if (pc) rmax = fmaxf(rmax, __fdividef(f64_abs_to_f32_trunc(a), trow32[i]));
             else if (a > dmax) dmax = a;
         }
@@ -319,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((threadIdx.x & 31) == 0) s_dmax[threadIdx.x >> 5] = dmax;
     __syncthreads();
-    const int nfc = s_nfc, nfr = s_nfr, fc = s_fc, fr = s_fr;
+    const int nfc = sf[0], nfr = sf[1], fc = sf[2], fr = sf[3];
     if (nfc == 0 && nfr == 0) {
         if (threadIdx.x == 0) {
             double m = 0.0;
@@ -390,6 +383,191 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
     }
 #undef TCOL
 #undef TROW
+}
+
+template <int MODE, int TM>
+__global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevStatus* st) {
+    __shared__ double part[kWarps][kMaxG];
+    __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
+    __shared__ int sf[4];
+    __shared__ double s_dmax[kWarps];
+    if (st->info != 0) return;
+    int64_t I, J;
+    tile_coords(ts, blockIdx.x, I, J);
+    int nr, nc;
+    tile_extent(ts, I, J, nr, nc);
+    if (nr <= 0 || nc <= 0) return;
+    double* T = ts.A + I * ts.g * ts.lda + J * ts.g;
+    const int vexp = st->vexp;
+    if (vexp <= 0 ||
+        !tile_sums_fixed<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, vexp, colsum,
+                                                                     wsum, rowsum, part))
+        tile_sums<TM, MODE == MODE_SINGLE, MODE == MODE_FULL>(T, ts.lda, nr, nc, colsum, wsum,
+                                                             rowsum, part);
+    verify_classify(ts, MODE, step, st, I, J, nr, nc, T, colsum, wsum, rowsum, part, sf, s_dmax);
+}
+
+// ---- few tiles: one cluster of S CTAs per tile ----
+// A launch with few tiles (the block column verified ahead of the next panel,
+// the panel itself) leaves most SMs idle, and one CTA takes ~25 us for a
+// 256 x 256 tile, on the critical path of the look-ahead.  Here the S CTAs of
+// a cluster (S <= 8) each sum a slab of ceil(g / S) rows: the slab's row sums
+// complete and its column partial sums, in its own shared memory.  After a
+// cluster barrier, rank 0 adds the column partials of ranks 0 .. S-1 in rank
+// order (exact in fixed point, a fixed order in FP64), gathers the row sums
+// from the slabs' CTAs and classifies.  When any slab holds an entry above the fixed-point
+// bound, every slab is summed again in FP64, so the ranks agree on the form of
+// the sums.  The failure flag st->info is read by rank 0 alone and shared, so
+// every CTA of a cluster passes the same barriers.
+
+// Sums of rows ra .. rb - 1 of a tile (FIX: 64-bit fixed point, false when an
+// entry exceeds the bound): column (weighted) partials into cpart / wpart, row
+// sums into rdst (as long long when FIX).
+template <int TM, bool COLW, bool ROWS, bool FIX>
+__device__ bool slab_sums(const double* T, int64_t ldt, int ra, int rb, int nc, int vexp,
+                          double* cpart, double* wpart, double* rdst, double (*part)[kMaxG]) {
+    using Acc = typename std::conditional<FIX, long long, double>::type;
+    constexpr int U = 32 / TM;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = (nc + 31) >> 5;
+    Acc acc[TM], wacc[TM];
+#pragma unroll
+    for (int t = 0; t < TM; ++t) { acc[t] = 0; wacc[t] = 0; }
+    int emax = 0;
+    for (int i0 = ra + warp; i0 < rb; i0 += U * kWarps) {
+        double v[U][TM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            const double* row = T + (int64_t)i * ldt;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                const int j = lane + 32 * t;
+                v[u][t] = (t < nt && i < rb && j < nc) ? row[j] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kWarps;
+            Acc rs = 0;
+#pragma unroll
+            for (int t = 0; t < TM; ++t) {
+                if constexpr (FIX) {
+                    const long long q = to_fixed(v[u][t], vexp, emax);
+                    acc[t] += q;
+                    if (COLW) wacc[t] += (long long)(i + 1) * (q >> 10);
+                    rs += q;
+                } else {
+                    acc[t] += v[u][t];
+                    if (COLW) wacc[t] = fma((double)(i + 1), v[u][t], wacc[t]);
+                    rs += v[u][t];
+                }
+            }
+            if (ROWS) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                if (lane == 0 && i < rb) reinterpret_cast<Acc*>(rdst)[i] = rs;
+            }
+        }
+    }
+    Acc (*ip)[kMaxG] = reinterpret_cast<Acc (*)[kMaxG]>(part);
+#pragma unroll
+    for (int t = 0; t < TM; ++t)
+        if (t < nt) ip[warp][lane + 32 * t] = acc[t];
+    const bool bad = __syncthreads_or(FIX && emax > vexp ? 1 : 0) != 0;
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        Acc sm = 0;
+        for (int w = 0; w < kWarps; ++w) sm += ip[w][j];
+        reinterpret_cast<Acc*>(cpart)[j] = sm;
+    }
+    if (COLW) {
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < TM; ++t)
+            if (t < nt) ip[warp][lane + 32 * t] = wacc[t];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            Acc sm = 0;
+            for (int w = 0; w < kWarps; ++w) sm += ip[w][j];
+            reinterpret_cast<Acc*>(wpart)[j] = sm;
+        }
+    }
+    return !bad;
+}
+
+template <int MODE, int TM, int S>
+__global__ void __launch_bounds__(kThreads, 2) k_verify_cl(TileSet ts, int step, DevStatus* st) {
+    __shared__ double part[kWarps][kMaxG];
+    // colsum / wsum hold this slab's column partials until rank 0 adds them up
+    // (each of its threads reads and then overwrites its own columns)
+    __shared__ double colsum[kMaxG], wsum[kMaxG], rowsum[kMaxG];
+    __shared__ int sf[4];
+    __shared__ double s_dmax[kWarps];
+    __shared__ int s_info, s_bad;
+    constexpr bool COLW = MODE == MODE_SINGLE, ROWS = MODE == MODE_FULL;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    int64_t I, J;
+    tile_coords(ts, blockIdx.x / S, I, J);
+    int nr, nc;
+    tile_extent(ts, I, J, nr, nc);   // the same for every CTA of the cluster
+    if (nr <= 0 || nc <= 0) return;
+    double* T = ts.A + I * ts.g * ts.lda + J * ts.g;
+    const int slab = (int)((ts.g + S - 1) / S);
+    const int ra = rank * slab < nr ? rank * slab : nr;
+    const int rb = ra + slab < nr ? ra + slab : nr;
+    const int vexp = st->vexp;
+    if (rank == 0 && threadIdx.x == 0) s_info = st->info;
+    bool fix = vexp > 0;
+    int ok = 1;
+    if (fix)
+        ok = slab_sums<TM, COLW, ROWS, true>(T, ts.lda, ra, rb, nc, vexp, colsum, wsum, rowsum,
+                                             part);
+    else
+        slab_sums<TM, COLW, ROWS, false>(T, ts.lda, ra, rb, nc, 0, colsum, wsum, rowsum, part);
+    if (threadIdx.x == 0) s_bad = ok ? 0 : 1;
+    cl.sync();
+    const int info = *cl.map_shared_rank(&s_info, 0);
+    int bad = 0;
+    for (int r = 0; r < S; ++r) bad |= *cl.map_shared_rank(&s_bad, r);
+    if (info == 0 && bad) {   // every slab again in FP64 (the flags stay as they are)
+        fix = false;
+        slab_sums<TM, COLW, ROWS, false>(T, ts.lda, ra, rb, nc, 0, colsum, wsum, rowsum, part);
+        cl.sync();
+    }
+    if (info == 0 && rank == 0) {
+        const double unit = fix ? ldexp(1.0, vexp - 1075) : 1.0;
+        const double wunit = fix ? ldexp(1.0, vexp - 1065) : 1.0;
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            if (fix) {
+                long long c = 0, w = 0;
+                for (int r = 0; r < S; ++r) {
+                    c += reinterpret_cast<const long long*>(cl.map_shared_rank(colsum, r))[j];
+                    if (COLW) w += reinterpret_cast<const long long*>(cl.map_shared_rank(wsum, r))[j];
+                }
+                colsum[j] = (double)c * unit;
+                if (COLW) wsum[j] = (double)w * wunit;
+            } else {
+                double c = 0.0, w = 0.0;
+                for (int r = 0; r < S; ++r) {
+                    c += cl.map_shared_rank(colsum, r)[j];
+                    if (COLW) w += cl.map_shared_rank(wsum, r)[j];
+                }
+                colsum[j] = c;
+                if (COLW) wsum[j] = w;
+            }
+        }
+        if (ROWS)
+            for (int i = threadIdx.x; i < nr; i += kThreads) {
+                const double* src = cl.map_shared_rank(rowsum, i / slab);
+                rowsum[i] = fix ? (double)reinterpret_cast<const long long*>(src)[i] * unit : src[i];
+            }
+        __syncthreads();
+    }
+    cl.sync();   // rank 0 has read every slab's partials: no CTA leaves before
+    if (info == 0 && rank == 0)
+        verify_classify(ts, MODE, step, st, I, J, nr, nc, T, colsum, wsum, rowsum, part, sf,
+                        s_dmax);
 }
 
 __global__ void k_inject(double* A, int64_t lda, int64_t row, int64_t col, int64_t len, int along_row,
@@ -475,6 +653,31 @@ void encode_t(const TileSet& ts, int mode, int64_t nt, cudaStream_t s) {
     else k_encode<TM, true, false><<<(unsigned)nt, kThreads, 0, s>>>(ts);
 }
 
+template <int MODE, int S>
+cudaError_t launch_cl(const TileSet& ts, int step, DevStatus* st, int64_t nt, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nt * S), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_verify_cl<MODE, 8, S>, ts, step, st);
+}
+
+template <int MODE>
+cudaError_t verify_cl_t(const TileSet& ts, int S, int step, DevStatus* st, int64_t nt,
+                        cudaStream_t s) {
+    if (S == 8) return launch_cl<MODE, 8>(ts, step, st, nt, s);
+    if (S == 4) return launch_cl<MODE, 4>(ts, step, st, nt, s);
+    return launch_cl<MODE, 2>(ts, step, st, nt, s);
+}
+
 template <int TM>
 void verify_t(const TileSet& ts, int mode, int step, DevStatus* st, int64_t nt, cudaStream_t s) {
     if (mode == MODE_FULL) k_verify<MODE_FULL, TM><<<(unsigned)nt, kThreads, 0, s>>>(ts, step, st);
@@ -497,8 +700,19 @@ cudaError_t launch_verify(const TileSet& ts, int mode, int step, DevStatus* st, 
     int64_t nt = tile_count(ts);
     if (nt <= 0 || mode == MODE_NONE) return cudaSuccess;
     if (ts.g > kMaxG) return cudaErrorInvalidValue;
-    if (ts.g <= 256) verify_t<8>(ts, mode, step, st, nt, s);
-    else verify_t<16>(ts, mode, step, st, nt, s);
+    // few tiles: S CTAs per tile, the largest S in {2, 4, 8} with at most two
+    // CTAs per SM in all (one per tile from num_sms() tiles on)
+    const int64_t slots = 2 * (int64_t)num_sms();
+    const int S = nt * 8 <= slots ? 8 : nt * 4 <= slots ? 4 : nt * 2 <= slots ? 2 : 1;
+    if (S > 1 && ts.g <= 256) {
+        const cudaError_t e = mode == MODE_FULL ? verify_cl_t<MODE_FULL>(ts, S, step, st, nt, s)
+                                                : verify_cl_t<MODE_SINGLE>(ts, S, step, st, nt, s);
+        if (e != cudaSuccess) return e;
+    } else if (ts.g <= 256) {
+        verify_t<8>(ts, mode, step, st, nt, s);
+    } else {
+        verify_t<16>(ts, mode, step, st, nt, s);
+    }
     note_launch();
     return cudaGetLastError();
 }
