@@ -15,6 +15,14 @@
 // earlier scheme met twice per column, the pivot chosen and the rows swapped
 // by one CTA between the barriers.)  The panel (<= 32 MB at n = 16384)
 // stays in L2 across the column loop.
+//
+// When every CTA's rows fit its shared memory (n <= 16384 at kb = 256 on
+// 148 SMs), k_getf2_smem runs the same column loop with those rows held in
+// shared memory from the first column to the last: the scan, the interchange,
+// the scaling and the rank-1 update then make no global round trip, and only
+// the published candidates and the pivot-row copies go through memory.  Its
+// arithmetic is that of k_getf2_coop operation for operation (the same
+// division, the same fused multiply-add), so both give identical panels.
 #include <math.h>
 
 #include "common.cuh"
@@ -149,6 +157,99 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
         }
         __syncthreads();
     }
+}
+
+// k_getf2_coop with the CTA's rows r0 .. r1 - 1 of the panel in shared memory:
+// sp[(i - r0) (kb + 1) + c] (one pad column, so that a column read by the rows
+// of a warp hits 16 banks twice), then urow[kb].  Rows are read once before
+// the column loop and written once after it.
+__global__ void __launch_bounds__(PT) k_getf2_smem(double* P, int64_t lda, int64_t m, int kb,
+                                                   int64_t K0, int64_t* ipiv, DevStatus* st,
+                                                   double* part_v, int64_t* part_i,
+                                                   double* stage) {
+    extern __shared__ double gsm[];
+    const unsigned G = gridDim.x;
+    const int64_t R = (m + G - 1) / G;
+    const int64_t r0 = blockIdx.x * R < m ? blockIdx.x * R : m;
+    const int64_t r1 = (r0 + R < m) ? r0 + R : m;
+    const int nr = (int)(r1 - r0);
+    const int ld = kb + 1;
+    double* sp = gsm;
+    double* urow = gsm + (size_t)R * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < nr; r += PT / 32)
+        for (int c = lane; c < kb; c += 32) sp[r * ld + c] = P[(r0 + r) * lda + c];
+    __syncthreads();
+    unsigned long long nbar = 0;   // grid barriers passed
+    bool alive = true;
+    for (int j = 0; j < kb && alive; ++j) {
+        const int par = j & 1;
+        double* slot = stage + (size_t)par * (G + 1) * kb;
+        // A: local first max over my rows i >= j, published with a copy of the
+        // candidate row; the owner of row j publishes row j
+        double bv = -1.0;
+        int64_t bi = INT64_MAX;
+        const int rj = j - r0 > 0 ? (int)(j - r0) : 0;
+        for (int r = rj + threadIdx.x; r < nr; r += PT) better(bv, bi, fabs(sp[r * ld + j]), r0 + r);
+        block_argmax(bv, bi);
+        if (threadIdx.x == 0) {
+            part_v[par * G + blockIdx.x] = bv;
+            part_i[par * G + blockIdx.x] = bi;
+        }
+        if (bi != INT64_MAX)
+            for (int c = threadIdx.x; c < kb; c += PT)
+                slot[(size_t)blockIdx.x * kb + c] = sp[(bi - r0) * ld + c];
+        if (j >= r0 && j < r1)
+            for (int c = threadIdx.x; c < kb; c += PT)
+                slot[(size_t)G * kb + c] = sp[(j - r0) * ld + c];
+        if (!grid_barrier(st, G, nbar)) {
+            alive = false;
+            break;
+        }
+        // B: every CTA picks the pivot from the published values
+        double v = -1.0;
+        int64_t idx = INT64_MAX;
+        unsigned win = 0;
+        for (unsigned b = threadIdx.x; b < G; b += PT) {
+            const double pv = part_v[par * G + b];
+            const int64_t pi = part_i[par * G + b];
+            if (pv > v || (pv == v && pi < idx)) { v = pv; idx = pi; }
+        }
+        block_argmax(v, idx);
+        const int64_t p = (idx == INT64_MAX) ? j : idx;
+        if (idx != INT64_MAX) win = (unsigned)(idx / R);
+        if (blockIdx.x == 0 && threadIdx.x == 0) ipiv[K0 + j] = K0 + p;
+        for (int c = threadIdx.x; c < kb; c += PT)
+            urow[c] = p == j ? slot[(size_t)G * kb + c] : slot[(size_t)win * kb + c];
+        __syncthreads();
+        const double piv = urow[j];
+        if (piv == 0.0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->lu_info, 0, (int)(K0 + j + 1));
+            continue;
+        }
+        if (p != j) {   // the interchange, in the owners' shared rows
+            if (j >= r0 && j < r1)
+                for (int c = threadIdx.x; c < kb; c += PT) sp[(j - r0) * ld + c] = urow[c];
+            if (p >= r0 && p < r1)
+                for (int c = threadIdx.x; c < kb; c += PT)
+                    sp[(p - r0) * ld + c] = slot[(size_t)G * kb + c];
+            __syncthreads();
+        }
+        // C: scale and rank-1 update of my rows below the pivot; warp w takes
+        // rows w, w + 8, ..., lane l columns j + 1 + l + 32 q
+        const int rb = j + 1 - r0 > 0 ? (int)(j + 1 - r0) : 0;
+        for (int r = rb + threadIdx.x; r < nr; r += PT) sp[r * ld + j] = sp[r * ld + j] / piv;
+        __syncthreads();
+        for (int r = rb + warp; r < nr; r += PT / 32) {
+            const double l = sp[r * ld + j];
+            double* row = sp + r * ld;
+            for (int c = j + 1 + lane; c < kb; c += 32) row[c] = fma(-l, urow[c], row[c]);
+        }
+        __syncthreads();
+    }
+    if (!alive) return;
+    for (int r = warp; r < nr; r += PT / 32)
+        for (int c = lane; c < kb; c += 32) P[(r0 + r) * lda + c] = sp[r * ld + c];
 }
 
 // Row interchanges of the panel applied to every column outside the panel
@@ -485,9 +586,47 @@ size_t getf2_stage_bytes(int64_t kb) {
     return sizeof(double) * 2 * ((size_t)num_sms() + 1) * (size_t)kb;
 }
 
+// shared memory of k_getf2_smem for G CTAs (0 when the rows do not fit)
+size_t getf2_smem_bytes(int64_t m, int64_t kb, int64_t G) {
+    static int cap = -1;
+    if (cap < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 0;
+        cap = v;
+    }
+    const int64_t R = (m + G - 1) / G;
+    const size_t bytes = sizeof(double) * ((size_t)R * (size_t)(kb + 1) + (size_t)kb);
+    // static shared memory of the kernel (block_argmax, grid_barrier): < 512 bytes
+    return bytes + 512 <= (size_t)cap ? bytes : 0;
+}
+
 cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int64_t K0,
                               int64_t* ipiv, DevStatus* st, double* part_v, int64_t* part_i,
                               double* stage, cudaStream_t s) {
+    {   // rows in shared memory: every SM, one CTA each
+        const int64_t G = m < num_sms() ? (m > 0 ? m : 1) : num_sms();
+        const size_t sm = getf2_smem_bytes(m, kb, G);
+        if (sm > 0 && kb <= 512) {
+            static int attr = -1;
+            if ((int)sm > attr) {
+                cudaError_t ea = cudaFuncSetAttribute(k_getf2_smem,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sm);
+                if (ea != cudaSuccess) return ea;
+                attr = (int)sm;
+            }
+            cudaError_t e0 = cudaMemsetAsync(&st->bar_count, 0, sizeof(st->bar_count), s);
+            if (e0 != cudaSuccess) return e0;
+            int kbi = (int)kb;
+            void* args[] = {&P, &lda, &m, &kbi, &K0, &ipiv, &st, &part_v, &part_i, &stage};
+            cudaError_t e = cudaLaunchCooperativeKernel((void*)k_getf2_smem, dim3((unsigned)G),
+                                                        dim3(PT), args, sm, s);
+            note_launch();
+            return e;
+        }
+    }
     int64_t want = (m + 63) / 64;
     int64_t G = want < num_sms() ? want : num_sms();
     if (G < 1) G = 1;
