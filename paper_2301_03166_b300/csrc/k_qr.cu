@@ -212,6 +212,150 @@ __global__ void __launch_bounds__(QT) k_geqr2_coop(double* P, int64_t lda, int64
     }
 }
 
+// k_geqr2_coop with the CTA's rows r0 .. r1 - 1 of the panel in shared memory
+// (sp[(i - r0) kb + c]), then vloc[R] and wl[kb]: the norms, the partial dot
+// products, the scaling and the update read and write shared memory, and only
+// the partial sums, w and the current row j (published by its owner before
+// the first barrier of column j) go through global memory.  The same CTA
+// count, row chunks and operation order as k_geqr2_coop: identical panels.
+__global__ void __launch_bounds__(QT) k_geqr2_smem(double* P, int64_t lda, int64_t m, int kb,
+                                                   double* tau, double* nrm, double* part,
+                                                   double* wv, DevStatus* st) {
+    extern __shared__ double qsm[];
+    __shared__ double red[QT / 32];
+    __shared__ double dpart[QT];    // (row chunk, column) partial dot products
+    __shared__ double s_sst;
+    const unsigned G = gridDim.x;
+    const int64_t R = (m + G - 1) / G;
+    const int64_t r0 = blockIdx.x * R < m ? blockIdx.x * R : m;
+    const int64_t r1 = (r0 + R < m) ? r0 + R : m;
+    const int ld = kb + 1;          // row stride of part
+    double* sp = qsm;
+    double* vloc = qsm + (size_t)R * kb;
+    double* wl = vloc + R;
+    double* mypart = part + (int64_t)blockIdx.x * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t r = warp; r < r1 - r0; r += QT / 32)
+        for (int c = lane; c < kb; c += 32) sp[r * kb + c] = P[(r0 + r) * lda + c];
+    __syncthreads();
+#define SP(i, c) sp[((i) - r0) * kb + (c)]
+    unsigned long long nbar = 0;   // grid barriers passed
+    // column norms before the PD (for the norm-preservation check)
+    for (int c = threadIdx.x; c < kb; c += QT) {
+        double s = 0.0;
+        for (int64_t i = r0; i < r1; ++i) s += SP(i, c) * SP(i, c);
+        mypart[c] = s;
+    }
+    if (!grid_barrier(st, G, nbar)) return;
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < kb; c += QT) {
+            nrm[c] = sqrt(ordered_sum(part + c, ld, G));
+        }
+    if (!grid_barrier(st, G, nbar)) return;
+    for (int j = 0; j < kb; ++j) {
+        // row j as it stands, for every CTA's beta, tau and w
+        if (j >= r0 && j < r1)
+            for (int c = j + threadIdx.x; c < kb; c += QT) P[(int64_t)j * lda + c] = SP(j, c);
+        // A: partial |x(2:)|^2 and partial dots x(2:)^T P[:, c] over my rows i > j
+        const int64_t ibeg = r0 > j + 1 ? r0 : j + 1;
+        double ss = 0.0;
+        for (int64_t i = ibeg + threadIdx.x; i < r1; i += QT) {
+            double x = SP(i, j);
+            ss += x * x;
+        }
+        ss = block_sum(ss, red);
+        if (threadIdx.x == 0) mypart[0] = ss;
+        {
+            const int w = kb - j - 1;
+            const int64_t nrow = r1 - ibeg;
+            int rsp = w > 0 ? QT / w : 1;
+            if ((int64_t)rsp > (nrow + 7) / 8) rsp = (int)((nrow + 7) / 8);
+            if (rsp < 1) rsp = 1;
+            const int64_t rch = (nrow + rsp - 1) / rsp;
+            for (int t = threadIdx.x; t < w * rsp; t += QT) {
+                const int c = j + 1 + t % w;
+                const int64_t ia = ibeg + (int64_t)(t / w) * rch;
+                const int64_t ie = ia + rch < r1 ? ia + rch : r1;
+                double d = 0.0;
+                for (int64_t i = ia; i < ie; i += 8) {
+                    double xv[8], av[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < ie) { xv[u] = SP(i + u, j); av[u] = SP(i + u, c); }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i + u < ie) d += xv[u] * av[u];
+                }
+                dpart[t] = d;
+            }
+            __syncthreads();
+            for (int c = j + 1 + threadIdx.x; c < kb; c += QT) {
+                double d = 0.0;
+                for (int q = 0; q < rsp; ++q) d += dpart[q * w + (c - j - 1)];
+                mypart[1 + c] = d;
+            }
+        }
+        if (!grid_barrier(st, G, nbar)) return;
+        // B: every CTA forms beta, tau; warp q of CTA b reduces the dots of
+        // columns c = j + 1 + 8 b + q, then + 8 G, ...
+        if (threadIdx.x < 32) {
+            const double t = warp_tree_sum(part, ld, G);
+            if (threadIdx.x == 0) s_sst = t;
+        }
+        __syncthreads();
+        const double sst = s_sst;
+        const double alpha = P[(int64_t)j * lda + j];
+        double tj = 0.0, beta = alpha, scal = 1.0;
+        if (sst != 0.0) {
+            double nr = sqrt(alpha * alpha + sst);
+            beta = alpha >= 0.0 ? -nr : nr;
+            tj = (beta - alpha) / beta;
+            scal = alpha - beta;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) tau[j] = tj;
+        if (tj != 0.0) {
+            const int nw = QT / 32;
+            for (int c = j + 1 + (int)blockIdx.x * nw + warp; c < kb; c += (int)G * nw) {
+                const double d = warp_tree_sum(part + 1 + c, ld, G);
+                if (lane == 0) wv[c] = P[(int64_t)j * lda + c] + d / scal;
+            }
+        }
+        if (!grid_barrier(st, G, nbar)) return;
+        // C: v_i = x_i / (alpha - beta); a -= tau v w on my rows
+        if (tj == 0.0) continue;
+        for (int c = j + 1 + threadIdx.x; c < kb; c += QT) wl[c] = wv[c];
+        for (int64_t i = ibeg + threadIdx.x; i < r1; i += QT) {
+            double v = SP(i, j) / scal;
+            SP(i, j) = v;
+            vloc[i - r0] = __dmul_rn(tj, v);  // tau_j v_i, once per row
+        }
+        __syncthreads();
+        const int w = kb - j - 1;
+        if (w > 0) {
+            const int64_t nrow = r1 - ibeg;
+            int rsp = QT / w;
+            if ((int64_t)rsp > (nrow + 7) / 8) rsp = (int)((nrow + 7) / 8);
+            if (rsp < 1) rsp = 1;
+            const int64_t rch = (nrow + rsp - 1) / rsp;
+            for (int t = threadIdx.x; t < w * rsp && ibeg < r1; t += QT) {
+                const int c = j + 1 + t % w;
+                const int64_t ia = ibeg + (int64_t)(t / w) * rch;
+                const int64_t ie = ia + rch < r1 ? ia + rch : r1;
+                const double wc = wl[c];
+                for (int64_t i = ia; i < ie; ++i) SP(i, c) = fma(-vloc[i - r0], wc, SP(i, c));
+            }
+            if (j >= r0 && j < r1)
+                for (int c = j + 1 + threadIdx.x; c < kb; c += QT)
+                    SP(j, c) = __dsub_rn(SP(j, c), __dmul_rn(tj, wl[c]));
+        }
+        if (threadIdx.x == 0 && j >= r0 && j < r1) SP(j, j) = beta;
+        __syncthreads();
+    }
+    for (int64_t r = warp; r < r1 - r0; r += QT / 32)
+        for (int c = lane; c < kb; c += 32) P[(r0 + r) * lda + c] = sp[r * kb + c];
+#undef SP
+}
+
 // PD check: column norms preserved, ||R[0:j+1, j]|| vs the norm before the PD.
 __global__ void k_qr_pd_check(const double* P, int64_t lda, int kb, const double* nrm, int step,
                               int64_t K0, DevStatus* st) {
@@ -330,6 +474,30 @@ cudaError_t launch_geqr2_coop(double* P, int64_t lda, int64_t m, int64_t kb, dou
     cudaError_t e0 = cudaMemsetAsync(&st->bar_count, 0, sizeof(st->bar_count), s);
     if (e0 != cudaSuccess) return e0;
     void* args[] = {&P, &lda, &m, &kbi, &tau, &nrm, &part, &wv, &st};
+    // the rows of every CTA in shared memory when they fit (with the kernel's
+    // static shared memory, about 2.2 KB)
+    static int cap = -1, attr = -1;
+    if (cap < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 0;
+        cap = v;
+    }
+    const int64_t R = (m + G - 1) / G;
+    const size_t sm = sizeof(double) * ((size_t)R * (size_t)kb + (size_t)R + (size_t)kb);
+    if (kb <= 512 && sm + 2304 <= (size_t)cap) {
+        if ((int)sm > attr) {
+            cudaError_t ea = cudaFuncSetAttribute(k_geqr2_smem,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (ea != cudaSuccess) return ea;
+            attr = (int)sm;
+        }
+        cudaError_t e = cudaLaunchCooperativeKernel((void*)k_geqr2_smem, dim3((unsigned)G),
+                                                    dim3(QT), args, sm, s);
+        note_launch();
+        return e;
+    }
     cudaError_t e = cudaLaunchCooperativeKernel((void*)k_geqr2_coop, dim3((unsigned)G), dim3(QT),
                                                 args, 0, s);
     note_launch();
