@@ -20,9 +20,11 @@
 // 148 SMs), k_getf2_smem runs the same column loop with those rows held in
 // shared memory from the first column to the last: the scan, the interchange,
 // the scaling and the rank-1 update then make no global round trip, and only
-// the published candidates and the pivot-row copies go through memory.  Its
-// arithmetic is that of k_getf2_coop operation for operation (the same
-// division, the same fused multiply-add), so both give identical panels.
+// the published candidates and the pivot-row copies go through memory.  It
+// also takes most of each rank-1 update off the chain of barriers (see the
+// kernel).  Its arithmetic is that of k_getf2_coop operation for operation
+// (the same division, the same fused multiply-adds), so both give identical
+// panels.
 #include <math.h>
 
 #include "common.cuh"
@@ -159,97 +161,194 @@ __global__ void __launch_bounds__(PT) k_getf2_coop(double* P, int64_t lda, int64
     }
 }
 
-// k_getf2_coop with the CTA's rows r0 .. r1 - 1 of the panel in shared memory:
-// sp[(i - r0) (kb + 1) + c] (one pad column, so that a column read by the rows
-// of a warp hits 16 banks twice), then urow[kb].  Rows are read once before
-// the column loop and written once after it.
+// Split form of grid_barrier: arrive, do work that the barrier need not wait
+// for, then wait for barrier number `passed` (same counter, same bound).
+__device__ __forceinline__ void grid_arrive(DevStatus* st) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&st->bar_count, 1ull);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(DevStatus* st, unsigned G, unsigned long long passed,
+                                          int* s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long target = passed * G;
+        volatile unsigned long long* vc = &st->bar_count;
+        if (*vc < target) {
+            const unsigned long long t0 = global_ns();
+            while (*vc < target) {
+                if (global_ns() - t0 > kBarrierNs) {
+                    atomicExch(&st->error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, int64_t& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        better(v, idx, ov, oi);
+    }
+}
+
+// k_getf2_coop with the CTA's rows r0 .. r1 - 1 of the panel in shared memory,
+// element (i, c) at sp[(i - r0) kb + (c ^ ((i - r0) & 31))] (kb a multiple of
+// 32: a column read by the rows of a warp and a row read by its lanes both hit
+// 32 banks), then urow[kb] (the pivot row) and uprev[kb] (the previous one).
+// Rows are read once before the column loop and written once after it.
+//
+// The rank-1 update of step j is split: column j + 1 first, then the
+// candidates of column j + 1 are published and the CTA arrives at the
+// barrier, and only then are columns j + 2 .. updated, while the other CTAs
+// arrive.  The published rows are therefore copies in which step j has reached
+// columns <= j + 1 only; after the barrier every CTA completes the pivot row
+// (and row j + 1, for the interchange) with the same fused multiply-add,
+// a_c - l a_jc with the row's own multiplier l from column j, that the owner
+// applies to its row, so the rows agree bit for bit with k_getf2_coop's.
 __global__ void __launch_bounds__(PT) k_getf2_smem(double* P, int64_t lda, int64_t m, int kb,
                                                    int64_t K0, int64_t* ipiv, DevStatus* st,
                                                    double* part_v, int64_t* part_i,
                                                    double* stage) {
     extern __shared__ double gsm[];
+    __shared__ int64_t s_i;
+    __shared__ int s_ok;
     const unsigned G = gridDim.x;
     const int64_t R = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * R < m ? blockIdx.x * R : m;
     const int64_t r1 = (r0 + R < m) ? r0 + R : m;
     const int nr = (int)(r1 - r0);
-    const int ld = kb + 1;
     double* sp = gsm;
-    double* urow = gsm + (size_t)R * ld;
+    double* urow = gsm + (size_t)R * kb;
+    double* uprev = urow + kb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#define SX(r, c) sp[(r) * kb + ((c) ^ ((r) & 31))]
     for (int r = warp; r < nr; r += PT / 32)
-        for (int c = lane; c < kb; c += 32) sp[r * ld + c] = P[(r0 + r) * lda + c];
+        for (int c = lane; c < kb; c += 32) SX(r, c) = P[(r0 + r) * lda + c];
     __syncthreads();
-    unsigned long long nbar = 0;   // grid barriers passed
-    bool alive = true;
-    for (int j = 0; j < kb && alive; ++j) {
+    // publish the candidates of column j: my first max of |a_ij| over my rows
+    // i >= j with a copy of that row, and (owner) a copy of row j
+    auto publish = [&](int j) {
         const int par = j & 1;
         double* slot = stage + (size_t)par * (G + 1) * kb;
-        // A: local first max over my rows i >= j, published with a copy of the
-        // candidate row; the owner of row j publishes row j
-        double bv = -1.0;
-        int64_t bi = INT64_MAX;
-        const int rj = j - r0 > 0 ? (int)(j - r0) : 0;
-        for (int r = rj + threadIdx.x; r < nr; r += PT) better(bv, bi, fabs(sp[r * ld + j]), r0 + r);
-        block_argmax(bv, bi);
-        if (threadIdx.x == 0) {
-            part_v[par * G + blockIdx.x] = bv;
-            part_i[par * G + blockIdx.x] = bi;
+        if (warp == 0) {
+            double bv = -1.0;
+            int64_t bi = INT64_MAX;
+            const int rj = j - r0 > 0 ? (int)(j - r0) : 0;
+            for (int r = rj + lane; r < nr; r += 32) better(bv, bi, fabs(SX(r, j)), r0 + r);
+            warp_argmax(bv, bi);
+            if (lane == 0) {
+                s_i = bi;
+                part_v[par * G + blockIdx.x] = bv;
+                part_i[par * G + blockIdx.x] = bi;
+            }
         }
-        if (bi != INT64_MAX)
-            for (int c = threadIdx.x; c < kb; c += PT)
-                slot[(size_t)blockIdx.x * kb + c] = sp[(bi - r0) * ld + c];
-        if (j >= r0 && j < r1)
-            for (int c = threadIdx.x; c < kb; c += PT)
-                slot[(size_t)G * kb + c] = sp[(j - r0) * ld + c];
-        if (!grid_barrier(st, G, nbar)) {
-            alive = false;
-            break;
+        __syncthreads();
+        const int64_t bi = s_i;
+        if (bi != INT64_MAX) {
+            const int r = (int)(bi - r0);
+            for (int c = threadIdx.x; c < kb; c += PT) slot[(size_t)blockIdx.x * kb + c] = SX(r, c);
         }
-        // B: every CTA picks the pivot from the published values
-        double v = -1.0;
-        int64_t idx = INT64_MAX;
-        unsigned win = 0;
-        for (unsigned b = threadIdx.x; b < G; b += PT) {
-            const double pv = part_v[par * G + b];
-            const int64_t pi = part_i[par * G + b];
-            if (pv > v || (pv == v && pi < idx)) { v = pv; idx = pi; }
+        if (j >= r0 && j < r1) {
+            const int r = (int)(j - r0);
+            for (int c = threadIdx.x; c < kb; c += PT) slot[(size_t)G * kb + c] = SX(r, c);
         }
-        block_argmax(v, idx);
+    };
+    unsigned long long nbar = 0;   // grid barriers arrived at
+    publish(0);
+    ++nbar;
+    grid_arrive(st);
+    bool upd_prev = false;   // the copies of this column still lack step j - 1 beyond column j
+    for (int j = 0; j < kb; ++j) {
+        const int par = j & 1;
+        const double* slot = stage + (size_t)par * (G + 1) * kb;
+        if (!grid_wait(st, G, nbar, &s_ok)) return;
+        // every CTA picks the pivot from the published values (same result)
+        if (warp == 0) {
+            double v = -1.0;
+            int64_t idx = INT64_MAX;
+            for (unsigned b = lane; b < G; b += 32) better(v, idx, part_v[par * G + b], part_i[par * G + b]);
+            warp_argmax(v, idx);
+            if (lane == 0) s_i = idx;
+        }
+        __syncthreads();
+        const int64_t idx = s_i;
         const int64_t p = (idx == INT64_MAX) ? j : idx;
-        if (idx != INT64_MAX) win = (unsigned)(idx / R);
+        const unsigned win = idx == INT64_MAX ? 0u : (unsigned)(idx / R);
         if (blockIdx.x == 0 && threadIdx.x == 0) ipiv[K0 + j] = K0 + p;
-        for (int c = threadIdx.x; c < kb; c += PT)
-            urow[c] = p == j ? slot[(size_t)G * kb + c] : slot[(size_t)win * kb + c];
+        const double* prow = p == j ? slot + (size_t)G * kb : slot + (size_t)win * kb;
+        const double* jrow = slot + (size_t)G * kb;
+        const double lp = upd_prev ? prow[j - 1] : 0.0;
+        for (int c = threadIdx.x; c < kb; c += PT) {
+            double x = prow[c];
+            if (upd_prev && c > j) x = fma(-lp, uprev[c], x);
+            urow[c] = x;
+        }
         __syncthreads();
         const double piv = urow[j];
+        const bool last = j + 1 >= kb;
         if (piv == 0.0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->lu_info, 0, (int)(K0 + j + 1));
+            upd_prev = false;
+            if (!last) {
+                publish(j + 1);
+                ++nbar;
+                grid_arrive(st);
+            }
             continue;
         }
-        if (p != j) {   // the interchange, in the owners' shared rows
-            if (j >= r0 && j < r1)
-                for (int c = threadIdx.x; c < kb; c += PT) sp[(j - r0) * ld + c] = urow[c];
-            if (p >= r0 && p < r1)
-                for (int c = threadIdx.x; c < kb; c += PT)
-                    sp[(p - r0) * ld + c] = slot[(size_t)G * kb + c];
+        if (p != j) {   // the interchange, in the owners' rows (mine are complete)
+            if (j >= r0 && j < r1) {
+                const int r = (int)(j - r0);
+                for (int c = threadIdx.x; c < kb; c += PT) SX(r, c) = urow[c];
+            }
+            if (p >= r0 && p < r1) {
+                const int r = (int)(p - r0);
+                const double lj = upd_prev ? jrow[j - 1] : 0.0;
+                for (int c = threadIdx.x; c < kb; c += PT) {
+                    double x = jrow[c];
+                    if (upd_prev && c > j) x = fma(-lj, uprev[c], x);
+                    SX(r, c) = x;
+                }
+            }
             __syncthreads();
         }
-        // C: scale and rank-1 update of my rows below the pivot; warp w takes
-        // rows w, w + 8, ..., lane l columns j + 1 + l + 32 q
+        // scale column j of my rows below the pivot, update column j + 1
         const int rb = j + 1 - r0 > 0 ? (int)(j + 1 - r0) : 0;
-        for (int r = rb + threadIdx.x; r < nr; r += PT) sp[r * ld + j] = sp[r * ld + j] / piv;
-        __syncthreads();
-        for (int r = rb + warp; r < nr; r += PT / 32) {
-            const double l = sp[r * ld + j];
-            double* row = sp + r * ld;
-            for (int c = j + 1 + lane; c < kb; c += 32) row[c] = fma(-l, urow[c], row[c]);
+        for (int r = rb + threadIdx.x; r < nr; r += PT) {
+            const double l = SX(r, j) / piv;
+            SX(r, j) = l;
+            if (!last) SX(r, j + 1) = fma(-l, urow[j + 1], SX(r, j + 1));
         }
         __syncthreads();
+        if (last) break;
+        publish(j + 1);
+        ++nbar;
+        grid_arrive(st);
+        // the rest of step j while the other CTAs arrive
+        for (int r = rb + warp; r < nr; r += PT / 32) {
+            const double l = SX(r, j);
+            for (int c = j + 2 + lane; c < kb; c += 32) SX(r, c) = fma(-l, urow[c], SX(r, c));
+        }
+        for (int c = threadIdx.x; c < kb; c += PT) uprev[c] = urow[c];
+        upd_prev = true;
     }
-    if (!alive) return;
+    __syncthreads();
     for (int r = warp; r < nr; r += PT / 32)
-        for (int c = lane; c < kb; c += 32) P[(r0 + r) * lda + c] = sp[r * ld + c];
+        for (int c = lane; c < kb; c += 32) P[(r0 + r) * lda + c] = SX(r, c);
+#undef SX
 }
 
 // Row interchanges of the panel applied to every column outside the panel
@@ -597,7 +696,7 @@ size_t getf2_smem_bytes(int64_t m, int64_t kb, int64_t G) {
         cap = v;
     }
     const int64_t R = (m + G - 1) / G;
-    const size_t bytes = sizeof(double) * ((size_t)R * (size_t)(kb + 1) + (size_t)kb);
+    const size_t bytes = sizeof(double) * ((size_t)R * (size_t)kb + 2 * (size_t)kb);
     // static shared memory of the kernel (block_argmax, grid_barrier): < 512 bytes
     return bytes + 512 <= (size_t)cap ? bytes : 0;
 }
@@ -608,7 +707,7 @@ cudaError_t launch_getf2_coop(double* P, int64_t lda, int64_t m, int64_t kb, int
     {   // rows in shared memory: every SM, one CTA each
         const int64_t G = m < num_sms() ? (m > 0 ? m : 1) : num_sms();
         const size_t sm = getf2_smem_bytes(m, kb, G);
-        if (sm > 0 && kb <= 512) {
+        if (sm > 0 && kb <= 512 && kb % 32 == 0) {
             static int attr = -1;
             if ((int)sm > attr) {
                 cudaError_t ea = cudaFuncSetAttribute(k_getf2_smem,
