@@ -12,7 +12,9 @@
 // Verification sums in fixed point: B300 issues one FP64 instruction per
 // sub-partition every ~64 cycles, so FP64 column / row / weighted sums bound the
 // verify by the FP64 pipe.  When the factorization has a magnitude bound
-// (st->vexp > 0: every entry has biased exponent <= vexp), each entry is
+// (st->vexp > 0, set by the threshold kernels: Cholesky max(max a_ii, its
+// square root); QR twice the largest column norm; LU 16 times the largest
+// |a_ij| and |u_ij| seen, a heuristic), each entry of biased exponent <= vexp is
 // truncated to an integer multiple of 2^(vexp - 1075) (less than one unit,
 // 2^-52 of the bound, per entry) and summed exactly in 64-bit integers on the
 // integer pipes; the weighted sums use units 2^10 larger to stay inside 64
@@ -415,9 +417,9 @@ __global__ void __launch_bounds__(kThreads) k_verify(TileSet ts, int step, DevSt
 // complete and its column partial sums, in its own shared memory.  After a
 // cluster barrier, rank 0 adds the column partials of ranks 0 .. S-1 in rank
 // order (exact in fixed point, a fixed order in FP64), gathers the row sums
-// from the slabs' CTAs and classifies.  When any slab holds an entry above the fixed-point
-// bound, every slab is summed again in FP64, so the ranks agree on the form of
-// the sums.  The failure flag st->info is read by rank 0 alone and shared, so
+// from the slabs' CTAs and classifies.  When any slab holds an entry above
+// the fixed-point bound, every slab is summed again in FP64, so the ranks agree
+// on the form of the sums.  The failure flag st->info is read by rank 0 alone and shared, so
 // every CTA of a cluster passes the same barriers.
 
 // Sums of rows ra .. rb - 1 of a tile (FIX: 64-bit fixed point, false when an

@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 
 namespace abft {
 
@@ -468,6 +469,12 @@ __global__ void __launch_bounds__(512) k_lu_pd_check(const double* P, int64_t ld
         tau *= (double)g;
         tau *= M;
         st->tau = tau;
+        // fixed-point bound of the verify sums: 16 max(|a|, |u| so far); a tile
+        // holding an entry above it (growth beyond that, an injected error) is
+        // summed in FP64
+        const double bnd = 16.0 * M;
+        const int ve = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+        st->vexp = (bnd > 0.0 && bnd < 1e300 && ve >= kFixedMinExp) ? ve : 0;
     }
     __syncthreads();
     if (mode == MODE_NONE) return;

@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fp_bits.cuh"
 
 namespace abft {
 
@@ -458,6 +459,12 @@ __global__ void k_set_tau(double tau_scale, int64_t n, int64_t g, DevStatus* st)
     t *= (double)g;
     t *= st->amax;
     st->tau = t;
+    // fixed-point bound of the verify sums: orthogonal updates keep every
+    // column's norm, so no trailing entry exceeds the largest column norm
+    // (twice it, for rounding)
+    const double bnd = 2.0 * st->amax;
+    const int ve = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
+    st->vexp = (bnd > 0.0 && bnd < 1e300 && ve >= kFixedMinExp) ? ve : 0;
 }
 
 }  // namespace
