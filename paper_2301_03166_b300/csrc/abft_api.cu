@@ -677,10 +677,51 @@ int lu_steps(int64_t n, int64_t nb, int32_t mode, double* A, int64_t lda, int64_
         if (m <= 0) break;
         // PU: U = L_kk^{-1} A_kJ with the row-checksum columns t_J = L_kk^{-1} r_kJ folded in
         timing_mark(PH_PU, 1, s);
-        ABFT_CUDA_TRY(launch_trsm_llu(P, lda, kb, A + K0 * lda + T0, lda, m,
-                                      full ? Cr + K0 * nt + (k + 1) : nullptr, nt, nt - k - 1,
-                                      check ? z : nullptr, zw, colchk + T0,
-                                      mode == ABFT_MODE_SINGLE ? colchkw + T0 : nullptr, s));
+        if (emu && kb % 64 == 0 && kb >= 128 && m >= 64) {
+            // blocked by 64 rows: U_b = L_bb^{-1} (A_b - L_b,<b U_<b).  The products
+            // run FP64-accurate from BF16 slices on the tensor cores (rows of
+            // L_b,<b; columns of U_<b and of its row-checksum columns), the 64-wide
+            // unit-lower solves in FP64; the predicted column sums z^T A_kJ are
+            // formed first, from A_kJ as it stands
+            constexpr int64_t RW = 64;
+            uint16_t* Sl = (uint16_t*)(base + w.eslice);
+            int* ex = (int*)(base + w.eex);
+            double* U = A + K0 * lda + T0;
+            const int64_t q = full ? nt - k - 1 : 0;
+            double* Ucr = full ? Cr + K0 * nt + (k + 1) : nullptr;
+            if (check)
+                ABFT_CUDA_TRY(launch_trsm_llu(P, lda, kb, U, lda, m, nullptr, 0, 0, z, zw,
+                                              colchk + T0,
+                                              mode == ABFT_MODE_SINGLE ? colchkw + T0 : nullptr,
+                                              s, true));
+            for (int64_t b = 0; b < kb / RW; ++b) {
+                if (b > 0) {
+                    const int64_t K = b * RW, Mt = RW + m + q;
+                    ABFT_CUDA_TRY(launch_slice_panel(P + b * RW * lda, lda, RW, K, Sl, Mt, 0, ex, s));
+                    ABFT_CUDA_TRY(launch_slice_cols(U, lda, K, m, Sl, Mt, RW, ex, s));
+                    if (full) ABFT_CUDA_TRY(launch_slice_cols(Ucr, nt, K, q, Sl, Mt, RW + m, ex, s));
+                    EmuRectHost rc[2] = {};
+                    rc[0].C = U + b * RW * lda; rc[0].ldc = lda;
+                    rc[0].a0 = 0; rc[0].na = RW; rc[0].b0 = RW; rc[0].nb = m; rc[0].cdiv = 1;
+                    rc[0].frow = -1;
+                    if (full) {
+                        rc[1].C = Ucr + b * RW * nt; rc[1].ldc = nt;
+                        rc[1].a0 = 0; rc[1].na = RW; rc[1].b0 = RW + m; rc[1].nb = q;
+                        rc[1].cdiv = 1; rc[1].frow = -1;
+                    }
+                    ABFT_CUDA_TRY(launch_tmu_emu(Sl, ex, Mt, K, nullptr, 0, 0, 0, 128, rc,
+                                                 full && q > 0 ? 2 : 1, nullptr, 0, 0, st, s));
+                }
+                ABFT_CUDA_TRY(launch_trsm_llu(P + b * RW * (lda + 1), lda, RW, U + b * RW * lda,
+                                              lda, m, full ? Ucr + b * RW * nt : nullptr, nt, q,
+                                              nullptr, nullptr, nullptr, nullptr, s));
+            }
+        } else {
+            ABFT_CUDA_TRY(launch_trsm_llu(P, lda, kb, A + K0 * lda + T0, lda, m,
+                                          full ? Cr + K0 * nt + (k + 1) : nullptr, nt, nt - k - 1,
+                                          check ? z : nullptr, zw, colchk + T0,
+                                          mode == ABFT_MODE_SINGLE ? colchkw + T0 : nullptr, s));
+        }
         for (int f = 0; f < nfaults; ++f)
             if (faults[f].step == k && faults[f].kind == ABFT_FAULT_PANEL)
                 ABFT_CUDA_TRY(launch_inject(A, lda, n, g, faults[f], s));

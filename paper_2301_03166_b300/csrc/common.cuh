@@ -218,7 +218,7 @@ cudaError_t launch_lu_pd_check(const double* P, int64_t lda, int64_t kb, const d
 cudaError_t launch_trsm_llu(const double* L, int64_t ldl, int64_t kb, double* B0, int64_t ldb0,
                             int64_t ncols0, double* B1, int64_t ldb1, int64_t ncols1,
                             const double* z, const double* zw, double* colchk, double* colchkw,
-                            cudaStream_t s);
+                            cudaStream_t s, bool colchk_only = false);
 cudaError_t launch_absmax(const double* A, int64_t lda, int64_t rows, int64_t cols, double* out,
                           cudaStream_t s);
 

@@ -560,6 +560,7 @@ struct TrsmLArgs {
     const double* zw;
     double* colchk;
     double* colchkw;
+    int colchk_only;   // form colchk / colchkw from B and leave B as it is
 };
 
 // U = L^{-1} B (L unit lower kb x kb) for CB columns per CTA, in place; the
@@ -602,6 +603,7 @@ __global__ void __launch_bounds__(256) k_trsm_llu(TrsmLArgs a) {
         }
         __syncthreads();
     }
+    if (a.colchk_only) return;
     const int gr = t >> 3, gq = (t & 7) * 4;   // row gr of the chunk, columns gq..gq+3
     for (int r0 = 0; r0 < kb; r0 += 32) {
         const int w = (kb - r0) < 32 ? (kb - r0) : 32;
@@ -788,8 +790,9 @@ cudaError_t launch_lu_pd_check(const double* P, int64_t lda, int64_t kb, const d
 cudaError_t launch_trsm_llu(const double* L, int64_t ldl, int64_t kb, double* B0, int64_t ldb0,
                             int64_t ncols0, double* B1, int64_t ldb1, int64_t ncols1,
                             const double* z, const double* zw, double* colchk, double* colchkw,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool colchk_only) {
     TrsmLArgs a{};
+    a.colchk_only = colchk_only ? 1 : 0;
     a.L = L; a.ldl = ldl; a.kb = (int)kb;
     a.nseg = 0;
     int64_t total = 0;
