@@ -17,6 +17,16 @@ namespace abft {
 
 constexpr int EMU_SLICES = 8;
 
+// The BF16 pattern of a small integer v (|v| <= 128, exact in BF16): the bits
+// 0x4B400000 + v are the float 1.5 2^23 + v, so subtracting 1.5 2^23 gives v
+// exactly as a float, whose low 16 bits are zero (at most 8 significant bits);
+// its upper half is the BF16 pattern.  One integer add, one FP32 add and a
+// shift instead of two conversions.
+__device__ __forceinline__ uint16_t small_int_bf16(int v) {
+    const float f = __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
 // The eight BF16 slice values (bit patterns) of the value with bits b.
 __device__ __forceinline__ void slice_digits(unsigned long long b, int emax, uint16_t (&out)[8]) {
     const int e = (int)((b >> 52) & 0x7ffull);
@@ -38,7 +48,7 @@ __device__ __forceinline__ void slice_digits(unsigned long long b, int emax, uin
             d -= 128;
             carry = 1;
         }
-        out[p] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -d : d)));
+        out[p] = small_int_bf16(neg ? -d : d);
     }
 }
 

@@ -259,44 +259,105 @@ __global__ void __launch_bounds__(R_THREADS, 1) k_resid_emu(const __grid_constan
 }
 
 // Largest biased exponent of each full row of the symmetric A (lower triangle
-// stored), over 32 x 32 tiles (I >= J) of the lower triangle: a tile's entries
-// count for their rows and, mirrored, for the rows of their columns.
+// stored), over 256 x 256 tiles (I >= J) of the lower triangle: a tile's entries
+// count for their rows and, mirrored, for the rows of their columns.  Thread t
+// reads column t of the tile row by row (coalesced rows, eight loads in flight)
+// and keeps that column's maximum in a register; a row's maximum is a warp
+// reduction per warp and a maximum over the eight warps.  Two global atomics
+// per row and column of a tile (8 per 1024 entries with 32 x 32 tiles).
 __global__ void __launch_bounds__(256) k_sym_exp(const double* __restrict__ A, int64_t lda,
-                                                 int64_t nt, int* __restrict__ emax) {
-    __shared__ int rmax[32], cmax[32];
+                                                 int64_t n, int* __restrict__ emax) {
+    __shared__ unsigned rpart[8][256];
     const int64_t idx = blockIdx.x;
     int64_t I = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
     while (I * (I + 1) / 2 > idx) --I;
     while ((I + 1) * (I + 2) / 2 <= idx) ++I;
     const int64_t J = idx - I * (I + 1) / 2;
-    if (threadIdx.x < 32) {
-        rmax[threadIdx.x] = 0;
-        cmax[threadIdx.x] = 0;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t r0 = I * 256, c = J * 256 + t;
+    const int rows = n - r0 < 256 ? (int)(n - r0) : 256;
+    unsigned cm = 0u;
+    for (int r = 0; r < rows; r += 8) {
+        unsigned long long b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int rr = r + u;
+            const bool ok = rr < rows && c < n && !(I == J && t > rr);
+            b[u] = ok ? (unsigned long long)__double_as_longlong(A[(r0 + rr) * lda + c]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned ex = (unsigned)((b[u] >> 52) & 0x7ffull);
+            cm = ex > cm ? ex : cm;
+            const unsigned rm = __reduce_max_sync(0xffffffffu, ex);
+            if (lane == 0) rpart[warp][(r + u) & 255] = rm;
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-        const int r = e >> 5, c = e & 31;
-        if (I == J && c > r) continue;
-        const unsigned long long b =
-            (unsigned long long)__double_as_longlong(A[(I * 32 + r) * lda + J * 32 + c]);
-        const int ex = (int)((b >> 52) & 0x7ffull);
-        atomicMax(&rmax[r], ex);
-        atomicMax(&cmax[c], ex);
+    if (t < rows) {
+        unsigned m = 0u;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) m = rpart[w][t] > m ? rpart[w][t] : m;
+        atomicMax(&emax[r0 + t], (int)m);
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        atomicMax(&emax[I * 32 + threadIdx.x], rmax[threadIdx.x]);
-        atomicMax(&emax[J * 32 + threadIdx.x], cmax[threadIdx.x]);
-    }
-    (void)nt;
+    if (c < n) atomicMax(&emax[c], (int)cm);
 }
 
 // Slices of the full rows of A: S[p][i][k] for all i, k < n, written per lower
-// 32 x 32 tile directly and (off the diagonal) mirrored through shared memory,
-// so both writes are coalesced along k.
+// 64 x 64 tile directly and (off the diagonal) mirrored through shared memory
+// (n a multiple of 64).  A thread slices two adjacent entries of a row and
+// stores each slice's two digits as one 32-bit word, so that a warp writes one
+// 128-byte row piece per slice.
 __global__ void __launch_bounds__(256) k_sym_slice(const double* __restrict__ A, int64_t lda,
                                                    int64_t n, const int* __restrict__ emax,
                                                    uint16_t* __restrict__ S) {
+    __shared__ double T[64][65];
+    const int64_t idx = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while (I * (I + 1) / 2 > idx) --I;
+    while ((I + 1) * (I + 2) / 2 <= idx) ++I;
+    const int64_t J = idx - I * (I + 1) / 2;
+    for (int e = threadIdx.x; e < 4096; e += 256) {
+        const int r = e >> 6, c = e & 63;
+        T[r][c] = (I == J && c > r) ? 0.0 : A[(I * 64 + r) * lda + J * 64 + c];
+    }
+    __syncthreads();
+    // direct: row I*64 + r, columns J*64 + c, c + 1 (the diagonal tile mirrored in place)
+    for (int e = threadIdx.x; e < 2048; e += 256) {
+        const int r = e >> 5, c = 2 * (e & 31);
+        const double v0 = (I == J && c > r) ? T[c][r] : T[r][c];
+        const double v1 = (I == J && c + 1 > r) ? T[c + 1][r] : T[r][c + 1];
+        const int64_t row = I * 64 + r;
+        const int em = emax[row] > 1 ? emax[row] : 1;
+        uint16_t d0[EMU_SLICES], d1[EMU_SLICES];
+        slice_digits((unsigned long long)__double_as_longlong(v0), em, d0);
+        slice_digits((unsigned long long)__double_as_longlong(v1), em, d1);
+#pragma unroll
+        for (int p = 0; p < EMU_SLICES; ++p)
+            *reinterpret_cast<uint32_t*>(S + ((int64_t)p * n + row) * n + J * 64 + c) =
+                (uint32_t)d0[p] | ((uint32_t)d1[p] << 16);
+    }
+    if (I == J) return;
+    // mirrored: row J*64 + c, columns I*64 + r, r + 1
+    for (int e = threadIdx.x; e < 2048; e += 256) {
+        const int c = e >> 5, r = 2 * (e & 31);
+        const double v0 = T[r][c], v1 = T[r + 1][c];
+        const int64_t row = J * 64 + c;
+        const int em = emax[row] > 1 ? emax[row] : 1;
+        uint16_t d0[EMU_SLICES], d1[EMU_SLICES];
+        slice_digits((unsigned long long)__double_as_longlong(v0), em, d0);
+        slice_digits((unsigned long long)__double_as_longlong(v1), em, d1);
+#pragma unroll
+        for (int p = 0; p < EMU_SLICES; ++p)
+            *reinterpret_cast<uint32_t*>(S + ((int64_t)p * n + row) * n + I * 64 + r) =
+                (uint32_t)d0[p] | ((uint32_t)d1[p] << 16);
+    }
+}
+
+// The same for orders that are a multiple of 32 only (32 x 32 tiles).
+__global__ void __launch_bounds__(256) k_sym_slice32(const double* __restrict__ A, int64_t lda,
+                                                     int64_t n, const int* __restrict__ emax,
+                                                     uint16_t* __restrict__ S) {
     __shared__ double T[32][33];
     const int64_t idx = blockIdx.x;
     int64_t I = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
@@ -308,7 +369,6 @@ __global__ void __launch_bounds__(256) k_sym_slice(const double* __restrict__ A,
         T[r][c] = (I == J && c > r) ? 0.0 : A[(I * 32 + r) * lda + J * 32 + c];
     }
     __syncthreads();
-    // direct: row I*32 + r, column J*32 + c (the diagonal tile mirrored in place)
     for (int e = threadIdx.x; e < 1024; e += 256) {
         const int r = e >> 5, c = e & 31;
         const double v = (I == J && c > r) ? T[c][r] : T[r][c];
@@ -320,7 +380,6 @@ __global__ void __launch_bounds__(256) k_sym_slice(const double* __restrict__ A,
         for (int p = 0; p < EMU_SLICES; ++p) S[((int64_t)p * n + row) * n + J * 32 + c] = d[p];
     }
     if (I == J) return;
-    // mirrored: row J*32 + c, column I*32 + r
     for (int e = threadIdx.x; e < 1024; e += 256) {
         const int c = e >> 5, r = e & 31;
         const double v = T[r][c];
@@ -431,10 +490,16 @@ cudaError_t launch_resid_emu_prepare(const double* A, int64_t lda, int64_t n, vo
     const ResidPtrs r = resid_ptrs(ws, n);
     cudaError_t e = cudaMemsetAsync(r.exA, 0, sizeof(int) * ((size_t)n + RNR + 16), s);
     if (e != cudaSuccess) return e;
-    const int64_t nt = n / 32, tiles = nt * (nt + 1) / 2;
-    k_sym_exp<<<(unsigned)tiles, 256, 0, s>>>(A, lda, nt, r.exA);
+    const int64_t ne = (n + 255) / 256;
+    k_sym_exp<<<(unsigned)(ne * (ne + 1) / 2), 256, 0, s>>>(A, lda, n, r.exA);
     note_launch();
-    k_sym_slice<<<(unsigned)tiles, 256, 0, s>>>(A, lda, n, r.exA, r.SA);
+    if (n % 64 == 0) {
+        const int64_t nt = n / 64;
+        k_sym_slice<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(A, lda, n, r.exA, r.SA);
+    } else {
+        const int64_t nt = n / 32;
+        k_sym_slice32<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(A, lda, n, r.exA, r.SA);
+    }
     note_launch();
     k_exp_to_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r.exA, n);
     note_launch();
