@@ -74,11 +74,13 @@ def parse():
     p.add_argument("--campaign-trials", type=int, default=60)
     p.add_argument("--profile-case", default=None,
                    choices=["fp64", "fp64-emu", "mixed-bf16", "mixed-f16", "potrs-f32", "lu",
-                            "lu-emu", "qr", "qr-emu", "batched-f64", "batched-f32", "fp64-pipes"],
+                            "lu-emu", "qr", "qr-emu", "batched-f64", "batched-f32", "fp64-pipes",
+                            "adjoint", "adjoint-emu"],
                    help="run one case once after one warm-up, print nothing (for ncu): the FP64 "
                         "ABFT Cholesky of the benchmark, a BF16 / FP16 solve with iterative "
                         "refinement, an FP32 two-sweep solve with the FP64 factor, or the ABFT "
-                        "LU (FP64 / FP64-accurate update) or QR of the uniform matrix; at --n, --nb")
+                        "LU (FP64 / FP64-accurate update) or QR of the uniform matrix, or the GP "
+                        "loss forward and backward (FP64 / FP64-accurate); at --n, --nb")
     return p.parse_args()
 
 
@@ -1041,6 +1043,22 @@ def profile_case(args):
                 dt = abft.F64 if args.profile_case == "lu" else abft.F64_EMU
                 abft.getrf(A, nb, abft.FULL, dtype=dt,
                            faults=W.fault_schedule(n, nb, "lu", seed=3000 + n), workspace=wsp)
+        torch.cuda.synchronize(dev)
+        return
+    if args.profile_case in ("adjoint", "adjoint-emu"):
+        # the GP loss of the adjoint configuration (X n x 8, K = exp(-|xi - xj|^2 / 2)
+        # + 1e-2 I), forward and backward through torch.autograd, twice
+        from paper_2301_03166_b300 import autograd as ag
+        Xn, yn = W.gp_inputs(n, 8, seed=1004)
+        Xg = torch.from_numpy(Xn).to(dev)
+        yg = torch.from_numpy(yn).to(dev)
+        sq = (Xg * Xg).sum(1)
+        D = torch.clamp(sq[:, None] + sq[None, :] - 2.0 * Xg @ Xg.T, min=0.0)
+        K0 = torch.exp(-D / 2.0) + 1e-2 * torch.eye(n, dtype=torch.float64, device=dev)
+        dt = abft.F64 if args.profile_case == "adjoint" else abft.F64_EMU
+        for _ in range(2):
+            Kr = K0.clone().requires_grad_(True)
+            ag.gp_negative_log_likelihood_terms(Kr, yg, nb, dtype=dt).backward()
         torch.cuda.synchronize(dev)
         return
     if args.profile_case == "potrs-f32":

@@ -1659,7 +1659,7 @@ size_t adj_base_bytes(int64_t nb) {
 // L21 cut to block row J), 8 BF16 slices of nb columns each; one exponent per
 // slice row; a status block for the tensor-core kernel; the symmetric diagonal block.
 struct AdjEmu {
-    size_t st, S, ex, D, total;
+    size_t st, S, ex, D, PS, pex, total;
     int64_t N, R;
 };
 AdjEmu adj_emu_layout(int64_t n, int64_t nb) {
@@ -1671,6 +1671,10 @@ AdjEmu adj_emu_layout(int64_t n, int64_t nb) {
     a.S = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)a.N * (size_t)a.R * (size_t)nb);
     a.ex = off; off = align_up(off + sizeof(int) * (size_t)a.N * (size_t)a.R);
     a.D = off; off = align_up(off + sizeof(double) * (size_t)nb * (size_t)nb);
+    // the blocked panel solve's own slices: rows of X_>c and columns of L_>c,c
+    const size_t pk = nb > 64 ? (size_t)(nb - 64) : 0;
+    a.PS = off; off = align_up(off + sizeof(uint16_t) * 8 * (size_t)(n + 64) * pk);
+    a.pex = off; off = align_up(off + sizeof(int) * (size_t)(n + 64));
     a.total = off;
     return a;
 }
@@ -1699,6 +1703,8 @@ int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, doub
     uint16_t* S = (uint16_t*)(ws + ae.S);
     int* ex = (int*)(ws + ae.ex);
     double* D = (double*)(ws + ae.D);
+    uint16_t* PS = (uint16_t*)(ws + ae.PS);
+    int* pex = (int*)(ws + ae.pex);
     const int64_t R = ae.R, Mtot = N * R;
     if (emu) ABFT_CUDA_TRY(cudaMemsetAsync(est, 0, sizeof(DevStatus), s));
     for (int64_t k = N - 1; k >= 0; --k) {
@@ -1732,16 +1738,67 @@ int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, doub
             timing_mark(PH_TMU, 0, s);
             // L21 = A21 L11^{-T}  =>  Abar21 = Lbar21 L11^{-1}, Lbar11 -= tril(Abar21^T L21)
             timing_mark(PH_PU, 1, s);
-            TrsmSeg seg{Ab + T0 * ldab + K0, ldab, m};
-            ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &seg, 1, nullptr, nullptr, nullptr, s,
-                                          false, true));
-            GemmSeg g3{};
-            g3.A = Ab + T0 * ldab + K0; g3.lda = ldab;
-            g3.B = L + T0 * ldl + K0; g3.ldb = ldl;
-            g3.C = A11; g3.ldc = ldab;
-            g3.M = kb; g3.N = kb; g3.K = m;
-            g3.g = 1; g3.row0 = 0; g3.col0 = 0;
-            ABFT_CUDA_TRY(launch_gemm_f64_splitk(g3, 1, 1, kAdjSplit, part, nullptr, s));
+            if (emu && kb == nb && kb % 64 == 0 && kb >= 128) {
+                // blocked by 64 columns from the right, X_c L_cc = B_c - X_>c L_>c,c
+                // (X = Abar21, B = Lbar21): the products FP64-accurate from BF16
+                // slices on the tensor cores (rows of X_>c, columns of L_>c,c), the
+                // 64-wide solves in FP64
+                constexpr int64_t CW = 64;
+                double* X = Ab + T0 * ldab + K0;
+                const int64_t ncb = kb / CW;
+                for (int64_t c = ncb - 1; c >= 0; --c) {
+                    if (c < ncb - 1) {
+                        const int64_t K = kb - (c + 1) * CW, Mt = m + CW;
+                        ABFT_CUDA_TRY(launch_slice_panel(X + (c + 1) * CW, ldab, m, K, PS, Mt, 0,
+                                                         pex, s));
+                        ABFT_CUDA_TRY(launch_slice_cols(L11 + (c + 1) * CW * ldl + c * CW, ldl, K,
+                                                        CW, PS, Mt, m, pex, s));
+                        EmuRectHost rc{};
+                        rc.C = X + c * CW; rc.ldc = ldab;
+                        rc.a0 = 0; rc.na = m; rc.b0 = m; rc.nb = CW; rc.cdiv = 1;
+                        rc.frow = -1; rc.fcol = -1;
+                        ABFT_CUDA_TRY(launch_tmu_emu(PS, pex, Mt, K, nullptr, 0, 0, 0, 128, &rc, 1,
+                                                     nullptr, 0, 0, est, s));
+                    }
+                    TrsmSeg sg{X + c * CW, ldab, m};
+                    ABFT_CUDA_TRY(launch_trsm_rows(L11 + c * CW * (ldl + 1), ldl, CW, &sg, 1,
+                                                   nullptr, s, false, true));
+                }
+            } else {
+                TrsmSeg seg{Ab + T0 * ldab + K0, ldab, m};
+                ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &seg, 1, nullptr, nullptr, nullptr, s,
+                                              false, true));
+            }
+            if (emu) {
+                // F's block column k below the diagonal is final with Abar21: slice it
+                // now (its rows for the later steps' products, and Abar21^T as rows
+                // of the later block columns' tensors), then Lbar11 -= tril(Abar21^T
+                // L21) from those rows and L21's: one launch per block row J, each
+                // subtracting its piece into P in order of J
+                ABFT_CUDA_TRY(launch_slice_panel(Ab + T0 * ldab + K0, ldab, m, kb, S, Mtot,
+                                                 k * R + T0, ex, s));
+                ABFT_CUDA_TRY(launch_slice_cols_chunked(Ab + T0 * ldab + K0, ldab, nb, m, kb, S,
+                                                        Mtot, (k + 1) * R + K0, R, ex, s));
+                ABFT_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * kb * kb, s));
+                for (int64_t J = k + 1; J < N; ++J) {
+                    EmuRectHost rc{};
+                    rc.C = P; rc.ldc = kb;
+                    rc.a0 = J * R + K0; rc.na = kb;    // Abar21's columns, block row J
+                    rc.b0 = J * R + n; rc.nb = kb;     // L21's columns, block row J
+                    rc.cdiv = 1; rc.frow = -1; rc.fcol = -1;
+                    ABFT_CUDA_TRY(launch_tmu_emu(S, ex, Mtot, nb, nullptr, 0, 0, 0, 128, &rc, 1,
+                                                 nullptr, 0, 0, est, s));
+                }
+                ABFT_CUDA_TRY(launch_add_tril(P, A11, ldab, kb, s));
+            } else {
+                GemmSeg g3{};
+                g3.A = Ab + T0 * ldab + K0; g3.lda = ldab;
+                g3.B = L + T0 * ldl + K0; g3.ldb = ldl;
+                g3.C = A11; g3.ldc = ldab;
+                g3.M = kb; g3.N = kb; g3.K = m;
+                g3.g = 1; g3.row0 = 0; g3.col0 = 0;
+                ABFT_CUDA_TRY(launch_gemm_f64_splitk(g3, 1, 1, kAdjSplit, part, nullptr, s));
+            }
             timing_mark(PH_PU, 0, s);
         }
         // L11 = chol(A11)  =>  Abar11 = Phi(S + S^T), S = L11^{-T} Phi(L11^T Lbar11) L11^{-1}
@@ -1762,14 +1819,8 @@ int potrf_backward_run(int64_t n, int64_t nb, const double* L, int64_t ldl, doub
         ABFT_CUDA_TRY(launch_trsm_rlt(L11, ldl, kb, &sy, 1, nullptr, nullptr, nullptr, s, false, true));
         ABFT_CUDA_TRY(launch_assemble_diag(Y, kb, A11, ldab, kb, s));
         timing_mark(PH_PD, 0, s);
-        if (emu) {   // block column k of F is final: slice it for the steps still to come
+        if (emu) {   // F's diagonal block is final: slice it for the steps still to come
             timing_mark(PH_OTHER, 1, s);
-            if (m > 0) {
-                ABFT_CUDA_TRY(launch_slice_panel(Ab + T0 * ldab + K0, ldab, m, kb, S, Mtot,
-                                                 k * R + T0, ex, s));
-                ABFT_CUDA_TRY(launch_slice_cols_chunked(Ab + T0 * ldab + K0, ldab, nb, m, kb, S,
-                                                        Mtot, (k + 1) * R + K0, R, ex, s));
-            }
             ABFT_CUDA_TRY(launch_sym_diag(A11, ldab, kb, D, s));
             ABFT_CUDA_TRY(launch_slice_panel(D, kb, kb, kb, S, Mtot, k * R + K0, ex, s));
             timing_mark(PH_OTHER, 0, s);

@@ -186,7 +186,8 @@ struct TrsmSeg {
     int64_t rows;
 };
 cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
-                             int nseg, const DevStatus* st, cudaStream_t s, bool f32 = false);
+                             int nseg, const DevStatus* st, cudaStream_t s, bool f32 = false,
+                             bool rev = false);
 // lf (FP32 X L^T = B only): L rounded to FP32 beforehand by launch_l_to_f32.
 cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
                             int nseg, const double* v, double* x, const DevStatus* st,
@@ -326,6 +327,7 @@ cudaError_t launch_copy_lower(const double* src, int64_t lds, double* dst, int64
 cudaError_t launch_phi_neg(double* P, int64_t ld, int64_t kb, cudaStream_t s);
 // D (kb x kb, ld kb) = A + A^T for the lower-stored block A (diagonal doubled).
 cudaError_t launch_sym_diag(const double* A, int64_t lda, int64_t kb, double* D, cudaStream_t s);
+cudaError_t launch_add_tril(const double* P, double* A, int64_t lda, int64_t kb, cudaStream_t s);
 cudaError_t launch_transpose(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t kb,
                              cudaStream_t s);
 cudaError_t launch_assemble_diag(const double* St, int64_t lds, double* A, int64_t lda, int64_t kb,

@@ -61,6 +61,14 @@ __global__ void k_sym_diag(const double* A, int64_t lda, int kb, double* D) {
     D[e] = i > j ? A[(int64_t)i * lda + j] : (i < j ? A[(int64_t)j * lda + i] : 2.0 * A[(int64_t)i * lda + i]);
 }
 
+// A += tril(P) for a kb x kb block (P dense, ld kb).
+__global__ void k_add_tril(const double* P, double* A, int64_t lda, int kb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kb * kb) return;
+    const int i = e / kb, j = e % kb;
+    if (j <= i) A[(int64_t)i * lda + j] += P[e];
+}
+
 // U = L^T X for lower L (only p >= i of column i used): U[i][r] = sum_{p >= i} L[p][i] X[p][r].
 __global__ void __launch_bounds__(256) k_ltx(const double* L, int64_t ldl, int64_t n,
                                              const double* X, int64_t ldx, int nrhs, double* U,
@@ -180,6 +188,13 @@ cudaError_t launch_copy_lower(const double* src, int64_t lds, double* dst, int64
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_copy_lower<<<blocks_for(n * n), 256, 0, s>>>(src, lds, dst, ldd, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_tril(const double* P, double* A, int64_t lda, int64_t kb, cudaStream_t s) {
+    if (kb <= 0) return cudaSuccess;
+    k_add_tril<<<blocks_for(kb * kb), 256, 0, s>>>(P, A, lda, (int)kb);
     note_launch();
     return cudaGetLastError();
 }

@@ -78,6 +78,7 @@ struct TrsmArgs {
     double* x;
     const DevStatus* st;
     const float* Lf;    // FP32 solves: L rounded to FP32 once (nb x nb, ld nb), or null
+    int rev;            // k_trsm_rows2 only: solve X L = B instead of X L^T = B
 };
 
 // The lower triangle of L rounded to FP32 (ld nb), once per panel solve
@@ -312,7 +313,11 @@ __global__ void __launch_bounds__(RW_ROWS) k_trsm_rows(TrsmArgs a) {
 // The full-width FP64 case (nb = 64) with two threads per row, lanes 2 r and
 // 2 r + 1: thread h sums the terms p = h (mod 2) of every unknown, in two
 // partial sums, and keeps those x_p in registers; one shuffle per unknown adds
-// the pair's sums (even + odd, the same order on both threads).  Twice the
+// the pair's sums (even + odd, the same order on both threads).
+// rev: X L = B (the reverse sweep's panel solve).  With j' = 63 - j, that is
+// x'_j' = (b'_j' - sum_{p' < j'} x'_p' M_j'p') / M_j'j' for M_j'p' = L_(63-p')(63-j')
+// (lower triangular again): the same recurrence on the reversed columns of X
+// and B with the anti-transpose of L.  Twice the
 // warps of k_trsm_rows and half the dependent chain per thread: at these
 // orders one thread per row leaves a quarter of the sub-partitions without a
 // warp and the rest waiting on dependent FP64 FMAs.
@@ -330,15 +335,19 @@ __global__ void __launch_bounds__(2 * RW2_ROWS) k_trsm_rows2(TrsmArgs a) {
     const int64_t r0 = (bid - (sg ? a.start[1] : a.start[0])) * RW2_ROWS;
     const int nr = (int)((g.rows - r0) < RW2_ROWS ? (g.rows - r0) : RW2_ROWS);
     const int t = threadIdx.x;
+    const int rv = a.rev ? RW_MAXNB - 1 : 0;   // column p of X, B is column |rv - p|
     for (int e = t; e < RW2_ROWS * RW_MAXNB; e += 2 * RW2_ROWS) {
         const int r = e / RW_MAXNB, p = e % RW_MAXNB;
-        X[r * RW_LD + p] = r < nr ? g.B[(r0 + r) * g.ldb + p] : 0.0;
+        X[r * RW_LD + p] = r < nr ? g.B[(r0 + r) * g.ldb + (rv ? rv - p : p)] : 0.0;
     }
     for (int e = t; e < RW_MAXNB * RW_MAXNB; e += 2 * RW2_ROWS) {
         const int j = e / RW_MAXNB, p = e % RW_MAXNB;
-        Ls[j * RW_LD + p] = p <= j ? a.L[(int64_t)j * a.ldl + p] : 0.0;
+        Ls[j * RW_LD + p] = p > j ? 0.0
+                            : rv  ? a.L[(int64_t)(rv - p) * a.ldl + (rv - j)]
+                                  : a.L[(int64_t)j * a.ldl + p];
     }
-    for (int j = t; j < RW_MAXNB; j += 2 * RW2_ROWS) rinv[j] = 1.0 / a.L[(int64_t)j * a.ldl + j];
+    for (int j = t; j < RW_MAXNB; j += 2 * RW2_ROWS)
+        rinv[j] = 1.0 / a.L[(int64_t)(rv ? rv - j : j) * a.ldl + (rv ? rv - j : j)];
     __syncthreads();
     const int r = t >> 1, h = t & 1;
     double* xr = X + r * RW_LD;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(2 * RW2_ROWS) k_trsm_rows2(TrsmArgs a) {
     __syncthreads();
     for (int e = t; e < nr * RW_MAXNB; e += 2 * RW2_ROWS) {
         const int rr = e / RW_MAXNB, p = e % RW_MAXNB;
-        g.B[(r0 + rr) * g.ldb + p] = X[rr * RW_LD + p];
+        g.B[(r0 + rr) * g.ldb + (rv ? rv - p : p)] = X[rr * RW_LD + p];
     }
 }
 
@@ -498,10 +507,12 @@ cudaError_t launch_trsm_rlt(const double* L, int64_t ldl, int64_t nb, const Trsm
 // X L^T = B for nb <= 64 with k_trsm_rows (f32: in FP32, the FP64 B and L
 // rounded on load).
 cudaError_t launch_trsm_rows(const double* L, int64_t ldl, int64_t nb, const TrsmSeg* segs,
-                             int nseg, const DevStatus* st, cudaStream_t s, bool f32) {
+                             int nseg, const DevStatus* st, cudaStream_t s, bool f32, bool rev) {
     if (nb <= 0) return cudaSuccess;
     if (nb > RW_MAXNB || nseg < 1 || nseg > 2) return cudaErrorInvalidValue;
+    if (rev && (f32 || nb != RW_MAXNB)) return cudaErrorInvalidValue;
     TrsmArgs a{};
+    a.rev = rev ? 1 : 0;
     a.L = L;
     a.ldl = ldl;
     a.nb = (int)nb;
