@@ -16,6 +16,7 @@ namespace {
 
 constexpr int QT = 256;
 constexpr int QMAXR = 1024;
+constexpr int QT_PF = 8;   // partials per lane held by k_geqr2_smem's phase B (G <= 256)
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -298,14 +299,32 @@ __global__ void __launch_bounds__(QT) k_geqr2_smem(double* P, int64_t lda, int64
         }
         if (!grid_barrier(st, G, nbar)) return;
         // B: every CTA forms beta, tau; warp q of CTA b reduces the dots of
-        // columns c = j + 1 + 8 b + q, then + 8 G, ...
-        if (threadIdx.x < 32) {
-            const double t = warp_tree_sum(part, ld, G);
-            if (threadIdx.x == 0) s_sst = t;
+        // columns c = j + 1 + 8 b + q, then + 8 G, ...  Every load of this phase
+        // (the |x|^2 partials, alpha, the first column's dot partials and a_jc)
+        // is issued before the first sum, and each sum adds its values in the
+        // order of warp_tree_sum, so the results are those of k_geqr2_coop
+        const int nw = QT / 32;
+        const int c1 = j + 1 + (int)blockIdx.x * nw + warp;   // this warp's first column
+        double sv[QT_PF], dv[QT_PF];
+#pragma unroll
+        for (int q = 0; q < QT_PF; ++q) {
+            const unsigned bq = lane + 32u * q;
+            sv[q] = (warp == 0 && bq < G) ? part[(int64_t)bq * ld] : 0.0;
+            dv[q] = (c1 < kb && bq < G) ? part[(int64_t)bq * ld + 1 + c1] : 0.0;
+        }
+        const double alpha = P[(int64_t)j * lda + j];
+        const double ajc1 = c1 < kb ? P[(int64_t)j * lda + c1] : 0.0;
+        if (warp == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < QT_PF; ++q)
+                if (lane + 32u * q < G) t += sv[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) s_sst = t;
         }
         __syncthreads();
         const double sst = s_sst;
-        const double alpha = P[(int64_t)j * lda + j];
         double tj = 0.0, beta = alpha, scal = 1.0;
         if (sst != 0.0) {
             double nr = sqrt(alpha * alpha + sst);
@@ -315,8 +334,16 @@ __global__ void __launch_bounds__(QT) k_geqr2_smem(double* P, int64_t lda, int64
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) tau[j] = tj;
         if (tj != 0.0) {
-            const int nw = QT / 32;
-            for (int c = j + 1 + (int)blockIdx.x * nw + warp; c < kb; c += (int)G * nw) {
+            if (c1 < kb) {
+                double d = 0.0;
+#pragma unroll
+                for (int q = 0; q < QT_PF; ++q)
+                    if (lane + 32u * q < G) d += dv[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (lane == 0) wv[c1] = ajc1 + d / scal;
+            }
+            for (int c = c1 + (int)G * nw; c < kb; c += (int)G * nw) {
                 const double d = warp_tree_sum(part + 1 + c, ld, G);
                 if (lane == 0) wv[c] = P[(int64_t)j * lda + c] + d / scal;
             }
@@ -493,7 +520,7 @@ cudaError_t launch_geqr2_coop(double* P, int64_t lda, int64_t m, int64_t kb, dou
     }
     const int64_t R = (m + G - 1) / G;
     const size_t sm = sizeof(double) * ((size_t)R * (size_t)kb + (size_t)R + (size_t)kb);
-    if (kb <= 512 && sm + 2304 <= (size_t)cap) {
+    if (kb <= 512 && G <= 32 * QT_PF && sm + 2304 <= (size_t)cap) {
         if ((int)sm > attr) {
             cudaError_t ea = cudaFuncSetAttribute(k_geqr2_smem,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
