@@ -27,6 +27,8 @@
 // panels.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "fp_bits.cuh"
 
@@ -434,40 +436,45 @@ __global__ void k_lu_colsums(const double* P, int64_t lda, int64_t m, int kb, in
 // Single CTA: running max |U| and the step's threshold, the PD check
 // (total panel column sums vs (1^T L) U_kk), and z = L_kk^{-T} 1,
 // zw = L_kk^{-T} (1..kb) for the column sums of U.
+// The largest |u_ij| of the U11 block (j >= i), merged into st->umax (an
+// atomic maximum on the bits of a non-negative double): the first half of the
+// PD check, over many CTAs.
+__global__ void __launch_bounds__(256) k_lu_umax(const double* P, int64_t lda, int kb,
+                                                DevStatus* st) {
+    double m = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)kb * kb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / kb), j = (int)(e % kb);
+        if (j >= i) m = fmax(m, fabs(P[(int64_t)i * lda + j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg((unsigned long long*)&st->umax, m);
+}
+
+// The rest of the PD check, after k_lu_umax: the threshold from max(amax, umax)
+// (every CTA forms the same value; CTA 0 stores it and the fixed-point bound),
+// the check of the carried column sums 1^T [L11; L21] U11 against ptot with
+// one warp per column (CTAs 0 .. nchk - 1, columns nw b + w, ...), and, on the
+// last CTA, z = L^{-T} 1 and zw = L^{-T} w (unit upper L^T) for the carried
+// row checksums.  Each part keeps the operations and order of the one-CTA form.
 __global__ void __launch_bounds__(512) k_lu_pd_check(const double* P, int64_t lda, int kb,
                                                      const double* ptot, const double* part,
                                                      int64_t ldpart, int nparts, int step,
                                                      int64_t K0, int64_t n, int64_t g,
                                                      double tau_scale, double* z, double* zw,
-                                                     int mode, DevStatus* st) {
+                                                     int mode, DevStatus* st, int nchk) {
     __shared__ double lsum[512];
-    __shared__ double red[16];
     __shared__ double tz[512], tw[512];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-    double m = 0.0;
-    for (int e = t; e < kb * kb; e += blockDim.x) {
-        int i = e / kb, j = e % kb;
-        if (j >= i) m = fmax(m, fabs(P[(int64_t)i * lda + j]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) red[warp] = m;
-    for (int q = t; q < kb; q += blockDim.x) {
-        double s = 1.0;
-        for (int b = 0; b < nparts; ++b) s += part[b * ldpart + q];
-        lsum[q] = s;
-    }
-    __syncthreads();
-    if (t == 0) {
-        for (int w = 1; w < nw; ++w) m = fmax(m, red[w]);
-        double um = fmax(st->umax, m);
-        st->umax = um;
-        double M = st->amax > um ? st->amax : um;
-        double tau = tau_scale * 8.0;
-        tau *= 0x1p-53;
-        tau *= (double)n;
-        tau *= (double)g;
-        tau *= M;
+    const double um = st->umax;
+    const double M = st->amax > um ? st->amax : um;
+    double tau = tau_scale * 8.0;
+    tau *= 0x1p-53;
+    tau *= (double)n;
+    tau *= (double)g;
+    tau *= M;
+    if (blockIdx.x == 0 && t == 0) {
         st->tau = tau;
         // fixed-point bound of the verify sums: 16 max(|a|, |u| so far); a tile
         // holding an entry above it (growth beyond that, an injected error) is
@@ -476,22 +483,29 @@ __global__ void __launch_bounds__(512) k_lu_pd_check(const double* P, int64_t ld
         const int ve = (int)((__double_as_longlong(bnd) >> 52) & 0x7ff);
         st->vexp = (bnd > 0.0 && bnd < 1e300 && ve >= kFixedMinExp) ? ve : 0;
     }
-    __syncthreads();
     if (mode == MODE_NONE) return;
-    const double tau = st->tau;
-    for (int j = warp; j < kb; j += nw) {
-        double y = 0.0;
-        for (int q = lane; q <= j; q += 32) y = fma(lsum[q], P[(int64_t)q * lda + j], y);
+    if ((int)blockIdx.x < nchk) {
+        for (int q = t; q < kb; q += blockDim.x) {
+            double s = 1.0;
+            for (int b = 0; b < nparts; ++b) s += part[b * ldpart + q];
+            lsum[q] = s;
+        }
+        __syncthreads();
+        for (int j = (int)blockIdx.x * nw + warp; j < kb; j += nchk * nw) {
+            double y = 0.0;
+            for (int q = lane; q <= j; q += 32) y = fma(lsum[q], P[(int64_t)q * lda + j], y);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-        if (lane == 0) {
-            double d = y - ptot[j];
-            if (!(fabs(d) <= tau)) {
-                atomicAdd(&st->detected, 1ull);
-                atomicAdd(&st->uncorrectable, 1ull);
-                record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane == 0) {
+                double d = y - ptot[j];
+                if (!(fabs(d) <= tau)) {
+                    atomicAdd(&st->detected, 1ull);
+                    atomicAdd(&st->uncorrectable, 1ull);
+                    record_event(st, step, EV_PD, K0 + j, K0 + j, d);
+                }
             }
         }
+        return;
     }
     // z = L^{-T} 1, zw = L^{-T} w (unit upper L^T), chunks of 32 from the end
     for (int p = t; p < kb; p += blockDim.x) { tz[p] = 1.0; tw[p] = (double)(p + 1); }
@@ -781,8 +795,15 @@ cudaError_t launch_lu_pd_check(const double* P, int64_t lda, int64_t kb, const d
                                const double* part, int64_t ldpart, int nparts, int step,
                                int64_t K0, int64_t n, int64_t g, double tau_scale, double* z,
                                double* zw, int mode, DevStatus* st, cudaStream_t s) {
-    k_lu_pd_check<<<1, 512, 0, s>>>(P, lda, (int)kb, ptot, part, ldpart, nparts, step, K0, n, g,
-                                    tau_scale, z, zw, mode, st);
+    const int64_t els = kb * kb;
+    k_lu_umax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (els + 255) / 256)), 256, 0,
+                s>>>(P, lda, (int)kb, st);
+    note_launch();
+    // columns over nchk CTAs of 16 warps (one column per warp), one more CTA for z
+    const int nchk = (int)std::max<int64_t>(1, (kb + 15) / 16);
+    k_lu_pd_check<<<(unsigned)(nchk + 1), 512, 0, s>>>(P, lda, (int)kb, ptot, part, ldpart, nparts,
+                                                       step, K0, n, g, tau_scale, z, zw, mode, st,
+                                                       nchk);
     note_launch();
     return cudaGetLastError();
 }
