@@ -115,3 +115,31 @@ def test_full_size_sampled(n):
         u = cols[t].copy(); u[j + 1:] = 0.0
         recon[t] = float(np.dot(l[:min(i, j) + 1], u[:min(i, j) + 1]))
     assert np.abs(recon - PA).max() <= 1e-12 * n
+
+
+@pytest.mark.parametrize("n,nb", [(64, 32), (96, 32)])
+def test_growth_beyond_fixed_point_bound(n, nb):
+    # Wilkinson's growth example: unit diagonal, -1 below it, ones in the last
+    # column.  Partial pivoting keeps the diagonal (ties go to the first row),
+    # the last column doubles at every step (u_in = 2^i), and every entry of
+    # the factors is a power of two or +-1, so both sides are exact.  The
+    # entries soon exceed the fixed-point bound of the verify sums (16 times
+    # the largest |a| and |u| seen so far), so those tiles are summed in FP64.
+    A = np.tril(-np.ones((n, n)), -1) + np.eye(n)
+    A[:, -1] = 1.0
+    for mode in (oracle.SINGLE, oracle.FULL):
+        LUo, ipo, info_o, rep_o = oracle.getrf(A, nb, mode)
+        rc, LU, ip, rep = gpu_getrf(A, nb, mode)
+        assert rc == 0 and info_o == 0
+        assert np.array_equal(ip, ipo) and np.array_equal(LU, LUo)
+        assert LU[-1, -1] == 2.0 ** (n - 1)
+        assert rep["detected"] == 0
+        # an error in the growing last column, where the tile's sums run in FP64
+        f = [(0, oracle.F_MEMORY, 50, n - 1, 2.0 ** 48)]
+        LUo, ipo, _, rep_o = oracle.getrf(A, nb, mode, f)
+        rc, LU, ip, rep = gpu_getrf(A, nb, mode, f)
+        assert events(rep) == events(rep_o)
+        for key in ("detected", "corrected", "uncorrectable"):
+            assert rep[key] == rep_o[key], key
+        if rep_o["uncorrectable"] == 0:
+            assert np.array_equal(ip, ipo) and np.array_equal(LU, LUo)
