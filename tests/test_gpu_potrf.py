@@ -185,3 +185,30 @@ def test_n4096_every_entry_vs_oracle():
         assert rc == 0 and info_o == 0
         assert events(rep) == events(rep_o)
         assert np.abs(np.tril(T.cpu().numpy()) - Lo).max() <= 1e-12 * np.abs(Lo).max()
+
+
+@pytest.mark.parametrize("mode", [oracle.SINGLE, oracle.FULL])
+def test_zero_and_subnormal_entries(mode):
+    # A block-diagonal SPD matrix (exact zeros between the blocks) with subnormal
+    # couplings in some entries: the verify's fixed-point conversion reads zeros
+    # and subnormals below one unit of its bound; the sums, the (absent) events
+    # and the factor must agree with the oracle, and an error is still located.
+    n, nb = 256, 64
+    r = W.rng(77)
+    A = np.zeros((n, n))
+    for b in range(0, n, 32):
+        M = r.standard_normal((32, 32))
+        A[b:b + 32, b:b + 32] = M @ M.T / 32 + np.eye(32)
+    idx = r.integers(0, n, size=(40, 2))
+    for i, j in idx:
+        if i != j:
+            A[i, j] = A[j, i] = 3e-310 * (1 + (i % 3))
+    assert np.all(np.linalg.eigvalsh(A) > 0)
+    Lo, info_o, rep_o = oracle.potrf(A, nb, mode)
+    rc, rep, L = gpu_potrf(A, nb, mode)
+    assert rc == 0 and info_o == 0 and rep["detected"] == 0 and rep_o["detected"] == 0
+    assert np.abs(np.tril(L) - np.tril(Lo)).max() <= 1e-13
+    f = [(1, oracle.F_MEMORY, 200, 150, 1.5)]
+    _, _, rep_o = oracle.potrf(A, nb, mode, f)
+    rc, rep, L = gpu_potrf(A, nb, mode, f)
+    assert events(rep) == events(rep_o) and rep["corrected"] == rep_o["corrected"] == 1
