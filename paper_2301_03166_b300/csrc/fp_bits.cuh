@@ -72,6 +72,54 @@ __device__ __forceinline__ float f64_abs_to_f32_trunc(double x) {
     return __uint_as_float(((uint32_t)(e - 896) << 23) | m);
 }
 
+// x rounded to nearest (ties to even) in a 16-bit format with EB exponent bits
+// and MB mantissa bits (BF16: 8, 7; FP16: 5, 10), as its bit pattern, by integer
+// operations on the binary64 fields: normal results keep the top MB bits of the
+// significand and round on the 52 - MB bits below; results below the format's
+// normal range are multiples of its smallest subnormal 2^(1 - bias - MB),
+// rounded the same way (a carry out of the subnormal range gives the smallest
+// normal number, as the encoding implies).  ok = false for NaN, infinities and
+// values that would overflow (the caller converts those on the FP64 pipe).
+template <int EB, int MB>
+__device__ __forceinline__ uint32_t f64_to_small_rn(double x, bool& ok) {
+    constexpr int BIAS = (1 << (EB - 1)) - 1;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sgn = (uint32_t)(b >> 63) << (EB + MB);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    ok = true;
+    if (e == 0) return sgn;                        // zero, FP64 subnormal: below half an ulp
+    if (e == 0x7ff) {
+        ok = false;
+        return 0u;
+    }
+    const int E = e - 1023;
+    const unsigned long long full = (b & 0xfffffffffffffull) | (1ull << 52);
+    int sh;                                        // bits dropped from the 53-bit significand
+    uint32_t ebits;
+    if (E >= 1 - BIAS) {                           // normal in the small format
+        sh = 52 - MB;
+        ebits = (uint32_t)(E + BIAS);
+    } else {                                       // subnormal: units of 2^(1 - BIAS - MB)
+        sh = 52 - MB + (1 - BIAS - E);
+        ebits = 0u;
+        if (sh > 54) return sgn;                   // below half the smallest subnormal
+    }
+    unsigned long long q = full >> sh;
+    const unsigned long long rem = full & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    uint32_t r;
+    if (ebits) {                                   // q in [2^MB, 2^(MB+1)]: hidden bit in q
+        r = (ebits << MB) + (uint32_t)(q - (1ull << MB));
+        if (r >= ((1u << EB) - 1u) << MB) {        // rounded up to infinity
+            ok = false;
+            return 0u;
+        }
+    } else {
+        r = (uint32_t)q;                           // a carry to 2^MB is the smallest normal
+    }
+    return sgn | r;
+}
+
 // a >> s for any s; PTX clamps shift amounts above 31 to 32 (a result of 0)
 __device__ __forceinline__ uint32_t shr_clamp(uint32_t a, uint32_t s) {
     uint32_t d;

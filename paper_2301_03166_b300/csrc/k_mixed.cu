@@ -336,16 +336,25 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
     const int64_t rps = (g + QCL - 1) / QCL;
     const int64_t s0 = (r0 + rank * rps < r1) ? r0 + rank * rps : r1;
     const int64_t s1 = (s0 + rps < r1) ? s0 + rps : r1;
-    double m = 0.0;
+    // the largest |x| by an integer maximum of the bit patterns of |x| (the
+    // order of non-negative doubles), NaN ignored as fmax ignores it: no FP64
+    // pipe instruction per element
+    unsigned long long mbits = 0ull;
     for (int p = t; p < kb; p += 256) {
         for (int64_t r = s0; r < s1; r += 8) {
             double v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = (r + u < s1) ? P[(r + u) * lda + p] : 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) m = fmax(m, fabs(v[u]));
+            for (int u = 0; u < 8; ++u) {
+                unsigned long long a = (unsigned long long)__double_as_longlong(v[u]) &
+                                       0x7fffffffffffffffull;
+                if (a > 0x7ff0000000000000ull) a = 0ull;
+                mbits = a > mbits ? a : mbits;
+            }
         }
     }
+    double m = __longlong_as_double((long long)mbits);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((t & 31) == 0) red[t >> 5] = m;
@@ -382,14 +391,20 @@ __global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(256)
             const double x = use_mul ? scale_f64(P[r * lda + p], -ex) : P[r * lda + p] / sigma;
             double xq;
             uint16_t bits;
+            bool okr;
+            // round to nearest even in 16 bits by integer operations (the
+            // conversion instruction runs on the FP64 pipe); NaN, infinities
+            // and overflow take the instruction
             if (BF16) {
-                __nv_bfloat16 h = __double2bfloat16(x);
-                bits = __bfloat16_as_ushort(h);
-                xq = f32_to_f64_exact(__bfloat162float(h));
+                uint32_t b16 = f64_to_small_rn<8, 7>(x, okr);
+                if (!okr) b16 = __bfloat16_as_ushort(__double2bfloat16(x));
+                bits = (uint16_t)b16;
+                xq = f32_to_f64_exact(__uint_as_float(b16 << 16));
             } else {
-                __half h = __double2half(x);
-                bits = __half_as_ushort(h);
-                xq = f32_to_f64_exact(__half2float(h));
+                uint32_t b16 = f64_to_small_rn<5, 10>(x, okr);
+                if (!okr) b16 = __half_as_ushort(__double2half(x));
+                bits = (uint16_t)b16;
+                xq = f32_to_f64_exact(__half2float(__ushort_as_half((unsigned short)b16)));
             }
             Lq[(r - T0) * kb + p] = bits;
             s += xq;
