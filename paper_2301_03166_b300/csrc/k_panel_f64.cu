@@ -111,21 +111,7 @@ __global__ void __launch_bounds__(TT) k_trsm_rlt(TrsmArgs a) {
     const int nb = a.nb, t = threadIdx.x;
     for (int e = t; e < RB * nb; e += TT) {
         int r = e / nb, p = e % nb;
-        T xv = (T)0;
-        if (r < nr) {
-            const double b = g.B[(r0 + r) * g.ldb + p];
-            if (std::is_same<T, float>::value) {
-                // FP64 -> FP32 rounding by integer operations (the conversion
-                // instruction runs on the FP64 pipe); NaN, infinities, overflow
-                // take the instruction
-                bool ok;
-                const uint32_t fb = f64_to_small_rn<8, 23>(b, ok);
-                xv = ok ? (T)__uint_as_float(fb) : (T)b;
-            } else {
-                xv = (T)b;
-            }
-        }
-        X[r * ldx + p] = xv;
+        X[r * ldx + p] = (r < nr) ? (T)g.B[(r0 + r) * g.ldb + p] : (T)0;
     }
     __syncthreads();
     if (a.v != nullptr && s == 0) {  // carried row sums x = B v, before the solve
