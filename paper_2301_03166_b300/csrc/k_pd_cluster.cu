@@ -16,7 +16,8 @@
 //      division by L_jj is a multiplication by its reciprocal, formed once per
 //      tile (one FP64 division per column instead of one per row: on B300 a
 //      dependent FP64 division costs hundreds of clocks; the reciprocals of the
-//      power-of-two pivots of exact integer cases are exact);
+//      power-of-two pivots of exact integer cases are exact), folded into the
+//      tile's columns so that each unknown costs one FMA;
 //   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
 //      of 16 rows; operands are fetched from their home CTAs through
 //      distributed shared memory.  Look-ahead: the home CTA of tile
@@ -200,16 +201,25 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             __syncthreads();
             if (t < PT) s_rinv[t] = 1.0 / sD[t * PLD + t];
             __syncthreads();
+            // the columns scaled by 1 / L_jj once per tile (L_lj / L_jj, l > j):
+            // each unknown then costs one FMA in the row's recurrence, not also a
+            // multiplication on one lane (the FP64 pipe charges a warp
+            // instruction whatever its active lanes), and the row is scaled at
+            // the end: y_l -= y_j (L_lj / L_jj), x_l = y_l / L_ll
+            for (int e = t; e < PT * PT; e += PTHREADS) {
+                const int l = e >> 5, j = e & 31;
+                if (l > j) sD[l * PLD + j] *= s_rinv[j];
+            }
+            __syncthreads();
             const int rows = below * PT;
             for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
                 double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
                 double x = X[lane];
                 for (int j = 0; j < PT; ++j) {
-                    if (lane == j) x *= s_rinv[j];
-                    const double xj = __shfl_sync(0xffffffffu, x, j);
-                    if (lane > j) x -= xj * sD[lane * PLD + j];
+                    const double yj = __shfl_sync(0xffffffffu, x, j);
+                    if (lane > j) x -= yj * sD[lane * PLD + j];
                 }
-                X[lane] = x;
+                X[lane] = x * s_rinv[lane];
             }
         }
         cl.sync();
