@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     // (a, b), b <= a, of a trailing triangle in row-major order: the first
     // m (m + 1) / 2 entries are the triangle of order m
     __shared__ unsigned char s_ta[PT * (PT - 1) / 2], s_tb[PT * (PT - 1) / 2];
-    __shared__ double s_sc[PT];
+    __shared__ double s_sc2[2][PT];
     __shared__ double s_sq[PT];
     for (int e = t; e < PT * (PT - 1) / 2; e += PTHREADS) {
         int a = 0;
@@ -114,28 +114,44 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     // right-looking): per pivot one reciprocal of d_j on the dependent chain
     // (an FP64 square root and a division per pivot cost 675 and 431 clocks on
     // B300); the trailing entries take D[i][j] (D[l][j] / d_j), the quotient
-    // formed once per row l.  Then L = L_unit D^(1/2): column j is
-    // D[i][j] / sqrt(d_j), taken as a product with 1 / sqrt(d_j).  A
-    // non-positive d_j fails at the same pivot as the Cholesky recurrence
-    // (d_j is the value under its square root).
+    // formed once per row l.  Look-ahead by one pivot, one barrier per pivot:
+    // while warps 1 .. 7 update the trailing entries of columns l >= j + 2 for
+    // pivot j, warp 0 updates column j + 1, then forms 1 / d_(j+1) and the
+    // quotients of pivot j + 1 (in the other buffer of s_sc), so that the
+    // division overlaps the bulk of the update.  Every entry takes the same
+    // operations in the same order as the plain recurrence.  Then
+    // L = L_unit D^(1/2): column j is D[i][j] / sqrt(d_j), taken as a product
+    // with 1 / sqrt(d_j).  A non-positive d_j fails at the same pivot as the
+    // Cholesky recurrence (d_j is the value under its square root).
     auto factor_diag = [&](int p) {
         const int idp = p * (p + 1) / 2 + p;
         double* D = home + (idp / CL) * TILE;
-        for (int j = 0; j < PT; ++j) {
-            if (t == 0) {
-                const double d = D[j * PLD + j];
-                if (!(d > 0.0)) s_fail = j;
-                else s_rinv[j] = 1.0 / d;
+        // warp 0: the quotients D[l][j] / d_j of pivot j (l > j) into s_sc2[j & 1]
+        auto pivot = [&](int j) {
+            const double d = D[j * PLD + j];
+            if (!(d > 0.0)) {
+                if (lane == 0) s_fail = j;
+                return;
             }
-            __syncthreads();
+            const double rj = 1.0 / d;
+            if (lane > j) s_sc2[j & 1][lane] = D[lane * PLD + j] * rj;
+        };
+        if (warp == 0) pivot(0);
+        __syncthreads();
+        for (int j = 0; j < PT; ++j) {
             if (s_fail >= 0) return;
-            const double rj = s_rinv[j];
-            if (t > j && t < PT) s_sc[t] = D[t * PLD + j] * rj;
-            __syncthreads();
-            const int m = PT - 1 - j;
-            for (int e = t; e < m * (m + 1) / 2; e += PTHREADS) {
-                const int i = j + 1 + s_ta[e], l = j + 1 + s_tb[e];
-                D[i * PLD + l] -= D[i * PLD + j] * s_sc[l];
+            if (j == PT - 1) break;
+            const double* sc = s_sc2[j & 1];
+            if (warp == 0) {
+                if (lane > j) D[lane * PLD + j + 1] -= D[lane * PLD + j] * sc[j + 1];
+                __syncwarp();
+                pivot(j + 1);
+            } else {
+                const int m = PT - 2 - j;                    // columns j + 2 .. PT - 1
+                for (int e = t - 32; e < m * (m + 1) / 2; e += PTHREADS - 32) {
+                    const int i = j + 2 + s_ta[e], l = j + 2 + s_tb[e];
+                    D[i * PLD + l] -= D[i * PLD + j] * sc[l];
+                }
             }
             __syncthreads();
         }
@@ -184,6 +200,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
         C[ci * PLD + l0 + 16] -= acc1;
         __syncthreads();
     };
+    __syncthreads();               // tiles, tables and s_fail seen by the whole CTA
     int fail = -1;
     if (me == 0) factor_diag(0);   // tile 0 lives in CTA 0
     cl.sync();
