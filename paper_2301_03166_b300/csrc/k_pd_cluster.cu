@@ -45,6 +45,7 @@ constexpr int PMAXT = 8;           // tiles per side: kb <= 256
 constexpr int PTHREADS = 256;
 constexpr int PWARPS = PTHREADS / 32;
 constexpr int TILE = PT * PLD;
+static_assert(PT * PT == 4 * PTHREADS, "tile copies take 4 entries per thread");
 
 template <int CL>
 __host__ __device__ constexpr int pd_slots() {
@@ -177,27 +178,56 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
         int a, b;
         tile_of(tid, a, b);
         const int q = p + 1 + a, r = p + 1 + b;
+        // the first 16 rows of a diagonal tile: only columns 0 .. 15 hold the
+        // lower triangle (the strict upper part of a diagonal tile is never read)
+        const bool narrow = a == b && half == 0;
         const double* Lq = tile_ptr(q, p);
         const double* Lr = tile_ptr(r, p);
-        for (int e = t; e < 16 * PT; e += PTHREADS) {
-            const int i = 16 * half + (e >> 5), j = e & 31;
-            sQ[(e >> 5) * PLD + j] = Lq[i * PLD + j];
+        // the remote operands into registers before the first store (stores to
+        // shared memory cannot be moved past loads through cluster-mapped
+        // pointers, so a load-store loop waits for each remote load in turn)
+        double vq[2], vr[4];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = t + k * PTHREADS;
+            vq[k] = Lq[(16 * half + (e >> 5)) * PLD + (e & 31)];
         }
-        for (int e = t; e < PT * PT; e += PTHREADS) sR[(e >> 5) * PLD + (e & 31)] = Lr[(e >> 5) * PLD + (e & 31)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = t + k * PTHREADS;
+            if (k < 2 || !narrow) vr[k] = Lr[(e >> 5) * PLD + (e & 31)];
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = t + k * PTHREADS;
+            sQ[(e >> 5) * PLD + (e & 31)] = vq[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = t + k * PTHREADS;
+            if (k < 2 || !narrow) sR[(e >> 5) * PLD + (e & 31)] = vr[k];
+        }
         __syncthreads();
         double* C = tile_ptr(q, r);
-        // thread: row i (16) x columns l = (t & 15) + 16 c (2)
+        // thread: row i (16) x columns l = (t & 15) + 16 c (2; 1 when narrow)
         const int i = t >> 4, l0 = t & 15;
-        double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll 8
-        for (int k = 0; k < PT; ++k) {
-            const double lq = sQ[i * PLD + k];
-            acc0 = fma(lq, sR[l0 * PLD + k], acc0);
-            acc1 = fma(lq, sR[(l0 + 16) * PLD + k], acc1);
-        }
         const int ci = 16 * half + i;
-        C[ci * PLD + l0] -= acc0;
-        C[ci * PLD + l0 + 16] -= acc1;
+        if (narrow) {
+            double acc0 = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < PT; ++k) acc0 = fma(sQ[i * PLD + k], sR[l0 * PLD + k], acc0);
+            C[ci * PLD + l0] -= acc0;
+        } else {
+            double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < PT; ++k) {
+                const double lq = sQ[i * PLD + k];
+                acc0 = fma(lq, sR[l0 * PLD + k], acc0);
+                acc1 = fma(lq, sR[(l0 + 16) * PLD + k], acc1);
+            }
+            C[ci * PLD + l0] -= acc0;
+            C[ci * PLD + l0 + 16] -= acc1;
+        }
         __syncthreads();
     };
     __syncthreads();               // tiles, tables and s_fail seen by the whole CTA
@@ -214,7 +244,17 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
         // B: rows of the panel tiles below, x L_pp^T = a, one warp per row
         {
             const double* Dr = tile_ptr(p, p);
-            for (int e = t; e < PT * PT; e += PTHREADS) sD[(e >> 5) * PLD + (e & 31)] = Dr[(e >> 5) * PLD + (e & 31)];
+            double vd[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = t + k * PTHREADS;
+                vd[k] = Dr[(e >> 5) * PLD + (e & 31)];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = t + k * PTHREADS;
+                sD[(e >> 5) * PLD + (e & 31)] = vd[k];
+            }
             __syncthreads();
             if (t < PT) s_rinv[t] = 1.0 / sD[t * PLD + t];
             __syncthreads();
