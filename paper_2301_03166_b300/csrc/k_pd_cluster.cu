@@ -13,11 +13,12 @@
 //      the column scalings by their reciprocals at the end);
 //   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
 //      per row (lane l holds x_l), spread over every warp of the cluster; the
-//      division by L_jj is a multiplication by its reciprocal, formed once per
-//      tile (one FP64 division per column instead of one per row: on B300 a
-//      dependent FP64 division costs hundreds of clocks; the reciprocals of the
-//      power-of-two pivots of exact integer cases are exact), folded into the
-//      tile's columns so that each unknown costs one FMA;
+//      division by L_jj is a multiplication by its reciprocal (one FP64
+//      division per column instead of one per row: on B300 a dependent FP64
+//      division costs hundreds of clocks; the reciprocals of the power-of-two
+//      pivots of exact integer cases are exact), folded into the tile's
+//      columns (L_lj / L_jj) so that each unknown costs one FMA; the home CTA
+//      forms this operand when it factors the tile, the others copy it;
 //   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
 //      of 16 rows; operands are fetched from their home CTAs through
 //      distributed shared memory.  Look-ahead: the home CTA of tile
@@ -54,7 +55,7 @@ __host__ __device__ constexpr int pd_slots() {
 
 template <int CL>
 constexpr size_t pd_smem() {
-    return sizeof(double) * (size_t)TILE * (pd_slots<CL>() + 3);
+    return sizeof(double) * (size_t)TILE * (pd_slots<CL>() + 4);
 }
 
 __device__ __forceinline__ void tile_of(int id, int& q, int& r) {
@@ -74,8 +75,9 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
     double* sD = pd_sm + pd_slots<CL>() * TILE;        // copy of L(p, p)
     double* sQ = sD + TILE;                            // operand copies for phase C
     double* sR = sQ + TILE;
+    double* sB = sR + TILE;                            // solve operand of the last tile factored here
     __shared__ int s_fail;
-    __shared__ double s_rinv[PT];                      // 1 / L_jj (B); 1 / d_j, then sqrt(d_j) (A)
+    __shared__ double s_rinv[PT];                      // 1 / sqrt(d_j) (A)
     __shared__ double s_cs[PMAXT * PT];
     if (st->info != 0) return;                         // same answer in every CTA
     const int me = (int)cl.block_rank();
@@ -162,12 +164,21 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             s_rinv[t] = 1.0 / sq;
         }
         __syncthreads();
+        // and the operand of the row solves of phase B: L_ij / L_jj below the
+        // diagonal, 1 / L_jj on it
         for (int e = t; e < PT * PT; e += PTHREADS) {
             const int i = e >> 5, jj = e & 31;
-            if (i > jj) D[i * PLD + jj] = D[i * PLD + jj] * s_rinv[jj];
+            if (i > jj) {
+                const double v = D[i * PLD + jj] * s_rinv[jj];
+                D[i * PLD + jj] = v;
+                sB[i * PLD + jj] = v * s_rinv[jj];
+            }
         }
         __syncthreads();
-        if (t < PT) D[t * PLD + t] = s_sq[t];
+        if (t < PT) {
+            D[t * PLD + t] = s_sq[t];
+            sB[t * PLD + t] = s_rinv[t];
+        }
         __syncthreads();
     };
     // C item w of step p: half (w & 1) of the 16-row halves of trailing tile
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
         if (below == 0) break;
         // B: rows of the panel tiles below, x L_pp^T = a, one warp per row
         {
-            const double* Dr = tile_ptr(p, p);
+            const double* Dr = cl.map_shared_rank(sB, (p * (p + 1) / 2 + p) % CL);
             double vd[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -256,18 +267,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
                 sD[(e >> 5) * PLD + (e & 31)] = vd[k];
             }
             __syncthreads();
-            if (t < PT) s_rinv[t] = 1.0 / sD[t * PLD + t];
-            __syncthreads();
-            // the columns scaled by 1 / L_jj once per tile (L_lj / L_jj, l > j):
-            // each unknown then costs one FMA in the row's recurrence, not also a
+            // each unknown costs one FMA in the row's recurrence, not also a
             // multiplication on one lane (the FP64 pipe charges a warp
             // instruction whatever its active lanes), and the row is scaled at
             // the end: y_l -= y_j (L_lj / L_jj), x_l = y_l / L_ll
-            for (int e = t; e < PT * PT; e += PTHREADS) {
-                const int l = e >> 5, j = e & 31;
-                if (l > j) sD[l * PLD + j] *= s_rinv[j];
-            }
-            __syncthreads();
             const int rows = below * PT;
             for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
                 double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
                     const double yj = __shfl_sync(0xffffffffu, x, j);
                     if (lane > j) x -= yj * sD[lane * PLD + j];
                 }
-                X[lane] = x * s_rinv[lane];
+                X[lane] = x * sD[lane * PLD + lane];
             }
         }
         cl.sync();
