@@ -133,6 +133,26 @@ def test_not_spd_info():
     assert rc == info_o == 218 and rep["info"] == 218
 
 
+@pytest.mark.parametrize("dtype", [abft.F64, abft.MIXED_BF16, abft.F64_EMU])
+@pytest.mark.parametrize("pos", [0, 31, 32, 255, 256, 287, 288, 319, 511])
+def test_not_spd_info_at_tile_boundaries(dtype, pos):
+    """The diagonal block is factored in 32 x 32 tiles, each with a one-pivot
+    look-ahead (the next pivot's reciprocal is formed while the current one's
+    update runs): a negative pivot at the first or last pivot of a tile, of a
+    block or of the matrix is reported at its own index (the oracle pins it,
+    since d_pos = A[pos, pos] - |L[pos, :pos]|^2 < 0 and the earlier pivots
+    are untouched), in every form of the trailing update."""
+    n, nb = 512, 256
+    A = W.spd_mmt(n, 7)
+    A[pos, pos] = -5.0
+    _, info_o, _ = oracle.potrf(A, nb, oracle.FULL)
+    assert info_o == pos + 1
+    T = torch.from_numpy(np.ascontiguousarray(A)).to(DEV)
+    rc, rep = abft.potrf(T, nb, abft.FULL, dtype=dtype)
+    torch.cuda.synchronize()
+    assert rc == info_o and rep["info"] == info_o
+
+
 def test_invalid_arguments():
     T = torch.eye(64, dtype=torch.float64, device=DEV)
     with pytest.raises(abft.AbftError):
