@@ -272,14 +272,39 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_potrf_pd_cluster(double* A, int
             // instruction whatever its active lanes), and the row is scaled at
             // the end: y_l -= y_j (L_lj / L_jj), x_l = y_l / L_ll
             const int rows = below * PT;
-            for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
-                double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
-                double x = X[lane];
-                for (int j = 0; j < PT; ++j) {
-                    const double yj = __shfl_sync(0xffffffffu, x, j);
-                    if (lane > j) x -= yj * sD[lane * PLD + j];
+            if (rows > CL * PWARPS) {
+                // more rows than warps: two rows per warp, one per half-warp,
+                // lane h holding unknowns h and 16 + h; the terms of the lower
+                // half's unknowns reach the upper half as each is found (one
+                // chain of 32 steps for both rows, 48 FMA instructions instead
+                // of 64; every unknown takes its terms in the same order)
+                const int h = lane & 15, hs = lane & 16;
+                for (int pr = me * PWARPS + warp; 2 * pr < rows; pr += CL * PWARPS) {
+                    const int gr = 2 * pr + (lane >> 4);       // rows is even: gr < rows
+                    double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
+                    double ya = X[h], yb = X[16 + h];
+                    for (int j = 0; j < 16; ++j) {
+                        const double yj = __shfl_sync(0xffffffffu, ya, hs | j);
+                        if (h > j) ya -= yj * sD[h * PLD + j];
+                        yb -= yj * sD[(16 + h) * PLD + j];
+                    }
+                    for (int j = 0; j < 16; ++j) {
+                        const double yj = __shfl_sync(0xffffffffu, yb, hs | j);
+                        if (h > j) yb -= yj * sD[(16 + h) * PLD + 16 + j];
+                    }
+                    X[h] = ya * sD[h * PLD + h];
+                    X[16 + h] = yb * sD[(16 + h) * PLD + 16 + h];
                 }
-                X[lane] = x * sD[lane * PLD + lane];
+            } else {
+                for (int gr = me * PWARPS + warp; gr < rows; gr += CL * PWARPS) {
+                    double* X = tile_ptr(p + 1 + gr / PT, p) + (gr % PT) * PLD;
+                    double x = X[lane];
+                    for (int j = 0; j < PT; ++j) {
+                        const double yj = __shfl_sync(0xffffffffu, x, j);
+                        if (lane > j) x -= yj * sD[lane * PLD + j];
+                    }
+                    X[lane] = x * sD[lane * PLD + lane];
+                }
             }
         }
         cl.sync();
