@@ -9,10 +9,12 @@
 // home CTA id % CL, slot id / CL; rows past kb are the identity) and factored
 // right-looking by tile columns p = 0 .. NT - 1:
 //   A  the home CTA of tile (p, p) factors it square-root free (L D L^T, one
-//      reciprocal per pivot on the dependent chain; the 32 square roots and
-//      the column scalings by their reciprocals at the end);
+//      reciprocal per pivot on the dependent chain, formed while the other
+//      warps apply the previous pivot; the 32 square roots and the column
+//      scalings by their reciprocals at the end);
 //   B  the rows of the tiles (q, p), q > p, are solved against it, one warp
-//      per row (lane l holds x_l), spread over every warp of the cluster; the
+//      per row (lane l holds x_l), or two rows per warp when there are more
+//      rows than warps, spread over every warp of the cluster; the
 //      division by L_jj is a multiplication by its reciprocal (one FP64
 //      division per column instead of one per row: on B300 a dependent FP64
 //      division costs hundreds of clocks; the reciprocals of the power-of-two
@@ -20,7 +22,8 @@
 //      columns (L_lj / L_jj) so that each unknown costs one FMA; the home CTA
 //      forms this operand when it factors the tile, the others copy it;
 //   C  the trailing tiles C(q, r) -= L(q, p) L(r, p)^T, p < r <= q, in halves
-//      of 16 rows; operands are fetched from their home CTAs through
+//      of 16 rows (the first half of a diagonal tile in its lower 16 columns
+//      only); operands are fetched from their home CTAs through
 //      distributed shared memory.  Look-ahead: the home CTA of tile
 //      (p + 1, p + 1) updates that tile first and factors it (A of the next
 //      step) while the other CTAs share the rest of the tiles.
